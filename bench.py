@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ST-HOSVD (Algorithm 1) on the combustion-shaped workload.
+
+One step = one full ST-HOSVD (norm, then per mode: Gram, Jacobi eigensolve,
+rank rule, TTM) of the 5-way float64 tensor 128 x 128 x 128 x 48 x 32
+(space^3 x variables x time, 25.8 GB, Tucker ranks (40,40,40,20,10) with a
+decaying core, smoothed factors and 1e-6 noise) at eps = 1e-5, with the
+tensor resident in HBM.  The metric is input GB/s (bytes of X per second of
+tucker_sthosvd); the Gram step's TFLOP/s (symmetric count J(J+1) L B) is
+reported beside it.  The input (25.8 GB) is far larger than the 129 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+single-tensor method has an all-reduce in every Gram, so it is not sharded.
+--impl reference times the CPU oracle on the host cores on a bounded sample
+(a prefix of the time mode) of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ST-HOSVD input GB/s & Gram TFLOP/s, split-prec vs FP64 on GB300, equal rel. error"
+WORKLOAD = "combustion5"
+# Float64 pipe peak of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# ncu DRAM traffic of the Gram kernel (read + write bytes per launch), keyed by
+# the hash of the kernel source it was captured with; see profiles/.
+TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1510_06689_gb300", "csrc", "kernels_f64.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--eps", type=float, default=1e-5)
+    p.add_argument("--cpu-slices", type=int, default=8, help="time slices in the CPU oracle sample")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        mx = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        power = [num(s[2]) for s in self.samples if num(s[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_oracle_sample(w, eps, slices, x_host=None):
+    """Times the CPU oracle once on the first `slices` time slices; returns (GB/s, seconds, dims)."""
+    import numpy as np
+
+    import oracle
+    from synthetic import tucker_prefix_np
+
+    if x_host is None:
+        x, dims = tucker_prefix_np(w.dims, w.ranks, slices, seed=0, decay=w.decay, smooth=w.smooth, noise=w.noise)
+    else:
+        dims = w.dims[:-1] + (slices,)
+        x = np.asarray(x_host[: math.prod(dims)])
+    t0 = time.perf_counter()
+    oracle.sthosvd(x, dims, eps)
+    dt = time.perf_counter() - t0
+    return x.nbytes / dt / 1e9, dt, dims
+
+
+def reference_main(args):
+    """CPU oracle on the host cores (rank 0 only), same metric and config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synthetic import WORKLOADS, tucker_prefix_np
+
+    import oracle
+
+    w = WORKLOADS[WORKLOAD]
+    slices = max(1, min(w.dims[-1], args.cpu_slices // 2))
+    x, dims = tucker_prefix_np(w.dims, w.ranks, slices, seed=0, decay=w.decay, smooth=w.smooth, noise=w.noise)
+    for _ in range(args.warmup):
+        oracle.sthosvd(x, dims, args.eps)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sthosvd(x, dims, args.eps)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = x.nbytes / t / 1e9
+    sample = f"first {slices} of {w.dims[-1]} time slices ({x.nbytes / 1e9:.2f} GB), numpy/OpenBLAS float64 oracle"
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, args.eps, "oracle"),
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, eps, precision):
+    return {
+        "workload": f"{w.name}: {'x'.join(map(str, w.dims))} float64 Tucker-form tensor, ranks "
+                    f"{tuple(w.ranks)}, core decay exp(-{w.decay} sum i), smoothed factors, noise {w.noise}",
+        "eps": eps, "mode_order": "1,2,3,4,5", "precision": precision,
+        "input_bytes": w.nbytes, "l2_policy": "input 25.8 GB >> 129 MB L2 (no flush needed)",
+        "parallelism": "replicas (one independent tensor per GPU)",
+    }
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+    import numpy as np
+    import torch
+
+    from paper_1510_06689_gb300 import tucker
+    from synthetic import WORKLOADS, tucker_tensor_torch
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if rank == 0 and not os.path.exists(tucker.LIB_PATH):
+        from paper_1510_06689_gb300 import build
+
+        build.build()
+    barrier(world)
+    tucker.load()
+    w = WORKLOADS[WORKLOAD]
+    dims = w.dims
+    x = tucker_tensor_torch(dims, w.ranks, seed=rank, decay=w.decay, smooth=w.smooth, noise=w.noise,
+                            device="cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        res = tucker.sthosvd(x, dims, args.eps)
+        res.free()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    tucker.profile_enable(True)
+    launches0 = tucker.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ranks = None
+    for _ in range(args.steps):
+        res = tucker.sthosvd(x, dims, args.eps)
+        ranks = res.ranks
+        res.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.stop()
+    launches = tucker.launch_count() - launches0
+    prof = tucker.profile_read()
+    tucker.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(world, ms)
+    value = world * w.nbytes / (ms / 1e3) / 1e9
+
+    # accuracy of the timed configuration (outside the timed region)
+    res = tucker.sthosvd(x, dims, args.eps)
+    rel = tucker.rel_error(x, res)
+    res.free()
+
+    gram = prof["gram"]
+    gram_tflops = gram["flops"] / (gram["ms"] / 1e3) / 1e12 if gram["ms"] > 0 else None
+    per_launch_ms = gram["ms"] / max(gram["launches"], 1)
+    per_launch_flops = gram["flops"] / max(gram["launches"], 1)
+    step_ms_sum = sum(v["ms"] for v in prof.values()) / args.steps
+    shares = {k: round(v["ms"] / args.steps / ms, 4) for k, v in prof.items()}
+    traffic = TRAFFIC.get(kernel_source_hash())
+    roofline = {
+        "kernel": "k_gram_partial (float64 split-K symmetric Gram)",
+        "bound": "alu", "achieved": round(per_launch_flops / (per_launch_ms / 1e3) / 1e12, 4),
+        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+        "frac": round(per_launch_flops / (per_launch_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+        "traffic": traffic,
+        "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 1.25 TFLOP/s; "
+                       "measured DFMA loop 1.193 TFLOP/s)",
+        "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4),
+    }
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, "fp64"),
+        "gram_tflops": round(gram_tflops, 4) if gram_tflops else None,
+        "ranks": list(ranks), "rel_error": rel,
+        "phase_share": shares, "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
+        "phase_time_covered": round(step_ms_sum / ms, 4),
+        "roofline": roofline, "gpu_launches": launches, "clocks": sampler.summary(),
+    }
+
+    # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
+    if not args.no_e2e:
+        xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
+        xh.copy_(x)
+        del x
+        torch.cuda.empty_cache()
+        r = tucker.sthosvd_host(xh, dims, args.eps)
+        d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)) + sum(d + 3 for d in dims) + 1)
+        r.free()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = tucker.sthosvd_host(xh, dims, args.eps)
+            r.free()
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        t_e2e = max_over_ranks(world, t_e2e)
+        line["e2e"] = {"value": round(world * w.nbytes / t_e2e / 1e9, 4), "unit": "GB/s",
+                       "h2d_bytes_per_step": w.nbytes, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": round(t_e2e * 1e3, 3)}
+    else:
+        xh = None
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        src = xh if xh is not None else x.cpu()
+        gbs, secs, sdims = run_oracle_sample(w, args.eps, min(args.cpu_slices, w.dims[-1]),
+                                             x_host=src.numpy())
+        line["cpu_baseline"] = {
+            "value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {sdims[-1]} of {w.dims[-1]} time slices of the same tensor "
+                      f"({math.prod(sdims) * 8 / 1e9:.2f} GB), one oracle ST-HOSVD in {secs:.2f} s "
+                      f"(numpy/OpenBLAS float64 on all host cores)",
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * tucker.h -- C ABI of the GB300 (sm_103a) ST-HOSVD library.
+ *
+ * The library computes the sequentially-truncated HOSVD of Algorithm 1
+ * (Sec. 2.2): for each mode n in turn it forms the Gram matrix
+ * S = Y_(n) Y_(n)^T of the current tensor, eigendecomposes it, keeps the
+ * R_n leading eigenvectors with R_n chosen by the error rule
+ * sum_{r>R} lambda_r <= eps^2 ||X||^2 / N, and shrinks the tensor with the
+ * mode-n product Y <- Y x_n U_n^T.  Every step runs in this library's own
+ * CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Tensors are dense and stored in *natural layout*: element
+ *   (i_1, ..., i_N) (0-based) sits at offset i_1 + I_1 (i_2 + I_2 (i_3 + ...)),
+ *   i.e. the mode-1 unfolding is column-major (Sec. 3.1).  At mode n the
+ *   library views a tensor of current dimensions J_1..J_N as the 3-D array
+ *   (L, J_n, B) with L = prod_{m<n} J_m (fastest) and B = prod_{m>n} J_m;
+ *   entry (l, j, b) is at l + L (j + J_n b).  This is the unfolding of
+ *   Sec. 2.1 read in place: no data is moved.
+ * - Matrices (factors, Gram matrices, eigenvector matrices) are column-major.
+ * - Sizes are int64_t; mode numbers and mode orders are 0-based.
+ * - "device" pointers are CUDA global-memory pointers on the current device;
+ *   "host" pointers are ordinary (ideally pinned) host memory.
+ * - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call is stream-ordered on it; calls that return results on the host
+ *   synchronise that stream before returning.
+ * - Inputs are never modified.  Errors are reported only through the returned
+ *   tucker_status (never by exceptions, exit() or a device trap); the text of
+ *   the last error of the calling thread is available from tucker_last_error().
+ * - Device kernels contain no unbounded waits: the only iterative kernel (the
+ *   Jacobi eigensolver) stops after a fixed number of sweeps and reports
+ *   TUCKER_ENOCONV.
+ */
+#ifndef TUCKER_GB300_H
+#define TUCKER_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TUCKER_API __attribute__((visibility("default")))
+#else
+#define TUCKER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUCKER_MAX_MODES 16
+/* Largest mode length the eigensolver accepts (the paper assumes I_n <= 2000,
+ * Sec. 2.2; the Gram-plus-eigensolver route is the paper's choice there). */
+#define TUCKER_MAX_DIM 1024
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_EINVAL = -1,      /* invalid argument (null pointer, size, NaN eps, bad order) */
+  TUCKER_ENOMEM = -2,      /* device or pinned host allocation failed */
+  TUCKER_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+  TUCKER_ENOCONV = -4,     /* Jacobi eigensolver hit its sweep cap */
+  TUCKER_ETIMEOUT = -5,    /* reserved: a bounded device wait expired */
+  TUCKER_ENONFINITE = -6,  /* input holds Inf/NaN (||X||^2 is not finite) */
+  TUCKER_EUNSUPPORTED = -7 /* valid request this build does not implement */
+} tucker_status;
+
+/* Element type of an input tensor.  Internal tensors are always float64. */
+typedef enum { TUCKER_F64 = 0, TUCKER_F32 = 1 } tucker_dtype;
+
+/* Arithmetic of the Gram step.  TUCKER_PREC_FP64 is the plain method. */
+typedef enum { TUCKER_PREC_FP64 = 0 } tucker_precision;
+
+/* Result of an ST-HOSVD (Algorithm 1's output (G, {U_n}) plus diagnostics).
+ * Owned by the library; release with tucker_result_free(). */
+typedef struct tucker_result {
+  int N;                              /* number of modes */
+  int on_host;                        /* 0: core/factors are device pointers; 1: host */
+  int64_t dims[TUCKER_MAX_MODES];     /* I_n */
+  int64_t ranks[TUCKER_MAX_MODES];    /* R_n chosen by the error rule */
+  int mode_order[TUCKER_MAX_MODES];   /* order in which the modes were processed */
+  int sweeps[TUCKER_MAX_MODES];       /* Jacobi sweeps used per mode */
+  double *core;                       /* prod(R_n) float64, natural layout, mode positions as in X */
+  double *factors[TUCKER_MAX_MODES];  /* U_n: I_n x R_n float64, column-major, orthonormal columns */
+  double *eigvals[TUCKER_MAX_MODES];  /* host: the I_n eigenvalues of S_n, descending */
+  double tail[TUCKER_MAX_MODES];      /* discarded eigenvalue sum per mode (clamped at 0) */
+  double norm2_x;                     /* ||X||^2 */
+  double threshold;                   /* eps^2 ||X||^2 / N (0 when eps <= 0) */
+  void *priv;                         /* library bookkeeping; do not touch */
+} tucker_result;
+
+/*
+ * tucker_sthosvd -- Algorithm 1 (ST-HOSVD), Sec. 2.2.
+ *   X          device, prod(dims) elements of type dt, natural layout; read only.
+ *   dims, N    I_1..I_N, 1 <= N <= TUCKER_MAX_MODES, 1 <= I_n <= TUCKER_MAX_DIM.
+ *   eps        relative error target (not squared).  eps <= 0 keeps every index
+ *              (R_n = I_n); NaN is rejected.  R_n is the smallest R in [1, J_n]
+ *              with sum_{r>R} max(lambda_r, 0) <= eps^2 ||X||^2 / N, where ||X|| is
+ *              the norm of the original X (Algorithm 1; Sec. 6.2).
+ *   mode_order 0-based permutation of 0..N-1 giving the processing order, or NULL
+ *              for 0..N-1 ("the modes can be processed in any arbitrary order",
+ *              Sec. 2.2).  The core keeps the original mode positions.
+ *   prec       arithmetic of the Gram step (TUCKER_PREC_FP64).
+ *   out        filled on success with device-resident core and factors
+ *              (stream-ordered allocations) and host eigenvalues.
+ * Synchronises `stream` once per mode (the rank decides the next launch shape).
+ * Returns TUCKER_OK, EINVAL, ENOMEM, ECUDA, ENOCONV or ENONFINITE; on error
+ * `out` holds nothing that needs freeing.
+ */
+TUCKER_API int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                   const int *mode_order, tucker_precision prec, void *stream, tucker_result *out);
+
+/*
+ * tucker_sthosvd_host -- the same computation for a tensor in host memory.
+ * Copies X_host (pinned memory recommended) to the device on `stream`, runs
+ * tucker_sthosvd, and returns the core and factors in library-allocated host
+ * memory (out->on_host = 1).  Device buffers are released before returning.
+ */
+TUCKER_API int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                        const int *mode_order, tucker_precision prec, void *stream, tucker_result *out);
+
+/*
+ * tucker_reconstruct -- X~ = G x_1 U_1 ... x_N U_N (Eq. reconstruct, Sec. 2.3).
+ *   r     a device-resident result (r->on_host == 0).
+ *   Xhat  device, caller-allocated, prod(r->dims) float64, natural layout.
+ * Uses stream-ordered temporaries for the partial expansions.
+ */
+TUCKER_API int tucker_reconstruct(const tucker_result *r, double *Xhat, void *stream);
+
+/*
+ * tucker_rel_error -- ||X - X~|| / ||X|| (the normalised RMS error of Sec. 6.2).
+ * X~ is never materialised: the last mode's expansion is fused with reading X
+ * and accumulating (x - x~)^2 in float64.  rel_out is a host double.
+ * Returns 0 for X = 0 = X~, +Inf for X = 0 != X~.  Synchronises `stream`.
+ */
+TUCKER_API int tucker_rel_error(const void *X, tucker_dtype dt, const tucker_result *r, double *rel_out, void *stream);
+
+/* Release everything a tucker_result owns (device and host) and zero it.
+ * Safe on a zeroed struct.  Synchronises the device if device memory is freed. */
+TUCKER_API void tucker_result_free(tucker_result *r);
+
+/* ---------------------------------------------------------------------------
+ * The steps of Algorithm 1 as separate calls (same kernels as tucker_sthosvd).
+ * ------------------------------------------------------------------------- */
+
+/* ||X||^2 = sum of squares of n elements (Sec. 2.1), float64 accumulation in a
+ * fixed order (run-to-run identical).  X may be NULL when n == 0.  out is a
+ * host double; synchronises. */
+TUCKER_API int tucker_norm2(const void *X, tucker_dtype dt, int64_t n, double *out, void *stream);
+
+/* Gram step of Algorithm 1: S = Y_(n) Y_(n)^T for Y viewed as (L, J, B):
+ * S[i + J j] = sum_{b<B} sum_{l<L} Y[l + L(i + J b)] Y[l + L(j + J b)].
+ *   Y  device, L*J*B elements of type dt.   S  device, J*J float64, written in
+ *   full (both triangles, exactly symmetric).  J <= TUCKER_MAX_DIM. */
+TUCKER_API int tucker_gram(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream);
+
+/* Eigenvector step of Algorithm 1: all eigenpairs of the symmetric J x J matrix S
+ * (device, column-major; only its upper triangle is read) by cyclic Jacobi in
+ * float64 with a parallel (round-robin) rotation order.
+ *   lam  device, J values, descending (ties keep the lower index first).
+ *   V    device, J*J column-major; column r is the eigenvector of lam[r], signed so
+ *        that its largest-magnitude entry is positive (lowest row on ties).
+ *   sweeps  host int (may be NULL): sweeps used.  Synchronises; returns
+ *   TUCKER_ENOCONV after the sweep cap. */
+TUCKER_API int tucker_eig(const double *S, int64_t J, double *lam, double *V, int *sweeps, void *stream);
+
+/* Rank step of Algorithm 1: smallest R in [1, J] with sum_{r>R} max(lam[r], 0) <=
+ * threshold, tails summed from the smallest eigenvalue upward; keep_all != 0
+ * returns R = J.  lam is device (descending); R and tail are host; synchronises. */
+TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, int keep_all, int64_t *R, double *tail,
+                    void *stream);
+
+/* TTM step of Algorithm 1 (Sec. 2.1 mode-n product): Z = Y x_n M with Y viewed as
+ * (L, J, B) and Z as (L, K, B): Z[l + L(k + K b)] = sum_j M[k, j] Y[l + L(j + J b)].
+ *   M is given column-major as either K x J (trans_m == 0, M[k,j] = Mp[k + K j]) or
+ *   J x K and used transposed (trans_m != 0, M[k,j] = Mp[j + J k]; pass U_n with
+ *   trans_m = 1 for the shrinking product Y x_n U_n^T).
+ *   Y device (dt), M device float64, Z device float64 with L*K*B elements. */
+TUCKER_API int tucker_ttm(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *M, int64_t K,
+               int trans_m, double *Z, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics.
+ * ------------------------------------------------------------------------- */
+
+TUCKER_API const char *tucker_status_string(int status);
+/* Message of the last failing call on this thread ("" if none). */
+TUCKER_API const char *tucker_last_error(void);
+/* Number of kernels this library has launched in this process. */
+TUCKER_API int64_t tucker_launch_count(void);
+
+/* Per-phase device timing with CUDA events recorded on the caller's stream. */
+typedef enum {
+  TUCKER_PHASE_NORM = 0,
+  TUCKER_PHASE_GRAM = 1,   /* the Gram split-K kernel (partials) */
+  TUCKER_PHASE_GRAM_REDUCE = 2,
+  TUCKER_PHASE_EIG = 3,
+  TUCKER_PHASE_RANK = 4,
+  TUCKER_PHASE_TTM = 5,
+  TUCKER_PHASE_COUNT = 6
+} tucker_phase;
+
+typedef struct tucker_profile {
+  double ms[TUCKER_PHASE_COUNT];       /* summed kernel time per phase */
+  int64_t launches[TUCKER_PHASE_COUNT];
+  double flops[TUCKER_PHASE_COUNT];    /* algorithmic flops (Gram: J(J+1) L B, symmetric count;
+                                          TTM: 2 J K L B) */
+  double bytes[TUCKER_PHASE_COUNT];    /* algorithmic bytes (inputs read once + outputs written once) */
+} tucker_profile;
+
+/* Enable (1) or disable (0) phase timing for calls made afterwards on this process;
+ * enabling resets the counters. */
+TUCKER_API void tucker_profile_enable(int on);
+/* Copy the accumulated counters (phases of completed calls only). */
+TUCKER_API void tucker_profile_read(tucker_profile *p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_GB300_H */

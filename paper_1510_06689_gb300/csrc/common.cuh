@@ -1,0 +1,115 @@
+// Shared declarations of the ST-HOSVD CUDA library (host driver + kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tucker.h"
+
+namespace tk {
+
+// ---------------------------------------------------------------------------
+// error reporting (host)
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+int64_t bump_launches(int64_t n = 1);
+
+#define TK_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::tk::set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__,             \
+                      cudaGetErrorString(e_));                                         \
+      return e_ == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA;           \
+    }                                                                                  \
+  } while (0)
+
+#define TK_LAUNCHED()                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) {                                                           \
+      ::tk::set_error("kernel launch failed at %s:%d: %s", __FILE__, __LINE__,         \
+                      cudaGetErrorString(e_));                                         \
+      return TUCKER_ECUDA;                                                             \
+    }                                                                                  \
+    ::tk::bump_launches();                                                             \
+  } while (0)
+
+#define TK_CHECK(st)                                                                   \
+  do {                                                                                 \
+    int s_ = (st);                                                                     \
+    if (s_ != TUCKER_OK) return s_;                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device description (cached per device)
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  int smem_optin = 0;
+};
+int device_info(DeviceInfo *out);
+
+// ---------------------------------------------------------------------------
+// phase timing: CUDA events on the launching stream, resolved after the
+// caller's stream has been synchronised.
+// ---------------------------------------------------------------------------
+struct Prof {
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+    double flops, bytes;
+    int launches;
+  };
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<Rec> recs;
+  explicit Prof(cudaStream_t stream);
+  ~Prof();
+  void begin(int phase);
+  void end(double flops, double bytes, int launches);
+  // Adds the elapsed times of all recorded phases to the process counters;
+  // call only after `s` has been synchronised.
+  void flush();
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (return tucker_status)
+// ---------------------------------------------------------------------------
+
+// Sum of squares of n elements into *d_out (device double).  d_partials holds
+// norm2_partials() doubles.
+int64_t norm2_partials();
+int launch_norm2(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out,
+                 cudaStream_t s, Prof *prof);
+
+// Gram of the (L, J, B) view into d_S (J x J, both triangles).  d_ws holds
+// gram_workspace_doubles() doubles of split-K partials.
+int64_t gram_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
+int launch_gram(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
+                const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+
+// Mode product Z(L,K,B) = sum_j A[k,j] Y(L,J,B) with A[k,j] = a[k*ak + j*aj].
+int launch_ttm(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *a, int64_t ak,
+               int64_t aj, int64_t K, double *z, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+// Same product, not stored: sum over all entries of (x - z)^2 into *d_out,
+// with x of the (L, K, B) shape.  d_partials holds ttm_diff_partials() doubles.
+int64_t ttm_diff_partials(int64_t L, int64_t J, int64_t B, int64_t K, const DeviceInfo &dev);
+int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const double *a, int64_t ak, int64_t aj,
+                    int64_t K, const void *x, tucker_dtype xdt, double *d_partials, double *d_out,
+                    const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+
+// Jacobi eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
+// matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if
+// converged else 1.
+int64_t eig_workspace_doubles(int64_t J);
+int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
+               cudaStream_t s, Prof *prof);
+// Rank rule: *d_rank = R, *d_tail = discarded sum.
+int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
+                    double *d_tail, cudaStream_t s, Prof *prof);
+
+}  // namespace tk

@@ -1,0 +1,257 @@
+// Eigenvector and rank steps of Algorithm 1 (Sec. 2.2): all eigenpairs of the
+// symmetric Gram matrix S by cyclic Jacobi in float64, then the error rule
+// that picks R_n.
+//
+// The paper calls LAPACK's dsyevx redundantly on every process (Sec. 4.3,
+// Algorithm 5) and notes the cost is negligible.  Here one CTA runs a
+// parallel-order Jacobi: each step applies m/2 disjoint rotations chosen by
+// the round-robin (circle) tournament over the m = J rounded-up-to-even
+// indices, so that after m - 1 steps every pair has met once (one sweep).
+// S is kept as its packed upper triangle; with the rotations of a step fixed,
+// every 2 x 2 block {p_P, q_P} x {p_Q, q_Q} of S is updated independently as
+// R_P^T B R_Q, and the rotations accumulate into V.  A dummy zero row and
+// column pad odd J; rotations that involve it are never taken.  For J <= 128
+// S and V live in shared memory (194 KB at J = 128); larger J use a global
+// workspace.  A rotation is taken when |s_pq| > eps_mach * sqrt(|s_pp s_qq|)
+// and |s_pq| exceeds a tiny absolute floor; a sweep without rotations ends
+// the iteration, and the sweep cap ends it with a "not converged" flag (no
+// unbounded loop on the device).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace tk {
+
+namespace {
+
+constexpr int kEigThreads = 1024;
+constexpr int kMaxSweeps = 60;
+constexpr int kSmemMaxJ = 128;
+constexpr int kMaxPairs = TUCKER_MAX_DIM / 2;
+
+__device__ __forceinline__ int64_t pidx(int i, int j) {
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  return (int64_t)j * (j + 1) / 2 + i;
+}
+
+__device__ __forceinline__ void decode_pair_block(int e, int &P, int &Q) {
+  int q = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+  while ((q + 1) * (q + 2) / 2 <= e) ++q;
+  while (q * (q + 1) / 2 > e) --q;
+  Q = q;
+  P = e - q * (q + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict__ S_in, int J,
+                                                         double *__restrict__ lam, double *__restrict__ V_out,
+                                                         double *__restrict__ gws, int *__restrict__ info) {
+  extern __shared__ __align__(16) double dyn[];
+  __shared__ double cs[kMaxPairs], sn[kMaxPairs];
+  __shared__ int pp[kMaxPairs], qq[kMaxPairs];
+  __shared__ int rotated;
+  __shared__ double abs_floor;
+  const int m = J + (J & 1);
+  const int np = m / 2;
+  const int64_t packed = (int64_t)m * (m + 1) / 2;
+  double *Sp = gws ? gws : dyn;
+  double *V = Sp + packed;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i <= j) Sp[pidx(i, j)] = (j < J) ? S_in[i + (int64_t)J * j] : 0.0;
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < J; ++i) mx = fmax(mx, fabs(S_in[i + (int64_t)J * i]));
+    abs_floor = mx * (DBL_EPSILON * DBL_EPSILON) + DBL_MIN;
+  }
+  __syncthreads();
+
+  int sweep = 0;
+  bool converged = false;
+  const int nblk = np * (np + 1) / 2;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < m - 1; ++step) {
+      for (int t = tid; t < np; t += nt) {
+        int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
+        int q = ((m - 2 - t + step) % (m - 1)) + 1;  // position m - 1 - t
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        double c = 1.0, s = 0.0;
+        const double b = Sp[pidx(p, q)];
+        if (b != 0.0) {
+          const double a = Sp[pidx(p, p)], d = Sp[pidx(q, q)];
+          const double ab = fabs(b);
+          if (ab > DBL_EPSILON * sqrt(fabs(a)) * sqrt(fabs(d)) && ab > abs_floor) {
+            const double tau = (d - a) / (2.0 * b);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+            rotated = 1;
+          }
+        }
+        cs[t] = c;
+        sn[t] = s;
+        pp[t] = p;
+        qq[t] = q;
+      }
+      __syncthreads();
+      for (int e = tid; e < nblk; e += nt) {
+        int P, Q;
+        decode_pair_block(e, P, Q);
+        const double s1 = sn[P], s2 = sn[Q];
+        const int p1 = pp[P], q1 = qq[P];
+        if (P == Q) {
+          if (s1 != 0.0) {
+            const double t1 = s1 / cs[P];
+            const int64_t ipq = pidx(p1, q1), ipp = pidx(p1, p1), iqq = pidx(q1, q1);
+            const double b = Sp[ipq];
+            Sp[ipp] = Sp[ipp] - t1 * b;
+            Sp[iqq] = Sp[iqq] + t1 * b;
+            Sp[ipq] = 0.0;
+          }
+          continue;
+        }
+        if (s1 == 0.0 && s2 == 0.0) continue;
+        const double c1 = cs[P], c2 = cs[Q];
+        const int p2 = pp[Q], q2 = qq[Q];
+        const int64_t i11 = pidx(p1, p2), i12 = pidx(p1, q2), i21 = pidx(q1, p2), i22 = pidx(q1, q2);
+        const double x11 = Sp[i11], x12 = Sp[i12], x21 = Sp[i21], x22 = Sp[i22];
+        // R_P^T B with R = [[c, s], [-s, c]]
+        const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+        const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+        // (.) R_Q
+        Sp[i11] = y11 * c2 - y12 * s2;
+        Sp[i12] = y11 * s2 + y12 * c2;
+        Sp[i21] = y21 * c2 - y22 * s2;
+        Sp[i22] = y21 * s2 + y22 * c2;
+      }
+      for (int e = tid; e < np * m; e += nt) {
+        const int t = e / m, i = e - t * m;
+        const double s = sn[t];
+        if (s == 0.0) continue;
+        const double c = cs[t];
+        double *vp = V + (int64_t)pp[t] * m + i;
+        double *vq = V + (int64_t)qq[t] * m + i;
+        const double a = *vp, b = *vq;
+        *vp = c * a - s * b;
+        *vq = s * a + c * b;
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) {
+      converged = true;
+      break;
+    }
+  }
+
+  // Sort descending (ties: lower index first), sign-normalise, write out.
+  for (int i = tid; i < J; i += nt) {
+    const double di = Sp[pidx(i, i)];
+    int rank = 0;
+    for (int j = 0; j < J; ++j) {
+      const double dj = Sp[pidx(j, j)];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    lam[rank] = di;
+    const double *col = V + (int64_t)i * m;
+    double best = -1.0;
+    int br = 0;
+    for (int r = 0; r < J; ++r) {
+      const double v = fabs(col[r]);
+      if (v > best) {
+        best = v;
+        br = r;
+      }
+    }
+    const double sg = col[br] < 0.0 ? -1.0 : 1.0;
+    for (int r = 0; r < J; ++r) V_out[r + (int64_t)J * rank] = sg * col[r];
+  }
+  if (tid == 0) {
+    info[0] = converged ? sweep + 1 : kMaxSweeps;
+    info[1] = converged ? 0 : 1;
+  }
+}
+
+// Rank rule of Algorithm 1: tails[r] = sum_{k >= r} max(lam[k], 0) accumulated
+// from the smallest eigenvalue upward; R = smallest r in [1, J] with
+// tails[r] <= threshold.
+__global__ void k_rank_cut(const double *__restrict__ lam, int J, double threshold, int keep_all,
+                           int64_t *__restrict__ R, double *__restrict__ tail) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (keep_all) {
+    R[0] = J;
+    tail[0] = 0.0;
+    return;
+  }
+  double acc = 0.0;
+  int best = J;
+  double best_tail = 0.0;
+  for (int r = J - 1; r >= 1; --r) {
+    acc += fmax(lam[r], 0.0);
+    if (acc <= threshold) {
+      best = r;
+      best_tail = acc;
+    } else {
+      break;
+    }
+  }
+  R[0] = best;
+  tail[0] = best_tail;
+}
+
+}  // namespace
+
+int64_t eig_workspace_doubles(int64_t J) {
+  if (J <= kSmemMaxJ) return 0;
+  const int64_t m = J + (J & 1);
+  return m * (m + 1) / 2 + m * m;
+}
+
+int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
+               cudaStream_t s, Prof *prof) {
+  const int64_t m = J + (J & 1);
+  size_t smem = 0;
+  double *ws = nullptr;
+  if (J <= kSmemMaxJ) {
+    smem = (size_t)(m * (m + 1) / 2 + m * m) * sizeof(double);
+    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  } else {
+    ws = d_ws;
+    if (!ws) {
+      set_error("eigensolver workspace missing for J = %lld", (long long)J);
+      return TUCKER_EINVAL;
+    }
+  }
+  if (prof) prof->begin(TUCKER_PHASE_EIG);
+  k_jacobi<<<1, kEigThreads, smem, s>>>(d_S, (int)J, d_lam, d_V, ws, d_info);
+  TK_LAUNCHED();
+  if (prof) prof->end(0.0, (double)J * J * 16, 1);
+  return TUCKER_OK;
+}
+
+int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
+                    double *d_tail, cudaStream_t s, Prof *prof) {
+  if (prof) prof->begin(TUCKER_PHASE_RANK);
+  k_rank_cut<<<1, 32, 0, s>>>(d_lam, (int)J, threshold, keep_all, d_rank, d_tail);
+  TK_LAUNCHED();
+  if (prof) prof->end((double)J, (double)J * 8, 1);
+  return TUCKER_OK;
+}
+
+}  // namespace tk

@@ -1,0 +1,778 @@
+// Host driver and C ABI of the ST-HOSVD library (declarations in include/tucker.h).
+//
+// tucker_sthosvd sequences Algorithm 1 (Sec. 2.2) on one GPU:
+//   ||X||^2 (sum-of-squares kernel) -> threshold eps^2 ||X||^2 / N,
+//   then for each mode n of the order:
+//     Gram of the (L, J_n, B) view   (split-K kernel + fixed-order reduce)
+//     Jacobi eigensolve              (one CTA)
+//     rank rule                      (one thread)
+//     copy R_n, tail and eigenvalues to pinned host memory; synchronise
+//     factor U_n = first R_n eigenvector columns
+//     TTM  Y <- Y x_n U_n^T          (into a fresh stream-ordered buffer)
+// The only host<->device round trip per mode is the rank, which fixes the
+// shape of the next launch.  All device memory is stream-ordered
+// (cudaMallocAsync on the caller's stream).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tk {
+
+// ---------------------------------------------------------------------------
+// errors, counters, device info
+// ---------------------------------------------------------------------------
+static thread_local char g_err[1024];
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+int64_t bump_launches(int64_t n) { return g_launches.fetch_add(n) + n; }
+
+int device_info(DeviceInfo *out) {
+  static std::mutex mu;
+  static DeviceInfo cache[64];
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return TUCKER_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache[dev].device != dev) {
+    DeviceInfo d;
+    d.device = dev;
+    TK_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    TK_CUDA(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // Keep freed stream-ordered memory in the pool across calls (up to 64 GB)
+    // so repeated compressions do not return it to the driver each time.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = 64ull << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cache[dev] = d;
+  }
+  *out = cache[dev];
+  return TUCKER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling
+// ---------------------------------------------------------------------------
+static std::mutex g_prof_mu;
+static std::atomic<bool> g_prof_on{false};
+static tucker_profile g_prof;
+
+Prof::Prof(cudaStream_t stream) : on(g_prof_on.load()), s(stream) {}
+
+Prof::~Prof() {
+  for (auto &r : recs) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+}
+
+void Prof::begin(int phase) {
+  if (!on) return;
+  Rec r{phase, nullptr, nullptr, 0, 0, 0};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    on = false;
+    return;
+  }
+  cudaEventRecord(r.a, s);
+  recs.push_back(r);
+}
+
+void Prof::end(double flops, double bytes, int launches) {
+  if (!on || recs.empty()) return;
+  Rec &r = recs.back();
+  r.flops = flops;
+  r.bytes = bytes;
+  r.launches = launches;
+  cudaEventRecord(r.b, s);
+}
+
+void Prof::flush() {
+  if (!on) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  for (auto &r : recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_prof.ms[r.phase] += ms;
+      g_prof.launches[r.phase] += r.launches;
+      g_prof.flops[r.phase] += r.flops;
+      g_prof.bytes[r.phase] += r.bytes;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  recs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// small RAII helpers for stream-ordered device memory and pinned staging
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { reset(); }
+  int alloc(size_t bytes, cudaStream_t stream) {
+    reset();
+    s = stream;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA;
+    }
+    return TUCKER_OK;
+  }
+  void reset() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  void *release() {
+    void *q = p;
+    p = nullptr;
+    return q;
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
+// Per-thread pinned staging area for the per-mode device->host copies.
+struct Pinned {
+  void *p = nullptr;
+  size_t n = 0;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+static thread_local Pinned g_pinned;
+
+static int pinned(size_t bytes, void **out) {
+  if (g_pinned.n < bytes) {
+    if (g_pinned.p) cudaFreeHost(g_pinned.p);
+    g_pinned.p = nullptr;
+    g_pinned.n = 0;
+    TK_CUDA(cudaMallocHost(&g_pinned.p, bytes));
+    g_pinned.n = bytes;
+  }
+  *out = g_pinned.p;
+  return TUCKER_OK;
+}
+
+static int fault_injection(const char *what) {
+  const char *f = getenv("TUCKER_FAULT");
+  return f && strcmp(f, what) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static int check_dims(const int64_t *dims, int N) {
+  if (!dims || N < 1 || N > TUCKER_MAX_MODES) {
+    set_error("N must be in [1, %d] and dims non-null", TUCKER_MAX_MODES);
+    return TUCKER_EINVAL;
+  }
+  double total = 1.0;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 1 || dims[n] > TUCKER_MAX_DIM) {
+      set_error("dims[%d] = %lld outside [1, %d]", n, (long long)dims[n], TUCKER_MAX_DIM);
+      return TUCKER_EINVAL;
+    }
+    total *= (double)dims[n];
+  }
+  if (total > 9.0e18) {
+    set_error("tensor too large");
+    return TUCKER_EINVAL;
+  }
+  return TUCKER_OK;
+}
+
+static int check_order(const int *order, int N, int *out) {
+  if (!order) {
+    for (int n = 0; n < N; ++n) out[n] = n;
+    return TUCKER_OK;
+  }
+  bool seen[TUCKER_MAX_MODES] = {false};
+  for (int k = 0; k < N; ++k) {
+    const int n = order[k];
+    if (n < 0 || n >= N || seen[n]) {
+      set_error("mode_order is not a permutation of 0..%d", N - 1);
+      return TUCKER_EINVAL;
+    }
+    seen[n] = true;
+    out[k] = n;
+  }
+  return TUCKER_OK;
+}
+
+static size_t elem_size(tucker_dtype dt) { return dt == TUCKER_F64 ? 8 : 4; }
+
+struct Priv {
+  int device = 0;
+};
+
+static void free_result_device(tucker_result *r) {
+  if (r->on_host) {
+    free(r->core);
+    for (int n = 0; n < TUCKER_MAX_MODES; ++n) free(r->factors[n]);
+  } else {
+    if (r->core) cudaFree(r->core);
+    for (int n = 0; n < TUCKER_MAX_MODES; ++n)
+      if (r->factors[n]) cudaFree(r->factors[n]);
+  }
+  r->core = nullptr;
+  for (int n = 0; n < TUCKER_MAX_MODES; ++n) r->factors[n] = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1
+// ---------------------------------------------------------------------------
+static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *order,
+                        cudaStream_t s, tucker_result *out) {
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  const int64_t I = [&] {
+    int64_t t = 1;
+    for (int n = 0; n < N; ++n) t *= dims[n];
+    return t;
+  }();
+  int64_t maxJ = 1;
+  for (int n = 0; n < N; ++n) maxJ = std::max(maxJ, dims[n]);
+
+  // small device scratch: norm partials, ||X||^2, S, lam, V, eig info, rank/tail
+  DevBuf partials, scal, S, lam, V, eigws, gramws;
+  TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
+  TK_CHECK(scal.alloc(64, s));
+  TK_CHECK(S.alloc(sizeof(double) * maxJ * maxJ, s));
+  TK_CHECK(lam.alloc(sizeof(double) * maxJ, s));
+  TK_CHECK(V.alloc(sizeof(double) * maxJ * maxJ, s));
+  double *d_nx2 = scal.as<double>();
+  double *d_tail = d_nx2 + 1;
+  int64_t *d_rank = reinterpret_cast<int64_t *>(d_nx2 + 2);
+  int *d_info = reinterpret_cast<int *>(d_nx2 + 3);
+
+  void *host = nullptr;
+  TK_CHECK(pinned(sizeof(double) * (8 + maxJ), &host));
+  double *h = static_cast<double *>(host);
+
+  // ||X||^2 and the threshold of the rank rule
+  TK_CHECK(launch_norm2(X, dt, I, partials.as<double>(), d_nx2, s, &prof));
+  TK_CUDA(cudaMemcpyAsync(h, d_nx2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  const double nx2 = h[0];
+  if (!std::isfinite(nx2) || fault_injection("nan")) {
+    set_error("||X||^2 is not finite (%g): the input holds Inf or NaN", nx2);
+    return TUCKER_ENONFINITE;
+  }
+  const int keep_all = !(eps > 0.0);
+  const double threshold = keep_all ? 0.0 : eps * eps * nx2 / N;
+
+  out->N = N;
+  out->on_host = 0;
+  out->norm2_x = nx2;
+  out->threshold = threshold;
+  for (int n = 0; n < N; ++n) {
+    out->dims[n] = dims[n];
+    out->mode_order[n] = order[n];
+  }
+
+  int64_t cur[TUCKER_MAX_MODES];
+  for (int n = 0; n < N; ++n) cur[n] = dims[n];
+  const void *Y = X;
+  tucker_dtype ydt = dt;
+  DevBuf ybuf;  // owns Y when Y != X
+  DevBuf factor_bufs[TUCKER_MAX_MODES];
+  std::vector<double *> eig_host(N, nullptr);
+  struct EigFree {
+    std::vector<double *> &v;
+    bool keep = false;
+    ~EigFree() {
+      if (!keep)
+        for (double *p : v) free(p);
+    }
+  } eig_guard{eig_host};
+
+  for (int k = 0; k < N; ++k) {
+    const int n = order[k];
+    int64_t L = 1, B = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < N; ++m) B *= cur[m];
+    const int64_t J = cur[n];
+
+    // Gram step
+    const int64_t gws = gram_workspace_doubles(L, J, B, dev);
+    TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
+    TK_CHECK(launch_gram(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
+    // eigenvector step
+    const int64_t ews = eig_workspace_doubles(J);
+    if (ews > 0) TK_CHECK(eigws.alloc(sizeof(double) * ews, s));
+    TK_CHECK(launch_eig(S.as<double>(), J, lam.as<double>(), V.as<double>(), ews > 0 ? eigws.as<double>() : nullptr,
+                        d_info, s, &prof));
+    // rank step
+    TK_CHECK(launch_rank_cut(lam.as<double>(), J, threshold, keep_all, d_rank, d_tail, s, &prof));
+    TK_CUDA(cudaMemcpyAsync(h, d_tail, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(h + 8, lam.as<double>(), sizeof(double) * J, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    const double tail = h[0];
+    int64_t R;
+    int info[2];
+    memcpy(&R, h + 1, sizeof R);
+    memcpy(info, h + 2, sizeof info);
+    if (info[1] != 0 || fault_injection("noconv")) {
+      set_error("Jacobi eigensolver did not converge for mode %d (J = %lld) within %d sweeps", n, (long long)J,
+                info[0]);
+      return TUCKER_ENOCONV;
+    }
+    if (R < 1 || R > J) {
+      set_error("rank rule returned R = %lld outside [1, %lld]", (long long)R, (long long)J);
+      return TUCKER_ECUDA;
+    }
+    eig_host[n] = static_cast<double *>(malloc(sizeof(double) * J));
+    if (!eig_host[n]) {
+      set_error("host allocation failed");
+      return TUCKER_ENOMEM;
+    }
+    memcpy(eig_host[n], h + 8, sizeof(double) * J);
+    out->ranks[n] = R;
+    out->tail[n] = tail;
+    out->sweeps[n] = info[0];
+
+    // factor U_n = leading R eigenvectors (first R columns of V)
+    TK_CHECK(factor_bufs[n].alloc(sizeof(double) * J * R, s));
+    TK_CUDA(cudaMemcpyAsync(factor_bufs[n].p, V.p, sizeof(double) * J * R, cudaMemcpyDeviceToDevice, s));
+
+    // TTM step Y <- Y x_n U_n^T
+    if (fault_injection("alloc")) {
+      set_error("injected allocation failure");
+      return TUCKER_ENOMEM;
+    }
+    DevBuf ynew;
+    TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
+    TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev,
+                        s, &prof));
+    ybuf.reset();
+    ybuf.p = ynew.release();
+    ybuf.s = s;
+    Y = ybuf.p;
+    ydt = TUCKER_F64;
+    cur[n] = R;
+  }
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  out->core = static_cast<double *>(ybuf.release());
+  for (int n = 0; n < N; ++n) {
+    out->factors[n] = factor_bufs[n].as<double>();
+    factor_bufs[n].release();
+    out->eigvals[n] = eig_host[n];
+  }
+  eig_guard.keep = true;
+  Priv *pv = new Priv;
+  pv->device = dev.device;
+  out->priv = pv;
+  return TUCKER_OK;
+}
+
+// Expands core x {U_n} over every mode except `skip` (or all when skip < 0),
+// smallest growth first; returns the buffer and its current dims.
+static int expand_modes(const tucker_result *r, int skip, double *final_out, DevBuf &hold, const double **res,
+                        int64_t *cur, const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
+  const int N = r->N;
+  for (int n = 0; n < N; ++n) cur[n] = r->ranks[n];
+  int seq[TUCKER_MAX_MODES], cnt = 0;
+  for (int n = 0; n < N; ++n)
+    if (n != skip) seq[cnt++] = n;
+  for (int a = 1; a < cnt; ++a)  // insertion sort by growth I_n / R_n
+    for (int b = a; b > 0; --b) {
+      const double gb = (double)r->dims[seq[b]] / r->ranks[seq[b]];
+      const double ga = (double)r->dims[seq[b - 1]] / r->ranks[seq[b - 1]];
+      if (gb < ga) std::swap(seq[b], seq[b - 1]);
+    }
+  const double *y = r->core;
+  DevBuf tmp;
+  for (int k = 0; k < cnt; ++k) {
+    const int n = seq[k];
+    int64_t L = 1, B = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < N; ++m) B *= cur[m];
+    const int64_t J = cur[n], K = r->dims[n];
+    double *z;
+    DevBuf next;
+    if (final_out && k == cnt - 1) {
+      z = final_out;
+    } else {
+      TK_CHECK(next.alloc(sizeof(double) * L * K * B, s));
+      z = next.as<double>();
+    }
+    // A = U_n (K x J, column-major): A[k, j] = U[k + K j]
+    TK_CHECK(launch_ttm(y, TUCKER_F64, L, J, B, r->factors[n], /*ak=*/1, /*aj=*/K, K, z, dev, s, prof));
+    if (!(final_out && k == cnt - 1)) {
+      tmp.reset();
+      tmp.p = next.release();
+      tmp.s = s;
+    }
+    y = z;
+    cur[n] = K;
+  }
+  if (cnt == 0 && final_out) {
+    int64_t tot = 1;
+    for (int n = 0; n < N; ++n) tot *= cur[n];
+    TK_CUDA(cudaMemcpyAsync(final_out, r->core, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    y = final_out;
+  }
+  hold.reset();
+  hold.p = tmp.release();
+  hold.s = s;
+  *res = y;
+  return TUCKER_OK;
+}
+
+static int check_result(const tucker_result *r) {
+  if (!r || r->N < 1 || r->N > TUCKER_MAX_MODES || !r->core) {
+    set_error("result is empty or invalid");
+    return TUCKER_EINVAL;
+  }
+  if (r->on_host) {
+    set_error("result lives on the host; device entry points need a device result");
+    return TUCKER_EINVAL;
+  }
+  for (int n = 0; n < r->N; ++n)
+    if (!r->factors[n] || r->ranks[n] < 1 || r->ranks[n] > r->dims[n]) {
+      set_error("result factor %d is invalid", n);
+      return TUCKER_EINVAL;
+    }
+  return TUCKER_OK;
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *tucker_status_string(int status) {
+  switch (status) {
+    case TUCKER_OK: return "ok";
+    case TUCKER_EINVAL: return "invalid argument";
+    case TUCKER_ENOMEM: return "out of memory";
+    case TUCKER_ECUDA: return "CUDA error";
+    case TUCKER_ENOCONV: return "eigensolver did not converge";
+    case TUCKER_ETIMEOUT: return "device wait timed out";
+    case TUCKER_ENONFINITE: return "input is not finite";
+    case TUCKER_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char *tucker_last_error(void) { return g_err; }
+
+int64_t tucker_launch_count(void) { return g_launches.load(); }
+
+void tucker_profile_enable(int on) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  if (on) memset(&g_prof, 0, sizeof g_prof);
+  g_prof_on = on != 0;
+}
+
+void tucker_profile_read(tucker_profile *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  *p = g_prof;
+}
+
+int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *mode_order,
+                   tucker_precision prec, void *stream, tucker_result *out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_error("out is NULL");
+    return TUCKER_EINVAL;
+  }
+  memset(out, 0, sizeof *out);
+  if (!X) {
+    set_error("X is NULL");
+    return TUCKER_EINVAL;
+  }
+  if (dt != TUCKER_F64 && dt != TUCKER_F32) {
+    set_error("unknown dtype %d", (int)dt);
+    return TUCKER_EINVAL;
+  }
+  if (prec != TUCKER_PREC_FP64) {
+    set_error("unknown precision %d", (int)prec);
+    return TUCKER_EINVAL;
+  }
+  if (std::isnan(eps)) {
+    set_error("eps is NaN");
+    return TUCKER_EINVAL;
+  }
+  TK_CHECK(check_dims(dims, N));
+  int order[TUCKER_MAX_MODES];
+  TK_CHECK(check_order(mode_order, N, order));
+  int st = sthosvd_impl(X, dt, dims, N, eps, order, static_cast<cudaStream_t>(stream), out);
+  if (st != TUCKER_OK) {
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    memset(out, 0, sizeof *out);
+  }
+  return st;
+}
+
+int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                        const int *mode_order, tucker_precision prec, void *stream, tucker_result *out) {
+  g_err[0] = 0;
+  if (!out || !X_host) {
+    set_error("X_host and out must be non-null");
+    return TUCKER_EINVAL;
+  }
+  memset(out, 0, sizeof *out);
+  if (dt != TUCKER_F64 && dt != TUCKER_F32) {
+    set_error("unknown dtype %d", (int)dt);
+    return TUCKER_EINVAL;
+  }
+  TK_CHECK(check_dims(dims, N));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t I = 1;
+  for (int n = 0; n < N; ++n) I *= dims[n];
+  DevBuf dX;
+  TK_CHECK(dX.alloc(elem_size(dt) * I, s));
+  TK_CUDA(cudaMemcpyAsync(dX.p, X_host, elem_size(dt) * I, cudaMemcpyHostToDevice, s));
+  tucker_result dres;
+  int st = tucker_sthosvd(dX.p, dt, dims, N, eps, mode_order, prec, stream, &dres);
+  if (st != TUCKER_OK) return st;
+  *out = dres;
+  out->on_host = 1;
+  out->core = nullptr;
+  for (int n = 0; n < TUCKER_MAX_MODES; ++n) out->factors[n] = nullptr;
+  int64_t G = 1;
+  for (int n = 0; n < N; ++n) G *= dres.ranks[n];
+  out->core = static_cast<double *>(malloc(sizeof(double) * G));
+  bool ok = out->core != nullptr;
+  for (int n = 0; n < N && ok; ++n) {
+    out->factors[n] = static_cast<double *>(malloc(sizeof(double) * dims[n] * dres.ranks[n]));
+    ok = out->factors[n] != nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (ok) {
+    e = cudaMemcpyAsync(out->core, dres.core, sizeof(double) * G, cudaMemcpyDeviceToHost, s);
+    for (int n = 0; n < N && e == cudaSuccess; ++n)
+      e = cudaMemcpyAsync(out->factors[n], dres.factors[n], sizeof(double) * dims[n] * dres.ranks[n],
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  // release the device copies (eigenvalues and priv now belong to *out)
+  for (int n = 0; n < TUCKER_MAX_MODES; ++n) dres.eigvals[n] = nullptr;
+  dres.priv = nullptr;
+  free_result_device(&dres);
+  if (!ok || e != cudaSuccess) {
+    if (!ok) set_error("host allocation failed");
+    else set_error("device-to-host copy failed: %s", cudaGetErrorString(e));
+    tucker_result_free(out);
+    return ok ? TUCKER_ECUDA : TUCKER_ENOMEM;
+  }
+  return TUCKER_OK;
+}
+
+int tucker_reconstruct(const tucker_result *r, double *Xhat, void *stream) {
+  g_err[0] = 0;
+  TK_CHECK(check_result(r));
+  if (!Xhat) {
+    set_error("Xhat is NULL");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  DevBuf hold;
+  const double *res = nullptr;
+  int64_t cur[TUCKER_MAX_MODES];
+  int st = expand_modes(r, -1, Xhat, hold, &res, cur, dev, s, &prof);
+  if (st != TUCKER_OK) return st;
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  return TUCKER_OK;
+}
+
+int tucker_rel_error(const void *X, tucker_dtype dt, const tucker_result *r, double *rel_out, void *stream) {
+  g_err[0] = 0;
+  TK_CHECK(check_result(r));
+  if (!X || !rel_out || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("X and rel_out must be non-null and dt valid");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  const int N = r->N;
+  // the last (fused) expansion is the mode with the largest growth
+  int last = 0;
+  for (int n = 1; n < N; ++n)
+    if ((double)r->dims[n] / r->ranks[n] >= (double)r->dims[last] / r->ranks[last]) last = n;
+  DevBuf hold, scal, partials;
+  const double *y = nullptr;
+  int64_t cur[TUCKER_MAX_MODES];
+  TK_CHECK(expand_modes(r, last, nullptr, hold, &y, cur, dev, s, &prof));
+  int64_t L = 1, B = 1, I = 1;
+  for (int m = 0; m < last; ++m) L *= cur[m];
+  for (int m = last + 1; m < N; ++m) B *= cur[m];
+  for (int m = 0; m < N; ++m) I *= r->dims[m];
+  const int64_t J = cur[last], K = r->dims[last];
+  TK_CHECK(scal.alloc(2 * sizeof(double), s));
+  const int64_t np = std::max(norm2_partials(), ttm_diff_partials(L, J, B, K, dev));
+  TK_CHECK(partials.alloc(sizeof(double) * np, s));
+  TK_CHECK(launch_ttm_diff(y, L, J, B, r->factors[last], 1, K, K, X, dt, partials.as<double>(), scal.as<double>(),
+                           dev, s, &prof));
+  TK_CHECK(launch_norm2(X, dt, I, partials.as<double>(), scal.as<double>() + 1, s, &prof));
+  double h[2];
+  TK_CUDA(cudaMemcpyAsync(h, scal.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  if (h[1] == 0.0) *rel_out = (h[0] == 0.0) ? 0.0 : INFINITY;
+  else *rel_out = std::sqrt(h[0] / h[1]);
+  return TUCKER_OK;
+}
+
+void tucker_result_free(tucker_result *r) {
+  if (!r) return;
+  free_result_device(r);
+  for (int n = 0; n < TUCKER_MAX_MODES; ++n) {
+    free(r->eigvals[n]);
+    r->eigvals[n] = nullptr;
+  }
+  delete static_cast<Priv *>(r->priv);
+  memset(r, 0, sizeof *r);
+}
+
+int tucker_norm2(const void *X, tucker_dtype dt, int64_t n, double *out, void *stream) {
+  g_err[0] = 0;
+  if ((!X && n > 0) || !out || n < 0 || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("invalid arguments to tucker_norm2");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Prof prof(s);
+  DevBuf partials, scal;
+  TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
+  TK_CHECK(scal.alloc(sizeof(double), s));
+  TK_CHECK(launch_norm2(X, dt, n, partials.as<double>(), scal.as<double>(), s, &prof));
+  TK_CUDA(cudaMemcpyAsync(out, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  return TUCKER_OK;
+}
+
+int tucker_gram(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream) {
+  g_err[0] = 0;
+  if (!Y || !S || L < 1 || B < 1 || J < 1 || J > TUCKER_MAX_DIM || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("invalid arguments to tucker_gram");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  DevBuf ws;
+  TK_CHECK(ws.alloc(sizeof(double) * gram_workspace_doubles(L, J, B, dev), s));
+  TK_CHECK(launch_gram(Y, dt, L, J, B, S, ws.as<double>(), dev, s, &prof));
+  if (prof.on) {
+    TK_CUDA(cudaStreamSynchronize(s));
+    prof.flush();
+  }
+  return TUCKER_OK;
+}
+
+int tucker_eig(const double *S, int64_t J, double *lam, double *V, int *sweeps, void *stream) {
+  g_err[0] = 0;
+  if (!S || !lam || !V || J < 1 || J > TUCKER_MAX_DIM) {
+    set_error("invalid arguments to tucker_eig");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Prof prof(s);
+  DevBuf ws, info;
+  const int64_t ews = eig_workspace_doubles(J);
+  if (ews > 0) TK_CHECK(ws.alloc(sizeof(double) * ews, s));
+  TK_CHECK(info.alloc(2 * sizeof(int), s));
+  TK_CHECK(launch_eig(S, J, lam, V, ews > 0 ? ws.as<double>() : nullptr, info.as<int>(), s, &prof));
+  int h[2];
+  TK_CUDA(cudaMemcpyAsync(h, info.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  if (sweeps) *sweeps = h[0];
+  if (h[1] != 0) {
+    set_error("Jacobi eigensolver did not converge within %d sweeps", h[0]);
+    return TUCKER_ENOCONV;
+  }
+  return TUCKER_OK;
+}
+
+int tucker_rank_cut(const double *lam, int64_t J, double threshold, int keep_all, int64_t *R, double *tail,
+                    void *stream) {
+  g_err[0] = 0;
+  if (!lam || !R || !tail || J < 1 || J > TUCKER_MAX_DIM || std::isnan(threshold)) {
+    set_error("invalid arguments to tucker_rank_cut");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Prof prof(s);
+  DevBuf buf;
+  TK_CHECK(buf.alloc(2 * sizeof(double), s));
+  TK_CHECK(launch_rank_cut(lam, J, threshold, keep_all, reinterpret_cast<int64_t *>(buf.as<double>()),
+                           buf.as<double>() + 1, s, &prof));
+  double h[2];
+  TK_CUDA(cudaMemcpyAsync(h, buf.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  memcpy(R, h, sizeof *R);
+  *tail = h[1];
+  return TUCKER_OK;
+}
+
+int tucker_ttm(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *M, int64_t K,
+               int trans_m, double *Z, void *stream) {
+  g_err[0] = 0;
+  if (!Y || !M || !Z || L < 1 || B < 1 || J < 1 || K < 1 || J > TUCKER_MAX_DIM || K > TUCKER_MAX_DIM ||
+      (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("invalid arguments to tucker_ttm");
+    return TUCKER_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  const int64_t ak = trans_m ? J : 1, aj = trans_m ? 1 : K;
+  TK_CHECK(launch_ttm(Y, dt, L, J, B, M, ak, aj, K, Z, dev, s, &prof));
+  if (prof.on) {
+    TK_CUDA(cudaStreamSynchronize(s));
+    prof.flush();
+  }
+  return TUCKER_OK;
+}
+
+}  // extern "C"

@@ -42,6 +42,7 @@ __all__ = [
     "WORKLOADS",
     "tucker_tensor_np",
     "tucker_tensor_torch",
+    "tucker_prefix_np",
     "random_dims_ranks",
 ]
 
@@ -130,11 +131,25 @@ def _factors_np(dims, ranks, seed, tensor, smooth):
 
 
 def _expand_np(core_flat: np.ndarray, ranks, factors) -> np.ndarray:
-    """G x {U_n} with numpy.tensordot; arrays kept in natural (F) layout."""
-    t = core_flat.reshape(ranks, order="F")
-    for n, u in enumerate(factors):
-        t = np.moveaxis(np.tensordot(u, t, axes=(1, n)), 0, n)
-    return np.asfortranarray(t).ravel(order="F")
+    """G x {U_n} with numpy matmuls on the flat natural layout.
+
+    Mode n views the buffer as the C-ordered array (B, R_n, L) (L = product of
+    the earlier dimensions, B of the later ones) and multiplies by U_n on the
+    left; the modes with the smallest growth go first.
+    """
+    cur = list(ranks)
+    t = np.asarray(core_flat, dtype=np.float64)
+    for n in sorted(range(len(cur)), key=lambda m: factors[m].shape[0] / cur[m]):
+        u = factors[n]
+        lo, hi = math.prod(cur[:n]), math.prod(cur[n + 1:])
+        if lo == 1:
+            t = (t.reshape(hi, cur[n]) @ u.T).reshape(-1)
+        elif hi == 1:
+            t = (u @ t.reshape(cur[n], lo)).reshape(-1)
+        else:
+            t = np.matmul(u, t.reshape(hi, cur[n], lo)).reshape(-1)
+        cur[n] = u.shape[0]
+    return t
 
 
 def tucker_tensor_np(dims, ranks, seed=0, *, decay=0.0, smooth=False, noise=0.0, tensor=0,
@@ -210,6 +225,30 @@ def tucker_tensor_torch(dims, ranks, seed=0, *, decay=0.0, smooth=False, noise=0
     if dtype == "f32":
         x = x.to(torch.float32)
     return x
+
+
+def tucker_prefix_np(dims, ranks, slices, seed=0, *, decay=0.0, smooth=False, noise=0.0, tensor=0):
+    """The first ``slices`` indices of the last mode of the workload ``dims``.
+
+    Because the last mode is the slowest in natural layout, this is a
+    contiguous prefix of the full tensor's buffer: the same core and factors
+    (the last factor's leading rows), with i.i.d. noise at the full tensor's
+    per-entry scale noise * ||X_clean|| / sqrt(prod(dims)), where
+    ||X_clean|| = ||G|| since the factors are orthonormal.  Used for bounded
+    CPU samples of workloads too large for the host oracle.
+    """
+    dims = tuple(int(d) for d in dims)
+    ranks = tuple(int(r) for r in ranks)
+    core = _rng(seed, tensor, _CORE).standard_normal(math.prod(ranks))
+    if decay:
+        core = core * _decay_weights(ranks, decay)
+    us = _factors_np(dims, ranks, seed, tensor, smooth)
+    us[-1] = us[-1][:slices]
+    x = _expand_np(core, ranks, us)
+    if noise:
+        scale = noise * float(np.linalg.norm(core)) / math.sqrt(math.prod(dims))
+        x += scale * _rng(seed, tensor, _NOISE).standard_normal(x.size)
+    return x, dims[:-1] + (int(slices),)
 
 
 def random_dims_ranks(count, seed=0, dim_range=(16, 128), rank_range=(4, 16), n_modes=3):

@@ -1,0 +1,389 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (derived from the float64 arithmetic; u = 2^-53):
+
+* Gram and TTM entries: the rigorous dot-product bound gamma_K * (|A||B|)_ij
+  for each side, K the contraction length, gamma_K = K u / (1 - K u).
+* Eigenvalues: |lam_gpu - lam_oracle| <= 64 J u ||S||_2 (both are backward
+  stable to a few J u ||S||); eigenvectors by residual, orthogonality and
+  Davis-Kahan subspace angles sin(theta) <= 64 J u ||S|| / gap.
+* Rank rule: bit-exact (it is a decision on identical eigenvalues).
+* End to end: identical ranks, |rel_gpu - rel_oracle| <= 1e-12 and principal
+  angles <= 1e-8 between factor subspaces wherever the retained and discarded
+  eigenvalues are separated by (lam_R - lam_{R+1}) / lam_1 >= 1e-4; closer
+  gaps get the Davis-Kahan bound 10 * 1e-14 * lam_1 / gap.  The core is
+  compared after aligning factor signs, to 1e-10 ||G||.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import tucker_tensor_np
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def gamma(k):
+    return k * U / (1 - k * U)
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def principal_sines(a, b):
+    return np.linalg.svd(b - a @ (a.T @ b), compute_uv=False)
+
+
+def view3(x_flat, dims, n):
+    l = math.prod(dims[:n])
+    b = math.prod(dims[n + 1:])
+    return l, dims[n], b
+
+
+# ---------------------------------------------------------------------------
+# a1: ||X||^2
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 7, 1000, 262144 + 13, 3_000_001])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_norm2(gpu_lib, n, dtype):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n)
+    if dtype == "f32":
+        x = x.astype(np.float32)
+    ref = float(np.dot(x.astype(np.float64), x.astype(np.float64)))
+    got = gpu_lib.norm2(dev(x))
+    assert abs(got - ref) <= gamma(max(n, 1)) * ref + 1e-300
+
+
+# ---------------------------------------------------------------------------
+# a2: Gram of the (L, J, B) view, read in place
+# ---------------------------------------------------------------------------
+GRAM_SHAPES = [
+    (1, 1, 1), (1, 5, 3), (1, 64, 4096), (7, 13, 5), (40, 128, 33), (1600, 48, 3),
+    (64000 // 100, 32, 1), (1, 129, 257), (3, 200, 17), (2, 512, 40), (1, 1024, 3),
+]
+
+
+@pytest.mark.parametrize("L,J,B", GRAM_SHAPES)
+def test_gram(gpu_lib, L, J, B):
+    rng = np.random.default_rng(L * 7 + J * 3 + B)
+    y = rng.standard_normal(L * J * B)
+    s = gpu_lib.gram(dev(y), L, J, B).cpu().numpy()
+    t = y.reshape((L, J, B), order="F")
+    yn = oracle.unfold(t, 1)  # J x (L B) mode-2 unfolding of the 3-way view
+    ref = oracle.gram(t, 1)
+    assert np.array_equal(s, s.T)
+    k = L * B
+    bound = 2 * gamma(k) * (np.abs(yn) @ np.abs(yn).T)
+    assert np.all(np.abs(s - ref) <= bound + 1e-300)
+
+
+def test_gram_f32_input(gpu_lib):
+    rng = np.random.default_rng(5)
+    L, J, B = 9, 24, 31
+    y = rng.standard_normal(L * J * B).astype(np.float32)
+    s = gpu_lib.gram(dev(y), L, J, B).cpu().numpy()
+    t = y.astype(np.float64).reshape((L, J, B), order="F")
+    yn = oracle.unfold(t, 1)
+    ref = oracle.gram(t, 1)
+    assert np.all(np.abs(s - ref) <= 2 * gamma(L * B) * (np.abs(yn) @ np.abs(yn).T))
+
+
+def test_gram_deterministic(gpu_lib):
+    rng = np.random.default_rng(6)
+    L, J, B = 33, 96, 700
+    y = dev(rng.standard_normal(L * J * B))
+    a = gpu_lib.gram(y, L, J, B).cpu().numpy()
+    b = gpu_lib.gram(y, L, J, B).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# a3: eigenpairs
+# ---------------------------------------------------------------------------
+def _check_eig(gpu_lib, s):
+    import torch
+
+    j = s.shape[0]
+    lam, v, sweeps = gpu_lib.eig(torch.from_numpy(s).cuda())
+    lam = lam.cpu().numpy()
+    v = v.cpu().numpy()
+    ref_lam, ref_v = oracle.leading_eigenpairs(s)
+    nrm = max(np.linalg.norm(s, 2), 1e-300)
+    tol = 64 * j * U * nrm
+    assert np.all(np.diff(lam) <= 0)
+    assert np.abs(lam - ref_lam).max() <= tol
+    assert np.abs(s @ v - v * lam).max() <= tol
+    assert np.abs(v.T @ v - np.eye(j)).max() <= 64 * j * U
+    # sign rule: largest-magnitude entry of each column is positive
+    for c in range(j):
+        col = v[:, c]
+        assert col[int(np.argmax(np.abs(col)))] > 0
+    # Davis-Kahan on every separated leading subspace
+    for r in range(1, j):
+        gap = ref_lam[r - 1] - ref_lam[r]
+        if gap > 1e-6 * nrm:
+            assert principal_sines(ref_v[:, :r], v[:, :r]).max() <= tol / gap + 1e-15
+    return sweeps
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 8, 17, 64, 127, 128, 129, 200])
+def test_eig_random_psd(gpu_lib, j):
+    rng = np.random.default_rng(j)
+    a = rng.standard_normal((j, 2 * j + 3)) * (0.7 ** np.arange(j))[:, None]
+    _check_eig(gpu_lib, a @ a.T)
+
+
+@pytest.mark.parametrize("j", [5, 48, 130])
+def test_eig_special(gpu_lib, j):
+    import torch
+
+    # identity: every eigenvalue equal, ties keep index order, V = I
+    lam, v, _ = gpu_lib.eig(torch.eye(j, dtype=torch.float64).cuda())
+    assert np.array_equal(lam.cpu().numpy(), np.ones(j))
+    assert np.array_equal(v.cpu().numpy(), np.eye(j))
+    # zero matrix
+    lam, v, _ = gpu_lib.eig(torch.zeros((j, j), dtype=torch.float64).cuda())
+    assert not lam.cpu().numpy().any()
+    # rank-deficient and indefinite diagonal-plus-low-rank
+    rng = np.random.default_rng(j)
+    a = rng.standard_normal((j, 3))
+    _check_eig(gpu_lib, a @ a.T)
+    d = np.diag(np.linspace(-1, 1, j))
+    _check_eig(gpu_lib, d + 1e-3 * (a @ a.T))
+
+
+def test_eig_large_dim(gpu_lib):
+    rng = np.random.default_rng(9)
+    j = 512
+    a = rng.standard_normal((j, 600)) * (0.97 ** np.arange(j))[:, None]
+    _check_eig(gpu_lib, a @ a.T)
+
+
+# ---------------------------------------------------------------------------
+# a4: rank rule (bit-exact)
+# ---------------------------------------------------------------------------
+def test_rank_cut_bit_exact(gpu_lib):
+    import torch
+
+    rng = np.random.default_rng(11)
+    for j in (1, 2, 7, 64, 300, 1024):
+        lam = np.sort(rng.standard_normal(j) ** 4)[::-1].copy()
+        lam[-1] = -abs(lam[-1]) * 1e-3  # a rounding-negative eigenvalue
+        total = float(np.clip(lam, 0, None).sum())
+        for thr in (0.0, 1e-12 * total, 1e-3 * total, 0.1 * total, total, 10 * total):
+            r, tail = gpu_lib.rank_cut(torch.from_numpy(lam).cuda(), thr)
+            rr, tt = oracle.rank_from_eps(lam, thr)
+            assert (r, tail) == (rr, tt)
+        assert gpu_lib.rank_cut(torch.from_numpy(lam).cuda(), 1.0, keep_all=True)[0] == j
+    # equality case: tail == threshold is kept (<=)
+    lam = np.array([4.0, 1.0, 0.5, 0.5])
+    assert gpu_lib.rank_cut(torch.from_numpy(lam).cuda(), 1.0) == (2, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# a6 / a8: mode products (shrinking with U^T, expanding with U)
+# ---------------------------------------------------------------------------
+TTM_SHAPES = [(1, 64, 4096, 8), (40, 128, 33, 40), (7, 13, 5, 13), (1600, 48, 3, 20), (1, 1, 9, 1),
+              (3, 200, 17, 64), (2, 512, 6, 16), (5, 16, 7, 512), (1, 9, 1000, 1024)]
+
+
+@pytest.mark.parametrize("L,J,B,K", TTM_SHAPES)
+@pytest.mark.parametrize("transpose", [True, False])
+def test_ttm(gpu_lib, L, J, B, K, transpose):
+    import torch
+
+    rng = np.random.default_rng(L + J + B + K)
+    y = rng.standard_normal(L * J * B)
+    m = rng.standard_normal((J, K) if transpose else (K, J))
+    mk = m.T if transpose else m
+    z = gpu_lib.ttm(dev(y), L, J, B, torch.from_numpy(m).cuda(), transpose=transpose).cpu().numpy()
+    t = y.reshape((L, J, B), order="F")
+    ref = np.asarray(oracle.ttm(t, 1, mk)).ravel(order="F")
+    absref = np.asarray(oracle.ttm(np.abs(t), 1, np.abs(mk))).ravel(order="F")
+    assert np.all(np.abs(z - ref) <= 2 * gamma(J) * absref + 1e-300)
+
+
+def test_ttm_f32_input(gpu_lib):
+    import torch
+
+    rng = np.random.default_rng(3)
+    L, J, B, K = 6, 20, 11, 7
+    y = rng.standard_normal(L * J * B).astype(np.float32)
+    m = rng.standard_normal((J, K))
+    z = gpu_lib.ttm(dev(y), L, J, B, torch.from_numpy(m).cuda(), transpose=True).cpu().numpy()
+    t = y.astype(np.float64).reshape((L, J, B), order="F")
+    ref = np.asarray(oracle.ttm(t, 1, m.T)).ravel(order="F")
+    absref = np.asarray(oracle.ttm(np.abs(t), 1, np.abs(m.T))).ravel(order="F")
+    assert np.all(np.abs(z - ref) <= 2 * gamma(J) * absref)
+
+
+# ---------------------------------------------------------------------------
+# end to end: Algorithm 1, reconstruction and relative error
+# ---------------------------------------------------------------------------
+def compare_sthosvd(gpu_lib, x, dims, eps, order=None, dtype="f64"):
+    xin = x.astype(np.float32) if dtype == "f32" else x
+    xo = xin.astype(np.float64)
+    ref = oracle.sthosvd(xo, dims, eps, order)
+    xd = dev(xin)
+    res = gpu_lib.sthosvd(xd, dims, eps, order)
+    assert res.ranks == ref["ranks"]
+    assert res.norm2 == pytest.approx(ref["norm2"], rel=1e-13)
+    n_modes = len(dims)
+    flips = []
+    for n in range(n_modes):
+        u = res.factor(n).cpu().numpy()
+        v = ref["factors"][n]
+        lam = ref["eigvals"][n]
+        r = ref["ranks"][n]
+        assert np.abs(u.T @ u - np.eye(r)).max() <= 1e-13 * dims[n]
+        # eigenvalues
+        assert np.abs(np.asarray(res.eigvals[n]) - lam).max() <= 1e-12 * max(lam[0], 1e-300)
+        gap = (lam[r - 1] - lam[r]) if r < dims[n] else lam[r - 1]
+        lim = 1e-8 if gap >= 1e-4 * lam[0] else max(1e-8, 10 * 1e-14 * lam[0] / max(gap, 1e-300))
+        if r < dims[n]:
+            assert principal_sines(v, u).max() <= lim, (n, gap / lam[0])
+        flips.append(np.sign(np.sum(u * v, axis=0)))
+    # core after aligning signs column by column
+    g = res.core().cpu().numpy().reshape(res.ranks, order="F")
+    for n, f in enumerate(flips):
+        shape = [1] * n_modes
+        shape[n] = -1
+        g = g * f.reshape(shape)
+    gref = ref["core"].reshape(ref["ranks"], order="F")
+    gn = max(np.linalg.norm(gref), 1e-300)
+    if all(
+        (ref["eigvals"][n][ref["ranks"][n] - 1] - (ref["eigvals"][n][ref["ranks"][n]] if ref["ranks"][n] < dims[n]
+                                                     else 0.0)) >= 1e-4 * ref["eigvals"][n][0]
+        for n in range(n_modes)
+    ):
+        # within-subspace rotations are fixed only where the retained eigenvalues are separated
+        sep = all(np.min(-np.diff(ref["eigvals"][n][: ref["ranks"][n]]), initial=np.inf) >= 1e-6 * ref["eigvals"][n][0]
+                  for n in range(n_modes))
+        if sep:
+            assert np.abs(g - gref).max() <= 1e-10 * gn
+    rel = gpu_lib.rel_error(xd, res)
+    rel_ref = oracle.rel_error(xo, ref["core"], ref["ranks"], ref["factors"])
+    assert abs(rel - rel_ref) <= 1e-12, (rel, rel_ref)
+    if eps > 0:
+        assert rel <= eps * (1 + 1e-9)
+    return res, ref
+
+
+def test_cube64(gpu_lib):
+    """64^3, core 8^3, noise 1e-4, eps 1e-3, order 1,2,3."""
+    dims = (64, 64, 64)
+    x = tucker_tensor_np(dims, (8, 8, 8), seed=0, noise=1e-4)
+    res, ref = compare_sthosvd(gpu_lib, x, dims, 1e-3, (0, 1, 2))
+    assert res.ranks == (8, 8, 8)
+
+
+@pytest.mark.parametrize("order", [(0, 1, 2, 3, 4), (4, 3, 2, 1, 0), (2, 0, 4, 1, 3)])
+@pytest.mark.parametrize("eps", [1e-5, 1e-3])
+def test_combustion_shaped_small(gpu_lib, order, eps):
+    """The 5-way generator (decaying core, smoothed factors) at a size the oracle runs in a second."""
+    dims, ranks = (40, 36, 32, 12, 10), (12, 12, 12, 6, 4)
+    x = tucker_tensor_np(dims, ranks, seed=1, decay=0.15, smooth=True, noise=1e-6)
+    compare_sthosvd(gpu_lib, x, dims, eps, order)
+
+
+def test_f32_input(gpu_lib):
+    dims, ranks = (30, 28, 26, 10, 8), (10, 10, 10, 5, 3)
+    x = tucker_tensor_np(dims, ranks, seed=2, decay=0.15, smooth=True, noise=1e-6)
+    compare_sthosvd(gpu_lib, x, dims, 1e-4, None, dtype="f32")
+
+
+@pytest.mark.parametrize("dims,ranks,eps", [
+    ((37,), (1,), 0.5),                  # N = 1
+    ((50, 33), (6, 6), 1e-3),            # matrix: truncated SVD
+    ((1, 9, 1, 7), (1, 3, 1, 2), 1e-2),  # unit modes
+    ((17, 13, 11), (4, 5, 3), 0.0),      # eps = 0 keeps everything
+    ((17, 13, 11), (4, 5, 3), -1.0),
+    ((129, 5, 6), (7, 3, 2), 1e-3),      # J above the shared-memory eigensolver
+    ((3, 2, 300), (2, 2, 4), 1e-3),
+])
+def test_edge_shapes(gpu_lib, dims, ranks, eps):
+    x = tucker_tensor_np(dims, ranks, seed=3, noise=1e-3)
+    res, _ = compare_sthosvd(gpu_lib, x, dims, eps)
+    if eps <= 0:
+        assert res.ranks == dims
+
+
+def test_exact_low_rank_recovery(gpu_lib):
+    dims, ranks = (20, 18, 16, 9), (3, 4, 2, 3)
+    x = tucker_tensor_np(dims, ranks, seed=4)
+    res, _ = compare_sthosvd(gpu_lib, x, dims, 1e-6)
+    assert res.ranks == ranks
+    assert gpu_lib.rel_error(dev(x), res) < 1e-13
+
+
+def test_zero_tensor(gpu_lib):
+    dims = (6, 5, 4)
+    x = np.zeros(math.prod(dims))
+    res = gpu_lib.sthosvd(dev(x), dims, 1e-3)
+    assert res.ranks == (1, 1, 1)
+    assert not res.core().cpu().numpy().any()
+    assert gpu_lib.rel_error(dev(x), res) == 0.0
+
+
+def test_reconstruct_matches_oracle(gpu_lib):
+    dims, ranks = (21, 19, 17, 5), (4, 6, 3, 2)
+    x = tucker_tensor_np(dims, ranks, seed=5, noise=1e-2)
+    xd = dev(x)
+    res = gpu_lib.sthosvd(xd, dims, 5e-2)
+    xr = gpu_lib.reconstruct(res).cpu().numpy()
+    xr_ref = oracle.reconstruct(res.core().cpu().numpy(), res.ranks, [f.cpu().numpy() for f in res.factors()])
+    assert np.abs(xr - xr_ref).max() <= 1e-13 * np.abs(x).max()
+    # Pythagoras: ||X - X~||^2 = sum of discarded tails (Sec. 6.2 bound, tight for ST-HOSVD)
+    err2 = float(((x - xr) ** 2).sum())
+    assert err2 == pytest.approx(sum(res.tails), rel=1e-8)
+
+
+def test_host_entry_point(gpu_lib):
+    import torch
+
+    dims, ranks = (24, 20, 18), (5, 4, 3)
+    x = tucker_tensor_np(dims, ranks, seed=6, noise=1e-3)
+    xh = torch.from_numpy(x).pin_memory()
+    res_h = gpu_lib.sthosvd_host(xh, dims, 1e-2)
+    res_d = gpu_lib.sthosvd(dev(x), dims, 1e-2)
+    assert res_h.on_host and res_h.ranks == res_d.ranks
+    assert torch.equal(res_h.core(), res_d.core().cpu())
+    for n in range(3):
+        assert torch.equal(res_h.factor(n), res_d.factor(n).cpu())
+
+
+def test_run_to_run_identical(gpu_lib):
+    dims, ranks = (48, 40, 30, 12), (8, 8, 6, 4)
+    x = dev(tucker_tensor_np(dims, ranks, seed=7, decay=0.1, noise=1e-5))
+    a = gpu_lib.sthosvd(x, dims, 1e-4)
+    b = gpu_lib.sthosvd(x, dims, 1e-4)
+    assert a.ranks == b.ranks
+    assert np.array_equal(a.core().cpu().numpy(), b.core().cpu().numpy())
+
+
+def test_nonfinite_input_is_reported(gpu_lib):
+    x = np.ones(60)
+    x[17] = np.nan
+    with pytest.raises(gpu_lib.TuckerError) as e:
+        gpu_lib.sthosvd(dev(x), (3, 4, 5), 1e-3)
+    assert e.value.status == -6
+
+
+def test_host_side_fault_injection(gpu_lib, monkeypatch):
+    dims = (6, 5, 4)
+    x = dev(tucker_tensor_np(dims, (2, 2, 2), seed=8, noise=1e-2))
+    for fault, status in (("noconv", -4), ("alloc", -2), ("nan", -6)):
+        monkeypatch.setenv("TUCKER_FAULT", fault)
+        with pytest.raises(gpu_lib.TuckerError) as e:
+            gpu_lib.sthosvd(x, dims, 1e-3)
+        assert e.value.status == status
+    monkeypatch.delenv("TUCKER_FAULT")
+    assert gpu_lib.sthosvd(x, dims, 1e-3).ranks == (2, 2, 2)  # context still usable
