@@ -210,6 +210,19 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ 
   }
 }
 
+// Resident CTAs per SM for a launch shape; the dynamic shared memory limit is
+// raised to exactly `smem` first.  Failures of these optional queries are
+// cleared so they cannot surface as a later launch error.
+template <typename K>
+int occupancy(K kernel, int threads, size_t smem) {
+  int occ = 1;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess)
+    occ = 1;
+  cudaGetLastError();
+  return occ < 1 ? 1 : occ;
+}
+
 GramPlan gram_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   GramPlan p{};
   p.J = (int)J;
@@ -224,10 +237,7 @@ GramPlan gram_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   p.K = L * B;
   // One balanced wave: as many splits as resident CTAs allow, never more
   // splits than column chunks.
-  int occ = 1;
-  cudaFuncSetAttribute(k_gram_partial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev.smem_optin);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_partial<double>, p.threads, p.smem);
-  occ = std::max(occ, 1);
+  int occ = occupancy(k_gram_partial<double>, p.threads, p.smem);
   const int64_t slots = (int64_t)dev.sms * occ;
   const int64_t chunks = (p.K + p.kc - 1) / p.kc;
   int64_t ns = std::max<int64_t>(1, slots / p.groups);
@@ -361,10 +371,7 @@ TtmPlan ttm_plan(int64_t L, int64_t J, int64_t B, int64_t K, const DeviceInfo &d
   p.ncg = p.kc / 4;
   p.threads = (p.nkg * p.ncg + 31) / 32 * 32;
   p.smem = ((size_t)p.J * p.ktp + (size_t)p.J * p.kc) * sizeof(double);
-  int occ = 1;
-  cudaFuncSetAttribute(k_ttm<T, TX, DIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev.smem_optin);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ttm<T, TX, DIFF>, p.threads, p.smem);
-  occ = std::max(occ, 1);
+  int occ = occupancy(k_ttm<T, TX, DIFF>, p.threads, p.smem);
   const int64_t slots = (int64_t)dev.sms * occ;
   const int64_t chunks = (p.Kc + p.kc - 1) / p.kc;
   int64_t xs = std::max<int64_t>(1, slots / p.ktiles);
@@ -381,7 +388,7 @@ int set_smem(K kernel, size_t bytes, const DeviceInfo &dev) {
     set_error("kernel needs %zu bytes of shared memory, device allows %d", bytes, dev.smem_optin);
     return TUCKER_EUNSUPPORTED;
   }
-  if (bytes > 48 * 1024) TK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  TK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return TUCKER_OK;
 }
 
