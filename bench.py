@@ -38,9 +38,13 @@ METRIC = "ST-HOSVD input GB/s & Gram TFLOP/s, split-prec vs FP64 on GB300, equal
 WORKLOAD = "combustion5"
 # Float64 pipe peak of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# ncu DRAM traffic of the Gram kernel (read + write bytes per launch), keyed by
-# the hash of the kernel source it was captured with; see profiles/.
-TRAFFIC = {}
+# ncu DRAM traffic of the Gram kernel, keyed by the hash of the kernel source it
+# was captured with (profiles/k_gram_partial_combustion5_t2.md): measured
+# dram__bytes_read.sum + dram__bytes_write.sum of the mode-1 launch on the
+# 128x128x128x48x2 case divided by that launch's algorithmic bytes.  The
+# reported traffic is this ratio times the per-launch algorithmic bytes of the
+# timed run; it is dropped as soon as the kernel source changes.
+TRAFFIC = {"f172da5c229e3897": {"ratio": 1.6274e9 / 1.6260e9, "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"}}
 
 
 def kernel_source_hash():
@@ -58,6 +62,8 @@ def parse_args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--eps", type=float, default=1e-5)
     p.add_argument("--cpu-slices", type=int, default=8, help="time slices in the CPU oracle sample")
+    p.add_argument("--slices", type=int, default=None,
+                   help="keep only the first SLICES of the 32 time slices (smaller case for profiling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -213,7 +219,7 @@ def config_dict(w, eps, precision):
         "workload": f"{w.name}: {'x'.join(map(str, w.dims))} float64 Tucker-form tensor, ranks "
                     f"{tuple(w.ranks)}, core decay exp(-{w.decay} sum i), smoothed factors, noise {w.noise}",
         "eps": eps, "mode_order": "1,2,3,4,5", "precision": precision,
-        "input_bytes": w.nbytes, "l2_policy": "input 25.8 GB >> 129 MB L2 (no flush needed)",
+        "input_bytes": w.nbytes, "l2_policy": f"input {w.nbytes / 1e9:.1f} GB >> 129 MB L2 (no flush needed)",
         "parallelism": "replicas (one independent tensor per GPU)",
     }
 
@@ -237,6 +243,12 @@ def main():
     barrier(world)
     tucker.load()
     w = WORKLOADS[WORKLOAD]
+    if args.slices:
+        import dataclasses
+
+        t = max(1, min(args.slices, w.dims[-1]))
+        w = dataclasses.replace(w, name=f"{w.name}[time<{t}]", dims=w.dims[:-1] + (t,),
+                                ranks=w.ranks[:-1] + (min(w.ranks[-1], t),))
     dims = w.dims
     x = tucker_tensor_torch(dims, w.ranks, seed=rank, decay=w.decay, smooth=w.smooth, noise=w.noise,
                             device="cuda")
@@ -283,7 +295,9 @@ def main():
     per_launch_flops = gram["flops"] / max(gram["launches"], 1)
     step_ms_sum = sum(v["ms"] for v in prof.values()) / args.steps
     shares = {k: round(v["ms"] / args.steps / ms, 4) for k, v in prof.items()}
-    traffic = TRAFFIC.get(kernel_source_hash())
+    tr = TRAFFIC.get(kernel_source_hash())
+    per_launch_bytes = gram["bytes"] / max(gram["launches"], 1)
+    traffic = round(tr["ratio"] * per_launch_bytes) if tr else None
     roofline = {
         "kernel": "k_gram_partial (float64 split-K symmetric Gram)",
         "bound": "alu", "achieved": round(per_launch_flops / (per_launch_ms / 1e3) / 1e12, 4),
@@ -293,6 +307,9 @@ def main():
         "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 1.25 TFLOP/s; "
                        "measured DFMA loop 1.193 TFLOP/s)",
         "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4),
+        "per_launch_algorithmic_bytes": round(per_launch_bytes),
+        "traffic_source": ("ncu ratio DRAM/algorithmic bytes " + tr["captured"] + ", scaled to the timed launches")
+        if tr else "kernel changed since the last ncu capture",
     }
 
     line = {
