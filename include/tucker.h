@@ -177,6 +177,25 @@ TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, i
 TUCKER_API int tucker_ttm(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *M, int64_t K,
                int trans_m, double *Z, void *stream);
 
+/* tucker_gram_noalloc -- the Gram step of tucker_gram, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: it is an addition for
+ * callers such as a process whose framework has already reserved nearly all
+ * of the GPU's memory for its own pool, or code that must not trigger the
+ * device-wide synchronisation that cudaMalloc/cudaFree can cause.
+ *   Same arguments, layout and result as tucker_gram (the caller passes Y and S).
+ *   The split-K partial sums live in a static device array of
+ *   TUCKER_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until
+ *   the process exits; the call allocates nothing.  Requests whose partial sums
+ *   cannot fit (J > TUCKER_MAX_DIM) return TUCKER_EINVAL with a message.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls on a device share the array: calls whose kernels overlap on the
+ *   GPU (different streams or host threads) race and must be serialised.
+ *   Stream-ordered; does not synchronise. */
+#define TUCKER_NOALLOC_SCRATCH_BYTES (16ll << 20)
+TUCKER_API int tucker_gram_noalloc(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
+                                   void *stream);
+
 /* ---------------------------------------------------------------------------
  * Diagnostics.
  * ------------------------------------------------------------------------- */

@@ -12,6 +12,7 @@
 // memory.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -510,3 +511,105 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
 }
 
 }  // namespace tk
+
+// ---------------------------------------------------------------------------
+// Gram step for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: a process whose framework has already
+// reserved nearly all of the GPU's memory for its own pool (a library
+// allocation then fails or takes memory the pool counts on), and code that
+// must not trigger the device-wide synchronisation cudaMalloc/cudaFree can
+// cause.  tucker_gram_noalloc runs the same two kernels as tucker_gram, with
+// the split-K partial sums in the file-scope array below instead of an
+// allocation.  The array is TUCKER_NOALLOC_SCRATCH_BYTES (16 MiB) of device
+// memory that every GPU which loads this library holds until the process
+// exits.  Every call on a device shares it and it keeps the last call's
+// partial sums; nothing in it has to start at zero, because each call writes
+// every slot its reduction reads before reading it.  Two calls whose kernels
+// overlap on the GPU (other streams, or other host threads) race on the
+// array: order them on one stream or serialise them.
+// ---------------------------------------------------------------------------
+namespace tk {
+namespace {
+
+constexpr int64_t kNoallocDoubles = TUCKER_NOALLOC_SCRATCH_BYTES / sizeof(double);
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device.  In host code
+// the symbol names a host-side stand-in, so the address is looked up once per
+// device (the first call on that device does it) and cached.
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return TUCKER_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("cudaGetSymbolAddress of the Gram scratch failed on device %d: %s", dev, cudaGetErrorString(e));
+      return TUCKER_ECUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TUCKER_OK;
+}
+
+template <typename T>
+int gram_noalloc_typed(const T *y, int64_t L, int64_t J, int64_t B, double *d_S, const DeviceInfo &dev,
+                       cudaStream_t s) {
+  GramPlan p = gram_plan(L, J, B, dev);
+  const int64_t per_split = (int64_t)p.n_micro * 16;
+  const int64_t max_splits = kNoallocDoubles / per_split;
+  if (max_splits < 1) {
+    set_error("tucker_gram_noalloc: J = %lld needs %lld bytes of scratch for one split, the static scratch holds %lld",
+              (long long)J, (long long)(per_split * 8), (long long)TUCKER_NOALLOC_SCRATCH_BYTES);
+    return TUCKER_EINVAL;
+  }
+  if (p.nsplit > max_splits) {  // fewer, longer column ranges so the partials fit
+    const int64_t chunks = (p.K + p.kc - 1) / p.kc;
+    const int64_t chunks_per = (chunks + max_splits - 1) / max_splits;
+    p.cols_per_split = chunks_per * p.kc;
+    p.nsplit = (int)((p.K + p.cols_per_split - 1) / p.cols_per_split);
+  }
+  double *ws = nullptr;
+  TK_CHECK(noalloc_scratch(&ws));
+  TK_CHECK(set_smem(k_gram_partial<T>, p.smem, dev));
+  k_gram_partial<T><<<dim3(p.groups, p.nsplit), p.threads, p.smem, s>>>(y, L, B, p, ws);
+  TK_LAUNCHED();
+  const int64_t n = per_split;
+  k_gram_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws, p, d_S);
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+}  // namespace tk
+
+extern "C" int tucker_gram_noalloc(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
+                                   void *stream) {
+  using namespace tk;
+  if (!Y || !S || L < 1 || B < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("invalid arguments to tucker_gram_noalloc");
+    return TUCKER_EINVAL;
+  }
+  if (J < 1 || J > TUCKER_MAX_DIM) {
+    set_error("tucker_gram_noalloc: J = %lld outside [1, %d] (the static scratch is sized for J <= %d)",
+              (long long)J, TUCKER_MAX_DIM, TUCKER_MAX_DIM);
+    return TUCKER_EINVAL;
+  }
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dt == TUCKER_F64) return gram_noalloc_typed(static_cast<const double *>(Y), L, J, B, S, dev, s);
+  return gram_noalloc_typed(static_cast<const float *>(Y), L, J, B, S, dev, s);
+}

@@ -26,6 +26,7 @@ EXPORTS = (
     "tucker_sthosvd", "tucker_sthosvd_host", "tucker_reconstruct", "tucker_rel_error", "tucker_result_free",
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
+    "tucker_gram_noalloc",
 )
 
 
@@ -87,6 +88,7 @@ def load(path=LIB_PATH):
         "tucker_eig": (i32, [vp, i64, vp, vp, pi32, vp]),
         "tucker_rank_cut": (i32, [vp, i64, dbl, i32, pi64, pdbl, vp]),
         "tucker_ttm": (i32, [vp, i32, i64, i64, i64, vp, i64, i32, vp, vp]),
+        "tucker_gram_noalloc": (i32, [vp, i32, i64, i64, i64, vp, vp]),
         "tucker_status_string": (ctypes.c_char_p, [i32]),
         "tucker_last_error": (ctypes.c_char_p, []),
         "tucker_launch_count": (i64, []),
@@ -272,6 +274,17 @@ def gram(y, L, J, B, stream=None):
     _check(lib.tucker_gram(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
                            _stream(stream)))
     return s.t()  # column-major storage -> logical S
+
+
+def gram_noalloc(y, L, J, B, out=None, stream=None):
+    """Same result as :func:`gram`, computed without any device allocation by the
+    library (its split-K scratch is a static device array).  ``out`` (J x J
+    float64, caller-allocated) receives S when given."""
+    lib = load()
+    s = out if out is not None else torch.empty((J, J), dtype=torch.float64, device="cuda")
+    _check(lib.tucker_gram_noalloc(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
+                                   _stream(stream)))
+    return s.t()
 
 
 def eig(s, stream=None):
