@@ -287,6 +287,7 @@ def main():
     # accuracy of the timed configuration (outside the timed region)
     res = tucker.sthosvd(x, dims, args.eps)
     rel = tucker.rel_error(x, res)
+    sweeps = list(res.sweeps)
     res.free()
 
     gram = prof["gram"]
@@ -317,7 +318,7 @@ def main():
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, "fp64"),
         "gram_tflops": round(gram_tflops, 4) if gram_tflops else None,
-        "ranks": list(ranks), "rel_error": rel,
+        "ranks": list(ranks), "rel_error": rel, "jacobi_sweeps": sweeps,
         "phase_share": shares, "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
         "phase_time_covered": round(step_ms_sum / ms, 4),
         "roofline": roofline, "gpu_launches": launches, "clocks": sampler.summary(),

@@ -16,11 +16,15 @@
 // and |s_pq| exceeds a tiny absolute floor; a sweep without rotations ends
 // the iteration, and the sweep cap ends it with a "not converged" flag (no
 // unbounded loop on the device).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tk {
 
@@ -41,7 +45,7 @@ __device__ __forceinline__ int64_t pidx(int i, int j) {
 }
 
 __device__ __forceinline__ void decode_pair_block(int e, int &P, int &Q) {
-  int q = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+  int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
   while ((q + 1) * (q + 2) / 2 <= e) ++q;
   while (q * (q + 1) / 2 > e) --q;
   Q = q;
@@ -188,6 +192,169 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster Jacobi: the same parallel-order sweeps, spread over the CTAs of one
+// thread-block cluster (up to 16 SMs) so that the float64 work of a step runs
+// on all of them.  S (packed upper triangle), V and the rotation parameters
+// live in a global workspace that stays in L2; loads bypass L1 (__ldcg) so a
+// CTA never reads a line another CTA rewrote.  Each step is two phases
+// separated by hardware cluster barriers: (A) every pair's rotation from the
+// current diagonal entries, (B) the 2 x 2 block updates of S and the column
+// updates of V.  Rotation flags are kept per sweep, so no flag is reset while
+// another CTA may still read it.
+// ---------------------------------------------------------------------------
+constexpr int kClusterThreads = 1024;
+
+__global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const double *__restrict__ S_in, int J,
+                                                                      double *__restrict__ lam,
+                                                                      double *__restrict__ V_out,
+                                                                      double *__restrict__ ws,
+                                                                      int *__restrict__ info) {
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double cs[kMaxPairs], sn[kMaxPairs];
+  __shared__ int pp[kMaxPairs], qq[kMaxPairs];
+  const int m = J + (J & 1);
+  const int np = m / 2;
+  const int64_t packed = (int64_t)m * (m + 1) / 2;
+  double *Sp = ws;
+  double *V = Sp + packed;
+  double *par = V + (int64_t)m * m;                       // np x {c, s}
+  int *flags = reinterpret_cast<int *>(par + 2 * np);     // one per sweep
+  const int rank = (int)cluster.block_rank();
+  const int nct = (int)cluster.num_blocks();
+  const int gtid = rank * blockDim.x + threadIdx.x;
+  const int gthreads = nct * blockDim.x;
+
+  for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i <= j) Sp[pidx(i, j)] = (j < J) ? S_in[i + (int64_t)J * j] : 0.0;
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int k = gtid; k < kMaxSweeps; k += gthreads) flags[k] = 0;
+  double mx = 0.0;
+  for (int i = 0; i < J; ++i) mx = fmax(mx, fabs(S_in[i + (int64_t)J * i]));
+  const double abs_floor = mx * (DBL_EPSILON * DBL_EPSILON) + DBL_MIN;
+  cluster.sync();
+
+  const int nblk = np * (np + 1) / 2;
+  const int64_t items = (int64_t)nblk + (int64_t)np * m;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    for (int step = 0; step < m - 1; ++step) {
+      // (A) rotations of this step
+      for (int t = gtid; t < np; t += gthreads) {
+        int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
+        int q = ((m - 2 - t + step) % (m - 1)) + 1;
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        double c = 1.0, s = 0.0;
+        const double b = __ldcg(Sp + pidx(p, q));
+        if (b != 0.0) {
+          const double a = __ldcg(Sp + pidx(p, p)), d = __ldcg(Sp + pidx(q, q));
+          const double ab = fabs(b);
+          if (ab > DBL_EPSILON * sqrt(fabs(a)) * sqrt(fabs(d)) && ab > abs_floor) {
+            const double tau = (d - a) / (2.0 * b);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+            flags[sweep] = 1;
+          }
+        }
+        __stcg(par + 2 * t, c);
+        __stcg(par + 2 * t + 1, s);
+      }
+      cluster.sync();
+      for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
+        int q = ((m - 2 - t + step) % (m - 1)) + 1;
+        pp[t] = min(p, q);
+        qq[t] = max(p, q);
+        cs[t] = __ldcg(par + 2 * t);
+        sn[t] = __ldcg(par + 2 * t + 1);
+      }
+      __syncthreads();
+      // (B) block updates of S, then column updates of V
+      for (int64_t e = gtid; e < items; e += gthreads) {
+        if (e < nblk) {
+          int P, Q;
+          decode_pair_block((int)e, P, Q);
+          const double s1 = sn[P], s2 = sn[Q];
+          const int p1 = pp[P], q1 = qq[P];
+          if (P == Q) {
+            if (s1 != 0.0) {
+              const double t1 = s1 / cs[P];
+              const int64_t ipq = pidx(p1, q1), ipp = pidx(p1, p1), iqq = pidx(q1, q1);
+              const double b = __ldcg(Sp + ipq);
+              __stcg(Sp + ipp, __ldcg(Sp + ipp) - t1 * b);
+              __stcg(Sp + iqq, __ldcg(Sp + iqq) + t1 * b);
+              __stcg(Sp + ipq, 0.0);
+            }
+            continue;
+          }
+          if (s1 == 0.0 && s2 == 0.0) continue;
+          const double c1 = cs[P], c2 = cs[Q];
+          const int p2 = pp[Q], q2 = qq[Q];
+          const int64_t i11 = pidx(p1, p2), i12 = pidx(p1, q2), i21 = pidx(q1, p2), i22 = pidx(q1, q2);
+          const double x11 = __ldcg(Sp + i11), x12 = __ldcg(Sp + i12);
+          const double x21 = __ldcg(Sp + i21), x22 = __ldcg(Sp + i22);
+          const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          __stcg(Sp + i11, y11 * c2 - y12 * s2);
+          __stcg(Sp + i12, y11 * s2 + y12 * c2);
+          __stcg(Sp + i21, y21 * c2 - y22 * s2);
+          __stcg(Sp + i22, y21 * s2 + y22 * c2);
+        } else {
+          const int64_t r = e - nblk;
+          const int t = (int)(r / m), i = (int)(r - (int64_t)t * m);
+          const double s = sn[t];
+          if (s == 0.0) continue;
+          const double c = cs[t];
+          double *vp = V + (int64_t)pp[t] * m + i;
+          double *vq = V + (int64_t)qq[t] * m + i;
+          const double a = __ldcg(vp), b = __ldcg(vq);
+          __stcg(vp, c * a - s * b);
+          __stcg(vq, s * a + c * b);
+        }
+      }
+      cluster.sync();
+    }
+    if (__ldcg(flags + sweep) == 0) {
+      converged = true;
+      break;
+    }
+  }
+
+  for (int i = gtid; i < J; i += gthreads) {
+    const double di = __ldcg(Sp + pidx(i, i));
+    int rk = 0;
+    for (int j = 0; j < J; ++j) {
+      const double dj = __ldcg(Sp + pidx(j, j));
+      rk += (dj > di) || (dj == di && j < i);
+    }
+    lam[rk] = di;
+    const double *col = V + (int64_t)i * m;
+    double best = -1.0;
+    int br = 0;
+    for (int r = 0; r < J; ++r) {
+      const double v = fabs(__ldcg(col + r));
+      if (v > best) {
+        best = v;
+        br = r;
+      }
+    }
+    const double sg = __ldcg(col + br) < 0.0 ? -1.0 : 1.0;
+    for (int r = 0; r < J; ++r) V_out[r + (int64_t)J * rk] = sg * __ldcg(col + r);
+  }
+  if (gtid == 0) {
+    info[0] = converged ? sweep + 1 : kMaxSweeps;
+    info[1] = converged ? 0 : 1;
+  }
+}
+
 // Rank rule of Algorithm 1: tails[r] = sum_{k >= r} max(lam[k], 0) accumulated
 // from the smallest eigenvalue upward; R = smallest r in [1, J] with
 // tails[r] <= threshold.
@@ -217,15 +384,68 @@ __global__ void k_rank_cut(const double *__restrict__ lam, int J, double thresho
 
 }  // namespace
 
+// J up to this size runs in one CTA with S and V in shared memory; larger J
+// run on a cluster.
+constexpr int kOneCtaMaxJ = 32;
+
 int64_t eig_workspace_doubles(int64_t J) {
-  if (J <= kSmemMaxJ) return 0;
   const int64_t m = J + (J & 1);
-  return m * (m + 1) / 2 + m * m;
+  if (J <= kOneCtaMaxJ) return 0;
+  return m * (m + 1) / 2 + m * m + m + kMaxSweeps;  // S, V, rotations, flags
+}
+
+// Largest cluster (16 with the non-portable opt-in, else 8) the device can
+// co-schedule for k_jacobi_cluster.
+static int cluster_size_for_eig() {
+  static int cached = 0;
+  if (cached) return cached;
+  int best = 8;
+  if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kClusterThreads);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 16;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_jacobi_cluster, &cfg) == cudaSuccess && n >= 1) best = 16;
+  }
+  cudaGetLastError();
+  cached = best;
+  return best;
 }
 
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof) {
   const int64_t m = J + (J & 1);
+  if (J > kOneCtaMaxJ) {
+    if (!d_ws) {
+      set_error("eigensolver workspace missing for J = %lld", (long long)J);
+      return TUCKER_EINVAL;
+    }
+    const int csize = cluster_size_for_eig();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = csize;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if (prof) prof->begin(TUCKER_PHASE_EIG);
+    TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, d_S, (int)J, d_lam, d_V, d_ws, d_info));
+    TK_LAUNCHED();
+    if (prof) prof->end(0.0, (double)J * J * 16, 1);
+    return TUCKER_OK;
+  }
   size_t smem = 0;
   double *ws = nullptr;
   if (J <= kSmemMaxJ) {
