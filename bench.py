@@ -64,6 +64,8 @@ def parse_args():
     p.add_argument("--cpu-slices", type=int, default=8, help="time slices in the CPU oracle sample")
     p.add_argument("--slices", type=int, default=None,
                    help="keep only the first SLICES of the 32 time slices (smaller case for profiling)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "bf16x4"],
+                   help="Gram arithmetic of the timed line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -256,7 +258,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3)):
-        res = tucker.sthosvd(x, dims, args.eps)
+        res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
         res.free()
     torch.cuda.synchronize()
 
@@ -270,7 +272,7 @@ def main():
     ev0.record(stream)
     ranks = None
     for _ in range(args.steps):
-        res = tucker.sthosvd(x, dims, args.eps)
+        res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
         ranks = res.ranks
         res.free()
     ev1.record(stream)
@@ -285,7 +287,7 @@ def main():
     value = world * w.nbytes / (ms / 1e3) / 1e9
 
     # accuracy of the timed configuration (outside the timed region)
-    res = tucker.sthosvd(x, dims, args.eps)
+    res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
     rel = tucker.rel_error(x, res)
     sweeps = list(res.sweeps)
     res.free()
@@ -316,7 +318,7 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, "fp64"),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, args.precision),
         "gram_tflops": round(gram_tflops, 4) if gram_tflops else None,
         "ranks": list(ranks), "rel_error": rel, "jacobi_sweeps": sweeps,
         "phase_share": shares, "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},

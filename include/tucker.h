@@ -66,8 +66,13 @@ typedef enum {
 /* Element type of an input tensor.  Internal tensors are always float64. */
 typedef enum { TUCKER_F64 = 0, TUCKER_F32 = 1 } tucker_dtype;
 
-/* Arithmetic of the Gram step.  TUCKER_PREC_FP64 is the plain method. */
-typedef enum { TUCKER_PREC_FP64 = 0 } tucker_precision;
+/* Arithmetic of the Gram step.  TUCKER_PREC_FP64 is the plain method.
+ * TUCKER_PREC_BF16X4 forms each Gram on the BF16 tensor cores from four exact
+ * 7-bit integer slices of every entry (28 bits below a power-of-two bound of
+ * max|Y|), with exact FP32 accumulation in tensor memory and float64
+ * reduction (see tucker_gram_split); eigensolve, rank rule and TTM stay
+ * float64.  It needs J_n <= 128 at every mode. */
+typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_BF16X4 = 1 } tucker_precision;
 
 /* Result of an ST-HOSVD (Algorithm 1's output (G, {U_n}) plus diagnostics).
  * Owned by the library; release with tucker_result_free(). */
@@ -167,6 +172,23 @@ TUCKER_API int tucker_eig(const double *S, int64_t J, double *lam, double *V, in
  * returns R = J.  lam is device (descending); R and tail are host; synchronises. */
 TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, int keep_all, int64_t *R, double *tail,
                     void *stream);
+
+/* Split-precision Gram step: the Gram of tucker_gram (same view, layout and
+ * output) computed on the BF16 tensor cores (tcgen05, accumulators in tensor
+ * memory).  With 2^E the smallest power of two above max|Y|, each entry is
+ * rounded to the integer v = round(y 2^(28-E)) and split into four balanced
+ * digits (|s1| <= 128, |s2|,|s3|,|s4| <= 64) that BF16 holds exactly; digit
+ * products of level p+q <= 5 are accumulated exactly in FP32 (drained every
+ * 512 columns), the dropped levels' diagonal squares are added back exactly,
+ * and the float64 result is (C + C^T)/2 2^(2E-56).  The difference from the
+ * float64 Gram is the rounding of Y to 28 bits below 2^E plus zero-mean
+ * off-diagonal terms of relative size ~2^-24 / sqrt(L B).
+ *   maxabs  an upper bound of max|Y| (the largest magnitude), or <= 0 to let
+ *           the call compute it (one extra pass over Y).
+ *   J <= 128 (else TUCKER_EUNSUPPORTED).  Synchronises `stream`; returns
+ *   TUCKER_ETIMEOUT if a bounded tensor-core wait expired. */
+TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs,
+                                 double *S, void *stream);
 
 /* TTM step of Algorithm 1 (Sec. 2.1 mode-n product): Z = Y x_n M with Y viewed as
  * (L, J, B) and Z as (L, K, B): Z[l + L(k + K b)] = sum_j M[k, j] Y[l + L(j + J b)].

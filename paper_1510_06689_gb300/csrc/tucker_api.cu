@@ -252,7 +252,7 @@ static void free_result_device(tucker_result *r) {
 // Algorithm 1
 // ---------------------------------------------------------------------------
 static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *order,
-                        cudaStream_t s, tucker_result *out) {
+                        tucker_precision prec, cudaStream_t s, tucker_result *out) {
   DeviceInfo dev;
   TK_CHECK(device_info(&dev));
   Prof prof(s);
@@ -275,6 +275,15 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   double *d_tail = d_nx2 + 1;
   int64_t *d_rank = reinterpret_cast<int64_t *>(d_nx2 + 2);
   int *d_info = reinterpret_cast<int *>(d_nx2 + 3);
+  double *d_max = d_nx2 + 4;
+  if (prec == TUCKER_PREC_BF16X4) {
+    TK_CHECK(partials.alloc(sizeof(double) * std::max(norm2_partials(), maxabs_partials()), s));
+    for (int n = 0; n < N; ++n)
+      if (dims[n] > 128) {
+        set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);
+        return TUCKER_EUNSUPPORTED;
+      }
+  }
 
   void *host = nullptr;
   TK_CHECK(pinned(sizeof(double) * (8 + maxJ), &host));
@@ -325,9 +334,20 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     const int64_t J = cur[n];
 
     // Gram step
-    const int64_t gws = gram_workspace_doubles(L, J, B, dev);
-    TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
-    TK_CHECK(launch_gram(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
+    if (prec == TUCKER_PREC_BF16X4) {
+      const int64_t I_cur = L * J * B;
+      TK_CHECK(launch_maxabs(Y, ydt, I_cur, partials.as<double>(), d_max, s));
+      TK_CUDA(cudaMemcpyAsync(h + 4, d_max, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
+      TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
+      TK_CHECK(launch_gram_split(Y, ydt, L, J, B, h[4], S.as<double>(), gramws.as<double>(), dev, s, &prof));
+      TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
+    } else {
+      const int64_t gws = gram_workspace_doubles(L, J, B, dev);
+      TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
+      TK_CHECK(launch_gram(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
+    }
     // eigenvector step
     const int64_t ews = eig_workspace_doubles(J);
     if (ews > 0) TK_CHECK(eigws.alloc(sizeof(double) * ews, s));
@@ -338,6 +358,10 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     TK_CUDA(cudaMemcpyAsync(h, d_tail, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(h + 8, lam.as<double>(), sizeof(double) * J, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
+    if (prec == TUCKER_PREC_BF16X4 && reinterpret_cast<int *>(h + 5)[0] != 0) {
+      set_error("split-precision Gram: a bounded tensor-core wait expired (mode %d)", n);
+      return TUCKER_ETIMEOUT;
+    }
     const double tail = h[0];
     int64_t R;
     int info[2];
@@ -523,7 +547,7 @@ int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, d
     set_error("unknown dtype %d", (int)dt);
     return TUCKER_EINVAL;
   }
-  if (prec != TUCKER_PREC_FP64) {
+  if (prec != TUCKER_PREC_FP64 && prec != TUCKER_PREC_BF16X4) {
     set_error("unknown precision %d", (int)prec);
     return TUCKER_EINVAL;
   }
@@ -534,7 +558,7 @@ int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, d
   TK_CHECK(check_dims(dims, N));
   int order[TUCKER_MAX_MODES];
   TK_CHECK(check_order(mode_order, N, order));
-  int st = sthosvd_impl(X, dt, dims, N, eps, order, static_cast<cudaStream_t>(stream), out);
+  int st = sthosvd_impl(X, dt, dims, N, eps, order, prec, static_cast<cudaStream_t>(stream), out);
   if (st != TUCKER_OK) {
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     memset(out, 0, sizeof *out);
@@ -703,6 +727,46 @@ int tucker_gram(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B,
   if (prof.on) {
     TK_CUDA(cudaStreamSynchronize(s));
     prof.flush();
+  }
+  return TUCKER_OK;
+}
+
+int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs, double *S,
+                      void *stream) {
+  g_err[0] = 0;
+  if (!Y || !S || L < 1 || B < 1 || J < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32) || std::isnan(maxabs)) {
+    set_error("invalid arguments to tucker_gram_split");
+    return TUCKER_EINVAL;
+  }
+  if (J > 128) {
+    set_error("tucker_gram_split supports J <= 128 (got %lld)", (long long)J);
+    return TUCKER_EUNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  DevBuf ws, part, mx;
+  if (!(maxabs > 0.0)) {
+    TK_CHECK(part.alloc(sizeof(double) * maxabs_partials(), s));
+    TK_CHECK(mx.alloc(sizeof(double), s));
+    TK_CHECK(launch_maxabs(Y, dt, L * J * B, part.as<double>(), mx.as<double>(), s));
+    TK_CUDA(cudaMemcpyAsync(&maxabs, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(maxabs)) {
+      set_error("max|Y| is not finite");
+      return TUCKER_ENONFINITE;
+    }
+  }
+  TK_CHECK(ws.alloc(sizeof(double) * gram_split_workspace_doubles(L, J, B, dev), s));
+  TK_CHECK(launch_gram_split(Y, dt, L, J, B, maxabs, S, ws.as<double>(), dev, s, &prof));
+  int herr = 0;
+  TK_CHECK(gram_split_error(ws.as<double>(), L, J, B, dev, &herr, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  if (herr) {
+    set_error("tucker_gram_split: a bounded tensor-core wait expired");
+    return TUCKER_ETIMEOUT;
   }
   return TUCKER_OK;
 }

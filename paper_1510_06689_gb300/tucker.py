@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtucker_gb300.so")
 
 F64, F32 = 0, 1
-PREC = {"fp64": 0}
+PREC = {"fp64": 0, "bf16x4": 1}
 PHASES = ("norm", "gram", "gram_reduce", "eig", "rank", "ttm")
 
 # Every symbol include/tucker.h declares (checked by the CPU test suite).
@@ -26,7 +26,7 @@ EXPORTS = (
     "tucker_sthosvd", "tucker_sthosvd_host", "tucker_reconstruct", "tucker_rel_error", "tucker_result_free",
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
-    "tucker_gram_noalloc",
+    "tucker_gram_noalloc", "tucker_gram_split",
 )
 
 
@@ -89,6 +89,7 @@ def load(path=LIB_PATH):
         "tucker_rank_cut": (i32, [vp, i64, dbl, i32, pi64, pdbl, vp]),
         "tucker_ttm": (i32, [vp, i32, i64, i64, i64, vp, i64, i32, vp, vp]),
         "tucker_gram_noalloc": (i32, [vp, i32, i64, i64, i64, vp, vp]),
+        "tucker_gram_split": (i32, [vp, i32, i64, i64, i64, dbl, vp, vp]),
         "tucker_status_string": (ctypes.c_char_p, [i32]),
         "tucker_last_error": (ctypes.c_char_p, []),
         "tucker_launch_count": (i64, []),
@@ -284,6 +285,15 @@ def gram_noalloc(y, L, J, B, out=None, stream=None):
     s = out if out is not None else torch.empty((J, J), dtype=torch.float64, device="cuda")
     _check(lib.tucker_gram_noalloc(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
                                    _stream(stream)))
+    return s.t()
+
+
+def gram_split(y, L, J, B, maxabs=0.0, stream=None):
+    """Split-precision Gram on the tensor cores (J <= 128); same layout as :func:`gram`."""
+    lib = load()
+    s = torch.empty((J, J), dtype=torch.float64, device="cuda")
+    _check(lib.tucker_gram_split(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), float(maxabs),
+                                 _dev_ptr(s, "S"), _stream(stream)))
     return s.t()
 
 

@@ -1,0 +1,116 @@
+"""GPU parity of the split-precision Gram (tcgen05, exact integer digits).
+
+The kernel computes the Gram of Y with every entry rounded to 21 bits below
+the power of two above its row's largest magnitude within a 512-column
+group.  Rigorous bound per entry, with h_i = 2^(E_i - 22) and 2^E_i the
+power of two above row i's largest magnitude over all columns (an upper
+bound of every group's rounding radius):
+
+  |S~_ij - S_ij| <= sum_k (h_i |y_jk| + |y_ik| h_j) + K h_i h_j     (rounding)
+                  + 2^-40 (|Y||Y|^T)_ij       (FP32 rounding of the two lowest
+                                               digit levels, double-float and
+                                               float64 sums)
+
+Inputs whose entries are multiples of 2^(E-7) have a single digit, so the
+kernel must then return the exact integer Gram: that checks the
+shared-memory descriptors, the TMEM layout and the exactness of the FP32
+tensor-core accumulation bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import tucker_tensor_np
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def split_bound(y, L, J, B):
+    t = y.astype(np.float64).reshape((L, J, B), order="F")
+    yn = oracle.unfold(t, 1)
+    k = L * B
+    rmax = np.abs(yn).max(axis=1) if yn.size else np.zeros(J)
+    h = np.array([2.0 ** (math.frexp(m)[1] - 22) if m > 0 else 0.0 for m in rmax])
+    a = np.abs(yn)
+    bound = h[:, None] * a.sum(axis=1)[None, :] + a.sum(axis=1)[:, None] * h[None, :] + k * np.outer(h, h)
+    bound = bound + 2.0 ** -40 * (a @ a.T)
+    return bound, oracle.gram(t, 1)
+
+
+@pytest.mark.parametrize("L,J,B", [(1, 128, 5000), (1, 64, 4096), (40, 128, 33), (7, 13, 5), (1600, 48, 3),
+                                   (640, 32, 1), (1, 1, 1), (3, 100, 777), (1, 128, 64 * 152 * 9 + 17)])
+def test_gram_split_bound(gpu_lib, L, J, B):
+    rng = np.random.default_rng(L * 3 + J * 5 + B)
+    y = rng.standard_normal(L * J * B)
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    bound, ref = split_bound(y, L, J, B)
+    assert np.array_equal(s, s.T)
+    err = np.abs(s - ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+def test_gram_split_exact_on_leading_digit_inputs(gpu_lib):
+    """Entries j * 2^(E-7) with |j| <= 127: one digit each, so S must be exact."""
+    rng = np.random.default_rng(7)
+    L, J, B = 1, 128, 3000
+    ints = rng.integers(-127, 128, size=L * J * B)
+    ints[0] = 127  # max|Y| = 127/128 < 2^0, so E = 0 and the digit unit is 2^-7
+    y = ints.astype(np.float64) / 128.0
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    m = ints.reshape((J, B), order="F").astype(np.int64)
+    exact = m @ m.T  # integer matmul: exact (|entries| <= 127^2 * 3000)
+    assert np.array_equal(s * 2 ** 14, exact.astype(np.float64))
+
+
+def test_gram_split_f32_and_maxabs_argument(gpu_lib):
+    rng = np.random.default_rng(9)
+    L, J, B = 5, 96, 400
+    y = rng.standard_normal(L * J * B).astype(np.float32)
+    s1 = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    s2 = gpu_lib.gram_split(dev(y), L, J, B, maxabs=float(np.abs(y).max())).cpu().numpy()
+    assert np.array_equal(s1, s2)
+    bound, ref = split_bound(y, L, J, B)
+    assert np.all(np.abs(s1 - ref) <= bound)
+
+
+def test_gram_split_deterministic_and_rejects_large_j(gpu_lib):
+    rng = np.random.default_rng(10)
+    y = dev(rng.standard_normal(1 * 128 * 20000))
+    a = gpu_lib.gram_split(y, 1, 128, 20000).cpu().numpy()
+    b = gpu_lib.gram_split(y, 1, 128, 20000).cpu().numpy()
+    assert np.array_equal(a, b)
+    with pytest.raises(gpu_lib.TuckerError) as e:
+        gpu_lib.gram_split(dev(np.zeros(129 * 2)), 1, 129, 2)
+    assert e.value.status == -7
+
+
+@pytest.mark.parametrize("dims,ranks,eps,dtype", [
+    ((64, 64, 64), (8, 8, 8), 1e-3, "f64"),
+    ((40, 36, 32, 12, 10), (12, 12, 12, 6, 4), 1e-5, "f64"),
+    ((40, 36, 32, 12, 10), (12, 12, 12, 6, 4), 1e-3, "f64"),
+    ((30, 28, 26, 10, 8), (10, 10, 10, 5, 3), 1e-4, "f32"),
+])
+def test_sthosvd_split_matches_oracle_ranks_and_error(gpu_lib, dims, ranks, eps, dtype):
+    """Identical ranks; achieved error within 1e-3 eps of the oracle's (stated tolerance)."""
+    x = tucker_tensor_np(dims, ranks, seed=11, decay=0.15 if len(dims) == 5 else 0.0, smooth=len(dims) == 5,
+                         noise=1e-6 if len(dims) == 5 else 1e-4)
+    xin = x.astype(np.float32) if dtype == "f32" else x
+    ref = oracle.sthosvd(xin.astype(np.float64), dims, eps)
+    xd = dev(xin)
+    res = gpu_lib.sthosvd(xd, dims, eps, precision="bf16x4")
+    assert res.ranks == ref["ranks"]
+    rel = gpu_lib.rel_error(xd, res)
+    rel_ref = oracle.rel_error(xin.astype(np.float64), ref["core"], ref["ranks"], ref["factors"])
+    assert abs(rel - rel_ref) <= 1e-3 * eps, (rel, rel_ref)
+    assert rel <= eps
+    for n in range(len(dims)):
+        u = res.factor(n).cpu().numpy()
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-13 * dims[n]
