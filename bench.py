@@ -38,18 +38,21 @@ METRIC = "ST-HOSVD input GB/s & Gram TFLOP/s, split-prec vs FP64 on GB300, equal
 WORKLOAD = "combustion5"
 # Float64 pipe peak of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# ncu DRAM traffic of the Gram kernel, keyed by the hash of the kernel source it
-# was captured with (profiles/k_gram_partial_combustion5_t2.md): measured
+# ncu DRAM traffic, keyed by kernel and the hash of the kernel source it was
+# captured with (profiles/k_gram_partial_combustion5_t2.md): measured
 # dram__bytes_read.sum + dram__bytes_write.sum of the mode-1 launch on the
 # 128x128x128x48x2 case divided by that launch's algorithmic bytes.  The
 # reported traffic is this ratio times the per-launch algorithmic bytes of the
 # timed run; it is dropped as soon as the kernel source changes.
-TRAFFIC = {"f172da5c229e3897": {"ratio": 1.6274e9 / 1.6260e9, "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"}}
+TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9,
+                                                   "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"}}
+HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
 
-def kernel_source_hash():
+def kernel_source_hash(phase, precision):
+    name = "gram_split.cu" if (phase == "gram" and precision != "fp64") else "kernels_f64.cu"
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1510_06689_gb300", "csrc", "kernels_f64.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1510_06689_gb300", "csrc", name), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -64,8 +67,9 @@ def parse_args():
     p.add_argument("--cpu-slices", type=int, default=8, help="time slices in the CPU oracle sample")
     p.add_argument("--slices", type=int, default=None,
                    help="keep only the first SLICES of the 32 time slices (smaller case for profiling)")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "bf16x4"],
-                   help="Gram arithmetic of the timed line")
+    p.add_argument("--precision", default="both", choices=["both", "fp64", "bf16x4"],
+                   help="Gram arithmetic; 'both' times the two and heads the line with the split-precision "
+                        "result when its ranks and error equal the float64 ones")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -226,11 +230,77 @@ def config_dict(w, eps, precision):
     }
 
 
+def time_method(tucker, x, dims, eps, precision, steps, warmup, world, local, stream):
+    """Warm up, then time `steps` ST-HOSVDs of x with CUDA events; returns a dict."""
+    import torch
+
+    for _ in range(max(warmup, 3)):
+        tucker.sthosvd(x, dims, eps, precision=precision).free()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    tucker.profile_enable(True)
+    launches0 = tucker.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ranks = None
+    for _ in range(steps):
+        res = tucker.sthosvd(x, dims, eps, precision=precision)
+        ranks = res.ranks
+        res.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.stop()
+    launches = tucker.launch_count() - launches0
+    prof = tucker.profile_read()
+    tucker.profile_enable(False)
+    ms = max_over_ranks(world, ev0.elapsed_time(ev1) / steps)
+    res = tucker.sthosvd(x, dims, eps, precision=precision)
+    rel = tucker.rel_error(x, res)
+    sweeps = list(res.sweeps)
+    res.free()
+    return {"ms": ms, "prof": prof, "ranks": tuple(ranks), "rel": rel, "sweeps": sweeps, "launches": launches,
+            "clocks": sampler.summary()}
+
+
+def roofline_of(t, steps, precision):
+    """Roofline object for the phase that takes the most time in the step."""
+    prof = t["prof"]
+    phase = max(("gram", "ttm"), key=lambda k: prof[k]["ms"])
+    ph = prof[phase]
+    per_ms = ph["ms"] / max(ph["launches"], 1)
+    per_flops = ph["flops"] / max(ph["launches"], 1)
+    per_bytes = ph["bytes"] / max(ph["launches"], 1)
+    if phase == "gram" and precision != "fp64":
+        achieved = per_bytes / (per_ms / 1e3) / 1e9
+        peak = HBM_PEAK_GBS
+        r = {"kernel": "k_gram_split (tcgen05 BF16 digit Gram, exact FP32 accumulation)", "bound": "hbm",
+             "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    else:
+        achieved = per_flops / (per_ms / 1e3) / 1e12
+        name = "k_gram_partial (float64 split-K symmetric Gram)" if phase == "gram" else \
+            "k_ttm (float64 mode-n product)"
+        r = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+             "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+             "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 "
+                            "1.25 TFLOP/s; measured DFMA loop 1.193 TFLOP/s)"}
+    tr = TRAFFIC.get((r["kernel"].split()[0], kernel_source_hash(phase, precision)))
+    r["traffic"] = round(tr["ratio"] * per_bytes) if tr else None
+    r["traffic_source"] = (f"ncu DRAM/algorithmic ratio of {tr['captured']}, scaled to the timed launches"
+                           if tr else "no ncu capture of this kernel version")
+    r.update({"phase": phase, "launches_per_step": ph["launches"] / steps, "per_launch_ms": round(per_ms, 4),
+              "per_launch_algorithmic_flops": per_flops, "per_launch_algorithmic_bytes": round(per_bytes)})
+    return r
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_main(args)
-    import numpy as np
     import torch
 
     from paper_1510_06689_gb300 import tucker
@@ -257,101 +327,65 @@ def main():
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
-    for _ in range(max(args.warmup, 3)):
-        res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
-        res.free()
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    tucker.profile_enable(True)
-    launches0 = tucker.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    ranks = None
-    for _ in range(args.steps):
-        res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
-        ranks = res.ranks
-        res.free()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    sampler.stop()
-    launches = tucker.launch_count() - launches0
-    prof = tucker.profile_read()
-    tucker.profile_enable(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(world, ms)
+    methods = ["bf16x4", "fp64"] if args.precision == "both" else [args.precision]
+    timed = {m: time_method(tucker, x, dims, args.eps, m, args.steps, args.warmup, world, local, stream)
+             for m in methods}
+    # "equal rel. error": the split-precision result counts only with the float64 ranks and error
+    head = methods[0]
+    equal = None
+    if "fp64" in timed and "bf16x4" in timed:
+        a, b = timed["bf16x4"], timed["fp64"]
+        equal = a["ranks"] == b["ranks"] and abs(a["rel"] - b["rel"]) <= 1e-3 * args.eps
+        head = "bf16x4" if equal else "fp64"
+    t = timed[head]
+    ms = t["ms"]
     value = world * w.nbytes / (ms / 1e3) / 1e9
-
-    # accuracy of the timed configuration (outside the timed region)
-    res = tucker.sthosvd(x, dims, args.eps, precision=args.precision)
-    rel = tucker.rel_error(x, res)
-    sweeps = list(res.sweeps)
-    res.free()
-
-    gram = prof["gram"]
+    gram = t["prof"]["gram"]
     gram_tflops = gram["flops"] / (gram["ms"] / 1e3) / 1e12 if gram["ms"] > 0 else None
-    per_launch_ms = gram["ms"] / max(gram["launches"], 1)
-    per_launch_flops = gram["flops"] / max(gram["launches"], 1)
-    step_ms_sum = sum(v["ms"] for v in prof.values()) / args.steps
-    shares = {k: round(v["ms"] / args.steps / ms, 4) for k, v in prof.items()}
-    tr = TRAFFIC.get(kernel_source_hash())
-    per_launch_bytes = gram["bytes"] / max(gram["launches"], 1)
-    traffic = round(tr["ratio"] * per_launch_bytes) if tr else None
-    roofline = {
-        "kernel": "k_gram_partial (float64 split-K symmetric Gram)",
-        "bound": "alu", "achieved": round(per_launch_flops / (per_launch_ms / 1e3) / 1e12, 4),
-        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-        "frac": round(per_launch_flops / (per_launch_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-        "traffic": traffic,
-        "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 1.25 TFLOP/s; "
-                       "measured DFMA loop 1.193 TFLOP/s)",
-        "per_launch_flops": per_launch_flops, "per_launch_ms": round(per_launch_ms, 4),
-        "per_launch_algorithmic_bytes": round(per_launch_bytes),
-        "traffic_source": ("ncu ratio DRAM/algorithmic bytes " + tr["captured"] + ", scaled to the timed launches")
-        if tr else "kernel changed since the last ncu capture",
-    }
+
+    def summary(m):
+        tm = timed[m]
+        g = tm["prof"]["gram"]
+        return {"value": round(world * w.nbytes / (tm["ms"] / 1e3) / 1e9, 4), "ms_per_step": round(tm["ms"], 3),
+                "gram_tflops": round(g["flops"] / (g["ms"] / 1e3) / 1e12, 4) if g["ms"] > 0 else None,
+                "ranks": list(tm["ranks"]), "rel_error": tm["rel"], "jacobi_sweeps": tm["sweeps"],
+                "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in tm["prof"].items()}}
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, args.precision),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, head),
         "gram_tflops": round(gram_tflops, 4) if gram_tflops else None,
-        "ranks": list(ranks), "rel_error": rel, "jacobi_sweeps": sweeps,
-        "phase_share": shares, "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in prof.items()},
-        "phase_time_covered": round(step_ms_sum / ms, 4),
-        "roofline": roofline, "gpu_launches": launches, "clocks": sampler.summary(),
+        "ranks": list(t["ranks"]), "rel_error": t["rel"], "jacobi_sweeps": t["sweeps"],
+        "methods": {m: summary(m) for m in methods},
+        "equal_rel_error": equal,
+        "phase_share": {k: round(v["ms"] / args.steps / ms, 4) for k, v in t["prof"].items()},
+        "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in t["prof"].items()},
+        "roofline": roofline_of(t, args.steps, head), "gpu_launches": t["launches"], "clocks": t["clocks"],
     }
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
+    xh = None
     if not args.no_e2e:
         xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
         xh.copy_(x)
         del x
         torch.cuda.empty_cache()
-        r = tucker.sthosvd_host(xh, dims, args.eps)
+        r = tucker.sthosvd_host(xh, dims, args.eps, precision=head)
         d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)) + sum(d + 3 for d in dims) + 1)
         r.free()
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            r = tucker.sthosvd_host(xh, dims, args.eps)
-            r.free()
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        t_e2e = max_over_ranks(world, t_e2e)
+            tucker.sthosvd_host(xh, dims, args.eps, precision=head).free()
+        t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / args.steps)
         line["e2e"] = {"value": round(world * w.nbytes / t_e2e / 1e9, 4), "unit": "GB/s",
                        "h2d_bytes_per_step": w.nbytes, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": round(t_e2e * 1e3, 3)}
-    else:
-        xh = None
+                       "ms_per_step": round(t_e2e * 1e3, 3), "precision": head}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         src = xh if xh is not None else x.cpu()
-        gbs, secs, sdims = run_oracle_sample(w, args.eps, min(args.cpu_slices, w.dims[-1]),
-                                             x_host=src.numpy())
+        gbs, secs, sdims = run_oracle_sample(w, args.eps, min(args.cpu_slices, w.dims[-1]), x_host=src.numpy())
         line["cpu_baseline"] = {
             "value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"first {sdims[-1]} of {w.dims[-1]} time slices of the same tensor "

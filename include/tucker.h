@@ -70,8 +70,9 @@ typedef enum { TUCKER_F64 = 0, TUCKER_F32 = 1 } tucker_dtype;
  * TUCKER_PREC_BF16X4 forms each Gram on the BF16 tensor cores from four exact
  * 7-bit integer slices of every entry (28 bits below a power-of-two bound of
  * max|Y|), with exact FP32 accumulation in tensor memory and float64
- * reduction (see tucker_gram_split); eigensolve, rank rule and TTM stay
- * float64.  It needs J_n <= 128 at every mode. */
+ * reduction (see tucker_gram_split); eigensolve and rank rule stay
+ * float64 while the TTM also runs on the tensor cores (see tucker_ttm_split).
+ * It needs I_n <= 128 at every mode. */
 typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_BF16X4 = 1 } tucker_precision;
 
 /* Result of an ST-HOSVD (Algorithm 1's output (G, {U_n}) plus diagnostics).
@@ -189,6 +190,22 @@ TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, i
  *   TUCKER_ETIMEOUT if a bounded tensor-core wait expired. */
 TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs,
                                  double *S, void *stream);
+
+/* Split-precision TTM step: Z = Y x_n U^T for Y viewed as (L, J, B) and Z as
+ * (L, R, B), i.e. Z[l + L(r + R b)] = sum_j U[j + J r] Y[l + L(j + J b)], on the
+ * BF16 tensor cores.  Each column of U is rounded to 28 bits below the power of
+ * two above its largest magnitude, and so is each column (l, b) of Y (its J
+ * entries); both are split into four exact BF16 digits; digit products of
+ * levels 2..5 accumulate exactly in FP32 tensor memory (levels 6..8 are
+ * dropped), and every output is assembled exactly in int64 before the
+ * float64 store.  The difference from the float64 product is bounded by
+ * h_r |y_c|_1 + |u_r|_1 h_c + J h_r h_c + 2^-26 (|U|^T |Y|)_rc with h the
+ * rounding radii 2^(e - 29).
+ *   U  device, J x R float64 column-major; R <= J <= 128 (else
+ *   TUCKER_EUNSUPPORTED).  Synchronises; TUCKER_ETIMEOUT if a bounded
+ *   tensor-core wait expired. */
+TUCKER_API int tucker_ttm_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U,
+                                int64_t R, double *Z, void *stream);
 
 /* TTM step of Algorithm 1 (Sec. 2.1 mode-n product): Z = Y x_n M with Y viewed as
  * (L, J, B) and Z as (L, K, B): Z[l + L(k + K b)] = sum_j M[k, j] Y[l + L(j + J b)].

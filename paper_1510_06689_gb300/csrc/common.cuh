@@ -111,6 +111,10 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
                       double *d_ws, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s);
+// Split-precision mode product Z(L,R,B) = U^T Y(L,J,B) on tcgen05 (R <= J <= 128);
+// U is J x R column-major float64.  *d_err becomes 1 if a bounded wait expired.
+int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
+                     double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
 // max |x| of n elements into *d_out; d_partials holds maxabs_partials() doubles.
 int64_t maxabs_partials();
 int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s);

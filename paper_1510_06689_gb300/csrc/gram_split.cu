@@ -42,6 +42,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace tk {
 
@@ -56,126 +57,9 @@ constexpr int kStageBytes = kTiles * kTileBytes;
 constexpr int kStages = 2;
 constexpr int kDrainChunks = 8;    // 512 columns between drains
 constexpr int kTmemCols = 512;
-constexpr long long kWaitLimit = 1ll << 22;
 
-// tcgen05 instruction descriptor, kind::f16: D = F32, A = B = BF16, both
-// K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRows >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: start, LBO, SBO (bytes), version 1,
-// no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 16 consecutive 32-bit TMEM columns per warp.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// hi + lo += x (x exact in float), error-free TwoSum then renormalisation.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
-  const float s = __fadd_rn(hi, x);
-  const float bp = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-  const float l = __fadd_rn(lo, e);
-  const float t = __fadd_rn(s, l);
-  lo = __fsub_rn(l, __fsub_rn(t, s));
-  hi = t;
-}
-
-// round(|y| 2^(21 - E)) with the sign of y, from the bits (no float64 math);
-// requires |y| < 2^E.
-__device__ __forceinline__ int scaled_int(double y, int E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return 0;  // zero or subnormal
-  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int shift = 31 + E - (ex - 1023);  // >= 32 because |y| < 2^E
-  int v = 0;
-  if (shift < 64) v = (int)((mant + (1ull << (shift - 1))) >> shift);
-  return (b >> 63) ? -v : v;
-}
-
-__device__ __forceinline__ int scaled_int(float y, int E) {
-  const unsigned b = __float_as_uint(y);
-  const int ex = (int)((b >> 23) & 0xFF);
-  if (ex == 0) return 0;
-  const unsigned mant = (b & 0x7FFFFFu) | 0x800000u;
-  const int shift = 2 + E - (ex - 127);  // >= 3 because |y| < 2^E
-  const int v = (shift < 32) ? (int)((mant + (1u << (shift - 1))) >> shift) : 0;
-  return (b >> 31) ? -v : v;
-}
-
-// Magnitude bits (sign cleared): ordered like the magnitudes.
-__device__ __forceinline__ unsigned long long mag_bits(double y) {
-  return (unsigned long long)__double_as_longlong(y) & 0x7FFFFFFFFFFFFFFFull;
-}
-__device__ __forceinline__ unsigned long long mag_bits(float y) { return __float_as_uint(y) & 0x7FFFFFFFu; }
-// Exponent E with max < 2^E from the largest magnitude's bits; very small for 0.
-__device__ __forceinline__ int exp_above(unsigned long long bits, bool is_f64) {
-  if (is_f64) {
-    const int ex = (int)(bits >> 52);
-    return ex == 0 ? -4000 : ex - 1023 + 1;
-  }
-  const int ex = (int)(bits >> 23);
-  return ex == 0 ? -4000 : ex - 127 + 1;
-}
-
-// Two floats that BF16 holds exactly (at most 8 significant bits), packed.
-__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
-  return (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xFFFF0000u);
-}
+using namespace tc;
+constexpr uint32_t kIdesc = idesc_bf16(kRows, kRows);
 
 struct SplitPlan {
   int J;
@@ -332,12 +216,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
         const uint64_t a3 = smem_desc(base + 2 * kTileBytes + 256 * s, 128, 1024);
         const uint64_t a3x2 = smem_desc(base + 3 * kTileBytes + 256 * s, 128, 1024);
         const uint64_t a3s = smem_desc(base + 4 * kTileBytes + 256 * s, 128, 1024);
-        mma_bf16(tmem + 0, a1, a1, acc);
-        mma_bf16(tmem + 128, a1, a2, acc);
-        mma_bf16(tmem + 256, a1, a3x2, acc);
-        mma_bf16(tmem + 256, a2, a2, 1u);
-        mma_bf16(tmem + 384, a2, a3x2, acc);
-        mma_bf16(tmem + 384, a3, a3s, 1u);
+        mma_bf16(tmem + 0, a1, a1, kIdesc, acc);
+        mma_bf16(tmem + 128, a1, a2, kIdesc, acc);
+        mma_bf16(tmem + 256, a1, a3x2, kIdesc, acc);
+        mma_bf16(tmem + 256, a2, a2, kIdesc, 1u);
+        mma_bf16(tmem + 384, a2, a3x2, kIdesc, acc);
+        mma_bf16(tmem + 384, a3, a3s, kIdesc, 1u);
       }
       mma_commit(smem_addr(&mbar[buf]));
     }

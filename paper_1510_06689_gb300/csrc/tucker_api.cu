@@ -276,11 +276,13 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   int64_t *d_rank = reinterpret_cast<int64_t *>(d_nx2 + 2);
   int *d_info = reinterpret_cast<int *>(d_nx2 + 3);
   double *d_max = d_nx2 + 4;
+  int *d_terr = reinterpret_cast<int *>(d_nx2 + 6);
+  TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
   if (prec == TUCKER_PREC_BF16X4) {
     TK_CHECK(partials.alloc(sizeof(double) * std::max(norm2_partials(), maxabs_partials()), s));
     for (int n = 0; n < N; ++n)
       if (dims[n] > 128) {
-        set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);
+        set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
         return TUCKER_EUNSUPPORTED;
       }
   }
@@ -397,8 +399,12 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     }
     DevBuf ynew;
     TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
-    TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev,
-                        s, &prof));
+    if (prec == TUCKER_PREC_BF16X4)
+      TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, factor_bufs[n].as<double>(), R, ynew.as<double>(), d_terr, dev, s,
+                                &prof));
+    else
+      TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(),
+                          dev, s, &prof));
     ybuf.reset();
     ybuf.p = ynew.release();
     ybuf.s = s;
@@ -406,8 +412,14 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     ydt = TUCKER_F64;
     cur[n] = R;
   }
+  int terr = 0;
+  TK_CUDA(cudaMemcpyAsync(&terr, d_terr, sizeof(int), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   prof.flush();
+  if (terr) {
+    set_error("split-precision TTM: a bounded tensor-core wait expired");
+    return TUCKER_ETIMEOUT;
+  }
   out->core = static_cast<double *>(ybuf.release());
   for (int n = 0; n < N; ++n) {
     out->factors[n] = factor_bufs[n].as<double>();
@@ -766,6 +778,36 @@ int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int6
   prof.flush();
   if (herr) {
     set_error("tucker_gram_split: a bounded tensor-core wait expired");
+    return TUCKER_ETIMEOUT;
+  }
+  return TUCKER_OK;
+}
+
+int tucker_ttm_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
+                     double *Z, void *stream) {
+  g_err[0] = 0;
+  if (!Y || !U || !Z || L < 1 || B < 1 || J < 1 || R < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
+    set_error("invalid arguments to tucker_ttm_split");
+    return TUCKER_EINVAL;
+  }
+  if (J > 128 || R > J) {
+    set_error("tucker_ttm_split supports R <= J <= 128 (got J = %lld, R = %lld)", (long long)J, (long long)R);
+    return TUCKER_EUNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  DevBuf e;
+  TK_CHECK(e.alloc(sizeof(int), s));
+  TK_CUDA(cudaMemsetAsync(e.p, 0, sizeof(int), s));
+  TK_CHECK(launch_ttm_split(Y, dt, L, J, B, U, R, Z, e.as<int>(), dev, s, &prof));
+  int herr = 0;
+  TK_CUDA(cudaMemcpyAsync(&herr, e.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  if (herr) {
+    set_error("tucker_ttm_split: a bounded tensor-core wait expired");
     return TUCKER_ETIMEOUT;
   }
   return TUCKER_OK;

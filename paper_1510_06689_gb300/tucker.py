@@ -26,7 +26,7 @@ EXPORTS = (
     "tucker_sthosvd", "tucker_sthosvd_host", "tucker_reconstruct", "tucker_rel_error", "tucker_result_free",
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
-    "tucker_gram_noalloc", "tucker_gram_split",
+    "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split",
 )
 
 
@@ -90,6 +90,7 @@ def load(path=LIB_PATH):
         "tucker_ttm": (i32, [vp, i32, i64, i64, i64, vp, i64, i32, vp, vp]),
         "tucker_gram_noalloc": (i32, [vp, i32, i64, i64, i64, vp, vp]),
         "tucker_gram_split": (i32, [vp, i32, i64, i64, i64, dbl, vp, vp]),
+        "tucker_ttm_split": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, vp]),
         "tucker_status_string": (ctypes.c_char_p, [i32]),
         "tucker_last_error": (ctypes.c_char_p, []),
         "tucker_launch_count": (i64, []),
@@ -331,6 +332,19 @@ def ttm(y, L, J, B, m, transpose=False, stream=None):
     z = torch.empty(int(L) * k * int(B), dtype=torch.float64, device="cuda")
     _check(lib.tucker_ttm(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(mc, "M"), k,
                           int(bool(transpose)), _dev_ptr(z, "Z"), _stream(stream)))
+    return z
+
+
+def ttm_split(y, L, J, B, u, stream=None):
+    """Z(L, R, B) = Y x_n U^T on the tensor cores; u is the (J, R) factor."""
+    lib = load()
+    jj, r = u.shape
+    if jj != J:
+        raise ValueError("u does not match J")
+    uc = u.t().contiguous()  # column-major storage of u
+    z = torch.empty(int(L) * r * int(B), dtype=torch.float64, device="cuda")
+    _check(lib.tucker_ttm_split(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(uc, "U"), r,
+                                _dev_ptr(z, "Z"), _stream(stream)))
     return z
 
 

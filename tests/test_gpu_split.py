@@ -92,6 +92,70 @@ def test_gram_split_deterministic_and_rejects_large_j(gpu_lib):
     assert e.value.status == -7
 
 
+def ttm_split_bound(y, L, J, B, u):
+    t = y.astype(np.float64).reshape((L, J, B), order="F")
+    yn = oracle.unfold(t, 1)  # J x K
+    ref = u.T @ yn
+    hr = np.array([2.0 ** (math.frexp(m)[1] - 29) if m > 0 else 0.0 for m in np.abs(u).max(axis=0)])
+    cm = np.abs(yn).max(axis=0)
+    hc = np.array([2.0 ** (math.frexp(m)[1] - 29) if m > 0 else 0.0 for m in cm])
+    # rounding of both operands, plus the dropped digit levels 6..8: per term at most
+    # (2 64 64 2^14 + 64 64 2^14 + 2 64 64 2^7 + 64 64) 2^(e_r + f_c - 56) <= 2^-27.4 2^(e_r + f_c)
+    drop = J * np.outer(hr, hc) * 2.0 ** 58 * 2.0 ** -27.4
+    bound = (hr[:, None] * np.abs(yn).sum(axis=0)[None, :] + np.abs(u).sum(axis=0)[:, None] * hc[None, :]
+             + J * np.outer(hr, hc) + drop + 2.0 ** -44 * (np.abs(u).T @ np.abs(yn)))
+    return bound, ref
+
+
+@pytest.mark.parametrize("L,J,B,R", [(1, 128, 3000, 40), (40, 128, 33, 40), (7, 13, 5, 4), (1600, 48, 3, 20),
+                                     (1, 1, 9, 1), (3, 100, 77, 100), (64, 32, 50, 10), (1, 128, 4096 * 3 + 7, 128)])
+def test_ttm_split_bound(gpu_lib, L, J, B, R):
+    import torch
+
+    rng = np.random.default_rng(L + 3 * J + 7 * B + R)
+    y = rng.standard_normal(L * J * B) * np.exp(rng.standard_normal(L * J * B))
+    u, _ = np.linalg.qr(rng.standard_normal((J, R)))
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    bound, ref = ttm_split_bound(y, L, J, B, u)
+    got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+def test_ttm_split_exact_on_single_digit_inputs(gpu_lib):
+    """U and Y entries of one digit each: every output is an exact integer product sum."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    L, J, B, R = 1, 64, 500, 16
+    ui = rng.integers(-127, 128, size=(J, R))
+    ui[0, :] = 127
+    yi = rng.integers(-127, 128, size=(J, L * B))
+    yi[0, :] = 127
+    u = ui / 128.0
+    y = (yi / 128.0).ravel(order="F")
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    exact = (ui.T.astype(np.int64) @ yi.astype(np.int64)).astype(np.float64) / 2 ** 14
+    got = z.reshape((R, L * B), order="F")
+    assert np.array_equal(got, exact)
+
+
+def test_ttm_split_f32_and_limits(gpu_lib):
+    import torch
+
+    rng = np.random.default_rng(4)
+    L, J, B, R = 6, 96, 120, 30
+    y = rng.standard_normal(L * J * B).astype(np.float32)
+    u, _ = np.linalg.qr(rng.standard_normal((J, R)))
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    bound, ref = ttm_split_bound(y, L, J, B, u)
+    got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
+    assert np.all(np.abs(got - ref) <= bound)
+    with pytest.raises(gpu_lib.TuckerError) as e:
+        gpu_lib.ttm_split(dev(np.zeros(129 * 2)), 1, 129, 2, torch.zeros((129, 3), dtype=torch.float64).cuda())
+    assert e.value.status == -7
+
+
 @pytest.mark.parametrize("dims,ranks,eps,dtype", [
     ((64, 64, 64), (8, 8, 8), 1e-3, "f64"),
     ((40, 36, 32, 12, 10), (12, 12, 12, 6, 4), 1e-5, "f64"),
