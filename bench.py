@@ -49,8 +49,12 @@ TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9
 HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
 
-def kernel_source_hash(phase, precision):
-    name = "gram_split.cu" if (phase == "gram" and precision != "fp64") else "kernels_f64.cu"
+KERNEL_FILES = {"k_gram_partial": "kernels_f64.cu", "k_ttm": "kernels_f64.cu", "k_gram_split": "gram_split.cu",
+                "k_ttm_split": "ttm_split.cu"}
+
+
+def kernel_source_hash(kernel):
+    name = KERNEL_FILES[kernel]
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_1510_06689_gb300", "csrc", name), "rb") as f:
         h.update(f.read())
@@ -267,19 +271,25 @@ def time_method(tucker, x, dims, eps, precision, steps, warmup, world, local, st
 
 
 def roofline_of(t, steps, precision):
-    """Roofline object for the phase that takes the most time in the step."""
+    """Roofline object for the Gram or TTM phase, whichever takes more of the step.
+
+    The float64 kernels are bound by the float64 pipe ("alu"); the
+    tensor-core kernels of the split-precision path move far fewer flops per
+    byte than the BF16 ridge, so HBM bounds them ("hbm", algorithmic bytes:
+    input read once plus output written once).
+    """
     prof = t["prof"]
     phase = max(("gram", "ttm"), key=lambda k: prof[k]["ms"])
     ph = prof[phase]
     per_ms = ph["ms"] / max(ph["launches"], 1)
     per_flops = ph["flops"] / max(ph["launches"], 1)
     per_bytes = ph["bytes"] / max(ph["launches"], 1)
-    if phase == "gram" and precision != "fp64":
+    if precision != "fp64":
         achieved = per_bytes / (per_ms / 1e3) / 1e9
-        peak = HBM_PEAK_GBS
-        r = {"kernel": "k_gram_split (tcgen05 BF16 digit Gram, exact FP32 accumulation)", "bound": "hbm",
-             "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        name = ("k_gram_split (tcgen05 BF16 digit Gram, exact FP32 accumulation)" if phase == "gram" else
+                "k_ttm_split (tcgen05 BF16 digit TTM, exact FP32 accumulation)")
+        r = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s",
+             "frac": round(achieved / HBM_PEAK_GBS, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     else:
         achieved = per_flops / (per_ms / 1e3) / 1e12
         name = "k_gram_partial (float64 split-K symmetric Gram)" if phase == "gram" else \
@@ -288,7 +298,7 @@ def roofline_of(t, steps, precision):
              "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
              "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 "
                             "1.25 TFLOP/s; measured DFMA loop 1.193 TFLOP/s)"}
-    tr = TRAFFIC.get((r["kernel"].split()[0], kernel_source_hash(phase, precision)))
+    tr = TRAFFIC.get((r["kernel"].split()[0], kernel_source_hash(r["kernel"].split()[0])))
     r["traffic"] = round(tr["ratio"] * per_bytes) if tr else None
     r["traffic_source"] = (f"ncu DRAM/algorithmic ratio of {tr['captured']}, scaled to the timed launches"
                            if tr else "no ncu capture of this kernel version")

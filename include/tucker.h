@@ -253,7 +253,8 @@ typedef enum {
   TUCKER_PHASE_EIG = 3,
   TUCKER_PHASE_RANK = 4,
   TUCKER_PHASE_TTM = 5,
-  TUCKER_PHASE_COUNT = 6
+  TUCKER_PHASE_SCALE = 6,  /* max|Y| passes of the split-precision path */
+  TUCKER_PHASE_COUNT = 7
 } tucker_phase;
 
 typedef struct tucker_profile {

@@ -117,7 +117,8 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
                      double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
 // max |x| of n elements into *d_out; d_partials holds maxabs_partials() doubles.
 int64_t maxabs_partials();
-int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s);
+int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s,
+                  Prof *prof);
 
 // Jacobi eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
 // matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if

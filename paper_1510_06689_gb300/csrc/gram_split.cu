@@ -347,12 +347,15 @@ SplitPlan split_plan(int64_t L, int64_t J, int64_t B, double maxabs, const Devic
 
 int64_t maxabs_partials() { return 1024; }
 
-int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s) {
+int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s,
+                  Prof *prof) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (n + 1023) / 1024));
+  if (prof) prof->begin(TUCKER_PHASE_SCALE);
   k_maxabs_partial<<<blocks, 256, 0, s>>>(x, dt == TUCKER_F64, n, d_partials);
   TK_LAUNCHED();
   k_maxabs_final<<<1, 256, 0, s>>>(d_partials, blocks, d_out);
   TK_LAUNCHED();
+  if (prof) prof->end(0.0, (double)n * (dt == TUCKER_F64 ? 8 : 4), 2);
   return TUCKER_OK;
 }
 

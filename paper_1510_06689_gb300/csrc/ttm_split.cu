@@ -114,9 +114,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split(const T *__restrict__
                                                            double *__restrict__ z, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   __shared__ __align__(8) unsigned long long mbar[2];
-  __shared__ unsigned long long colmax[kN];
-  __shared__ int colexp[2][kN];
-  __shared__ int64_t colin[kN], colout[2][kN];
+  // per-tile column metadata, three slots (tile it uses slot it % 3): the
+  // next tile's loads fill one slot while the previous tile drains from another
+  __shared__ unsigned long long colmax[3][kN];
+  __shared__ int colexp[3][kN];
+  __shared__ int64_t colin[3][kN], colout[3][kN];
   __shared__ int rowexp[kM];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
@@ -178,129 +180,140 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split(const T *__restrict__
   fence_after();
   const uint32_t tmem = tmem_slot;
   const int64_t in_b = L * (int64_t)p.J, out_b = L * (int64_t)p.R;
-  const int units = kN * (Jp / 8);
-  const int my_c = tid / (Jp / 8), my_jg = tid % (Jp / 8);  // this thread's load unit (if tid < units)
+  const int ngroups = Jp / 8;
+  const int units = kN * ngroups;
+  // load unit: column my_c (= lane) and 8 consecutive j; lanes write consecutive
+  // 16-byte core-matrix rows, so the operand stores are free of bank conflicts
+  const int my_c = tid % kN, my_jg = tid / kN;
+  const bool loader = tid < units;
 
-  int prev_t = -1, prev_set = 0, last_it = -1;
+  // --- load phase of a tile: column addresses, then the raw entries into registers
+  T raw[8];
+  auto load_tile = [&](int64_t t, int slot) {
+    if (tid < kN) {
+      colmax[slot][tid] = 0ull;
+      const int64_t c = t * kN + tid;
+      int64_t bi = -1, bo = -1;
+      if (c < p.K) {
+        const int64_t b = c / L, l = c - b * L;
+        bi = l + in_b * b;
+        bo = l + out_b * b;
+      }
+      colin[slot][tid] = bi;
+      colout[slot][tid] = bo;
+    }
+    __syncthreads();
+    if (loader) {
+      const int64_t bi = colin[slot][my_c];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int j = 8 * my_jg + k;
+        raw[k] = (bi >= 0 && j < p.J) ? __ldg(y + bi + L * (int64_t)j) : T(0);
+      }
+    }
+  };
+
+  // --- drain of a finished tile: all 16 warps, warp w reads TMEM lanes
+  // 32 (w % 4) .. +31 and columns 8 (w / 4) .. +7 of the four levels
+  auto drain = [&](int done_it) {
+    const int dset = done_it & 1, dm = done_it % 3;
+    if (tid == 0 && !mbar_wait(smem_addr(&mbar[dset]), (done_it >> 1) & 1)) stop = 1;
+    __syncthreads();
+    const int q = warp & 3, cg = warp >> 2;
+    if (!stop && 32 * q < p.R) {
+      fence_after();
+      const int r = 32 * q + lane;
+      const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(dset * 128 + 8 * cg);
+      uint32_t a[4][8];
+#pragma unroll
+      for (int lev = 0; lev < 4; ++lev) tmem_ld8(tb + (uint32_t)(32 * lev), a[lev]);
+      if (r < p.R) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int c = 8 * cg + e;
+          const int64_t ob = colout[dm][c];
+          if (ob < 0) continue;
+          const long long v = ((long long)__float2int_rn(__uint_as_float(a[0][e])) << 28) +
+                              ((long long)__float2int_rn(__uint_as_float(a[1][e])) << 21) +
+                              ((long long)__float2int_rn(__uint_as_float(a[2][e])) << 14) +
+                              ((long long)__float2int_rn(__uint_as_float(a[3][e])) << 7);
+          z[ob + L * (int64_t)r] = scaled_ll_to_double(v, rowexp[r] + colexp[dm][c] - 42);
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+  };
+
+  int last_it = -1;
   int it = 0;
-  for (int64_t t = blockIdx.x;; t += gridDim.x, ++it) {
-    const bool have = t < p.ntiles;
-    const int set = it & 1;
-    if (have) {
-      // operand stage `set` is free once the MMAs of tile it - 2 have finished
-      if (it >= 2) {
-        if (tid == 0 && !mbar_wait(smem_addr(&mbar[set]), ((it - 2) >> 1) & 1)) stop = 1;
-      }
-      const int64_t c0 = t * kN;
-      if (tid < kN) {
-        colmax[tid] = 0ull;
-        const int64_t c = c0 + tid;
-        int64_t bi = -1, bo = -1;
-        if (c < p.K) {
-          const int64_t b = c / L, l = c - b * L;
-          bi = l + in_b * b;
-          bo = l + out_b * b;
-        }
-        colin[tid] = bi;
-        colout[set][tid] = bo;
-      }
-      __syncthreads();
-      if (stop) break;
-      T raw[8];
+  int64_t t = blockIdx.x;
+  if (t < p.ntiles) load_tile(t, 0);
+  for (; t < p.ntiles; t += gridDim.x, ++it) {
+    const int set = it & 1, ms = it % 3;
+    // column exponents of this tile
+    if (loader) {
       unsigned long long m = 0ull;
-      if (tid < units) {
-        const int64_t bi = colin[my_c];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = 8 * my_jg + k;
-          raw[k] = (bi >= 0 && j < p.J) ? __ldg(y + bi + L * (int64_t)j) : T(0);
-          m = max(m, mag_bits(raw[k]));
-        }
-        atomicMax(&colmax[my_c], m);
-      }
-      __syncthreads();
-      if (tid < kN) colexp[set][tid] = exp_above(colmax[tid], kF64);
-      __syncthreads();
-      if (tid < units) {
-        const int e = colexp[set][my_c];
-        uint32_t w[kBTiles][4];
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          int d[2][4];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) digits4(scaled_int28(raw[k + h], e), d[h]);
-#pragma unroll
-          for (int q = 0; q < kBTiles; ++q) w[q][k >> 1] = bf16_pair((float)d[0][q], (float)d[1][q]);
-        }
-        unsigned char *st = Bst + set * kBTiles * b_tile;
-        const int off = (my_c >> 3) * (int)sbo + my_jg * 128 + (my_c & 7) * 16;
-#pragma unroll
-        for (int q = 0; q < kBTiles; ++q)
-          *reinterpret_cast<uint4 *>(st + q * b_tile + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        fence_after();
-        const uint32_t ab = smem_addr(A), bb = smem_addr(Bst + set * kBTiles * b_tile);
-        const uint32_t d0 = tmem + (uint32_t)(set * 128);
-        for (int ks = 0; ks < Jp / 16; ++ks) {
-          const uint32_t acc = ks ? 1u : 0u;
-          uint64_t ua[kATiles], yb[kBTiles];
-#pragma unroll
-          for (int q = 0; q < kATiles; ++q) ua[q] = smem_desc(ab + q * a_tile + 256 * ks, 128, sbo);
-#pragma unroll
-          for (int q = 0; q < kBTiles; ++q) yb[q] = smem_desc(bb + q * b_tile + 256 * ks, 128, sbo);
-          mma_bf16(d0 + 0, ua[0], yb[0], kIdesc, acc);
-          mma_bf16(d0 + 32, ua[0], yb[1], kIdesc, acc);
-          mma_bf16(d0 + 32, ua[1], yb[0], kIdesc, 1u);
-          mma_bf16(d0 + 64, ua[0], yb[2], kIdesc, acc);
-          mma_bf16(d0 + 64, ua[1], yb[1], kIdesc, 1u);
-          mma_bf16(d0 + 64, ua[2], yb[0], kIdesc, 1u);
-          mma_bf16(d0 + 96, ua[0], yb[3], kIdesc, acc);
-          mma_bf16(d0 + 96, ua[1], yb[2], kIdesc, 1u);
-          mma_bf16(d0 + 96, ua[2], yb[1], kIdesc, 1u);
-          mma_bf16(d0 + 96, ua[3], yb[0], kIdesc, 1u);
-        }
-        mma_commit(smem_addr(&mbar[set]));
-      }
-      last_it = it;
+      for (int k = 0; k < 8; ++k) m = max(m, mag_bits(raw[k]));
+      atomicMax(&colmax[ms][my_c], m);
     }
-    // drain the previous tile while the tensor cores work on this one
-    if (prev_t >= 0) {
-      if (tid == 0 && !mbar_wait(smem_addr(&mbar[prev_set]), ((it - 1) >> 1) & 1)) stop = 1;
-      __syncthreads();
-      if (!stop && warp < 4 && 32 * warp < p.R) {
-        fence_after();
-        const int r = 32 * warp + lane;
-        const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(prev_set * 128);
-        for (int half = 0; half < 2; ++half) {
-          uint32_t a[4][16];
+    // operand stage `set` is free once the MMAs of tile it - 2 have finished
+    if (it >= 2 && tid == 0 && !mbar_wait(smem_addr(&mbar[set]), ((it - 2) >> 1) & 1)) stop = 1;
+    __syncthreads();
+    if (stop) break;
+    if (tid < kN) colexp[ms][tid] = exp_above(colmax[ms][tid], kF64);
+    __syncthreads();
+    if (loader) {
+      const int e = colexp[ms][my_c];
+      uint32_t w[kBTiles][4];
 #pragma unroll
-          for (int lev = 0; lev < 4; ++lev) tmem_ld16(tb + (uint32_t)(32 * lev + 16 * half), a[lev]);
-          if (r < p.R) {
+      for (int k = 0; k < 8; k += 2) {
+        int d[2][4];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int c = 16 * half + e;
-              const int64_t ob = colout[prev_set][c];
-              if (ob < 0) continue;
-              const long long v = ((long long)__float2int_rn(__uint_as_float(a[0][e])) << 28) +
-                                  ((long long)__float2int_rn(__uint_as_float(a[1][e])) << 21) +
-                                  ((long long)__float2int_rn(__uint_as_float(a[2][e])) << 14) +
-                                  ((long long)__float2int_rn(__uint_as_float(a[3][e])) << 7);
-              z[ob + L * (int64_t)r] = scaled_ll_to_double(v, rowexp[r] + colexp[prev_set][c] - 42);
-            }
-          }
-        }
+        for (int h = 0; h < 2; ++h) digits4(scaled_int28(raw[k + h], e), d[h]);
+#pragma unroll
+        for (int q = 0; q < kBTiles; ++q) w[q][k >> 1] = bf16_pair((float)d[0][q], (float)d[1][q]);
       }
-      fence_before();
-      __syncthreads();
-      if (stop) break;
+      unsigned char *st = Bst + set * kBTiles * b_tile;
+      const int off = (my_c >> 3) * (int)sbo + my_jg * 128 + (my_c & 7) * 16;
+#pragma unroll
+      for (int q = 0; q < kBTiles; ++q)
+        *reinterpret_cast<uint4 *>(st + q * b_tile + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
     }
-    if (!have) break;
-    prev_t = (int)(t & 0x7fffffff);
-    prev_set = set;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      const uint32_t ab = smem_addr(A), bb = smem_addr(Bst + set * kBTiles * b_tile);
+      const uint32_t d0 = tmem + (uint32_t)(set * 128);
+      for (int ks = 0; ks < Jp / 16; ++ks) {
+        const uint32_t acc = ks ? 1u : 0u;
+        uint64_t ua[kATiles], yb[kBTiles];
+#pragma unroll
+        for (int q = 0; q < kATiles; ++q) ua[q] = smem_desc(ab + q * a_tile + 256 * ks, 128, sbo);
+#pragma unroll
+        for (int q = 0; q < kBTiles; ++q) yb[q] = smem_desc(bb + q * b_tile + 256 * ks, 128, sbo);
+        mma_bf16(d0 + 0, ua[0], yb[0], kIdesc, acc);
+        mma_bf16(d0 + 32, ua[0], yb[1], kIdesc, acc);
+        mma_bf16(d0 + 32, ua[1], yb[0], kIdesc, 1u);
+        mma_bf16(d0 + 64, ua[0], yb[2], kIdesc, acc);
+        mma_bf16(d0 + 64, ua[1], yb[1], kIdesc, 1u);
+        mma_bf16(d0 + 64, ua[2], yb[0], kIdesc, 1u);
+        mma_bf16(d0 + 96, ua[0], yb[3], kIdesc, acc);
+        mma_bf16(d0 + 96, ua[1], yb[2], kIdesc, 1u);
+        mma_bf16(d0 + 96, ua[2], yb[1], kIdesc, 1u);
+        mma_bf16(d0 + 96, ua[3], yb[0], kIdesc, 1u);
+      }
+      mma_commit(smem_addr(&mbar[set]));
+    }
+    last_it = it;
+    // loads of the next tile are in flight while the previous tile drains
+    if (t + gridDim.x < p.ntiles) load_tile(t + gridDim.x, (it + 1) % 3);
+    if (it >= 1) drain(it - 1);
+    if (stop) break;
   }
+  if (!stop && it >= 1) drain(it - 1);
   if (stop && tid == 0 && last_it >= 0)  // let our own MMAs finish before TMEM is released
     mbar_wait(smem_addr(&mbar[last_it & 1]), (last_it >> 1) & 1);
   fence_before();

@@ -338,7 +338,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     // Gram step
     if (prec == TUCKER_PREC_BF16X4) {
       const int64_t I_cur = L * J * B;
-      TK_CHECK(launch_maxabs(Y, ydt, I_cur, partials.as<double>(), d_max, s));
+      TK_CHECK(launch_maxabs(Y, ydt, I_cur, partials.as<double>(), d_max, s, &prof));
       TK_CUDA(cudaMemcpyAsync(h + 4, d_max, sizeof(double), cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaStreamSynchronize(s));
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
@@ -762,7 +762,7 @@ int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (!(maxabs > 0.0)) {
     TK_CHECK(part.alloc(sizeof(double) * maxabs_partials(), s));
     TK_CHECK(mx.alloc(sizeof(double), s));
-    TK_CHECK(launch_maxabs(Y, dt, L * J * B, part.as<double>(), mx.as<double>(), s));
+    TK_CHECK(launch_maxabs(Y, dt, L * J * B, part.as<double>(), mx.as<double>(), s, &prof));
     TK_CUDA(cudaMemcpyAsync(&maxabs, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
     if (!std::isfinite(maxabs)) {
