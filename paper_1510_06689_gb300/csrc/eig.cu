@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -277,8 +279,13 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const double
         sn[t] = __ldcg(par + 2 * t + 1);
       }
       __syncthreads();
-      // (B) block updates of S, then column updates of V
-      for (int64_t e = gtid; e < items; e += gthreads) {
+      // (B) block updates of S, then column updates of V; every CTA takes an
+      // equal contiguous share of each kind
+      const int64_t b0 = (int64_t)nblk * rank / nct, b1 = (int64_t)nblk * (rank + 1) / nct;
+      const int64_t v0 = (int64_t)np * m * rank / nct, v1 = (int64_t)np * m * (rank + 1) / nct;
+      const int64_t mine = (b1 - b0) + (v1 - v0);
+      for (int64_t k = threadIdx.x; k < mine; k += blockDim.x) {
+        const int64_t e = k < b1 - b0 ? b0 + k : nblk + v0 + (k - (b1 - b0));
         if (e < nblk) {
           int P, Q;
           decode_pair_block((int)e, P, Q);
@@ -355,6 +362,265 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const double
   }
 }
 
+// ---------------------------------------------------------------------------
+// Distributed-shared-memory Jacobi (J up to 512): the same rotations as the
+// kernels above, with S (packed upper triangle) and V spread over the shared
+// memory of a 16-CTA cluster (element e lives in CTA e mod 16) and ONE cluster
+// barrier per step.  The barrier count halves because every step also
+// computes the next step's rotations: each next-step pair {a, b} lies in
+// exactly one 2 x 2 block of the current step (consecutive rounds of the
+// tournament never repeat a pair), so the thread that rewrites that block
+// knows s'_ab, and the next diagonal follows in closed form from the current
+// one (d_p - t b, d_q + t b).  It broadcasts (c, s) and the new diagonal
+// entries into every CTA's shared memory; after the barrier each CTA holds
+// the whole step locally.  Distributed shared memory keeps each step's
+// remote accesses at shared-memory-network latency instead of L2 round trips.
+// ---------------------------------------------------------------------------
+constexpr int kDsmThreads = 1024;
+constexpr int kDsmMaxJ = 512;
+
+// Element e of the distributed S / V array: in distributed shared memory
+// (CTA e mod 16, slot e / 16) or, for kL2, at ws[e] in global memory with all
+// loads bypassing L1 (other CTAs rewrite those lines every step).
+template <bool kL2>
+struct MatView {
+  cg::cluster_group cl;
+  double *local;
+  double *ws;
+  int lg, mask;
+  __device__ double *at(int64_t e) const {
+    if (kL2) return ws + e;
+    return cl.map_shared_rank(local + (e >> lg), (int)(e & mask));
+  }
+  __device__ double ld(int64_t e) const {
+    if (kL2) return __ldcg(ws + e);
+    return *at(e);
+  }
+  __device__ void st(int64_t e, double v) const {
+    if (kL2) __stcg(ws + e, v);
+    else *at(e) = v;
+  }
+};
+
+__device__ __forceinline__ int tour_player(int pos, int step, int m) {
+  return pos == 0 ? 0 : ((pos - 1 + step) % (m - 1)) + 1;
+}
+__device__ __forceinline__ int tour_pos(int player, int step, int m) {
+  return player == 0 ? 0 : ((player - 1 - step) % (m - 1) + (m - 1)) % (m - 1) + 1;
+}
+
+// Rotation annihilating b of [[a, b], [b, d]] (same rule as the other kernels).
+__device__ __forceinline__ bool jacobi_rotation(double a, double b, double d, double abs_floor, double &c,
+                                                double &s, double &na, double &nd) {
+  c = 1.0;
+  s = 0.0;
+  na = a;
+  nd = d;
+  if (b == 0.0) return false;
+  const double ab = fabs(b);
+  if (!(ab > DBL_EPSILON * sqrt(fabs(a)) * sqrt(fabs(d)) && ab > abs_floor)) return false;
+  const double tau = (d - a) / (2.0 * b);
+  const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + tt * tt);
+  s = tt * c;
+  na = a - tt * b;
+  nd = d + tt * b;
+  return true;
+}
+
+template <bool kL2>
+__global__ void __launch_bounds__(kDsmThreads) k_jacobi_dsm(const double *__restrict__ S_in, int J,
+                                                           double *__restrict__ lam, double *__restrict__ V_out,
+                                                           double *__restrict__ ws, int *__restrict__ info) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double dyn[];
+  // the step's rotations and new diagonal, gathered into every CTA
+  __shared__ double cpar[kDsmMaxJ / 2], spar[kDsmMaxJ / 2];
+  __shared__ double dnew[kDsmMaxJ];
+  // home slots (this CTA's share, two step parities): pair t lives in CTA
+  // t mod 16 at t / 16, diagonal entry i in CTA i mod 16 at i / 16
+  __shared__ double hc[2][kDsmMaxJ / 32], hs[2][kDsmMaxJ / 32], hd[2][kDsmMaxJ / 16];
+  __shared__ int flags[kMaxSweeps + 2];
+  // this step's pairs and, for every index, its next-step partner and pair
+  __shared__ short spp[kDsmMaxJ / 2], sqq[kDsmMaxJ / 2], npart[kDsmMaxJ], npair[kDsmMaxJ];
+  const int nct = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int lg = __ffs(nct) - 1;
+  const int mask = nct - 1;
+  MatView<kL2> D{cl, dyn, ws, lg, mask};
+  const int m = J + (J & 1);
+  const int np = m / 2;
+  const int64_t packed = (int64_t)m * (m + 1) / 2;
+  const int64_t total = packed + (int64_t)m * m;
+  const int tid = threadIdx.x;
+  const int gtid = rank * blockDim.x + tid, gthreads = nct * blockDim.x;
+
+  for (int k = tid; k < kMaxSweeps + 2; k += blockDim.x) flags[k] = 0;
+  for (int64_t e = gtid; e < total; e += gthreads) {
+    double v;
+    if (e < packed) {
+      int j = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+      while ((int64_t)(j + 1) * (j + 2) / 2 <= e) ++j;
+      while ((int64_t)j * (j + 1) / 2 > e) --j;
+      const int i = (int)(e - (int64_t)j * (j + 1) / 2);
+      v = (j < J) ? S_in[i + (int64_t)J * j] : 0.0;
+    } else {
+      const int64_t f = e - packed;
+      v = (f % m == f / m) ? 1.0 : 0.0;
+    }
+    D.st(e, v);
+  }
+  double mx = 0.0;
+  for (int i = 0; i < J; ++i) mx = fmax(mx, fabs(S_in[i + (int64_t)J * i]));
+  const double abs_floor = mx * (DBL_EPSILON * DBL_EPSILON) + DBL_MIN;
+  cl.sync();
+
+  // one remote store per value, to its home CTA; the sweep flag goes to CTA 0
+  auto publish = [&](int buf, int t, int p, int q, double c, double s, double na, double nd) {
+    *cl.map_shared_rank(&hc[buf][t >> lg], t & mask) = c;
+    *cl.map_shared_rank(&hs[buf][t >> lg], t & mask) = s;
+    *cl.map_shared_rank(&hd[buf][p >> lg], p & mask) = na;
+    *cl.map_shared_rank(&hd[buf][q >> lg], q & mask) = nd;
+  };
+  for (int t = gtid; t < np; t += gthreads) {
+    int p = tour_player(t, 0, m), q = tour_player(m - 1 - t, 0, m);
+    if (p > q) {
+      const int x = p;
+      p = q;
+      q = x;
+    }
+    double c, s, na, nd;
+    const bool rot = jacobi_rotation(D.ld(pidx(p, p)), D.ld(pidx(p, q)), D.ld(pidx(q, q)), abs_floor, c, s, na, nd);
+    publish(0, t, p, q, c, s, na, nd);
+    if (rot) *cl.map_shared_rank(&flags[0], 0) = 1;
+  }
+  cl.sync();
+
+  const int nblk = np * (np + 1) / 2;
+  const int64_t items = (int64_t)nblk + (int64_t)np * m;
+  int sweep = 0;
+  bool converged = false;
+  int64_t gstep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    for (int step = 0; step < m - 1; ++step, ++gstep) {
+      const int cur = (int)(gstep & 1), nxt = cur ^ 1;
+      const int nstep = (step + 1) % (m - 1);
+      const int nsweep = (step + 1 == m - 1) ? sweep + 1 : sweep;
+      // gather this step's rotations and diagonal; tabulate the pairings once
+      for (int k = tid; k < np + m; k += blockDim.x) {
+        if (k < np) {
+          cpar[k] = *cl.map_shared_rank(&hc[cur][k >> lg], k & mask);
+          spar[k] = *cl.map_shared_rank(&hs[cur][k >> lg], k & mask);
+          const int p = tour_player(k, step, m), q = tour_player(m - 1 - k, step, m);
+          spp[k] = (short)min(p, q);
+          sqq[k] = (short)max(p, q);
+        } else {
+          const int i = k - np;
+          dnew[i] = *cl.map_shared_rank(&hd[cur][i >> lg], i & mask);
+          const int pa = tour_pos(i, nstep, m);
+          npart[i] = (short)tour_player(m - 1 - pa, nstep, m);
+          npair[i] = (short)min(pa, m - 1 - pa);
+        }
+      }
+      __syncthreads();
+      // every CTA takes an equal contiguous share of the 2 x 2 blocks and of the
+      // V rows (a global stride would put all block work on the first CTAs)
+      const int64_t b0 = (int64_t)nblk * rank / nct, b1 = (int64_t)nblk * (rank + 1) / nct;
+      const int64_t v0 = (int64_t)np * m * rank / nct, v1 = (int64_t)np * m * (rank + 1) / nct;
+      const int64_t mine = (b1 - b0) + (v1 - v0);
+      for (int64_t k = tid; k < mine; k += blockDim.x) {
+        const int64_t e = k < b1 - b0 ? b0 + k : nblk + v0 + (k - (b1 - b0));
+        if (e < nblk) {
+          int P, Q;
+          decode_pair_block((int)e, P, Q);
+          const int p1 = spp[P], q1 = sqq[P];
+          if (P == Q) {
+            if (spar[P] != 0.0) {
+              D.st(pidx(p1, p1), dnew[p1]);
+              D.st(pidx(q1, q1), dnew[q1]);
+              D.st(pidx(p1, q1), 0.0);
+            }
+            continue;
+          }
+          const int p2 = spp[Q], q2 = sqq[Q];
+          const double c1 = cpar[P], s1 = spar[P], c2 = cpar[Q], s2 = spar[Q];
+          const int64_t i11 = pidx(p1, p2), i12 = pidx(p1, q2), i21 = pidx(q1, p2), i22 = pidx(q1, q2);
+          double x11 = D.ld(i11), x12 = D.ld(i12), x21 = D.ld(i21), x22 = D.ld(i22);
+          if (s1 != 0.0 || s2 != 0.0) {
+            const double y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+            const double y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+            x11 = y11 * c2 - y12 * s2;
+            x12 = y11 * s2 + y12 * c2;
+            x21 = y21 * c2 - y22 * s2;
+            x22 = y21 * s2 + y22 * c2;
+            D.st(i11, x11);
+            D.st(i12, x12);
+            D.st(i21, x21);
+            D.st(i22, x22);
+          }
+          // any of the four elements a next-step pair?  Then its rotation is made here.
+          const int rows[2] = {p1, q1}, cols[2] = {p2, q2};
+          const double vals[2][2] = {{x11, x12}, {x21, x22}};
+#pragma unroll
+          for (int ri = 0; ri < 2; ++ri)
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci) {
+              const int a = rows[ri], b = cols[ci];
+              if (npart[a] != b) continue;
+              const int t = npair[a];
+              const int lo = min(a, b), hi = max(a, b);
+              double c, s, na, nd;
+              const bool rot = jacobi_rotation(dnew[lo], vals[ri][ci], dnew[hi], abs_floor, c, s, na, nd);
+              publish(nxt, t, lo, hi, c, s, na, nd);
+              if (rot) *cl.map_shared_rank(&flags[nsweep], 0) = 1;
+            }
+        } else {
+          const int64_t r = e - nblk;
+          const int t = (int)(r / m), i = (int)(r - (int64_t)t * m);
+          const double s = spar[t];
+          if (s == 0.0) continue;
+          const double c = cpar[t];
+          const int64_t ep = packed + (int64_t)spp[t] * m + i, eq = packed + (int64_t)sqq[t] * m + i;
+          const double a = D.ld(ep), b = D.ld(eq);
+          D.st(ep, c * a - s * b);
+          D.st(eq, s * a + c * b);
+        }
+      }
+      cl.sync();
+    }
+    if (*cl.map_shared_rank(&flags[sweep], 0) == 0) {
+      converged = true;
+      break;
+    }
+  }
+
+  // eigenvalues: the diagonal after the last applied step (dnew of that step)
+  for (int i = gtid; i < J; i += gthreads) {
+    const double di = dnew[i];
+    int rk = 0;
+    for (int j = 0; j < J; ++j) {
+      const double dj = dnew[j];
+      rk += (dj > di) || (dj == di && j < i);
+    }
+    lam[rk] = di;
+    double best = -1.0, sgv = 0.0;
+    for (int r = 0; r < J; ++r) {
+      const double v = D.ld(packed + (int64_t)i * m + r);
+      if (fabs(v) > best) {
+        best = fabs(v);
+        sgv = v;
+      }
+    }
+    const double sg = sgv < 0.0 ? -1.0 : 1.0;
+    for (int r = 0; r < J; ++r) V_out[r + (int64_t)J * rk] = sg * D.ld(packed + (int64_t)i * m + r);
+  }
+  if (gtid == 0) {
+    info[0] = converged ? sweep + 1 : kMaxSweeps;
+    info[1] = converged ? 0 : 1;
+  }
+  cl.sync();  // no CTA may exit while others still read its shared memory
+}
+
 // Rank rule of Algorithm 1: tails[r] = sum_{k >= r} max(lam[k], 0) accumulated
 // from the smallest eigenvalue upward; R = smallest r in [1, J] with
 // tails[r] <= threshold.
@@ -419,9 +685,63 @@ static int cluster_size_for_eig() {
   return best;
 }
 
+// True if a 16-CTA cluster of k_jacobi_dsm with `dsmem` bytes of dynamic
+// shared memory per CTA can be co-scheduled on this device.
+template <bool kL2>
+static bool dsm_cluster_ok(size_t dsmem) {
+  if (cudaFuncSetAttribute(k_jacobi_dsm<kL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_jacobi_dsm<kL2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(kDsmThreads);
+  cfg.dynamicSmemBytes = dsmem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 16;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&n, k_jacobi_dsm<kL2>, &cfg) == cudaSuccess && n >= 1;
+  cudaGetLastError();
+  return ok;
+}
+
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof) {
   const int64_t m = J + (J & 1);
+  const char *ev = getenv("TUCKER_EIG_KERNEL");  // "dsm" | "l2m" | "l2" (default l2m)
+  const bool use_dsm = ev && !strcmp(ev, "dsm");
+  const bool use_l2 = ev && !strcmp(ev, "l2");
+  if (J > kOneCtaMaxJ && J <= kDsmMaxJ && !use_l2 && (use_dsm || d_ws)) {
+    const size_t dsmem = use_dsm ? (size_t)((m * (m + 1) / 2 + m * m + 15) / 16) * sizeof(double) : 0;
+    if (use_dsm ? dsm_cluster_ok<false>(dsmem) : dsm_cluster_ok<true>(0)) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kDsmThreads);
+      cfg.dynamicSmemBytes = dsmem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = 16;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      if (prof) prof->begin(TUCKER_PHASE_EIG);
+      if (use_dsm)
+        TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_dsm<false>, d_S, (int)J, d_lam, d_V, (double *)nullptr, d_info));
+      else
+        TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_dsm<true>, d_S, (int)J, d_lam, d_V, d_ws, d_info));
+      TK_LAUNCHED();
+      if (prof) prof->end(0.0, (double)J * J * 16, 1);
+      return TUCKER_OK;
+    }
+  }
   if (J > kOneCtaMaxJ) {
     if (!d_ws) {
       set_error("eigensolver workspace missing for J = %lld", (long long)J);
