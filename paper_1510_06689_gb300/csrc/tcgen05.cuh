@@ -14,7 +14,7 @@ constexpr long long kTcWaitLimit = 1ll << 22;
 
 // tcgen05 instruction descriptor for kind::f16: D = F32, A = B = BF16, both
 // K-major, shape M x N.
-constexpr uint32_t idesc_bf16(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
