@@ -176,20 +176,24 @@ TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, i
 
 /* Split-precision Gram step: the Gram of tucker_gram (same view, layout and
  * output) computed on the BF16 tensor cores (tcgen05, accumulators in tensor
- * memory).  With 2^E the smallest power of two above max|Y|, each entry is
- * rounded to the integer v = round(y 2^(28-E)) and split into four balanced
- * digits (|s1| <= 128, |s2|,|s3|,|s4| <= 64) that BF16 holds exactly; digit
- * products of level p+q <= 5 are accumulated exactly in FP32 (drained every
- * 512 columns), the dropped levels' diagonal squares are added back exactly,
- * and the float64 result is (C + C^T)/2 2^(2E-56).  The difference from the
- * float64 Gram is the rounding of Y to 28 bits below 2^E plus zero-mean
- * off-diagonal terms of relative size ~2^-24 / sqrt(L B).
- *   maxabs  an upper bound of max|Y| (the largest magnitude), or <= 0 to let
- *           the call compute it (one extra pass over Y).
- *   J <= 128 (else TUCKER_EUNSUPPORTED).  Synchronises `stream`; returns
- *   TUCKER_ETIMEOUT if a bounded tensor-core wait expired. */
-TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs,
-                                 double *S, void *stream);
+ * memory).  Columns are taken in groups of 512; with 2^E_ig the smallest
+ * power of two above row i's largest magnitude in group g, each entry is
+ * rounded to the integer v = round(y 2^(21 - E_ig)) and split into three
+ * balanced digits (|s1| <= 128, |s2|, |s3| <= 64) that BF16 holds exactly;
+ * digit products of levels 2..5 are accumulated exactly in FP32 and drained
+ * into double-float sums every 512 columns, the level-6 squares of the
+ * diagonal are added exactly, and the float64 result is symmetrised.  The
+ * difference from the float64 Gram is the rounding of Y to 21 bits below
+ * each local power of two, plus zero-mean level-6 off-diagonal terms of
+ * relative size ~2^-28.  The exponents come from a pass over Y on the device
+ * (no host round trip besides the final synchronisation).
+ *   J <= 128 (else TUCKER_EUNSUPPORTED).  An Inf or NaN in Y makes every
+ *   entry of S NaN.  Synchronises `stream`; returns TUCKER_ETIMEOUT if a
+ *   bounded tensor-core wait expired.  No counterpart in the paper (its Gram
+ *   is float64, Sec. 4.3); this is the split-precision reading of the Gram
+ *   step of Algorithm 1. */
+TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
+                                 void *stream);
 
 /* Split-precision TTM step: Z = Y x_n U^T for Y viewed as (L, J, B) and Z as
  * (L, R, B), i.e. Z[l + L(r + R b)] = sum_j U[j + J r] Y[l + L(j + J b)], on the

@@ -102,24 +102,19 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
                     int64_t K, const void *x, tucker_dtype xdt, double *d_partials, double *d_out,
                     const DeviceInfo &dev, cudaStream_t s, Prof *prof);
 
-// Split-precision Gram (tcgen05, exact integer slices; J <= 128).  maxabs must
-// bound max|Y| (0 for an all-zero Y).  d_ws holds
-// gram_split_workspace_doubles() doubles; its last word is an error flag
-// read back by gram_split_error().
+// Split-precision Gram (tcgen05, exact integer digits; J <= 128).  Takes its
+// exponents from a first pass over Y on the device (no host round trip).  d_ws
+// holds gram_split_workspace_doubles() doubles, including an error flag read
+// back by gram_split_error().
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
-int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs, double *d_S,
-                      double *d_ws, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof);
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s);
 // Split-precision mode product Z(L,R,B) = U^T Y(L,J,B) on tcgen05 (R <= J <= 128);
 // U is J x R column-major float64.  *d_err becomes 1 if a bounded wait expired.
 int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
                      double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
-// max |x| of n elements into *d_out; d_partials holds maxabs_partials() doubles.
-int64_t maxabs_partials();
-int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s,
-                  Prof *prof);
-
 // Jacobi eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
 // matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if
 // converged else 1.

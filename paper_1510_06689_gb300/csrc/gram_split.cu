@@ -4,40 +4,46 @@
 // flops; GB300 runs float64 at ~1.2 TFLOP/s but BF16 tensor MMAs at ~1.9
 // PFLOP/s.  This kernel forms the Gram from exact integer digits:
 //
-//   * Columns are taken in groups of 512.  For row i of group g, with
-//     2^E_ig the smallest power of two above the row's largest magnitude in
-//     the group, every entry becomes v = round(y 2^(21 - E_ig)), |v| <= 2^21,
-//     split into three balanced digits v = s1 2^14 + s2 2^7 + s3 with
-//     |s1| <= 128 and |s2|, |s3| <= 64.  Every digit (and 2 s3, s3 / 128) is
-//     exact in BF16.  Scaling per row and per group keeps 21 significant bits
-//     relative to the local magnitude, so rows and regions of small entries
-//     keep their relative precision.
-//   * Products are grouped by level p + q (weight 2^(7 (6 - p - q))):
-//       acc0 = A1 A1^T                       (level 2, exact)
-//       acc1 = A1 A2^T                       (level 3, exact, counted twice)
-//       acc2 = A1 (2 A3)^T + A2 A2^T         (level 4, exact)
-//       acc3 = A2 (2 A3)^T + A3 (A3 / 128)^T (levels 5 and 6)
-//     Digit products are integers below 2^15; FP32 sums of integers stay
-//     exact below 2^24, so acc0..acc2 are exact over a 512-column group
-//     (acc2 <= 512 (128^2 + 64^2) < 2^24).  acc3 carries the two lowest
-//     levels with ordinary FP32 rounding: its relative weight is 2^-21, so its
-//     rounding error is ~2^-45 of the result.
-//   * At the end of each group the four accumulators are drained:
+//   * Columns are taken in groups of 512.  A first pass (k_rowgroup_exp)
+//     tabulates, for row i of group g, the exponent E_ig of the smallest
+//     power of two above the row's largest magnitude in the group, and the
+//     largest magnitude overall.  Every entry then becomes
+//     v = round(y 2^(21 - E_ig)), |v| <= 2^21, split into three balanced
+//     digits v = s1 2^14 + s2 2^7 + s3 (|s1| <= 128, |s2|, |s3| <= 64); the
+//     digits and 2 s3 are exact in BF16.  Scaling per row and per group keeps
+//     21 significant bits relative to the local magnitude, so rows and regions
+//     of small entries keep their relative precision.
+//   * Digit products are grouped by level p + q (weight 2^(7 (6 - p - q))),
+//     and only the symmetric part of each accumulator counts (S is formed
+//     from C + C^T below):
+//       acc0 = A1 A1^T                                (level 2)
+//       acc1 = A1 A2^T                                (level 3)
+//       acc2 = A1 (2 A3)^T + A2 A2^T                  (level 4)
+//       acc3 = A2 (2 A3)^T + (2 A3) (A3 / 256)^T      (levels 5 and 6)
+//     Digit products of levels 2..5 are integers of at most 2^14; FP32 sums
+//     of integers stay exact below 2^24 and acc0..acc2 do over a group
+//     (acc2 <= 512 (128 128 + 64 64) < 2^24).  acc3 carries level 6 in units
+//     of 2^-7 with ordinary FP32 rounding; its weight is 2^-21 of level 2, so
+//     that rounding is ~2^-45 of the result.
+//   * At the end of each group the accumulators are drained:
 //     C += (2^28 acc0 + 2^22 acc1 + 2^14 acc2 + 2^7 acc3) 2^(E_ig + E_jg - 2 E)
-//     into per-thread double-float (FP32 pair) accumulators, E the exponent of
-//     the global bound 2^E > max|Y|.  Every product of every level is counted,
-//     and S = (C + C^T) 2^(2E - 43) after a fixed-order float64 reduction of
-//     the per-CTA partials.  The four 128 x 128 accumulators fill TMEM's 512
-//     columns.
+//     into per-thread double-float (FP32 pair) accumulators, with 2^E above
+//     the global largest magnitude; S = (C + C^T) 2^(2E - 43) after a
+//     fixed-order float64 reduction of the per-CTA partials.  The four
+//     128 x 128 accumulators fill TMEM's 512 columns; the double-float C
+//     (128 KB) sits in shared memory beside two 32-column digit stages, so
+//     the converting threads keep their registers for a two-chunk prefetch.
 //
-// The result is the Gram of Y rounded to 21 bits below each local power of
-// two (zero-mean rounding); the noise this adds to the tail eigenvalues is
-// ~ (J - R)/J 2^-42/12 (2^E_ig / rms)^2 of ||Y||^2, a few 1e-13 for smooth
-// data.  Operand tiles use the K-major, no-swizzle canonical layout of tcgen05
-// shared-memory descriptors (8-row x 16-byte core matrices; LBO = 128 B
-// between core matrices along K, SBO = 1024 B between 8-row groups).  Every
-// mbarrier wait is bounded and CTA-uniform; on expiry the kernel raises an
-// error flag, waits (bounded) for its own MMAs, frees its TMEM and returns.
+// Both exponents are read on the device, so the step needs no host round
+// trip.  The result is the Gram of Y rounded to 21 bits below each local
+// power of two (zero-mean rounding); the noise this adds to the tail
+// eigenvalues is ~ (J - R)/J 2^-42/12 (2^E_ig / rms)^2 of ||Y||^2, a few
+// 1e-13 for smooth data.  Operand tiles use the K-major, no-swizzle canonical
+// layout of tcgen05 shared-memory descriptors (8-row x 16-byte core
+// matrices; LBO = 128 B between core matrices along K, SBO = 512 B between
+// 8-row groups).  Every mbarrier wait is bounded and CTA-uniform; on expiry
+// the kernel raises an error flag, waits (bounded) for its own MMAs, frees
+// its TMEM and returns.
 #include <algorithm>
 #include <cmath>
 
@@ -48,30 +54,70 @@ namespace tk {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kThreads = 512;
 constexpr int kRows = 128;         // M = N = 128 (J <= 128, zero padded)
-constexpr int kChunk = 64;         // columns staged per stage
-constexpr int kTiles = 5;          // A1, A2, A3, 2*A3, A3/128
+constexpr int kChunk = 32;         // columns staged per stage
+constexpr int kTiles = 4;          // digit tiles A1, A2, 2 A3, A3 / 256
 constexpr int kTileBytes = kRows * kChunk * 2;
+constexpr int kSbo = kChunk / 8 * 128;  // bytes between 8-row core-matrix groups
 constexpr int kStageBytes = kTiles * kTileBytes;
 constexpr int kStages = 2;
-constexpr int kDrainChunks = 8;    // 512 columns between drains
+constexpr int kGroup = 512;        // columns per exponent group and per exact accumulation
+constexpr int kDrainChunks = kGroup / kChunk;
 constexpr int kTmemCols = 512;
-
-using namespace tc;
+constexpr int kAccPerThread = kRows * kRows / kThreads;  // C entries each thread drains (32)
+constexpr int kZeroExp = -4000;    // exponent of an all-zero row (see exp_above)
 constexpr uint32_t kIdesc = idesc_bf16(kRows, kRows);
 
 struct SplitPlan {
   int J;
-  int E;
   int64_t K;
-  int64_t cols_per_split;
+  int64_t cols_per_split;  // a multiple of kGroup, so groups never straddle CTAs
   int nsplit;
+  int64_t ngroups;
 };
 
+// round(|y| 2^(21 - E)) with the sign of y (ties away from zero) from the
+// bits, in 32-bit integer arithmetic; e1022 = E + 1022 and |y| < 2^E.  With
+// m22 the leading 22 bits of the significand, v = (m22 + 2^sh) >> (sh + 1),
+// sh = E + 1022 - exponent field; the bits below m22 cannot change the result.
+__device__ __forceinline__ int scaled_int21(double y, int e1022) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m22 = (__funnelshift_l(lo, hi, 1) & 0x1FFFFFu) | 0x200000u;
+  const int sh = max(min(e1022 - ex, 30), 0);
+  unsigned v = (m22 + (1u << sh)) >> (sh + 1);
+  v = ex ? v : 0u;  // zero or subnormal
+  const int sgn = (int)hi >> 31;
+  return ((int)v ^ sgn) - sgn;
+}
+
+// Same for float: e1022 = E + 1022 as above; v = round(m24 / 2^sh) with
+// sh = E + 129 - exponent field >= 3.
+__device__ __forceinline__ int scaled_int21(float y, int e1022) {
+  const unsigned b = __float_as_uint(y);
+  const int ex = (int)((b >> 23) & 0xFFu);
+  const unsigned mant = (b & 0x7FFFFFu) | 0x800000u;
+  const int sh = max(min(e1022 - 893 - ex, 31), 1);
+  unsigned v = (mant + (1u << (sh - 1))) >> sh;
+  v = ex ? v : 0u;
+  const int sgn = (int)b >> 31;
+  return ((int)v ^ sgn) - sgn;
+}
+
+// Exact float of an integer |n| < 2^22, without a conversion instruction.
+__device__ __forceinline__ float small_int_float(int n) {
+  return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
+}
+// round-to-nearest integer of |x| < 2^22 as a float
+__device__ __forceinline__ float round_float(float x) { return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f); }
+
 template <typename T>
-__device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, int J, int64_t K, int64_t stride_b,
-                                          int i, int64_t c, int64_t c_end, T (&raw)[8]) {
+__device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, int J, int64_t stride_b, int i,
+                                          int64_t c, int64_t c_end, T (&raw)[8]) {
   // columns c .. c + 7 of row i (zero past the range or past J)
   if (i >= J || c >= c_end) {
 #pragma unroll
@@ -89,17 +135,73 @@ __device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Exponent table: E[g J + i] = exponent of the power of two above max |y_ic|
+// over the columns c of group g; the largest magnitude of all goes to *gmax
+// as its bit pattern (ordered like the magnitude).  One CTA per group.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, int64_t L, int J, int64_t K,
+                                                      int *__restrict__ E, unsigned long long *__restrict__ gmax) {
+  __shared__ unsigned long long rmax[kRows];
+  constexpr bool kF64 = sizeof(T) == 8;
+  const int64_t g = blockIdx.x;
+  const int64_t c0 = g * kGroup, c1 = min(K, c0 + kGroup);
+  const int ncols = (int)(c1 - c0);
+  for (int i = threadIdx.x; i < kRows; i += blockDim.x) rmax[i] = 0ull;
+  __syncthreads();
+  if (L == 1 && (2 * 256) % J == 0 && J % 2 == 0) {
+    // the group is one contiguous block of ncols * J entries; entry e is in
+    // row e % J, so each thread meets the same two rows throughout
+    const T *base = y + c0 * (int64_t)J;
+    const int n = ncols * J;
+    const int r0 = (2 * threadIdx.x) % J;
+    unsigned long long m0 = 0ull, m1 = 0ull;
+    for (int e = 2 * threadIdx.x; e < n; e += 2 * 256) {
+      m0 = max(m0, mag_bits(__ldg(base + e)));
+      m1 = max(m1, mag_bits(__ldg(base + e + 1)));
+    }
+    atomicMax(&rmax[r0], m0);
+    atomicMax(&rmax[r0 + 1], m1);
+  } else {
+    // row by row, the group's columns spread over the threads
+    const int64_t stride_b = L * (int64_t)J;
+    for (int i = 0; i < J; ++i) {
+      unsigned long long m = 0ull;
+      for (int cc = threadIdx.x; cc < ncols; cc += 256) {
+        const int64_t c = c0 + cc, b = c / L, l = c - b * L;
+        m = max(m, mag_bits(__ldg(y + l + stride_b * b + L * (int64_t)i)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(&rmax[i], m);
+    }
+  }
+  __syncthreads();
+  unsigned long long gm = 0ull;
+  for (int i = threadIdx.x; i < J; i += 256) {
+    E[g * J + i] = exp_above(rmax[i], kF64);
+    gm = max(gm, rmax[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  if ((threadIdx.x & 31) == 0 && gm != 0ull) atomicMax(gmax, gm);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict__ y, int64_t L, SplitPlan p,
+                                                            const int *__restrict__ Etab,
+                                                            const unsigned long long *__restrict__ gmax,
                                                             double *__restrict__ ws, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   __shared__ __align__(8) unsigned long long mbar[kStages];
-  __shared__ unsigned long long rowmax[kRows];
   __shared__ int rowexp[kRows];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
   unsigned char *stage_base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  // double-float accumulators of C, element e of thread t at [e][t]
+  float2 *cacc = reinterpret_cast<float2 *>(stage_base + kStages * kStageBytes);
   constexpr bool kF64 = sizeof(T) == 8;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -115,90 +217,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
   }
+#pragma unroll
+  for (int e = 0; e < kAccPerThread; ++e) cacc[e * kThreads + tid] = make_float2(0.f, 0.f);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
+  const int Eref = exp_above(*gmax, kF64);
 
   const int64_t c_begin = (int64_t)blockIdx.x * p.cols_per_split;
   const int64_t c_end = min(p.K, c_begin + p.cols_per_split);
   const int nchunks = (int)((c_end - c_begin + kChunk - 1) / kChunk);
   const int64_t stride_b = L * (int64_t)p.J;
 
-  // loader/converter role: row `row`, column groups kg0 and kg0 + 4 of a chunk
+  // converter role: row `row`, columns 8 kg .. 8 kg + 7 of each chunk
   const int row = tid % kRows;
-  const int kg0 = tid / kRows;
+  const int kg = tid / kRows;
   // drain role: TMEM lanes 32 q .. 32 q + 31, columns 32 cb .. 32 cb + 31
   const int q = warp & 3, cb = warp >> 2;
   const int drow = 32 * q + lane;
-  float acc_hi[32], acc_lo[32];
-#pragma unroll
-  for (int e = 0; e < 32; ++e) acc_hi[e] = acc_lo[e] = 0.f;
 
-  T raw[2][8];
   int last_committed = -1;
-  int my_exp = 0;
-  for (int ch = 0; ch < nchunks; ++ch) {
+  int my_e1022 = 0;
+
+  // One chunk: convert `raw` (this chunk's unit) to digits, issue its MMAs,
+  // refill `raw` with the unit two chunks ahead, and drain at a group's end.
+  // Returns false when a bounded wait expired (stop is then set CTA-wide).
+  auto chunk = [&](int ch, T(&raw)[8]) -> bool {
     const int buf = ch & 1;
     const int in_group = ch % kDrainChunks;
-    if (in_group == 0) {
-      // exponent of each row over this group's columns (the re-read below hits L2)
-      if (tid < kRows) rowmax[tid] = 0ull;
-      __syncthreads();
-      unsigned long long m = 0ull;
-      const int last = min(nchunks, ch + kDrainChunks);
-      for (int c2 = ch; c2 < last; ++c2) {
-        const int64_t cc = c_begin + (int64_t)c2 * kChunk;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          load_unit(y, L, p.J, p.K, stride_b, row, cc + 8 * (kg0 + 4 * u), c_end, raw[u]);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) m = max(m, mag_bits(raw[u][k]));
-        }
-      }
-      atomicMax(&rowmax[row], m);
-      __syncthreads();
-      if (tid < kRows) rowexp[tid] = exp_above(rowmax[tid], kF64);
-      __syncthreads();
-      my_exp = rowexp[row];
-      const int64_t cc = c_begin + (int64_t)ch * kChunk;
-      load_unit(y, L, p.J, p.K, stride_b, row, cc + 8 * kg0, c_end, raw[0]);
-      load_unit(y, L, p.J, p.K, stride_b, row, cc + 8 * (kg0 + 4), c_end, raw[1]);
+    if (in_group == 0 && tid < kRows) {
+      const int64_t g = (c_begin + (int64_t)ch * kChunk) / kGroup;
+      rowexp[tid] = tid < p.J ? Etab[g * p.J + tid] : kZeroExp;
     }
     // stage `buf` is free once the MMAs of chunk ch - 2 have completed; one
     // thread waits (bounded) and the barrier hands the outcome to all
-    if (ch >= 2) {
-      if (tid == 0 && !mbar_wait(smem_addr(&mbar[buf]), ((ch - 2) >> 1) & 1)) stop = 1;
-      __syncthreads();
-      if (stop) break;
-    }
+    if (ch >= 2 && tid == 0 && !mbar_wait(smem_addr(&mbar[buf]), ((ch - 2) >> 1) & 1)) stop = 1;
+    __syncthreads();
+    if (stop) return false;
+    if (in_group == 0) my_e1022 = rowexp[row] + 1022;
     unsigned char *st = stage_base + buf * kStageBytes;
-    // convert the two units to digits and store one 16-byte core-matrix row per tile
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int kg = kg0 + 4 * u;
+    {
       uint32_t w[kTiles][4];
 #pragma unroll
       for (int k = 0; k < 8; k += 2) {
-        int d1[2], d2[2], d3[2];
+        float d[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int v = scaled_int(raw[u][k + h], my_exp);
-          const int s1 = (v + (1 << 13)) >> 14;
-          const int r1 = v - (s1 << 14);
-          const int s2 = (r1 + 64) >> 7;
-          d1[h] = s1;
-          d2[h] = s2;
-          d3[h] = r1 - (s2 << 7);
+          const float v = small_int_float(scaled_int21(raw[k + h], my_e1022));
+          const float s1 = round_float(v * 0x1p-14f);
+          const float r1 = __fmaf_rn(s1, -16384.0f, v);
+          const float s2 = round_float(r1 * 0x1p-7f);
+          const float s3 = __fmaf_rn(s2, -128.0f, r1);
+          d[h][0] = s1;
+          d[h][1] = s2;
+          d[h][2] = s3 + s3;
+          d[h][3] = s3 * 0x1p-8f;
         }
         const int j = k >> 1;
-        w[0][j] = bf16_pair((float)d1[0], (float)d1[1]);
-        w[1][j] = bf16_pair((float)d2[0], (float)d2[1]);
-        w[2][j] = bf16_pair((float)d3[0], (float)d3[1]);
-        w[3][j] = bf16_pair((float)(2 * d3[0]), (float)(2 * d3[1]));
-        w[4][j] = bf16_pair((float)d3[0] * 0x1p-7f, (float)d3[1] * 0x1p-7f);
+#pragma unroll
+        for (int t = 0; t < kTiles; ++t) w[t][j] = bf16_pair(d[0][t], d[1][t]);
       }
-      const int off = (row >> 3) * 1024 + kg * 128 + (row & 7) * 16;
+      const int off = (row >> 3) * kSbo + kg * 128 + (row & 7) * 16;
 #pragma unroll
       for (int t = 0; t < kTiles; ++t)
         *reinterpret_cast<uint4 *>(st + t * kTileBytes + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
@@ -211,56 +291,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
 #pragma unroll
       for (int s = 0; s < kChunk / 16; ++s) {
         const uint32_t acc = (in_group == 0 && s == 0) ? 0u : 1u;
-        const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * s, 128, 1024);
-        const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * s, 128, 1024);
-        const uint64_t a3 = smem_desc(base + 2 * kTileBytes + 256 * s, 128, 1024);
-        const uint64_t a3x2 = smem_desc(base + 3 * kTileBytes + 256 * s, 128, 1024);
-        const uint64_t a3s = smem_desc(base + 4 * kTileBytes + 256 * s, 128, 1024);
+        const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * s, 128, kSbo);
         mma_bf16(tmem + 0, a1, a1, kIdesc, acc);
         mma_bf16(tmem + 128, a1, a2, kIdesc, acc);
         mma_bf16(tmem + 256, a1, a3x2, kIdesc, acc);
         mma_bf16(tmem + 256, a2, a2, kIdesc, 1u);
         mma_bf16(tmem + 384, a2, a3x2, kIdesc, acc);
-        mma_bf16(tmem + 384, a3, a3s, kIdesc, 1u);
+        mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
       }
       mma_commit(smem_addr(&mbar[buf]));
     }
     last_committed = ch;
+    // refill with the unit two chunks ahead while the tensor cores work
+    load_unit(y, L, p.J, stride_b, row, c_begin + (int64_t)(ch + 2) * kChunk + 8 * kg, c_end, raw);
     if (in_group == kDrainChunks - 1 || ch == nchunks - 1) {
       if (tid == 0 && !mbar_wait(smem_addr(&mbar[buf]), (ch >> 1) & 1)) stop = 1;
       __syncthreads();
       if (!stop) {  // uniform across the CTA, so the .sync.aligned loads below never diverge
         fence_after();
         const float wts[4] = {0x1p28f, 0x1p22f, 0x1p14f, 0x1p7f};  // 2^28, 2 2^21, 2^14, 2^7
-        const int ei = rowexp[drow] - p.E;
+        const int ei = rowexp[drow] - Eref;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float sc[16];
+        for (int part = 0; part < 4; ++part) {
+          float sc[8], hi[8], lo[8];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int x = ei + rowexp[32 * cb + 16 * half + e] - p.E;  // <= 0
+          for (int e = 0; e < 8; ++e) {
+            const int x = ei + rowexp[32 * cb + 8 * part + e] - Eref;  // <= 0
             sc[e] = x < -120 ? 0.f : __int_as_float((127 + x) << 23);
+            const float2 a = cacc[(8 * part + e) * kThreads + tid];
+            hi[e] = a.x;
+            lo[e] = a.y;
           }
 #pragma unroll
           for (int lev = 0; lev < 4; ++lev) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * lev + 32 * cb + 16 * half), r);
+            uint32_t r[8];
+            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * lev + 32 * cb + 8 * part), r);
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              df_add(acc_hi[16 * half + e], acc_lo[16 * half + e], __uint_as_float(r[e]) * wts[lev] * sc[e]);
+            for (int e = 0; e < 8; ++e) df_add(hi[e], lo[e], __uint_as_float(r[e]) * wts[lev] * sc[e]);
           }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) cacc[(8 * part + e) * kThreads + tid] = make_float2(hi[e], lo[e]);
         }
       }
       fence_before();
       __syncthreads();
-      if (stop) break;
+      if (stop) return false;
     }
-    // prefetch the next chunk of this group while the tensor cores work
-    if (ch + 1 < nchunks && (ch + 1) % kDrainChunks != 0) {
-      const int64_t cn = c_begin + (int64_t)(ch + 1) * kChunk;
-      load_unit(y, L, p.J, p.K, stride_b, row, cn + 8 * kg0, c_end, raw[0]);
-      load_unit(y, L, p.J, p.K, stride_b, row, cn + 8 * (kg0 + 4), c_end, raw[1]);
-    }
+    return true;
+  };
+
+  T raw0[8], raw1[8];
+  load_unit(y, L, p.J, stride_b, row, c_begin + 8 * kg, c_end, raw0);
+  load_unit(y, L, p.J, stride_b, row, c_begin + kChunk + 8 * kg, c_end, raw1);
+  for (int ch = 0; ch < nchunks; ch += 2) {
+    if (!chunk(ch, raw0)) break;
+    if (ch + 1 < nchunks && !chunk(ch + 1, raw1)) break;
   }
   // make sure no MMA of ours is still running before TMEM is released
   if (stop && last_committed >= 0 && tid == 0)
@@ -278,11 +366,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
   // per-CTA C (not yet symmetrised), row-major 128 x 128
   double *dst = ws + (size_t)blockIdx.x * kRows * kRows + (size_t)drow * kRows + 32 * cb;
 #pragma unroll
-  for (int e = 0; e < 32; ++e) dst[e] = (double)acc_hi[e] + (double)acc_lo[e];
+  for (int e = 0; e < kAccPerThread; ++e) {
+    const float2 a = cacc[e * kThreads + tid];
+    dst[e] = (double)a.x + (double)a.y;
+  }
 }
 
+// S = (sum of the per-CTA C + C^T) 2^(2E - 43); NaN throughout when the
+// largest magnitude is not finite (Y holds Inf or NaN).
 __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, int nsplit, int J,
-                                                           double scale, double *__restrict__ S) {
+                                                           const unsigned long long *__restrict__ gmax, int is_f64,
+                                                           double *__restrict__ S) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= J * J) return;
   const int i = idx % J, j = idx / J;
@@ -291,101 +385,91 @@ __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restr
     const double *c = ws + (size_t)sp * kRows * kRows;
     s += c[i * kRows + j] + c[j * kRows + i];
   }
-  S[i + (int64_t)J * j] = s * scale;
+  const unsigned long long gm = *gmax;
+  const bool finite = is_f64 ? gm < 0x7FF0000000000000ull : gm < 0x7F800000ull;
+  const int E = exp_above(gm, is_f64 != 0);
+  S[i + (int64_t)J * j] = !finite ? __longlong_as_double(0x7FF8000000000000ll) : (E == kZeroExp ? 0.0 : ldexp(s, 2 * E - 43));
 }
 
-__global__ void __launch_bounds__(256) k_maxabs_partial(const void *__restrict__ x, int is_f64, int64_t n,
-                                                        double *__restrict__ partial) {
-  __shared__ double red[256];
-  double m = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double v = is_f64 ? fabs(__ldg(static_cast<const double *>(x) + i))
-                            : (double)fabsf(__ldg(static_cast<const float *>(x) + i));
-    m = fmax(m, v);
-  }
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kRows * kRows * sizeof(float2) + 1024;
 
-__global__ void k_maxabs_final(const double *__restrict__ partial, int n, double *__restrict__ out) {
-  __shared__ double red[256];
-  double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, partial[i]);
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[0] = red[0];
-}
-
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024;
-
-SplitPlan split_plan(int64_t L, int64_t J, int64_t B, double maxabs, const DeviceInfo &dev) {
+SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   SplitPlan p{};
   p.J = (int)J;
   p.K = L * B;
-  int e = 0;
-  if (maxabs > 0.0) std::frexp(maxabs, &e);  // maxabs < 2^e
-  p.E = e;
-  const int64_t chunks = (p.K + kChunk - 1) / kChunk;
-  const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(dev.sms, chunks));
-  const int64_t chunks_per = (chunks + ns - 1) / ns;
-  p.cols_per_split = chunks_per * kChunk;
+  p.ngroups = (p.K + kGroup - 1) / kGroup;
+  const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ngroups));
+  const int64_t groups_per = (p.ngroups + ns - 1) / ns;
+  p.cols_per_split = groups_per * kGroup;
   p.nsplit = (int)((p.K + p.cols_per_split - 1) / p.cols_per_split);
   return p;
 }
 
+// workspace (in doubles): per-CTA partials | exponent table (ints) | gmax | error flag
+struct SplitWs {
+  double *partials;
+  int *table;
+  unsigned long long *gmax;
+  int *err;
+};
+
+SplitWs split_ws(double *d_ws, const SplitPlan &p) {
+  const int64_t np = (int64_t)p.nsplit * kRows * kRows;
+  const int64_t tab = (p.ngroups * p.J + 1) / 2;
+  SplitWs w;
+  w.partials = d_ws;
+  w.table = reinterpret_cast<int *>(d_ws + np);
+  w.gmax = reinterpret_cast<unsigned long long *>(d_ws + np + tab);
+  w.err = reinterpret_cast<int *>(d_ws + np + tab + 1);
+  return w;
+}
+
 }  // namespace
 
-int64_t maxabs_partials() { return 1024; }
-
-int launch_maxabs(const void *x, tucker_dtype dt, int64_t n, double *d_partials, double *d_out, cudaStream_t s,
-                  Prof *prof) {
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (n + 1023) / 1024));
-  if (prof) prof->begin(TUCKER_PHASE_SCALE);
-  k_maxabs_partial<<<blocks, 256, 0, s>>>(x, dt == TUCKER_F64, n, d_partials);
-  TK_LAUNCHED();
-  k_maxabs_final<<<1, 256, 0, s>>>(d_partials, blocks, d_out);
-  TK_LAUNCHED();
-  if (prof) prof->end(0.0, (double)n * (dt == TUCKER_F64 ? 8 : 4), 2);
-  return TUCKER_OK;
-}
-
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
-  const SplitPlan p = split_plan(L, J, B, 1.0, dev);
-  return (int64_t)p.nsplit * kRows * kRows + 8;
+  const SplitPlan p = split_plan(L, J, B, dev);
+  return (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + 4;
 }
 
-int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs, double *d_S,
-                      double *d_ws, const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
+int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
   if (J > kRows) {
     set_error("split-precision Gram supports J <= %d (got %lld)", kRows, (long long)J);
     return TUCKER_EUNSUPPORTED;
   }
-  const SplitPlan p = split_plan(L, J, B, maxabs, dev);
-  int *d_err = reinterpret_cast<int *>(d_ws + (int64_t)p.nsplit * kRows * kRows);
-  TK_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  const SplitPlan p = split_plan(L, J, B, dev);
+  if (p.ngroups > 0x7FFFFFFFll) {
+    set_error("split-precision Gram: too many column groups (%lld)", (long long)p.ngroups);
+    return TUCKER_EUNSUPPORTED;
+  }
+  const SplitWs w = split_ws(d_ws, p);
+  const bool f64 = dt == TUCKER_F64;
+  const double in_bytes = (double)p.K * J * (f64 ? 8 : 4);
+  TK_CUDA(cudaMemsetAsync(w.gmax, 0, 2 * sizeof(double), s));  // gmax and the error flag
+  if (prof) prof->begin(TUCKER_PHASE_SCALE);
+  if (f64)
+    k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
+                                                               w.table, w.gmax);
+  else
+    k_rowgroup_exp<float><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const float *>(y), L, (int)J, p.K,
+                                                              w.table, w.gmax);
+  TK_LAUNCHED();
+  if (prof) prof->end(0.0, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM);
-  if (dt == TUCKER_F64) {
+  if (f64) {
     TK_CUDA(cudaFuncSetAttribute(k_gram_split<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    k_gram_split<double><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const double *>(y), L, p, d_ws, d_err);
+    k_gram_split<double><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const double *>(y), L, p, w.table,
+                                                                w.gmax, w.partials, w.err);
   } else {
     TK_CUDA(cudaFuncSetAttribute(k_gram_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    k_gram_split<float><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const float *>(y), L, p, d_ws, d_err);
+    k_gram_split<float><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const float *>(y), L, p, w.table,
+                                                               w.gmax, w.partials, w.err);
   }
   TK_LAUNCHED();
-  if (prof) prof->end((double)J * (J + 1) * (double)p.K, (double)p.K * J * (dt == TUCKER_F64 ? 8 : 4), 1);
+  if (prof) prof->end((double)J * (J + 1) * (double)p.K, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
-  const double scale = std::ldexp(1.0, 2 * p.E - 43);
-  k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(d_ws, p.nsplit, (int)J, scale, d_S);
+  k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(w.partials, p.nsplit, (int)J, w.gmax, f64,
+                                                                      d_S);
   TK_LAUNCHED();
   if (prof) prof->end((double)p.nsplit * J * J * 2, (double)p.nsplit * kRows * kRows * 8, 1);
   return TUCKER_OK;
@@ -393,8 +477,9 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
 
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s) {
-  const SplitPlan p = split_plan(L, J, B, 1.0, dev);
-  TK_CUDA(cudaMemcpyAsync(h_err, d_ws + (int64_t)p.nsplit * kRows * kRows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const SplitPlan p = split_plan(L, J, B, dev);
+  const SplitWs w = split_ws(const_cast<double *>(d_ws), p);
+  TK_CUDA(cudaMemcpyAsync(h_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return TUCKER_OK;
 }
 

@@ -275,11 +275,10 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   double *d_tail = d_nx2 + 1;
   int64_t *d_rank = reinterpret_cast<int64_t *>(d_nx2 + 2);
   int *d_info = reinterpret_cast<int *>(d_nx2 + 3);
-  double *d_max = d_nx2 + 4;
   int *d_terr = reinterpret_cast<int *>(d_nx2 + 6);
   TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
   if (prec == TUCKER_PREC_BF16X4) {
-    TK_CHECK(partials.alloc(sizeof(double) * std::max(norm2_partials(), maxabs_partials()), s));
+    TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
     for (int n = 0; n < N; ++n)
       if (dims[n] > 128) {
         set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
@@ -337,13 +336,9 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
 
     // Gram step
     if (prec == TUCKER_PREC_BF16X4) {
-      const int64_t I_cur = L * J * B;
-      TK_CHECK(launch_maxabs(Y, ydt, I_cur, partials.as<double>(), d_max, s, &prof));
-      TK_CUDA(cudaMemcpyAsync(h + 4, d_max, sizeof(double), cudaMemcpyDeviceToHost, s));
-      TK_CUDA(cudaStreamSynchronize(s));
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
-      TK_CHECK(launch_gram_split(Y, ydt, L, J, B, h[4], S.as<double>(), gramws.as<double>(), dev, s, &prof));
+      TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
       TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
     } else {
       const int64_t gws = gram_workspace_doubles(L, J, B, dev);
@@ -743,10 +738,9 @@ int tucker_gram(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B,
   return TUCKER_OK;
 }
 
-int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double maxabs, double *S,
-                      void *stream) {
+int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream) {
   g_err[0] = 0;
-  if (!Y || !S || L < 1 || B < 1 || J < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32) || std::isnan(maxabs)) {
+  if (!Y || !S || L < 1 || B < 1 || J < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
     set_error("invalid arguments to tucker_gram_split");
     return TUCKER_EINVAL;
   }
@@ -758,20 +752,9 @@ int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int6
   DeviceInfo dev;
   TK_CHECK(device_info(&dev));
   Prof prof(s);
-  DevBuf ws, part, mx;
-  if (!(maxabs > 0.0)) {
-    TK_CHECK(part.alloc(sizeof(double) * maxabs_partials(), s));
-    TK_CHECK(mx.alloc(sizeof(double), s));
-    TK_CHECK(launch_maxabs(Y, dt, L * J * B, part.as<double>(), mx.as<double>(), s, &prof));
-    TK_CUDA(cudaMemcpyAsync(&maxabs, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
-    if (!std::isfinite(maxabs)) {
-      set_error("max|Y| is not finite");
-      return TUCKER_ENONFINITE;
-    }
-  }
+  DevBuf ws;
   TK_CHECK(ws.alloc(sizeof(double) * gram_split_workspace_doubles(L, J, B, dev), s));
-  TK_CHECK(launch_gram_split(Y, dt, L, J, B, maxabs, S, ws.as<double>(), dev, s, &prof));
+  TK_CHECK(launch_gram_split(Y, dt, L, J, B, S, ws.as<double>(), dev, s, &prof));
   int herr = 0;
   TK_CHECK(gram_split_error(ws.as<double>(), L, J, B, dev, &herr, s));
   TK_CUDA(cudaStreamSynchronize(s));

@@ -89,7 +89,7 @@ def load(path=LIB_PATH):
         "tucker_rank_cut": (i32, [vp, i64, dbl, i32, pi64, pdbl, vp]),
         "tucker_ttm": (i32, [vp, i32, i64, i64, i64, vp, i64, i32, vp, vp]),
         "tucker_gram_noalloc": (i32, [vp, i32, i64, i64, i64, vp, vp]),
-        "tucker_gram_split": (i32, [vp, i32, i64, i64, i64, dbl, vp, vp]),
+        "tucker_gram_split": (i32, [vp, i32, i64, i64, i64, vp, vp]),
         "tucker_ttm_split": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, vp]),
         "tucker_status_string": (ctypes.c_char_p, [i32]),
         "tucker_last_error": (ctypes.c_char_p, []),
@@ -289,12 +289,12 @@ def gram_noalloc(y, L, J, B, out=None, stream=None):
     return s.t()
 
 
-def gram_split(y, L, J, B, maxabs=0.0, stream=None):
+def gram_split(y, L, J, B, stream=None):
     """Split-precision Gram on the tensor cores (J <= 128); same layout as :func:`gram`."""
     lib = load()
     s = torch.empty((J, J), dtype=torch.float64, device="cuda")
-    _check(lib.tucker_gram_split(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), float(maxabs),
-                                 _dev_ptr(s, "S"), _stream(stream)))
+    _check(lib.tucker_gram_split(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
+                                 _stream(stream)))
     return s.t()
 
 

@@ -2,7 +2,7 @@
 
 The kernel computes the Gram of Y with every entry rounded to 21 bits below
 the power of two above its row's largest magnitude within a 512-column
-group.  Rigorous bound per entry, with h_i = 2^(E_i - 22) and 2^E_i the
+group (the exponents come from a device-side pass over Y).  Rigorous bound per entry, with h_i = 2^(E_i - 22) and 2^E_i the
 power of two above row i's largest magnitude over all columns (an upper
 bound of every group's rounding radius):
 
@@ -70,15 +70,48 @@ def test_gram_split_exact_on_leading_digit_inputs(gpu_lib):
     assert np.array_equal(s * 2 ** 14, exact.astype(np.float64))
 
 
-def test_gram_split_f32_and_maxabs_argument(gpu_lib):
+def test_gram_split_f32(gpu_lib):
     rng = np.random.default_rng(9)
     L, J, B = 5, 96, 400
     y = rng.standard_normal(L * J * B).astype(np.float32)
-    s1 = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
-    s2 = gpu_lib.gram_split(dev(y), L, J, B, maxabs=float(np.abs(y).max())).cpu().numpy()
-    assert np.array_equal(s1, s2)
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
     bound, ref = split_bound(y, L, J, B)
-    assert np.all(np.abs(s1 - ref) <= bound)
+    assert np.all(np.abs(s - ref) <= bound)
+
+
+def test_gram_split_local_exponents(gpu_lib):
+    """Rows and 512-column groups of very different magnitude keep their own 21 bits.
+
+    Row i of group g is scaled by 10^(-3 i / J - 4 [g odd]); the bound with a
+    per-(row, group) rounding radius must hold, which a single exponent per row
+    (or for the whole matrix) would break on the small rows and groups.
+    """
+    rng = np.random.default_rng(12)
+    L, J, B = 1, 64, 4 * 512 + 100
+    y = rng.standard_normal((J, B)) * 10.0 ** (-3.0 * np.arange(J) / J)[:, None]
+    y[:, 512:1024] *= 1e-4
+    y[:, 1536:2048] *= 1e-4
+    s = gpu_lib.gram_split(dev(y.ravel(order="F")), L, J, B).cpu().numpy()
+    ref = y @ y.T
+    h = np.zeros_like(y)
+    for g0 in range(0, B, 512):
+        blk = np.abs(y[:, g0:g0 + 512]).max(axis=1)
+        h[:, g0:g0 + 512] = np.array([2.0 ** (math.frexp(m)[1] - 22) for m in blk])[:, None]
+    a = np.abs(y)
+    bound = h @ a.T + a @ h.T + h @ h.T + 2.0 ** -40 * (a @ a.T)
+    assert np.all(np.abs(s - ref) <= bound)
+
+
+def test_gram_split_zero_and_nonfinite(gpu_lib):
+    z = gpu_lib.gram_split(dev(np.zeros(3 * 40 * 700)), 3, 40, 700).cpu().numpy()
+    assert np.array_equal(z, np.zeros((40, 40)))
+    y = np.random.default_rng(13).standard_normal(2 * 16 * 300)
+    y[777] = np.nan
+    s = gpu_lib.gram_split(dev(y), 2, 16, 300).cpu().numpy()
+    assert np.isnan(s).all()
+    y[777] = np.inf
+    s = gpu_lib.gram_split(dev(y.astype(np.float32)), 2, 16, 300).cpu().numpy()
+    assert np.isnan(s).all()
 
 
 def test_gram_split_deterministic_and_rejects_large_j(gpu_lib):
