@@ -46,6 +46,7 @@
 // its TMEM and returns.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tcgen05.cuh"
@@ -108,29 +109,83 @@ __device__ __forceinline__ int scaled_int21(float y, int e1022) {
   return ((int)v ^ sgn) - sgn;
 }
 
-// Exact float of an integer |n| < 2^22, without a conversion instruction.
-__device__ __forceinline__ float small_int_float(int n) {
-  return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
-}
-// round-to-nearest integer of |x| < 2^22 as a float
-__device__ __forceinline__ float round_float(float x) { return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f); }
+// How a unit of 8 consecutive columns of one row is addressed in the
+// (L, J, B) view, where column c = l + L b of row i is y[l + L i + L J b]:
+//   kColsStrided   L == 1: the 8 entries are J apart;
+//   kColsContig    L % 8 == 0 and y 16-byte aligned: units start at l % 8 == 0,
+//                  never cross a run of L, and are read as 16-byte vectors;
+//   kColsGeneric   anything else, entry by entry.
+enum { kColsGeneric = 0, kColsStrided = 1, kColsContig = 2 };
+
+// Position (l, b) of a column, advanced without divisions.
+struct ColPos {
+  int64_t l, b;
+  __device__ __forceinline__ void init(int64_t c, int64_t L) {
+    b = c / L;
+    l = c - b * L;
+  }
+  __device__ __forceinline__ void advance(int64_t n, int64_t L) {
+    l += n;
+    while (l >= L) {  // at most n / L + 1 times
+      l -= L;
+      ++b;
+    }
+  }
+};
 
 template <typename T>
+__device__ __forceinline__ void load8_vec(const T *__restrict__ p, T (&raw)[8]) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
+      raw[2 * k] = v.x;
+      raw[2 * k + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
+      raw[4 * k] = v.x;
+      raw[4 * k + 1] = v.y;
+      raw[4 * k + 2] = v.z;
+      raw[4 * k + 3] = v.w;
+    }
+  }
+}
+
+// Columns c .. c + 7 of row i (zero past c_end or past J); pos is column c's
+// position (used by kColsContig only).
+template <typename T, int kMode>
 __device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, int J, int64_t stride_b, int i,
-                                          int64_t c, int64_t c_end, T (&raw)[8]) {
-  // columns c .. c + 7 of row i (zero past the range or past J)
+                                          int64_t c, int64_t c_end, const ColPos &pos, T (&raw)[8]) {
   if (i >= J || c >= c_end) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) raw[k] = T(0);
     return;
   }
-  int64_t b = c / L, l = c - b * L;
+  const bool full = c + 8 <= c_end;
+  if constexpr (kMode == kColsStrided) {
+    const T *p = y + i + (int64_t)J * c;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    raw[k] = (c + k < c_end) ? __ldg(y + l + stride_b * b + L * (int64_t)i) : T(0);
-    if (++l == L) {
-      l = 0;
-      ++b;
+    for (int k = 0; k < 8; ++k) raw[k] = (full || c + k < c_end) ? __ldg(p + (int64_t)J * k) : T(0);
+  } else if constexpr (kMode == kColsContig) {
+    const T *p = y + pos.l + L * (int64_t)i + stride_b * pos.b;
+    if (full) {
+      load8_vec(p, raw);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) raw[k] = (c + k < c_end) ? __ldg(p + k) : T(0);
+    }
+  } else {
+    int64_t b = c / L, l = c - b * L;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      raw[k] = (c + k < c_end) ? __ldg(y + l + stride_b * b + L * (int64_t)i) : T(0);
+      if (++l == L) {
+        l = 0;
+        ++b;
+      }
     }
   }
 }
@@ -138,57 +193,82 @@ __device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, in
 // ---------------------------------------------------------------------------
 // Exponent table: E[g J + i] = exponent of the power of two above max |y_ic|
 // over the columns c of group g; the largest magnitude of all goes to *gmax
-// as its bit pattern (ordered like the magnitude).  One CTA per group.
+// as a bit pattern ordered like the magnitude.  One CTA of 256 threads per
+// group.  With L == 1 (J dividing 512, J even) the group is one contiguous
+// block read as 16-byte vectors, each thread meeting the same two rows
+// throughout; otherwise each warp takes whole rows, its lanes spread over the
+// group's columns (consecutive columns are consecutive entries within a run
+// of L).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, int64_t L, int J, int64_t K,
-                                                      int *__restrict__ E, unsigned long long *__restrict__ gmax) {
-  __shared__ unsigned long long rmax[kRows];
+                                                      int contig_pairs, int *__restrict__ E,
+                                                      unsigned long long *__restrict__ gmax) {
+  __shared__ unsigned rmax[kRows];
   constexpr bool kF64 = sizeof(T) == 8;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t g = blockIdx.x;
   const int64_t c0 = g * kGroup, c1 = min(K, c0 + kGroup);
   const int ncols = (int)(c1 - c0);
-  for (int i = threadIdx.x; i < kRows; i += blockDim.x) rmax[i] = 0ull;
-  __syncthreads();
-  if (L == 1 && (2 * 256) % J == 0 && J % 2 == 0) {
-    // the group is one contiguous block of ncols * J entries; entry e is in
-    // row e % J, so each thread meets the same two rows throughout
-    const T *base = y + c0 * (int64_t)J;
-    const int n = ncols * J;
-    const int r0 = (2 * threadIdx.x) % J;
-    unsigned long long m0 = 0ull, m1 = 0ull;
-    for (int e = 2 * threadIdx.x; e < n; e += 2 * 256) {
-      m0 = max(m0, mag_bits(__ldg(base + e)));
-      m1 = max(m1, mag_bits(__ldg(base + e + 1)));
+  if (contig_pairs) {
+    for (int i = tid; i < kRows; i += 256) rmax[i] = 0u;
+    __syncthreads();
+    using V2 = typename std::conditional<kF64, double2, float2>::type;
+    const V2 *base = reinterpret_cast<const V2 *>(y + c0 * (int64_t)J);
+    const int n2 = ncols * J / 2;  // pairs; pair e covers rows (2e) % J and (2e) % J + 1
+    const int r0 = (2 * tid) % J;
+    unsigned m0 = 0u, m1 = 0u;
+    int e = tid;
+    for (; e + 3 * 256 < n2; e += 4 * 256) {
+      V2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(base + e + u * 256);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        m0 = max(m0, hi_mag(v[u].x));
+        m1 = max(m1, hi_mag(v[u].y));
+      }
+    }
+    for (; e < n2; e += 256) {
+      const V2 v = __ldg(base + e);
+      m0 = max(m0, hi_mag(v.x));
+      m1 = max(m1, hi_mag(v.y));
     }
     atomicMax(&rmax[r0], m0);
     atomicMax(&rmax[r0 + 1], m1);
   } else {
-    // row by row, the group's columns spread over the threads
+    // lane `lane` reads columns c0 + lane + 32 k, k < 16; their offsets are
+    // computed once and reused for every row
     const int64_t stride_b = L * (int64_t)J;
-    for (int i = 0; i < J; ++i) {
-      unsigned long long m = 0ull;
-      for (int cc = threadIdx.x; cc < ncols; cc += 256) {
-        const int64_t c = c0 + cc, b = c / L, l = c - b * L;
-        m = max(m, mag_bits(__ldg(y + l + stride_b * b + L * (int64_t)i)));
-      }
+    int64_t off[kGroup / 32];
+#pragma unroll
+    for (int k = 0; k < kGroup / 32; ++k) {
+      const int cc = lane + 32 * k;
+      const int64_t c = c0 + cc, b = c / L, l = c - b * L;
+      off[k] = cc < ncols ? l + stride_b * b : -1;
+    }
+    for (int i = warp; i < J; i += 8) {
+      unsigned m = 0u;
+#pragma unroll
+      for (int k = 0; k < kGroup / 32; ++k)
+        if (off[k] >= 0) m = max(m, hi_mag(__ldg(y + off[k] + L * (int64_t)i)));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((threadIdx.x & 31) == 0) atomicMax(&rmax[i], m);
+      if (lane == 0) rmax[i] = m;
     }
   }
   __syncthreads();
-  unsigned long long gm = 0ull;
-  for (int i = threadIdx.x; i < J; i += 256) {
-    E[g * J + i] = exp_above(rmax[i], kF64);
+  unsigned gm = 0u;
+  for (int i = tid; i < J; i += 256) {
+    E[g * J + i] = exp_above(mag_pattern(rmax[i], kF64), kF64);
     gm = max(gm, rmax[i]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-  if ((threadIdx.x & 31) == 0 && gm != 0ull) atomicMax(gmax, gm);
+  if (lane == 0 && gm != 0u) atomicMax(gmax, mag_pattern(gm, kF64));
 }
 
-template <typename T>
+template <typename T, int kMode>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict__ y, int64_t L, SplitPlan p,
                                                             const int *__restrict__ Etab,
                                                             const unsigned long long *__restrict__ gmax,
@@ -243,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
   // One chunk: convert `raw` (this chunk's unit) to digits, issue its MMAs,
   // refill `raw` with the unit two chunks ahead, and drain at a group's end.
   // Returns false when a bounded wait expired (stop is then set CTA-wide).
-  auto chunk = [&](int ch, T(&raw)[8]) -> bool {
+  auto chunk = [&](int ch, T(&raw)[8], ColPos &pos) -> bool {
     const int buf = ch & 1;
     const int in_group = ch % kDrainChunks;
     if (in_group == 0 && tid < kRows) {
@@ -306,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
     }
     last_committed = ch;
     // refill with the unit two chunks ahead while the tensor cores work
-    load_unit(y, L, p.J, stride_b, row, c_begin + (int64_t)(ch + 2) * kChunk + 8 * kg, c_end, raw);
+    if constexpr (kMode == kColsContig) pos.advance(2 * kChunk, L);
+    load_unit<T, kMode>(y, L, p.J, stride_b, row, c_begin + (int64_t)(ch + 2) * kChunk + 8 * kg, c_end, pos, raw);
     if (in_group == kDrainChunks - 1 || ch == nchunks - 1) {
       if (tid == 0 && !mbar_wait(smem_addr(&mbar[buf]), (ch >> 1) & 1)) stop = 1;
       __syncthreads();
@@ -344,11 +425,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
   };
 
   T raw0[8], raw1[8];
-  load_unit(y, L, p.J, stride_b, row, c_begin + 8 * kg, c_end, raw0);
-  load_unit(y, L, p.J, stride_b, row, c_begin + kChunk + 8 * kg, c_end, raw1);
+  ColPos pos0{0, 0}, pos1{0, 0};
+  if constexpr (kMode == kColsContig) {
+    pos0.init(c_begin + 8 * kg, L);
+    pos1.init(c_begin + kChunk + 8 * kg, L);
+  }
+  load_unit<T, kMode>(y, L, p.J, stride_b, row, c_begin + 8 * kg, c_end, pos0, raw0);
+  load_unit<T, kMode>(y, L, p.J, stride_b, row, c_begin + kChunk + 8 * kg, c_end, pos1, raw1);
   for (int ch = 0; ch < nchunks; ch += 2) {
-    if (!chunk(ch, raw0)) break;
-    if (ch + 1 < nchunks && !chunk(ch + 1, raw1)) break;
+    if (!chunk(ch, raw0, pos0)) break;
+    if (ch + 1 < nchunks && !chunk(ch + 1, raw1, pos1)) break;
   }
   // make sure no MMA of ours is still running before TMEM is released
   if (stop && last_committed >= 0 && tid == 0)
@@ -424,6 +510,17 @@ SplitWs split_ws(double *d_ws, const SplitPlan &p) {
   return w;
 }
 
+template <typename T, int kMode>
+int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &w, const DeviceInfo &dev,
+                   cudaStream_t s) {
+  (void)dev;
+  TK_CUDA(cudaFuncSetAttribute(k_gram_split<T, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  k_gram_split<T, kMode><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const T *>(y), L, p, w.table, w.gmax,
+                                                                w.partials, w.err);
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
 }  // namespace
 
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
@@ -446,26 +543,29 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   const bool f64 = dt == TUCKER_F64;
   const double in_bytes = (double)p.K * J * (f64 ? 8 : 4);
   TK_CUDA(cudaMemsetAsync(w.gmax, 0, 2 * sizeof(double), s));  // gmax and the error flag
+  const int contig_pairs = L == 1 && (2 * 256) % J == 0 && J % 2 == 0 &&
+                           reinterpret_cast<uintptr_t>(y) % (f64 ? 16 : 8) == 0;
+  const int mode = L == 1 ? kColsStrided
+                          : (L % 8 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) ? kColsContig : kColsGeneric;
   if (prof) prof->begin(TUCKER_PHASE_SCALE);
   if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
-                                                               w.table, w.gmax);
+                                                               contig_pairs, w.table, w.gmax);
   else
     k_rowgroup_exp<float><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const float *>(y), L, (int)J, p.K,
-                                                              w.table, w.gmax);
+                                                              contig_pairs, w.table, w.gmax);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM);
   if (f64) {
-    TK_CUDA(cudaFuncSetAttribute(k_gram_split<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    k_gram_split<double><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const double *>(y), L, p, w.table,
-                                                                w.gmax, w.partials, w.err);
+    if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided>(y, L, p, w, dev, s)));
+    else if (mode == kColsContig) TK_CHECK((run_gram_split<double, kColsContig>(y, L, p, w, dev, s)));
+    else TK_CHECK((run_gram_split<double, kColsGeneric>(y, L, p, w, dev, s)));
   } else {
-    TK_CUDA(cudaFuncSetAttribute(k_gram_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    k_gram_split<float><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const float *>(y), L, p, w.table,
-                                                               w.gmax, w.partials, w.err);
+    if (mode == kColsStrided) TK_CHECK((run_gram_split<float, kColsStrided>(y, L, p, w, dev, s)));
+    else if (mode == kColsContig) TK_CHECK((run_gram_split<float, kColsContig>(y, L, p, w, dev, s)));
+    else TK_CHECK((run_gram_split<float, kColsGeneric>(y, L, p, w, dev, s)));
   }
-  TK_LAUNCHED();
   if (prof) prof->end((double)J * (J + 1) * (double)p.K, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
   k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(w.partials, p.nsplit, (int)J, w.gmax, f64,

@@ -33,6 +33,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: rows of 128 bytes (64 bf16 along K), 8-row atoms of 1 KB at
+// stride `sbo`, the 16-byte chunk c of row r stored at chunk c ^ (r % 8).  The
+// atoms must be 1024-byte aligned; `addr` may step through a row in 32-byte
+// K-steps.  The leading-byte offset is unused for this layout (set to 16).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t sbo) {
+  return smem_desc(addr, 16, sbo) | ((uint64_t)2 << 61);
+}
+
 // D (TMEM) = A B^T (+ D when accumulate != 0), A and B from shared-memory
 // descriptors, kind::f16 with instruction descriptor idesc.
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -137,6 +146,25 @@ __device__ __forceinline__ int exp_above(unsigned long long bits, bool is_f64) {
   const int ex = (int)(bits >> 23);
   return ex == 0 ? -4000 : ex - 127 + 1;
 }
+
+// Magnitude of an entry as far as its exponent goes: the high word of a
+// double (sign cleared), the bits of a float.  Ordered like the magnitude up
+// to ties within a binade, which is all the exponent table needs.
+__device__ __forceinline__ unsigned hi_mag(double v) {
+  return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7FFFFFFFu;
+}
+__device__ __forceinline__ unsigned hi_mag(float v) { return __float_as_uint(v) & 0x7FFFFFFFu; }
+// back to the bit pattern exp_above() reads
+__device__ __forceinline__ unsigned long long mag_pattern(unsigned m, bool is_f64) {
+  return is_f64 ? (unsigned long long)m << 32 : (unsigned long long)m;
+}
+
+// Exact float of an integer |n| < 2^22, without a conversion instruction.
+__device__ __forceinline__ float small_int_float(int n) {
+  return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
+}
+// round-to-nearest integer of |x| < 2^22 as a float
+__device__ __forceinline__ float round_float(float x) { return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f); }
 
 // Two floats that BF16 holds exactly (at most 8 significant bits), packed.
 __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {

@@ -141,7 +141,10 @@ def ttm_split_bound(y, L, J, B, u):
 
 
 @pytest.mark.parametrize("L,J,B,R", [(1, 128, 3000, 40), (40, 128, 33, 40), (7, 13, 5, 4), (1600, 48, 3, 20),
-                                     (1, 1, 9, 1), (3, 100, 77, 100), (64, 32, 50, 10), (1, 128, 4096 * 3 + 7, 128)])
+                                     (1, 1, 9, 1), (3, 100, 77, 100), (64, 32, 50, 10), (1, 128, 4096 * 3 + 7, 128),
+                                     # L == 1 kernel: one and two 64-wide parts, ragged J, many tiles per CTA
+                                     (1, 48, 700, 20), (1, 100, 5000, 33), (1, 128, 40000, 40), (1, 64, 3000, 64),
+                                     (1, 126, 1000, 48), (1, 2, 300, 1)])
 def test_ttm_split_bound(gpu_lib, L, J, B, R):
     import torch
 
@@ -155,22 +158,37 @@ def test_ttm_split_bound(gpu_lib, L, J, B, R):
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
 
 
-def test_ttm_split_exact_on_single_digit_inputs(gpu_lib):
+@pytest.mark.parametrize("L,J,B,R", [(1, 64, 500, 16), (1, 128, 777, 48), (8, 128, 100, 40)])
+def test_ttm_split_exact_on_single_digit_inputs(gpu_lib, L, J, B, R):
     """U and Y entries of one digit each: every output is an exact integer product sum."""
     import torch
 
     rng = np.random.default_rng(3)
-    L, J, B, R = 1, 64, 500, 16
     ui = rng.integers(-127, 128, size=(J, R))
     ui[0, :] = 127
     yi = rng.integers(-127, 128, size=(J, L * B))
     yi[0, :] = 127
     u = ui / 128.0
-    y = (yi / 128.0).ravel(order="F")
+    # y[l, j, b] = yi[j, l + L b] / 128, stored first index fastest
+    y = np.transpose((yi / 128.0).reshape((J, L, B), order="F"), (1, 0, 2)).ravel(order="F")
     z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
     exact = (ui.T.astype(np.int64) @ yi.astype(np.int64)).astype(np.float64) / 2 ** 14
-    got = z.reshape((R, L * B), order="F")
+    # yi's columns are the unfolding's columns (l, b); z is the (L, R, B) tensor
+    got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
     assert np.array_equal(got, exact)
+
+
+def test_ttm_split_f32_columns_contiguous(gpu_lib):
+    import torch
+
+    rng = np.random.default_rng(5)
+    L, J, B, R = 1, 96, 3001, 24
+    y = (rng.standard_normal(L * J * B) * np.exp(rng.standard_normal(L * J * B))).astype(np.float32)
+    u, _ = np.linalg.qr(rng.standard_normal((J, R)))
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    bound, ref = ttm_split_bound(y, L, J, B, u)
+    got = z.reshape((R, B), order="F")
+    assert np.all(np.abs(got - ref) <= bound)
 
 
 def test_ttm_split_f32_and_limits(gpu_lib):
