@@ -121,6 +121,11 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
 int64_t eig_workspace_doubles(int64_t J);
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof);
+// Mixed-precision eigensolver (float32 Jacobi + float64 refinement, J <= 128):
+// *verified = 1 when lam, V and d_info hold a result that passed the device
+// check; otherwise the caller runs the float64 Jacobi.  Synchronises s.
+int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
+                  cudaStream_t s, Prof *prof);
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

@@ -714,9 +714,22 @@ static bool dsm_cluster_ok(size_t dsmem) {
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof) {
   const int64_t m = J + (J & 1);
-  const char *ev = getenv("TUCKER_EIG_KERNEL");  // "dsm" | "l2m" | "l2" (default l2m)
+  // "mp" (default: mixed precision, J <= 128, float64 Jacobi if unverified) |
+  // "jacobi" (float64 Jacobi only) | "dsm" | "l2m" | "l2" (cluster variants)
+  const char *ev = getenv("TUCKER_EIG_KERNEL");
   const bool use_dsm = ev && !strcmp(ev, "dsm");
   const bool use_l2 = ev && !strcmp(ev, "l2");
+  const bool jacobi_only = ev && (use_dsm || use_l2 || !strcmp(ev, "jacobi") || !strcmp(ev, "l2m"));
+  if (!jacobi_only && J <= 128) {
+    int verified = 0;
+    TK_CHECK(launch_eig_mp(d_S, J, d_lam, d_V, d_info, &verified, s, prof));
+    if (verified) return TUCKER_OK;
+    const char *strict = getenv("TUCKER_EIG_MP_STRICT");  // tests: report instead of falling back
+    if (strict && strict[0] == '1') {
+      set_error("mixed-precision eigensolver failed its check (J = %lld)", (long long)J);
+      return TUCKER_ENOCONV;
+    }
+  }
   if (J > kOneCtaMaxJ && J <= kDsmMaxJ && !use_l2 && (use_dsm || d_ws)) {
     const size_t dsmem = use_dsm ? (size_t)((m * (m + 1) / 2 + m * m + 15) / 16) * sizeof(double) : 0;
     if (use_dsm ? dsm_cluster_ok<false>(dsmem) : dsm_cluster_ok<true>(0)) {

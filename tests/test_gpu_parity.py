@@ -108,6 +108,14 @@ def test_gram_deterministic(gpu_lib):
 # ---------------------------------------------------------------------------
 # a3: eigenpairs
 # ---------------------------------------------------------------------------
+@pytest.fixture(params=["mp", "jacobi"])
+def eig_path(request, monkeypatch):
+    """Both eigensolvers: mixed precision (strict: no silent fallback) and float64 Jacobi."""
+    monkeypatch.setenv("TUCKER_EIG_KERNEL", request.param)
+    monkeypatch.setenv("TUCKER_EIG_MP_STRICT", "1" if request.param == "mp" else "0")
+    return request.param
+
+
 def _check_eig(gpu_lib, s):
     import torch
 
@@ -135,14 +143,14 @@ def _check_eig(gpu_lib, s):
 
 
 @pytest.mark.parametrize("j", [1, 2, 3, 8, 17, 64, 127, 128, 129, 200])
-def test_eig_random_psd(gpu_lib, j):
+def test_eig_random_psd(gpu_lib, eig_path, j):
     rng = np.random.default_rng(j)
     a = rng.standard_normal((j, 2 * j + 3)) * (0.7 ** np.arange(j))[:, None]
     _check_eig(gpu_lib, a @ a.T)
 
 
 @pytest.mark.parametrize("j", [5, 48, 130])
-def test_eig_special(gpu_lib, j):
+def test_eig_special(gpu_lib, eig_path, j):
     import torch
 
     # identity: every eigenvalue equal, ties keep index order, V = I
@@ -158,6 +166,18 @@ def test_eig_special(gpu_lib, j):
     _check_eig(gpu_lib, a @ a.T)
     d = np.diag(np.linspace(-1, 1, j))
     _check_eig(gpu_lib, d + 1e-3 * (a @ a.T))
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_eig_mp_on_tucker_grams(gpu_lib, monkeypatch, seed):
+    """Graded spectra with a noise cluster (the Grams ST-HOSVD meets): the
+    mixed-precision solver must pass on its own, without the float64 fallback."""
+    monkeypatch.setenv("TUCKER_EIG_MP_STRICT", "1")
+    dims, ranks = (128, 64, 48, 16), (40, 40, 20, 10)
+    x = tucker_tensor_np(dims, ranks, seed=seed, decay=0.15, smooth=True, noise=1e-6)
+    t = oracle.as_tensor(x, dims)
+    for n in range(len(dims)):
+        _check_eig(gpu_lib, oracle.gram(t, n))
 
 
 def test_eig_large_dim(gpu_lib):
