@@ -56,23 +56,17 @@ constexpr double kClusterC = 64.0;
 constexpr int kRefineSteps = 3;
 constexpr int kPolishSteps = 2;
 
-__device__ __forceinline__ int pidx32(int i, int j) {
-  if (i > j) {
-    const int t = i;
-    i = j;
-    j = t;
-  }
-  return j * (j + 1) / 2 + i;
-}
-
 // ---------------------------------------------------------------------------
-// float32 parallel-order cyclic Jacobi on A / max|A| (one CTA).  The packed
-// upper triangle of S and V live in shared memory; each step applies the
-// m/2 disjoint rotations of the round-robin tournament (every pair meets
-// once in m - 1 steps).  A rotation is taken when |s_pq| exceeds 2^-23 times
-// the largest diagonal magnitude at the start of the sweep (an absolute
-// criterion: the float64 refinement that follows needs no more).  Writes
-// X = V (float64, unsorted columns) and the number of sweeps.
+// float32 parallel-order cyclic Jacobi on A / max|A| (one CTA).  S (full,
+// row-major, kept symmetric) and V (column-major) live in shared memory,
+// padded with zero rows and columns to m = n rounded up to a multiple of 4.
+// Each step applies the m/2 disjoint rotations of the round-robin tournament
+// (every pair meets once in m - 1 steps): S is updated in 2 x 2 blocks
+// {p_P, q_P} x {p_Q, q_Q} as R_P^T B R_Q (one block per pair of pairs P <= Q,
+// mirrored), V by 16-byte column vectors.  A rotation is taken when |s_pq|
+// exceeds 2^-23 times the largest diagonal magnitude at the start of the
+// sweep (an absolute criterion: the float64 refinement that follows needs no
+// more).  Writes X = V (float64, unsorted columns) and the number of sweeps.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restrict__ A, int lda, int n,
                                                            double *__restrict__ X, int ldx, int *__restrict__ sweeps) {
@@ -82,16 +76,15 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
   __shared__ float red[kJ32Threads / 32];
   __shared__ float scale_s, tol_s;
   __shared__ int rotated;
-  const int m = n + (n & 1), np = m / 2;
-  const int packed = m * (m + 1) / 2;
-  float *Sp = sm32;
-  float *V = Sp + packed;
+  const int m = (n + 3) & ~3, np = m / 2;
+  const int ld = m + 1;    // odd row stride: S[i ld + j] and its mirror S[j ld + i] fall in different banks
+  float *S = sm32;         // m x ld
+  float *V = S + ((m * ld + 3) & ~3);  // m x m, column j at V + j m (16-byte aligned)
   short *blkP = reinterpret_cast<short *>(V + m * m);
-  short *blkQ = blkP + np * (np + 1) / 2;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = np * (np + 1) / 2;
+  short *blkQ = blkP + nblk;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
 
-  // scale
   float mx = 0.f;
   for (int e = tid; e < n * n; e += nt) mx = fmaxf(mx, (float)fabs(A[(e % n) + (int64_t)lda * (e / n)]));
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -99,14 +92,15 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
   __syncthreads();
   if (tid == 0) {
     float v = 0.f;
-    for (int w = 0; w < nt / 32; ++w) v = fmaxf(v, red[w]);
+    for (int w = 0; w < nwarps; ++w) v = fmaxf(v, red[w]);
     scale_s = v;
   }
   __syncthreads();
   const double inv = scale_s > 0.f ? 1.0 / (double)scale_s : 0.0;
   for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    if (i <= j) Sp[pidx32(i, j)] = (j < n) ? (float)(A[i + (int64_t)lda * j] * inv) : 0.f;
+    const int i = e / m, j = e - (e / m) * m;
+    const int lo = min(i, j), hi = max(i, j);  // read the upper triangle, mirror it
+    S[i * ld + j] = (hi < n) ? (float)(A[lo + (int64_t)lda * hi] * inv) : 0.f;
     V[e] = (i == j) ? 1.f : 0.f;
   }
   for (int e = tid; e < nblk; e += nt) {  // pair-block table: e -> (P <= Q)
@@ -120,11 +114,11 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
 
   int sweep = 0;
   for (; sweep < kJ32MaxSweeps; ++sweep) {
-    if (tid < 32) {
+    if (warp == 0) {
       float d = 0.f;
-      for (int i = tid; i < m; i += 32) d = fmaxf(d, fabsf(Sp[pidx32(i, i)]));
+      for (int i = lane; i < m; i += 32) d = fmaxf(d, fabsf(S[i * ld + i]));
       for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
-      if (tid == 0) {
+      if (lane == 0) {
         tol_s = FLT_EPSILON * fmaxf(d, FLT_MIN);
         rotated = 0;
       }
@@ -132,7 +126,8 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
     __syncthreads();
     const float tol = tol_s;
     for (int step = 0; step < m - 1; ++step) {
-      for (int t = tid; t < np; t += nt) {
+      if (tid < np) {
+        const int t = tid;
         int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
         int q = ((m - 2 - t + step) % (m - 1)) + 1;
         if (p > q) {
@@ -140,19 +135,19 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
           p = q;
           q = tmp;
         }
-        float c = 1.f, s = 0.f;
-        const float b = Sp[pidx32(p, q)];
+        float c = 1.f, sv = 0.f;
+        const float b = S[p * ld + q];
         if (fabsf(b) > tol) {
-          const float a = Sp[pidx32(p, p)], d = Sp[pidx32(q, q)];
+          const float a = S[p * ld + p], d = S[q * ld + q];
           const float tau = (d - a) / (2.f * b);
           const float at = fabsf(tau);
           const float tt = at > 1e18f ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
           c = rsqrtf(1.f + tt * tt);
-          s = tt * c;
-          if (s != 0.f) rotated = 1;
+          sv = tt * c;
+          if (sv != 0.f) rotated = 1;
         }
         cs[t] = c;
-        sn[t] = s;
+        sn[t] = sv;
         pp[t] = p;
         qq[t] = q;
       }
@@ -160,40 +155,42 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
       for (int e = tid; e < nblk; e += nt) {
         const int P = blkP[e], Q = blkQ[e];
         const float s1 = sn[P], s2 = sn[Q];
+        if (s1 == 0.f && s2 == 0.f) continue;
         const int p1 = pp[P], q1 = qq[P];
         if (P == Q) {
-          if (s1 != 0.f) {
-            const float t1 = s1 / cs[P];
-            const int ipq = pidx32(p1, q1), ipp = pidx32(p1, p1), iqq = pidx32(q1, q1);
-            const float b = Sp[ipq];
-            Sp[ipp] = Sp[ipp] - t1 * b;
-            Sp[iqq] = Sp[iqq] + t1 * b;
-            Sp[ipq] = 0.f;
-          }
+          const float t1 = s1 / cs[P];
+          const float b = S[p1 * ld + q1];
+          S[p1 * ld + p1] -= t1 * b;
+          S[q1 * ld + q1] += t1 * b;
+          S[p1 * ld + q1] = 0.f;
+          S[q1 * ld + p1] = 0.f;
           continue;
         }
-        if (s1 == 0.f && s2 == 0.f) continue;
         const float c1 = cs[P], c2 = cs[Q];
         const int p2 = pp[Q], q2 = qq[Q];
-        const int i11 = pidx32(p1, p2), i12 = pidx32(p1, q2), i21 = pidx32(q1, p2), i22 = pidx32(q1, q2);
-        const float x11 = Sp[i11], x12 = Sp[i12], x21 = Sp[i21], x22 = Sp[i22];
+        const float x11 = S[p1 * ld + p2], x12 = S[p1 * ld + q2], x21 = S[q1 * ld + p2], x22 = S[q1 * ld + q2];
         const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
         const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-        Sp[i11] = y11 * c2 - y12 * s2;
-        Sp[i12] = y11 * s2 + y12 * c2;
-        Sp[i21] = y21 * c2 - y22 * s2;
-        Sp[i22] = y21 * s2 + y22 * c2;
+        const float z11 = y11 * c2 - y12 * s2, z12 = y11 * s2 + y12 * c2;
+        const float z21 = y21 * c2 - y22 * s2, z22 = y21 * s2 + y22 * c2;
+        S[p1 * ld + p2] = z11;
+        S[p2 * ld + p1] = z11;
+        S[p1 * ld + q2] = z12;
+        S[q2 * ld + p1] = z12;
+        S[q1 * ld + p2] = z21;
+        S[p2 * ld + q1] = z21;
+        S[q1 * ld + q2] = z22;
+        S[q2 * ld + q1] = z22;
       }
-      for (int e = tid; e < np * m; e += nt) {
-        const int t = e / m, i = e - t * m;
-        const float s = sn[t];
-        if (s == 0.f) continue;
+      for (int t = warp; t < np; t += nwarps) {
+        const float sv = sn[t];
+        if (sv == 0.f || 4 * lane >= m) continue;
         const float c = cs[t];
-        float *vp = V + pp[t] * m + i;
-        float *vq = V + qq[t] * m + i;
-        const float a = *vp, b = *vq;
-        *vp = c * a - s * b;
-        *vq = s * a + c * b;
+        float4 *vp = reinterpret_cast<float4 *>(V + pp[t] * m) + lane;
+        float4 *vq = reinterpret_cast<float4 *>(V + qq[t] * m) + lane;
+        const float4 a = *vp, b = *vq;
+        *vp = make_float4(c * a.x - sv * b.x, c * a.y - sv * b.y, c * a.z - sv * b.z, c * a.w - sv * b.w);
+        *vq = make_float4(sv * a.x + c * b.x, sv * a.y + c * b.y, sv * a.z + c * b.z, sv * a.w + c * b.w);
       }
       __syncthreads();
     }
@@ -209,6 +206,11 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
     X[i + (int64_t)ldx * j] = (double)V[j * m + i];
   }
   if (tid == 0 && sweeps) *sweeps = sweep;
+}
+
+size_t jacobi32_smem(int n) {
+  const int m = (n + 3) & ~3, np = m / 2;
+  return (size_t)(((m * (m + 1) + 3) & ~3) + m * m) * sizeof(float) + (size_t)np * (np + 1) * sizeof(short) + 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -245,12 +247,15 @@ __global__ void __launch_bounds__(kGT *kGT) k_dgemm_small(int M, int N, int K, c
 
 // ---------------------------------------------------------------------------
 // Refinement step kernels.  G = X^T [A X | X] (m x 2m): S = G[:, :m],
-// X^T X = G[:, m:].  Everything here is one CTA (m <= 128).
+// X^T X = G[:, m:].  The m^2-sized passes run on many CTAs (the float64 pipe
+// of one SM would take tens of microseconds); the partition is one CTA.
 // ---------------------------------------------------------------------------
+constexpr int kStatBlocks = 64;
+constexpr int kStatThreads = 256;
+
 struct LevelInfo {
   double norm_a;   // ||A||_F of the level's matrix
   int nclusters;
-  int degenerate;  // A is a multiple of I up to the noise floor
   int start[kMpMaxJ + 1];
 };
 
@@ -265,97 +270,125 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;
 }
 
-// First step of a level: eigenvalue approximations, clusters (sorted order),
-// the permuted X (Xp = X P) and E in the permuted basis.  noise < 0 stands
-// for ||A||_F (the top level).
-__global__ void __launch_bounds__(1024) k_oa_partition(const double *__restrict__ G, int m, const double *__restrict__ A,
-                                                       int lda, const double *__restrict__ X, int ldx, double noise,
-                                                       double *__restrict__ Xp, double *__restrict__ E,
-                                                       int *__restrict__ label, LevelInfo *__restrict__ info) {
-  __shared__ double lam[kMpMaxJ];
-  __shared__ int perm[kMpMaxJ], lab[kMpMaxJ];
-  __shared__ double red[32];
-  __shared__ double delta_s;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int ldg = m;
-  const double *S = G;
-  const double *P = G + (int64_t)m * m;  // X^T X
-  double off2 = 0.0, r2 = 0.0, a2 = 0.0, dev2 = 0.0;
-  double tr = 0.0;
-  for (int i = tid; i < m; i += nt) tr += A[i + (int64_t)lda * i];
-  tr = block_sum(tr, red);
-  const double mu = tr / m;
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    const double s = S[i + ldg * j];
-    const double r = (i == j ? 1.0 : 0.0) - P[i + ldg * j];
-    if (i != j) off2 += s * s;
-    r2 += r * r;
+// Per-CTA partial sums: part[3 b + 0] = ||off(S)||^2, [1] = ||I - X^T X||^2,
+// [2] = ||A||^2 (with G == nullptr: [0] = ||A - mu I||^2, mu = tr(A) / m).
+__global__ void __launch_bounds__(kStatThreads) k_oa_stats(const double *__restrict__ G, int m,
+                                                           const double *__restrict__ A, int lda,
+                                                           double *__restrict__ part) {
+  __shared__ double red[kStatThreads / 32];
+  __shared__ double mu_s;
+  if (!G) {
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < m; i += 32) t += A[i + (int64_t)lda * i];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) mu_s = t / m;
+    }
+    __syncthreads();
+  }
+  const double mu = G ? 0.0 : mu_s;
+  double off2 = 0.0, r2 = 0.0, a2 = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int j = e / m, i = e - j * m;
     const double a = A[i + (int64_t)lda * j];
     a2 += a * a;
-    const double d = a - (i == j ? mu : 0.0);
-    dev2 += d * d;
+    if (!G) {
+      const double d = a - (i == j ? mu : 0.0);
+      off2 += d * d;
+      continue;
+    }
+    const double sv = G[e];
+    const double r = (i == j ? 1.0 : 0.0) - G[(int64_t)m * m + e];
+    if (i != j) off2 += sv * sv;
+    r2 += r * r;
   }
   off2 = block_sum(off2, red);
   r2 = block_sum(r2, red);
   a2 = block_sum(a2, red);
-  dev2 = block_sum(dev2, red);
-  for (int i = tid; i < m; i += nt) lam[i] = S[i + ldg * i] / P[i + ldg * i];  // s_ii / (1 - r_ii)
-  if (noise < 0.0) noise = sqrt(a2);
-  if (tid == 0) delta_s = kClusterC * (sqrt(off2) + sqrt(a2) * sqrt(r2) + m * kU * noise);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = off2;
+    part[3 * blockIdx.x + 1] = r2;
+    part[3 * blockIdx.x + 2] = a2;
+  }
+}
+
+// A total order on doubles as unsigned integers (finite values and +-0).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// First step of a level: eigenvalue approximations l_i = s_ii / (X^T X)_ii,
+// sorted descending (ties by index) into perm, and clusters of the sorted
+// order (label per position, starts in info).  noise < 0 stands for ||A||_F
+// (the top level).
+__global__ void __launch_bounds__(256) k_oa_partition(const double *__restrict__ G, int m,
+                                                      const double *__restrict__ part, double noise,
+                                                      int *__restrict__ perm_out, int *__restrict__ label,
+                                                      LevelInfo *__restrict__ info) {
+  __shared__ double lam[kMpMaxJ];
+  __shared__ unsigned long long key[kMpMaxJ];
+  __shared__ int perm[kMpMaxJ];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m; i += nt) {
+    lam[i] = G[i + (int64_t)m * i] / G[(int64_t)m * m + i + (int64_t)m * i];
+    key[i] = order_key(lam[i]);
+  }
   __syncthreads();
-  // descending order, ties by index
   for (int i = tid; i < m; i += nt) {
     int rank = 0;
-    for (int j = 0; j < m; ++j) rank += (lam[j] > lam[i]) || (lam[j] == lam[i] && j < i);
+    const unsigned long long ki = key[i];
+    for (int j = 0; j < m; ++j) rank += (key[j] > ki) || (key[j] == ki && j < i);
     perm[rank] = i;
   }
   __syncthreads();
   if (tid == 0) {
-    const double delta = delta_s;
+    double off2 = 0.0, r2 = 0.0, a2 = 0.0;
+    for (int b = 0; b < kStatBlocks; ++b) {  // fixed order
+      off2 += part[3 * b];
+      r2 += part[3 * b + 1];
+      a2 += part[3 * b + 2];
+    }
+    if (noise < 0.0) noise = sqrt(a2);
+    const double delta = kClusterC * (sqrt(off2) + sqrt(a2) * sqrt(r2) + m * kU * noise);
     int k = 0;
     info->start[0] = 0;
-    lab[0] = 0;
+    label[0] = 0;
     for (int a = 1; a < m; ++a) {
       if (lam[perm[a - 1]] - lam[perm[a]] > delta) info->start[++k] = a;
-      lab[a] = k;
+      label[a] = k;
     }
     info->nclusters = k + 1;
-    info->norm_a = sqrt(a2);
     info->start[k + 1] = m;
-    info->degenerate = sqrt(dev2) <= kClusterC * m * kU * noise;
+    info->norm_a = sqrt(a2);
   }
-  __syncthreads();
-  for (int a = tid; a < m; a += nt) label[a] = lab[a];
-  for (int e = tid; e < m * m; e += nt) {
-    const int a = e % m, b = e / m;
-    Xp[a + (int64_t)ldx * b] = X[a + (int64_t)ldx * perm[b]];
-    const int i = perm[a], j = perm[b];
-    const double r = (i == j ? 1.0 : 0.0) - P[i + ldg * j];
-    double v;
-    if (a == b || lab[a] == lab[b]) v = 0.5 * r;
-    else v = (S[i + ldg * j] + lam[j] * r) / (lam[j] - lam[i]);
-    E[a + (int64_t)m * b] = v;
-  }
+  for (int a = tid; a < m; a += nt) perm_out[a] = perm[a];
 }
 
-// Later steps: E from G with the clusters fixed.
-__global__ void __launch_bounds__(1024) k_oa_update(const double *__restrict__ G, int m, const int *__restrict__ label,
-                                                    double *__restrict__ E) {
+// E of a refinement step, in the basis permuted by perm (nullptr: identity),
+// with the clusters `label` of the permuted positions; with Xp != nullptr
+// also Xp = X perm.
+__global__ void __launch_bounds__(kStatThreads) k_oa_E(const double *__restrict__ G, int m,
+                                                       const int *__restrict__ perm, const int *__restrict__ label,
+                                                       const double *__restrict__ X, double *__restrict__ Xp,
+                                                       double *__restrict__ E) {
   __shared__ double lam[kMpMaxJ];
-  __shared__ int lab[kMpMaxJ];
+  __shared__ int lab[kMpMaxJ], pm[kMpMaxJ];
   const double *S = G;
   const double *P = G + (int64_t)m * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     lam[i] = S[i + (int64_t)m * i] / P[i + (int64_t)m * i];
     lab[i] = label[i];
+    pm[i] = perm ? perm[i] : i;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e % m, j = e / m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int b = e / m, a = e - b * m;
+    const int i = pm[a], j = pm[b];
+    if (Xp) Xp[e] = X[a + (int64_t)m * j];
     const double r = (i == j ? 1.0 : 0.0) - P[i + (int64_t)m * j];
     double v;
-    if (i == j || lab[i] == lab[j]) v = 0.5 * r;
+    if (a == b || lab[a] == lab[b]) v = 0.5 * r;
     else v = (S[i + (int64_t)m * j] + lam[j] * r) / (lam[j] - lam[i]);
     E[e] = v;
   }
@@ -453,14 +486,35 @@ struct MpWork {
   double *e(int d) const { return base + (size_t)d * 9 * J * J + (size_t)6 * J * J; }
   double *c(int d) const { return base + (size_t)d * 9 * J * J + (size_t)7 * J * J; }
   double *t(int d) const { return base + (size_t)d * 9 * J * J + (size_t)8 * J * J; }
-  int *labels = nullptr;      // per depth, J ints
-  LevelInfo *info = nullptr;  // per depth (device)
+  double *part = nullptr;     // 3 kStatBlocks partial sums
   double *check = nullptr;    // 4 doubles
   int *sweeps = nullptr;      // 1 int
+  int *labels = nullptr;      // per depth, J ints
+  int *perms = nullptr;       // per depth, J ints
+  LevelInfo *info = nullptr;  // per depth (device)
+  static size_t bytes(int J) {
+    return ((size_t)kMaxDepth * 9 * J * J + 3 * kStatBlocks + 8) * sizeof(double) +
+           (size_t)2 * kMaxDepth * J * sizeof(int) + (size_t)kMaxDepth * sizeof(LevelInfo) + 64;
+  }
+  void carve(void *mem, int J_) {
+    J = J_;
+    base = static_cast<double *>(mem);
+    part = base + (size_t)kMaxDepth * 9 * J * J;
+    check = part + 3 * kStatBlocks;
+    sweeps = reinterpret_cast<int *>(check + 4);
+    labels = reinterpret_cast<int *>(check + 8);
+    perms = labels + kMaxDepth * J;
+    info = reinterpret_cast<LevelInfo *>((reinterpret_cast<uintptr_t>(perms + kMaxDepth * J) + 15) &
+                                         ~static_cast<uintptr_t>(15));
+  }
 };
 
 int gemm(int M, int N, int K, const double *A, int lda, int transA, const double *B, int ldb, const double *D, int ldd,
          double *C, int ldc, cudaStream_t s) {
+  if (K > 2 * kMpMaxJ) {
+    set_error("small GEMM: K = %d exceeds %d", K, 2 * kMpMaxJ);
+    return TUCKER_EINVAL;
+  }
   dim3 grid((M + kGT - 1) / kGT, (N + kGT - 1) / kGT);
   k_dgemm_small<<<grid, kGT * kGT, 0, s>>>(M, N, K, A, lda, transA, B, ldb, D, ldd, C, ldc);
   TK_LAUNCHED();
@@ -475,22 +529,41 @@ int products(const double *A, int lda, int m, double *tx, double *G, cudaStream_
   return TUCKER_OK;
 }
 
-// One level: eigenvectors of A (m x m, lda) into out (m x m, ld m).
+// ||A - mu I||_F (mu = tr(A) / m) and ||A||_F, on the host.
+int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStream_t s, double *dev, double *norm) {
+  k_oa_stats<<<kStatBlocks, kStatThreads, 0, s>>>(nullptr, m, A, lda, w.part);
+  TK_LAUNCHED();
+  double h[3 * kStatBlocks];
+  TK_CUDA(cudaMemcpyAsync(h, w.part, sizeof h, cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  double d2 = 0.0, a2 = 0.0;
+  for (int b = 0; b < kStatBlocks; ++b) {
+    d2 += h[3 * b];
+    a2 += h[3 * b + 2];
+  }
+  *dev = std::sqrt(d2);
+  if (norm) *norm = std::sqrt(a2);
+  return TUCKER_OK;
+}
+
+// One level: eigenvectors of A (m x m, lda) into out (m x m, ld m).  noise is
+// ||A||_F of the top problem: the float64 noise floor of every level.
 int mp_level(const double *A, int lda, int m, double noise, int depth, const MpWork &w, double *out, cudaStream_t s) {
   double *tx0 = w.tx(depth, 0), *tx1 = w.tx(depth, 1);
   double *G = w.g(depth), *E = w.e(depth);
-  int *label = w.labels + depth * w.J;
+  int *label = w.labels + depth * w.J, *perm = w.perms + depth * w.J;
   LevelInfo *dinfo = w.info + depth;
-  const size_t smem32 = (size_t)((m + 1) / 2 * 2) * ((m + 1) / 2 * 2 + 1) / 2 * sizeof(float) +
-                        (size_t)((m + 1) / 2 * 2) * ((m + 1) / 2 * 2) * sizeof(float) +
-                        (size_t)((m + 1) / 2) * ((m + 1) / 2 + 1) * sizeof(short) + 16;
+  const size_t smem32 = jacobi32_smem(m);
   TK_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
   k_jacobi32<<<1, kJ32Threads, smem32, s>>>(A, lda, m, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr);
   TK_LAUNCHED();
   // first refinement step: clusters and the permuted basis
   TK_CHECK(products(A, lda, m, tx0, G, s));
-  k_oa_partition<<<1, 1024, 0, s>>>(G, m, A, lda, tx0 + (size_t)m * m, m, noise, tx1 + (size_t)m * m, E, label,
-                                    dinfo);
+  k_oa_stats<<<kStatBlocks, kStatThreads, 0, s>>>(G, m, A, lda, w.part);
+  TK_LAUNCHED();
+  k_oa_partition<<<1, 256, 0, s>>>(G, m, w.part, noise, perm, label, dinfo);
+  TK_LAUNCHED();
+  k_oa_E<<<kStatBlocks, kStatThreads, 0, s>>>(G, m, perm, label, tx0 + (size_t)m * m, tx1 + (size_t)m * m, E);
   TK_LAUNCHED();
   double *cur = tx1, *nxt = tx0;
   // X <- X + X E
@@ -502,7 +575,7 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   };
   auto refine = [&]() -> int {
     TK_CHECK(products(A, lda, m, cur, G, s));
-    k_oa_update<<<1, 1024, 0, s>>>(G, m, label, E);
+    k_oa_E<<<kStatBlocks, kStatThreads, 0, s>>>(G, m, nullptr, label, nullptr, nullptr, E);
     TK_LAUNCHED();
     return apply();
   };
@@ -511,21 +584,18 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   LevelInfo h;
   TK_CUDA(cudaMemcpyAsync(&h, dinfo, sizeof h, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
-  if (noise < 0.0) noise = h.norm_a;  // the top level fixes the noise floor for its descendants
-  if (h.degenerate) {
-    k_set_identity<<<(m * m + 255) / 256, 256, 0, s>>>(out, m, m);
-    TK_LAUNCHED();
-    return TUCKER_OK;
-  }
   double *X = cur + (size_t)m * m;
   for (int k = 0; k < h.nclusters; ++k) {
     const int c0 = h.start[k], mc = h.start[k + 1] - c0;
     if (mc < 2 || depth + 1 >= kMaxDepth) continue;
-    // C = X_c^T A X_c
+    // C = X_c^T A X_c; a multiple of I up to the noise floor needs no rotation
     double *T = w.t(depth), *C = w.c(depth);
     TK_CHECK(gemm(m, mc, m, A, lda, 0, X + (size_t)m * c0, m, nullptr, 0, T, m, s));
     TK_CHECK(gemm(mc, mc, m, X + (size_t)m * c0, m, 1, T, m, nullptr, 0, C, mc, s));
-    double *Q = w.e(depth + 1);  // the child's E is free until it runs; Q is copied out first
+    double dev = 0.0;
+    TK_CHECK(scalar_deviation(C, mc, mc, w, s, &dev, nullptr));
+    if (dev <= kClusterC * mc * kU * noise) continue;
+    double *Q = w.e(depth + 1);  // the child's E is free once it has returned
     double *Qc = w.t(depth + 1);
     TK_CHECK(mp_level(C, mc, mc, noise, depth + 1, w, Qc, s));
     // X_c <- X_c Q
@@ -548,28 +618,28 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   *verified = 0;
   if (J < 1 || J > kMpMaxJ) return TUCKER_OK;
   const int m = (int)J;
-  MpWork w;
-  w.J = m;
-  const size_t doubles = (size_t)kMaxDepth * 9 * m * m + 8;
-  const size_t bytes = doubles * sizeof(double) + (size_t)kMaxDepth * m * sizeof(int) +
-                       (size_t)kMaxDepth * sizeof(LevelInfo) + 64;
   void *mem = nullptr;
-  TK_CUDA(cudaMallocAsync(&mem, bytes, s));
+  TK_CUDA(cudaMallocAsync(&mem, MpWork::bytes(m), s));
   struct Free {
     void *p;
     cudaStream_t s;
     ~Free() { cudaFreeAsync(p, s); }
   } guard{mem, s};
-  w.base = static_cast<double *>(mem);
-  w.check = w.base + (size_t)kMaxDepth * 9 * m * m;
-  w.sweeps = reinterpret_cast<int *>(w.check + 4);
-  w.labels = reinterpret_cast<int *>(w.check + 8);
-  w.info = reinterpret_cast<LevelInfo *>(
-      (reinterpret_cast<uintptr_t>(w.labels + kMaxDepth * m) + 15) & ~static_cast<uintptr_t>(15));
+  MpWork w;
+  w.carve(mem, m);
 
   if (prof) prof->begin(TUCKER_PHASE_EIG);
+  double dev = 0.0, noise = 0.0;
+  TK_CHECK(scalar_deviation(d_S, m, m, w, s, &dev, &noise));
   double *X = w.c(kMaxDepth - 1);  // never a cluster block: the deepest level takes no clusters
-  TK_CHECK(mp_level(d_S, m, m, -1.0, 0, w, X, s));
+  int sw = 0;
+  TK_CUDA(cudaMemsetAsync(w.sweeps, 0, sizeof(int), s));
+  if (dev <= kClusterC * m * kU * noise) {
+    k_set_identity<<<(m * m + 255) / 256, 256, 0, s>>>(X, m, m);  // a multiple of I: V = I
+    TK_LAUNCHED();
+  } else {
+    TK_CHECK(mp_level(d_S, m, m, noise, 0, w, X, s));
+  }
   // final products, Rayleigh quotients, verification, output
   double *tx0 = w.tx(0, 0);
   k_copy_cols<<<(m * m + 255) / 256, 256, 0, s>>>(X, m, tx0 + (size_t)m * m, m, m, m);
@@ -578,7 +648,6 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   k_mp_finalize<<<1, 1024, 0, s>>>(w.g(0), tx0, tx0 + (size_t)m * m, m, d_lam, d_V, w.check);
   TK_LAUNCHED();
   double chk[3];
-  int sw = 0;
   TK_CUDA(cudaMemcpyAsync(chk, w.check, sizeof chk, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&sw, w.sweeps, sizeof sw, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
