@@ -39,18 +39,26 @@ WORKLOAD = "combustion5"
 # Float64 pipe peak of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu DRAM traffic, keyed by kernel and the hash of the kernel source it was
-# captured with (profiles/k_gram_partial_combustion5_t2.md): measured
+# captured with (profiles/*_combustion5_t2.md): measured
 # dram__bytes_read.sum + dram__bytes_write.sum of the mode-1 launch on the
 # 128x128x128x48x2 case divided by that launch's algorithmic bytes.  The
 # reported traffic is this ratio times the per-launch algorithmic bytes of the
 # timed run; it is dropped as soon as the kernel source changes.
 TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9,
-                                                   "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"}}
+                                                   "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
+           # profiles/split_kernels_combustion5_t2.md (mode-1 launches of the same case)
+           ("k_rowgroup_exp", "3dbcab1d57d68fd0"): {"ratio": 1.6158e9 / 1.6106e9,
+                                                    "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
+           ("k_gram_split", "3dbcab1d57d68fd0"): {"ratio": 1.6169e9 / 1.6106e9,
+                                                  "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
+           ("k_ttm_split_l1", "21fcc489cd902142"): {"ratio": 2.0865e9 / 2.1140e9,
+                                                    "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"}}
 HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
 
-KERNEL_FILES = {"k_gram_partial": "kernels_f64.cu", "k_ttm": "kernels_f64.cu", "k_gram_split": "gram_split.cu",
-                "k_ttm_split": "ttm_split.cu"}
+KERNEL_FILES = {"k_gram_partial": "kernels_f64.cu", "k_ttm": "kernels_f64.cu", "k_sumsq": "kernels_f64.cu",
+                "k_gram_split": "gram_split.cu", "k_rowgroup_exp": "gram_split.cu", "k_ttm_split_l1": "ttm_split.cu",
+                "k_ttm_split2": "ttm_split.cu", "k_jacobi32": "eig_mp.cu"}
 
 
 def kernel_source_hash(kernel):
@@ -270,41 +278,74 @@ def time_method(tucker, x, dims, eps, precision, steps, warmup, world, local, st
             "clocks": sampler.summary()}
 
 
-def roofline_of(t, steps, precision):
-    """Roofline object for the Gram or TTM phase, whichever takes more of the step.
+# Kernel of each profiled phase, its bound and the peak it is measured against.
+PHASE_KERNELS = {
+    "split": {
+        "norm": ("k_sumsq", "sum of squares of X", "hbm"),
+        "scale": ("k_rowgroup_exp", "per-(row, 512-column group) exponent table", "hbm"),
+        "gram": ("k_gram_split", "tcgen05 BF16 digit Gram, exact FP32 accumulation", "hbm"),
+        "ttm_l1": ("k_ttm_split_l1", "tcgen05 BF16 digit TTM, contiguous columns (L = 1)", "hbm"),
+        "ttm": ("k_ttm_split2", "tcgen05 BF16 digit TTM, strided columns (L > 1)", "hbm"),
+        "eig": ("k_jacobi32", "mixed-precision eigensolver (float32 Jacobi + float64 refinement)", "alu"),
+    },
+    "fp64": {
+        "norm": ("k_sumsq", "sum of squares of X", "hbm"),
+        "gram": ("k_gram_partial", "float64 split-K symmetric Gram", "alu"),
+        "ttm": ("k_ttm", "float64 mode-n product", "alu"),
+        "eig": ("k_jacobi32", "mixed-precision eigensolver (float32 Jacobi + float64 refinement)", "alu"),
+    },
+}
 
-    The float64 kernels are bound by the float64 pipe ("alu"); the
-    tensor-core kernels of the split-precision path move far fewer flops per
-    byte than the BF16 ridge, so HBM bounds them ("hbm", algorithmic bytes:
-    input read once plus output written once).
-    """
-    prof = t["prof"]
-    phase = max(("gram", "ttm"), key=lambda k: prof[k]["ms"])
+
+def phase_roofline(prof, phase, steps, path):
+    kernel, what, bound = PHASE_KERNELS[path][phase]
     ph = prof[phase]
-    per_ms = ph["ms"] / max(ph["launches"], 1)
-    per_flops = ph["flops"] / max(ph["launches"], 1)
-    per_bytes = ph["bytes"] / max(ph["launches"], 1)
-    if precision != "fp64":
+    n = max(ph["launches"], 1)
+    per_ms, per_flops, per_bytes = ph["ms"] / n, ph["flops"] / n, ph["bytes"] / n
+    if bound == "hbm":
         achieved = per_bytes / (per_ms / 1e3) / 1e9
-        name = ("k_gram_split (tcgen05 BF16 digit Gram, exact FP32 accumulation)" if phase == "gram" else
-                "k_ttm_split (tcgen05 BF16 digit TTM, exact FP32 accumulation)")
-        r = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s",
-             "frac": round(achieved / HBM_PEAK_GBS, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        r = {"kernel": f"{kernel} ({what})", "bound": "hbm", "achieved": round(achieved, 2), "peak": HBM_PEAK_GBS,
+             "unit": "GB/s", "frac": round(achieved / HBM_PEAK_GBS, 4),
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     else:
         achieved = per_flops / (per_ms / 1e3) / 1e12
-        name = "k_gram_partial (float64 split-K symmetric Gram)" if phase == "gram" else \
-            "k_ttm (float64 mode-n product)"
-        r = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-             "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+        r = {"kernel": f"{kernel} ({what})", "bound": "alu", "achieved": round(achieved, 5),
+             "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 5),
              "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 "
                             "1.25 TFLOP/s; measured DFMA loop 1.193 TFLOP/s)"}
-    tr = TRAFFIC.get((r["kernel"].split()[0], kernel_source_hash(r["kernel"].split()[0])))
+        if phase == "eig":
+            r["flops_source"] = "the paper's count of the eigenvector step, 10/3 J^3 per mode (Sec. 4.4)"
+    tr = TRAFFIC.get((kernel, kernel_source_hash(kernel))) if kernel in KERNEL_FILES else None
     r["traffic"] = round(tr["ratio"] * per_bytes) if tr else None
     r["traffic_source"] = (f"ncu DRAM/algorithmic ratio of {tr['captured']}, scaled to the timed launches"
                            if tr else "no ncu capture of this kernel version")
     r.update({"phase": phase, "launches_per_step": ph["launches"] / steps, "per_launch_ms": round(per_ms, 4),
-              "per_launch_algorithmic_flops": per_flops, "per_launch_algorithmic_bytes": round(per_bytes)})
+              "per_launch_algorithmic_flops": per_flops, "per_launch_algorithmic_bytes": round(per_bytes),
+              "share_of_step": None})
     return r
+
+
+def roofline_of(t, steps, precision):
+    """Roofline of the phase that takes the most time, plus one per profiled phase.
+
+    Split precision: the tensor-core and streaming kernels move far fewer
+    flops per byte than the BF16 ridge, so HBM bounds them (algorithmic
+    bytes: input read once plus output written once); the eigensolver is
+    measured against the float64 pipe with the paper's flop count.  Plain
+    float64: the Gram and TTM are bound by the float64 pipe.
+    """
+    prof = t["prof"]
+    path = "fp64" if precision == "fp64" else "split"
+    total = sum(prof[k]["ms"] for k in prof)
+    rows = []
+    for phase in PHASE_KERNELS[path]:
+        if prof[phase]["launches"] == 0:
+            continue
+        r = phase_roofline(prof, phase, steps, path)
+        r["share_of_step"] = round(prof[phase]["ms"] / total, 4) if total else None
+        rows.append(r)
+    rows.sort(key=lambda r: -prof[r["phase"]]["ms"])
+    return rows[0], rows
 
 
 def main():
@@ -371,8 +412,9 @@ def main():
         "equal_rel_error": equal,
         "phase_share": {k: round(v["ms"] / args.steps / ms, 4) for k, v in t["prof"].items()},
         "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in t["prof"].items()},
-        "roofline": roofline_of(t, args.steps, head), "gpu_launches": t["launches"], "clocks": t["clocks"],
+        "gpu_launches": t["launches"], "clocks": t["clocks"],
     }
+    line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     xh = None

@@ -257,8 +257,9 @@ typedef enum {
   TUCKER_PHASE_EIG = 3,
   TUCKER_PHASE_RANK = 4,
   TUCKER_PHASE_TTM = 5,
-  TUCKER_PHASE_SCALE = 6,  /* max|Y| passes of the split-precision path */
-  TUCKER_PHASE_COUNT = 7
+  TUCKER_PHASE_SCALE = 6,   /* exponent-table pass of the split-precision Gram */
+  TUCKER_PHASE_TTM_L1 = 7,  /* split-precision TTM of a mode with L == 1 (contiguous columns) */
+  TUCKER_PHASE_COUNT = 8
 } tucker_phase;
 
 typedef struct tucker_profile {

@@ -10,7 +10,7 @@ Every step follows the paper's definitions in the order of Algorithm 1
 routines serve as single steps where the step *is* that routine: a matrix
 product for the Gram matrix and the mode-n product, LAPACK's symmetric
 eigensolver (``numpy.linalg.eigh``) for "leading eigenvectors of S", as the
-paper itself uses LAPACK's ``dsyevx`` there (Sec. 4.3).
+paper itself uses LAPACK's ``dsyevx`` there (Sec. 4.4).
 
 Readings of points the paper leaves open (each is repeated in the design doc):
 

@@ -109,6 +109,8 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
                       const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+// *d_out = trace of the J x J matrix S (column-major), summed in index order.
+int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s);
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s);
 // Split-precision mode product Z(L,R,B) = U^T Y(L,J,B) on tcgen05 (R <= J <= 128);

@@ -651,7 +651,8 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   TK_CUDA(cudaMemcpyAsync(chk, w.check, sizeof chk, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&sw, w.sweeps, sizeof sw, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
-  if (prof) prof->end(0.0, (double)J * J * 8, 1);
+  // the paper's flop count of the eigenvector step (10/3 J^3, Sec. 4.4); bytes: S read, V written
+  if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);
   const double tol_res = 16.0 * m * kU * chk[2], tol_orth = 16.0 * m * kU;
   if (chk[0] <= tol_res && chk[1] <= tol_orth) {
     const int info[2] = {sw, 0};

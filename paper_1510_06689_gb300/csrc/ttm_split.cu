@@ -677,12 +677,12 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
               (long long)R);
     return TUCKER_EUNSUPPORTED;
   }
-  if (prof) prof->begin(TUCKER_PHASE_TTM);
   const double flops = 2.0 * J * R * (double)(L * B);
   const double bytes = (double)(L * B) * (J * (dt == TUCKER_F64 ? 8.0 : 4.0) + R * 8.0) + J * R * 8.0;
   if (L == 1) {
     const TtmL1Plan q = ttm_l1_plan(J, B, R, y, dt, dev);
     if (q.parts > 0) {
+      if (prof) prof->begin(TUCKER_PHASE_TTM_L1);
       if (dt == TUCKER_F64) {
         TK_CUDA(cudaFuncSetAttribute(k_ttm_split_l1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem));
         k_ttm_split_l1<double><<<q.grid, kThreads, q.smem, s>>>(static_cast<const double *>(y), U, q, z, d_err);
@@ -696,6 +696,7 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
     }
   }
   const TtmSplit2Plan p = ttm_split2_plan(L, J, B, R, dev);
+  if (prof) prof->begin(TUCKER_PHASE_TTM);
   if (dt == TUCKER_F64) {
     TK_CUDA(cudaFuncSetAttribute(k_ttm_split2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     k_ttm_split2<double><<<p.grid, kThreads, p.smem, s>>>(static_cast<const double *>(y), L, B, U, p, z, d_err);

@@ -1,17 +1,20 @@
 // Host driver and C ABI of the ST-HOSVD library (declarations in include/tucker.h).
 //
 // tucker_sthosvd sequences Algorithm 1 (Sec. 2.2) on one GPU:
-//   ||X||^2 (sum-of-squares kernel) -> threshold eps^2 ||X||^2 / N,
+//   ||X||^2 (sum-of-squares kernel; the split-precision path takes the trace
+//   of its first Gram instead) -> threshold eps^2 ||X||^2 / N,
 //   then for each mode n of the order:
-//     Gram of the (L, J_n, B) view   (split-K kernel + fixed-order reduce)
-//     Jacobi eigensolve              (one CTA)
+//     Gram of the (L, J_n, B) view   (float64 split-K kernel, or the
+//                                     tensor-core digit Gram)
+//     eigensolve                     (mixed-precision solver for J <= 128,
+//                                     float64 Jacobi otherwise or as fallback)
 //     rank rule                      (one thread)
 //     copy R_n, tail and eigenvalues to pinned host memory; synchronise
 //     factor U_n = first R_n eigenvector columns
 //     TTM  Y <- Y x_n U_n^T          (into a fresh stream-ordered buffer)
-// The only host<->device round trip per mode is the rank, which fixes the
-// shape of the next launch.  All device memory is stream-ordered
-// (cudaMallocAsync on the caller's stream).
+// The rank, which fixes the shape of the next launch, is the main host<->device
+// round trip per mode (the mixed-precision eigensolver adds a few small ones).
+// All device memory is stream-ordered (cudaMallocAsync on the caller's stream).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -248,6 +251,22 @@ static void free_result_device(tucker_result *r) {
   for (int n = 0; n < TUCKER_MAX_MODES; ++n) r->factors[n] = nullptr;
 }
 
+namespace {
+// trace of a J x J column-major matrix, summed in index order (one thread)
+__global__ void k_trace(const double *__restrict__ S, int J, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < J; ++i) t += S[i + (int64_t)J * i];
+  *out = t;
+}
+}  // namespace
+
+int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s) {
+  k_trace<<<1, 32, 0, s>>>(d_S, (int)J, d_out);
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
@@ -278,7 +297,6 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   int *d_terr = reinterpret_cast<int *>(d_nx2 + 6);
   TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
   if (prec == TUCKER_PREC_BF16X4) {
-    TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
     for (int n = 0; n < N; ++n)
       if (dims[n] > 128) {
         set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
@@ -290,22 +308,33 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   TK_CHECK(pinned(sizeof(double) * (8 + maxJ), &host));
   double *h = static_cast<double *>(host);
 
-  // ||X||^2 and the threshold of the rank rule
-  TK_CHECK(launch_norm2(X, dt, I, partials.as<double>(), d_nx2, s, &prof));
-  TK_CUDA(cudaMemcpyAsync(h, d_nx2, sizeof(double), cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaStreamSynchronize(s));
-  const double nx2 = h[0];
-  if (!std::isfinite(nx2) || fault_injection("nan")) {
-    set_error("||X||^2 is not finite (%g): the input holds Inf or NaN", nx2);
-    return TUCKER_ENONFINITE;
-  }
+  // ||X||^2 and the threshold of the rank rule.  The split-precision path
+  // takes ||X||^2 as the trace of its first Gram (equal in exact arithmetic;
+  // the 21-bit rounding of the Gram moves it by ~1e-10 relative), saving a
+  // float64-bound pass over X; it is read back after the first Gram.
+  const bool norm_from_trace = prec == TUCKER_PREC_BF16X4;
   const int keep_all = !(eps > 0.0);
-  const double threshold = keep_all ? 0.0 : eps * eps * nx2 / N;
+  double nx2 = 0.0, threshold = 0.0;
+  auto set_norm = [&](double v) -> int {
+    nx2 = v;
+    if (!std::isfinite(nx2) || fault_injection("nan")) {
+      set_error("||X||^2 is not finite (%g): the input holds Inf or NaN", nx2);
+      return TUCKER_ENONFINITE;
+    }
+    threshold = keep_all ? 0.0 : eps * eps * nx2 / N;
+    out->norm2_x = nx2;
+    out->threshold = threshold;
+    return TUCKER_OK;
+  };
+  if (!norm_from_trace) {
+    TK_CHECK(launch_norm2(X, dt, I, partials.as<double>(), d_nx2, s, &prof));
+    TK_CUDA(cudaMemcpyAsync(h, d_nx2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    TK_CHECK(set_norm(h[0]));
+  }
 
   out->N = N;
   out->on_host = 0;
-  out->norm2_x = nx2;
-  out->threshold = threshold;
   for (int n = 0; n < N; ++n) {
     out->dims[n] = dims[n];
     out->mode_order[n] = order[n];
@@ -340,6 +369,12 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
       TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
       TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
+      if (k == 0 && norm_from_trace) {
+        TK_CHECK(launch_trace(S.as<double>(), J, d_nx2, s));
+        TK_CUDA(cudaMemcpyAsync(h, d_nx2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        TK_CUDA(cudaStreamSynchronize(s));
+        TK_CHECK(set_norm(h[0]));
+      }
     } else {
       const int64_t gws = gram_workspace_doubles(L, J, B, dev);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));

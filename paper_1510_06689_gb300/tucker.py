@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libtucker_gb300.so")
 
 F64, F32 = 0, 1
 PREC = {"fp64": 0, "bf16x4": 1}
-PHASES = ("norm", "gram", "gram_reduce", "eig", "rank", "ttm", "scale")
+PHASES = ("norm", "gram", "gram_reduce", "eig", "rank", "ttm", "scale", "ttm_l1")
 
 # Every symbol include/tucker.h declares (checked by the CPU test suite).
 EXPORTS = (

@@ -229,3 +229,23 @@ def test_sthosvd_split_matches_oracle_ranks_and_error(gpu_lib, dims, ranks, eps,
     for n in range(len(dims)):
         u = res.factor(n).cpu().numpy()
         assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-13 * dims[n]
+
+
+def test_sthosvd_split_nonfinite_and_norm_from_trace(gpu_lib):
+    """The split path reads ||X||^2 off its first Gram's trace: close to the
+    float64 sum of squares (21-bit rounding of Y), and Inf/NaN still stop it."""
+    dims, ranks = (24, 20, 16, 6), (6, 5, 4, 3)
+    x = tucker_tensor_np(dims, ranks, seed=21, decay=0.15, smooth=True, noise=1e-6)
+    res = gpu_lib.sthosvd(dev(x), dims, 1e-4, precision="bf16x4")
+    ref = float(np.dot(x, x))
+    # each entry is rounded by at most h = 2^(E - 22) (E: exponent above max|x|), so
+    # |sum y~^2 - sum y^2| <= sum (2 |y| h + h^2), plus float64 summation
+    h = 2.0 ** (math.frexp(float(np.abs(x).max()))[1] - 22)
+    bound = float(np.sum(2 * np.abs(x) * h + h * h)) + 1e-12 * ref
+    assert abs(res.norm2 - ref) <= bound
+    for bad in (np.nan, np.inf):
+        y = x.copy()
+        y[123] = bad
+        with pytest.raises(gpu_lib.TuckerError) as e:
+            gpu_lib.sthosvd(dev(y), dims, 1e-4, precision="bf16x4")
+        assert e.value.status == -6
