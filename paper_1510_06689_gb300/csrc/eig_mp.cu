@@ -71,8 +71,7 @@ constexpr int kPolishSteps = 2;
 __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restrict__ A, int lda, int n,
                                                            double *__restrict__ X, int ldx, int *__restrict__ sweeps) {
   extern __shared__ __align__(16) float sm32[];
-  __shared__ float cs[kMpMaxJ / 2], sn[kMpMaxJ / 2];
-  __shared__ int pp[kMpMaxJ / 2], qq[kMpMaxJ / 2];
+  __shared__ float4 rot[kMpMaxJ / 2];  // per pair: c, s, t = s / c, (p | q << 16) as bits
   __shared__ float red[kJ32Threads / 32];
   __shared__ float scale_s, tol_s;
   __shared__ int rotated;
@@ -80,9 +79,8 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
   const int ld = m + 1;    // odd row stride: S[i ld + j] and its mirror S[j ld + i] fall in different banks
   float *S = sm32;         // m x ld
   float *V = S + ((m * ld + 3) & ~3);  // m x m, column j at V + j m (16-byte aligned)
-  short *blkP = reinterpret_cast<short *>(V + m * m);
+  int *blk = reinterpret_cast<int *>(V + m * m);  // pair block e -> P | Q << 16, P <= Q
   const int nblk = np * (np + 1) / 2;
-  short *blkQ = blkP + nblk;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
 
   float mx = 0.f;
@@ -103,12 +101,11 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
     S[i * ld + j] = (hi < n) ? (float)(A[lo + (int64_t)lda * hi] * inv) : 0.f;
     V[e] = (i == j) ? 1.f : 0.f;
   }
-  for (int e = tid; e < nblk; e += nt) {  // pair-block table: e -> (P <= Q)
+  for (int e = tid; e < nblk; e += nt) {
     int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while ((q + 1) * (q + 2) / 2 <= e) ++q;
     while (q * (q + 1) / 2 > e) --q;
-    blkQ[e] = (short)q;
-    blkP[e] = (short)(e - q * (q + 1) / 2);
+    blk[e] = (e - q * (q + 1) / 2) | (q << 16);
   }
   __syncthreads();
 
@@ -135,39 +132,44 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
           p = q;
           q = tmp;
         }
-        float c = 1.f, sv = 0.f;
+        // rotation annihilating s_pq (approximate reciprocals and roots are
+        // enough: c and s = t c stay orthonormal to rounding, and s_pq is
+        // then set to zero exactly)
+        float c = 1.f, sv = 0.f, tt = 0.f;
         const float b = S[p * ld + q];
         if (fabsf(b) > tol) {
           const float a = S[p * ld + p], d = S[q * ld + q];
-          const float tau = (d - a) / (2.f * b);
+          const float tau = __fdividef(d - a, 2.f * b);
           const float at = fabsf(tau);
-          const float tt = at > 1e18f ? 0.5f / tau : copysignf(1.f, tau) / (at + sqrtf(1.f + tau * tau));
-          c = rsqrtf(1.f + tt * tt);
+          const float h = fmaf(tau, tau, 1.f);
+          tt = at > 1e18f ? __fdividef(0.5f, tau) : copysignf(__fdividef(1.f, at + h * rsqrtf(h)), tau);
+          c = rsqrtf(fmaf(tt, tt, 1.f));
           sv = tt * c;
           if (sv != 0.f) rotated = 1;
         }
-        cs[t] = c;
-        sn[t] = sv;
-        pp[t] = p;
-        qq[t] = q;
+        rot[t] = make_float4(c, sv, tt, __int_as_float(p | (q << 16)));
       }
       __syncthreads();
       for (int e = tid; e < nblk; e += nt) {
-        const int P = blkP[e], Q = blkQ[e];
-        const float s1 = sn[P], s2 = sn[Q];
-        if (s1 == 0.f && s2 == 0.f) continue;
-        const int p1 = pp[P], q1 = qq[P];
+        const int pq = blk[e];
+        const int P = pq & 0xFFFF, Q = pq >> 16;
+        const float4 rP = rot[P];
         if (P == Q) {
-          const float t1 = s1 / cs[P];
+          if (rP.y == 0.f) continue;
+          const int k = __float_as_int(rP.w), p1 = k & 0xFFFF, q1 = k >> 16;
           const float b = S[p1 * ld + q1];
-          S[p1 * ld + p1] -= t1 * b;
-          S[q1 * ld + q1] += t1 * b;
+          S[p1 * ld + p1] -= rP.z * b;
+          S[q1 * ld + q1] += rP.z * b;
           S[p1 * ld + q1] = 0.f;
           S[q1 * ld + p1] = 0.f;
           continue;
         }
-        const float c1 = cs[P], c2 = cs[Q];
-        const int p2 = pp[Q], q2 = qq[Q];
+        const float4 rQ = rot[Q];
+        const float s1 = rP.y, s2 = rQ.y;
+        if (s1 == 0.f && s2 == 0.f) continue;
+        const float c1 = rP.x, c2 = rQ.x;
+        const int kP = __float_as_int(rP.w), kQ = __float_as_int(rQ.w);
+        const int p1 = kP & 0xFFFF, q1 = kP >> 16, p2 = kQ & 0xFFFF, q2 = kQ >> 16;
         const float x11 = S[p1 * ld + p2], x12 = S[p1 * ld + q2], x21 = S[q1 * ld + p2], x22 = S[q1 * ld + q2];
         const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
         const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
@@ -183,11 +185,12 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
         S[q2 * ld + q1] = z22;
       }
       for (int t = warp; t < np; t += nwarps) {
-        const float sv = sn[t];
-        if (sv == 0.f || 4 * lane >= m) continue;
-        const float c = cs[t];
-        float4 *vp = reinterpret_cast<float4 *>(V + pp[t] * m) + lane;
-        float4 *vq = reinterpret_cast<float4 *>(V + qq[t] * m) + lane;
+        const float4 r = rot[t];
+        if (r.y == 0.f || 4 * lane >= m) continue;
+        const float c = r.x, sv = r.y;
+        const int k = __float_as_int(r.w);
+        float4 *vp = reinterpret_cast<float4 *>(V + (k & 0xFFFF) * m) + lane;
+        float4 *vq = reinterpret_cast<float4 *>(V + (k >> 16) * m) + lane;
         const float4 a = *vp, b = *vq;
         *vp = make_float4(c * a.x - sv * b.x, c * a.y - sv * b.y, c * a.z - sv * b.z, c * a.w - sv * b.w);
         *vq = make_float4(sv * a.x + c * b.x, sv * a.y + c * b.y, sv * a.z + c * b.z, sv * a.w + c * b.w);
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
 
 size_t jacobi32_smem(int n) {
   const int m = (n + 3) & ~3, np = m / 2;
-  return (size_t)(((m * (m + 1) + 3) & ~3) + m * m) * sizeof(float) + (size_t)np * (np + 1) * sizeof(short) + 16;
+  return (size_t)(((m * (m + 1) + 3) & ~3) + m * m) * sizeof(float) + (size_t)np * (np + 1) / 2 * sizeof(int) + 16;
 }
 
 // ---------------------------------------------------------------------------

@@ -97,6 +97,50 @@ __device__ __forceinline__ double scaled_ll_to_double(long long v, int sc) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | frac));
 }
 
+// round(|y| 2^(28 - f)) with the sign of y, from the bits in 32-bit integer
+// arithmetic (ties away from zero); f1022 = f + 1022 and |y| < 2^f.  With m29
+// the leading 29 bits of the significand, v = (m29 + 2^sh) >> (sh + 1) for
+// sh = f + 1022 - exponent field; the lower bits cannot change the result.
+__device__ __forceinline__ int scaled_int28_bits(double y, int f1022) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m29 = (((hi & 0xFFFFFu) | 0x100000u) << 8) | (lo >> 24);
+  const int sh = max(min(f1022 - ex, 30), 0);
+  unsigned v = (m29 + (1u << sh)) >> (sh + 1);
+  v = ex ? v : 0u;
+  const int sgn = (int)hi >> 31;
+  return ((int)v ^ sgn) - sgn;
+}
+__device__ __forceinline__ int scaled_int28_bits(float y, int f1022) {
+  return scaled_int28(y, f1022 - 1022);
+}
+
+// the four balanced digits of v (|v| <= 2^28) as exact floats
+__device__ __forceinline__ void digits4_float(int v, float (&d)[4]) {
+  const int h = (v + 64) >> 7;  // |h| <= 2^21
+  d[3] = small_int_float(v - (h << 7));
+  const float hf = small_int_float(h);
+  d[0] = round_float(hf * 0x1p-14f);
+  const float r = __fmaf_rn(d[0], -16384.0f, hf);
+  d[1] = round_float(r * 0x1p-7f);
+  d[2] = __fmaf_rn(d[1], -128.0f, r);
+}
+
+// sum_k a_k 2^(28 - 7k) 2^sc as a float64, from four float accumulators that
+// hold integers |a_k| < 2^22 (the levels 2..5 of a digit product): the
+// integers come out of the floats exactly by magic-number addition, pairs
+// combine in 32 bits (|a0 2^7 + a1| < 2^30), and the 50-bit sum converts
+// exactly from its bits.
+__device__ __forceinline__ double levels_to_double(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, int sc) {
+  const int i0 = __float_as_int(__fadd_rn(__uint_as_float(a0), 12582912.0f)) - 0x4B400000;
+  const int i1 = __float_as_int(__fadd_rn(__uint_as_float(a1), 12582912.0f)) - 0x4B400000;
+  const int i2 = __float_as_int(__fadd_rn(__uint_as_float(a2), 12582912.0f)) - 0x4B400000;
+  const int i3 = __float_as_int(__fadd_rn(__uint_as_float(a3), 12582912.0f)) - 0x4B400000;
+  const long long v = ((long long)(i0 * 128 + i1) << 21) + ((long long)(i2 * 128 + i3) << 7);
+  return scaled_ll_to_double(v, sc);
+}
+
 // ---------------------------------------------------------------------------
 // The 128 columns of a tile are the M = 128 rows of the MMA (A = Y's digits)
 // and the factor is the N operand (B = U's digits, N = R rounded up to 16).  One MMA then covers 128 columns, each column's exponent belongs
@@ -122,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
   extern __shared__ __align__(1024) unsigned char dsmem[];
   __shared__ __align__(8) unsigned long long mbar[2];   // operand stages
   __shared__ __align__(8) unsigned long long tbar[2];   // accumulator sets (tile done)
-  __shared__ unsigned long long colmax[kM2];
+  __shared__ unsigned colmax[kM2];
   __shared__ int colexp[2][kM2];
   __shared__ int64_t colout[2][kM2];
   __shared__ int rowexp[kM];
@@ -238,11 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
           for (int e = 0; e < 4; ++e) {
             const int r = r0 + e;
             if (r >= p.R) continue;
-            const long long v = ((long long)__float2int_rn(__uint_as_float(a[0][e])) << 28) +
-                                ((long long)__float2int_rn(__uint_as_float(a[1][e])) << 21) +
-                                ((long long)__float2int_rn(__uint_as_float(a[2][e])) << 14) +
-                                ((long long)__float2int_rn(__uint_as_float(a[3][e])) << 7);
-            z[ob + L * (int64_t)r] = scaled_ll_to_double(v, rowexp[r] + colexp[set][c] - 42);
+            z[ob + L * (int64_t)r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + colexp[set][c] - 42);
           }
         }
       }
@@ -260,14 +300,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
   for (; t < p.ntiles; t += gridDim.x, ++it) {
     const int set = (p.sets == 2) ? (it & 1) : 0;
     // column exponents and output addresses of this tile
-    if (tid < kM2) colmax[tid] = 0ull;
+    if (tid < kM2) colmax[tid] = 0u;
     __syncthreads();
     {
-      unsigned long long m = 0ull;
+      unsigned m = 0u;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) m = max(m, mag_bits(raw[k][e]));
+        for (int e = 0; e < 8; ++e) m = max(m, hi_mag(raw[k][e]));
       atomicMax(&colmax[my_c], m);
     }
     if (tid < kM2) {
@@ -280,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
       colout[set][tid] = ob;
     }
     __syncthreads();
-    if (tid < kM2) colexp[set][tid] = exp_above(colmax[tid], kF64);
+    if (tid < kM2) colexp[set][tid] = exp_above(mag_pattern(colmax[tid], kF64), kF64);
     __syncthreads();
     const int e_col = colexp[set][my_c];
     for (int part = 0; part < p.parts; ++part, ++unit) {
@@ -296,11 +336,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
         uint32_t w[kBTiles][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          int d[2][4];
-          digits4(scaled_int28(raw[k][e], e_col), d[0]);
-          digits4(scaled_int28(raw[k][e + 1], e_col), d[1]);
+          float d0[4], d1[4];
+          digits4_float(scaled_int28_bits(raw[k][e], e_col + 1022), d0);
+          digits4_float(scaled_int28_bits(raw[k][e + 1], e_col + 1022), d1);
 #pragma unroll
-          for (int q = 0; q < kBTiles; ++q) w[q][e >> 1] = bf16_pair((float)d[0][q], (float)d[1][q]);
+          for (int q = 0; q < kBTiles; ++q) w[q][e >> 1] = bf16_pair(d0[q], d1[q]);
         }
         const int jl = jg % (KH / 8);
         const int off = (my_c >> 3) * (int)sbo_a + jl * 128 + (my_c & 7) * 16;
@@ -385,15 +425,26 @@ TtmSplit2Plan ttm_split2_plan(int64_t L, int64_t J, int64_t B, int64_t R, const 
 
 // ---------------------------------------------------------------------------
 // L == 1 (the first mode of the natural layout): column c of the unfolding
-// is the contiguous vector y[c J .. c J + J - 1].  A warp takes whole columns,
-// its lanes reading consecutive 16-byte pairs (fully coalesced), finds the
-// column exponent with a warp reduction, and writes each digit row into a
-// 128-byte swizzled K-major tile (one row per store instruction, no bank
-// conflicts).  Each warp keeps four columns in flight in registers.  Two TMEM
-// accumulator sets (R <= 64) let a tile's MMAs run while the previous tile
-// drains; the drain stages the outputs of a
-// tile (R contiguous doubles per column, so the tile's output is one
-// contiguous block) in shared memory and writes them out row by row.
+// is the contiguous vector y[c J .. c J + J - 1].  The CTA's warps have
+// fixed roles and meet only at mbarriers, so conversion, tensor-core work
+// and the drain of the previous tile overlap:
+//   16 converter warps take whole columns (8 per warp per tile): lanes read
+//      consecutive 16-byte pairs (coalesced), a warp reduction gives the
+//      column exponent, and each digit row goes to a 128-byte swizzled
+//      K-major tile (one row per store instruction, no bank conflicts); two
+//      columns per warp are in flight in registers;
+//   1 MMA warp issues the tile's MMAs (columns are the M = 128 rows, U the N
+//      operand: 4 MMAs per k-step, one per digit of Y against U's stacked
+//      digit tiles) into one of two TMEM accumulator sets;
+//   8 drain warps (two per TMEM lane quarter) assemble each output exactly
+//      from the four levels, stage the tile's outputs (R contiguous doubles
+//      per column: the tile's output is one contiguous block) in shared
+//      memory and write them out row by row.
+// Barriers: a_full (converters -> MMA: digits written), a_free (MMA commit:
+// digits read), acc_full[2] (MMA commit: a set holds a finished tile),
+// acc_free[2] (drain -> MMA: set read out), cexp[4] (converters -> drain:
+// column exponents of a tile, in a ring of four slots).  Every wait is
+// bounded and also gives up once another role has flagged an error.
 // ---------------------------------------------------------------------------
 struct TtmL1Plan {
   int J, Jp, R, Rp, parts, Rs, tmem_cols;
@@ -402,49 +453,47 @@ struct TtmL1Plan {
   size_t u_bytes, a_bytes, stg_bytes, smem;
 };
 
-constexpr int kL1ColsPerWarp = kM2 / (kThreads / 32);  // 8
-constexpr int kL1Depth = 4;                             // columns in flight per warp
+constexpr int kL1Conv = 16;                             // converter warps
+constexpr int kL1Drain = 8;                             // drain warps (two per TMEM lane quarter)
+constexpr int kL1Threads = (kL1Conv + kL1Drain + 1) * 32;
+constexpr int kL1ColsPerWarp = kM2 / kL1Conv;           // 8
+constexpr int kL1Depth = 4;                             // columns in flight per converter warp (64 KB per SM)
+constexpr int kL1Slots = 4;                             // column-exponent ring
 
-// round(|y| 2^(28 - f)) with the sign of y, from the bits in 32-bit integer
-// arithmetic (ties away from zero); f1022 = f + 1022 and |y| < 2^f.  With m29
-// the leading 29 bits of the significand, v = (m29 + 2^sh) >> (sh + 1) for
-// sh = f + 1022 - exponent field; the lower bits cannot change the result.
-__device__ __forceinline__ int scaled_int28_bits(double y, int f1022) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const int ex = (int)((hi >> 20) & 0x7FFu);
-  const unsigned m29 = (((hi & 0xFFFFFu) | 0x100000u) << 8) | (lo >> 24);
-  const int sh = max(min(f1022 - ex, 30), 0);
-  unsigned v = (m29 + (1u << sh)) >> (sh + 1);
-  v = ex ? v : 0u;
-  const int sgn = (int)hi >> 31;
-  return ((int)v ^ sgn) - sgn;
-}
-__device__ __forceinline__ int scaled_int28_bits(float y, int f1022) {
-  return scaled_int28(y, f1022 - 1022);
+// round(|y| 2^(28 - f)) etc. are above; the two roles' bounded wait:
+// true once the phase of `parity` has completed, false on expiry (which
+// raises *stop) or when another role has raised *stop.
+__device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int *stop) {
+  for (long long it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255 && *stop) return false;
+  }
+  *stop = 1;
+  return false;
 }
 
-// the four balanced digits of v (|v| <= 2^28) as exact floats
-__device__ __forceinline__ void digits4_float(int v, float (&d)[4]) {
-  const int h = (v + 64) >> 7;  // |h| <= 2^21
-  d[3] = small_int_float(v - (h << 7));
-  const float hf = small_int_float(h);
-  d[0] = round_float(hf * 0x1p-14f);
-  const float r = __fmaf_rn(d[0], -16384.0f, hf);
-  d[1] = round_float(r * 0x1p-7f);
-  d[2] = __fmaf_rn(d[1], -128.0f, r);
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) k_ttm_split_l1(const T *__restrict__ y, const double *__restrict__ U,
+__global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restrict__ y, const double *__restrict__ U,
                                                               TtmL1Plan p, double *__restrict__ z,
                                                               int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
-  __shared__ __align__(8) unsigned long long done_bar;  // a tile's MMAs have completed
-  __shared__ int colexp[2][kM2];
+  __shared__ __align__(8) unsigned long long a_full, a_free, acc_full[2], acc_free[2], cexp_full[kL1Slots];
+  __shared__ int colexp[kL1Slots][kM2];
   __shared__ int rowexp[kM];
   __shared__ uint32_t tmem_slot;
-  __shared__ int stop;
+  __shared__ volatile int stop;
+  __shared__ int drain_go;
   constexpr bool kF64 = sizeof(T) == 8;
   using V2 = typename std::conditional<kF64, double2, float2>::type;
   unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -455,7 +504,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_l1(const T *__restric
   const int a_tile = p.parts * kM2 * 128;
   const int u_tile = p.Rp * p.Jp * 2;
   const uint32_t sbo_u = (uint32_t)(p.Jp / 8) * 128u;
-  const uint32_t idesc = idesc_bf16(kM2, p.Rp);
+  uint32_t idesc_q[kBTiles];  // N = (4 - q) Rp: digit q of Y against U1 .. U(4-q)
+#pragma unroll
+  for (int q = 0; q < kBTiles; ++q) idesc_q[q] = idesc_bf16(kM2, (kBTiles - q) * p.Rp);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
@@ -465,7 +516,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_l1(const T *__restric
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_addr(&done_bar), 1);
+    mbar_init(smem_addr(&a_full), kL1Conv);
+    mbar_init(smem_addr(&a_free), 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_addr(&acc_full[k]), 1);
+      mbar_init(smem_addr(&acc_free[k]), kL1Drain);
+    }
+    for (int k = 0; k < kL1Slots; ++k) mbar_init(smem_addr(&cexp_full[k]), kL1Conv);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
   }
@@ -477,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_l1(const T *__restric
   }
   __syncthreads();
   // U's digit tiles (B operands: row r, k = j), as in the general kernel
-  for (int u = tid; u < p.Rp * (p.Jp / 8); u += kThreads) {
+  for (int u = tid; u < p.Rp * (p.Jp / 8); u += kL1Threads) {
     const int r = u / (p.Jp / 8), jg = u % (p.Jp / 8);
     uint32_t w[kATiles][4];
 #pragma unroll
@@ -498,140 +555,148 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_l1(const T *__restric
       *reinterpret_cast<uint4 *>(Ut + t * u_tile + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
   }
   // zero the A tiles once: K columns past J (up to the 64-wide part) stay zero
-  for (int e = tid; e < (int)(p.a_bytes / 16); e += kThreads) reinterpret_cast<uint4 *>(At)[e] = make_uint4(0, 0, 0, 0);
+  for (int e = tid; e < (int)(p.a_bytes / 16); e += kL1Threads) reinterpret_cast<uint4 *>(At)[e] = make_uint4(0, 0, 0, 0);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
+  const int64_t t0 = blockIdx.x, tstride = gridDim.x;
+  const int ntc = t0 < p.ntiles ? (int)((p.ntiles - t0 + tstride - 1) / tstride) : 0;
 
-  // column m of tile t, entries j = 2 lane + 64 h (h < 2) as two pairs
-  auto load_col = [&](int64_t t, int m, V2 (&v)[2]) {
-    const int64_t c = t * kM2 + m;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = 2 * lane + 64 * h;
-      if (t < p.ntiles && c < p.K && j < p.J)
-        v[h] = __ldg(reinterpret_cast<const V2 *>(y + c * (int64_t)p.J + j));
-      else
-        v[h].x = v[h].y = T(0);
-    }
-  };
-
-  // drain tile t from accumulator set `set` into z
-  auto drain = [&](int64_t t, int set) {
-    fence_after();
-    const int q = warp & 3, g = warp >> 2;
-    const int m = 32 * q + lane;
-    const int rq = p.Rp / 4;
-    const int fcol = colexp[set][m];
-    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * 4 * p.Rp);
-    for (int r0 = g * rq; r0 < (g + 1) * rq; r0 += 4) {
-      uint32_t a[4][4];
-#pragma unroll
-      for (int lev = 0; lev < 4; ++lev)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(a[lev][0]), "=r"(a[lev][1]), "=r"(a[lev][2]), "=r"(a[lev][3])
-                     : "r"(tb + (uint32_t)(lev * p.Rp + r0)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = r0 + e;
-        if (r < p.R) {
-          const long long v = ((long long)__float2int_rn(__uint_as_float(a[0][e])) << 28) +
-                              ((long long)__float2int_rn(__uint_as_float(a[1][e])) << 21) +
-                              ((long long)__float2int_rn(__uint_as_float(a[2][e])) << 14) +
-                              ((long long)__float2int_rn(__uint_as_float(a[3][e])) << 7);
-          stg[m * p.Rs + r] = scaled_ll_to_double(v, rowexp[r] + fcol - 42);
-        }
-      }
-    }
-    fence_before();
-    __syncthreads();
-    // the tile's output is z[t 128 R ..]: rows of R contiguous doubles
-    double *zt = z + t * kM2 * (int64_t)p.R;
-    const int nvalid = (int)(p.K - t * kM2 < kM2 ? p.K - t * kM2 : kM2);
-    for (int mm = warp; mm < nvalid; mm += kThreads / 32)
-      for (int r = lane; r < p.R; r += 32) zt[(int64_t)mm * p.R + r] = stg[mm * p.Rs + r];
-  };
-
-  V2 cb[kL1Depth][2];
-  const int64_t t0 = blockIdx.x;
-#pragma unroll
-  for (int k = 0; k < kL1Depth; ++k) load_col(t0, warp + 16 * k, cb[k]);
-  int64_t prev_t = -1;
-  int it = 0;
-  for (int64_t t = t0; t < p.ntiles; t += gridDim.x, ++it) {
-    const int set = it & 1;
-    // the A tiles are free once the previous tile's MMAs have completed
-    if (it >= 1 && tid == 0 && !mbar_wait(smem_addr(&done_bar), (it - 1) & 1)) stop = 1;
-    __syncthreads();
-    if (stop) break;
-#pragma unroll
-    for (int k = 0; k < kL1ColsPerWarp; ++k) {
-      const int m = warp + 16 * k;
-      V2 (&v)[2] = cb[k % kL1Depth];
-      // column exponent: the largest magnitude over the column's J entries
-      unsigned mx = max(max(hi_mag(v[0].x), hi_mag(v[0].y)), max(hi_mag(v[1].x), hi_mag(v[1].y)));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      const int f = exp_above(kF64 ? (unsigned long long)mx << 32 : (unsigned long long)mx, kF64);
-      if (lane == 0) colexp[set][m] = f;
-      const int f1022 = f + 1022;
+  if (warp < kL1Conv) {
+    // ---------------- converters ----------------
+    // column m of tile t, entries j = 2 lane + 64 h (h < 2) as two pairs
+    auto load_col = [&](int it, int m, V2(&v)[2]) {
+      const int64_t t = t0 + (int64_t)it * tstride;
+      const int64_t c = t * kM2 + m;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (2 * lane + 64 * h < p.Jp) {
-          float d0[4], d1[4];
-          digits4_float(scaled_int28_bits(v[h].x, f1022), d0);
-          digits4_float(scaled_int28_bits(v[h].y, f1022), d1);
-          const int off = h * (kM2 * 128) + m * 128 + (((lane >> 2) ^ (m & 7)) << 4) + (lane & 3) * 4;
+        const int j = 2 * lane + 64 * h;
+        if (it < ntc && c < p.K && j < p.J)
+          v[h] = __ldg(reinterpret_cast<const V2 *>(y + c * (int64_t)p.J + j));
+        else
+          v[h].x = v[h].y = T(0);
+      }
+    };
+    V2 cb[kL1Depth][2];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint32_t *>(At + q * a_tile + off) = bf16_pair(d0[q], d1[q]);
+    for (int k = 0; k < kL1Depth; ++k) load_col(0, warp + kL1Conv * k, cb[k]);
+    for (int it = 0; it < ntc; ++it) {
+      if (it >= 1) {  // the previous tile's MMAs have read the digit tiles
+        int ok = 0;
+        if (lane == 0) ok = role_wait(smem_addr(&a_free), (uint32_t)((it - 1) & 1), &stop);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      }
+      const int slot = it % kL1Slots;
+#pragma unroll
+      for (int k = 0; k < kL1ColsPerWarp; ++k) {
+        const int m = warp + kL1Conv * k;
+        V2(&v)[2] = cb[k % kL1Depth];
+        unsigned mx = max(max(hi_mag(v[0].x), hi_mag(v[0].y)), max(hi_mag(v[1].x), hi_mag(v[1].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int f = exp_above(mag_pattern(mx, kF64), kF64);
+        if (lane == 0) colexp[slot][m] = f;
+        const int f1022 = f + 1022;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (2 * lane + 64 * h < p.Jp) {
+            float d0[4], d1[4];
+            digits4_float(scaled_int28_bits(v[h].x, f1022), d0);
+            digits4_float(scaled_int28_bits(v[h].y, f1022), d1);
+            const int off = h * (kM2 * 128) + m * 128 + (((lane >> 2) ^ (m & 7)) << 4) + (lane & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint32_t *>(At + q * a_tile + off) = bf16_pair(d0[q], d1[q]);
+          }
+        }
+        // refill: the column kL1Depth ahead (possibly of this CTA's next tile)
+        const int kn = k + kL1Depth;
+        if (kn < kL1ColsPerWarp) load_col(it, warp + kL1Conv * kn, v);
+        else load_col(it + 1, warp + kL1Conv * (kn - kL1ColsPerWarp), v);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_addr(&cexp_full[slot]));
+        mbar_arrive(smem_addr(&a_full));
+      }
+    }
+  } else if (warp < kL1Conv + kL1Drain) {
+    // ---------------- drain ----------------
+    const int dw = warp - kL1Conv;
+    const int q = warp & 3;           // the TMEM lane quarter this warp may read
+    const int half = dw >> 2;         // which half of the r range
+    const int m = 32 * q + lane;
+    const int rh = p.Rp / 2;          // a multiple of 8
+    for (int it = 0; it < ntc; ++it) {
+      const int set = it & 1, slot = it % kL1Slots;
+      if (dw == 0 && lane == 0) {
+        drain_go = role_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1), &stop) &&
+                   role_wait(smem_addr(&cexp_full[slot]), (uint32_t)((it / kL1Slots) & 1), &stop);
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");
+      if (!drain_go) break;
+      fence_after();
+      const int fcol = colexp[slot][m];
+      const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * 4 * p.Rp);
+      for (int r0 = half * rh; r0 < (half + 1) * rh; r0 += 4) {
+        uint32_t a[4][4];
+#pragma unroll
+        for (int lev = 0; lev < 4; ++lev)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(a[lev][0]), "=r"(a[lev][1]), "=r"(a[lev][2]), "=r"(a[lev][3])
+                       : "r"(tb + (uint32_t)(lev * p.Rp + r0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = r0 + e;
+          if (r < p.R)
+            stg[m * p.Rs + r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + fcol - 42);
         }
       }
-      // refill: the column kL1Depth ahead (possibly of this CTA's next tile)
-      const int kn = k + kL1Depth;
-      if (kn < kL1ColsPerWarp) load_col(t, warp + 16 * kn, v);
-      else load_col(t + gridDim.x, warp + 16 * (kn - kL1ColsPerWarp), v);
+      fence_before();
+      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");
+      if (lane == 0) mbar_arrive(smem_addr(&acc_free[set]));  // this warp's reads of the set are complete
+      // the tile's output is z[t 128 R ..]: rows of R contiguous doubles
+      const int64_t t = t0 + (int64_t)it * tstride;
+      double *zt = z + t * kM2 * (int64_t)p.R;
+      const int nvalid = (int)(p.K - t * kM2 < kM2 ? p.K - t * kM2 : kM2);
+      for (int mm = dw; mm < nvalid; mm += kL1Drain)
+        for (int r = lane; r < p.R; r += 32) zt[(int64_t)mm * p.R + r] = stg[mm * p.Rs + r];
+      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");  // staging free for the next tile
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (lane == 0) {
+    // ---------------- MMA issue ----------------
+    const uint32_t ab = smem_addr(At), ub = smem_addr(Ut);
+    int issued = -1;
+    for (int it = 0; it < ntc; ++it) {
+      const int set = it & 1;
+      if (!role_wait(smem_addr(&a_full), (uint32_t)(it & 1), &stop)) break;
+      if (it >= 2 && !role_wait(smem_addr(&acc_free[set]), (uint32_t)(((it - 2) >> 1) & 1), &stop)) break;
       fence_after();
-      const uint32_t ab = smem_addr(At), ub = smem_addr(Ut);
+      // U's four digit tiles are stacked rows of one K-major operand (U1 first),
+      // so the MMA of Y's digit q against its first (4 - q) Rp rows, written
+      // at column q Rp of the set, adds Y_q U_a into level q + a for every
+      // a <= 3 - q at once: 4 MMAs per k-step carry the 10 digit products.
       const uint32_t d0 = tmem + (uint32_t)(set * 4 * p.Rp);
       for (int ks = 0; ks < p.Jp / 16; ++ks) {
-        const uint32_t acc = ks == 0 ? 0u : 1u;
         const uint32_t koff = (uint32_t)((ks >> 2) * (kM2 * 128) + (ks & 3) * 32);
-        uint64_t ya[kBTiles], ub4[kATiles];
+        const uint64_t ucat = smem_desc(ub + 256 * ks, 128, sbo_u);
 #pragma unroll
-        for (int q = 0; q < kBTiles; ++q) ya[q] = smem_desc_sw128(ab + q * a_tile + koff, 1024);
-#pragma unroll
-        for (int q = 0; q < kATiles; ++q) ub4[q] = smem_desc(ub + q * u_tile + 256 * ks, 128, sbo_u);
-        mma_bf16(d0 + 0 * p.Rp, ya[0], ub4[0], idesc, acc);
-        mma_bf16(d0 + 1 * p.Rp, ya[0], ub4[1], idesc, acc);
-        mma_bf16(d0 + 1 * p.Rp, ya[1], ub4[0], idesc, 1u);
-        mma_bf16(d0 + 2 * p.Rp, ya[0], ub4[2], idesc, acc);
-        mma_bf16(d0 + 2 * p.Rp, ya[1], ub4[1], idesc, 1u);
-        mma_bf16(d0 + 2 * p.Rp, ya[2], ub4[0], idesc, 1u);
-        mma_bf16(d0 + 3 * p.Rp, ya[0], ub4[3], idesc, acc);
-        mma_bf16(d0 + 3 * p.Rp, ya[1], ub4[2], idesc, 1u);
-        mma_bf16(d0 + 3 * p.Rp, ya[2], ub4[1], idesc, 1u);
-        mma_bf16(d0 + 3 * p.Rp, ya[3], ub4[0], idesc, 1u);
+        for (int q = 0; q < kBTiles; ++q) {
+          const uint64_t ya = smem_desc_sw128(ab + q * a_tile + koff, 1024);
+          // levels q..3 start accumulating at the first k-step of digit q = 0;
+          // later digits add into levels the q = 0 MMA has already initialised
+          mma_bf16(d0 + q * p.Rp, ya, ucat, idesc_q[q], (ks == 0 && q == 0) ? 0u : 1u);
+        }
       }
-      mma_commit(smem_addr(&done_bar));
+      mma_commit(smem_addr(&a_free));
+      mma_commit(smem_addr(&acc_full[set]));
+      issued = it;
     }
-    // drain the previous tile while the tensor cores work on this one
-    if (prev_t >= 0) drain(prev_t, set ^ 1);
-    prev_t = t;
-  }
-  // the last tile
-  if (!stop && prev_t >= 0) {
-    if (tid == 0 && !mbar_wait(smem_addr(&done_bar), (it - 1) & 1)) stop = 1;
-    __syncthreads();
-    if (!stop) drain(prev_t, (it - 1) & 1);
-  } else if (stop && it >= 1 && tid == 0) {
-    mbar_wait(smem_addr(&done_bar), (it - 1) & 1);  // let our own MMAs finish before TMEM is released
+    // no MMA of ours may still run when TMEM is released
+    if (issued >= 0) mbar_wait(smem_addr(&a_free), (uint32_t)(issued & 1));
   }
   fence_before();
   __syncthreads();
@@ -685,10 +750,10 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
       if (prof) prof->begin(TUCKER_PHASE_TTM_L1);
       if (dt == TUCKER_F64) {
         TK_CUDA(cudaFuncSetAttribute(k_ttm_split_l1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem));
-        k_ttm_split_l1<double><<<q.grid, kThreads, q.smem, s>>>(static_cast<const double *>(y), U, q, z, d_err);
+        k_ttm_split_l1<double><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const double *>(y), U, q, z, d_err);
       } else {
         TK_CUDA(cudaFuncSetAttribute(k_ttm_split_l1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem));
-        k_ttm_split_l1<float><<<q.grid, kThreads, q.smem, s>>>(static_cast<const float *>(y), U, q, z, d_err);
+        k_ttm_split_l1<float><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const float *>(y), U, q, z, d_err);
       }
       TK_LAUNCHED();
       if (prof) prof->end(flops, bytes, 1);
