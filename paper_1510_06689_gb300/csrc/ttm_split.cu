@@ -593,9 +593,8 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
       for (int k = 0; k < kL1ColsPerWarp; ++k) {
         const int m = warp + kL1Conv * k;
         V2(&v)[2] = cb[k % kL1Depth];
-        unsigned mx = max(max(hi_mag(v[0].x), hi_mag(v[0].y)), max(hi_mag(v[1].x), hi_mag(v[1].y)));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const unsigned mx = __reduce_max_sync(
+            0xffffffffu, max(max(hi_mag(v[0].x), hi_mag(v[0].y)), max(hi_mag(v[1].x), hi_mag(v[1].y))));
         const int f = exp_above(mag_pattern(mx, kF64), kF64);
         if (lane == 0) colexp[slot][m] = f;
         const int f1022 = f + 1022;
