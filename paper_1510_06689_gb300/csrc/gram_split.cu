@@ -26,15 +26,19 @@
 //     of 2^-7 with ordinary FP32 rounding; its weight is 2^-21 of level 2, so
 //     that rounding is ~2^-45 of the result.
 //   * At the end of each group the accumulators are drained:
-//     C += (2^28 acc0 + 2^22 acc1 + 2^14 acc2 + 2^7 acc3) 2^(E_ig + E_jg - 2 E)
-//     into per-thread double-float (FP32 pair) accumulators, with 2^E above
-//     the global largest magnitude; S = (C + C^T) 2^(2E - 43) after a
-//     fixed-order float64 reduction of the per-CTA partials.  The four
-//     128 x 128 accumulators fill TMEM's 512 columns; the double-float C
-//     (128 KB) sits in shared memory beside two 32-column digit stages, so
-//     the converting threads keep their registers for a two-chunk prefetch.
+//     C += (2^28 acc0 + 2^22 acc1 + 2^14 acc2 + 2^7 acc3)
+//          2^(E_ig - ref_i + E_jg - ref_j)
+//     into per-thread double-float (FP32 pair) accumulators, with ref_i the
+//     largest E_ig over the CTA's groups; S_ij = sum over CTAs of
+//     (C_ij + C_ji) 2^(ref_i + ref_j - 43) by a fixed-order float64
+//     reduction.  The four 128 x 128 accumulators fill TMEM's 512 columns.
+//     In the register-staged kernel the double-float C (128 KB) sits in
+//     shared memory beside two 32-column digit stages, so the converting
+//     threads keep their registers for a two-chunk prefetch; the tensor-map
+//     kernel (L == 1) keeps C in registers and its raw input in a ring of
+//     shared-memory slots.
 //
-// Both exponents are read on the device, so the step needs no host round
+// The exponents are read on the device, so the step needs no host round
 // trip.  The result is the Gram of Y rounded to 21 bits below each local
 // power of two (zero-mean rounding); the noise this adds to the tail
 // eigenvalues is ~ (J - R)/J 2^-42/12 (2^E_ig / rms)^2 of ||Y||^2, a few
@@ -46,7 +50,12 @@
 // its TMEM and returns.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "tcgen05.cuh"
@@ -71,6 +80,38 @@ constexpr int kTmemCols = 512;
 constexpr int kAccPerThread = kRows * kRows / kThreads;  // C entries each thread drains (32)
 constexpr int kZeroExp = -4000;    // exponent of an all-zero row (see exp_above)
 constexpr uint32_t kIdesc = idesc_bf16(kRows, kRows);
+
+// Row exponent as the table stores it: E with max |y| < 2^E, raised to a
+// floor (float64: 2^-850, whose square is already below the smallest float64
+// subnormal; float32: 2^-100, so rows below it are rounded on the 2^-121
+// grid), or kZeroExp for an all-zero row.  The reference exponent of the
+// drain uses the same rule, so every scale 2^(E_i + E_j - 2 E) stays <= 1.
+__device__ __forceinline__ int table_exp(unsigned long long pattern, bool f64) {
+  const int e = exp_above(pattern, f64);
+  return e == kZeroExp ? e : max(e, f64 ? -850 : -100);
+}
+
+// Reference exponent of row i for this CTA: the largest table exponent of the
+// row over the CTA's groups [g_begin, g_end) (kZeroExp for a row that is zero
+// there).  The drain scales group g's products by 2^(E_ig - ref_i + E_jg -
+// ref_j) <= 1, so only a row's own range over the CTA's columns limits the
+// float32 exponent range of the double-float accumulators; the per-CTA
+// partial carries the factor 2^(ref_i + ref_j) to the reduction.  All threads
+// call it; ends with a barrier.
+__device__ void cta_row_ref(const int *__restrict__ Etab, int J, int64_t g_begin, int64_t g_end, int *ref,
+                            int *__restrict__ ref_out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < kRows) ref[tid] = kZeroExp;
+  __syncthreads();
+  const int i = tid % kRows;
+  if (i < J) {
+    int m = kZeroExp;
+    for (int64_t g = g_begin + tid / kRows; g < g_end; g += nt / kRows) m = max(m, __ldg(Etab + g * J + i));
+    atomicMax(&ref[i], m);
+  }
+  __syncthreads();
+  if (tid < kRows) ref_out[tid] = ref[tid];
+}
 
 struct SplitPlan {
   int J;
@@ -260,7 +301,7 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
   __syncthreads();
   unsigned gm = 0u;
   for (int i = tid; i < J; i += 256) {
-    E[g * J + i] = exp_above(mag_pattern(rmax[i], kF64), kF64);
+    E[g * J + i] = table_exp(mag_pattern(rmax[i], kF64), kF64);
     gm = max(gm, rmax[i]);
   }
 #pragma unroll
@@ -271,18 +312,18 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
 template <typename T, int kMode>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict__ y, int64_t L, SplitPlan p,
                                                             const int *__restrict__ Etab,
-                                                            const unsigned long long *__restrict__ gmax,
-                                                            double *__restrict__ ws, int *__restrict__ err) {
+                                                            int *__restrict__ refs, double *__restrict__ ws,
+                                                            int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   __shared__ __align__(8) unsigned long long mbar[kStages];
   __shared__ int rowexp[kRows];
+  __shared__ int ref[kRows];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
   unsigned char *stage_base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
   // double-float accumulators of C, element e of thread t at [e][t]
   float2 *cacc = reinterpret_cast<float2 *>(stage_base + kStages * kStageBytes);
-  constexpr bool kF64 = sizeof(T) == 8;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
@@ -303,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const int Eref = exp_above(*gmax, kF64);
 
   const int64_t c_begin = (int64_t)blockIdx.x * p.cols_per_split;
   const int64_t c_end = min(p.K, c_begin + p.cols_per_split);
   const int nchunks = (int)((c_end - c_begin + kChunk - 1) / kChunk);
   const int64_t stride_b = L * (int64_t)p.J;
+  cta_row_ref(Etab, p.J, c_begin / kGroup, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
 
   // converter role: row `row`, columns 8 kg .. 8 kg + 7 of each chunk
   const int row = tid % kRows;
@@ -394,13 +435,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
       if (!stop) {  // uniform across the CTA, so the .sync.aligned loads below never diverge
         fence_after();
         const float wts[4] = {0x1p28f, 0x1p22f, 0x1p14f, 0x1p7f};  // 2^28, 2 2^21, 2^14, 2^7
-        const int ei = rowexp[drow] - Eref;
+        const int ei = rowexp[drow] - ref[drow];
 #pragma unroll
         for (int part = 0; part < 4; ++part) {
           float sc[8], hi[8], lo[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const int x = ei + rowexp[32 * cb + 8 * part + e] - Eref;  // <= 0
+            const int x = ei + rowexp[32 * cb + 8 * part + e] - ref[32 * cb + 8 * part + e];  // <= 0
             sc[e] = x < -120 ? 0.f : __int_as_float((127 + x) << 23);
             const float2 a = cacc[(8 * part + e) * kThreads + tid];
             hi[e] = a.x;
@@ -449,18 +490,320 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
     if (tid == 0) atomicExch(err, 1);
     return;
   }
-  // per-CTA C (not yet symmetrised), row-major 128 x 128
-  double *dst = ws + (size_t)blockIdx.x * kRows * kRows + (size_t)drow * kRows + 32 * cb;
+  // per-CTA C (not yet symmetrised) as double-float pairs, row-major 128 x 128
+  float2 *dst = reinterpret_cast<float2 *>(ws) + (size_t)blockIdx.x * kRows * kRows + (size_t)drow * kRows + 32 * cb;
 #pragma unroll
-  for (int e = 0; e < kAccPerThread; ++e) {
-    const float2 a = cacc[e * kThreads + tid];
-    dst[e] = (double)a.x + (double)a.y;
-  }
+  for (int e = 0; e < kAccPerThread; ++e) dst[e] = cacc[e * kThreads + tid];
 }
 
-// S = (sum of the per-CTA C + C^T) 2^(2E - 43); NaN throughout when the
-// largest magnitude is not finite (Y holds Inf or NaN).
-__global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, int nsplit, int J,
+// ---------------------------------------------------------------------------
+// L == 1 with 16-byte column strides (J sizeof(T) a multiple of 16, Y 16-byte
+// aligned): the unfolding is a 2-D tensor of K columns of J contiguous
+// entries.  Thread 0 has the tensor-memory accelerator copy each chunk as one
+// 128 x 32 box (cp.async.bulk.tensor; rows >= J and columns >= K arrive as
+// zeros) into a ring of kRing shared-memory slots, completion counted in bytes
+// on the slot's mbarrier: the loads in flight are not bounded by registers,
+// every shared load of the conversion has a constant offset and the ragged
+// edges need no predicates.
+// Every thread converts row tid % 128, columns 8 (tid / 128) .. + 7 of a
+// chunk from shared memory:
+//   * f = |y| 2^(21 - E) is built as a float straight from the bits (the
+//     exponent field rebased by one integer subtraction clamped at zero, the
+//     significand cut to 24 bits with the last bit set, i.e. rounded to odd,
+//     so that rounding f to an integer is the correct rounding of y 2^(21-E),
+//     ties away from zero);
+//   * digits s1 = rn(f 2^-14), s2 = rn((f - 2^14 s1) 2^-7), s3 = rn(rest) by
+//     magic-number rounding, packed to BF16 pairs; 2 s3 and s3 / 256 are
+//     exact BF16 pair products of the packed s3.
+// The digit tiles A1, A2, 2 A3, A3 / 256 lie back to back with one
+// row-group stride, so [A1; A2] and [A2; 2 A3] are N = 256 operands and a
+// K-step takes four MMAs:
+//   D[0, 256)   = A1 [A1; A2]^T           (acc0, acc1)
+//   D[256, 512) = A2 [A2; 2 A3]^T         (acc2 part, acc3 part)
+//   D[256, 384) += A1 (2 A3)^T            (acc2)
+//   D[384, 512) += (2 A3) (A3 / 256)^T    (acc3)
+// At a group's end each thread folds its 32 entries into double-float
+// registers: the exact levels are merged into p 2^28 + r 2^7 with p an exact
+// integer below 2^24 (digit carries moved up by magic-number rounding), so
+// one TwoSum per entry and group replaces one per level.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 4;                                  // raw slots
+constexpr int kRawBytes = kChunk * kRows * 8;             // one slot: 32 columns of J <= 128 entries
+constexpr size_t kBulkSmemBytes = (size_t)kRing * kRawBytes + (size_t)kStages * kStageBytes + 1024;
+constexpr uint32_t kIdesc256 = idesc_bf16(kRows, 2 * kRows);
+constexpr float kMagic = 12582912.0f;                     // 1.5 2^23: adding it rounds |x| < 2^22 to an integer
+
+// f = |y| 2^(21 - E) with the sign of y, rounded to odd at 24 bits (see above).
+// cvt = (E + 875) << 20, or 2047 << 20 for an all-zero row (every entry then
+// gives |f| < 2^-126).  Entries below 2^(E - 23) give |f| < 1/4.
+__device__ __forceinline__ float scaled_float(double y, int cvt) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int x = max((int)(hi & 0x7FFFFFFFu) - cvt, 0);
+  return __uint_as_float(__funnelshift_l(lo, (unsigned)x, 3) | 1u | (hi & 0x80000000u));
+}
+// float: cvt = (21 - E) << 23, or -(255 << 23) for an all-zero row; values
+// that would fall below 1/16 become 1/16 (then rounded to 0).
+__device__ __forceinline__ float scaled_float(float y, int cvt) {
+  const unsigned b = __float_as_uint(y);
+  const int x = max((int)(b & 0x7FFFFFFFu) + cvt, 0x3D800000);
+  return __uint_as_float((unsigned)x | 1u | (b & 0x80000000u));
+}
+template <typename T>
+__device__ __forceinline__ int scaled_float_param(int e) {
+  if constexpr (sizeof(T) == 8) return e == kZeroExp ? (2047 << 20) : (e + 875) << 20;
+  else return e == kZeroExp ? -(255 << 23) : (21 - e) << 23;
+}
+
+// balanced digits of rn(f): f - rn(f) = r - s3 exactly, |s1| <= 128, |s2|, |s3| <= 64
+__device__ __forceinline__ void split3(float f, float &s1, float &s2, float &s3) {
+  s1 = __fsub_rn(__fmaf_rn(f, 0x1p-14f, kMagic), kMagic);
+  const float r1 = __fmaf_rn(s1, -16384.0f, f);
+  s2 = __fsub_rn(__fmaf_rn(r1, 0x1p-7f, kMagic), kMagic);
+  const float r2 = __fmaf_rn(s2, -128.0f, r1);
+  s3 = __fsub_rn(__fadd_rn(r2, kMagic), kMagic);
+}
+
+__device__ __forceinline__ uint32_t bf16x2_mul(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Row `row`, columns 8 kg .. 8 kg + 7 of the chunk in `raw` (column c of row
+// i at raw[c 128 + i]) as digits into the four tiles at st.
+template <typename T>
+__device__ __forceinline__ void convert_bulk(const T *raw, int row, int kg, int cvt, unsigned char *st) {
+  uint32_t w[kTiles][4];
+  const T *src = raw + row + 8 * kg * kRows;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) {
+    float a1, a2, a3, b1, b2, b3;
+    split3(scaled_float(src[k * kRows], cvt), a1, a2, a3);
+    split3(scaled_float(src[(k + 1) * kRows], cvt), b1, b2, b3);
+    const uint32_t p3 = bf16_pair(a3, b3);
+    w[0][k >> 1] = bf16_pair(a1, b1);
+    w[1][k >> 1] = bf16_pair(a2, b2);
+    w[2][k >> 1] = bf16x2_mul(p3, 0x40004000u);  // 2 s3
+    w[3][k >> 1] = bf16x2_mul(p3, 0x3B803B80u);  // s3 / 256
+  }
+  const int off = (row >> 3) * kSbo + kg * 128 + (row & 7) * 16;
+#pragma unroll
+  for (int t = 0; t < kTiles; ++t)
+    *reinterpret_cast<uint4 *>(st + t * kTileBytes + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+// (H, Lo) += (2^28 a0 + 2^22 a1 + 2^14 a2 + 2^7 a3) 2^x with sc28 = 2^(28 + x).
+// a0, a1, a2 are exact integers (|a0| <= 2^23, |a1| <= 2^22, |a2| < 10.5e6):
+// a1 = 64 a1h + a1l and 256 a1l + a2 = 2^14 qh + ql move their high parts
+// into p2 = a0 + a1h + qh (exact, < 2^24); r = 128 ql + a3 is the one rounded
+// step (its error is ~2^-45 of the group's largest term).
+__device__ __forceinline__ void drain_entry(float a0, float a1, float a2, float a3, float sc28, float &H,
+                                            float &Lo) {
+  const float a1h = __fsub_rn(__fmaf_rn(a1, 0x1p-6f, kMagic), kMagic);
+  const float a1l = __fmaf_rn(a1h, -64.0f, a1);
+  const float q = __fmaf_rn(a1l, 256.0f, a2);
+  const float qh = __fsub_rn(__fmaf_rn(q, 0x1p-14f, kMagic), kMagic);
+  const float ql = __fmaf_rn(qh, -16384.0f, q);
+  const float p2 = __fadd_rn(__fadd_rn(a0, a1h), qh);
+  const float r = __fmaf_rn(ql, 128.0f, a3);
+  const float hg = __fmul_rn(p2, sc28);
+  const float lg = __fmul_rn(r, __fmul_rn(sc28, 0x1p-21f));
+  const float s = __fadd_rn(H, hg);  // TwoSum(H, hg)
+  const float bp = __fsub_rn(s, H);
+  const float e = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bp)), __fsub_rn(hg, bp));
+  const float l = __fadd_rn(Lo, __fadd_rn(e, lg));
+  const float t = __fadd_rn(s, l);  // renormalise
+  Lo = __fsub_rn(l, __fsub_rn(t, s));
+  H = t;
+}
+
+// four 32-lane x 4-column TMEM loads (the four levels of 4 entries), then the wait
+__device__ __forceinline__ void tmem_ld4x4(uint32_t taddr, uint32_t (&r)[4][4]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%17];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%18];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%19];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]),
+        "=r"(r[1][3]), "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[3][0]), "=r"(r[3][1]),
+        "=r"(r[3][2]), "=r"(r[3][3])
+      : "r"(taddr), "r"(taddr + 128), "r"(taddr + 256), "r"(taddr + 384)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// 2-D tensor-map box load into shared memory, completion counted on mbar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_constant__ CUtensorMap ymap, SplitPlan p,
+                                                                 const int *__restrict__ Etab,
+                                                                 int *__restrict__ refs, double *__restrict__ ws,
+                                                                 int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  __shared__ __align__(8) unsigned long long raw_full[kRing];
+  __shared__ __align__(8) unsigned long long mma_done[kStages];
+  __shared__ __align__(16) int rowexp[2][kRows];  // E_ig of the current and the next group
+  __shared__ __align__(16) int relexp[2][kRows];  // E_ig - ref_i
+  __shared__ int ref[kRows];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int stop;
+  // offsets from dsmem keep the shared address space visible (shared loads and stores)
+  unsigned char *ring = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
+  unsigned char *stages = ring + kRing * kRawBytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int J = p.J;
+  const int64_t c_begin = (int64_t)blockIdx.x * p.cols_per_split;
+  const int64_t c_end = min(p.K, c_begin + p.cols_per_split);
+  const int nchunks = (int)((c_end - c_begin + kChunk - 1) / kChunk);
+  const int64_t g0 = c_begin / kGroup;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kRing; ++s) mbar_init(smem_addr(&raw_full[s]), 1);
+    for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&mma_done[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  cta_row_ref(Etab, J, g0, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
+  // exponents of the group starting at chunk ch go to buffer (ch / kDrainChunks) & 1
+  auto load_exps = [&](int ch) {
+    if (tid < kRows) {
+      const int gi = ch / kDrainChunks;
+      const int e = tid < J ? Etab[(g0 + gi) * J + tid] : kZeroExp;
+      rowexp[gi & 1][tid] = e;
+      relexp[gi & 1][tid] = e - ref[tid];
+    }
+  };
+  load_exps(0);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // chunk ch -> slot ch % kRing as the box at (row 0, column c_begin + 32 ch) (thread 0)
+  auto issue_copy = [&](int ch) {
+    const int slot = ch % kRing;
+    const uint32_t bar = smem_addr(&raw_full[slot]);
+    mbar_expect_tx(bar, (uint32_t)(kChunk * kRows * sizeof(T)));
+    tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < kRing && issued < nchunks; ++issued) issue_copy(issued);
+
+  const int row = tid & (kRows - 1), kg = tid >> 7;       // converter role
+  const int q = warp & 3, cb = warp >> 2;                  // drain role: TMEM lanes 32 q.., columns 32 cb..
+  const int drow = 32 * q + lane;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cb);
+  float H[kAccPerThread], Lo[kAccPerThread];
+#pragma unroll
+  for (int e = 0; e < kAccPerThread; ++e) H[e] = Lo[e] = 0.f;
+
+  int cvt = 0, last_committed = -1;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int slot = ch % kRing, stg = ch & 1, in_group = ch % kDrainChunks, gi = ch / kDrainChunks;
+    if (in_group == 0) {
+      cvt = scaled_float_param<T>(rowexp[gi & 1][row]);
+      // the next group's exponents go to the other buffer, read after a later barrier
+      if (ch + kDrainChunks < nchunks) load_exps(ch + kDrainChunks);
+    }
+    bool ok = mbar_wait(smem_addr(&raw_full[slot]), (uint32_t)(ch / kRing) & 1u);
+    if (ok && ch >= 2) ok = mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)((ch - 2) >> 1) & 1u);
+    if (ok)
+      convert_bulk<T>(reinterpret_cast<const T *>(ring + slot * kRawBytes), row, kg, cvt, stages + stg * kStageBytes);
+    else
+      stop = 1;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (stop) break;
+    if (tid == 0) {
+      if (issued < nchunks) issue_copy(issued++);  // slot ch % kRing has been read by every thread
+      fence_after();
+      const uint32_t base = smem_addr(stages + stg * kStageBytes);
+#pragma unroll
+      for (int s = 0; s < kChunk / 16; ++s) {
+        const uint32_t acc = (in_group == 0 && s == 0) ? 0u : 1u;
+        const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * s, 128, kSbo);
+        const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * s, 128, kSbo);
+        mma_bf16(tmem + 0, a1, a1, kIdesc256, acc);
+        mma_bf16(tmem + 256, a2, a2, kIdesc256, acc);
+        mma_bf16(tmem + 256, a1, a3x2, kIdesc, 1u);
+        mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
+      }
+      mma_commit(smem_addr(&mma_done[stg]));
+    }
+    last_committed = ch;
+    if (in_group == kDrainChunks - 1 || ch == nchunks - 1) {
+      const bool done = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)(ch >> 1) & 1u));
+      if (done) {  // warp-uniform, so the .sync.aligned loads below never diverge
+        fence_after();
+        const int xi = relexp[gi & 1][drow] + 155;  // exponent field of 2^(28 + E_ig - ref_i)
+#pragma unroll
+        for (int part = 0; part < 8; ++part) {
+          uint32_t r[4][4];
+          tmem_ld4x4(taddr + 4 * part, r);
+          const int4 ej = *reinterpret_cast<const int4 *>(&relexp[gi & 1][32 * cb + 4 * part]);
+          const int ejs[4] = {ej.x, ej.y, ej.z, ej.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float sc28 = __int_as_float(max(xi + ejs[e], 0) << 23);
+            drain_entry(__uint_as_float(r[0][e]), __uint_as_float(r[1][e]), __uint_as_float(r[2][e]),
+                        __uint_as_float(r[3][e]), sc28, H[4 * part + e], Lo[4 * part + e]);
+          }
+        }
+      } else {
+        stop = 1;
+      }
+      fence_before();
+      __syncthreads();
+      if (stop) break;
+    }
+  }
+  if (stop && tid == 0) {
+    // let our own MMAs and bulk copies finish (bounded) before TMEM and shared memory go
+    if (last_committed >= 0) mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)(last_committed >> 1) & 1u);
+    for (int c = max(0, issued - kRing); c < issued; ++c)
+      mbar_wait(smem_addr(&raw_full[c % kRing]), (uint32_t)(c / kRing) & 1u);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (stop) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  // per-CTA C (not yet symmetrised) as double-float pairs, row-major 128 x 128
+  float2 *dst = reinterpret_cast<float2 *>(ws) + (size_t)blockIdx.x * kRows * kRows + (size_t)drow * kRows + 32 * cb;
+#pragma unroll
+  for (int e = 0; e < kAccPerThread; ++e) dst[e] = make_float2(H[e], Lo[e]);
+}
+
+// S_ij = sum over CTAs of (C_ij + C_ji) 2^(ref_i + ref_j - 43); NaN throughout
+// when the largest magnitude is not finite (Y holds Inf or NaN).
+__global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, const int *__restrict__ refs,
+                                                           int nsplit, int J,
                                                            const unsigned long long *__restrict__ gmax, int is_f64,
                                                            double *__restrict__ S) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -468,13 +811,15 @@ __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restr
   const int i = idx % J, j = idx / J;
   double s = 0.0;
   for (int sp = 0; sp < nsplit; ++sp) {
-    const double *c = ws + (size_t)sp * kRows * kRows;
-    s += c[i * kRows + j] + c[j * kRows + i];
+    const float2 *c = reinterpret_cast<const float2 *>(ws) + (size_t)sp * kRows * kRows;
+    const float2 a = c[i * kRows + j], b = c[j * kRows + i];
+    const int ri = refs[sp * kRows + i], rj = refs[sp * kRows + j];
+    if (ri != kZeroExp && rj != kZeroExp)
+      s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - 43);
   }
   const unsigned long long gm = *gmax;
   const bool finite = is_f64 ? gm < 0x7FF0000000000000ull : gm < 0x7F800000ull;
-  const int E = exp_above(gm, is_f64 != 0);
-  S[i + (int64_t)J * j] = !finite ? __longlong_as_double(0x7FF8000000000000ll) : (E == kZeroExp ? 0.0 : ldexp(s, 2 * E - 43));
+  S[i + (int64_t)J * j] = finite ? s : __longlong_as_double(0x7FF8000000000000ll);
 }
 
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kRows * kRows * sizeof(float2) + 1024;
@@ -491,10 +836,12 @@ SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   return p;
 }
 
-// workspace (in doubles): per-CTA partials | exponent table (ints) | gmax | error flag
+// workspace (in doubles): per-CTA partials (double-float pairs) | exponent
+// table (ints) | per-CTA row reference exponents (ints) | gmax | error flag
 struct SplitWs {
   double *partials;
   int *table;
+  int *refs;
   unsigned long long *gmax;
   int *err;
 };
@@ -502,11 +849,13 @@ struct SplitWs {
 SplitWs split_ws(double *d_ws, const SplitPlan &p) {
   const int64_t np = (int64_t)p.nsplit * kRows * kRows;
   const int64_t tab = (p.ngroups * p.J + 1) / 2;
+  const int64_t nref = (int64_t)p.nsplit * kRows / 2;
   SplitWs w;
   w.partials = d_ws;
   w.table = reinterpret_cast<int *>(d_ws + np);
-  w.gmax = reinterpret_cast<unsigned long long *>(d_ws + np + tab);
-  w.err = reinterpret_cast<int *>(d_ws + np + tab + 1);
+  w.refs = reinterpret_cast<int *>(d_ws + np + tab);
+  w.gmax = reinterpret_cast<unsigned long long *>(d_ws + np + tab + nref);
+  w.err = reinterpret_cast<int *>(d_ws + np + tab + nref + 1);
   return w;
 }
 
@@ -515,9 +864,56 @@ int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &
                    cudaStream_t s) {
   (void)dev;
   TK_CUDA(cudaFuncSetAttribute(k_gram_split<T, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-  k_gram_split<T, kMode><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const T *>(y), L, p, w.table, w.gmax,
+  k_gram_split<T, kMode><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const T *>(y), L, p, w.table, w.refs,
                                                                 w.partials, w.err);
   TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); false when unavailable or the map is refused.
+bool encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t dim0, uint64_t dim1,
+                    uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
+  const cuuint64_t gdim[2] = {dim0, dim1};
+  const cuuint64_t gstride[1] = {stride1_bytes};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estride[2] = {1, 1};
+  return encode(map, dt, 2, const_cast<void *>(base), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor-map kernel takes L == 1 with 16-byte column strides, a 16-byte
+// aligned Y and K < 2^31; TUCKER_GRAM_SPLIT_KERNEL=regs forces the
+// register-staged kernel.  Returns 1 when it ran, 0 when it does not apply.
+template <typename T>
+int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cudaStream_t s, bool *ran) {
+  static const bool regs = [] {
+    const char *e = std::getenv("TUCKER_GRAM_SPLIT_KERNEL");
+    return e && std::strcmp(e, "regs") == 0;
+  }();
+  *ran = false;
+  const uint64_t col_bytes = (uint64_t)p.J * sizeof(T);
+  if (regs || col_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(y) % 16 != 0 || p.K >= (1ll << 31)) return TUCKER_OK;
+  CUtensorMap map;
+  if (!encode_tmap_2d(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, y,
+                      (uint64_t)p.J, (uint64_t)p.K, col_bytes, kRows, kChunk))
+    return TUCKER_OK;
+  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kBulkSmemBytes));
+  k_gram_split_bulk<T><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
+  TK_LAUNCHED();
+  *ran = true;
   return TUCKER_OK;
 }
 
@@ -525,7 +921,7 @@ int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &
 
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   const SplitPlan p = split_plan(L, J, B, dev);
-  return (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + 4;
+  return (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + (int64_t)p.nsplit * kRows / 2 + 4;
 }
 
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
@@ -557,18 +953,23 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   TK_LAUNCHED();
   if (prof) prof->end(0.0, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM);
-  if (f64) {
+  bool ran = false;
+  if (L == 1) {
+    if (f64) TK_CHECK(run_gram_split_bulk<double>(y, p, w, s, &ran));
+    else TK_CHECK(run_gram_split_bulk<float>(y, p, w, s, &ran));
+  }
+  if (!ran && f64) {
     if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided>(y, L, p, w, dev, s)));
     else if (mode == kColsContig) TK_CHECK((run_gram_split<double, kColsContig>(y, L, p, w, dev, s)));
     else TK_CHECK((run_gram_split<double, kColsGeneric>(y, L, p, w, dev, s)));
-  } else {
+  } else if (!ran) {
     if (mode == kColsStrided) TK_CHECK((run_gram_split<float, kColsStrided>(y, L, p, w, dev, s)));
     else if (mode == kColsContig) TK_CHECK((run_gram_split<float, kColsContig>(y, L, p, w, dev, s)));
     else TK_CHECK((run_gram_split<float, kColsGeneric>(y, L, p, w, dev, s)));
   }
   if (prof) prof->end((double)J * (J + 1) * (double)p.K, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
-  k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(w.partials, p.nsplit, (int)J, w.gmax, f64,
+  k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
                                                                       d_S);
   TK_LAUNCHED();
   if (prof) prof->end((double)p.nsplit * J * J * 2, (double)p.nsplit * kRows * kRows * 8, 1);

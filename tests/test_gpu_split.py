@@ -46,7 +46,9 @@ def split_bound(y, L, J, B):
 
 
 @pytest.mark.parametrize("L,J,B", [(1, 128, 5000), (1, 64, 4096), (40, 128, 33), (7, 13, 5), (1600, 48, 3),
-                                   (640, 32, 1), (1, 1, 1), (3, 100, 777), (1, 128, 64 * 152 * 9 + 17)])
+                                   (640, 32, 1), (1, 1, 1), (3, 100, 777), (1, 128, 64 * 152 * 9 + 17),
+                                   # L == 1 tensor-map kernel: smallest J, ragged J and K, one column
+                                   (1, 2, 3001), (1, 34, 2049), (1, 126, 1), (1, 13, 700)])
 def test_gram_split_bound(gpu_lib, L, J, B):
     rng = np.random.default_rng(L * 3 + J * 5 + B)
     y = rng.standard_normal(L * J * B)
@@ -70,9 +72,9 @@ def test_gram_split_exact_on_leading_digit_inputs(gpu_lib):
     assert np.array_equal(s * 2 ** 14, exact.astype(np.float64))
 
 
-def test_gram_split_f32(gpu_lib):
-    rng = np.random.default_rng(9)
-    L, J, B = 5, 96, 400
+@pytest.mark.parametrize("L,J,B", [(5, 96, 400), (1, 36, 1500), (1, 128, 33 * 512 + 5), (1, 30, 100)])
+def test_gram_split_f32(gpu_lib, L, J, B):
+    rng = np.random.default_rng(9 + L + J)
     y = rng.standard_normal(L * J * B).astype(np.float32)
     s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
     bound, ref = split_bound(y, L, J, B)
@@ -102,9 +104,29 @@ def test_gram_split_local_exponents(gpu_lib):
     assert np.all(np.abs(s - ref) <= bound)
 
 
+@pytest.mark.parametrize("L,dtype,e", [(1, np.float64, 400), (3, np.float64, 400), (1, np.float32, 55),
+                                       (5, np.float32, 55)])
+def test_gram_split_rows_of_far_apart_magnitudes(gpu_lib, L, dtype, e):
+    """Rows 2^(2e) apart keep their own relative accuracy: every row's products are
+    scaled by the row's own reference exponent, not by the largest row's."""
+    rng = np.random.default_rng(15 + L + e)
+    J, B = 32, 1500
+    scale = 2.0 ** np.where(np.arange(J) % 2 == 0, e, -e) * 2.0 ** (np.arange(J) % 5)
+    y = (rng.standard_normal((L, J, B)) * scale[None, :, None]).astype(dtype).ravel(order="F")
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    bound, ref = split_bound(y, L, J, B)
+    assert np.all(np.abs(s - ref) <= bound)
+    assert np.all(np.diag(s) > 0)
+
+
 def test_gram_split_zero_and_nonfinite(gpu_lib):
     z = gpu_lib.gram_split(dev(np.zeros(3 * 40 * 700)), 3, 40, 700).cpu().numpy()
     assert np.array_equal(z, np.zeros((40, 40)))
+    z = gpu_lib.gram_split(dev(np.zeros(64 * 900)), 1, 64, 900).cpu().numpy()
+    assert np.array_equal(z, np.zeros((64, 64)))
+    y = np.random.default_rng(14).standard_normal(64 * 900)
+    y[64 * 600 + 5] = np.inf
+    assert np.isnan(gpu_lib.gram_split(dev(y), 1, 64, 900).cpu().numpy()).all()
     y = np.random.default_rng(13).standard_normal(2 * 16 * 300)
     y[777] = np.nan
     s = gpu_lib.gram_split(dev(y), 2, 16, 300).cpu().numpy()
