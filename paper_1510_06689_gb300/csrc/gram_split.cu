@@ -716,67 +716,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
 #pragma unroll
   for (int e = 0; e < kAccPerThread; ++e) H[e] = Lo[e] = 0.f;
 
-  int cvt = 0, last_committed = -1;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int slot = ch % kRing, stg = ch & 1, in_group = ch % kDrainChunks, gi = ch / kDrainChunks;
-    if (in_group == 0) {
-      cvt = scaled_float_param<T>(rowexp[gi & 1][row]);
-      // the next group's exponents go to the other buffer, read after a later barrier
-      if (ch + kDrainChunks < nchunks) load_exps(ch + kDrainChunks);
-    }
-    bool ok = mbar_wait(smem_addr(&raw_full[slot]), (uint32_t)(ch / kRing) & 1u);
-    if (ok && ch >= 2) ok = mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)((ch - 2) >> 1) & 1u);
-    if (ok)
-      convert_bulk<T>(reinterpret_cast<const T *>(ring + slot * kRawBytes), row, kg, cvt, stages + stg * kStageBytes);
-    else
-      stop = 1;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (stop) break;
-    if (tid == 0) {
-      if (issued < nchunks) issue_copy(issued++);  // slot ch % kRing has been read by every thread
+  // fold the group's four levels into the double-float registers (warp-uniform `ok`)
+  auto drain = [&](int gi, bool ok) {
+    if (ok) {  // warp-uniform, so the .sync.aligned loads below never diverge
       fence_after();
-      const uint32_t base = smem_addr(stages + stg * kStageBytes);
+      const int xi = relexp[gi & 1][drow] + 155;  // exponent field of 2^(28 + E_ig - ref_i)
 #pragma unroll
-      for (int s = 0; s < kChunk / 16; ++s) {
-        const uint32_t acc = (in_group == 0 && s == 0) ? 0u : 1u;
-        const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * s, 128, kSbo);
-        const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * s, 128, kSbo);
-        const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * s, 128, kSbo);
-        const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * s, 128, kSbo);
-        mma_bf16(tmem + 0, a1, a1, kIdesc256, acc);
-        mma_bf16(tmem + 256, a2, a2, kIdesc256, acc);
-        mma_bf16(tmem + 256, a1, a3x2, kIdesc, 1u);
-        mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
-      }
-      mma_commit(smem_addr(&mma_done[stg]));
-    }
-    last_committed = ch;
-    if (in_group == kDrainChunks - 1 || ch == nchunks - 1) {
-      const bool done = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)(ch >> 1) & 1u));
-      if (done) {  // warp-uniform, so the .sync.aligned loads below never diverge
-        fence_after();
-        const int xi = relexp[gi & 1][drow] + 155;  // exponent field of 2^(28 + E_ig - ref_i)
+      for (int part = 0; part < 8; ++part) {
+        uint32_t r[4][4];
+        tmem_ld4x4(taddr + 4 * part, r);
+        const int4 ej = *reinterpret_cast<const int4 *>(&relexp[gi & 1][32 * cb + 4 * part]);
+        const int ejs[4] = {ej.x, ej.y, ej.z, ej.w};
 #pragma unroll
-        for (int part = 0; part < 8; ++part) {
-          uint32_t r[4][4];
-          tmem_ld4x4(taddr + 4 * part, r);
-          const int4 ej = *reinterpret_cast<const int4 *>(&relexp[gi & 1][32 * cb + 4 * part]);
-          const int ejs[4] = {ej.x, ej.y, ej.z, ej.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float sc28 = __int_as_float(max(xi + ejs[e], 0) << 23);
-            drain_entry(__uint_as_float(r[0][e]), __uint_as_float(r[1][e]), __uint_as_float(r[2][e]),
-                        __uint_as_float(r[3][e]), sc28, H[4 * part + e], Lo[4 * part + e]);
-          }
+        for (int e = 0; e < 4; ++e) {
+          const float sc28 = __int_as_float(max(xi + ejs[e], 0) << 23);
+          drain_entry(__uint_as_float(r[0][e]), __uint_as_float(r[1][e]), __uint_as_float(r[2][e]),
+                      __uint_as_float(r[3][e]), sc28, H[4 * part + e], Lo[4 * part + e]);
         }
-      } else {
-        stop = 1;
       }
-      fence_before();
+    } else {
+      stop = 1;
+    }
+    fence_before();
+    __syncthreads();
+  };
+
+  // Chunks go four at a time (the ring depth), so slot, stage and every
+  // mbarrier parity below are compile-time constants: chunk ch0 + u uses slot
+  // u, digit stage u & 1, the ring phase (ch0 / 4) & 1 and, for the stage,
+  // commit number (ch0 + u) >> 1 (parity (u >> 1) & 1, as ch0 / 2 is even).
+  // Groups are 16 chunks, so a group starts only at u == 0 and ends at u == 3
+  // (or at the last chunk, drained after the loop).
+  int cvt = 0, last_committed = -1;
+  bool tail_drain = false;
+  for (int ch0 = 0; ch0 < nchunks && !stop; ch0 += kRing) {
+    const uint32_t ring_par = (uint32_t)(ch0 / kRing) & 1u;
+#pragma unroll
+    for (int u = 0; u < kRing; ++u) {
+      const int ch = ch0 + u;
+      if (ch >= nchunks) break;
+      const int in_group = ch % kDrainChunks, gi = ch / kDrainChunks;
+      if (u == 0 && in_group == 0) {
+        cvt = scaled_float_param<T>(rowexp[gi & 1][row]);
+        // the next group's exponents go to the other buffer, read after a later barrier
+        if (ch + kDrainChunks < nchunks) load_exps(ch + kDrainChunks);
+      }
+      bool ok = mbar_wait(smem_addr(&raw_full[u]), ring_par);
+      if (ok && ch >= 2) ok = mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)(((u + 2) >> 1) & 1));
+      if (ok)
+        convert_bulk<T>(reinterpret_cast<const T *>(ring + u * kRawBytes), row, kg, cvt, stages + (u & 1) * kStageBytes);
+      else
+        stop = 1;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (stop) break;
+      if (tid == 0) {
+        if (issued < nchunks) issue_copy(issued++);  // slot u has been read by every thread
+        fence_after();
+        const uint32_t base = smem_addr(stages + (u & 1) * kStageBytes);
+#pragma unroll
+        for (int k = 0; k < kChunk / 16; ++k) {
+          const uint32_t acc = (u == 0 && in_group == 0 && k == 0) ? 0u : 1u;
+          const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * k, 128, kSbo);
+          const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * k, 128, kSbo);
+          const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * k, 128, kSbo);
+          const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * k, 128, kSbo);
+          mma_bf16(tmem + 0, a1, a1, kIdesc256, acc);
+          mma_bf16(tmem + 256, a2, a2, kIdesc256, acc);
+          mma_bf16(tmem + 256, a1, a3x2, kIdesc, 1u);
+          mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
+        }
+        mma_commit(smem_addr(&mma_done[u & 1]));
+      }
+      last_committed = ch;
+      if (u == kRing - 1 && in_group == kDrainChunks - 1) {
+        drain(gi, __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)((u >> 1) & 1))));
+        if (stop) break;
+      } else if (ch == nchunks - 1) {
+        tail_drain = true;
+      }
     }
+  }
+  if (tail_drain && !stop) {
+    const int ch = nchunks - 1;
+    drain(ch / kDrainChunks,
+          __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[ch & 1]), (uint32_t)(ch >> 1) & 1u)));
   }
   if (stop && tid == 0) {
     // let our own MMAs and bulk copies finish (bounded) before TMEM and shared memory go

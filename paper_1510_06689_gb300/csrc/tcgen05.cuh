@@ -168,7 +168,7 @@ __device__ __forceinline__ float round_float(float x) { return __fsub_rn(__fadd_
 
 // Two floats that BF16 holds exactly (at most 8 significant bits), packed.
 __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
-  return (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xFFFF0000u);
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);  // high halves of a and b
 }
 
 
