@@ -3,12 +3,16 @@
 //
 // GB300's float64 pipe issues ~2 FMAs per clock per SM, so a float64 Jacobi
 // of a 128 x 128 Gram (18 sweeps of 127 dependent steps) is bound by latency
-// and float64 throughput at once.  This solver moves the sweeps to float32
-// and restores float64 accuracy with matrix products spread over all SMs:
+// and float64 throughput at once.  This solver finds the eigenvectors in
+// float32 and restores float64 accuracy with matrix products spread over all
+// SMs:
 //
 //   level(A):  (A symmetric m x m, float64)
-//     1. X = eigenvectors of A / max|A| by a float32 parallel-order Jacobi
-//        (one CTA, shared memory; accurate to ~2^-24 max|A| / gap).
+//     1. X = eigenvectors of A / max|A| in float32 (one CTA, shared memory;
+//        accurate to ~2^-24 max|A| / gap): Householder tridiagonalization,
+//        multisection, inverse iteration, orthonormalisation by Householder
+//        QR and back-transformation (k_eig32_tri), or with
+//        TUCKER_EIG32=jacobi the parallel-order Jacobi sweeps (k_jacobi32).
 //     2. Iterative refinement of X in float64 (the symmetric-eigenproblem
 //        refinement step of Ogita and Aishima): with R = I - X^T X and
 //        S = X^T A X, the approximations l_i = s_ii / (1 - r_ii) and the
@@ -38,6 +42,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -214,6 +219,375 @@ __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restri
 size_t jacobi32_smem(int n) {
   const int m = (n + 3) & ~3, np = m / 2;
   return (size_t)(((m * (m + 1) + 3) & ~3) + m * m) * sizeof(float) + (size_t)np * (np + 1) / 2 * sizeof(int) + 16;
+}
+
+// ---------------------------------------------------------------------------
+// float32 tridiagonal eigensolver on A / max|A| (one CTA of kT32Threads),
+// the first stage of a level in place of the Jacobi sweeps: O(n^3) work once
+// instead of per sweep, every phase data-parallel over rows, columns or
+// eigenvalues, with 2-3 block barriers per reflector.
+//   1. Householder tridiagonalization T = Q1^T A Q1 (LAPACK's sytd2 order:
+//      H_k = I - tau_k v_k v_k^T, v_k(0) = 1, acting on rows k+1..n-1; the
+//      trailing block is updated as A22 -= v w^T + w v^T with
+//      w = p - (tau/2)(p^T v) v, p = tau A22 v).  v_k is kept below the
+//      subdiagonal of column k.
+//   2. Eigenvalues of T by multisection on Sturm counts (four threads per
+//      eigenvalue, five sub-intervals per round, 12 rounds: below 2^-26 ||T||).
+//   3. Eigenvectors of T by two steps of inverse iteration (thread i solves
+//      (T - l_i I) z = b with the LDL^T factorization of T - l_i I, pivots
+//      kept above 2^-23 ||T||, first from a fixed pseudo-random b).
+//   4. Inverse iteration leaves vectors of close eigenvalues far from
+//      orthogonal (~2^-23 ||T|| / gap; nearly parallel below the float32
+//      resolution), and the float64 refinement's cluster width grows with
+//      ||I - X^T X||, so the vectors, in descending eigenvalue order, are
+//      replaced by the Q factor of their Householder QR (signs kept): each
+//      keeps its direction up to the components along larger ones, and
+//      vectors that were nearly dependent become an orthonormal basis of the
+//      complement of the others.
+//   5. X = Q1 Z by the tridiagonalization's reflectors in reverse order.
+// Accuracy is float32's (~2^-23 ||A|| / gap), as the Jacobi sweeps gave; the
+// float64 refinement that follows does not depend on which one ran.
+// Writes X (float64, columns in descending eigenvalue order).
+// ---------------------------------------------------------------------------
+constexpr int kT32Threads = 512;
+
+// floats: A (n x (n+1)), Z (n x (n+1)), W (n x n), 4 x 128 partials, 10 n vectors
+size_t tri32_smem(int n) { return (size_t)(2 * n * (n + 1) + n * n + 4 * kMpMaxJ + 10 * n) * sizeof(float) + 64; }
+
+__device__ __forceinline__ float warp_sum32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// fixed pseudo-random start vector entry in [-1, 1) (integer hash of i, k)
+__device__ __forceinline__ float start_entry(int i, int k) {
+  uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)k + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return (float)(int)(h >> 8) * 0x1p-23f - 1.0f;
+}
+
+// Householder reflector of x (length m, x(i) at x[i * stride]) as every lane
+// of a warp computes it: tau, 1 / (alpha - beta) and beta (LAPACK's larfg:
+// H x = beta e_1, v(0) = 1, v(i) = x(i) / (alpha - beta); tau = 0 when
+// x(1..m-1) ~ 0).  The norm is formed from x / max|x|, so that squares of
+// small entries do not fall into the subnormal range (where beta^2 would no
+// longer be alpha^2 + ||x(1..)||^2 and H would not be orthogonal).
+__device__ __forceinline__ void warp_larfg(const float *x, int stride, int m, int lane, float &tau, float &scal,
+                                           float &beta) {
+  const float alpha = x[0];
+  float mx = 0.f;
+  for (int i = 1 + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(x[i * stride]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  tau = 0.f;
+  scal = 0.f;
+  beta = alpha;
+  // entries below 2^-100 (the inputs are scaled to at most 1) are far below
+  // float32 resolution and are taken as zero; this also keeps 1 / max finite
+  if (mx > 0x1p-100f) {  // uniform: every lane has the same mx
+    const float sx = 1.f / fmaxf(mx, fabsf(alpha));
+    float sg = 0.f;
+    for (int i = 1 + lane; i < m; i += 32) {
+      const float v = x[i * stride] * sx;
+      sg = fmaf(v, v, sg);
+    }
+    sg = warp_sum32(sg);
+    const float a = alpha * sx;
+    const float nrm = sqrtf(fmaf(a, a, sg)) / sx;
+    beta = alpha >= 0.f ? -nrm : nrm;
+    tau = (beta - alpha) / beta;
+    scal = 1.f / (alpha - beta);
+  }
+}
+
+// Apply H = I - tau v v^T (v(0) = 1 at row r0; v(r) for r > r0 at
+// vcol[r * vstride]) from the left to columns c0..n-1 of M (row-major, ld),
+// rows r0..n-1.  Thread (column c = tid % 128, part = tid / 128) takes rows
+// r0 + part, r0 + part + 4, ...; ends with a barrier.
+__device__ __forceinline__ void apply_reflector(float *__restrict__ M, int ld, int n, int r0, int c0, float tau,
+                                                const float *__restrict__ vcol, int vstride, float *__restrict__ pd) {
+  const int tid = threadIdx.x, c = tid & (kMpMaxJ - 1), part = tid >> 7;
+  const bool mine = c >= c0 && c < n;
+  float acc = 0.f;
+  if (mine) {
+    if (part == 0) acc = M[r0 * ld + c];  // v(0) = 1
+    int r = r0 + (part == 0 ? 4 : part);
+    for (; r + 12 < n; r += 16) {  // four rows of this part at a time, loads first
+      const float v0 = vcol[r * vstride], v1 = vcol[(r + 4) * vstride], v2 = vcol[(r + 8) * vstride],
+                  v3 = vcol[(r + 12) * vstride];
+      const float m0 = M[r * ld + c], m1 = M[(r + 4) * ld + c], m2 = M[(r + 8) * ld + c], m3 = M[(r + 12) * ld + c];
+      acc = fmaf(v0, m0, fmaf(v1, m1, fmaf(v2, m2, fmaf(v3, m3, acc))));
+    }
+    for (; r < n; r += 4) acc = fmaf(vcol[r * vstride], M[r * ld + c], acc);
+  }
+  pd[part * kMpMaxJ + c] = acc;
+  __syncthreads();
+  if (mine) {
+    const float s = tau * (pd[c] + pd[kMpMaxJ + c] + pd[2 * kMpMaxJ + c] + pd[3 * kMpMaxJ + c]);
+    if (part == 0) M[r0 * ld + c] -= s;
+    int r = r0 + (part == 0 ? 4 : part);
+    for (; r + 12 < n; r += 16) {
+      const float v0 = vcol[r * vstride], v1 = vcol[(r + 4) * vstride], v2 = vcol[(r + 8) * vstride],
+                  v3 = vcol[(r + 12) * vstride];
+      const float m0 = M[r * ld + c], m1 = M[(r + 4) * ld + c], m2 = M[(r + 8) * ld + c], m3 = M[(r + 12) * ld + c];
+      M[r * ld + c] = fmaf(-s, v0, m0);
+      M[(r + 4) * ld + c] = fmaf(-s, v1, m1);
+      M[(r + 8) * ld + c] = fmaf(-s, v2, m2);
+      M[(r + 12) * ld + c] = fmaf(-s, v3, m3);
+    }
+    for (; r < n; r += 4) M[r * ld + c] = fmaf(-s, vcol[r * vstride], M[r * ld + c]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kT32Threads) k_eig32_tri(const double *__restrict__ A, int lda, int n,
+                                                           double *__restrict__ X, int ldx) {
+  extern __shared__ __align__(16) float smt[];
+  const int ld = n + 1;
+  float *Af = smt;           // n x ld, row-major
+  float *Z = Af + n * ld;    // n x ld, Z[k ld + c]: row k of eigenvector c of T
+  float *W = Z + n * ld;     // n x n, W[k n + i]: L factor of T - l_i I; later the QR reflectors
+  float *pd = W + n * n;     // 4 x 128 partial sums
+  float *d = pd + 4 * kMpMaxJ, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *vs = lam + n,
+        *qtau = vs + n, *sgn = qtau + n;
+  __shared__ float red[32];
+  __shared__ float sc[4];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+
+  // ---- load A / max|A| (upper triangle, mirrored)
+  float mx = 0.f;
+  for (int idx = tid; idx < n * n; idx += nt) mx = fmaxf(mx, (float)fabs(A[(idx % n) + (int64_t)lda * (idx / n)]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v = fmaxf(v, red[w]);
+    sc[0] = v;
+  }
+  __syncthreads();
+  const double inv = sc[0] > 0.f ? 1.0 / (double)sc[0] : 0.0;
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) Af[i * ld + j] = (float)(A[min(i, j) + (int64_t)lda * max(i, j)] * inv);
+  __syncthreads();
+
+  // ---- 1. tridiagonalization
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // x = A[k+1 .. n-1, k]
+    float t, scal, beta;
+    warp_larfg(Af + (k + 1) * ld + k, ld, m, lane, t, scal, beta);  // every warp, same values
+    if (tid == 0) {
+      d[k] = Af[k * ld + k];
+      e[k] = beta;
+      tau[k] = t;
+    }
+    if (t == 0.f) continue;  // H_k = I; column k + 1 is unchanged (uniform: t is the same everywhere)
+    for (int i = tid; i < m; i += nt) vs[i] = i == 0 ? 1.f : Af[(k + 1 + i) * ld + k] * scal;
+    __syncthreads();
+    // partial p: thread (i, part) sums rows j = part, part + 4, ... of column i (A22 symmetric)
+    {
+      const int i = tid & (kMpMaxJ - 1), part = tid >> 7;
+      float acc = 0.f;
+      if (i < m) {
+        const float *col = Af + (k + 1) * ld + (k + 1 + i);
+        int j = part;
+        for (; j + 12 < m; j += 16) {  // four rows at a time, loads first
+          const float a0 = col[j * ld], a1 = col[(j + 4) * ld], a2 = col[(j + 8) * ld], a3 = col[(j + 12) * ld];
+          acc = fmaf(a0, vs[j], fmaf(a1, vs[j + 4], fmaf(a2, vs[j + 8], fmaf(a3, vs[j + 12], acc))));
+        }
+        for (; j < m; j += 4) acc = fmaf(col[j * ld], vs[j], acc);
+      }
+      pd[part * kMpMaxJ + i] = acc;
+      // v is kept below the subdiagonal for the back-transform (every warp is past reading x)
+      if (part == 0 && i >= 1 && i < m) Af[(k + 1 + i) * ld + k] = vs[i];
+    }
+    __syncthreads();
+    // every warp: K = t/2 p^T v, then its rows of A22 -= v w^T + w v^T with w = p - K v
+    float kk = 0.f;
+    for (int j = lane; j < m; j += 32)
+      kk = fmaf(pd[j] + pd[kMpMaxJ + j] + pd[2 * kMpMaxJ + j] + pd[3 * kMpMaxJ + j], vs[j], kk);
+    kk = 0.5f * t * t * warp_sum32(kk);
+    float vj[kMpMaxJ / 32], wj[kMpMaxJ / 32];
+#pragma unroll
+    for (int c = 0; c < kMpMaxJ / 32; ++c) {
+      const int j = lane + 32 * c;
+      vj[c] = j < m ? vs[j] : 0.f;
+      wj[c] = j < m ? fmaf(-kk, vj[c], t * (pd[j] + pd[kMpMaxJ + j] + pd[2 * kMpMaxJ + j] + pd[3 * kMpMaxJ + j]))
+                    : 0.f;
+    }
+    for (int i0 = warp; i0 < m; i0 += 2 * nw) {  // two rows at a time, loads first
+      const int i1 = i0 + nw;
+      const bool two = i1 < m;
+      const float vi0 = vs[i0], vi1 = two ? vs[i1] : 0.f;
+      const float wi0 = fmaf(-kk, vi0, t * (pd[i0] + pd[kMpMaxJ + i0] + pd[2 * kMpMaxJ + i0] + pd[3 * kMpMaxJ + i0]));
+      const float wi1 =
+          two ? fmaf(-kk, vi1, t * (pd[i1] + pd[kMpMaxJ + i1] + pd[2 * kMpMaxJ + i1] + pd[3 * kMpMaxJ + i1])) : 0.f;
+      float *row0 = Af + (k + 1 + i0) * ld + (k + 1);
+      float *row1 = Af + (k + 1 + (two ? i1 : i0)) * ld + (k + 1);
+      float a0[kMpMaxJ / 32], a1[kMpMaxJ / 32];
+#pragma unroll
+      for (int c = 0; c < kMpMaxJ / 32; ++c) {
+        const int j = lane + 32 * c;
+        a0[c] = j < m ? row0[j] : 0.f;
+        a1[c] = (two && j < m) ? row1[j] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < kMpMaxJ / 32; ++c) {
+        const int j = lane + 32 * c;
+        if (j < m) {
+          row0[j] = fmaf(-vi0, wj[c], fmaf(-wi0, vj[c], a0[c]));
+          if (two) row1[j] = fmaf(-vi1, wj[c], fmaf(-wi1, vj[c], a1[c]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = Af[(n - 2) * ld + (n - 2)];
+      e[n - 2] = Af[(n - 1) * ld + (n - 2)];
+      tau[n - 2] = 0.f;
+    }
+    d[n - 1] = Af[(n - 1) * ld + (n - 1)];
+    e[n - 1] = 0.f;
+    tau[n - 1] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) e2[i] = e[i] * e[i];
+  if (warp == 0) {  // Gershgorin bounds and ||T||
+    float lo = FLT_MAX, hi = -FLT_MAX;
+    for (int i = lane; i < n; i += 32) {
+      const float r = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+      lo = fminf(lo, d[i] - r);
+      hi = fmaxf(hi, d[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const float tn = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), FLT_MIN);
+      sc[0] = lo - 0x1p-20f * tn;
+      sc[1] = hi + 0x1p-20f * tn;
+      sc[2] = tn;
+    }
+  }
+  __syncthreads();
+  const float gl = sc[0], gu = sc[1], tn = sc[2];
+  const float piv = 0x1p-23f * tn;  // smallest pivot magnitude kept
+
+  // ---- 2. multisection: threads 4 i .. 4 i + 3 find the i-th smallest eigenvalue
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    float lo = gl, hi = gu;
+    // 12 rounds shrink the interval 5^12 > 2^27 times (all lanes take part in the shuffles)
+    for (int it = 0; it < 12; ++it) {
+      const float x = lo + (hi - lo) * (0.2f * (float)(sub + 1));
+      int cnt = 0;
+      if (i < n) {
+        float q = d[0] - x;
+        for (int k = 0;; ++k) {
+          if (fabsf(q) < piv) q = -piv;
+          cnt += q < 0.f;
+          if (k + 1 >= n) break;
+          q = d[k + 1] - x - __fdividef(e2[k], q);
+        }
+      }
+      // counts grow with x: new lo = largest point with count <= i, new hi = smallest with count > i
+      float nlo = lo, nhi = hi;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int cs = __shfl_sync(0xffffffffu, cnt, (lane & ~3) | s);
+        const float xs = __shfl_sync(0xffffffffu, x, (lane & ~3) | s);
+        if (cs <= i) nlo = fmaxf(nlo, xs);
+        else nhi = fminf(nhi, xs);
+      }
+      lo = nlo;
+      hi = nhi;
+    }
+    if (i < n && sub == 0) lam[n - 1 - i] = 0.5f * (lo + hi);  // descending order
+  }
+  __syncthreads();
+
+  // ---- 3. inverse iteration: thread c solves (T - l_c I) z = b twice
+  for (int c = tid; c < n; c += nt) {
+    const float s = lam[c];
+    float D = d[0] - s;
+    for (int k = 0; k + 1 < n; ++k) {
+      if (fabsf(D) < piv) D = D < 0.f ? -piv : piv;
+      const float L = __fdividef(e[k], D);
+      W[k * n + c] = L;
+      D = d[k + 1] - s - L * e[k];
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      float Dk = d[0] - s, y = 0.f;
+      for (int k = 0; k < n; ++k) {  // forward: y = L^-1 b, z = D^-1 y
+        if (k > 0) Dk = d[k] - s - W[(k - 1) * n + c] * e[k - 1];
+        if (fabsf(Dk) < piv) Dk = Dk < 0.f ? -piv : piv;
+        const float b = pass == 0 ? start_entry(c, k) : Z[k * ld + c];
+        y = k == 0 ? b : b - W[(k - 1) * n + c] * y;
+        Z[k * ld + c] = __fdividef(y, Dk);
+      }
+      float xn = Z[(n - 1) * ld + c], nrm = xn * xn;
+      for (int k = n - 2; k >= 0; --k) {  // backward: x = L^-T z
+        xn = Z[k * ld + c] - W[k * n + c] * xn;
+        Z[k * ld + c] = xn;
+        nrm = fmaf(xn, xn, nrm);
+      }
+      // a solve that overflowed (or vanished) restarts from e_c
+      const bool good = nrm > 0.f && nrm <= FLT_MAX;
+      const float r = good ? rsqrtf(nrm) : 0.f;
+      for (int k = 0; k < n; ++k) Z[k * ld + c] = good ? Z[k * ld + c] * r : (k == c ? 1.f : 0.f);
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. Z <- Q of Z = Q R (Householder), columns in descending eigenvalue order
+  for (int j = 0; j < n; ++j) {
+    const int m = n - j;  // column j, rows j..n-1
+    float t, scal, beta;
+    warp_larfg(Z + j * ld + j, ld, m, lane, t, scal, beta);
+    if (tid == 0) {
+      qtau[j] = t;
+      sgn[j] = beta < 0.f ? -1.f : 1.f;  // R(j, j) = beta: Q's column j is sign(beta) times the new direction
+    }
+    if (t == 0.f) continue;
+    for (int i = tid + 1; i < m; i += nt) W[(j + i) * n + j] = Z[(j + i) * ld + j] * scal;  // v below row j
+    __syncthreads();
+    // trailing columns j+1..n-1 (column j itself is not needed any more)
+    apply_reflector(Z, ld, n, j, j + 1, t, W + j, n, pd);
+  }
+  // explicit Q: reflectors applied to I in reverse order, then signs so that
+  // column j points along the j-th input vector
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, c = idx - r * n;
+    Z[r * ld + c] = r == c ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const float t = qtau[j];
+    if (t != 0.f) apply_reflector(Z, ld, n, j, j, t, W + j, n, pd);
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, c = idx - r * n;
+    Z[r * ld + c] *= sgn[c];
+  }
+  __syncthreads();
+
+  // ---- 5. X = Q1 Z: H_{n-3} first, H_0 last
+  for (int k = n - 3; k >= 0; --k) {
+    const float t = tau[k];
+    if (t != 0.f) apply_reflector(Z, ld, n, k + 1, 0, t, Af + k, ld, pd);
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    X[r + (int64_t)ldx * c] = (double)Z[r * ld + c];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -556,9 +930,21 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   double *G = w.g(depth), *E = w.e(depth);
   int *label = w.labels + depth * w.J, *perm = w.perms + depth * w.J;
   LevelInfo *dinfo = w.info + depth;
-  const size_t smem32 = jacobi32_smem(m);
-  TK_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-  k_jacobi32<<<1, kJ32Threads, smem32, s>>>(A, lda, m, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr);
+  // float32 first stage: the tridiagonal solver, or the Jacobi sweeps with
+  // TUCKER_EIG32=jacobi (same accuracy; kept for comparison)
+  static const bool use_jacobi = [] {
+    const char *e = std::getenv("TUCKER_EIG32");
+    return e && std::strcmp(e, "jacobi") == 0;
+  }();
+  if (use_jacobi) {
+    const size_t smem32 = jacobi32_smem(m);
+    TK_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    k_jacobi32<<<1, kJ32Threads, smem32, s>>>(A, lda, m, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr);
+  } else {
+    const size_t smemt = tri32_smem(m);
+    TK_CUDA(cudaFuncSetAttribute(k_eig32_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemt));
+    k_eig32_tri<<<1, kT32Threads, smemt, s>>>(A, lda, m, tx0 + (size_t)m * m, m);
+  }
   TK_LAUNCHED();
   // first refinement step: clusters and the permuted basis
   TK_CHECK(products(A, lda, m, tx0, G, s));
