@@ -1,6 +1,7 @@
 // Shared declarations of the ST-HOSVD CUDA library (host driver + kernels).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,18 +106,30 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
 // Split-precision Gram (tcgen05, exact integer digits; J <= 128).  Takes its
 // exponents from a first pass over Y on the device (no host round trip).  d_ws
 // holds gram_split_workspace_doubles() doubles, including an error flag read
-// back by gram_split_error().
+// back by gram_split_error().  With L > 1 and d_colexp given (L B ints), the
+// first pass also writes every column's exponent (the scale the split mode
+// product of the same Y needs).
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
+// Tiled tensor map of a float64 (f64) or float32 array: rank dimensions
+// (innermost first), byte strides of dimensions 1..rank-1 (multiples of 16),
+// box extents; no swizzle, out-of-range elements read as zero.  Calls
+// cuTensorMapEncodeTiled through the runtime's driver entry point; false when
+// it is unavailable or refuses the map.
+bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const uint64_t *dims,
+                 const uint64_t *strides_bytes, const uint32_t *box);
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
-                      const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp = nullptr);
 // *d_out = trace of the J x J matrix S (column-major), summed in index order.
 int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s);
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s);
 // Split-precision mode product Z(L,R,B) = U^T Y(L,J,B) on tcgen05 (R <= J <= 128);
 // U is J x R column-major float64.  *d_err becomes 1 if a bounded wait expired.
+// With L > 1, d_colexp (L B ints, from launch_gram_split's exponent pass over
+// the same Y) saves a pass over Y; without it the kernel computes them.
 int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
-                     double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof);
+                     double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof,
+                     const int *d_colexp = nullptr);
 // Jacobi eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
 // matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if
 // converged else 1.

@@ -54,7 +54,6 @@
 #include <cstring>
 #include <type_traits>
 
-#include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -237,15 +236,26 @@ __device__ __forceinline__ void load_unit(const T *__restrict__ y, int64_t L, in
 // as a bit pattern ordered like the magnitude.  One CTA of 256 threads per
 // group.  With L == 1 (J dividing 512, J even) the group is one contiguous
 // block read as 16-byte vectors, each thread meeting the same two rows
-// throughout; otherwise each warp takes whole rows, its lanes spread over the
-// group's columns (consecutive columns are consecutive entries within a run
-// of L).
+// throughout.  Otherwise each warp takes rows two at a time, its lanes spread
+// over the group's columns (consecutive columns are consecutive entries
+// within a run of L), loading only the high 32-bit word of each float64 (all
+// the magnitude order needs) with 32 loads in flight per lane; with colexp
+// given, the exponent above each column's largest magnitude (over all J rows:
+// the per-column scale of the split mode product) is written too.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ unsigned ldg_mag(const T *p) {
+  if constexpr (sizeof(T) == 8) return __ldg(reinterpret_cast<const unsigned *>(p) + 1) & 0x7FFFFFFFu;
+  else return __ldg(reinterpret_cast<const unsigned *>(p)) & 0x7FFFFFFFu;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, int64_t L, int J, int64_t K,
                                                       int contig_pairs, int *__restrict__ E,
-                                                      unsigned long long *__restrict__ gmax) {
+                                                      unsigned long long *__restrict__ gmax,
+                                                      int *__restrict__ colexp) {
   __shared__ unsigned rmax[kRows];
+  __shared__ unsigned cmax[kGroup];
   constexpr bool kF64 = sizeof(T) == 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t g = blockIdx.x;
@@ -281,21 +291,45 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
     // lane `lane` reads columns c0 + lane + 32 k, k < 16; their offsets are
     // computed once and reused for every row
     const int64_t stride_b = L * (int64_t)J;
-    int64_t off[kGroup / 32];
+    constexpr int kPer = kGroup / 32;
+    int64_t off[kPer];
+    unsigned colm[kPer];
 #pragma unroll
-    for (int k = 0; k < kGroup / 32; ++k) {
+    for (int k = 0; k < kPer; ++k) {
       const int cc = lane + 32 * k;
       const int64_t c = c0 + cc, b = c / L, l = c - b * L;
       off[k] = cc < ncols ? l + stride_b * b : -1;
+      colm[k] = 0u;
     }
-    for (int i = warp; i < J; i += 8) {
-      unsigned m = 0u;
+    for (int i = warp; i < J; i += 16) {  // rows i and i + 8
+      const int i2 = i + 8;
+      unsigned a[kPer], b2[kPer];
 #pragma unroll
-      for (int k = 0; k < kGroup / 32; ++k)
-        if (off[k] >= 0) m = max(m, hi_mag(__ldg(y + off[k] + L * (int64_t)i)));
+      for (int k = 0; k < kPer; ++k) {
+        a[k] = off[k] >= 0 ? ldg_mag(y + off[k] + L * (int64_t)i) : 0u;
+        b2[k] = (off[k] >= 0 && i2 < J) ? ldg_mag(y + off[k] + L * (int64_t)i2) : 0u;
+      }
+      unsigned ma = 0u, mb = 0u;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) rmax[i] = m;
+      for (int k = 0; k < kPer; ++k) {
+        ma = max(ma, a[k]);
+        mb = max(mb, b2[k]);
+        colm[k] = max(colm[k], max(a[k], b2[k]));
+      }
+      ma = __reduce_max_sync(0xffffffffu, ma);
+      mb = __reduce_max_sync(0xffffffffu, mb);
+      if (lane == 0) {
+        rmax[i] = ma;
+        if (i2 < J) rmax[i2] = mb;
+      }
+    }
+    if (colexp) {
+      for (int cc = tid; cc < kGroup; cc += 256) cmax[cc] = 0u;
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) atomicMax(&cmax[lane + 32 * k], colm[k]);
+      __syncthreads();
+      for (int cc = tid; cc < ncols; cc += 256) colexp[c0 + cc] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
     }
   }
   __syncthreads();
@@ -633,18 +667,6 @@ __device__ __forceinline__ void tmem_ld4x4(uint32_t taddr, uint32_t (&r)[4][4]) 
       : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-// 2-D tensor-map box load into shared memory, completion counted on mbar
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_constant__ CUtensorMap ymap, SplitPlan p,
                                                                  const int *__restrict__ Etab,
@@ -894,29 +916,6 @@ int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &
   return TUCKER_OK;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library); false when unavailable or the map is refused.
-bool encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t dim0, uint64_t dim1,
-                    uint64_t stride1_bytes, uint32_t box0, uint32_t box1) {
-  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      fn = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }();
-  if (!encode) return false;
-  const cuuint64_t gdim[2] = {dim0, dim1};
-  const cuuint64_t gstride[1] = {stride1_bytes};
-  const cuuint32_t box[2] = {box0, box1};
-  const cuuint32_t estride[2] = {1, 1};
-  return encode(map, dt, 2, const_cast<void *>(base), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // The tensor-map kernel takes L == 1 with 16-byte column strides, a 16-byte
 // aligned Y and K < 2^31; TUCKER_GRAM_SPLIT_KERNEL=regs forces the
 // register-staged kernel.  Returns 1 when it ran, 0 when it does not apply.
@@ -930,9 +929,10 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
   const uint64_t col_bytes = (uint64_t)p.J * sizeof(T);
   if (regs || col_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(y) % 16 != 0 || p.K >= (1ll << 31)) return TUCKER_OK;
   CUtensorMap map;
-  if (!encode_tmap_2d(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, y,
-                      (uint64_t)p.J, (uint64_t)p.K, col_bytes, kRows, kChunk))
-    return TUCKER_OK;
+  const uint64_t dims[2] = {(uint64_t)p.J, (uint64_t)p.K};
+  const uint64_t strides[1] = {col_bytes};
+  const uint32_t box[2] = {kRows, kChunk};
+  if (!encode_tmap(&map, sizeof(T) == 8, y, 2, dims, strides, box)) return TUCKER_OK;
   TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kBulkSmemBytes));
   k_gram_split_bulk<T><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
@@ -943,13 +943,39 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
 
 }  // namespace
 
+bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const uint64_t *dims,
+                 const uint64_t *strides_bytes, const uint32_t *box) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || rank < 1 || rank > 5) return false;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t bx[5], estride[5];
+  for (int k = 0; k < rank; ++k) {
+    gdim[k] = dims[k];
+    bx[k] = box[k];
+    estride[k] = 1;
+    if (k + 1 < rank) gstride[k] = strides_bytes[k];
+  }
+  return encode(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                const_cast<void *>(base), gdim, gstride, bx, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   const SplitPlan p = split_plan(L, J, B, dev);
   return (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + (int64_t)p.nsplit * kRows / 2 + 4;
 }
 
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
-                      const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp) {
   if (J > kRows) {
     set_error("split-precision Gram supports J <= %d (got %lld)", kRows, (long long)J);
     return TUCKER_EUNSUPPORTED;
@@ -970,10 +996,10 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (prof) prof->begin(TUCKER_PHASE_SCALE);
   if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
-                                                               contig_pairs, w.table, w.gmax);
+                                                               contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
   else
     k_rowgroup_exp<float><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const float *>(y), L, (int)J, p.K,
-                                                              contig_pairs, w.table, w.gmax);
+                                                              contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM);

@@ -34,6 +34,8 @@
 // MMAs, frees TMEM and returns.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
@@ -732,10 +734,341 @@ TtmL1Plan ttm_l1_plan(int64_t J, int64_t B, int64_t R, const void *y, tucker_dty
   return p;
 }
 
+// ---------------------------------------------------------------------------
+// L > 1 through tensor-map tiles.  The unfolding's column (l, b) is J entries
+// L apart; a tile is 128 consecutive l of one b (L >= 128) or floor(128 / L)
+// whole runs of L (L < 128), i.e. one box {BL, 32, BB} of the 3-D tensor
+// map over Y (L, J, B) per K-part of 32 rows (j), copied by the
+// tensor-memory accelerator into a ring of shared-memory slots (rows j >= J
+// and columns past L or B arrive as zeros).  The column exponents come from
+// the exponent pass over the same Y (every column's largest magnitude over
+// all J rows), so a part can be converted as soon as it lands: thread
+// (column m, rows 8 (tid / 128) ..) reads its 8 entries with constant
+// offsets, forms the four 28-bit digits and stores one 16-byte K-major row
+// unit per digit tile.  Thread 0 issues the copies and, per part, four MMAs
+// per K-step against U's stacked digit tiles (as in the L == 1 kernel) into
+// one of two TMEM accumulator sets; each tile's outputs are assembled
+// exactly from the four levels and written while the next tile's MMAs run.
+// ---------------------------------------------------------------------------
+constexpr int kTmKH = 32;  // contraction rows per part (one box)
+
+struct TtmTmaPlan {
+  int J, Jp32, R, Rp, parts, BL, BB, slots, tmem_cols, grid;
+  int64_t L, B, tiles_per_b, ntiles;
+  size_t u_bytes, raw_slot, smem;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_constant__ CUtensorMap ymap,
+                                                               const double *__restrict__ U, TtmTmaPlan p,
+                                                               const int *__restrict__ colexp,
+                                                               double *__restrict__ z, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  __shared__ __align__(8) unsigned long long raw_full[4], mma_done[2], acc_full[2];
+  __shared__ int rowexp[kM];
+  __shared__ int cexp[4][kM2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int stop;
+  unsigned char *base = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
+  unsigned char *Ut = base;                                 // 4 stacked digit tiles of U (Rp x Jp32)
+  unsigned char *Ast = Ut + p.u_bytes;                      // 2 stages x 4 digit tiles (128 x 32)
+  constexpr int kATile = kM2 * kTmKH * 2;                   // 8 KB
+  unsigned char *ring = Ast + 2 * 4 * kATile;               // p.slots raw slots
+  const int u_tile = p.Rp * p.Jp32 * 2;
+  const uint32_t sbo_u = (uint32_t)(p.Jp32 / 8) * 128u;
+  constexpr uint32_t kSboA = (kTmKH / 8) * 128u;            // 512
+  uint32_t idesc_q[kBTiles];
+#pragma unroll
+  for (int q = 0; q < kBTiles; ++q) idesc_q[q] = idesc_bf16(kM2, (kBTiles - q) * p.Rp);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < p.slots; ++k) mbar_init(smem_addr(&raw_full[k]), 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_addr(&mma_done[k]), 1);
+      mbar_init(smem_addr(&acc_full[k]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  if (tid < kM) {
+    unsigned long long m = 0ull;
+    if (tid < p.R)
+      for (int j = 0; j < p.J; ++j) m = max(m, mag_bits(U[j + (int64_t)p.J * tid]));
+    rowexp[tid] = exp_above(m, true);
+  }
+  __syncthreads();
+  for (int u = tid; u < p.Rp * (p.Jp32 / 8); u += kThreads) {  // U's digit tiles (row r, k = j)
+    const int r = u / (p.Jp32 / 8), jg = u % (p.Jp32 / 8);
+    uint32_t w[kATiles][4];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      int d[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 8 * jg + k + h;
+        const double v = (r < p.R && j < p.J) ? U[j + (int64_t)p.J * r] : 0.0;
+        digits4(scaled_int28(v, rowexp[r]), d[h]);
+      }
+#pragma unroll
+      for (int t = 0; t < kATiles; ++t) w[t][k >> 1] = bf16_pair((float)d[0][t], (float)d[1][t]);
+    }
+    const int off = (r >> 3) * (int)sbo_u + jg * 128 + (r & 7) * 16;
+#pragma unroll
+    for (int t = 0; t < kATiles; ++t)
+      *reinterpret_cast<uint4 *>(Ut + t * u_tile + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+  }
+
+  const int64_t t0 = blockIdx.x, tstride = gridDim.x;
+  const int ntc = t0 < p.ntiles ? (int)((p.ntiles - t0 + tstride - 1) / tstride) : 0;
+  const int nunits = ntc * p.parts;
+  // tile it's box origin: (l0, b0)
+  auto tile_origin = [&](int it, int64_t &l0, int64_t &b0) {
+    const int64_t tg = t0 + (int64_t)it * tstride;
+    if (p.BB == 1) {
+      b0 = tg / p.tiles_per_b;
+      l0 = (tg - b0 * p.tiles_per_b) * kM2;
+    } else {
+      b0 = tg * p.BB;
+      l0 = 0;
+    }
+  };
+  auto issue_copy = [&](int u) {  // part u % parts of tile u / parts -> slot u % slots (thread 0)
+    int64_t l0, b0;
+    tile_origin(u / p.parts, l0, b0);
+    const int slot = u % p.slots;
+    const uint32_t bar = smem_addr(&raw_full[slot]);
+    mbar_expect_tx(bar, (uint32_t)p.raw_slot);
+    tma_load_3d(smem_addr(ring + (size_t)slot * p.raw_slot), &ymap, (int)l0, kTmKH * (u % p.parts), (int)b0, bar);
+  };
+  // tile row m: box column loff of run s; constant per thread
+  const int m = tid & (kM2 - 1), jq = tid >> 7;
+  const int s_m = m / p.BL, loff = m - s_m * p.BL;
+  const bool m_in_box = s_m < p.BB;
+  const int raw_off = (s_m * kTmKH + 8 * jq) * p.BL + loff;  // element (m, 8 jq) of a slot
+  auto load_cexp = [&](int it) {  // column exponents of tile it -> cexp[it % 4]
+    if (tid < kM2 && it < ntc) {
+      int64_t l0, b0;
+      tile_origin(it, l0, b0);
+      const int64_t l = l0 + loff, b = b0 + s_m;
+      cexp[it % 4][tid] = (m_in_box && l < p.L && b < p.B) ? colexp[l + p.L * b] : -4000;
+    }
+  };
+  load_cexp(0);
+  load_cexp(1);
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < p.slots && issued < nunits; ++issued) issue_copy(issued);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // outputs of tile it (set it & 1): TMEM lanes 32 q.. (columns), rows g Rp/4 ..
+  auto drain = [&](int it) {
+    const int set = it & 1;
+    const bool ok =
+        __all_sync(0xffffffffu, mbar_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1)));
+    if (ok) {
+      fence_after();
+      const int q = warp & 3, g = warp >> 2;
+      const int mm = 32 * q + lane;
+      const int sm2 = mm / p.BL, lo2 = mm - sm2 * p.BL;
+      int64_t l0, b0;
+      tile_origin(it, l0, b0);
+      const int64_t l = l0 + lo2, b = b0 + sm2;
+      const bool valid = sm2 < p.BB && l < p.L && b < p.B;
+      const int fc = cexp[it % 4][mm];
+      double *zc = z + l + p.L * (int64_t)p.R * b;
+      const int rq = p.Rp / 4;
+      const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * 4 * p.Rp);
+      for (int r0 = g * rq; r0 < (g + 1) * rq; r0 += 4) {
+        uint32_t a[4][4];
+#pragma unroll
+        for (int lev = 0; lev < 4; ++lev)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(a[lev][0]), "=r"(a[lev][1]), "=r"(a[lev][2]), "=r"(a[lev][3])
+                       : "r"(tb + (uint32_t)(lev * p.Rp + r0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = r0 + e;
+            if (r < p.R) zc[p.L * (int64_t)r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + fc - 42);
+          }
+        }
+      }
+    } else {
+      stop = 1;
+    }
+    fence_before();
+    __syncthreads();
+  };
+
+  int last_committed = -1;
+  for (int it = 0; it < ntc && !stop; ++it) {
+    const int set = it & 1;
+    const int f1022 = cexp[it % 4][m] + 1022;
+    // read after later barriers; buffer (it + 2) % 4 is no longer needed (tile it - 2 is drained)
+    if (it + 2 < ntc) load_cexp(it + 2);
+    for (int pp = 0; pp < p.parts; ++pp) {
+      const int u = it * p.parts + pp, slot = u % p.slots, stg = u & 1;
+      bool ok = mbar_wait(smem_addr(&raw_full[slot]), (uint32_t)((u / p.slots) & 1));
+      if (ok && u >= 2) ok = mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)(((u - 2) >> 1) & 1));
+      if (ok) {
+        const T *raw = reinterpret_cast<const T *>(ring + (size_t)slot * p.raw_slot) + raw_off;
+        uint32_t w[kBTiles][4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          float d0[4], d1[4];
+          const T y0 = m_in_box ? raw[k * p.BL] : T(0), y1 = m_in_box ? raw[(k + 1) * p.BL] : T(0);
+          digits4_float(scaled_int28_bits(y0, f1022), d0);
+          digits4_float(scaled_int28_bits(y1, f1022), d1);
+#pragma unroll
+          for (int qq = 0; qq < kBTiles; ++qq) w[qq][k >> 1] = bf16_pair(d0[qq], d1[qq]);
+        }
+        unsigned char *st = Ast + stg * 4 * kATile;
+        const int off = (m >> 3) * (int)kSboA + jq * 128 + (m & 7) * 16;
+#pragma unroll
+        for (int qq = 0; qq < kBTiles; ++qq)
+          *reinterpret_cast<uint4 *>(st + qq * kATile + off) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
+      } else {
+        stop = 1;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (stop) break;
+      if (tid == 0) {
+        if (issued < nunits) issue_copy(issued++);  // slot u has been read by every thread
+        fence_after();
+        const uint32_t ab = smem_addr(Ast + stg * 4 * kATile), ub = smem_addr(Ut);
+        const uint32_t d0 = tmem + (uint32_t)(set * 4 * p.Rp);
+#pragma unroll
+        for (int ks = 0; ks < kTmKH / 16; ++ks) {
+          const uint64_t ucat = smem_desc(ub + (uint32_t)(((kTmKH / 8) * pp + 2 * ks) * 128), 128, sbo_u);
+#pragma unroll
+          for (int qq = 0; qq < kBTiles; ++qq) {
+            const uint64_t ya = smem_desc(ab + qq * kATile + 256 * ks, 128, kSboA);
+            mma_bf16(d0 + qq * p.Rp, ya, ucat, idesc_q[qq], (pp == 0 && ks == 0 && qq == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(smem_addr(&mma_done[stg]));
+        if (pp == p.parts - 1) mma_commit(smem_addr(&acc_full[set]));
+      }
+      last_committed = u;
+    }
+    if (stop) break;
+    if (it >= 1) drain(it - 1);  // the previous tile, while this one's MMAs run
+  }
+  if (!stop && ntc >= 1) drain(ntc - 1);
+  if (stop && tid == 0) {  // our own MMAs and copies finish (bounded) before TMEM and shared memory go
+    if (last_committed >= 0)
+      mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)((last_committed >> 1) & 1));
+    for (int c = max(0, issued - p.slots); c < issued; ++c)
+      mbar_wait(smem_addr(&raw_full[c % p.slots]), (uint32_t)((c / p.slots) & 1));
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+  if (stop && tid == 0) atomicExch(err, 1);
+}
+
+// column exponents of Y (L, J, B) for the tensor-map kernel when no exponent
+// pass has run: thread per column (consecutive l: coalesced)
+template <typename T>
+__global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ y, int64_t L, int J, int64_t K,
+                                                int *__restrict__ colexp) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  const int64_t b = c / L, l = c - b * L;
+  const T *p = y + l + L * (int64_t)J * b;
+  unsigned mx = 0u;
+  for (int j = 0; j < J; ++j) mx = max(mx, hi_mag(__ldg(p + L * (int64_t)j)));
+  colexp[c] = exp_above(mag_pattern(mx, sizeof(T) == 8), sizeof(T) == 8);
+}
+
+
+// The plan, or parts == 0 when the shape does not suit the tensor-map kernel.
+TtmTmaPlan ttm_tma_plan(int64_t L, int64_t J, int64_t B, int64_t R, tucker_dtype dt, const void *y,
+                        const DeviceInfo &dev) {
+  TtmTmaPlan p{};
+  const size_t esz = dt == TUCKER_F64 ? 8 : 4;
+  p.J = (int)J;
+  p.R = (int)R;
+  p.Rp = (int)((R + 15) / 16 * 16);
+  p.Jp32 = (int)((J + 31) / 32 * 32);
+  p.parts = p.Jp32 / kTmKH;
+  p.L = L;
+  p.B = B;
+  if (L >= kM2) {
+    p.BL = kM2;
+    p.BB = 1;
+    p.tiles_per_b = (L + kM2 - 1) / kM2;
+    p.ntiles = B * p.tiles_per_b;
+  } else {
+    p.BL = (int)L;
+    p.BB = (int)(kM2 / L);
+    p.tiles_per_b = 1;
+    p.ntiles = (B + p.BB - 1) / p.BB;
+  }
+  p.raw_slot = (size_t)p.BL * kTmKH * p.BB * esz;
+  p.u_bytes = (size_t)4 * p.Rp * p.Jp32 * 2;
+  const int cols = 2 * 4 * p.Rp;
+  p.tmem_cols = 32;
+  while (p.tmem_cols < cols) p.tmem_cols <<= 1;
+  const size_t fixed = 1024 + p.u_bytes + (size_t)2 * 4 * kM2 * kTmKH * 2;
+  const size_t avail = (size_t)dev.smem_optin > fixed + 4096 ? (size_t)dev.smem_optin - fixed - 4096 : 0;
+  p.slots = (int)std::min<size_t>(4, avail / std::max<size_t>(p.raw_slot, 1));
+  p.smem = fixed + (size_t)p.slots * p.raw_slot;
+  p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ntiles));
+  const bool ok = L > 1 && J <= kMaxJp && R <= 64 && R <= J && (L * (int64_t)esz) % 16 == 0 &&
+                  reinterpret_cast<uintptr_t>(y) % 16 == 0 && cols <= 512 && p.slots >= 2 && L < (1ll << 31) &&
+                  B < (1ll << 31) && p.ntiles >= 1;
+  if (!ok) p.parts = 0;
+  return p;
+}
+
+bool ttm_tma_map(CUtensorMap *map, const void *y, int64_t L, int64_t J, int64_t B, const TtmTmaPlan &p, bool f64) {
+  const size_t esz = f64 ? 8 : 4;
+  const uint64_t dims[3] = {(uint64_t)L, (uint64_t)J, (uint64_t)B};
+  const uint64_t strides[2] = {(uint64_t)L * esz, (uint64_t)L * J * esz};
+  const uint32_t box[3] = {(uint32_t)p.BL, (uint32_t)kTmKH, (uint32_t)p.BB};
+  return encode_tmap(map, f64, y, 3, dims, strides, box);
+}
+
+template <typename T>
+int run_ttm_tma(const CUtensorMap &map, const void *y, int64_t L, int64_t J, int64_t B, const double *U,
+                const TtmTmaPlan &p, const int *d_colexp, double *z, int *d_err, cudaStream_t s) {
+  const int64_t K = L * B;
+  int *tmp = nullptr;
+  if (!d_colexp) {  // no exponent pass ran: the column exponents first
+    TK_CUDA(cudaMallocAsync(&tmp, sizeof(int) * (size_t)K, s));
+    k_colexp<T><<<(unsigned)((K + 255) / 256), 256, 0, s>>>(static_cast<const T *>(y), L, (int)J, K, tmp);
+    TK_LAUNCHED();
+    d_colexp = tmp;
+  }
+  TK_CUDA(cudaFuncSetAttribute(k_ttm_split_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+  k_ttm_split_tma<T><<<p.grid, kThreads, p.smem, s>>>(map, U, p, d_colexp, z, d_err);
+  TK_LAUNCHED();
+  if (tmp) TK_CUDA(cudaFreeAsync(tmp, s));
+  return TUCKER_OK;
+}
+
 }  // namespace
 
 int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
-                     double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
+                     double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof,
+                     const int *d_colexp) {
   if (J > kMaxJp || R > kM || R > J) {
     set_error("split-precision TTM supports R <= J <= %d (got J = %lld, R = %lld)", kMaxJp, (long long)J,
               (long long)R);
@@ -755,6 +1088,21 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
         k_ttm_split_l1<float><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const float *>(y), U, q, z, d_err);
       }
       TK_LAUNCHED();
+      if (prof) prof->end(flops, bytes, 1);
+      return TUCKER_OK;
+    }
+  }
+  if (L > 1) {
+    static const bool legacy = [] {  // TUCKER_TTM_SPLIT_KERNEL=regs: the register-staged kernel
+      const char *e = std::getenv("TUCKER_TTM_SPLIT_KERNEL");
+      return e && std::strcmp(e, "regs") == 0;
+    }();
+    const TtmTmaPlan q = ttm_tma_plan(L, J, B, R, dt, y, dev);
+    CUtensorMap map;
+    if (q.parts > 0 && !legacy && ttm_tma_map(&map, y, L, J, B, q, dt == TUCKER_F64)) {
+      if (prof) prof->begin(TUCKER_PHASE_TTM);
+      if (dt == TUCKER_F64) TK_CHECK(run_ttm_tma<double>(map, y, L, J, B, U, q, d_colexp, z, d_err, s));
+      else TK_CHECK(run_ttm_tma<float>(map, y, L, J, B, U, q, d_colexp, z, d_err, s));
       if (prof) prof->end(flops, bytes, 1);
       return TUCKER_OK;
     }

@@ -363,11 +363,14 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     for (int m = n + 1; m < N; ++m) B *= cur[m];
     const int64_t J = cur[n];
 
-    // Gram step
+    // Gram step (with L > 1 its exponent pass also leaves the column exponents the TTM needs)
+    DevBuf colexp;
     if (prec == TUCKER_PREC_BF16X4) {
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
-      TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
+      if (L > 1) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
+      TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof,
+                                 L > 1 ? colexp.as<int>() : nullptr));
       TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
       if (k == 0 && norm_from_trace) {
         TK_CHECK(launch_trace(S.as<double>(), J, d_nx2, s));
@@ -431,7 +434,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
     if (prec == TUCKER_PREC_BF16X4)
       TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, factor_bufs[n].as<double>(), R, ynew.as<double>(), d_terr, dev, s,
-                                &prof));
+                                &prof, L > 1 ? colexp.as<int>() : nullptr));
     else
       TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(),
                           dev, s, &prof));

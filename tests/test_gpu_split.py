@@ -166,7 +166,12 @@ def ttm_split_bound(y, L, J, B, u):
                                      (1, 1, 9, 1), (3, 100, 77, 100), (64, 32, 50, 10), (1, 128, 4096 * 3 + 7, 128),
                                      # L == 1 kernel: one and two 64-wide parts, ragged J, many tiles per CTA
                                      (1, 48, 700, 20), (1, 100, 5000, 33), (1, 128, 40000, 40), (1, 64, 3000, 64),
-                                     (1, 126, 1000, 48), (1, 2, 300, 1)])
+                                     (1, 126, 1000, 48), (1, 2, 300, 1),
+                                     # L > 1 tensor-map kernel: 128-column boxes with a ragged last one per b,
+                                     # whole runs of L < 128 with a ragged last tile, one and two 32-row parts,
+                                     # R = 64 and R = 1
+                                     (200, 64, 7, 33), (40, 48, 34, 20), (128, 128, 20, 64), (2, 96, 1000, 1),
+                                     (130, 32, 9, 16)])
 def test_ttm_split_bound(gpu_lib, L, J, B, R):
     import torch
 
@@ -180,7 +185,8 @@ def test_ttm_split_bound(gpu_lib, L, J, B, R):
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
 
 
-@pytest.mark.parametrize("L,J,B,R", [(1, 64, 500, 16), (1, 128, 777, 48), (8, 128, 100, 40)])
+@pytest.mark.parametrize("L,J,B,R", [(1, 64, 500, 16), (1, 128, 777, 48), (8, 128, 100, 40), (40, 48, 7, 20),
+                                     (256, 40, 3, 24)])
 def test_ttm_split_exact_on_single_digit_inputs(gpu_lib, L, J, B, R):
     """U and Y entries of one digit each: every output is an exact integer product sum."""
     import torch
@@ -210,6 +216,19 @@ def test_ttm_split_f32_columns_contiguous(gpu_lib):
     z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
     bound, ref = ttm_split_bound(y, L, J, B, u)
     got = z.reshape((R, B), order="F")
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("L,J,B,R", [(12, 60, 200, 30), (160, 128, 5, 40)])
+def test_ttm_split_f32_strided_columns(gpu_lib, L, J, B, R):
+    import torch
+
+    rng = np.random.default_rng(L + J)
+    y = (rng.standard_normal(L * J * B) * np.exp(rng.standard_normal(L * J * B))).astype(np.float32)
+    u, _ = np.linalg.qr(rng.standard_normal((J, R)))
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    bound, ref = ttm_split_bound(y, L, J, B, u)
+    got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
     assert np.all(np.abs(got - ref) <= bound)
 
 
