@@ -86,7 +86,13 @@ typedef struct tucker_result {
   int sweeps[TUCKER_MAX_MODES];       /* Jacobi sweeps used per mode */
   double *core;                       /* prod(R_n) float64, natural layout, mode positions as in X */
   double *factors[TUCKER_MAX_MODES];  /* U_n: I_n x R_n float64, column-major, orthonormal columns */
-  double *eigvals[TUCKER_MAX_MODES];  /* host: the I_n eigenvalues of S_n, descending */
+  double *eigvals[TUCKER_MAX_MODES];  /* host: the I_n eigenvalues of S_n, descending.  Past the
+                                         rank cut, a cluster of eigenvalues whose sum with all
+                                         smaller ones is within the threshold may be left
+                                         unresolved (Algorithm 1 needs only the leading R_n
+                                         eigenvectors and the discarded sum): its entries are
+                                         then Rayleigh quotients of a basis of its invariant
+                                         subspace, and every sum from the cut on stays exact */
   double tail[TUCKER_MAX_MODES];      /* discarded eigenvalue sum per mode (clamped at 0) */
   double norm2_x;                     /* ||X||^2 */
   double threshold;                   /* eps^2 ||X||^2 / N (0 when eps <= 0) */

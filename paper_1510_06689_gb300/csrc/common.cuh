@@ -134,13 +134,19 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
 // matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if
 // converged else 1.
 int64_t eig_workspace_doubles(int64_t J);
+// tail_budget >= 0 (the rank rule's threshold) lets the mixed-precision
+// solver leave clusters unresolved whose eigenvalues, with all smaller ones,
+// sum to at most tail_budget: their columns span the clusters' invariant
+// subspace and their values are Rayleigh quotients (every sum from such a
+// cluster's first index on is exact, so the rank rule's cut is unchanged);
+// the default resolves every eigenpair.
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
-               cudaStream_t s, Prof *prof);
-// Mixed-precision eigensolver (float32 Jacobi + float64 refinement, J <= 128):
-// *verified = 1 when lam, V and d_info hold a result that passed the device
-// check; otherwise the caller runs the float64 Jacobi.  Synchronises s.
+               cudaStream_t s, Prof *prof, double tail_budget = -1.0);
+// Mixed-precision eigensolver (float32 first stage + float64 refinement,
+// J <= 128): *verified = 1 when lam, V and d_info hold a result that passed the
+// device check; otherwise the caller runs the float64 Jacobi.  Synchronises s.
 int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
-                  cudaStream_t s, Prof *prof);
+                  cudaStream_t s, Prof *prof, double tail_budget = -1.0);
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

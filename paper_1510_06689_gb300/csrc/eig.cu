@@ -712,7 +712,7 @@ static bool dsm_cluster_ok(size_t dsmem) {
 }
 
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
-               cudaStream_t s, Prof *prof) {
+               cudaStream_t s, Prof *prof, double tail_budget) {
   const int64_t m = J + (J & 1);
   // "mp" (default: mixed precision, J <= 128, float64 Jacobi if unverified) |
   // "jacobi" (float64 Jacobi only) | "dsm" | "l2m" | "l2" (cluster variants)
@@ -722,7 +722,7 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
   const bool jacobi_only = ev && (use_dsm || use_l2 || !strcmp(ev, "jacobi") || !strcmp(ev, "l2m"));
   if (!jacobi_only && J <= 128) {
     int verified = 0;
-    TK_CHECK(launch_eig_mp(d_S, J, d_lam, d_V, d_info, &verified, s, prof));
+    TK_CHECK(launch_eig_mp(d_S, J, d_lam, d_V, d_info, &verified, s, prof, tail_budget));
     if (verified) return TUCKER_OK;
     const char *strict = getenv("TUCKER_EIG_MP_STRICT");  // tests: report instead of falling back
     if (strict && strict[0] == '1') {

@@ -632,8 +632,10 @@ constexpr int kStatThreads = 256;
 
 struct LevelInfo {
   double norm_a;   // ||A||_F of the level's matrix
+  double delta;    // cluster gap: eigenvalue approximations are this accurate
   int nclusters;
   int start[kMpMaxJ + 1];
+  double csum[kMpMaxJ];  // per cluster, the sum of its eigenvalue approximations
 };
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -731,13 +733,21 @@ __global__ void __launch_bounds__(256) k_oa_partition(const double *__restrict__
     int k = 0;
     info->start[0] = 0;
     label[0] = 0;
+    double cs = lam[perm[0]];
     for (int a = 1; a < m; ++a) {
-      if (lam[perm[a - 1]] - lam[perm[a]] > delta) info->start[++k] = a;
+      if (lam[perm[a - 1]] - lam[perm[a]] > delta) {
+        info->csum[k] = cs;
+        cs = 0.0;
+        info->start[++k] = a;
+      }
+      cs += lam[perm[a]];
       label[a] = k;
     }
+    info->csum[k] = cs;
     info->nclusters = k + 1;
     info->start[k + 1] = m;
     info->norm_a = sqrt(a2);
+    info->delta = delta;
   }
   for (int a = tid; a < m; a += nt) perm_out[a] = perm[a];
 }
@@ -791,18 +801,28 @@ __global__ void k_copy_cols(const double *__restrict__ src, int lds, double *__r
 // the lowest row on ties), check[0] = max |A x - l x|, check[1] = max
 // |X^T X - I|, check[2] = max |l|.
 __global__ void __launch_bounds__(1024) k_mp_finalize(const double *__restrict__ G, const double *__restrict__ T,
-                                                      const double *__restrict__ X, int m, double *__restrict__ lam_out,
-                                                      double *__restrict__ V_out, double *__restrict__ check) {
+                                                      const double *__restrict__ X, int m, int u0,
+                                                      double *__restrict__ lam_out, double *__restrict__ V_out,
+                                                      double *__restrict__ check) {
   __shared__ double lam[kMpMaxJ];
+  __shared__ int rk[kMpMaxJ];
   const int tid = threadIdx.x, nt = blockDim.x;
   const double *S = G;
   const double *P = G + (int64_t)m * m;
   for (int i = tid; i < m; i += nt) lam[i] = S[i + (int64_t)m * i] / P[i + (int64_t)m * i];
   __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    const double di = lam[i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) rank += (lam[j] > di) || (lam[j] == di && j < i);
+    rk[i] = rank;
+  }
+  __syncthreads();
   double res = 0.0, orth = 0.0, lmax = 0.0;
   for (int e = tid; e < m * m; e += nt) {
     const int i = e % m, j = e / m;
-    res = fmax(res, fabs(T[e] - X[e] * lam[j]));
+    // columns sorted at or past u0 span the unresolved tail clusters: not eigenvectors
+    if (rk[j] < u0) res = fmax(res, fabs(T[e] - X[e] * lam[j]));
     orth = fmax(orth, fabs(P[e] - (i == j ? 1.0 : 0.0)));
     if (!(T[e] == T[e]) || !(P[e] == P[e])) res = INFINITY;  // NaN fails the check
   }
@@ -833,8 +853,7 @@ __global__ void __launch_bounds__(1024) k_mp_finalize(const double *__restrict__
   }
   for (int i = tid; i < m; i += nt) {
     const double di = lam[i];
-    int rank = 0;
-    for (int j = 0; j < m; ++j) rank += (lam[j] > di) || (lam[j] == di && j < i);
+    const int rank = rk[i];
     lam_out[rank] = di;
     const double *col = X + (int64_t)m * i;
     double best = -1.0;
@@ -925,7 +944,12 @@ int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStrea
 
 // One level: eigenvectors of A (m x m, lda) into out (m x m, ld m).  noise is
 // ||A||_F of the top problem: the float64 noise floor of every level.
-int mp_level(const double *A, int lda, int m, double noise, int depth, const MpWork &w, double *out, cudaStream_t s) {
+// budget >= 0: clusters whose eigenvalues, with everything after them in
+// descending order (tail_after this level's matrix, accurate to tail_err),
+// sum to at most budget are left unresolved; their column count goes to
+// *skipped.
+int mp_level(const double *A, int lda, int m, double noise, int depth, const MpWork &w, double *out, cudaStream_t s,
+             double budget, double tail_after, double tail_err, int *skipped) {
   double *tx0 = w.tx(depth, 0), *tx1 = w.tx(depth, 1);
   double *G = w.g(depth), *E = w.e(depth);
   int *label = w.labels + depth * w.J, *perm = w.perms + depth * w.J;
@@ -974,7 +998,21 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   TK_CUDA(cudaMemcpyAsync(&h, dinfo, sizeof h, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   double *X = cur + (size_t)m * m;
-  for (int k = 0; k < h.nclusters; ++k) {
+  // suffix sums of the clusters' eigenvalue approximations; the first
+  // cluster whose suffix (with its error) fits the budget, and all after it,
+  // stay unresolved: a rank cut never falls inside them
+  double suffix[kMpMaxJ + 1];
+  suffix[h.nclusters] = 0.0;
+  for (int k = h.nclusters - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + h.csum[k];
+  int first_skip = h.nclusters;
+  if (budget >= 0.0)
+    for (int k = 0; k < h.nclusters; ++k)
+      if (suffix[k] + tail_after + tail_err + (double)(m - h.start[k]) * h.delta <= budget) {
+        first_skip = k;
+        break;
+      }
+  if (first_skip < h.nclusters) *skipped += m - h.start[first_skip];
+  for (int k = 0; k < first_skip; ++k) {
     const int c0 = h.start[k], mc = h.start[k + 1] - c0;
     if (mc < 2 || depth + 1 >= kMaxDepth) continue;
     // C = X_c^T A X_c; a multiple of I up to the noise floor needs no rotation
@@ -986,7 +1024,8 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
     if (dev <= kClusterC * mc * kU * noise) continue;
     double *Q = w.e(depth + 1);  // the child's E is free once it has returned
     double *Qc = w.t(depth + 1);
-    TK_CHECK(mp_level(C, mc, mc, noise, depth + 1, w, Qc, s));
+    TK_CHECK(mp_level(C, mc, mc, noise, depth + 1, w, Qc, s, budget, tail_after + suffix[k + 1],
+                      tail_err + (double)(m - h.start[k + 1]) * h.delta, skipped));
     // X_c <- X_c Q
     TK_CHECK(gemm(m, mc, mc, X + (size_t)m * c0, m, 0, Qc, mc, nullptr, 0, Q, m, s));
     k_copy_cols<<<(m * mc + 255) / 256, 256, 0, s>>>(Q, m, X + (size_t)m * c0, m, m, mc);
@@ -1003,7 +1042,7 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
 // Returns TUCKER_OK with *verified = 1 when lam / V hold a verified result;
 // *verified = 0 leaves them to the float64 Jacobi.
 int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
-                  cudaStream_t s, Prof *prof) {
+                  cudaStream_t s, Prof *prof, double tail_budget) {
   *verified = 0;
   if (J < 1 || J > kMpMaxJ) return TUCKER_OK;
   const int m = (int)J;
@@ -1021,20 +1060,20 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   double dev = 0.0, noise = 0.0;
   TK_CHECK(scalar_deviation(d_S, m, m, w, s, &dev, &noise));
   double *X = w.c(kMaxDepth - 1);  // never a cluster block: the deepest level takes no clusters
-  int sw = 0;
+  int sw = 0, skipped = 0;
   TK_CUDA(cudaMemsetAsync(w.sweeps, 0, sizeof(int), s));
   if (dev <= kClusterC * m * kU * noise) {
     k_set_identity<<<(m * m + 255) / 256, 256, 0, s>>>(X, m, m);  // a multiple of I: V = I
     TK_LAUNCHED();
   } else {
-    TK_CHECK(mp_level(d_S, m, m, noise, 0, w, X, s));
+    TK_CHECK(mp_level(d_S, m, m, noise, 0, w, X, s, tail_budget, 0.0, 0.0, &skipped));
   }
   // final products, Rayleigh quotients, verification, output
   double *tx0 = w.tx(0, 0);
   k_copy_cols<<<(m * m + 255) / 256, 256, 0, s>>>(X, m, tx0 + (size_t)m * m, m, m, m);
   TK_LAUNCHED();
   TK_CHECK(products(d_S, m, m, tx0, w.g(0), s));
-  k_mp_finalize<<<1, 1024, 0, s>>>(w.g(0), tx0, tx0 + (size_t)m * m, m, d_lam, d_V, w.check);
+  k_mp_finalize<<<1, 1024, 0, s>>>(w.g(0), tx0, tx0 + (size_t)m * m, m, m - skipped, d_lam, d_V, w.check);
   TK_LAUNCHED();
   double chk[3];
   TK_CUDA(cudaMemcpyAsync(chk, w.check, sizeof chk, cudaMemcpyDeviceToHost, s));

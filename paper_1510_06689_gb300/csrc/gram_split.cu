@@ -847,22 +847,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
 }
 
 // S_ij = sum over CTAs of (C_ij + C_ji) 2^(ref_i + ref_j - 43); NaN throughout
-// when the largest magnitude is not finite (Y holds Inf or NaN).
+// when the largest magnitude is not finite (Y holds Inf or NaN).  Eight
+// threads per entry take every eighth partial and combine by a fixed
+// shuffle tree, so the result is the same on every run.
 __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, const int *__restrict__ refs,
                                                            int nsplit, int J,
                                                            const unsigned long long *__restrict__ gmax, int is_f64,
                                                            double *__restrict__ S) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= J * J) return;
-  const int i = idx % J, j = idx / J;
+  const int idx = blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3), sub = threadIdx.x & 7;
+  const bool live = idx < J * J;
+  const int i = live ? idx % J : 0, j = live ? idx / J : 0;
   double s = 0.0;
-  for (int sp = 0; sp < nsplit; ++sp) {
-    const float2 *c = reinterpret_cast<const float2 *>(ws) + (size_t)sp * kRows * kRows;
-    const float2 a = c[i * kRows + j], b = c[j * kRows + i];
-    const int ri = refs[sp * kRows + i], rj = refs[sp * kRows + j];
-    if (ri != kZeroExp && rj != kZeroExp)
-      s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - 43);
-  }
+  if (live)
+    for (int sp = sub; sp < nsplit; sp += 8) {
+      const float2 *c = reinterpret_cast<const float2 *>(ws) + (size_t)sp * kRows * kRows;
+      const float2 a = c[i * kRows + j], b = c[j * kRows + i];
+      const int ri = refs[sp * kRows + i], rj = refs[sp * kRows + j];
+      if (ri != kZeroExp && rj != kZeroExp)
+        s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - 43);
+    }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (!live || sub != 0) return;
   const unsigned long long gm = *gmax;
   const bool finite = is_f64 ? gm < 0x7FF0000000000000ull : gm < 0x7F800000ull;
   S[i + (int64_t)J * j] = finite ? s : __longlong_as_double(0x7FF8000000000000ll);
@@ -1019,7 +1026,7 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   }
   if (prof) prof->end((double)J * (J + 1) * (double)p.K, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
-  k_gram_split_reduce<<<(unsigned)((J * J + 255) / 256), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
+  k_gram_split_reduce<<<(unsigned)((J * J + 31) / 32), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
                                                                       d_S);
   TK_LAUNCHED();
   if (prof) prof->end((double)p.nsplit * J * J * 2, (double)p.nsplit * kRows * kRows * 8, 1);

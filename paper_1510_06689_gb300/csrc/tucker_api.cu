@@ -387,7 +387,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     const int64_t ews = eig_workspace_doubles(J);
     if (ews > 0) TK_CHECK(eigws.alloc(sizeof(double) * ews, s));
     TK_CHECK(launch_eig(S.as<double>(), J, lam.as<double>(), V.as<double>(), ews > 0 ? eigws.as<double>() : nullptr,
-                        d_info, s, &prof));
+                        d_info, s, &prof, keep_all ? -1.0 : threshold));
     // rank step
     TK_CHECK(launch_rank_cut(lam.as<double>(), J, threshold, keep_all, d_rank, d_tail, s, &prof));
     TK_CUDA(cudaMemcpyAsync(h, d_tail, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
