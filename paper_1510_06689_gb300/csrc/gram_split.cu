@@ -343,6 +343,93 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
   if (lane == 0 && gm != 0u) atomicMax(gmax, mag_pattern(gm, kF64));
 }
 
+// The exponent pass for L > 1 with 16-byte column strides (L sizeof(T) a
+// multiple of 16, Y 16-byte aligned): a group's rows pass through shared
+// memory in stages of RS rows, each thread copying 16-byte chunks (2 float64
+// or 4 float32 of consecutive columns, never straddling a run of L) with
+// cp.async, two stages in flight; a thread reads back only its own chunks,
+// so the stream needs no barrier until the per-column maxima are combined.
+template <typename T>
+__global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict__ y, int64_t L, int J, int64_t K,
+                                                            int *__restrict__ E,
+                                                            unsigned long long *__restrict__ gmax,
+                                                            int *__restrict__ colexp) {
+  constexpr bool kF64 = sizeof(T) == 8;
+  constexpr int V = 16 / (int)sizeof(T);  // entries per chunk
+  constexpr int NQ = kGroup / V;          // chunks per row of a group
+  constexpr int RT = 512 / NQ;            // threads per chunk column
+  constexpr int RS = 4 * RT;              // rows per stage: four chunks per thread
+  extern __shared__ uint4 stg[];          // 2 stages x RS x NQ chunks
+  __shared__ unsigned rmax[kRows];
+  __shared__ unsigned cmax[kGroup];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int q = tid % NQ, r0 = tid / NQ;
+  const int64_t c0 = (int64_t)blockIdx.x * kGroup;
+  const int ncols = (int)min((int64_t)kGroup, K - c0);
+  const bool valid = V * q < ncols;
+  int64_t goff = 0;
+  if (valid) {
+    const int64_t c = c0 + V * q, b = c / L, l = c - b * L;
+    goff = l + L * (int64_t)J * b;
+  }
+  for (int i = tid; i < kRows; i += 512) rmax[i] = 0u;
+  for (int i = tid; i < kGroup; i += 512) cmax[i] = 0u;
+  __syncthreads();
+  const int nst = (J + RS - 1) / RS;
+  auto issue = [&](int st) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = st * RS + r0 + RT * u;
+      if (valid && i < J) {
+        const uint32_t dst = smem_addr(&stg[((st & 1) * RS + r0 + RT * u) * NQ + q]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(y + goff + L * (int64_t)i)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  unsigned colm[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) colm[v] = 0u;
+  issue(0);
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) issue(st + 1);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // stage st has landed (this thread's copies)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = st * RS + r0 + RT * u;  // uniform across the warp (a warp has one r0)
+      if (i >= J) continue;
+      unsigned mr = 0u;
+      if (valid) {
+        const uint4 w = stg[((st & 1) * RS + r0 + RT * u) * NQ + q];
+        const T *e = reinterpret_cast<const T *>(&w);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const unsigned mv = hi_mag(e[v]);
+          mr = max(mr, mv);
+          colm[v] = max(colm[v], mv);
+        }
+      }
+      mr = __reduce_max_sync(0xffffffffu, mr);
+      if (lane == 0) atomicMax(&rmax[i], mr);
+    }
+  }
+  if (valid)
+#pragma unroll
+    for (int v = 0; v < V; ++v) atomicMax(&cmax[V * q + v], colm[v]);
+  __syncthreads();
+  if (colexp)
+    for (int cc = tid; cc < ncols; cc += 512) colexp[c0 + cc] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
+  unsigned gm = 0u;
+  for (int i = tid; i < J; i += 512) {
+    E[(int64_t)blockIdx.x * J + i] = table_exp(mag_pattern(rmax[i], kF64), kF64);
+    gm = max(gm, rmax[i]);
+  }
+  gm = __reduce_max_sync(0xffffffffu, gm);
+  if (lane == 0 && gm != 0u) atomicMax(gmax, mag_pattern(gm, kF64));
+}
+
 template <typename T, int kMode>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict__ y, int64_t L, SplitPlan p,
                                                             const int *__restrict__ Etab,
@@ -1001,7 +1088,21 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   const int mode = L == 1 ? kColsStrided
                           : (L % 8 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) ? kColsContig : kColsGeneric;
   if (prof) prof->begin(TUCKER_PHASE_SCALE);
-  if (f64)
+  const bool async_exp = L > 1 && (L * (int64_t)(f64 ? 8 : 4)) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
+  if (async_exp) {
+    constexpr size_t kExpSmem = (size_t)2 * 8 * 256 * 16;  // 2 stages x RS x NQ chunks (the same for both types)
+    if (f64) {
+      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kExpSmem));
+      k_rowgroup_exp_async<double><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
+          static_cast<const double *>(y), L, (int)J, p.K, w.table, w.gmax, d_colexp);
+    } else {
+      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kExpSmem));
+      k_rowgroup_exp_async<float><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
+          static_cast<const float *>(y), L, (int)J, p.K, w.table, w.gmax, d_colexp);
+    }
+  } else if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
                                                                contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
   else
