@@ -112,11 +112,12 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
 // Tiled tensor map of a float64 (f64) or float32 array: rank dimensions
 // (innermost first), byte strides of dimensions 1..rank-1 (multiples of 16),
-// box extents; no swizzle, out-of-range elements read as zero.  Calls
+// box extents; swizzle 0 (none), 64 or 128 (bytes); out-of-range elements
+// read as zero.  Calls
 // cuTensorMapEncodeTiled through the runtime's driver entry point; false when
 // it is unavailable or refuses the map.
 bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const uint64_t *dims,
-                 const uint64_t *strides_bytes, const uint32_t *box);
+                 const uint64_t *strides_bytes, const uint32_t *box, int swizzle = 0);
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
                       const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp = nullptr);
 // *d_out = trace of the J x J matrix S (column-major), summed in index order.

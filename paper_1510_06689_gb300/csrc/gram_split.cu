@@ -114,10 +114,12 @@ __device__ void cta_row_ref(const int *__restrict__ Etab, int J, int64_t g_begin
 
 struct SplitPlan {
   int J;
-  int64_t K;
+  int64_t K;               // columns (L > 1 tiled path: 32 per chunk of 8 l x 4 b)
   int64_t cols_per_split;  // a multiple of kGroup, so groups never straddle CTAs
   int nsplit;
   int64_t ngroups;
+  int64_t L8;              // tiled path (L > 1): L / 8 chunks per quad of b; 0 otherwise
+  int64_t B;
 };
 
 // round(|y| 2^(21 - E)) with the sign of y (ties away from zero) from the
@@ -349,12 +351,16 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
 // or 4 float32 of consecutive columns, never straddling a run of L) with
 // cp.async, two stages in flight; a thread reads back only its own chunks,
 // so the stream needs no barrier until the per-column maxima are combined.
-template <typename T>
+// kOct (float64): the group is 16 consecutive chunks of the tiled Gram (8
+// consecutive l of 4 consecutive b each, chunk ch at l = 8 (ch % L8),
+// b = 4 (ch / L8)), so its exponents are the ones that kernel's groups need.
+template <typename T, bool kOct>
 __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict__ y, int64_t L, int J, int64_t K,
-                                                            int *__restrict__ E,
+                                                            int64_t L8, int64_t B, int *__restrict__ E,
                                                             unsigned long long *__restrict__ gmax,
                                                             int *__restrict__ colexp) {
   constexpr bool kF64 = sizeof(T) == 8;
+  static_assert(!kOct || kF64, "the tiled groups take float64");
   constexpr int V = 16 / (int)sizeof(T);  // entries per chunk
   constexpr int NQ = kGroup / V;          // chunks per row of a group
   constexpr int RT = 512 / NQ;            // threads per chunk column
@@ -366,12 +372,23 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
   const int q = tid % NQ, r0 = tid / NQ;
   const int64_t c0 = (int64_t)blockIdx.x * kGroup;
   const int ncols = (int)min((int64_t)kGroup, K - c0);
-  const bool valid = V * q < ncols;
-  int64_t goff = 0;
-  if (valid) {
-    const int64_t c = c0 + V * q, b = c / L, l = c - b * L;
-    goff = l + L * (int64_t)J * b;
-  }
+  // the chunk q's first column (l, b) and its offset
+  auto chunk_col = [&](int qq, int64_t &l, int64_t &b) -> bool {
+    if (kOct) {
+      const int64_t ch = c0 / 32 + (qq >> 4);
+      const int w = qq & 15;
+      b = 4 * (ch / L8) + (w >> 2);
+      l = 8 * (ch - (ch / L8) * L8) + 2 * (w & 3);
+      return V * qq < ncols && b < B;
+    }
+    const int64_t c = c0 + V * qq;
+    b = c / L;
+    l = c - b * L;
+    return V * qq < ncols;
+  };
+  int64_t lq = 0, bq = 0;
+  const bool valid = chunk_col(q, lq, bq);
+  const int64_t goff = valid ? lq + L * (int64_t)J * bq : 0;
   for (int i = tid; i < kRows; i += 512) rmax[i] = 0u;
   for (int i = tid; i < kGroup; i += 512) cmax[i] = 0u;
   __syncthreads();
@@ -420,7 +437,10 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
     for (int v = 0; v < V; ++v) atomicMax(&cmax[V * q + v], colm[v]);
   __syncthreads();
   if (colexp)
-    for (int cc = tid; cc < ncols; cc += 512) colexp[c0 + cc] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
+    for (int cc = tid; cc < ncols; cc += 512) {
+      int64_t l, b;
+      if (chunk_col(cc / V, l, b)) colexp[l + cc % V + L * b] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
+    }
   unsigned gm = 0u;
   for (int i = tid; i < J; i += 512) {
     E[(int64_t)blockIdx.x * J + i] = table_exp(mag_pattern(rmax[i], kF64), kF64);
@@ -754,7 +774,33 @@ __device__ __forceinline__ void tmem_ld4x4(uint32_t taddr, uint32_t (&r)[4][4]) 
       : "memory");
 }
 
-template <typename T>
+// Row `row`, chunk columns of b offset kg (8 consecutive l) from a box
+// {8 l, 128 rows, 4 b} stored with the 64-byte swizzle: the 16-byte piece u of
+// line (kg 128 + row) sits at piece u ^ ((row >> 1) & 3), so each quarter-warp's
+// 16-byte loads hit eight distinct bank groups.
+__device__ __forceinline__ void convert_oct(const unsigned char *raw, int row, int kg, int cvt, unsigned char *st) {
+  uint32_t w[kTiles][4];
+  const unsigned char *line = raw + (kg * kRows + row) * 64;
+  const int sw = (row >> 1) & 3;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 y2 = *reinterpret_cast<const double2 *>(line + ((u ^ sw) << 4));
+    float a1, a2, a3, b1, b2, b3;
+    split3(scaled_float(y2.x, cvt), a1, a2, a3);
+    split3(scaled_float(y2.y, cvt), b1, b2, b3);
+    const uint32_t p3 = bf16_pair(a3, b3);
+    w[0][u] = bf16_pair(a1, b1);
+    w[1][u] = bf16_pair(a2, b2);
+    w[2][u] = bf16x2_mul(p3, 0x40004000u);
+    w[3][u] = bf16x2_mul(p3, 0x3B803B80u);
+  }
+  const int off = (row >> 3) * kSbo + kg * 128 + (row & 7) * 16;
+#pragma unroll
+  for (int t = 0; t < kTiles; ++t)
+    *reinterpret_cast<uint4 *>(st + t * kTileBytes + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+template <typename T, bool kOct>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_constant__ CUtensorMap ymap, SplitPlan p,
                                                                  const int *__restrict__ Etab,
                                                                  int *__restrict__ refs, double *__restrict__ ws,
@@ -811,7 +857,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     const int slot = ch % kRing;
     const uint32_t bar = smem_addr(&raw_full[slot]);
     mbar_expect_tx(bar, (uint32_t)(kChunk * kRows * sizeof(T)));
-    tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
+    if (kOct) {
+      const int64_t gch = c_begin / kChunk + ch;
+      tma_load_3d(smem_addr(ring + slot * kRawBytes), &ymap, (int)(8 * (gch % p.L8)), 0, (int)(4 * (gch / p.L8)),
+                  bar);
+    } else {
+      tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
+    }
   };
   int issued = 0;
   if (tid == 0)
@@ -873,7 +925,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
       bool ok = mbar_wait(smem_addr(&raw_full[u]), ring_par);
       if (ok && ch >= 2) ok = mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)(((u + 2) >> 1) & 1));
       if (ok)
-        convert_bulk<T>(reinterpret_cast<const T *>(ring + u * kRawBytes), row, kg, cvt, stages + (u & 1) * kStageBytes);
+        if constexpr (kOct) convert_oct(ring + u * kRawBytes, row, kg, cvt, stages + (u & 1) * kStageBytes);
+        else convert_bulk<T>(reinterpret_cast<const T *>(ring + u * kRawBytes), row, kg, cvt, stages + (u & 1) * kStageBytes);
       else
         stop = 1;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -964,10 +1017,14 @@ __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restr
 
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kRows * kRows * sizeof(float2) + 1024;
 
-SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
+// oct: the tiled L > 1 path, whose columns are counted as 32 per chunk of
+// 8 l x 4 b (a ragged last quad of b reads zeros past B)
+SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, bool oct = false) {
   SplitPlan p{};
   p.J = (int)J;
-  p.K = L * B;
+  p.B = B;
+  p.L8 = oct ? L / 8 : 0;
+  p.K = oct ? (L / 8) * ((B + 3) / 4) * kChunk : L * B;
   p.ngroups = (p.K + kGroup - 1) / kGroup;
   const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ngroups));
   const int64_t groups_per = (p.ngroups + ns - 1) / ns;
@@ -976,8 +1033,9 @@ SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   return p;
 }
 
-// workspace (in doubles): per-CTA partials (double-float pairs) | exponent
-// table (ints) | per-CTA row reference exponents (ints) | gmax | error flag
+// workspace (in doubles): gmax | error flag | (2 spare) | per-CTA partials
+// (double-float pairs) | exponent table (ints) | per-CTA row reference
+// exponents (ints)
 struct SplitWs {
   double *partials;
   int *table;
@@ -989,14 +1047,27 @@ struct SplitWs {
 SplitWs split_ws(double *d_ws, const SplitPlan &p) {
   const int64_t np = (int64_t)p.nsplit * kRows * kRows;
   const int64_t tab = (p.ngroups * p.J + 1) / 2;
-  const int64_t nref = (int64_t)p.nsplit * kRows / 2;
   SplitWs w;
-  w.partials = d_ws;
-  w.table = reinterpret_cast<int *>(d_ws + np);
-  w.refs = reinterpret_cast<int *>(d_ws + np + tab);
-  w.gmax = reinterpret_cast<unsigned long long *>(d_ws + np + tab + nref);
-  w.err = reinterpret_cast<int *>(d_ws + np + tab + nref + 1);
+  w.gmax = reinterpret_cast<unsigned long long *>(d_ws);
+  w.err = reinterpret_cast<int *>(d_ws + 1);
+  w.partials = d_ws + 4;
+  w.table = reinterpret_cast<int *>(d_ws + 4 + np);
+  w.refs = reinterpret_cast<int *>(d_ws + 4 + np + tab);
   return w;
+}
+
+int64_t split_ws_doubles(const SplitPlan &p) {
+  return 4 + (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + (int64_t)p.nsplit * kRows / 2 + 1;
+}
+
+// the tiled L > 1 path: float64, L a multiple of 8, 16-byte aligned Y
+bool use_oct(const void *y, tucker_dtype dt, int64_t L, int64_t B) {
+  static const bool regs = [] {
+    const char *e = std::getenv("TUCKER_GRAM_SPLIT_KERNEL");
+    return e && std::strcmp(e, "regs") == 0;
+  }();
+  return !regs && dt == TUCKER_F64 && L > 1 && L % 8 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0 &&
+         L < (1ll << 31) && (B + 3) / 4 * 4 < (1ll << 31);
 }
 
 template <typename T, int kMode>
@@ -1027,9 +1098,26 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
   const uint64_t strides[1] = {col_bytes};
   const uint32_t box[2] = {kRows, kChunk};
   if (!encode_tmap(&map, sizeof(T) == 8, y, 2, dims, strides, box)) return TUCKER_OK;
-  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kBulkSmemBytes));
-  k_gram_split_bulk<T><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
+  k_gram_split_bulk<T, false><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
+  TK_LAUNCHED();
+  *ran = true;
+  return TUCKER_OK;
+}
+
+// the tiled L > 1 kernel: boxes {8 l, 128 rows, 4 b} of the 3-D map over Y (L, J, B), 64-byte swizzle
+int run_gram_split_oct(const void *y, int64_t L, const SplitPlan &p, const SplitWs &w, cudaStream_t s, bool *ran) {
+  *ran = false;
+  CUtensorMap map;
+  const uint64_t dims[3] = {(uint64_t)L, (uint64_t)p.J, (uint64_t)p.B};
+  const uint64_t strides[2] = {(uint64_t)L * 8, (uint64_t)L * p.J * 8};
+  const uint32_t box[3] = {8, kRows, 4};
+  if (!encode_tmap(&map, true, y, 3, dims, strides, box, 64)) return TUCKER_OK;
+  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kBulkSmemBytes));
+  k_gram_split_bulk<double, true><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials,
+                                                                            w.err);
   TK_LAUNCHED();
   *ran = true;
   return TUCKER_OK;
@@ -1038,7 +1126,7 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
 }  // namespace
 
 bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const uint64_t *dims,
-                 const uint64_t *strides_bytes, const uint32_t *box) {
+                 const uint64_t *strides_bytes, const uint32_t *box, int swizzle) {
   static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -1059,13 +1147,17 @@ bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const u
   }
   return encode(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
                 const_cast<void *>(base), gdim, gstride, bx, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                swizzle == 64    ? CU_TENSOR_MAP_SWIZZLE_64B
+                : swizzle == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
-  const SplitPlan p = split_plan(L, J, B, dev);
-  return (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + (int64_t)p.nsplit * kRows / 2 + 4;
+  int64_t n = split_ws_doubles(split_plan(L, J, B, dev));
+  if (L > 1 && L % 8 == 0) n = std::max(n, split_ws_doubles(split_plan(L, J, B, dev, true)));
+  return n;
 }
 
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
@@ -1074,14 +1166,15 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
     set_error("split-precision Gram supports J <= %d (got %lld)", kRows, (long long)J);
     return TUCKER_EUNSUPPORTED;
   }
-  const SplitPlan p = split_plan(L, J, B, dev);
+  const bool oct = use_oct(y, dt, L, B);
+  const SplitPlan p = split_plan(L, J, B, dev, oct);
   if (p.ngroups > 0x7FFFFFFFll) {
     set_error("split-precision Gram: too many column groups (%lld)", (long long)p.ngroups);
     return TUCKER_EUNSUPPORTED;
   }
   const SplitWs w = split_ws(d_ws, p);
   const bool f64 = dt == TUCKER_F64;
-  const double in_bytes = (double)p.K * J * (f64 ? 8 : 4);
+  const double in_bytes = (double)L * B * J * (f64 ? 8 : 4);
   TK_CUDA(cudaMemsetAsync(w.gmax, 0, 2 * sizeof(double), s));  // gmax and the error flag
   const int contig_pairs = L == 1 && (2 * 256) % J == 0 && J % 2 == 0 &&
                            reinterpret_cast<uintptr_t>(y) % (f64 ? 16 : 8) == 0;
@@ -1091,16 +1184,21 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   const bool async_exp = L > 1 && (L * (int64_t)(f64 ? 8 : 4)) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0;
   if (async_exp) {
     constexpr size_t kExpSmem = (size_t)2 * 8 * 256 * 16;  // 2 stages x RS x NQ chunks (the same for both types)
-    if (f64) {
-      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (oct) {
+      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kExpSmem));
-      k_rowgroup_exp_async<double><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
-          static_cast<const double *>(y), L, (int)J, p.K, w.table, w.gmax, d_colexp);
+      k_rowgroup_exp_async<double, true><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
+          static_cast<const double *>(y), L, (int)J, p.K, p.L8, B, w.table, w.gmax, d_colexp);
+    } else if (f64) {
+      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kExpSmem));
+      k_rowgroup_exp_async<double, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
+          static_cast<const double *>(y), L, (int)J, p.K, 0, B, w.table, w.gmax, d_colexp);
     } else {
-      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kExpSmem));
-      k_rowgroup_exp_async<float><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
-          static_cast<const float *>(y), L, (int)J, p.K, w.table, w.gmax, d_colexp);
+      k_rowgroup_exp_async<float, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
+          static_cast<const float *>(y), L, (int)J, p.K, 0, B, w.table, w.gmax, d_colexp);
     }
   } else if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
@@ -1115,6 +1213,12 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (L == 1) {
     if (f64) TK_CHECK(run_gram_split_bulk<double>(y, p, w, s, &ran));
     else TK_CHECK(run_gram_split_bulk<float>(y, p, w, s, &ran));
+  } else if (oct) {
+    TK_CHECK(run_gram_split_oct(y, L, p, w, s, &ran));
+    if (!ran) {
+      set_error("split-precision Gram: the tensor map of the tiled path was refused");
+      return TUCKER_ECUDA;
+    }
   }
   if (!ran && f64) {
     if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided>(y, L, p, w, dev, s)));
@@ -1125,7 +1229,7 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
     else if (mode == kColsContig) TK_CHECK((run_gram_split<float, kColsContig>(y, L, p, w, dev, s)));
     else TK_CHECK((run_gram_split<float, kColsGeneric>(y, L, p, w, dev, s)));
   }
-  if (prof) prof->end((double)J * (J + 1) * (double)p.K, in_bytes, 1);
+  if (prof) prof->end((double)J * (J + 1) * (double)L * B, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
   k_gram_split_reduce<<<(unsigned)((J * J + 31) / 32), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
                                                                       d_S);
@@ -1136,9 +1240,12 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
 
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,
                      cudaStream_t s) {
-  const SplitPlan p = split_plan(L, J, B, dev);
-  const SplitWs w = split_ws(const_cast<double *>(d_ws), p);
-  TK_CUDA(cudaMemcpyAsync(h_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  (void)L;
+  (void)J;
+  (void)B;
+  (void)dev;
+  // the error flag sits at the same place for every plan (split_ws)
+  TK_CUDA(cudaMemcpyAsync(h_err, reinterpret_cast<const int *>(d_ws + 1), sizeof(int), cudaMemcpyDeviceToHost, s));
   return TUCKER_OK;
 }
 

@@ -48,7 +48,10 @@ def split_bound(y, L, J, B):
 @pytest.mark.parametrize("L,J,B", [(1, 128, 5000), (1, 64, 4096), (40, 128, 33), (7, 13, 5), (1600, 48, 3),
                                    (640, 32, 1), (1, 1, 1), (3, 100, 777), (1, 128, 64 * 152 * 9 + 17),
                                    # L == 1 tensor-map kernel: smallest J, ragged J and K, one column
-                                   (1, 2, 3001), (1, 34, 2049), (1, 126, 1), (1, 13, 700)])
+                                   (1, 2, 3001), (1, 34, 2049), (1, 126, 1), (1, 13, 700),
+                                   # L > 1 tiled kernel (float64, L % 8 == 0): chunks of 8 l x 4 b over
+                                   # many CTAs, a ragged last quad of b, ragged J, one row
+                                   (8, 128, 4 * 152 * 3 + 2), (16, 77, 1001), (24, 1, 9), (64, 128, 131)])
 def test_gram_split_bound(gpu_lib, L, J, B):
     rng = np.random.default_rng(L * 3 + J * 5 + B)
     y = rng.standard_normal(L * J * B)
@@ -59,15 +62,16 @@ def test_gram_split_bound(gpu_lib, L, J, B):
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
 
 
-def test_gram_split_exact_on_leading_digit_inputs(gpu_lib):
+@pytest.mark.parametrize("L,B", [(1, 3000), (8, 375)])
+def test_gram_split_exact_on_leading_digit_inputs(gpu_lib, L, B):
     """Entries j * 2^(E-7) with |j| <= 127: one digit each, so S must be exact."""
     rng = np.random.default_rng(7)
-    L, J, B = 1, 128, 3000
+    J = 128
     ints = rng.integers(-127, 128, size=L * J * B)
     ints[0] = 127  # max|Y| = 127/128 < 2^0, so E = 0 and the digit unit is 2^-7
     y = ints.astype(np.float64) / 128.0
     s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
-    m = ints.reshape((J, B), order="F").astype(np.int64)
+    m = ints.reshape((L, J, B), order="F").transpose(1, 0, 2).reshape(J, L * B).astype(np.int64)
     exact = m @ m.T  # integer matmul: exact (|entries| <= 127^2 * 3000)
     assert np.array_equal(s * 2 ** 14, exact.astype(np.float64))
 
@@ -104,7 +108,8 @@ def test_gram_split_local_exponents(gpu_lib):
     assert np.all(np.abs(s - ref) <= bound)
 
 
-@pytest.mark.parametrize("L,dtype,e", [(1, np.float64, 400), (3, np.float64, 400), (1, np.float32, 55),
+@pytest.mark.parametrize("L,dtype,e", [(1, np.float64, 400), (3, np.float64, 400), (8, np.float64, 400),
+                                       (1, np.float32, 55),
                                        (5, np.float32, 55)])
 def test_gram_split_rows_of_far_apart_magnitudes(gpu_lib, L, dtype, e):
     """Rows 2^(2e) apart keep their own relative accuracy: every row's products are
