@@ -35,8 +35,11 @@
 //     In the register-staged kernel the double-float C (128 KB) sits in
 //     shared memory beside two 32-column digit stages, so the converting
 //     threads keep their registers for a two-chunk prefetch; the tensor-map
-//     kernel (L == 1) keeps C in registers and its raw input in a ring of
-//     shared-memory slots.
+//     kernel keeps C in registers and its raw input in a ring of
+//     shared-memory slots.  It takes L == 1 (32 consecutive columns a chunk)
+//     and float64 L > 1 with L a multiple of 8, where a chunk is a box of
+//     nl octets of consecutive l times 4 / nl consecutive b (the Gram sums
+//     over columns in any order), nl chosen to pad the fewest columns.
 //
 // The exponents are read on the device, so the step needs no host round
 // trip.  The result is the Gram of Y rounded to 21 bits below each local
@@ -118,7 +121,10 @@ struct SplitPlan {
   int64_t cols_per_split;  // a multiple of kGroup, so groups never straddle CTAs
   int nsplit;
   int64_t ngroups;
-  int64_t L8;              // tiled path (L > 1): L / 8 chunks per quad of b; 0 otherwise
+  // tiled path (L > 1): a chunk is nl octets of l (8 l each) x nb = 4 / nl
+  // consecutive b; chunk ch covers octets nl (ch % nL) .. and b from nb (ch / nL)
+  int64_t nL;              // chunks along l (0: not the tiled path)
+  int nl, nb;
   int64_t B;
 };
 
@@ -351,12 +357,13 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
 // or 4 float32 of consecutive columns, never straddling a run of L) with
 // cp.async, two stages in flight; a thread reads back only its own chunks,
 // so the stream needs no barrier until the per-column maxima are combined.
-// kOct (float64): the group is 16 consecutive chunks of the tiled Gram (8
-// consecutive l of 4 consecutive b each, chunk ch at l = 8 (ch % L8),
-// b = 4 (ch / L8)), so its exponents are the ones that kernel's groups need.
+// kOct (float64): the group is 16 consecutive chunks of the tiled Gram (nl
+// octets of consecutive l times nb = 4 / nl consecutive b each; chunk ch
+// starts at octet nl (ch % nL) and at b = nb (ch / nL)), so its exponents are
+// the ones that kernel's groups need.
 template <typename T, bool kOct>
 __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict__ y, int64_t L, int J, int64_t K,
-                                                            int64_t L8, int64_t B, int *__restrict__ E,
+                                                            int64_t nL, int nl, int64_t B, int *__restrict__ E,
                                                             unsigned long long *__restrict__ gmax,
                                                             int *__restrict__ colexp) {
   constexpr bool kF64 = sizeof(T) == 8;
@@ -376,10 +383,11 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
   auto chunk_col = [&](int qq, int64_t &l, int64_t &b) -> bool {
     if (kOct) {
       const int64_t ch = c0 / 32 + (qq >> 4);
-      const int w = qq & 15;
-      b = 4 * (ch / L8) + (w >> 2);
-      l = 8 * (ch - (ch / L8) * L8) + 2 * (w & 3);
-      return V * qq < ncols && b < B;
+      const int w = qq & 15, kg = w >> 2;  // kg: the box's line block (b offset kg / nl, octet kg % nl)
+      const int64_t bb = ch / nL;
+      b = (4 / nl) * bb + kg / nl;
+      l = 8 * (nl * (ch - bb * nL) + kg % nl) + 2 * (w & 3);
+      return V * qq < ncols && b < B && l < L;
     }
     const int64_t c = c0 + V * qq;
     b = c / L;
@@ -858,8 +866,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     const uint32_t bar = smem_addr(&raw_full[slot]);
     mbar_expect_tx(bar, (uint32_t)(kChunk * kRows * sizeof(T)));
     if (kOct) {
-      const int64_t gch = c_begin / kChunk + ch;
-      tma_load_3d(smem_addr(ring + slot * kRawBytes), &ymap, (int)(8 * (gch % p.L8)), 0, (int)(4 * (gch / p.L8)),
+      const int64_t gch = c_begin / kChunk + ch, bb = gch / p.nL;
+      tma_load_4d(smem_addr(ring + slot * kRawBytes), &ymap, 0, 0, (int)(p.nl * (gch - bb * p.nL)), (int)(p.nb * bb),
                   bar);
     } else {
       tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
@@ -1023,8 +1031,25 @@ SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, boo
   SplitPlan p{};
   p.J = (int)J;
   p.B = B;
-  p.L8 = oct ? L / 8 : 0;
-  p.K = oct ? (L / 8) * ((B + 3) / 4) * kChunk : L * B;
+  p.nl = 1;
+  p.nb = 4;
+  p.nL = 0;
+  if (oct) {
+    // the chunk shape with the fewest padded columns; among equals, the longest runs of l
+    int64_t best = -1;
+    for (int nl = 1; nl <= 4; nl *= 2) {
+      const int64_t nL = (L / 8 + nl - 1) / nl, nB = (B + 4 / nl - 1) / (4 / nl);
+      if (best < 0 || nL * nB <= best) {
+        best = nL * nB;
+        p.nl = nl;
+        p.nb = 4 / nl;
+        p.nL = nL;
+      }
+    }
+    p.K = best * kChunk;
+  } else {
+    p.K = L * B;
+  }
   p.ngroups = (p.K + kGroup - 1) / kGroup;
   const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ngroups));
   const int64_t groups_per = (p.ngroups + ns - 1) / ns;
@@ -1106,14 +1131,15 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
   return TUCKER_OK;
 }
 
-// the tiled L > 1 kernel: boxes {8 l, 128 rows, 4 b} of the 3-D map over Y (L, J, B), 64-byte swizzle
+// the tiled L > 1 kernel: boxes {8 l, 128 rows, nl octets, nb b} of the 4-D
+// map over Y viewed as (l % 8, j, l / 8, b), 64-byte swizzle
 int run_gram_split_oct(const void *y, int64_t L, const SplitPlan &p, const SplitWs &w, cudaStream_t s, bool *ran) {
   *ran = false;
   CUtensorMap map;
-  const uint64_t dims[3] = {(uint64_t)L, (uint64_t)p.J, (uint64_t)p.B};
-  const uint64_t strides[2] = {(uint64_t)L * 8, (uint64_t)L * p.J * 8};
-  const uint32_t box[3] = {8, kRows, 4};
-  if (!encode_tmap(&map, true, y, 3, dims, strides, box, 64)) return TUCKER_OK;
+  const uint64_t dims[4] = {8, (uint64_t)p.J, (uint64_t)(L / 8), (uint64_t)p.B};
+  const uint64_t strides[3] = {(uint64_t)L * 8, 64, (uint64_t)L * p.J * 8};
+  const uint32_t box[4] = {8, kRows, (uint32_t)p.nl, (uint32_t)p.nb};
+  if (!encode_tmap(&map, true, y, 4, dims, strides, box, 64)) return TUCKER_OK;
   TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kBulkSmemBytes));
   k_gram_split_bulk<double, true><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials,
@@ -1188,17 +1214,17 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
       TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kExpSmem));
       k_rowgroup_exp_async<double, true><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
-          static_cast<const double *>(y), L, (int)J, p.K, p.L8, B, w.table, w.gmax, d_colexp);
+          static_cast<const double *>(y), L, (int)J, p.K, p.nL, p.nl, B, w.table, w.gmax, d_colexp);
     } else if (f64) {
       TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kExpSmem));
       k_rowgroup_exp_async<double, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
-          static_cast<const double *>(y), L, (int)J, p.K, 0, B, w.table, w.gmax, d_colexp);
+          static_cast<const double *>(y), L, (int)J, p.K, 1, 1, B, w.table, w.gmax, d_colexp);
     } else {
       TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kExpSmem));
       k_rowgroup_exp_async<float, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
-          static_cast<const float *>(y), L, (int)J, p.K, 0, B, w.table, w.gmax, d_colexp);
+          static_cast<const float *>(y), L, (int)J, p.K, 1, 1, B, w.table, w.gmax, d_colexp);
     }
   } else if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
