@@ -245,14 +245,38 @@ size_t jacobi32_smem(int n) {
 //      vectors that were nearly dependent become an orthonormal basis of the
 //      complement of the others.
 //   5. X = Q1 Z by the tridiagonalization's reflectors in reverse order.
+// Steps 4 and 5 apply reflectors kNb at a time in compact WY form,
+// H_j0 ... H_j0+nb-1 = I - V T V^T (T upper triangular, LAPACK's larft),
+// as two register-tiled products through shared memory: a reflector costs
+// a fraction of a matrix pass instead of two passes and two barriers.
 // Accuracy is float32's (~2^-23 ||A|| / gap), as the Jacobi sweeps gave; the
 // float64 refinement that follows does not depend on which one ran.
 // Writes X (float64, columns in descending eigenvalue order).
 // ---------------------------------------------------------------------------
 constexpr int kT32Threads = 512;
+constexpr int kNb = 8;  // reflectors per compact WY block
 
-// floats: A (n x (n+1)), Z (n x (n+1)), W (n x n), 4 x 128 partials, 10 n vectors
-size_t tri32_smem(int n) { return (size_t)(2 * n * (n + 1) + n * n + 4 * kMpMaxJ + 10 * n) * sizeof(float) + 64; }
+// row stride of Z and W: a multiple of 4 floats (16-byte rows for vector
+// loads) and 4 more, so that column walks spread over 8 banks
+__host__ __device__ __forceinline__ int tri32_ld(int n) { return ((n + 3) & ~3) + 4; }
+
+// float offsets of the shared-memory regions, each 16-byte aligned:
+// A (n x (n+1)), Z and W (n x ld), WY partials (4 x kNb x 128), the T
+// factors of the reflector blocks and 8 n-vectors
+struct Tri32Layout {
+  int z, w, part, tf, vec, total;
+  __host__ __device__ explicit Tri32Layout(int n) {
+    auto up = [](int v) { return (v + 3) & ~3; };
+    const int ld = tri32_ld(n);
+    z = up(n * (n + 1));
+    w = z + up(n * ld);
+    part = w + up(n * ld);
+    tf = part + 4 * kNb * kMpMaxJ;
+    vec = tf + ((n + kNb - 1) / kNb) * kNb * kNb;
+    total = vec + 8 * n;
+  }
+};
+size_t tri32_smem(int n) { return (size_t)Tri32Layout(n).total * sizeof(float) + 64; }
 
 __device__ __forceinline__ float warp_sum32(float v) {
 #pragma unroll
@@ -303,55 +327,263 @@ __device__ __forceinline__ void warp_larfg(const float *x, int stride, int m, in
   }
 }
 
-// Apply H = I - tau v v^T (v(0) = 1 at row r0; v(r) for r > r0 at
-// vcol[r * vstride]) from the left to columns c0..n-1 of M (row-major, ld),
-// rows r0..n-1.  Thread (column c = tid % 128, part = tid / 128) takes rows
-// r0 + part, r0 + part + 4, ...; ends with a barrier.
-__device__ __forceinline__ void apply_reflector(float *__restrict__ M, int ld, int n, int r0, int c0, float tau,
-                                                const float *__restrict__ vcol, int vstride, float *__restrict__ pd) {
-  const int tid = threadIdx.x, c = tid & (kMpMaxJ - 1), part = tid >> 7;
-  const bool mine = c >= c0 && c < n;
-  float acc = 0.f;
-  if (mine) {
-    if (part == 0) acc = M[r0 * ld + c];  // v(0) = 1
-    int r = r0 + (part == 0 ? 4 : part);
-    for (; r + 12 < n; r += 16) {  // four rows of this part at a time, loads first
-      const float v0 = vcol[r * vstride], v1 = vcol[(r + 4) * vstride], v2 = vcol[(r + 8) * vstride],
-                  v3 = vcol[(r + 12) * vstride];
-      const float m0 = M[r * ld + c], m1 = M[(r + 4) * ld + c], m2 = M[(r + 8) * ld + c], m3 = M[(r + 12) * ld + c];
-      acc = fmaf(v0, m0, fmaf(v1, m1, fmaf(v2, m2, fmaf(v3, m3, acc))));
-    }
-    for (; r < n; r += 4) acc = fmaf(vcol[r * vstride], M[r * ld + c], acc);
+__device__ __forceinline__ float4 fma4(float a, float4 b, float4 c) {
+  return make_float4(fmaf(a, b.x, c.x), fmaf(a, b.y, c.y), fmaf(a, b.z, c.z), fmaf(a, b.w, c.w));
+}
+
+// Column i of T (kNb x kNb, upper triangular) of a block of reflectors from
+// G(k, l) = v_k^T v_l (k < l, row-major kNb x kNb) and the block's taus
+// (zero past its last reflector): T = (diag(1 / tau) + striu(G))^-1 by back
+// substitution, x_i = tau_i, x_k = -tau_k sum_{l=k+1..i} G(k, l) x_l, which
+// stays valid (a zero row and column) for tau = 0.  Equals LAPACK's larft
+// recurrence T(0:i, i) = -tau_i T(0:i, 0:i) V(:, 0:i)^T v_i.
+__device__ __forceinline__ void wy_t_column(const float *__restrict__ G, const float *__restrict__ taus, int i,
+                                            float *__restrict__ T) {
+  float x[kNb];
+#pragma unroll
+  for (int k = kNb - 1; k >= 0; --k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int l = k + 1; l < kNb; ++l) acc = l <= i ? fmaf(G[k * kNb + l], x[l], acc) : acc;
+    x[k] = k > i ? 0.f : (k == i ? taus[k] : -taus[k] * acc);
   }
-  pd[part * kMpMaxJ + c] = acc;
+#pragma unroll
+  for (int k = 0; k < kNb; ++k) T[k * kNb + i] = x[k];
+}
+
+// T factors of the nblk blocks of kNb reflectors in columns 0, kNb, ... of V
+// (ldv; explicit unit entries and zeros above them; block b's rows start at
+// r0 + b kNb): all the G = V_b^T V_b products at once (a warp per entry),
+// then a thread per column of T.  taus[j] for reflector j (j < nref); the T
+// factors go to Tf + b kNb^2 and G to Gs (nblk kNb^2 floats).  Ends with a
+// barrier.
+__device__ void form_wy_ts(const float *__restrict__ V, int ldv, int nblk, int nref, int r0, int n,
+                           const float *__restrict__ taus, float *__restrict__ Tf, float *__restrict__ Gs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = warp; e < nblk * kNb * kNb; e += nw) {  // warp-uniform
+    const int b = e / (kNb * kNb), k = (e / kNb) % kNb, i = e % kNb, j0 = b * kNb;
+    if (k >= i) continue;
+    float g = 0.f;
+    for (int r = r0 + j0 + lane; r < n; r += 32) g = fmaf(V[r * ldv + j0 + k], V[r * ldv + j0 + i], g);
+    g = warp_sum32(g);
+    if (lane == 0) Gs[e] = g;
+  }
   __syncthreads();
-  if (mine) {
-    const float s = tau * (pd[c] + pd[kMpMaxJ + c] + pd[2 * kMpMaxJ + c] + pd[3 * kMpMaxJ + c]);
-    if (part == 0) M[r0 * ld + c] -= s;
-    int r = r0 + (part == 0 ? 4 : part);
-    for (; r + 12 < n; r += 16) {
-      const float v0 = vcol[r * vstride], v1 = vcol[(r + 4) * vstride], v2 = vcol[(r + 8) * vstride],
-                  v3 = vcol[(r + 12) * vstride];
-      const float m0 = M[r * ld + c], m1 = M[(r + 4) * ld + c], m2 = M[(r + 8) * ld + c], m3 = M[(r + 12) * ld + c];
-      M[r * ld + c] = fmaf(-s, v0, m0);
-      M[(r + 4) * ld + c] = fmaf(-s, v1, m1);
-      M[(r + 8) * ld + c] = fmaf(-s, v2, m2);
-      M[(r + 12) * ld + c] = fmaf(-s, v3, m3);
-    }
-    for (; r < n; r += 4) M[r * ld + c] = fmaf(-s, vcol[r * vstride], M[r * ld + c]);
+  for (int t = tid; t < nblk * kNb; t += blockDim.x) {
+    const int b = t / kNb, i = t % kNb;
+    float tb[kNb];
+#pragma unroll
+    for (int k = 0; k < kNb; ++k) tb[k] = b * kNb + k < nref ? taus[b * kNb + k] : 0.f;
+    wy_t_column(Gs + b * kNb * kNb, tb, i, Tf + b * kNb * kNb);
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kT32Threads) k_eig32_tri(const double *__restrict__ A, int lda, int n,
+// M[r0:n, c0:n] <- (I - V op(T) V^T) M[r0:n, c0:n], op(T) = T or T^T, for
+// the kNb reflectors in columns j0.. of V (rows r0 .. n-1, zeros above each
+// unit diagonal entry, zero columns past the block's last reflector).  M is
+// row-major with a row stride ldm that is a multiple of 4 (16-byte rows).
+// Three phases, each ending with a barrier:
+//   A. part[p][j][c] = sum over rows r = r0 + p (mod 4) of V[r][j] M[r][c]
+//      (thread: a column quad, a pair of reflectors and a row class);
+//   B. P = op(T) sum_p part[p] (thread: a column);
+//   C. M[r][c] -= sum_j V[r][j] P[j][c] (thread: a column quad and every
+//      16th row; V's row is two 16-byte loads, P sits in registers).
+__device__ void apply_wy(float *__restrict__ M, int ldm, int n, int r0, int c0, const float *__restrict__ V, int ldv,
+                         int j0, const float *__restrict__ T, bool trans, float *__restrict__ part) {
+  const int tid = threadIdx.x;
+  const int q0 = c0 >> 2, nq = (n + 3) >> 2;
+  {
+    const int q = q0 + (tid & 31), g = (tid >> 5) & 3, p = tid >> 7;
+    if (q < nq) {
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll 4
+      for (int r = r0 + p; r < n; r += 4) {
+        const float4 m = *reinterpret_cast<const float4 *>(M + r * ldm + 4 * q);
+        const float2 v = *reinterpret_cast<const float2 *>(V + r * ldv + j0 + 2 * g);
+        a0 = fma4(v.x, m, a0);
+        a1 = fma4(v.y, m, a1);
+      }
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g) * kMpMaxJ + 4 * q) = a0;
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g + 1) * kMpMaxJ + 4 * q) = a1;
+    }
+  }
+  __syncthreads();
+  if (tid < kMpMaxJ && tid >= 4 * q0 && tid < 4 * nq) {
+    const int c = tid;
+    float P[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j)
+      P[j] = (part[j * kMpMaxJ + c] + part[(kNb + j) * kMpMaxJ + c]) +
+             (part[(2 * kNb + j) * kMpMaxJ + c] + part[(3 * kNb + j) * kMpMaxJ + c]);
+#pragma unroll
+    for (int i = 0; i < kNb; ++i) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < kNb; ++k) t = fmaf(trans ? T[k * kNb + i] : T[i * kNb + k], P[k], t);
+      part[i * kMpMaxJ + c] = t;
+    }
+  }
+  __syncthreads();
+  {
+    const int q = q0 + (tid & 31), p = tid >> 5;
+    if (q < nq) {
+      float4 P[kNb];
+#pragma unroll
+      for (int j = 0; j < kNb; ++j) P[j] = *reinterpret_cast<const float4 *>(part + j * kMpMaxJ + 4 * q);
+      const bool whole = 4 * q >= c0;
+#pragma unroll 2
+      for (int r = r0 + p; r < n; r += 16) {
+        float4 m = *reinterpret_cast<const float4 *>(M + r * ldm + 4 * q);
+        const float4 va = *reinterpret_cast<const float4 *>(V + r * ldv + j0);
+        const float4 vb = *reinterpret_cast<const float4 *>(V + r * ldv + j0 + 4);
+        m = fma4(-va.x, P[0], m);
+        m = fma4(-va.y, P[1], m);
+        m = fma4(-va.z, P[2], m);
+        m = fma4(-va.w, P[3], m);
+        m = fma4(-vb.x, P[4], m);
+        m = fma4(-vb.y, P[5], m);
+        m = fma4(-vb.z, P[6], m);
+        m = fma4(-vb.w, P[7], m);
+        float *dst = M + r * ldm + 4 * q;
+        if (whole) {
+          *reinterpret_cast<float4 *>(dst) = m;
+        } else {  // the quad that straddles c0
+          const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (4 * q + u >= c0) dst[u] = mv[u];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One warp factors the panel of columns j0 .. j0 + nbk - 1 (rows j0 .. n-1)
+// of Z (row-major, lz) in registers: lane l holds rows j0 + l + 32 i.  Per
+// column the reflector as in warp_larfg (norm from x / max|x|), then its
+// application to the panel's later columns (their dot products reduced
+// together).  Writes the reflectors to W's panel columns (unit diagonal,
+// zeros above; the rows above j0 are already zero), taus and R's diagonal
+// signs, and the panel's T factor.  No block barrier.
+__device__ void qr_panel(const float *__restrict__ Z, int lz, float *__restrict__ W, int n, int j0, int nbk, int lane,
+                         float *__restrict__ qtau, float *__restrict__ sgn, float *__restrict__ T) {
+  constexpr int kR = kMpMaxJ / 32;
+  const int mrows = n - j0;
+  float P[kR][kNb];
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    const int row = lane + 32 * i;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (row < mrows) {
+      a = *reinterpret_cast<const float4 *>(Z + (j0 + row) * lz + j0);
+      b = *reinterpret_cast<const float4 *>(Z + (j0 + row) * lz + j0 + 4);
+    }
+    P[i][0] = a.x, P[i][1] = a.y, P[i][2] = a.z, P[i][3] = a.w;
+    P[i][4] = b.x, P[i][5] = b.y, P[i][6] = b.z, P[i][7] = b.w;
+  }
+  float tv[kNb];
+#pragma unroll
+  for (int jj = 0; jj < kNb; ++jj) {
+    tv[jj] = 0.f;
+    if (jj >= nbk) continue;  // uniform
+    const float alpha = __shfl_sync(0xffffffffu, P[0][jj], jj);
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < kR; ++i)
+      if (lane + 32 * i > jj) mx = fmaxf(mx, fabsf(P[i][jj]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float t = 0.f, scal = 0.f, beta = alpha;
+    if (mx > 0x1p-100f) {  // uniform
+      const float sx = 1.f / fmaxf(mx, fabsf(alpha));
+      float sg = 0.f;
+#pragma unroll
+      for (int i = 0; i < kR; ++i)
+        if (lane + 32 * i > jj) {
+          const float v = P[i][jj] * sx;
+          sg = fmaf(v, v, sg);
+        }
+      sg = warp_sum32(sg);
+      const float a = alpha * sx;
+      const float nrm = sqrtf(fmaf(a, a, sg)) / sx;
+      beta = alpha >= 0.f ? -nrm : nrm;
+      t = (beta - alpha) / beta;
+      scal = 1.f / (alpha - beta);
+    }
+    tv[jj] = t;
+    if (lane == 0) {
+      qtau[j0 + jj] = t;
+      sgn[j0 + jj] = beta < 0.f ? -1.f : 1.f;
+    }
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const int row = lane + 32 * i;
+      P[i][jj] = row == jj ? 1.f : (row > jj && t != 0.f ? P[i][jj] * scal : 0.f);
+    }
+    if (t != 0.f) {
+      float dd[kNb];
+#pragma unroll
+      for (int c = 0; c < kNb; ++c) {
+        dd[c] = 0.f;
+        if (c > jj)
+#pragma unroll
+          for (int i = 0; i < kR; ++i) dd[c] = fmaf(P[i][jj], P[i][c], dd[c]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < kNb; ++c)
+          if (c > jj) dd[c] += __shfl_xor_sync(0xffffffffu, dd[c], o);
+#pragma unroll
+      for (int c = 0; c < kNb; ++c)
+        if (c > jj)
+#pragma unroll
+          for (int i = 0; i < kR; ++i) P[i][c] = fmaf(-t * dd[c], P[i][jj], P[i][c]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    const int row = lane + 32 * i;
+    if (row < mrows) {
+      *reinterpret_cast<float4 *>(W + (j0 + row) * lz + j0) = make_float4(P[i][0], P[i][1], P[i][2], P[i][3]);
+      *reinterpret_cast<float4 *>(W + (j0 + row) * lz + j0 + 4) = make_float4(P[i][4], P[i][5], P[i][6], P[i][7]);
+    }
+  }
+  // G = V^T V (upper part) in every lane, then lane i < kNb forms T's column i
+  float G[kNb * kNb];
+#pragma unroll
+  for (int k = 0; k < kNb; ++k)
+#pragma unroll
+    for (int l = 0; l < kNb; ++l) {
+      G[k * kNb + l] = 0.f;
+      if (k < l)
+#pragma unroll
+        for (int i = 0; i < kR; ++i) G[k * kNb + l] = fmaf(P[i][k], P[i][l], G[k * kNb + l]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < kNb; ++k)
+#pragma unroll
+      for (int l = k + 1; l < kNb; ++l) G[k * kNb + l] += __shfl_xor_sync(0xffffffffu, G[k * kNb + l], o);
+  if (lane < kNb) wy_t_column(G, tv, lane, T);
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__restrict__ A, int lda, int n,
                                                            double *__restrict__ X, int ldx) {
   extern __shared__ __align__(16) float smt[];
-  const int ld = n + 1;
-  float *Af = smt;           // n x ld, row-major
-  float *Z = Af + n * ld;    // n x ld, Z[k ld + c]: row k of eigenvector c of T
-  float *W = Z + n * ld;     // n x n, W[k n + i]: L factor of T - l_i I; later the QR reflectors
-  float *pd = W + n * n;     // 4 x 128 partial sums
-  float *d = pd + 4 * kMpMaxJ, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *vs = lam + n,
+  const int ld = n + 1, lz = tri32_ld(n);
+  const Tri32Layout lay(n);
+  float *Af = smt;             // n x ld, row-major
+  float *Z = smt + lay.z;      // n x lz, Z[k lz + c]: row k of eigenvector c of T
+  float *W = smt + lay.w;      // W[k n + i]: L factor of T - l_i I; then reflectors, n x lz (column j: v_j)
+  float *part = smt + lay.part;  // WY partial products; 4 x 128 partial sums in step 1
+  float *pd = part;
+  float *Tf = smt + lay.tf;
+  float *d = smt + lay.vec, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *vs = lam + n,
         *qtau = vs + n, *sgn = qtau + n;
   __shared__ float red[32];
   __shared__ float sc[4];
@@ -529,64 +761,73 @@ __global__ void __launch_bounds__(kT32Threads) k_eig32_tri(const double *__restr
       for (int k = 0; k < n; ++k) {  // forward: y = L^-1 b, z = D^-1 y
         if (k > 0) Dk = d[k] - s - W[(k - 1) * n + c] * e[k - 1];
         if (fabsf(Dk) < piv) Dk = Dk < 0.f ? -piv : piv;
-        const float b = pass == 0 ? start_entry(c, k) : Z[k * ld + c];
+        const float b = pass == 0 ? start_entry(c, k) : Z[k * lz + c];
         y = k == 0 ? b : b - W[(k - 1) * n + c] * y;
-        Z[k * ld + c] = __fdividef(y, Dk);
+        Z[k * lz + c] = __fdividef(y, Dk);
       }
-      float xn = Z[(n - 1) * ld + c], nrm = xn * xn;
+      float xn = Z[(n - 1) * lz + c], nrm = xn * xn;
       for (int k = n - 2; k >= 0; --k) {  // backward: x = L^-T z
-        xn = Z[k * ld + c] - W[k * n + c] * xn;
-        Z[k * ld + c] = xn;
+        xn = Z[k * lz + c] - W[k * n + c] * xn;
+        Z[k * lz + c] = xn;
         nrm = fmaf(xn, xn, nrm);
       }
       // a solve that overflowed (or vanished) restarts from e_c
       const bool good = nrm > 0.f && nrm <= FLT_MAX;
       const float r = good ? rsqrtf(nrm) : 0.f;
-      for (int k = 0; k < n; ++k) Z[k * ld + c] = good ? Z[k * ld + c] * r : (k == c ? 1.f : 0.f);
+      for (int k = 0; k < n; ++k) Z[k * lz + c] = good ? Z[k * lz + c] * r : (k == c ? 1.f : 0.f);
     }
   }
   __syncthreads();
 
-  // ---- 4. Z <- Q of Z = Q R (Householder), columns in descending eigenvalue order
-  for (int j = 0; j < n; ++j) {
-    const int m = n - j;  // column j, rows j..n-1
-    float t, scal, beta;
-    warp_larfg(Z + j * ld + j, ld, m, lane, t, scal, beta);
-    if (tid == 0) {
-      qtau[j] = t;
-      sgn[j] = beta < 0.f ? -1.f : 1.f;  // R(j, j) = beta: Q's column j is sign(beta) times the new direction
-    }
-    if (t == 0.f) continue;
-    for (int i = tid + 1; i < m; i += nt) W[(j + i) * n + j] = Z[(j + i) * ld + j] * scal;  // v below row j
+  // ---- 4. Z <- Q of Z = Q R (Householder), columns in descending eigenvalue order.
+  // Panels of kNb columns, each factored by one warp in registers (its
+  // reflectors to W with unit diagonal and zeros above, its T factor kept);
+  // the trailing columns take the panel at once as (I - V T^T V^T).
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, c = idx - r * lz;
+    if (c >= n) Z[idx] = 0.f;  // padding columns stay zero (and finite)
+    W[idx] = 0.f;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += kNb) {
+    const int nbk = min(kNb, n - j0);
+    float *Tb = Tf + (j0 / kNb) * kNb * kNb;
+    if (warp == 0) qr_panel(Z, lz, W, n, j0, nbk, lane, qtau, sgn, Tb);
     __syncthreads();
-    // trailing columns j+1..n-1 (column j itself is not needed any more)
-    apply_reflector(Z, ld, n, j, j + 1, t, W + j, n, pd);
+    if (j0 + nbk < n) apply_wy(Z, lz, n, j0, j0 + nbk, W, lz, j0, Tb, true, part);
   }
-  // explicit Q: reflectors applied to I in reverse order, then signs so that
+  // explicit Q: the blocks applied to I in reverse order (block b leaves
+  // columns before its first one at the identity), then signs so that
   // column j points along the j-th input vector
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx / n, c = idx - r * n;
-    Z[r * ld + c] = r == c ? 1.f : 0.f;
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, c = idx - r * lz;
+    Z[idx] = r == c ? 1.f : 0.f;
   }
   __syncthreads();
-  for (int j = n - 1; j >= 0; --j) {
-    const float t = qtau[j];
-    if (t != 0.f) apply_reflector(Z, ld, n, j, j, t, W + j, n, pd);
-  }
+  for (int j0 = ((n - 1) / kNb) * kNb; j0 >= 0; j0 -= kNb)
+    apply_wy(Z, lz, n, j0, j0, W, lz, j0, Tf + (j0 / kNb) * kNb * kNb, false, part);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx / n, c = idx - r * n;
-    Z[r * ld + c] *= sgn[c];
+    Z[r * lz + c] *= sgn[c];
   }
   __syncthreads();
 
-  // ---- 5. X = Q1 Z: H_{n-3} first, H_0 last
-  for (int k = n - 3; k >= 0; --k) {
-    const float t = tau[k];
-    if (t != 0.f) apply_reflector(Z, ld, n, k + 1, 0, t, Af + k, ld, pd);
+  // ---- 5. X = Q1 Z: the tridiagonalization's reflectors (v_k below the
+  // subdiagonal of A's column k, unit entry at row k + 1) copied to W, blocks
+  // from the last to the first
+  const int nref = max(n - 2, 0);
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, k = idx - r * lz;
+    W[idx] = k < nref ? (r == k + 1 ? 1.f : (r > k + 1 && tau[k] != 0.f ? Af[r * ld + k] : 0.f)) : 0.f;
   }
+  __syncthreads();
+  const int nblk = (nref + kNb - 1) / kNb;
+  if (nblk > 0) form_wy_ts(W, lz, nblk, nref, 1, n, tau, Tf, part);  // the QR blocks' T factors are spent
+  for (int j0 = (nblk - 1) * kNb; j0 >= 0; j0 -= kNb)
+    apply_wy(Z, lz, n, j0 + 1, 0, W, lz, j0, Tf + (j0 / kNb) * kNb * kNb, false, part);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx % n, c = idx / n;
-    X[r + (int64_t)ldx * c] = (double)Z[r * ld + c];
+    X[r + (int64_t)ldx * c] = (double)Z[r * lz + c];
   }
 }
 
