@@ -226,11 +226,13 @@ size_t jacobi32_smem(int n) {
 // the first stage of a level in place of the Jacobi sweeps: O(n^3) work once
 // instead of per sweep, every phase data-parallel over rows, columns or
 // eigenvalues, with 2-3 block barriers per reflector.
-//   1. Householder tridiagonalization T = Q1^T A Q1 (LAPACK's sytd2 order:
-//      H_k = I - tau_k v_k v_k^T, v_k(0) = 1, acting on rows k+1..n-1; the
-//      trailing block is updated as A22 -= v w^T + w v^T with
-//      w = p - (tau/2)(p^T v) v, p = tau A22 v).  v_k is kept below the
-//      subdiagonal of column k.
+//   1. Householder tridiagonalization T = Q1^T A Q1 (H_k = I - tau_k v_k v_k^T,
+//      v_k(0) = 1, acting on rows k+1..n-1), blocked as LAPACK's sytrd/latrd:
+//      within a panel of kNb columns the trailing block's updates
+//      A22 -= v w^T + w v^T (w = tau A22 v - (tau/2)(tau v^T A22 v) v, with
+//      A22 v corrected for the panel's earlier columns) are deferred and
+//      applied at the panel's end as one rank-2 kNb update.  v_k is kept
+//      below the subdiagonal of column k.
 //   2. Eigenvalues of T by multisection on Sturm counts (four threads per
 //      eigenvalue, five sub-intervals per round, 12 rounds: below 2^-26 ||T||).
 //   3. Eigenvectors of T by two steps of inverse iteration (thread i solves
@@ -291,40 +293,6 @@ __device__ __forceinline__ float start_entry(int i, int k) {
   h *= 0x2C1B3C6Du;
   h ^= h >> 12;
   return (float)(int)(h >> 8) * 0x1p-23f - 1.0f;
-}
-
-// Householder reflector of x (length m, x(i) at x[i * stride]) as every lane
-// of a warp computes it: tau, 1 / (alpha - beta) and beta (LAPACK's larfg:
-// H x = beta e_1, v(0) = 1, v(i) = x(i) / (alpha - beta); tau = 0 when
-// x(1..m-1) ~ 0).  The norm is formed from x / max|x|, so that squares of
-// small entries do not fall into the subnormal range (where beta^2 would no
-// longer be alpha^2 + ||x(1..)||^2 and H would not be orthogonal).
-__device__ __forceinline__ void warp_larfg(const float *x, int stride, int m, int lane, float &tau, float &scal,
-                                           float &beta) {
-  const float alpha = x[0];
-  float mx = 0.f;
-  for (int i = 1 + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(x[i * stride]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  tau = 0.f;
-  scal = 0.f;
-  beta = alpha;
-  // entries below 2^-100 (the inputs are scaled to at most 1) are far below
-  // float32 resolution and are taken as zero; this also keeps 1 / max finite
-  if (mx > 0x1p-100f) {  // uniform: every lane has the same mx
-    const float sx = 1.f / fmaxf(mx, fabsf(alpha));
-    float sg = 0.f;
-    for (int i = 1 + lane; i < m; i += 32) {
-      const float v = x[i * stride] * sx;
-      sg = fmaf(v, v, sg);
-    }
-    sg = warp_sum32(sg);
-    const float a = alpha * sx;
-    const float nrm = sqrtf(fmaf(a, a, sg)) / sx;
-    beta = alpha >= 0.f ? -nrm : nrm;
-    tau = (beta - alpha) / beta;
-    scal = 1.f / (alpha - beta);
-  }
 }
 
 __device__ __forceinline__ float4 fma4(float a, float4 b, float4 c) {
@@ -460,9 +428,189 @@ __device__ void apply_wy(float *__restrict__ M, int ldm, int n, int r0, int c0, 
   __syncthreads();
 }
 
+__device__ __forceinline__ void load8(const float *__restrict__ p, float (&x)[kNb]) {
+  const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+  x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+}
+
+// The tridiagonalization's per-column work runs on warps 0..3 (threads
+// 0..127, one row each), synchronised among themselves by named barrier 1.
+// The functions below take no __restrict__ pointers: the barrier is inline
+// assembly, and a restrict-qualified access could be moved across it.
+__device__ __forceinline__ void bar128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Threads 0..127: the reflector of column j (panel position i) of the
+// tridiagonalization from its up-to-date entries (thread l holds a = A(j + l,
+// j), zero past row n - 1): d[j] = a_j, and for rows j+1 .. n-1 LAPACK's
+// larfg (H x = beta e_1, v(i) = x(i) / (alpha - beta), tau = (beta - alpha)
+// / beta; tau = 0 when x(1..) ~ 0; e[j] = beta, tau[j]).  v (unit entry at row
+// j + 1) goes to Vp's column i, below row j + 1 to A's column j, and from row
+// j + 1 on to the contiguous vs for the next A22 v.  Entries below 2^-100
+// (the inputs are scaled to at most 1) count as zero, which also keeps
+// 1 / max finite.  The norm is the plain sum of squares when max|x| >= 2^-40,
+// and otherwise formed from x / max|x|, so that squares that matter never
+// fall into the subnormal range (where beta^2 would no longer be alpha^2 +
+// ||x(1..)||^2 and H would not be orthogonal).  red: 24 floats of scratch.
+// Returns tau (the same in every thread).
+__device__ float tri_reflect(float a, int n, int j, int i, float *Af, int ld, float *Vp, float *vs, int tid,
+                             float *red, float *d, float *e, float *tau) {
+  const int lane = tid & 31, w4 = tid >> 5;
+  float mx = tid >= 2 ? fabsf(a) : 0.f, sq = tid >= 2 ? a * a : 0.f;  // rows j + 2 ..
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  }
+  if (lane == 0) {
+    red[w4] = mx;
+    red[4 + w4] = sq;
+  }
+  if (tid == 1) red[8] = a;  // alpha: row j + 1
+  bar128();
+  mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+  sq = (red[4] + red[5]) + (red[6] + red[7]);
+  const float alpha = red[8];
+  float t = 0.f, scal = 0.f, beta = alpha;
+  if (mx > 0x1p-100f) {  // uniform
+    const float sx = 1.f / fmaxf(mx, fabsf(alpha));
+    float sg = sq * sx * sx;
+    if (mx < 0x1p-40f) {  // uniform
+      const float v = tid >= 2 ? a * sx : 0.f;
+      sg = warp_sum32(v * v);
+      if (lane == 0) red[12 + w4] = sg;
+      bar128();
+      sg = (red[12] + red[13]) + (red[14] + red[15]);
+    }
+    const float aa = alpha * sx;
+    const float nrm = sqrtf(fmaf(aa, aa, sg)) / sx;
+    beta = alpha >= 0.f ? -nrm : nrm;
+    t = (beta - alpha) / beta;
+    scal = 1.f / (alpha - beta);
+  }
+  const int r = j + tid;
+  if (tid == 0) {
+    d[j] = a;
+    e[j] = beta;
+    tau[j] = t;
+  }
+  if (tid >= 1 && r < n) {  // every thread read vs before the first barrier above
+    const float v = tid == 1 ? 1.f : a * scal;
+    Vp[r * kNb + i] = v;
+    vs[tid - 1] = v;
+    if (tid >= 2) Af[r * ld + j] = v;
+  }
+  return t;
+}
+
+// Threads 0..127: column j (panel position 0) as it stands, and its reflector.
+__device__ float tri_column0(float *Af, int ld, int n, int j, float *Vp, float *vs, int tid, float *red, float *d,
+                             float *e, float *tau) {
+  const int r = j + tid;
+  const float a = Af[min(r, n - 1) * ld + j];
+  return tri_reflect(r < n ? a : 0.f, n, j, 0, Af, ld, Vp, vs, tid, red, d, e, tau);
+}
+
+// Threads 0..127, after the partial products pd of A22 v for column j
+// (panel position i; A22 = rows and columns j+1.., as at the panel's start;
+// thread c takes row j + 1 + c): y1 = W^T v and y2 = V^T v over the panel's
+// earlier columns (from the extra columns of the partial products when they
+// fitted, else reduced here), w = tau (A22 v - V y1 - W y2) - (tau / 2)
+// (w^T v) v with w^T v = tau (v^T A22 v - 2 y1 . y2) (LAPACK's latrd), to
+// Wp's column i.  Then, if next, column j + 1 on the same rows brought up
+// to date with the panel's reflectors 0 .. i, a_r = A(r, j+1) - sum_u
+// (V(r, u) W(j+1, u) + W(r, u) V(j+1, u)), and its reflector.  Loads are
+// unconditional (rows clamped into range, values past the end zeroed).
+// Returns that reflector's tau.
+__device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int i, float t, bool next, float *Vp,
+                          float *Wp, float *vs, int tid, float *red, float *d, float *e, float *tau) {
+  const int lane = tid & 31, w4 = tid >> 5;
+  const int m = n - j - 1;  // >= 2
+  const bool has_y = m + 2 * kNb <= kMpMaxJ;
+  const int c = tid, cc = min(c, m - 1), r = j + 1 + cc;
+  float vr[kNb], wr[kNb];
+  load8(Vp + r * kNb, vr);
+  load8(Wp + r * kNb, wr);
+  const float pp = (pd[cc] + pd[kMpMaxJ + cc]) + (pd[2 * kMpMaxJ + cc] + pd[3 * kMpMaxJ + cc]);
+  const float vv = vs[cc];
+  const float pq = c < m ? pp : 0.f, v = c < m ? vv : 0.f;
+  float y1[kNb], y2[kNb];
+  {
+    const int c0 = has_y ? m : 0;
+#pragma unroll
+    for (int u = 0; u < kNb; ++u) {
+      const float s2 = (pd[c0 + u] + pd[kMpMaxJ + c0 + u]) + (pd[2 * kMpMaxJ + c0 + u] + pd[3 * kMpMaxJ + c0 + u]);
+      const int cy = c0 + kNb + u;
+      const float s1 = (pd[cy] + pd[kMpMaxJ + cy]) + (pd[2 * kMpMaxJ + cy] + pd[3 * kMpMaxJ + cy]);
+      y1[u] = has_y && u < i ? s1 : 0.f;
+      y2[u] = has_y && u < i ? s2 : 0.f;
+    }
+  }
+  if (!has_y) {  // uniform: reduced here over the 128 rows
+#pragma unroll
+    for (int u = 0; u < kNb; ++u) {
+      y1[u] = u < i ? wr[u] * v : 0.f;
+      y2[u] = u < i ? vr[u] * v : 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < kNb; ++u)
+        if (u < i) {
+          y1[u] += __shfl_xor_sync(0xffffffffu, y1[u], o);
+          y2[u] += __shfl_xor_sync(0xffffffffu, y2[u], o);
+        }
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < kNb; ++u) {
+        red[32 + w4 * 2 * kNb + u] = y1[u];
+        red[32 + w4 * 2 * kNb + kNb + u] = y2[u];
+      }
+    bar128();
+#pragma unroll
+    for (int u = 0; u < kNb; ++u) {
+      y1[u] = (red[32 + u] + red[32 + 2 * kNb + u]) + (red[32 + 4 * kNb + u] + red[32 + 6 * kNb + u]);
+      y2[u] = (red[32 + kNb + u] + red[32 + 3 * kNb + u]) + (red[32 + 5 * kNb + u] + red[32 + 7 * kNb + u]);
+      if (u >= i) y1[u] = y2[u] = 0.f;
+    }
+  }
+  float x = pq;
+#pragma unroll
+  for (int u = 0; u < kNb; ++u)
+    if (u < i) x = fmaf(-vr[u], y1[u], fmaf(-wr[u], y2[u], x));
+  float pv = warp_sum32(pq * v);
+  if (lane == 0) red[16 + w4] = pv;
+  bar128();
+  pv = (red[16] + red[17]) + (red[18] + red[19]);
+  float y12 = 0.f;
+#pragma unroll
+  for (int u = 0; u < kNb; ++u) y12 = fmaf(y1[u], y2[u], y12);
+  const float kk = 0.5f * t * t * (pv - 2.f * y12);
+  const float w = fmaf(-kk, v, t * x);  // zero past row n - 1 (v and x are)
+  if (c < m) Wp[(j + 1 + c) * kNb + i] = w;
+  if (!next) return 0.f;
+  bar128();  // W(j + 1, i) (thread 0) is written
+  const int j1 = j + 1;
+  float vj[kNb], wj[kNb];  // row j + 1 of V and W
+  load8(Vp + j1 * kNb, vj);
+  load8(Wp + j1 * kNb, wj);
+  float a = Af[r * ld + j1];
+#pragma unroll
+  for (int u = 0; u < kNb; ++u)
+    if (u < i) a = fmaf(-vr[u], wj[u], fmaf(-wr[u], vj[u], a));
+  float vji = 0.f, wji = 0.f;
+#pragma unroll
+  for (int u = 0; u < kNb; ++u)
+    if (u == i) {
+      vji = vj[u];
+      wji = wj[u];
+    }
+  a = fmaf(-v, wji, fmaf(-w, vji, a));
+  return tri_reflect(c < m ? a : 0.f, n, j1, i + 1, Af, ld, Vp, vs, tid, red, d, e, tau);
+}
+
 // One warp factors the panel of columns j0 .. j0 + nbk - 1 (rows j0 .. n-1)
 // of Z (row-major, lz) in registers: lane l holds rows j0 + l + 32 i.  Per
-// column the reflector as in warp_larfg (norm from x / max|x|), then its
+// column the reflector as in tri_column (norm from x / max|x|), then its
 // application to the panel's later columns (their dot products reduced
 // together).  Writes the reflectors to W's panel columns (unit diagonal,
 // zeros above; the rows above j0 are already zero), taus and R's diagonal
@@ -583,9 +731,9 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
   float *part = smt + lay.part;  // WY partial products; 4 x 128 partial sums in step 1
   float *pd = part;
   float *Tf = smt + lay.tf;
-  float *d = smt + lay.vec, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *vs = lam + n,
-        *qtau = vs + n, *sgn = qtau + n;
-  __shared__ float red[32];
+  float *d = smt + lay.vec, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *qtau = lam + n,
+        *sgn = qtau + n;
+  __shared__ float red[96];
   __shared__ float sc[4];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
@@ -607,72 +755,76 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
     for (int j = lane; j < n; j += 32) Af[i * ld + j] = (float)(A[min(i, j) + (int64_t)lda * max(i, j)] * inv);
   __syncthreads();
 
-  // ---- 1. tridiagonalization
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;  // x = A[k+1 .. n-1, k]
-    float t, scal, beta;
-    warp_larfg(Af + (k + 1) * ld + k, ld, m, lane, t, scal, beta);  // every warp, same values
-    if (tid == 0) {
-      d[k] = Af[k * ld + k];
-      e[k] = beta;
-      tau[k] = t;
+  // ---- 1. tridiagonalization, kNb columns a panel (LAPACK's latrd, lower):
+  // the panel's reflectors V and the vectors W (columns of the n x kNb
+  // row-major Vp, Wp) stand for its updates of the trailing matrix until the
+  // panel ends, when A22 -= V W^T + W V^T in one pass.  Per column: the
+  // block's threads form the partial products of A22 v (A22 as at the
+  // panel's start), then warp 0 completes w and brings the next column up to
+  // date and forms its reflector.
+  float *Vp = W, *Wp = Z;  // both free until step 3
+  float *vs = part + 4 * kMpMaxJ;  // the current v, contiguous (16-byte aligned)
+  float tcur = 0.f;        // threads 0..127: tau of the current column
+  for (int k0 = 0; k0 + 2 < n; k0 += kNb) {
+    const int nbk = min(kNb, n - 2 - k0);
+    for (int idx = tid; idx < n * kNb; idx += nt) {
+      Vp[idx] = 0.f;
+      Wp[idx] = 0.f;
     }
-    if (t == 0.f) continue;  // H_k = I; column k + 1 is unchanged (uniform: t is the same everywhere)
-    for (int i = tid; i < m; i += nt) vs[i] = i == 0 ? 1.f : Af[(k + 1 + i) * ld + k] * scal;
     __syncthreads();
-    // partial p: thread (i, part) sums rows j = part, part + 4, ... of column i (A22 symmetric)
-    {
-      const int i = tid & (kMpMaxJ - 1), part = tid >> 7;
-      float acc = 0.f;
-      if (i < m) {
-        const float *col = Af + (k + 1) * ld + (k + 1 + i);
-        int j = part;
-        for (; j + 12 < m; j += 16) {  // four rows at a time, loads first
-          const float a0 = col[j * ld], a1 = col[(j + 4) * ld], a2 = col[(j + 8) * ld], a3 = col[(j + 12) * ld];
-          acc = fmaf(a0, vs[j], fmaf(a1, vs[j + 4], fmaf(a2, vs[j + 8], fmaf(a3, vs[j + 12], acc))));
+    if (tid < 128) tcur = tri_column0(Af, ld, n, k0, Vp, vs, tid, red, d, e, tau);
+    __syncthreads();
+    for (int i = 0; i < nbk; ++i) {
+      const int j = k0 + i, m = n - j - 1;
+      {  // partial A22 v: thread (column c, part) sums a quarter of the rows
+         // (a multiple of 4, for 16-byte loads of v); when they fit, the
+         // threads of columns m .. m + 15 form V^T v and W^T v the same way
+        const int c = tid & (kMpMaxJ - 1), part = tid >> 7;
+        const int rb = ((m + 15) >> 4) << 2, r1 = min(m, part * rb + rb);
+        const float *X = nullptr;
+        int xs = 0;
+        if (c < m) {
+          X = Af + (j + 1) * ld + (j + 1 + c);
+          xs = ld;
+        } else if (m + 2 * kNb <= kMpMaxJ && c < m + 2 * kNb) {
+          const int u = c - m;
+          X = (u < kNb ? Vp + u : Wp + (u - kNb)) + (j + 1) * kNb;
+          xs = kNb;
         }
-        for (; j < m; j += 4) acc = fmaf(col[j * ld], vs[j], acc);
+        float acc = 0.f, acc2 = 0.f;
+        if (X) {
+          int r = part * rb;
+          for (; r + 3 < r1; r += 4) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(vs + r);
+            const float a0 = X[r * xs], a1 = X[(r + 1) * xs], a2 = X[(r + 2) * xs], a3 = X[(r + 3) * xs];
+            acc = fmaf(a0, v4.x, fmaf(a2, v4.z, acc));
+            acc2 = fmaf(a1, v4.y, fmaf(a3, v4.w, acc2));
+          }
+          for (; r < r1; ++r) acc = fmaf(X[r * xs], vs[r], acc);
+        }
+        pd[part * kMpMaxJ + c] = acc + acc2;
       }
-      pd[part * kMpMaxJ + i] = acc;
-      // v is kept below the subdiagonal for the back-transform (every warp is past reading x)
-      if (part == 0 && i >= 1 && i < m) Af[(k + 1 + i) * ld + k] = vs[i];
+      __syncthreads();
+      if (tid < 128) tcur = tri_step(pd, Af, ld, n, j, i, tcur, i + 1 < nbk, Vp, Wp, vs, tid, red, d, e, tau);
+      __syncthreads();
     }
-    __syncthreads();
-    // every warp: K = t/2 p^T v, then its rows of A22 -= v w^T + w v^T with w = p - K v
-    float kk = 0.f;
-    for (int j = lane; j < m; j += 32)
-      kk = fmaf(pd[j] + pd[kMpMaxJ + j] + pd[2 * kMpMaxJ + j] + pd[3 * kMpMaxJ + j], vs[j], kk);
-    kk = 0.5f * t * t * warp_sum32(kk);
-    float vj[kMpMaxJ / 32], wj[kMpMaxJ / 32];
+    // A22 -= V W^T + W V^T on rows and columns t0 .. n-1: thread (column c,
+    // part) keeps row c of V and W and takes rows part, part + 4, ...
+    const int t0 = k0 + nbk, mt = n - t0;
+    {
+      const int c = tid & (kMpMaxJ - 1), part = tid >> 7;
+      if (c < mt) {
+        float vc[kNb], wc[kNb];
+        load8(Vp + (t0 + c) * kNb, vc);
+        load8(Wp + (t0 + c) * kNb, wc);
+        for (int r = part; r < mt; r += 4) {
+          float vr[kNb], wr[kNb];
+          load8(Vp + (t0 + r) * kNb, vr);
+          load8(Wp + (t0 + r) * kNb, wr);
+          float a = Af[(t0 + r) * ld + t0 + c];
 #pragma unroll
-    for (int c = 0; c < kMpMaxJ / 32; ++c) {
-      const int j = lane + 32 * c;
-      vj[c] = j < m ? vs[j] : 0.f;
-      wj[c] = j < m ? fmaf(-kk, vj[c], t * (pd[j] + pd[kMpMaxJ + j] + pd[2 * kMpMaxJ + j] + pd[3 * kMpMaxJ + j]))
-                    : 0.f;
-    }
-    for (int i0 = warp; i0 < m; i0 += 2 * nw) {  // two rows at a time, loads first
-      const int i1 = i0 + nw;
-      const bool two = i1 < m;
-      const float vi0 = vs[i0], vi1 = two ? vs[i1] : 0.f;
-      const float wi0 = fmaf(-kk, vi0, t * (pd[i0] + pd[kMpMaxJ + i0] + pd[2 * kMpMaxJ + i0] + pd[3 * kMpMaxJ + i0]));
-      const float wi1 =
-          two ? fmaf(-kk, vi1, t * (pd[i1] + pd[kMpMaxJ + i1] + pd[2 * kMpMaxJ + i1] + pd[3 * kMpMaxJ + i1])) : 0.f;
-      float *row0 = Af + (k + 1 + i0) * ld + (k + 1);
-      float *row1 = Af + (k + 1 + (two ? i1 : i0)) * ld + (k + 1);
-      float a0[kMpMaxJ / 32], a1[kMpMaxJ / 32];
-#pragma unroll
-      for (int c = 0; c < kMpMaxJ / 32; ++c) {
-        const int j = lane + 32 * c;
-        a0[c] = j < m ? row0[j] : 0.f;
-        a1[c] = (two && j < m) ? row1[j] : 0.f;
-      }
-#pragma unroll
-      for (int c = 0; c < kMpMaxJ / 32; ++c) {
-        const int j = lane + 32 * c;
-        if (j < m) {
-          row0[j] = fmaf(-vi0, wj[c], fmaf(-wi0, vj[c], a0[c]));
-          if (two) row1[j] = fmaf(-vi1, wj[c], fmaf(-wi1, vj[c], a1[c]));
+          for (int q = 0; q < kNb; ++q) a = fmaf(-vr[q], wc[q], fmaf(-wr[q], vc[q], a));
+          Af[(t0 + r) * ld + t0 + c] = a;
         }
       }
     }
