@@ -46,14 +46,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # timed run; it is dropped as soon as the kernel source changes.
 TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9,
                                                    "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           # profiles/split_kernels_combustion5_t2.md (the same case; mode 2 for the L > 1 mode product)
-           ("k_rowgroup_exp", "eefc6475e21ef40b"): {"ratio": (1.610714e9 + 4.884e6) / 1.6106e9,
+           # profiles/split_kernels_combustion5_t2.md (the same case)
+           ("k_gram_split_bulk", "c05caadd13b9da6c"): {
+               "ratio": (1.612648e9 + 4.068e6) / 1.6106e9,
+               "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB); the tiled mode-2 launch (L = 40) "
+                           "measured 1.031"},
+           ("k_ttm_split_l1", "ebc65708341fb159"): {"ratio": (1.611258e9 + 477.05e6) / 2.1140e9,
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           ("k_gram_split_bulk", "eefc6475e21ef40b"): {"ratio": (1.612567e9 + 4.197e6) / 1.6106e9,
-                                                       "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_l1", "ebc65708341fb159"): {"ratio": (1.6113e9 + 476.4e6) / 2.1140e9,
-                                                    "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_tma", "ebc65708341fb159"): {"ratio": (0.5054e9 + 129.6e6) / (0.50332e9 + 0.157286e9),
+           ("k_ttm_split_tma", "ebc65708341fb159"): {"ratio": (0.505518e9 + 129.19e6) / (0.50332e9 + 0.157286e9),
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB)"}}
 HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
@@ -285,9 +285,10 @@ def time_method(tucker, x, dims, eps, precision, steps, warmup, world, local, st
 PHASE_KERNELS = {
     "split": {
         "norm": ("k_sumsq", "sum of squares of X", "hbm"),
-        "scale": ("k_rowgroup_exp", "per-(row, 512-column group) exponent table, column exponents for L > 1", "hbm"),
-        "gram": ("k_gram_split_bulk", "tcgen05 BF16 digit Gram, exact FP32 accumulation: tensor-map ring for "
-                 "L = 1, k_gram_split for L > 1", "hbm"),
+        "scale": ("k_rowgroup_exp", "per-(row, 512-column group) exponent table (k_rowgroup_exp_async for "
+                  "L > 1, with the column exponents)", "hbm"),
+        "gram": ("k_gram_split_bulk", "tcgen05 BF16 digit Gram, exact FP32 accumulation, tensor-map ring: "
+                 "32-column boxes for L = 1, boxes of 8-l octets x b for L > 1", "hbm"),
         "ttm_l1": ("k_ttm_split_l1", "tcgen05 BF16 digit TTM, contiguous columns (L = 1)", "hbm"),
         "ttm": ("k_ttm_split_tma", "tcgen05 BF16 digit TTM, tensor-map tiles of strided columns (L > 1)", "hbm"),
         "eig": ("k_eig32_tri", "mixed-precision eigensolver (float32 tridiagonal stage + float64 refinement)",
