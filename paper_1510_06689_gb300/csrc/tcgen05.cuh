@@ -9,9 +9,17 @@
 namespace tk {
 namespace tc {
 
-// Iterations of a bounded mbarrier wait (each try_wait may itself block for a
-// short hardware-defined time); expiry is reported, never spun past.
+// Bounded mbarrier waits.  mbar_wait polls (each try_wait may block for a
+// short hardware-defined time) for at most kTcWaitLimit tries: the choice
+// for waits on which a whole CTA's pipeline turns.  mbar_try with a suspend
+// hint lets the thread sleep until the phase completes, for at most
+// kTcSuspendNs per try, so that a single waiting lane of a role warp takes
+// no issue slots from the working warps; its callers give up after
+// kTcWaitNs of globaltimer time (or kTcWaitLimit tries).  Expiry is
+// reported, never waited past.
 constexpr long long kTcWaitLimit = 1ll << 22;
+constexpr uint32_t kTcSuspendNs = 20000;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 // tcgen05 instruction descriptor for kind::f16: D = F32, A = B = BF16, both
 // K-major, shape M x N.
@@ -62,7 +70,26 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on expiry.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One try: true once the phase with the given parity has completed; the
+// thread may be suspended meanwhile (up to kTcSuspendNs).
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "r"(kTcSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded polling wait for the phase with the given parity; false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   for (long long it = 0; it < kTcWaitLimit; ++it) {
     uint32_t ok;

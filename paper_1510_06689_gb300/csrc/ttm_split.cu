@@ -466,16 +466,12 @@ constexpr int kL1Slots = 4;                             // column-exponent ring
 // true once the phase of `parity` has completed, false on expiry (which
 // raises *stop) or when another role has raised *stop.
 __device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int *stop) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
   for (long long it = 0; it < kTcWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 255) == 255 && *stop) return false;
+    if (mbar_try(bar, parity)) return true;
+    if (*stop) return false;
+    if (global_ns() - t0 > kTcWaitNs) break;
   }
   *stop = 1;
   return false;
