@@ -472,20 +472,25 @@ __device__ float tri_reflect(float a, int n, int j, int i, float *Af, int ld, fl
   const float alpha = red[8];
   float t = 0.f, scal = 0.f, beta = alpha;
   if (mx > 0x1p-100f) {  // uniform
-    const float sx = 1.f / fmaxf(mx, fabsf(alpha));
-    float sg = sq * sx * sx;
-    if (mx < 0x1p-40f) {  // uniform
+    float nrm;
+    if (mx >= 0x1p-40f) {  // uniform: alpha^2 + sum x^2 as it stands
+      nrm = sqrtf(fmaf(alpha, alpha, sq));
+    } else {
+      const float s = fmaxf(mx, fabsf(alpha)), sx = 1.f / s;
       const float v = tid >= 2 ? a * sx : 0.f;
-      sg = warp_sum32(v * v);
+      float sg = warp_sum32(v * v);
       if (lane == 0) red[12 + w4] = sg;
       bar128();
       sg = (red[12] + red[13]) + (red[14] + red[15]);
+      const float aa = alpha * sx;
+      nrm = s * sqrtf(fmaf(aa, aa, sg));
     }
-    const float aa = alpha * sx;
-    const float nrm = sqrtf(fmaf(aa, aa, sg)) / sx;
     beta = alpha >= 0.f ? -nrm : nrm;
-    t = (beta - alpha) / beta;
-    scal = 1.f / (alpha - beta);
+    // tau = (beta - alpha) / beta = 1 - alpha / beta and 1 / (alpha - beta),
+    // from two independent correctly rounded reciprocals
+    const float rb = __frcp_rn(beta), rd = __frcp_rn(alpha - beta);
+    t = fmaf(-alpha, rb, 1.f);
+    scal = rd;
   }
   const int r = j + tid;
   if (tid == 0) {
@@ -588,23 +593,23 @@ __device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int 
   const float w = fmaf(-kk, v, t * x);  // zero past row n - 1 (v and x are)
   if (c < m) Wp[(j + 1 + c) * kNb + i] = w;
   if (!next) return 0.f;
-  bar128();  // W(j + 1, i) (thread 0) is written
+  // row j + 1 of V and W: columns u < i as stored; column i is v = 1 there
+  // and w as thread 0 has it, recomputed here from the same values (so no
+  // barrier is needed before the column update)
   const int j1 = j + 1;
-  float vj[kNb], wj[kNb];  // row j + 1 of V and W
+  float vj[kNb], wj[kNb];
   load8(Vp + j1 * kNb, vj);
   load8(Wp + j1 * kNb, wj);
+  float x0 = (pd[0] + pd[kMpMaxJ]) + (pd[2 * kMpMaxJ] + pd[3 * kMpMaxJ]);
+#pragma unroll
+  for (int u = 0; u < kNb; ++u)
+    if (u < i) x0 = fmaf(-vj[u], y1[u], fmaf(-wj[u], y2[u], x0));
+  const float wji = fmaf(-kk, 1.f, t * x0);
   float a = Af[r * ld + j1];
 #pragma unroll
   for (int u = 0; u < kNb; ++u)
     if (u < i) a = fmaf(-vr[u], wj[u], fmaf(-wr[u], vj[u], a));
-  float vji = 0.f, wji = 0.f;
-#pragma unroll
-  for (int u = 0; u < kNb; ++u)
-    if (u == i) {
-      vji = vj[u];
-      wji = wj[u];
-    }
-  a = fmaf(-v, wji, fmaf(-w, vji, a));
+  a = fmaf(-v, wji, fmaf(-w, 1.f, a));
   return tri_reflect(c < m ? a : 0.f, n, j1, i + 1, Af, ld, Vp, vs, tid, red, d, e, tau);
 }
 
@@ -637,28 +642,40 @@ __device__ void qr_panel(const float *__restrict__ Z, int lz, float *__restrict_
     tv[jj] = 0.f;
     if (jj >= nbk) continue;  // uniform
     const float alpha = __shfl_sync(0xffffffffu, P[0][jj], jj);
-    float mx = 0.f;
+    float mx = 0.f, sq = 0.f;  // the reflector as in tri_reflect
 #pragma unroll
     for (int i = 0; i < kR; ++i)
-      if (lane + 32 * i > jj) mx = fmaxf(mx, fabsf(P[i][jj]));
+      if (lane + 32 * i > jj) {
+        mx = fmaxf(mx, fabsf(P[i][jj]));
+        sq = fmaf(P[i][jj], P[i][jj], sq);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
     float t = 0.f, scal = 0.f, beta = alpha;
     if (mx > 0x1p-100f) {  // uniform
-      const float sx = 1.f / fmaxf(mx, fabsf(alpha));
-      float sg = 0.f;
+      float nrm;
+      if (mx >= 0x1p-40f) {  // uniform
+        nrm = sqrtf(fmaf(alpha, alpha, sq));
+      } else {
+        const float sm = fmaxf(mx, fabsf(alpha)), sx = 1.f / sm;
+        float sg = 0.f;
 #pragma unroll
-      for (int i = 0; i < kR; ++i)
-        if (lane + 32 * i > jj) {
-          const float v = P[i][jj] * sx;
-          sg = fmaf(v, v, sg);
-        }
-      sg = warp_sum32(sg);
-      const float a = alpha * sx;
-      const float nrm = sqrtf(fmaf(a, a, sg)) / sx;
+        for (int i = 0; i < kR; ++i)
+          if (lane + 32 * i > jj) {
+            const float v = P[i][jj] * sx;
+            sg = fmaf(v, v, sg);
+          }
+        sg = warp_sum32(sg);
+        const float a = alpha * sx;
+        nrm = sm * sqrtf(fmaf(a, a, sg));
+      }
       beta = alpha >= 0.f ? -nrm : nrm;
-      t = (beta - alpha) / beta;
-      scal = 1.f / (alpha - beta);
+      const float rb = __frcp_rn(beta), rd = __frcp_rn(alpha - beta);
+      t = fmaf(-alpha, rb, 1.f);
+      scal = rd;
     }
     tv[jj] = t;
     if (lane == 0) {
