@@ -738,13 +738,20 @@ TtmL1Plan ttm_l1_plan(int64_t J, int64_t B, int64_t R, const void *y, tucker_dty
 // tensor-memory accelerator into a ring of shared-memory slots (rows j >= J
 // and columns past L or B arrive as zeros).  The column exponents come from
 // the exponent pass over the same Y (every column's largest magnitude over
-// all J rows), so a part can be converted as soon as it lands: thread
-// (column m, rows 8 (tid / 128) ..) reads its 8 entries with constant
-// offsets, forms the four 28-bit digits and stores one 16-byte K-major row
-// unit per digit tile.  Thread 0 issues the copies and, per part, four MMAs
-// per K-step against U's stacked digit tiles (as in the L == 1 kernel) into
-// one of two TMEM accumulator sets; each tile's outputs are assembled
-// exactly from the four levels and written while the next tile's MMAs run.
+// all J rows), so a part can be converted as soon as it lands.  The warps
+// have fixed roles and meet only at mbarriers (as in the L == 1 kernel):
+//   16 converter warps: thread (column m, rows 8 (tid / 128) ..) reads its
+//      8 entries of a part with constant offsets, forms the four 28-bit
+//      digits and stores one 16-byte K-major row unit per digit tile into
+//      one of two operand stages (a_full: stage written and slot read);
+//   1 control thread issues the copies (a slot is refilled as soon as the
+//      converters have read it) and, per part, four MMAs per K-step against
+//      U's stacked digit tiles into one of two TMEM accumulator sets
+//      (mma_done: stage free; acc_full: a tile's levels complete);
+//   8 drain warps assemble each output exactly from the four levels and
+//      write it (coalesced runs of l) while the next tile's MMAs run
+//      (acc_free: set read out).
+// Every wait is bounded and gives up once another role has flagged an error.
 // ---------------------------------------------------------------------------
 constexpr int kTmKH = 32;  // contraction rows per part (one box)
 
@@ -754,17 +761,21 @@ struct TtmTmaPlan {
   size_t u_bytes, raw_slot, smem;
 };
 
+constexpr int kTmConv = 16;                                // converter warps
+constexpr int kTmDrain = 8;                                // drain warps (two per TMEM lane quarter)
+constexpr int kTmThreads = (kTmConv + kTmDrain + 1) * 32;  // and the control warp
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_constant__ CUtensorMap ymap,
-                                                               const double *__restrict__ U, TtmTmaPlan p,
-                                                               const int *__restrict__ colexp,
-                                                               double *__restrict__ z, int *__restrict__ err) {
+__global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_constant__ CUtensorMap ymap,
+                                                                 const double *__restrict__ U, TtmTmaPlan p,
+                                                                 const int *__restrict__ colexp,
+                                                                 double *__restrict__ z, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
-  __shared__ __align__(8) unsigned long long raw_full[4], mma_done[2], acc_full[2];
+  __shared__ __align__(8) unsigned long long raw_full[4], a_full[2], mma_done[2], acc_full[2], acc_free[2];
   __shared__ int rowexp[kM];
-  __shared__ int cexp[4][kM2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int stop;
+  __shared__ volatile int stop;
+  __shared__ int drain_go;
   unsigned char *base = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
   unsigned char *Ut = base;                                 // 4 stacked digit tiles of U (Rp x Jp32)
   unsigned char *Ast = Ut + p.u_bytes;                      // 2 stages x 4 digit tiles (128 x 32)
@@ -787,8 +798,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_cons
   if (tid == 0) {
     for (int k = 0; k < p.slots; ++k) mbar_init(smem_addr(&raw_full[k]), 1);
     for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_addr(&a_full[k]), kTmConv);
       mbar_init(smem_addr(&mma_done[k]), 1);
       mbar_init(smem_addr(&acc_full[k]), 1);
+      mbar_init(smem_addr(&acc_free[k]), kTmDrain);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
@@ -800,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_cons
     rowexp[tid] = exp_above(m, true);
   }
   __syncthreads();
-  for (int u = tid; u < p.Rp * (p.Jp32 / 8); u += kThreads) {  // U's digit tiles (row r, k = j)
+  for (int u = tid; u < p.Rp * (p.Jp32 / 8); u += kTmThreads) {  // U's digit tiles (row r, k = j)
     const int r = u / (p.Jp32 / 8), jg = u % (p.Jp32 / 8);
     uint32_t w[kATiles][4];
 #pragma unroll
@@ -835,57 +848,77 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_cons
       l0 = 0;
     }
   };
-  auto issue_copy = [&](int u) {  // part u % parts of tile u / parts -> slot u % slots (thread 0)
+  // the column exponent of tile row mm (-4000 past the tile's columns: such
+  // a column converts to zeros and is not written)
+  auto col_exp = [&](int it, int mm) -> int {
+    const int s = mm / p.BL, lo = mm - s * p.BL;
     int64_t l0, b0;
-    tile_origin(u / p.parts, l0, b0);
-    const int slot = u % p.slots;
-    const uint32_t bar = smem_addr(&raw_full[slot]);
-    mbar_expect_tx(bar, (uint32_t)p.raw_slot);
-    tma_load_3d(smem_addr(ring + (size_t)slot * p.raw_slot), &ymap, (int)l0, kTmKH * (u % p.parts), (int)b0, bar);
+    tile_origin(it, l0, b0);
+    const int64_t l = l0 + lo, b = b0 + s;
+    return (s < p.BB && l < p.L && b < p.B) ? colexp[l + p.L * b] : -4000;
   };
-  // tile row m: box column loff of run s; constant per thread
-  const int m = tid & (kM2 - 1), jq = tid >> 7;
-  const int s_m = m / p.BL, loff = m - s_m * p.BL;
-  const bool m_in_box = s_m < p.BB;
-  const int raw_off = (s_m * kTmKH + 8 * jq) * p.BL + loff;  // element (m, 8 jq) of a slot
-  auto load_cexp = [&](int it) {  // column exponents of tile it -> cexp[it % 4]
-    if (tid < kM2 && it < ntc) {
-      int64_t l0, b0;
-      tile_origin(it, l0, b0);
-      const int64_t l = l0 + loff, b = b0 + s_m;
-      cexp[it % 4][tid] = (m_in_box && l < p.L && b < p.B) ? colexp[l + p.L * b] : -4000;
-    }
-  };
-  load_cexp(0);
-  load_cexp(1);
-  int issued = 0;
-  if (tid == 0)
-    for (; issued < p.slots && issued < nunits; ++issued) issue_copy(issued);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // outputs of tile it (set it & 1): TMEM lanes 32 q.. (columns), rows g Rp/4 ..
-  auto drain = [&](int it) {
-    const int set = it & 1;
-    const bool ok =
-        __all_sync(0xffffffffu, mbar_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1)));
-    if (ok) {
+  if (warp < kTmConv) {
+    // ---------------- converters: thread (column m, rows 8 jq ..) of each part ----------------
+    const int m = tid & (kM2 - 1), jq = tid >> 7;
+    const int s_m = m / p.BL, loff = m - s_m * p.BL;
+    const bool m_in_box = s_m < p.BB;
+    const int raw_off = (s_m * kTmKH + 8 * jq) * p.BL + loff;  // element (m, 8 jq) of a slot
+    const int off = (m >> 3) * (int)kSboA + jq * 128 + (m & 7) * 16;
+    int f1022 = 0;
+    for (int u = 0; u < nunits; ++u) {
+      const int it = u / p.parts, pp = u - it * p.parts, slot = u % p.slots, stg = u & 1;
+      if (pp == 0) f1022 = col_exp(it, m) + 1022;
+      int ok = 1;
+      if (lane == 0) {
+        ok = role_wait(smem_addr(&raw_full[slot]), (uint32_t)((u / p.slots) & 1), &stop);
+        if (ok && u >= 2) ok = role_wait(smem_addr(&mma_done[stg]), (uint32_t)(((u - 2) >> 1) & 1), &stop);
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      const T *raw = reinterpret_cast<const T *>(ring + (size_t)slot * p.raw_slot) + raw_off;
+      uint32_t w[kBTiles][4];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        float d0[4], d1[4];
+        const T y0 = m_in_box ? raw[k * p.BL] : T(0), y1 = m_in_box ? raw[(k + 1) * p.BL] : T(0);
+        digits4_float(scaled_int28_bits(y0, f1022), d0);
+        digits4_float(scaled_int28_bits(y1, f1022), d1);
+#pragma unroll
+        for (int qq = 0; qq < kBTiles; ++qq) w[qq][k >> 1] = bf16_pair(d0[qq], d1[qq]);
+      }
+      unsigned char *st = Ast + stg * 4 * kATile;
+#pragma unroll
+      for (int qq = 0; qq < kBTiles; ++qq)
+        *reinterpret_cast<uint4 *>(st + qq * kATile + off) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&a_full[stg]));  // this warp has read slot u and written stage stg
+    }
+  } else if (warp < kTmConv + kTmDrain) {
+    // ---------------- drain: TMEM lanes 32 q.. (columns), half of the rows ----------------
+    const int dw = warp - kTmConv, q = warp & 3, half = dw >> 2;
+    const int mm = 32 * q + lane;
+    const int sm2 = mm / p.BL, lo2 = mm - sm2 * p.BL;
+    const int rh = p.Rp / 2;  // a multiple of 8
+    for (int it = 0; it < ntc; ++it) {
+      const int set = it & 1;
+      if (dw == 0 && lane == 0) drain_go = role_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1), &stop);
+      asm volatile("bar.sync 1, %0;" ::"n"(kTmDrain * 32) : "memory");
+      if (!drain_go) break;
       fence_after();
-      const int q = warp & 3, g = warp >> 2;
-      const int mm = 32 * q + lane;
-      const int sm2 = mm / p.BL, lo2 = mm - sm2 * p.BL;
       int64_t l0, b0;
       tile_origin(it, l0, b0);
       const int64_t l = l0 + lo2, b = b0 + sm2;
       const bool valid = sm2 < p.BB && l < p.L && b < p.B;
-      const int fc = cexp[it % 4][mm];
+      const int fc = valid ? colexp[l + p.L * b] : 0;
       double *zc = z + l + p.L * (int64_t)p.R * b;
-      const int rq = p.Rp / 4;
       const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * 4 * p.Rp);
-      for (int r0 = g * rq; r0 < (g + 1) * rq; r0 += 4) {
+      for (int r0 = half * rh; r0 < (half + 1) * rh; r0 += 4) {
         uint32_t a[4][4];
 #pragma unroll
         for (int lev = 0; lev < 4; ++lev)
@@ -901,72 +934,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split_tma(const __grid_cons
           }
         }
       }
-    } else {
-      stop = 1;
+      fence_before();
+      asm volatile("bar.sync 1, %0;" ::"n"(kTmDrain * 32) : "memory");
+      if (lane == 0) mbar_arrive(smem_addr(&acc_free[set]));  // this warp's reads of the set are complete
     }
-    fence_before();
-    __syncthreads();
-  };
-
-  int last_committed = -1;
-  for (int it = 0; it < ntc && !stop; ++it) {
-    const int set = it & 1;
-    const int f1022 = cexp[it % 4][m] + 1022;
-    // read after later barriers; buffer (it + 2) % 4 is no longer needed (tile it - 2 is drained)
-    if (it + 2 < ntc) load_cexp(it + 2);
-    for (int pp = 0; pp < p.parts; ++pp) {
-      const int u = it * p.parts + pp, slot = u % p.slots, stg = u & 1;
-      bool ok = mbar_wait(smem_addr(&raw_full[slot]), (uint32_t)((u / p.slots) & 1));
-      if (ok && u >= 2) ok = mbar_wait(smem_addr(&mma_done[stg]), (uint32_t)(((u - 2) >> 1) & 1));
-      if (ok) {
-        const T *raw = reinterpret_cast<const T *>(ring + (size_t)slot * p.raw_slot) + raw_off;
-        uint32_t w[kBTiles][4];
+  } else if (lane == 0) {
+    // ---------------- control: copies and MMAs ----------------
+    auto issue_copy = [&](int u) {  // part u % parts of tile u / parts -> slot u % slots
+      int64_t l0, b0;
+      tile_origin(u / p.parts, l0, b0);
+      const int slot = u % p.slots;
+      const uint32_t bar = smem_addr(&raw_full[slot]);
+      mbar_expect_tx(bar, (uint32_t)p.raw_slot);
+      tma_load_3d(smem_addr(ring + (size_t)slot * p.raw_slot), &ymap, (int)l0, kTmKH * (u % p.parts), (int)b0, bar);
+    };
+    int issued = 0, last = -1;
+    for (; issued < p.slots && issued < nunits; ++issued) issue_copy(issued);
+    const uint32_t ub = smem_addr(Ut);
+    for (int u = 0; u < nunits; ++u) {
+      const int it = u / p.parts, pp = u - it * p.parts, stg = u & 1, set = it & 1;
+      if (!role_wait(smem_addr(&a_full[stg]), (uint32_t)((u >> 1) & 1), &stop)) break;
+      if (issued < nunits) issue_copy(issued++);  // slot u % slots has been read by every converter
+      if (pp == 0 && it >= 2 && !role_wait(smem_addr(&acc_free[set]), (uint32_t)(((it - 2) >> 1) & 1), &stop)) break;
+      fence_after();
+      const uint32_t ab = smem_addr(Ast + stg * 4 * kATile);
+      const uint32_t d0 = tmem + (uint32_t)(set * 4 * p.Rp);
 #pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          float d0[4], d1[4];
-          const T y0 = m_in_box ? raw[k * p.BL] : T(0), y1 = m_in_box ? raw[(k + 1) * p.BL] : T(0);
-          digits4_float(scaled_int28_bits(y0, f1022), d0);
-          digits4_float(scaled_int28_bits(y1, f1022), d1);
+      for (int ks = 0; ks < kTmKH / 16; ++ks) {
+        const uint64_t ucat = smem_desc(ub + (uint32_t)(((kTmKH / 8) * pp + 2 * ks) * 128), 128, sbo_u);
 #pragma unroll
-          for (int qq = 0; qq < kBTiles; ++qq) w[qq][k >> 1] = bf16_pair(d0[qq], d1[qq]);
+        for (int qq = 0; qq < kBTiles; ++qq) {
+          const uint64_t ya = smem_desc(ab + qq * kATile + 256 * ks, 128, kSboA);
+          mma_bf16(d0 + qq * p.Rp, ya, ucat, idesc_q[qq], (pp == 0 && ks == 0 && qq == 0) ? 0u : 1u);
         }
-        unsigned char *st = Ast + stg * 4 * kATile;
-        const int off = (m >> 3) * (int)kSboA + jq * 128 + (m & 7) * 16;
-#pragma unroll
-        for (int qq = 0; qq < kBTiles; ++qq)
-          *reinterpret_cast<uint4 *>(st + qq * kATile + off) = make_uint4(w[qq][0], w[qq][1], w[qq][2], w[qq][3]);
-      } else {
-        stop = 1;
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (stop) break;
-      if (tid == 0) {
-        if (issued < nunits) issue_copy(issued++);  // slot u has been read by every thread
-        fence_after();
-        const uint32_t ab = smem_addr(Ast + stg * 4 * kATile), ub = smem_addr(Ut);
-        const uint32_t d0 = tmem + (uint32_t)(set * 4 * p.Rp);
-#pragma unroll
-        for (int ks = 0; ks < kTmKH / 16; ++ks) {
-          const uint64_t ucat = smem_desc(ub + (uint32_t)(((kTmKH / 8) * pp + 2 * ks) * 128), 128, sbo_u);
-#pragma unroll
-          for (int qq = 0; qq < kBTiles; ++qq) {
-            const uint64_t ya = smem_desc(ab + qq * kATile + 256 * ks, 128, kSboA);
-            mma_bf16(d0 + qq * p.Rp, ya, ucat, idesc_q[qq], (pp == 0 && ks == 0 && qq == 0) ? 0u : 1u);
-          }
-        }
-        mma_commit(smem_addr(&mma_done[stg]));
-        if (pp == p.parts - 1) mma_commit(smem_addr(&acc_full[set]));
-      }
-      last_committed = u;
+      mma_commit(smem_addr(&mma_done[stg]));
+      if (pp == p.parts - 1) mma_commit(smem_addr(&acc_full[set]));
+      last = u;
     }
-    if (stop) break;
-    if (it >= 1) drain(it - 1);  // the previous tile, while this one's MMAs run
-  }
-  if (!stop && ntc >= 1) drain(ntc - 1);
-  if (stop && tid == 0) {  // our own MMAs and copies finish (bounded) before TMEM and shared memory go
-    if (last_committed >= 0)
-      mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)((last_committed >> 1) & 1));
+    // no MMA or copy of ours may still run when TMEM and shared memory go
+    if (last >= 0) mbar_wait(smem_addr(&mma_done[last & 1]), (uint32_t)((last >> 1) & 1));
     for (int c = max(0, issued - p.slots); c < issued; ++c)
       mbar_wait(smem_addr(&raw_full[c % p.slots]), (uint32_t)((c / p.slots) & 1));
   }
@@ -1054,7 +1061,7 @@ int run_ttm_tma(const CUtensorMap &map, const void *y, int64_t L, int64_t J, int
     d_colexp = tmp;
   }
   TK_CUDA(cudaFuncSetAttribute(k_ttm_split_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-  k_ttm_split_tma<T><<<p.grid, kThreads, p.smem, s>>>(map, U, p, d_colexp, z, d_err);
+  k_ttm_split_tma<T><<<p.grid, kTmThreads, p.smem, s>>>(map, U, p, d_colexp, z, d_err);
   TK_LAUNCHED();
   if (tmp) TK_CUDA(cudaFreeAsync(tmp, s));
   return TUCKER_OK;
