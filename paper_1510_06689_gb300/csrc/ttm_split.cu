@@ -132,14 +132,17 @@ __device__ __forceinline__ void digits4_float(int v, float (&d)[4]) {
 // sum_k a_k 2^(28 - 7k) 2^sc as a float64, from four float accumulators that
 // hold integers |a_k| < 2^22 (the levels 2..5 of a digit product): the
 // integers come out of the floats exactly by magic-number addition, pairs
-// combine in 32 bits (|a0 2^7 + a1| < 2^30), and the 50-bit sum converts
-// exactly from its bits.
+// combine in 32 bits (|a0 2^7 + a1| < 2^30), and the 50-bit sum is exact in
+// float64.  Its conversion and the power-of-two scale run on the float64
+// pipe (idle in these kernels, where the integer pipe is the busy one);
+// scales outside the normal exponent range take the exact bit assembly.
 __device__ __forceinline__ double levels_to_double(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, int sc) {
   const int i0 = __float_as_int(__fadd_rn(__uint_as_float(a0), 12582912.0f)) - 0x4B400000;
   const int i1 = __float_as_int(__fadd_rn(__uint_as_float(a1), 12582912.0f)) - 0x4B400000;
   const int i2 = __float_as_int(__fadd_rn(__uint_as_float(a2), 12582912.0f)) - 0x4B400000;
   const int i3 = __float_as_int(__fadd_rn(__uint_as_float(a3), 12582912.0f)) - 0x4B400000;
   const long long v = ((long long)(i0 * 128 + i1) << 21) + ((long long)(i2 * 128 + i3) << 7);
+  if (sc >= -1022 && sc <= 1023) return __dmul_rn((double)v, __longlong_as_double((long long)(sc + 1023) << 52));
   return scaled_ll_to_double(v, sc);
 }
 
