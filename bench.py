@@ -321,7 +321,7 @@ def phase_roofline(prof, phase, steps, path):
              "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 "
                             "1.25 TFLOP/s; measured DFMA loop 1.193 TFLOP/s)"}
         if phase == "eig":
-            r["flops_source"] = "the paper's count of the eigenvector step, 10/3 J^3 per mode (Sec. 4.4)"
+            r["flops_source"] = "the paper's count of the eigenvector step, 10/3 J^3 per mode (Sec. 5.4)"
     tr = TRAFFIC.get((kernel, kernel_source_hash(kernel))) if kernel in KERNEL_FILES else None
     r["traffic"] = round(tr["ratio"] * per_bytes) if tr else None
     r["traffic_source"] = (f"ncu DRAM/algorithmic ratio of {tr['captured']}, scaled to the timed launches"

@@ -13,7 +13,7 @@
  * ---------------------------------------
  * - Tensors are dense and stored in *natural layout*: element
  *   (i_1, ..., i_N) (0-based) sits at offset i_1 + I_1 (i_2 + I_2 (i_3 + ...)),
- *   i.e. the mode-1 unfolding is column-major (Sec. 3.1).  At mode n the
+ *   i.e. the mode-1 unfolding is column-major (Sec. 4.1).  At mode n the
  *   library views a tensor of current dimensions J_1..J_N as the 3-D array
  *   (L, J_n, B) with L = prod_{m<n} J_m (fastest) and B = prod_{m>n} J_m;
  *   entry (l, j, b) is at l + L (j + J_n b).  This is the unfolding of
@@ -106,7 +106,7 @@ typedef struct tucker_result {
  *   eps        relative error target (not squared).  eps <= 0 keeps every index
  *              (R_n = I_n); NaN is rejected.  R_n is the smallest R in [1, J_n]
  *              with sum_{r>R} max(lambda_r, 0) <= eps^2 ||X||^2 / N, where ||X|| is
- *              the norm of the original X (Algorithm 1; Sec. 6.2).
+ *              the norm of the original X (Algorithm 1; Sec. 7.2).
  *   mode_order 0-based permutation of 0..N-1 giving the processing order, or NULL
  *              for 0..N-1 ("the modes can be processed in any arbitrary order",
  *              Sec. 2.2).  The core keeps the original mode positions.
@@ -138,7 +138,71 @@ TUCKER_API int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const in
 TUCKER_API int tucker_reconstruct(const tucker_result *r, double *Xhat, void *stream);
 
 /*
- * tucker_rel_error -- ||X - X~|| / ||X|| (the normalised RMS error of Sec. 6.2).
+ * tucker_reconstruct_sub -- the subtensor X~[lo_1:hi_1, ..., lo_N:hi_N) of
+ * Eq. reconstruct without forming X~: G x_1 U_1[lo_1:hi_1, :] ... x_N
+ * U_N[lo_N:hi_N, :], i.e. the same product with subsets of rows of the factor
+ * matrices (Sec. 2.3; e.g. one variable, a few time steps or a subgrid).
+ *   lo, hi  host arrays of r->N indices, 0 <= lo[n] < hi[n] <= r->dims[n].
+ *   Xsub    device, caller-allocated, prod(hi - lo) float64, natural layout
+ *           (index lo fastest in mode 1).
+ * Returns TUCKER_OK, EINVAL (bad ranges or result), ENOMEM or ECUDA.
+ * Synchronises `stream`.
+ */
+TUCKER_API int tucker_reconstruct_sub(const tucker_result *r, const int64_t *lo, const int64_t *hi, double *Xsub,
+                                      void *stream);
+
+/*
+ * tucker_hooi -- Algorithm 2 (HOOI, Sec. 2.2), started from Algorithm 1.
+ *   X, dt, dims, N, eps, prec  as for tucker_sthosvd (identity mode order); the
+ *              ST-HOSVD fixes the ranks R_n and gives the starting factors.
+ *   max_iters  >= 0 iterations at most (0 returns the ST-HOSVD result).
+ *   tol        >= 0: stop after an iteration that lowers ||X||^2 - ||G||^2 by
+ *              at most tol ||X||^2 (the fit test of Algorithm 2).
+ *   out        as for tucker_sthosvd; eigvals and tail stay those of the
+ *              starting ST-HOSVD.
+ *   iters      host int: the iterations run.
+ *   fit        NULL or a host array of max_iters + 1 doubles: ||X||^2 - ||G||^2
+ *              at the start and after each iteration.
+ * One iteration: for n = 1..N, Y = X x {U_m^T}_{m != n} with the factors
+ * updated so far, U_n = the leading R_n eigenvectors of Y_(n) Y_(n)^T; then
+ * G = Y x_N U_N^T.  With prec = TUCKER_PREC_BF16X4 the mode products run on
+ * the split-precision kernels and the (small) Grams of Y in float64.
+ * Returns the codes of tucker_sthosvd; on error `out` holds nothing.
+ */
+TUCKER_API int tucker_hooi(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, int max_iters,
+                           double tol, tucker_precision prec, void *stream, tucker_result *out, int *iters,
+                           double *fit);
+
+/* Mode-order rules for tucker_mode_order (Sec. 8.3). */
+typedef enum {
+  TUCKER_ORDER_GREEDY_FLOPS = 0, /* at each step the mode whose step costs the fewest flops */
+  TUCKER_ORDER_GREEDY_RATIO = 1, /* at each step the mode with the largest I_n / R_n */
+  TUCKER_ORDER_EXHAUSTIVE = 2    /* the order of fewest total flops, every permutation tried (N <= 9) */
+} tucker_order_rule;
+
+/*
+ * tucker_order_flops -- flops of Algorithm 1 in a mode order, by the cost model
+ * of Sec. 6.1 with one process: the step on mode n, with J the product of the
+ * current dimensions, costs 2 I_n J (Gram) + 2 R_n J (TTM) + 10/3 I_n^3
+ * (eigenvectors), and then J_n becomes R_n.
+ *   dims, ranks  host, N values, 1 <= R_n <= I_n (ranks known or estimated).
+ *   order        0-based permutation or NULL (0..N-1).  flops: host double.
+ * Host only (no device work).  Returns TUCKER_OK or EINVAL.
+ */
+TUCKER_API int tucker_order_flops(const int64_t *dims, const int64_t *ranks, int N, const int *order,
+                                  double *flops);
+
+/*
+ * tucker_mode_order -- a processing order for tucker_sthosvd by one of the
+ * heuristics of Sec. 8.3 (rule: tucker_order_rule; ties keep the lower mode
+ * index, and the exhaustive search keeps the lexicographically first of
+ * equal-cost orders).  order: host, N ints (0-based).  Host only.
+ * Returns TUCKER_OK or EINVAL.
+ */
+TUCKER_API int tucker_mode_order(const int64_t *dims, const int64_t *ranks, int N, int rule, int *order);
+
+/*
+ * tucker_rel_error -- ||X - X~|| / ||X|| (the normalised RMS error of Sec. 7.2).
  * X~ is never materialised: the last mode's expansion is fused with reading X
  * and accumulating (x - x~)^2 in float64.  rel_out is a host double.
  * Returns 0 for X = 0 = X~, +Inf for X = 0 != X~.  Synchronises `stream`.
@@ -196,7 +260,7 @@ TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, i
  *   J <= 128 (else TUCKER_EUNSUPPORTED).  An Inf or NaN in Y makes every
  *   entry of S NaN.  Synchronises `stream`; returns TUCKER_ETIMEOUT if a
  *   bounded tensor-core wait expired.  No counterpart in the paper (its Gram
- *   is float64, Sec. 4.3); this is the split-precision reading of the Gram
+ *   is float64, Sec. 5.3); this is the split-precision reading of the Gram
  *   step of Algorithm 1. */
 TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
                                  void *stream);

@@ -10,16 +10,16 @@ Every step follows the paper's definitions in the order of Algorithm 1
 routines serve as single steps where the step *is* that routine: a matrix
 product for the Gram matrix and the mode-n product, LAPACK's symmetric
 eigensolver (``numpy.linalg.eigh``) for "leading eigenvectors of S", as the
-paper itself uses LAPACK's ``dsyevx`` there (Sec. 4.4).
+paper itself uses LAPACK's ``dsyevx`` there (Sec. 5.4).
 
 Readings of points the paper leaves open (each is repeated in the design doc):
 
 * Unfolding (Sec. 2.1): the printed column-index formula is garbled (it uses
   I/I_k where prefix products are meant).  We use the standard map
   j = sum_{k != n} i_k prod_{m<k, m != n} I_m (0-based), which is the order in
-  which the natural (first-index-fastest) layout of Sec. 3.1 stores the
+  which the natural (first-index-fastest) layout of Sec. 4.1 stores the
   columns.
-* Rank rule (Algorithm 1, Sec. 6.2): R_n is the smallest R in [1, I_n] with
+* Rank rule (Algorithm 1, Sec. 7.2): R_n is the smallest R in [1, I_n] with
   sum_{r>R} lambda_r <= eps^2 ||X||^2 / N, where ||X|| is the norm of the
   *original* tensor, negative eigenvalues (rounding) count as 0, and the tail
   sums are accumulated from the smallest eigenvalue upward.  eps <= 0 keeps
@@ -32,12 +32,25 @@ Readings of points the paper leaves open (each is repeated in the design doc):
   always I_n x R_n.
 * Reconstruction (Eq. reconstruct, Sec. 2.3): X~ = G x {U_n}, and the
   normalised RMS error is ||X - X~|| / ||X||, formed from the explicit
-  difference.
+  difference.  A subtensor uses the same product with row subsets of the
+  factors (Sec. 2.3).
+* HOOI (Algorithm 2): ranks fixed by the ST-HOSVD that starts it; within an
+  iteration every mode uses the factors already updated in that iteration
+  (the loop of Algorithm 2 as printed); the stopping test "||X||^2 - ||G||^2
+  ceases to decrease" is read as: stop after an iteration whose decrease is
+  at most tol ||X||^2 (tol = 0: no decrease at all), or after max_iters.
+* Mode-order flop model (the ST-HOSVD cost of Sec. 6.1 with P = 1): the step on
+  mode n, with J the product of the current dimensions, costs
+  2 I_n J (Gram) + 2 R_n J (TTM) + 10/3 I_n^3 (eigenvectors); J then shrinks
+  by R_n / I_n.  The two heuristics of Sec. 8.3 pick, at each step, the mode
+  with the fewest flops in that step, or the largest I_n / R_n (ties: lower
+  mode index).
 
 Parity pins for every function here live in ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 
+import itertools
 import math
 
 import numpy as np
@@ -54,6 +67,11 @@ __all__ = [
     "sthosvd",
     "reconstruct",
     "rel_error",
+    "reconstruct_sub",
+    "hooi",
+    "order_flops",
+    "greedy_order",
+    "best_order",
     "compression_ratio",
 ]
 
@@ -117,7 +135,7 @@ def rank_from_eps(lam, threshold, keep_all=False):
 
     ``lam`` is sorted descending.  Returns (R, tail) where tail is the
     discarded sum for that R.  Tail sums run from the smallest eigenvalue
-    upward (Algorithm 1, rank step; Sec. 6.2).
+    upward (Algorithm 1, rank step; Sec. 7.2).
     """
     j = len(lam)
     if keep_all:
@@ -198,7 +216,7 @@ def reconstruct(core_flat, ranks, factors):
 
 
 def rel_error(x_flat, core_flat, ranks, factors):
-    """||X - X~|| / ||X|| from the explicit difference (Sec. 6.2, normalised RMS error)."""
+    """||X - X~|| / ||X|| from the explicit difference (Sec. 7.2, normalised RMS error)."""
     x = np.asarray(x_flat, dtype=np.float64).ravel()
     d = x - reconstruct(core_flat, ranks, factors)
     nx2 = float(np.dot(x, x))
@@ -207,6 +225,93 @@ def rel_error(x_flat, core_flat, ranks, factors):
     return math.sqrt(float(np.dot(d, d)) / nx2)
 
 
+def reconstruct_sub(core_flat, ranks, factors, lo, hi):
+    """X~[lo_1:hi_1, ..., lo_N:hi_N] = G x {U_n[lo_n:hi_n, :]} (Sec. 2.3), flat natural layout."""
+    g = as_tensor(core_flat, ranks)
+    for n, u in enumerate(factors):
+        g = ttm(g, n, np.asarray(u)[int(lo[n]):int(hi[n]), :])
+    return np.asarray(g).ravel(order="F")
+
+
+def hooi(x_flat, dims, eps, max_iters=10, tol=0.0, order=None):
+    """Algorithm 2 (HOOI), started from Algorithm 1 with the same eps.
+
+    Returns the ST-HOSVD dict updated with the refined core and factors, the
+    fit history ||X||^2 - ||G||^2 (one value for the start and one per
+    iteration) and the number of iterations run.
+    """
+    res = sthosvd(x_flat, dims, eps, order)
+    dims = res["dims"]
+    n_modes = len(dims)
+    ranks = res["ranks"]
+    x = as_tensor(x_flat, dims)
+    nx2 = res["norm2"]
+    factors = [u.copy() for u in res["factors"]]
+    core = as_tensor(res["core"], ranks)
+    history = [nx2 - norm2(core)]
+    iters = 0
+    for _ in range(max_iters):
+        for n in range(n_modes):
+            y = x
+            for m in range(n_modes):  # Y = X x {U_m^T}, m != n
+                if m != n:
+                    y = ttm(y, m, factors[m].T)
+            _, v = leading_eigenpairs(gram(y, n))
+            factors[n] = v[:, : ranks[n]].copy()
+        core = ttm(y, n_modes - 1, factors[n_modes - 1].T)  # the last Y of the loop
+        iters += 1
+        history.append(nx2 - norm2(core))
+        if history[-2] - history[-1] <= tol * nx2:
+            break
+    out = dict(res)
+    out["factors"] = factors
+    out["core"] = np.asarray(core).ravel(order="F").copy()
+    out["history"] = history
+    out["iters"] = iters
+    return out
+
+
+def order_flops(dims, ranks, order):
+    """Flops of Algorithm 1 in the given mode order (Sec. 6.1 cost model, P = 1)."""
+    cur = [int(d) for d in dims]
+    total = 0.0
+    for n in order:
+        j = math.prod(cur)
+        total += 2.0 * dims[n] * j + 2.0 * ranks[n] * j + 10.0 / 3.0 * float(dims[n]) ** 3
+        cur[n] = int(ranks[n])
+    return total
+
+
+def greedy_order(dims, ranks, rule):
+    """The mode orders of the Sec. 8.3 heuristics: rule "flops" or "ratio"."""
+    left = list(range(len(dims)))
+    cur = [int(d) for d in dims]
+    order = []
+    while left:
+        if rule == "flops":
+            j = math.prod(cur)
+            cost = {n: 2.0 * dims[n] * j + 2.0 * ranks[n] * j + 10.0 / 3.0 * float(dims[n]) ** 3 for n in left}
+            pick = min(left, key=lambda n: (cost[n], n))
+        elif rule == "ratio":
+            pick = min(left, key=lambda n: (-dims[n] / ranks[n], n))
+        else:
+            raise ValueError("rule must be 'flops' or 'ratio'")
+        order.append(pick)
+        left.remove(pick)
+        cur[pick] = int(ranks[pick])
+    return order
+
+
+def best_order(dims, ranks):
+    """The order of fewest flops by trying every permutation (ties: lexicographically first)."""
+    best = None
+    for perm in itertools.permutations(range(len(dims))):
+        f = order_flops(dims, ranks, perm)
+        if best is None or f < best[0]:
+            best = (f, list(perm))
+    return best[1]
+
+
 def compression_ratio(dims, ranks):
-    """C = prod I_n / (prod R_n + sum I_n R_n) (Sec. 6.2)."""
+    """C = prod I_n / (prod R_n + sum I_n R_n) (Sec. 7.2)."""
     return math.prod(dims) / (math.prod(ranks) + sum(i * r for i, r in zip(dims, ranks)))

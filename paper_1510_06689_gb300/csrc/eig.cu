@@ -2,7 +2,7 @@
 // symmetric Gram matrix S by cyclic Jacobi in float64, then the error rule
 // that picks R_n.
 //
-// The paper calls LAPACK's dsyevx redundantly on every process (Sec. 4.4,
+// The paper calls LAPACK's dsyevx redundantly on every process (Sec. 5.4,
 // Algorithm 5) and notes the cost is negligible.  Here one CTA runs a
 // parallel-order Jacobi: each step applies m/2 disjoint rotations chosen by
 // the round-robin (circle) tournament over the m = J rounded-up-to-even
@@ -751,7 +751,7 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
       else
         TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_dsm<true>, d_S, (int)J, d_lam, d_V, d_ws, d_info));
       TK_LAUNCHED();
-      if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 4.4
+      if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 5.4
       return TUCKER_OK;
     }
   }
@@ -776,7 +776,7 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
     if (prof) prof->begin(TUCKER_PHASE_EIG);
     TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, d_S, (int)J, d_lam, d_V, d_ws, d_info));
     TK_LAUNCHED();
-    if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 4.4
+    if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 5.4
     return TUCKER_OK;
   }
   size_t smem = 0;
@@ -794,7 +794,7 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
   if (prof) prof->begin(TUCKER_PHASE_EIG);
   k_jacobi<<<1, kEigThreads, smem, s>>>(d_S, (int)J, d_lam, d_V, ws, d_info);
   TK_LAUNCHED();
-  if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 4.4
+  if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);  // flops: the paper's count, Sec. 5.4
   return TUCKER_OK;
 }
 

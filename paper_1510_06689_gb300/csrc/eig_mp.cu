@@ -1,5 +1,5 @@
 // Mixed-precision eigensolver for the eigenvector step of Algorithm 1
-// (Sec. 2.2; the paper calls LAPACK's dsyevx, Sec. 4.4, Algorithm 5).
+// (Sec. 2.2; the paper calls LAPACK's dsyevx, Sec. 5.4, Algorithm 5).
 //
 // GB300's float64 pipe issues ~2 FMAs per clock per SM, so a float64 Jacobi
 // of a 128 x 128 Gram (18 sweeps of 127 dependent steps) is bound by latency
@@ -1489,7 +1489,7 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   TK_CUDA(cudaMemcpyAsync(chk, w.check, sizeof chk, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaMemcpyAsync(&sw, w.sweeps, sizeof sw, cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
-  // the paper's flop count of the eigenvector step (10/3 J^3, Sec. 4.4); bytes: S read, V written
+  // the paper's flop count of the eigenvector step (10/3 J^3, Sec. 5.4); bytes: S read, V written
   if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);
   const double tol_res = 16.0 * m * kU * chk[2], tol_orth = 16.0 * m * kU;
   if (chk[0] <= tol_res && chk[1] <= tol_orth) {

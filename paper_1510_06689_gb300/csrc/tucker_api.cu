@@ -17,6 +17,7 @@
 // All device memory is stream-ordered (cudaMallocAsync on the caller's stream).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -467,18 +468,22 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
 }
 
 // Expands core x {U_n} over every mode except `skip` (or all when skip < 0),
-// smallest growth first; returns the buffer and its current dims.
+// smallest growth first; returns the buffer and its current dims.  With lo
+// and hi (both or neither), mode n expands to rows lo[n] .. hi[n]-1 of U_n
+// only: a subtensor of X~ (Sec. 2.3, subsets of rows of the factors).
 static int expand_modes(const tucker_result *r, int skip, double *final_out, DevBuf &hold, const double **res,
-                        int64_t *cur, const DeviceInfo &dev, cudaStream_t s, Prof *prof) {
+                        int64_t *cur, const DeviceInfo &dev, cudaStream_t s, Prof *prof, const int64_t *lo = nullptr,
+                        const int64_t *hi = nullptr) {
   const int N = r->N;
   for (int n = 0; n < N; ++n) cur[n] = r->ranks[n];
+  auto rows = [&](int n) -> int64_t { return lo ? hi[n] - lo[n] : r->dims[n]; };
   int seq[TUCKER_MAX_MODES], cnt = 0;
   for (int n = 0; n < N; ++n)
     if (n != skip) seq[cnt++] = n;
-  for (int a = 1; a < cnt; ++a)  // insertion sort by growth I_n / R_n
+  for (int a = 1; a < cnt; ++a)  // insertion sort by growth rows_n / R_n
     for (int b = a; b > 0; --b) {
-      const double gb = (double)r->dims[seq[b]] / r->ranks[seq[b]];
-      const double ga = (double)r->dims[seq[b - 1]] / r->ranks[seq[b - 1]];
+      const double gb = (double)rows(seq[b]) / r->ranks[seq[b]];
+      const double ga = (double)rows(seq[b - 1]) / r->ranks[seq[b - 1]];
       if (gb < ga) std::swap(seq[b], seq[b - 1]);
     }
   const double *y = r->core;
@@ -488,7 +493,7 @@ static int expand_modes(const tucker_result *r, int skip, double *final_out, Dev
     int64_t L = 1, B = 1;
     for (int m = 0; m < n; ++m) L *= cur[m];
     for (int m = n + 1; m < N; ++m) B *= cur[m];
-    const int64_t J = cur[n], K = r->dims[n];
+    const int64_t J = cur[n], K = rows(n);
     double *z;
     DevBuf next;
     if (final_out && k == cnt - 1) {
@@ -497,8 +502,9 @@ static int expand_modes(const tucker_result *r, int skip, double *final_out, Dev
       TK_CHECK(next.alloc(sizeof(double) * L * K * B, s));
       z = next.as<double>();
     }
-    // A = U_n (K x J, column-major): A[k, j] = U[k + K j]
-    TK_CHECK(launch_ttm(y, TUCKER_F64, L, J, B, r->factors[n], /*ak=*/1, /*aj=*/K, K, z, dev, s, prof));
+    // A = rows lo[n].. of U_n (I_n x J, column-major): A[k, j] = U[lo + k + I_n j]
+    TK_CHECK(launch_ttm(y, TUCKER_F64, L, J, B, r->factors[n] + (lo ? lo[n] : 0), /*ak=*/1, /*aj=*/r->dims[n], K, z,
+                        dev, s, prof));
     if (!(final_out && k == cnt - 1)) {
       tmp.reset();
       tmp.p = next.release();
@@ -518,6 +524,139 @@ static int expand_modes(const tucker_result *r, int skip, double *final_out, Dev
   hold.s = s;
   *res = y;
   return TUCKER_OK;
+}
+
+// Algorithm 2 (HOOI) after Algorithm 1 has filled `out` (ranks fixed).
+// Each iteration: for n = 0..N-1, Y = X x {U_m^T}_{m != n} with the factors
+// as updated so far (the TTM chain takes the largest reductions I_m / R_m
+// first), S = Y_(n) Y_(n)^T, U_n = leading R_n eigenvectors of S; then
+// G = Y x_{N-1} U_{N-1}^T from the last Y.  fit[k] = ||X||^2 - ||G||^2.
+static int hooi_iterate(const void *X, tucker_dtype dt, int max_iters, double tol, tucker_precision prec,
+                        cudaStream_t s, tucker_result *out, int *iters, double *fit) {
+  const int N = out->N;
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  int64_t maxJ = 1, ncore = 1;
+  for (int n = 0; n < N; ++n) {
+    maxJ = std::max(maxJ, out->dims[n]);
+    ncore *= out->ranks[n];
+  }
+  DevBuf S, lam, V, eigws, gramws, partials, scal;
+  TK_CHECK(S.alloc(sizeof(double) * maxJ * maxJ, s));
+  TK_CHECK(lam.alloc(sizeof(double) * maxJ, s));
+  TK_CHECK(V.alloc(sizeof(double) * maxJ * maxJ, s));
+  TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
+  TK_CHECK(scal.alloc(64, s));
+  double *d_g2 = scal.as<double>();
+  int *d_info = reinterpret_cast<int *>(d_g2 + 1);
+  int *d_terr = reinterpret_cast<int *>(d_g2 + 2);
+  TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
+  const double nx2 = out->norm2_x;
+  auto core_fit = [&](double *f) -> int {
+    TK_CHECK(launch_norm2(out->core, TUCKER_F64, ncore, partials.as<double>(), d_g2, s, &prof));
+    double g2 = 0.0;
+    TK_CUDA(cudaMemcpyAsync(&g2, d_g2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    *f = nx2 - g2;
+    return TUCKER_OK;
+  };
+  double prev = 0.0;
+  TK_CHECK(core_fit(&prev));
+  if (fit) fit[0] = prev;
+  *iters = 0;
+  for (int it = 0; it < max_iters; ++it) {
+    for (int n = 0; n < N; ++n) {
+      int seq[TUCKER_MAX_MODES], cnt = 0;
+      for (int m = 0; m < N; ++m)
+        if (m != n) seq[cnt++] = m;
+      std::stable_sort(seq, seq + cnt, [&](int a, int b) {
+        return (double)out->dims[a] / out->ranks[a] > (double)out->dims[b] / out->ranks[b];
+      });
+      int64_t cur[TUCKER_MAX_MODES];
+      for (int m = 0; m < N; ++m) cur[m] = out->dims[m];
+      const void *Y = X;
+      tucker_dtype ydt = dt;
+      DevBuf ybuf;
+      for (int k = 0; k < cnt; ++k) {
+        const int m = seq[k];
+        int64_t L = 1, B = 1;
+        for (int q = 0; q < m; ++q) L *= cur[q];
+        for (int q = m + 1; q < N; ++q) B *= cur[q];
+        const int64_t J = cur[m], R = out->ranks[m];
+        DevBuf ynew;
+        TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
+        if (prec == TUCKER_PREC_BF16X4)
+          TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, out->factors[m], R, ynew.as<double>(), d_terr, dev, s, &prof));
+        else
+          TK_CHECK(launch_ttm(Y, ydt, L, J, B, out->factors[m], /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev, s,
+                              &prof));
+        ybuf.reset();
+        ybuf.p = ynew.release();
+        ybuf.s = s;
+        Y = ybuf.p;
+        ydt = TUCKER_F64;
+        cur[m] = R;
+      }
+      int64_t L = 1, B = 1;
+      for (int q = 0; q < n; ++q) L *= cur[q];
+      for (int q = n + 1; q < N; ++q) B *= cur[q];
+      const int64_t J = out->dims[n], R = out->ranks[n];
+      TK_CHECK(gramws.alloc(sizeof(double) * gram_workspace_doubles(L, J, B, dev), s));
+      TK_CHECK(launch_gram(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof));
+      const int64_t ews = eig_workspace_doubles(J);
+      if (ews > 0) TK_CHECK(eigws.alloc(sizeof(double) * ews, s));
+      TK_CHECK(launch_eig(S.as<double>(), J, lam.as<double>(), V.as<double>(), ews > 0 ? eigws.as<double>() : nullptr,
+                          d_info, s, &prof, -1.0));
+      int info[2];
+      TK_CUDA(cudaMemcpyAsync(info, d_info, sizeof info, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      if (info[1] != 0) {
+        set_error("HOOI: the eigensolver did not converge for mode %d (J = %lld)", n, (long long)J);
+        return TUCKER_ENOCONV;
+      }
+      TK_CUDA(cudaMemcpyAsync(out->factors[n], V.p, sizeof(double) * J * R, cudaMemcpyDeviceToDevice, s));
+      if (n == N - 1) {  // G = Y x_{N-1} U_{N-1}^T
+        TK_CHECK(launch_ttm(Y, ydt, L, J, B, out->factors[n], /*ak=*/J, /*aj=*/1, R, out->core, dev, s, &prof));
+      }
+    }
+    double f = 0.0;
+    TK_CHECK(core_fit(&f));
+    *iters = it + 1;
+    if (fit) fit[it + 1] = f;
+    const bool done = prev - f <= tol * nx2;
+    prev = f;
+    if (done) break;
+  }
+  int terr = 0;
+  TK_CUDA(cudaMemcpyAsync(&terr, d_terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  if (terr) {
+    set_error("split-precision TTM: a bounded tensor-core wait expired");
+    return TUCKER_ETIMEOUT;
+  }
+  return TUCKER_OK;
+}
+
+// Flops of Algorithm 1 in a mode order (the ST-HOSVD cost of Sec. 6.1 with
+// one process): the step on mode n, with J the product of the current
+// dimensions, costs 2 I_n J (Gram) + 2 R_n J (TTM) + 10/3 I_n^3 (eigenvectors).
+static double step_flops(const int64_t *dims, const int64_t *ranks, const int64_t *cur, int N, int n) {
+  double j = 1.0;
+  for (int m = 0; m < N; ++m) j *= (double)cur[m];
+  return 2.0 * (double)dims[n] * j + 2.0 * (double)ranks[n] * j + 10.0 / 3.0 * std::pow((double)dims[n], 3.0);
+}
+
+static double order_flops(const int64_t *dims, const int64_t *ranks, int N, const int *order) {
+  int64_t cur[TUCKER_MAX_MODES];
+  for (int m = 0; m < N; ++m) cur[m] = dims[m];
+  double total = 0.0;
+  for (int k = 0; k < N; ++k) {
+    total += step_flops(dims, ranks, cur, N, order[k]);
+    cur[order[k]] = ranks[order[k]];
+  }
+  return total;
 }
 
 static int check_result(const tucker_result *r) {
@@ -684,6 +823,123 @@ int tucker_reconstruct(const tucker_result *r, double *Xhat, void *stream) {
   if (st != TUCKER_OK) return st;
   TK_CUDA(cudaStreamSynchronize(s));
   prof.flush();
+  return TUCKER_OK;
+}
+
+int tucker_reconstruct_sub(const tucker_result *r, const int64_t *lo, const int64_t *hi, double *Xsub,
+                           void *stream) {
+  g_err[0] = 0;
+  TK_CHECK(check_result(r));
+  if (!Xsub || !lo || !hi) {
+    set_error("Xsub, lo and hi must be non-null");
+    return TUCKER_EINVAL;
+  }
+  for (int n = 0; n < r->N; ++n)
+    if (lo[n] < 0 || hi[n] <= lo[n] || hi[n] > r->dims[n]) {
+      set_error("mode %d: need 0 <= lo < hi <= %lld (got %lld, %lld)", n, (long long)r->dims[n], (long long)lo[n],
+                (long long)hi[n]);
+      return TUCKER_EINVAL;
+    }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  Prof prof(s);
+  DevBuf hold;
+  const double *res = nullptr;
+  int64_t cur[TUCKER_MAX_MODES];
+  int st = expand_modes(r, -1, Xsub, hold, &res, cur, dev, s, &prof, lo, hi);
+  if (st != TUCKER_OK) return st;
+  TK_CUDA(cudaStreamSynchronize(s));
+  prof.flush();
+  return TUCKER_OK;
+}
+
+int tucker_hooi(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, int max_iters, double tol,
+                tucker_precision prec, void *stream, tucker_result *out, int *iters, double *fit) {
+  g_err[0] = 0;
+  if (!out || !iters || max_iters < 0 || !(tol >= 0.0)) {
+    set_error("tucker_hooi: out and iters must be non-null, max_iters >= 0 and tol >= 0");
+    return TUCKER_EINVAL;
+  }
+  *iters = 0;
+  TK_CHECK(tucker_sthosvd(X, dt, dims, N, eps, nullptr, prec, stream, out));
+  const int st = hooi_iterate(X, dt, max_iters, tol, prec, static_cast<cudaStream_t>(stream), out, iters, fit);
+  if (st != TUCKER_OK) tucker_result_free(out);
+  return st;
+}
+
+int tucker_order_flops(const int64_t *dims, const int64_t *ranks, int N, const int *order, double *flops) {
+  g_err[0] = 0;
+  int ord[TUCKER_MAX_MODES];
+  if (!ranks || !flops) {
+    set_error("tucker_order_flops: ranks and flops must be non-null");
+    return TUCKER_EINVAL;
+  }
+  TK_CHECK(check_dims(dims, N));
+  TK_CHECK(check_order(order, N, ord));
+  for (int n = 0; n < N; ++n)
+    if (ranks[n] < 1 || ranks[n] > dims[n]) {
+      set_error("rank %d out of [1, I_n]", n);
+      return TUCKER_EINVAL;
+    }
+  *flops = order_flops(dims, ranks, N, ord);
+  return TUCKER_OK;
+}
+
+int tucker_mode_order(const int64_t *dims, const int64_t *ranks, int N, int rule, int *order) {
+  g_err[0] = 0;
+  if (!ranks || !order) {
+    set_error("tucker_mode_order: ranks and order must be non-null");
+    return TUCKER_EINVAL;
+  }
+  TK_CHECK(check_dims(dims, N));
+  for (int n = 0; n < N; ++n)
+    if (ranks[n] < 1 || ranks[n] > dims[n]) {
+      set_error("rank %d out of [1, I_n]", n);
+      return TUCKER_EINVAL;
+    }
+  if (rule == TUCKER_ORDER_EXHAUSTIVE) {
+    if (N > 9) {
+      set_error("exhaustive mode order search takes N <= 9 (got %d)", N);
+      return TUCKER_EINVAL;
+    }
+    int perm[TUCKER_MAX_MODES];
+    for (int n = 0; n < N; ++n) perm[n] = n;
+    double best = 0.0;
+    bool have = false;
+    do {  // lexicographic: the first of equal-cost orders wins
+      const double f = order_flops(dims, ranks, N, perm);
+      if (!have || f < best) {
+        best = f;
+        have = true;
+        memcpy(order, perm, sizeof(int) * N);
+      }
+    } while (std::next_permutation(perm, perm + N));
+    return TUCKER_OK;
+  }
+  if (rule != TUCKER_ORDER_GREEDY_FLOPS && rule != TUCKER_ORDER_GREEDY_RATIO) {
+    set_error("unknown mode order rule %d", rule);
+    return TUCKER_EINVAL;
+  }
+  int64_t cur[TUCKER_MAX_MODES];
+  bool used[TUCKER_MAX_MODES] = {};
+  for (int n = 0; n < N; ++n) cur[n] = dims[n];
+  for (int k = 0; k < N; ++k) {
+    int pick = -1;
+    double key = 0.0;
+    for (int n = 0; n < N; ++n) {
+      if (used[n]) continue;
+      const double v = rule == TUCKER_ORDER_GREEDY_FLOPS ? step_flops(dims, ranks, cur, N, n)
+                                                          : -(double)dims[n] / (double)ranks[n];
+      if (pick < 0 || v < key) {  // strict: ties keep the lower mode index
+        pick = n;
+        key = v;
+      }
+    }
+    used[pick] = true;
+    order[k] = pick;
+    cur[pick] = ranks[pick];
+  }
   return TUCKER_OK;
 }
 

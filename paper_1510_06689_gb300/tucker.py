@@ -23,11 +23,14 @@ PHASES = ("norm", "gram", "gram_reduce", "eig", "rank", "ttm", "scale", "ttm_l1"
 
 # Every symbol include/tucker.h declares (checked by the CPU test suite).
 EXPORTS = (
-    "tucker_sthosvd", "tucker_sthosvd_host", "tucker_reconstruct", "tucker_rel_error", "tucker_result_free",
+    "tucker_sthosvd", "tucker_sthosvd_host", "tucker_reconstruct", "tucker_reconstruct_sub", "tucker_rel_error",
+    "tucker_result_free",
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
-    "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split",
+    "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
+    "tucker_mode_order",
 )
+ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
 
 
 class TuckerError(RuntimeError):
@@ -81,6 +84,10 @@ def load(path=LIB_PATH):
         "tucker_sthosvd": (i32, [vp, i32, pi64, i32, dbl, pi32, i32, vp, pres]),
         "tucker_sthosvd_host": (i32, [vp, i32, pi64, i32, dbl, pi32, i32, vp, pres]),
         "tucker_reconstruct": (i32, [pres, vp, vp]),
+        "tucker_reconstruct_sub": (i32, [pres, pi64, pi64, vp, vp]),
+        "tucker_hooi": (i32, [vp, i32, pi64, i32, dbl, i32, dbl, i32, vp, pres, pi32, pdbl]),
+        "tucker_order_flops": (i32, [pi64, pi64, i32, pi32, pdbl]),
+        "tucker_mode_order": (i32, [pi64, pi64, i32, i32, pi32]),
         "tucker_rel_error": (i32, [vp, i32, pres, pdbl, vp]),
         "tucker_result_free": (None, [pres]),
         "tucker_norm2": (i32, [vp, i32, i64, pdbl, vp]),
@@ -251,6 +258,55 @@ def reconstruct(result, out=None, stream=None):
         out = torch.empty(n, dtype=torch.float64, device="cuda")
     _check(lib.tucker_reconstruct(ctypes.byref(result.raw), _dev_ptr(out, "out"), _stream(stream)))
     return out
+
+
+def hooi(x, dims, eps, max_iters=10, tol=0.0, precision="fp64", stream=None):
+    """Algorithm 2 (HOOI) from Algorithm 1: returns (Result, iterations, fit history)."""
+    lib = load()
+    dims, cd = _dims_arg(dims)
+    if x.numel() != math.prod(dims):
+        raise ValueError("x must hold prod(dims) elements")
+    raw = _Result()
+    iters = ctypes.c_int(0)
+    fit = (ctypes.c_double * (int(max_iters) + 1))()
+    _check(lib.tucker_hooi(_dev_ptr(x, "x"), _dtype_code(x), cd, len(dims), float(eps), int(max_iters), float(tol),
+                           PREC[precision], _stream(stream), ctypes.byref(raw), ctypes.byref(iters), fit))
+    return Result(raw), iters.value, list(fit[: iters.value + 1])
+
+
+def order_flops(dims, ranks, order=None):
+    """Flops of Algorithm 1 in a mode order (host-only cost model)."""
+    lib = load()
+    n = len(dims)
+    cd, cr = (ctypes.c_int64 * n)(*dims), (ctypes.c_int64 * n)(*ranks)
+    out = ctypes.c_double()
+    _check(lib.tucker_order_flops(cd, cr, n, _order_arg(order, n), ctypes.byref(out)))
+    return out.value
+
+
+def mode_order(dims, ranks, rule="flops"):
+    """A mode order by a heuristic of the paper ("flops", "ratio") or exhaustive search."""
+    lib = load()
+    n = len(dims)
+    cd, cr = (ctypes.c_int64 * n)(*dims), (ctypes.c_int64 * n)(*ranks)
+    out = (ctypes.c_int * n)()
+    _check(lib.tucker_mode_order(cd, cr, n, ORDER_RULES[rule], out))
+    return list(out)
+
+
+def reconstruct_sub(result, lo, hi, out=None, stream=None):
+    """X~[lo_1:hi_1, ..., lo_N:hi_N] (natural layout) from row subsets of the factors."""
+    lib = load()
+    lo = [int(v) for v in lo]
+    hi = [int(v) for v in hi]
+    if len(lo) != len(result.dims) or len(hi) != len(result.dims):
+        raise ValueError("lo and hi need one index per mode")
+    n = math.prod(max(h - l, 0) for l, h in zip(lo, hi))
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    clo, chi = (ctypes.c_int64 * len(lo))(*lo), (ctypes.c_int64 * len(hi))(*hi)
+    _check(lib.tucker_reconstruct_sub(ctypes.byref(result.raw), clo, chi, _dev_ptr(out, "out"), _stream(stream)))
+    return out[:n]
 
 
 def rel_error(x, result, stream=None):

@@ -1,16 +1,16 @@
 """Seeded synthetic inputs for the ST-HOSVD tests and benchmarks.
 
 This module only *builds inputs*: a dense tensor in Tucker form plus
-Gaussian noise, shaped like the combustion workloads of Sec. 6 (space x
+Gaussian noise, shaped like the combustion workloads of Sec. 7 (space x
 space x space x variables x time, per-variable normalised so entries are
-roughly N(0,1) scale, Sec. 6.1).  It holds none of the compression method's
+roughly N(0,1) scale, Sec. 7.1).  It holds none of the compression method's
 arithmetic: no Gram matrices, eigensolves, rank cuts or truncations.  Both
 the CUDA path and the CPU oracle consume the arrays it returns; neither
 imports the other.
 
 Layout convention (used everywhere in this repository): a tensor of
 dimensions (I_1, ..., I_N) is stored flat in *natural layout*, first index
-fastest (the column-major mode-1 unfolding of Sec. 3.1).  In numpy that is
+fastest (the column-major mode-1 unfolding of Sec. 4.1).  In numpy that is
 ``X.ravel(order="F")``; in torch it is a contiguous tensor whose shape is the
 reversed dimension tuple.
 

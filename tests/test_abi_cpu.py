@@ -104,3 +104,50 @@ def test_binding_fails_loudly_without_library(tmp_path):
             tucker.load(str(tmp_path / "missing.so"))
     finally:
         tucker._lib = saved
+
+
+def test_mode_order_and_flops_match_the_oracle(lib):
+    """Host-only entry points of the mode-order heuristics (Sec. 8.3) against the oracle."""
+    import numpy as np
+
+    from oracle import st_hosvd as osth
+    from paper_1510_06689_gb300 import tucker
+
+    rng = np.random.default_rng(0)
+    cases = [((25, 250, 250, 250), (10, 10, 100, 100)), ((128, 128, 128, 48, 32), (40, 40, 40, 20, 10)),
+             ((4, 6), (2, 3)), ((7,), (3,))]
+    for _ in range(20):
+        n = int(rng.integers(2, 7))
+        dims = tuple(int(d) for d in rng.integers(2, 300, n))
+        ranks = tuple(int(rng.integers(1, d + 1)) for d in dims)
+        cases.append((dims, ranks))
+    for dims, ranks in cases:
+        for rule in ("flops", "ratio"):
+            assert tucker.mode_order(dims, ranks, rule) == osth.greedy_order(dims, ranks, rule), (dims, ranks, rule)
+        assert tucker.mode_order(dims, ranks, "exhaustive") == osth.best_order(dims, ranks)
+        for order in (None, tucker.mode_order(dims, ranks, "ratio")):
+            ref = osth.order_flops(dims, ranks, list(range(len(dims))) if order is None else order)
+            assert tucker.order_flops(dims, ranks, order) == pytest.approx(ref, rel=1e-12)
+
+
+def test_hooi_subtensor_and_order_arguments_rejected_on_host(lib):
+    from paper_1510_06689_gb300 import tucker
+
+    dims = (ctypes.c_int64 * 3)(4, 5, 6)
+    ranks = (ctypes.c_int64 * 3)(2, 6, 3)  # rank 6 > I_2 = 5
+    order = (ctypes.c_int * 3)()
+    flops = ctypes.c_double()
+    assert lib.tucker_mode_order(dims, ranks, 3, 0, order) == -1
+    good = (ctypes.c_int64 * 3)(2, 2, 3)
+    assert lib.tucker_mode_order(dims, good, 3, 7, order) == -1  # unknown rule
+    assert lib.tucker_mode_order(dims, good, 3, 0, None) == -1
+    bad_order = (ctypes.c_int * 3)(0, 0, 2)
+    assert lib.tucker_order_flops(dims, good, 3, bad_order, ctypes.byref(flops)) == -1
+    res = tucker._Result()
+    iters = ctypes.c_int()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    assert lib.tucker_hooi(fake, 0, dims, 3, 1e-3, -1, 0.0, 0, None, ctypes.byref(res), ctypes.byref(iters), None) == -1
+    assert lib.tucker_hooi(fake, 0, dims, 3, 1e-3, 2, float("nan"), 0, None, ctypes.byref(res), ctypes.byref(iters),
+                           None) == -1
+    lo = (ctypes.c_int64 * 3)(0, 0, 0)
+    assert lib.tucker_reconstruct_sub(ctypes.byref(res), lo, lo, fake, None) == -1  # empty result

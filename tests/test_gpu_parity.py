@@ -365,9 +365,56 @@ def test_reconstruct_matches_oracle(gpu_lib):
     xr = gpu_lib.reconstruct(res).cpu().numpy()
     xr_ref = oracle.reconstruct(res.core().cpu().numpy(), res.ranks, [f.cpu().numpy() for f in res.factors()])
     assert np.abs(xr - xr_ref).max() <= 1e-13 * np.abs(x).max()
-    # Pythagoras: ||X - X~||^2 = sum of discarded tails (Sec. 6.2 bound, tight for ST-HOSVD)
+    # Pythagoras: ||X - X~||^2 = sum of discarded tails (Sec. 7.2 bound, tight for ST-HOSVD)
     err2 = float(((x - xr) ** 2).sum())
     assert err2 == pytest.approx(sum(res.tails), rel=1e-8)
+
+
+def test_reconstruct_sub_matches_oracle_and_full(gpu_lib):
+    """Subtensors from row subsets of the factors (Sec. 2.3)."""
+    dims, ranks = (21, 19, 17, 5), (4, 6, 3, 2)
+    x = tucker_tensor_np(dims, ranks, seed=8, noise=1e-2)
+    res = gpu_lib.sthosvd(dev(x), dims, 5e-2)
+    full = gpu_lib.reconstruct(res).cpu().numpy().reshape(dims, order="F")
+    core, facs = res.core().cpu().numpy(), [f.cpu().numpy() for f in res.factors()]
+    for lo, hi in [((0, 0, 0, 0), dims), ((3, 0, 5, 1), (9, 19, 6, 4)), ((20, 18, 16, 4), dims), ((0, 2, 0, 0), (21, 3, 17, 5))]:
+        sub = gpu_lib.reconstruct_sub(res, lo, hi).cpu().numpy()
+        ref = oracle.reconstruct_sub(core, res.ranks, facs, lo, hi)
+        assert np.abs(sub - ref).max() <= 1e-13 * np.abs(x).max()
+        block = full[tuple(slice(a, b) for a, b in zip(lo, hi))].ravel(order="F")
+        assert np.abs(sub - block).max() <= 1e-13 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
+def test_hooi_matches_oracle(gpu_lib, precision):
+    """Algorithm 2: same ranks, the same fit history within the path's tolerance,
+    and factors spanning the oracle's subspaces (where they are separated)."""
+    dims, ranks = (24, 20, 18, 10), (5, 4, 4, 3)
+    x = tucker_tensor_np(dims, ranks, seed=12, noise=0.2)
+    eps = 0.15
+    ref = oracle.hooi(x, dims, eps, max_iters=6, tol=0.0)
+    res, iters, fit = gpu_lib.hooi(dev(x), dims, eps, max_iters=6, tol=0.0, precision=precision)
+    assert res.ranks == ref["ranks"]
+    nx2 = ref["norm2"]
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    assert len(fit) == iters + 1
+    for a, b in zip(fit, ref["history"]):
+        assert abs(a - b) <= tol * nx2
+    assert all(b <= a + tol * nx2 for a, b in zip(fit, fit[1:]))
+    x_hat = gpu_lib.reconstruct(res).cpu().numpy()
+    assert abs(float(((x - x_hat) ** 2).sum()) - fit[-1]) <= max(tol, 1e-9) * nx2
+    for n in range(len(dims)):
+        s = principal_sines(res.factor(n).cpu().numpy(), ref["factors"][n])
+        assert s.max() < (1e-6 if precision == "fp64" else 1e-3)
+
+
+def test_hooi_zero_iterations_is_sthosvd(gpu_lib):
+    dims, ranks = (16, 12, 10), (3, 3, 2)
+    x = dev(tucker_tensor_np(dims, ranks, seed=2, noise=1e-2))
+    a = gpu_lib.sthosvd(x, dims, 5e-2)
+    b, iters, fit = gpu_lib.hooi(x, dims, 5e-2, max_iters=0)
+    assert iters == 0 and len(fit) == 1 and b.ranks == a.ranks
+    assert np.array_equal(a.core().cpu().numpy(), b.core().cpu().numpy())
 
 
 def test_host_entry_point(gpu_lib):

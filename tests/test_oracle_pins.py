@@ -346,6 +346,96 @@ def test_compression_ratio_table2():
 
 
 # ----------------------------------------------------------------------------
+# partial reconstruction (Sec. 2.3), HOOI (Algorithm 2), mode-order cost model
+# ----------------------------------------------------------------------------
+
+def test_subtensor_is_the_slice_of_the_full_reconstruction():
+    """Row subsets of the factors give exactly that block of X~ (Sec. 2.3)."""
+    dims, ranks = (7, 6, 5, 4), (3, 2, 4, 2)
+    x = tucker_tensor_np(dims, ranks, seed=5, noise=1e-2)
+    res = oracle.sthosvd(x, dims, 0.05)
+    full = osth.as_tensor(oracle.reconstruct(res["core"], res["ranks"], res["factors"]), dims)
+    for lo, hi in [((0, 0, 0, 0), dims), ((2, 1, 3, 0), (5, 6, 4, 3)), ((6, 5, 4, 3), (7, 6, 5, 4))]:
+        sub = oracle.reconstruct_sub(res["core"], res["ranks"], res["factors"], lo, hi)
+        block = full[tuple(slice(a, b) for a, b in zip(lo, hi))]
+        assert np.allclose(sub, np.asarray(block).ravel(order="F"), rtol=0, atol=1e-13)
+
+
+def _top_subspace_angle(u, m, r):
+    """sin of the largest principal angle between span(u) and the top-r left singular subspace of m."""
+    w = np.linalg.svd(m, full_matrices=False)[0][:, :r]
+    return float(np.linalg.norm(w - u @ (u.T @ w), 2))
+
+
+def test_hooi_exact_rank_returns_sthosvd():
+    dims, ranks = (6, 5, 7), (2, 3, 2)
+    x = tucker_tensor_np(dims, ranks, seed=9, noise=0.0)
+    h = oracle.hooi(x, dims, 1e-6, max_iters=3)
+    assert h["ranks"] == ranks
+    assert h["history"][-1] <= 1e-12 * h["norm2"]
+    x_hat = oracle.reconstruct(h["core"], h["ranks"], h["factors"])
+    assert np.linalg.norm(x_hat - x) <= 1e-12 * math.sqrt(h["norm2"])
+
+
+def test_hooi_matrix_case_keeps_the_eckart_young_optimum():
+    """N = 2: ST-HOSVD already gives the truncated SVD, HOOI cannot improve it."""
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((9, 7))
+    h = oracle.hooi(a.ravel(order="F"), (9, 7), 0.3, max_iters=4)
+    r = h["ranks"][0]
+    sv = np.linalg.svd(a, compute_uv=False)
+    tail = float(np.sum(sv[r:] ** 2))
+    assert h["ranks"][1] == r
+    for f in h["history"]:
+        assert abs(f - tail) <= 1e-10 * h["norm2"]
+
+
+def test_hooi_noisy_monotone_stationary_and_pythagorean():
+    dims, ranks = (8, 7, 6), (3, 3, 2)
+    x = tucker_tensor_np(dims, ranks, seed=3, noise=0.3)
+    st = oracle.sthosvd(x, dims, 0.2)
+    h = oracle.hooi(x, dims, 0.2, max_iters=200, tol=0.0)
+    hist = h["history"]
+    assert h["ranks"] == st["ranks"]
+    assert all(b <= a + 1e-12 * h["norm2"] for a, b in zip(hist, hist[1:]))  # Algorithm 2 never increases the fit
+    assert hist[-1] <= hist[0]
+    # the fit is ||X - X~||^2 (orthogonal projections)
+    x_hat = oracle.reconstruct(h["core"], h["ranks"], h["factors"])
+    assert abs(float(np.sum((x - x_hat) ** 2)) - hist[-1]) <= 1e-10 * h["norm2"]
+    # at the fixed point each U_n spans the top R_n left singular vectors of (X x {U_m^T}_{m != n})_(n)
+    xt = osth.as_tensor(x, dims)
+    for n in range(3):
+        y = xt
+        for m in range(3):
+            if m != n:
+                y = osth.ttm(y, m, h["factors"][m].T)
+        assert _top_subspace_angle(h["factors"][n], osth.unfold(y, n), h["ranks"][n]) < 1e-6
+        assert np.allclose(h["factors"][n].T @ h["factors"][n], np.eye(h["ranks"][n]), atol=1e-13)
+
+
+def test_order_flops_hand_count():
+    # dims (4, 6), ranks (2, 3).  Order (0, 1): J = 24 then 12:
+    #   2*4*24 + 2*2*24 + 10/3*64 = 501.33..., then 2*6*12 + 2*3*12 + 10/3*216 = 936
+    assert osth.order_flops((4, 6), (2, 3), (0, 1)) == pytest.approx(192 + 96 + 640 / 3 + 144 + 72 + 720)
+    # order (1, 0): 2*6*24 + 2*3*24 + 720, then 2*4*12 + 2*2*12 + 640/3
+    assert osth.order_flops((4, 6), (2, 3), (1, 0)) == pytest.approx(288 + 144 + 720 + 96 + 48 + 640 / 3)
+    assert osth.best_order((4, 6), (2, 3)) == [0, 1]
+
+
+def test_order_heuristics_on_the_papers_mode_order_problem():
+    # Sec. 8.3: 25 x 250 x 250 x 250 with core 10 x 10 x 100 x 100; the second
+    # mode has by far the largest compression ratio I_n / R_n = 25
+    dims, ranks = (25, 250, 250, 250), (10, 10, 100, 100)
+    assert osth.greedy_order(dims, ranks, "ratio") == [1, 0, 2, 3]
+    # fewest flops in the first step: mode 0 (smallest I_n + R_n), as the paper says
+    # that heuristic starts there
+    assert osth.greedy_order(dims, ranks, "flops")[0] == 0
+    best = osth.best_order(dims, ranks)
+    costs = {p: osth.order_flops(dims, ranks, p) for p in itertools.permutations(range(4))}
+    assert osth.order_flops(dims, ranks, best) == min(costs.values())
+
+
+# ----------------------------------------------------------------------------
 # planted mistakes: each must break at least one pin above
 # ----------------------------------------------------------------------------
 
@@ -362,6 +452,10 @@ def _pins_pass():
         lambda: test_permutation_equivariance(),
         lambda: test_rank_rule_edges(),
         lambda: test_unfold_matches_index_map((2, 3, 4, 5)),
+        lambda: test_subtensor_is_the_slice_of_the_full_reconstruction(),
+        lambda: test_hooi_noisy_monotone_stationary_and_pythagorean(),
+        lambda: test_order_flops_hand_count(),
+        lambda: test_order_heuristics_on_the_papers_mode_order_problem(),
     ]
     for c in checks:
         try:
@@ -437,7 +531,38 @@ def _mut_current_norm_threshold(x_flat, dims, eps, order=None):
             "order": tuple(order), "dims": dims}
 
 
+def _mut_sub_ignores_lo(core_flat, ranks, factors, lo, hi, _orig=osth.reconstruct_sub):
+    return _orig(core_flat, ranks, factors, [0] * len(lo), [b - a for a, b in zip(lo, hi)])
+
+
+def _mut_hooi_no_update(x_flat, dims, eps, max_iters=10, tol=0.0, order=None):
+    res = osth.sthosvd(x_flat, dims, eps, order)
+    core = osth.as_tensor(res["core"], res["ranks"])
+    out = dict(res)
+    out["history"] = [res["norm2"] - osth.norm2(core)] * 2
+    out["iters"] = 1
+    return out
+
+
+def _mut_ttm_flops_with_i(dims, ranks, order):
+    cur = [int(d) for d in dims]
+    total = 0.0
+    for n in order:
+        j = math.prod(cur)
+        total += 4.0 * dims[n] * j + 10.0 / 3.0 * float(dims[n]) ** 3
+        cur[n] = int(ranks[n])
+    return total
+
+
+def _mut_greedy_max(dims, ranks, rule, _orig=osth.greedy_order):
+    return _orig(dims, ranks, rule)[::-1]
+
+
 MUTATIONS = {
+    "subtensor_ignores_lo": ("reconstruct_sub", _mut_sub_ignores_lo),
+    "hooi_never_updates": ("hooi", _mut_hooi_no_update),
+    "ttm_flops_with_I": ("order_flops", _mut_ttm_flops_with_i),
+    "greedy_reversed": ("greedy_order", _mut_greedy_max),
     "threshold_without_N": ("sthosvd", _mut_threshold_without_n),
     "unfold_column_order": ("unfold", _mut_unfold_c_order),
     "fold_column_order": ("fold", _mut_fold_c_order),
