@@ -87,6 +87,7 @@ def parse_args():
                         "result when its ranks and error equal the float64 ones")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-next", action="store_true", help="skip the HOOI / subtensor / mode-order measurements")
     return p.parse_args()
 
 
@@ -355,6 +356,60 @@ def roofline_of(t, steps, precision):
     return rows[0], rows
 
 
+def measure_next_rows(tucker, x, w, eps, precision, base_ms, stream):
+    """The scope table's next rows on the same tensor: one HOOI iteration (Algorithm 2),
+    a subtensor reconstruction (Sec. 2.3) and the mode-order heuristics (Sec. 8.3)."""
+    import torch
+
+    dims = w.dims
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    out = {}
+    # HOOI: Algorithm 1 plus one iteration, minus Algorithm 1 alone
+    ms1, (res, iters, fit) = timed(lambda: tucker.hooi(x, dims, eps, max_iters=1, tol=0.0, precision=precision),
+                                   reps=2)
+    ranks = res.ranks
+    res.free()
+    out["hooi"] = {"iteration_ms": round(ms1 - base_ms, 3), "with_sthosvd_ms": round(ms1, 3),
+                   "fit_relative": [f / fit[0] if fit[0] else 0.0 for f in fit],
+                   "note": "one iteration: per mode, the mode products from X of every other mode, the Gram and "
+                           "eigenvectors; fit = ||X||^2 - ||G||^2 (Algorithm 2)"}
+    # subtensor: the first variable at 4 time steps (mode 4 rows 0..0, mode 5 rows 0..3)
+    res = tucker.sthosvd(x, dims, eps, precision=precision)
+    lo = [0] * len(dims)
+    hi = list(dims[:-2]) + [1, min(4, dims[-1])]
+    nsub = math.prod(h - l for l, h in zip(lo, hi))
+    buf = torch.empty(nsub, dtype=torch.float64, device="cuda")
+    ms_sub, _ = timed(lambda: tucker.reconstruct_sub(res, lo, hi, out=buf))
+    res.free()
+    out["reconstruct_sub"] = {"lo": lo, "hi": hi, "ms": round(ms_sub, 4),
+                              "output_gb_s": round(nsub * 8 / (ms_sub / 1e3) / 1e9, 2)}
+    # mode orders by the cost model with the measured ranks; the fastest by flops is timed
+    orders = {rule: tucker.mode_order(dims, ranks, rule) for rule in ("flops", "ratio", "exhaustive")}
+    given = list(range(len(dims)))
+    mo = {"given": {"order": given, "gflop": round(tucker.order_flops(dims, ranks, given) / 1e9, 3)}}
+    for rule, o in orders.items():
+        mo[rule] = {"order": o, "gflop": round(tucker.order_flops(dims, ranks, o) / 1e9, 3)}
+    ms_best, r = timed(lambda: tucker.sthosvd(x, dims, eps, mode_order=orders["exhaustive"], precision=precision),
+                       reps=2)
+    mo["exhaustive"]["ms_per_step"] = round(ms_best, 3)
+    mo["exhaustive"]["ranks"] = list(r.ranks)
+    r.free()
+    mo["given"]["ms_per_step"] = round(base_ms, 3)
+    out["mode_order"] = mo
+    return out
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -422,6 +477,8 @@ def main():
         "gpu_launches": t["launches"], "clocks": t["clocks"],
     }
     line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
+    if not args.no_next and world == 1:
+        line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, stream)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     xh = None
