@@ -356,7 +356,7 @@ def roofline_of(t, steps, precision):
     return rows[0], rows
 
 
-def measure_next_rows(tucker, x, w, eps, precision, base_ms, stream):
+def measure_next_rows(tucker, x, w, eps, precision, base_ms, base_rel, stream):
     """The scope table's next rows on the same tensor: one HOOI iteration (Algorithm 2),
     a subtensor reconstruction (Sec. 2.3) and the mode-order heuristics (Sec. 8.3)."""
     import torch
@@ -379,11 +379,13 @@ def measure_next_rows(tucker, x, w, eps, precision, base_ms, stream):
     ms1, (res, iters, fit) = timed(lambda: tucker.hooi(x, dims, eps, max_iters=1, tol=0.0, precision=precision),
                                    reps=2)
     ranks = res.ranks
+    rel_after = tucker.rel_error(x, res)
     res.free()
     out["hooi"] = {"iteration_ms": round(ms1 - base_ms, 3), "with_sthosvd_ms": round(ms1, 3),
-                   "fit_relative": [f / fit[0] if fit[0] else 0.0 for f in fit],
-                   "note": "one iteration: per mode, the mode products from X of every other mode, the Gram and "
-                           "eigenvectors; fit = ||X||^2 - ||G||^2 (Algorithm 2)"}
+                   "rel_error_sthosvd": base_rel, "rel_error_after_one_iteration": rel_after,
+                   "note": "one iteration of Algorithm 2: per mode, the mode products from X of every other "
+                           "mode, the Gram and eigenvectors; errors from the explicit difference (the fit "
+                           "||X||^2 - ||G||^2 cancels at this eps)"}
     # subtensor: the first variable at 4 time steps (mode 4 rows 0..0, mode 5 rows 0..3)
     res = tucker.sthosvd(x, dims, eps, precision=precision)
     lo = [0] * len(dims)
@@ -478,7 +480,7 @@ def main():
     }
     line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
     if not args.no_next and world == 1:
-        line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, stream)
+        line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, t["rel"], stream)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     xh = None

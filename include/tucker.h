@@ -162,7 +162,10 @@ TUCKER_API int tucker_reconstruct_sub(const tucker_result *r, const int64_t *lo,
  *              starting ST-HOSVD.
  *   iters      host int: the iterations run.
  *   fit        NULL or a host array of max_iters + 1 doubles: ||X||^2 - ||G||^2
- *              at the start and after each iteration.
+ *              at the start and after each iteration (a difference of nearly
+ *              equal numbers: meaningful while it is well above the rounding
+ *              of ||G||^2, ~1e-16 ||X||^2 in float64 and ~1e-8 ||X||^2 with
+ *              the split-precision mode products).
  * One iteration: for n = 1..N, Y = X x {U_m^T}_{m != n} with the factors
  * updated so far, U_n = the leading R_n eigenvectors of Y_(n) Y_(n)^T; then
  * G = Y x_N U_N^T.  With prec = TUCKER_PREC_BF16X4 the mode products run on

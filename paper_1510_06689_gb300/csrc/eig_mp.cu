@@ -58,7 +58,7 @@ constexpr int kJ32MaxSweeps = 40;
 constexpr int kMaxDepth = 5;
 constexpr double kU = DBL_EPSILON / 2;
 constexpr double kClusterC = 64.0;
-constexpr int kRefineSteps = 3;
+constexpr int kRefineSteps = 2;
 constexpr int kPolishSteps = 2;
 
 // ---------------------------------------------------------------------------
