@@ -19,7 +19,8 @@
 //        correction X <- X + X E, where
 //          E_ij = (s_ij + l_j r_ij) / (l_j - l_i)   i, j in different clusters
 //          E_ij = r_ij / 2                          i, j in the same cluster,
-//        converge quadratically for separated eigenvalues.  Clusters are
+//        converge quadratically for separated eigenvalues (two steps from
+//        the float32 stage's ~1e-7).  Clusters are
 //        fixed once per level from the first step: sorted approximations
 //        whose neighbouring gaps are at most
 //          delta = 64 (||off(S)||_F + ||A||_F ||R||_F + m u ||A_top||_F),
@@ -28,7 +29,7 @@
 //        solved recursively and rotated in (X_c <- X_c Q); a level whose A is
 //        a multiple of I up to the float64 noise of the top problem keeps
 //        X = I.  Graded spectra thus descend ~7 decimal orders per level.
-//     4. Two more refinement steps with the same clusters (orthonormality,
+//     4. One more refinement step with the same clusters (orthonormality,
 //        and rotations between clusters, to float64 accuracy).
 //   Finally the eigenvalues are the Rayleigh quotients, sorted descending
 //   (ties by index) with the sign rule of the Jacobi path, and the result is
@@ -59,7 +60,7 @@ constexpr int kMaxDepth = 5;
 constexpr double kU = DBL_EPSILON / 2;
 constexpr double kClusterC = 64.0;
 constexpr int kRefineSteps = 2;
-constexpr int kPolishSteps = 2;
+constexpr int kPolishSteps = 1;
 
 // ---------------------------------------------------------------------------
 // float32 parallel-order cyclic Jacobi on A / max|A| (one CTA).  S (full,
