@@ -51,9 +51,9 @@ TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9
                "ratio": (1.612648e9 + 4.068e6) / 1.6106e9,
                "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB); the tiled mode-2 launch (L = 40) "
                            "measured 1.031"},
-           ("k_ttm_split_l1", "ebc65708341fb159"): {"ratio": (1.611258e9 + 477.05e6) / 2.1140e9,
+           ("k_ttm_split_l1", "11c279836b4f9651"): {"ratio": (1.611258e9 + 472.80e6) / 2.1140e9,
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_tma", "ebc65708341fb159"): {"ratio": (0.505518e9 + 129.19e6) / (0.50332e9 + 0.157286e9),
+           ("k_ttm_split_tma", "11c279836b4f9651"): {"ratio": (0.505569e9 + 131.04e6) / (0.50332e9 + 0.157286e9),
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB)"}}
 HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
