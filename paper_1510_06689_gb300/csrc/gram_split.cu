@@ -821,6 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   __shared__ int ref[kRows];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
+  __shared__ int n_issued;  // copies issued so far (thread 0, then thread 32)
   // offsets from dsmem keep the shared address space visible (shared loads and stores)
   unsigned char *ring = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
   unsigned char *stages = ring + kRing * kRawBytes;
@@ -860,22 +861,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // chunk ch -> slot ch % kRing as the box at (row 0, column c_begin + 32 ch) (thread 0)
+  // chunk ch -> slot ch % kRing as the box at (row 0, column c_begin + 32 ch)
+  // (thread 0 for the first ring, then thread 32: the MMAs are thread 0's)
   auto issue_copy = [&](int ch) {
     const int slot = ch % kRing;
     const uint32_t bar = smem_addr(&raw_full[slot]);
     mbar_expect_tx(bar, (uint32_t)(kChunk * kRows * sizeof(T)));
-    if (kOct) {
-      const int64_t gch = c_begin / kChunk + ch, bb = gch / p.nL;
-      tma_load_4d(smem_addr(ring + slot * kRawBytes), &ymap, 0, 0, (int)(p.nl * (gch - bb * p.nL)), (int)(p.nb * bb),
-                  bar);
+    if (kOct) {  // chunk indices stay below 2^31 (the plan checks it): 32-bit division
+      const uint32_t gch = (uint32_t)(c_begin / kChunk) + (uint32_t)ch, nL = (uint32_t)p.nL, bb = gch / nL;
+      tma_load_4d(smem_addr(ring + slot * kRawBytes), &ymap, 0, 0, (int)((uint32_t)p.nl * (gch - bb * nL)),
+                  (int)((uint32_t)p.nb * bb), bar);
     } else {
       tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
     }
   };
-  int issued = 0;
-  if (tid == 0)
-    for (; issued < kRing && issued < nchunks; ++issued) issue_copy(issued);
+  if (tid == 0) {
+    int c = 0;
+    for (; c < kRing && c < nchunks; ++c) issue_copy(c);
+    n_issued = c;  // read on the error path after the barriers that follow
+  }
 
   const int row = tid & (kRows - 1), kg = tid >> 7;       // converter role
   const int q = warp & 3, cb = warp >> 2;                  // drain role: TMEM lanes 32 q.., columns 32 cb..
@@ -940,8 +944,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (stop) break;
+      if (tid == 32 && ch + kRing < nchunks) {  // slot u has been read by every thread
+        issue_copy(ch + kRing);
+        n_issued = ch + kRing + 1;
+      }
       if (tid == 0) {
-        if (issued < nchunks) issue_copy(issued++);  // slot u has been read by every thread
         fence_after();
         const uint32_t base = smem_addr(stages + (u & 1) * kStageBytes);
 #pragma unroll
@@ -975,6 +982,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   if (stop && tid == 0) {
     // let our own MMAs and bulk copies finish (bounded) before TMEM and shared memory go
     if (last_committed >= 0) mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)(last_committed >> 1) & 1u);
+    const int issued = n_issued;
     for (int c = max(0, issued - kRing); c < issued; ++c)
       mbar_wait(smem_addr(&raw_full[c % kRing]), (uint32_t)(c / kRing) & 1u);
   }
