@@ -8,7 +8,8 @@
 // SMs:
 //
 //   level(A):  (A symmetric m x m, float64)
-//     1. X = eigenvectors of A / max|A| in float32 (one CTA, shared memory;
+//     1. X = eigenvectors of A in float32, scaled by a power of two so that
+//        its largest magnitude is in [1/2, 1) (one CTA, shared memory;
 //        accurate to ~2^-24 max|A| / gap): Householder tridiagonalization,
 //        multisection, inverse iteration, orthonormalisation by Householder
 //        QR and back-transformation (k_eig32_tri), or with
@@ -223,7 +224,8 @@ size_t jacobi32_smem(int n) {
 }
 
 // ---------------------------------------------------------------------------
-// float32 tridiagonal eigensolver on A / max|A| (one CTA of kT32Threads),
+// float32 tridiagonal eigensolver on A scaled by a power of two (largest
+// magnitude in [1/2, 1); one CTA of kT32Threads),
 // the first stage of a level in place of the Jacobi sweeps: O(n^3) work once
 // instead of per sweep, every phase data-parallel over rows, columns or
 // eigenvalues, with 2-3 block barriers per reflector.
@@ -755,22 +757,41 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
   __shared__ float sc[4];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
-  // ---- load A / max|A| (upper triangle, mirrored)
-  float mx = 0.f;
-  for (int idx = tid; idx < n * n; idx += nt) mx = fmaxf(mx, (float)fabs(A[(idx % n) + (int64_t)lda * (idx / n)]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) red[warp] = mx;
+  // ---- load A * 2^-s (upper triangle, mirrored), s such that the largest
+  // magnitude lands in [1/2, 1): thread idx reads entry (r, c) = (idx % n,
+  // idx / n) for r <= c, consecutive threads down a column.  The float is
+  // built from the float64 bits in integer arithmetic (the exponent rebased,
+  // the significand truncated to 23 bits, entries 2^-126 below the largest
+  // flushed to zero), so the float64 pipe does no work here.
+  unsigned mhi = 0u;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    if (r <= c) mhi = max(mhi, (unsigned)(__double_as_longlong(A[r + (int64_t)lda * c]) >> 32) & 0x7FFFFFFFu);
+  }
+  mhi = __reduce_max_sync(0xffffffffu, mhi);
+  if (lane == 0) red[warp] = __uint_as_float(mhi);
   __syncthreads();
   if (tid == 0) {
-    float v = 0.f;
-    for (int w = 0; w < nw; ++w) v = fmaxf(v, red[w]);
-    sc[0] = v;
+    unsigned v = 0u;
+    for (int w = 0; w < nw; ++w) v = max(v, __float_as_uint(red[w]));
+    sc[0] = __uint_as_float(v);
   }
   __syncthreads();
-  const double inv = sc[0] > 0.f ? 1.0 / (double)sc[0] : 0.0;
-  for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) Af[i * ld + j] = (float)(A[min(i, j) + (int64_t)lda * max(i, j)] * inv);
+  const unsigned amax = __float_as_uint(sc[0]);
+  // exponent field e of a float64 maps to e - (emax - 126) of a float32
+  const int rebase = (int)(amax >> 20) - 126;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    if (r <= c) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(A[r + (int64_t)lda * c]);
+      const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b, mag = hi & 0x7FFFFFFFu;
+      const int x = max((int)mag - (rebase << 20), 0);
+      const unsigned f = (amax == 0u || mag == 0u) ? 0u : ((hi & 0x80000000u) | __funnelshift_l(lo, (unsigned)x, 3));
+      const float v = __uint_as_float(f);
+      Af[r * ld + c] = v;
+      Af[c * ld + r] = v;
+    }
+  }
   __syncthreads();
 
   // ---- 1. tridiagonalization, kNb columns a panel (LAPACK's latrd, lower):
