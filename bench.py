@@ -412,6 +412,34 @@ def measure_next_rows(tucker, x, w, eps, precision, base_ms, base_rel, stream):
     return out
 
 
+def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=32):
+    """The many-small-tensors workload: `count` 3-way tensors, dims uniform in
+    [16, 128], ranks in [4, 16], noise 1e-5, eps 1e-3 (one call of the batched
+    entry point, the tensors already on the device)."""
+    import torch
+
+    from synthetic import random_dims_ranks, tucker_tensor_torch
+
+    dims_list, ranks_list = random_dims_ranks(count, seed=0)
+    xs = [tucker_tensor_torch(d, r, seed=0, tensor=i, noise=1e-5, device="cuda")
+          for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
+    torch.cuda.synchronize()
+    nbytes = sum(x.numel() * 8 for x in xs)
+    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)  # warm-up
+    ok = sum(r.ranks == tuple(rk) for r, rk in zip(res, ranks_list))
+    del res
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    del res
+    return {"tensors": count, "input_gb": round(nbytes / 1e9, 3), "ms": round(ms, 2),
+            "input_gb_s": round(nbytes / (ms / 1e3) / 1e9, 2), "tensors_per_s": round(count / (ms / 1e3), 1),
+            "true_ranks_recovered": ok, "precision": precision, "workers": workers}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -481,6 +509,7 @@ def main():
     line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
     if not args.no_next and world == 1:
         line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, t["rel"], stream)
+        line["next_rows"]["batched"] = measure_batched(tucker, head, stream)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     xh = None

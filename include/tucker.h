@@ -176,6 +176,26 @@ TUCKER_API int tucker_hooi(const void *X, tucker_dtype dt, const int64_t *dims, 
                            double tol, tucker_precision prec, void *stream, tucker_result *out, int *iters,
                            double *fit);
 
+/*
+ * tucker_sthosvd_batched -- Algorithm 1 on `count` independent tensors (the
+ * many-small-tensors workload): each tensor's ST-HOSVD as tucker_sthosvd
+ * (identity mode order), the tensors spread over `workers` host threads, each
+ * driving its own stream, so that one tensor's per-mode synchronisation
+ * overlaps the others' kernels.
+ *   X        host array of `count` device pointers (type dt, natural layout).
+ *   dims     host array of count x N sizes: row i holds tensor i's I_1..I_N.
+ *   eps, prec  as for tucker_sthosvd, shared by all tensors.
+ *   workers  host threads (0: 8), at most 64.
+ *   stream   the workers start after the work already queued on it.
+ *   out      host array of `count` results, filled on success; on error all
+ *            are released and zeroed, and the first failing tensor's status
+ *            and message are returned.
+ * Returns when every result is ready.
+ */
+TUCKER_API int tucker_sthosvd_batched(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, int count,
+                                      double eps, tucker_precision prec, int workers, void *stream,
+                                      tucker_result *out);
+
 /* Mode-order rules for tucker_mode_order (Sec. 8.3). */
 typedef enum {
   TUCKER_ORDER_GREEDY_FLOPS = 0, /* at each step the mode whose step costs the fewest flops */

@@ -54,6 +54,23 @@ struct DeviceInfo {
 };
 int device_info(DeviceInfo *out);
 
+// The device's opt-in shared memory per block (cached per device).
+int smem_optin_bytes();
+
+// Lets `kernel` take as much dynamic shared memory as the device allows next
+// to its static shared memory.  Kernels get this fixed limit, never a
+// launch's own size: host threads running ST-HOSVDs of different shapes at
+// once would otherwise lower the limit between another thread's setting and
+// its launch.
+template <typename K>
+cudaError_t allow_max_smem(K kernel) {
+  cudaFuncAttributes a;
+  const cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin_bytes() - (int)a.sharedSizeBytes);
+}
+
 // ---------------------------------------------------------------------------
 // phase timing: CUDA events on the launching stream, resolved after the
 // caller's stream has been synchronised.

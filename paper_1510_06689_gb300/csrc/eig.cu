@@ -690,7 +690,7 @@ static int cluster_size_for_eig() {
 template <bool kL2>
 static bool dsm_cluster_ok(size_t dsmem) {
   if (cudaFuncSetAttribute(k_jacobi_dsm<kL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-      cudaFuncSetAttribute(k_jacobi_dsm<kL2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem) != cudaSuccess) {
+      allow_max_smem(k_jacobi_dsm<kL2>) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -783,7 +783,7 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
   double *ws = nullptr;
   if (J <= kSmemMaxJ) {
     smem = (size_t)(m * (m + 1) / 2 + m * m) * sizeof(double);
-    TK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_CUDA(allow_max_smem(k_jacobi));
   } else {
     ws = d_ws;
     if (!ws) {

@@ -1394,11 +1394,11 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   }();
   if (use_jacobi) {
     const size_t smem32 = jacobi32_smem(m);
-    TK_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    TK_CUDA(allow_max_smem(k_jacobi32));
     k_jacobi32<<<1, kJ32Threads, smem32, s>>>(A, lda, m, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr);
   } else {
     const size_t smemt = tri32_smem(m);
-    TK_CUDA(cudaFuncSetAttribute(k_eig32_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemt));
+    TK_CUDA(allow_max_smem(k_eig32_tri));
     k_eig32_tri<<<1, kT32Threads, smemt, s>>>(A, lda, m, tx0 + (size_t)m * m, m);
   }
   TK_LAUNCHED();

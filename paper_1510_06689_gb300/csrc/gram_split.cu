@@ -1107,7 +1107,7 @@ template <typename T, int kMode>
 int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &w, const DeviceInfo &dev,
                    cudaStream_t s) {
   (void)dev;
-  TK_CUDA(cudaFuncSetAttribute(k_gram_split<T, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  TK_CUDA(allow_max_smem(k_gram_split<T, kMode>));
   k_gram_split<T, kMode><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const T *>(y), L, p, w.table, w.refs,
                                                                 w.partials, w.err);
   TK_LAUNCHED();
@@ -1131,8 +1131,7 @@ int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cud
   const uint64_t strides[1] = {col_bytes};
   const uint32_t box[2] = {kRows, kChunk};
   if (!encode_tmap(&map, sizeof(T) == 8, y, 2, dims, strides, box)) return TUCKER_OK;
-  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kBulkSmemBytes));
+  TK_CUDA(allow_max_smem(k_gram_split_bulk<T, false>));
   k_gram_split_bulk<T, false><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
   TK_LAUNCHED();
   *ran = true;
@@ -1148,8 +1147,7 @@ int run_gram_split_oct(const void *y, int64_t L, const SplitPlan &p, const Split
   const uint64_t strides[3] = {(uint64_t)L * 8, 64, (uint64_t)L * p.J * 8};
   const uint32_t box[4] = {8, kRows, (uint32_t)p.nl, (uint32_t)p.nb};
   if (!encode_tmap(&map, true, y, 4, dims, strides, box, 64)) return TUCKER_OK;
-  TK_CUDA(cudaFuncSetAttribute(k_gram_split_bulk<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kBulkSmemBytes));
+  TK_CUDA(allow_max_smem(k_gram_split_bulk<double, true>));
   k_gram_split_bulk<double, true><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials,
                                                                             w.err);
   TK_LAUNCHED();
@@ -1219,18 +1217,15 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (async_exp) {
     constexpr size_t kExpSmem = (size_t)2 * 8 * 256 * 16;  // 2 stages x RS x NQ chunks (the same for both types)
     if (oct) {
-      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kExpSmem));
+      TK_CUDA(allow_max_smem(k_rowgroup_exp_async<double, true>));
       k_rowgroup_exp_async<double, true><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
           static_cast<const double *>(y), L, (int)J, p.K, p.nL, p.nl, B, w.table, w.gmax, d_colexp);
     } else if (f64) {
-      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kExpSmem));
+      TK_CUDA(allow_max_smem(k_rowgroup_exp_async<double, false>));
       k_rowgroup_exp_async<double, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
           static_cast<const double *>(y), L, (int)J, p.K, 1, 1, B, w.table, w.gmax, d_colexp);
     } else {
-      TK_CUDA(cudaFuncSetAttribute(k_rowgroup_exp_async<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kExpSmem));
+      TK_CUDA(allow_max_smem(k_rowgroup_exp_async<float, false>));
       k_rowgroup_exp_async<float, false><<<(unsigned)p.ngroups, 512, kExpSmem, s>>>(
           static_cast<const float *>(y), L, (int)J, p.K, 1, 1, B, w.table, w.gmax, d_colexp);
     }

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ 
 template <typename K>
 int occupancy(K kernel, int threads, size_t smem) {
   int occ = 1;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (allow_max_smem(kernel) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess)
     occ = 1;
   cudaGetLastError();
@@ -389,7 +389,7 @@ int set_smem(K kernel, size_t bytes, const DeviceInfo &dev) {
     set_error("kernel needs %zu bytes of shared memory, device allows %d", bytes, dev.smem_optin);
     return TUCKER_EUNSUPPORTED;
   }
-  TK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  TK_CUDA(allow_max_smem(kernel));
   return TUCKER_OK;
 }
 

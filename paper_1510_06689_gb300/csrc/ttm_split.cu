@@ -1063,7 +1063,7 @@ int run_ttm_tma(const CUtensorMap &map, const void *y, int64_t L, int64_t J, int
     TK_LAUNCHED();
     d_colexp = tmp;
   }
-  TK_CUDA(cudaFuncSetAttribute(k_ttm_split_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+  TK_CUDA(allow_max_smem(k_ttm_split_tma<T>));
   k_ttm_split_tma<T><<<p.grid, kTmThreads, p.smem, s>>>(map, U, p, d_colexp, z, d_err);
   TK_LAUNCHED();
   if (tmp) TK_CUDA(cudaFreeAsync(tmp, s));
@@ -1087,10 +1087,10 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
     if (q.parts > 0) {
       if (prof) prof->begin(TUCKER_PHASE_TTM_L1);
       if (dt == TUCKER_F64) {
-        TK_CUDA(cudaFuncSetAttribute(k_ttm_split_l1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem));
+        TK_CUDA(allow_max_smem(k_ttm_split_l1<double>));
         k_ttm_split_l1<double><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const double *>(y), U, q, z, d_err);
       } else {
-        TK_CUDA(cudaFuncSetAttribute(k_ttm_split_l1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q.smem));
+        TK_CUDA(allow_max_smem(k_ttm_split_l1<float>));
         k_ttm_split_l1<float><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const float *>(y), U, q, z, d_err);
       }
       TK_LAUNCHED();
@@ -1116,10 +1116,10 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
   const TtmSplit2Plan p = ttm_split2_plan(L, J, B, R, dev);
   if (prof) prof->begin(TUCKER_PHASE_TTM);
   if (dt == TUCKER_F64) {
-    TK_CUDA(cudaFuncSetAttribute(k_ttm_split2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    TK_CUDA(allow_max_smem(k_ttm_split2<double>));
     k_ttm_split2<double><<<p.grid, kThreads, p.smem, s>>>(static_cast<const double *>(y), L, B, U, p, z, d_err);
   } else {
-    TK_CUDA(cudaFuncSetAttribute(k_ttm_split2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    TK_CUDA(allow_max_smem(k_ttm_split2<float>));
     k_ttm_split2<float><<<p.grid, kThreads, p.smem, s>>>(static_cast<const float *>(y), L, B, U, p, z, d_err);
   }
   TK_LAUNCHED();

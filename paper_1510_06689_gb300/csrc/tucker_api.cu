@@ -25,6 +25,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -45,6 +47,18 @@ void set_error(const char *fmt, ...) {
 }
 
 int64_t bump_launches(int64_t n) { return g_launches.fetch_add(n) + n; }
+
+int smem_optin_bytes() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cache[dev].load();
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) v = 48 * 1024;
+    cache[dev].store(v);
+  }
+  return v;
+}
 
 int device_info(DeviceInfo *out) {
   static std::mutex mu;
@@ -866,6 +880,79 @@ int tucker_hooi(const void *X, tucker_dtype dt, const int64_t *dims, int N, doub
   const int st = hooi_iterate(X, dt, max_iters, tol, prec, static_cast<cudaStream_t>(stream), out, iters, fit);
   if (st != TUCKER_OK) tucker_result_free(out);
   return st;
+}
+
+int tucker_sthosvd_batched(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, int count, double eps,
+                           tucker_precision prec, int workers, void *stream, tucker_result *out) {
+  g_err[0] = 0;
+  if (!X || !dims || !out || count < 0 || workers < 0 || workers > 64) {
+    set_error("tucker_sthosvd_batched: X, dims and out must be non-null, count >= 0, 0 <= workers <= 64");
+    return TUCKER_EINVAL;
+  }
+  memset(out, 0, sizeof(tucker_result) * (size_t)count);
+  if (count == 0) return TUCKER_OK;
+  for (int i = 0; i < count; ++i) {
+    TK_CHECK(check_dims(dims + (int64_t)i * N, N));
+    if (!X[i]) {
+      set_error("tensor %d is NULL", i);
+      return TUCKER_EINVAL;
+    }
+  }
+  if (workers == 0) workers = 8;
+  workers = std::min(workers, count);
+  int device = 0;
+  TK_CUDA(cudaGetDevice(&device));
+  // the workers' streams start after everything already queued on `stream`
+  cudaEvent_t ready;
+  TK_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  TK_CUDA(cudaEventRecord(ready, static_cast<cudaStream_t>(stream)));
+  std::atomic<int> next{0};
+  std::atomic<int> status{TUCKER_OK};
+  std::mutex mu;
+  std::string first_err;
+  auto work = [&]() {
+    cudaStream_t s = nullptr;
+    int st = cudaSetDevice(device) == cudaSuccess && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaStreamWaitEvent(s, ready, 0) == cudaSuccess
+                 ? TUCKER_OK
+                 : TUCKER_ECUDA;
+    if (st != TUCKER_OK) set_error("tucker_sthosvd_batched: worker stream setup failed");
+    while (st == TUCKER_OK && status.load() == TUCKER_OK) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      st = tucker_sthosvd(X[i], dt, dims + (int64_t)i * N, N, eps, nullptr, prec, s, &out[i]);
+      if (st != TUCKER_OK) {
+        const std::string msg = std::string("tensor ") + std::to_string(i) + ": " + tucker_last_error();
+        std::lock_guard<std::mutex> lk(mu);
+        if (status.load() == TUCKER_OK) {
+          first_err = msg;
+          status.store(st);
+        }
+      }
+    }
+    if (st != TUCKER_OK && status.load() == TUCKER_OK) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (status.load() == TUCKER_OK) {
+        first_err = tucker_last_error();
+        status.store(st);
+      }
+    }
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve((size_t)workers);
+  for (int w = 0; w < workers; ++w) pool.emplace_back(work);
+  for (auto &t : pool) t.join();
+  cudaEventDestroy(ready);
+  if (status.load() != TUCKER_OK) {
+    for (int i = 0; i < count; ++i) tucker_result_free(&out[i]);
+    set_error("%s", first_err.c_str());
+    return status.load();
+  }
+  return TUCKER_OK;
 }
 
 int tucker_order_flops(const int64_t *dims, const int64_t *ranks, int N, const int *order, double *flops) {

@@ -28,7 +28,7 @@ EXPORTS = (
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
-    "tucker_mode_order",
+    "tucker_mode_order", "tucker_sthosvd_batched",
 )
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
 
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "tucker_reconstruct_sub": (i32, [pres, pi64, pi64, vp, vp]),
         "tucker_hooi": (i32, [vp, i32, pi64, i32, dbl, i32, dbl, i32, vp, pres, pi32, pdbl]),
         "tucker_order_flops": (i32, [pi64, pi64, i32, pi32, pdbl]),
+        "tucker_sthosvd_batched": (i32, [ctypes.POINTER(vp), i32, pi64, i32, i32, dbl, i32, i32, vp, pres]),
         "tucker_mode_order": (i32, [pi64, pi64, i32, i32, pi32]),
         "tucker_rel_error": (i32, [vp, i32, pres, pdbl, vp]),
         "tucker_result_free": (None, [pres]),
@@ -272,6 +273,32 @@ def hooi(x, dims, eps, max_iters=10, tol=0.0, precision="fp64", stream=None):
     _check(lib.tucker_hooi(_dev_ptr(x, "x"), _dtype_code(x), cd, len(dims), float(eps), int(max_iters), float(tol),
                            PREC[precision], _stream(stream), ctypes.byref(raw), ctypes.byref(iters), fit))
     return Result(raw), iters.value, list(fit[: iters.value + 1])
+
+
+def sthosvd_batched(xs, dims_list, eps, precision="fp64", workers=0, stream=None):
+    """Algorithm 1 on many independent device tensors of the same order N and dtype."""
+    lib = load()
+    count = len(xs)
+    if count != len(dims_list) or count == 0:
+        raise ValueError("one dims tuple per tensor, at least one tensor")
+    n = len(dims_list[0])
+    if any(len(d) != n for d in dims_list):
+        raise ValueError("every tensor needs the same number of modes")
+    code = _dtype_code(xs[0])
+    for x, d in zip(xs, dims_list):
+        if _dtype_code(x) != code or x.numel() != math.prod(d):
+            raise ValueError("tensors need one dtype and prod(dims) elements each")
+    ptrs = (ctypes.c_void_p * count)(*[_dev_ptr(x, "x").value for x in xs])
+    flat = (ctypes.c_int64 * (count * n))(*[int(v) for d in dims_list for v in d])
+    raws = (_Result * count)()
+    _check(lib.tucker_sthosvd_batched(ptrs, code, flat, n, count, float(eps), PREC[precision], int(workers),
+                                      _stream(stream), raws))
+    out = []
+    for i in range(count):
+        r = _Result()
+        ctypes.memmove(ctypes.byref(r), ctypes.byref(raws[i]), ctypes.sizeof(_Result))
+        out.append(Result(r))
+    return out
 
 
 def order_flops(dims, ranks, order=None):

@@ -151,3 +151,17 @@ def test_hooi_subtensor_and_order_arguments_rejected_on_host(lib):
                            None) == -1
     lo = (ctypes.c_int64 * 3)(0, 0, 0)
     assert lib.tucker_reconstruct_sub(ctypes.byref(res), lo, lo, fake, None) == -1  # empty result
+
+
+def test_batched_arguments_rejected_on_host(lib):
+    from paper_1510_06689_gb300 import tucker
+
+    res = (tucker._Result * 2)()
+    dims = (ctypes.c_int64 * 6)(4, 5, 6, 4, 0, 6)  # second tensor has a zero size
+    fake = (ctypes.c_void_p * 2)(0x1000, 0x2000)   # never dereferenced: validation fails first
+    assert lib.tucker_sthosvd_batched(fake, 0, dims, 3, 2, 1e-3, 0, 0, None, res) == -1
+    good = (ctypes.c_int64 * 6)(4, 5, 6, 4, 5, 6)
+    null_x = (ctypes.c_void_p * 2)(0x1000, None)
+    assert lib.tucker_sthosvd_batched(null_x, 0, good, 3, 2, 1e-3, 0, 0, None, res) == -1
+    assert lib.tucker_sthosvd_batched(fake, 0, good, 3, 2, 1e-3, 0, 65, None, res) == -1  # too many workers
+    assert lib.tucker_sthosvd_batched(fake, 0, good, 3, 0, 1e-3, 0, 0, None, res) == 0    # nothing to do

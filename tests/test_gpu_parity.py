@@ -417,6 +417,29 @@ def test_hooi_zero_iterations_is_sthosvd(gpu_lib):
     assert np.array_equal(a.core().cpu().numpy(), b.core().cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
+def test_batched_matches_single_calls_and_oracle(gpu_lib, precision):
+    """Many small tensors (the batched workload's shape mix, smaller): each result
+    equals the single-tensor call bit for bit and matches the oracle."""
+    from synthetic import random_dims_ranks
+
+    dims_list, ranks_list = random_dims_ranks(24, seed=3, dim_range=(16, 48), rank_range=(4, 10))
+    xs_np = [tucker_tensor_np(d, r, seed=4, tensor=i, noise=1e-4) for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
+    xs = [dev(x) for x in xs_np]
+    eps = 1e-3
+    res = gpu_lib.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=4)
+    assert len(res) == len(xs)
+    for x_np, x, d, r in zip(xs_np, xs, dims_list, res):
+        one = gpu_lib.sthosvd(x, d, eps, precision=precision)
+        assert r.ranks == one.ranks
+        assert np.array_equal(r.core().cpu().numpy(), one.core().cpu().numpy())
+        ref = oracle.sthosvd(x_np, d, eps)
+        assert r.ranks == ref["ranks"]
+        rel = gpu_lib.rel_error(x, r)
+        rel_ref = oracle.rel_error(x_np, ref["core"], ref["ranks"], ref["factors"])
+        assert abs(rel - rel_ref) <= 1e-3 * eps
+
+
 def test_host_entry_point(gpu_lib):
     import torch
 
