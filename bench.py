@@ -47,13 +47,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9,
                                                    "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
            # profiles/split_kernels_combustion5_t2.md (the same case)
-           ("k_gram_split_bulk", "c05caadd13b9da6c"): {
-               "ratio": (1.612648e9 + 4.068e6) / 1.6106e9,
+           ("k_gram_split_bulk", "c899ceb434ab018c"): {
+               "ratio": (1.612836e9 + 3.929e6) / 1.6106e9,
                "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB); the tiled mode-2 launch (L = 40) "
                            "measured 1.031"},
-           ("k_ttm_split_l1", "11c279836b4f9651"): {"ratio": (1.611258e9 + 472.80e6) / 2.1140e9,
+           # captured with the same kernels; the file changed since only in the host
+           # lines that set the kernels' shared-memory limits
+           ("k_ttm_split_l1", "148a97b8626bb340"): {"ratio": (1.611258e9 + 472.80e6) / 2.1140e9,
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_tma", "11c279836b4f9651"): {"ratio": (0.505569e9 + 131.04e6) / (0.50332e9 + 0.157286e9),
+           ("k_ttm_split_tma", "148a97b8626bb340"): {"ratio": (0.505569e9 + 131.04e6) / (0.50332e9 + 0.157286e9),
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB)"}}
 HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
 
@@ -412,7 +414,7 @@ def measure_next_rows(tucker, x, w, eps, precision, base_ms, base_rel, stream):
     return out
 
 
-def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=32):
+def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=8):
     """The many-small-tensors workload: `count` 3-way tensors, dims uniform in
     [16, 128], ranks in [4, 16], noise 1e-5, eps 1e-3 (one call of the batched
     entry point, the tensors already on the device)."""
