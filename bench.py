@@ -89,7 +89,10 @@ def parse_args():
                         "result when its ranks and error equal the float64 ones")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-next", action="store_true", help="skip the HOOI / subtensor / mode-order measurements")
+    p.add_argument("--no-next", action="store_true",
+                   help="skip the HOOI / subtensor / mode-order / batched / paper-shape measurements")
+    p.add_argument("--paper-shapes-only", action="store_true",
+                   help="print only the paper-problem measurements (200^4 and 25x250^3, float64 path)")
     return p.parse_args()
 
 
@@ -414,6 +417,120 @@ def measure_next_rows(tucker, x, w, eps, precision, base_ms, base_rel, stream):
     return out
 
 
+def _timed_ms(fn, stream, reps):
+    """Milliseconds per call of `fn` over `reps` calls after one untimed call (CUDA events on `stream`)."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _phase_ms(tucker, fn):
+    """Per-phase milliseconds of one call of `fn` (the library's event profile)."""
+    import torch
+
+    torch.cuda.synchronize()
+    tucker.profile_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    prof = tucker.profile_read()
+    tucker.profile_enable(False)
+    return {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]}
+
+
+def measure_paper_shapes(tucker, stream, eps=1e-4, reps=2):
+    """The paper's own synthetic problems, on the float64 path (every I_n > 128):
+
+    * Sec. 8.4's strong-scaling problem, 200^4 compressed to a 20^4 core: one
+      ST-HOSVD and one HOOI iteration (the paper's single-node point: about 3 s
+      for both on 24 cores);
+    * Sec. 8.3's mode-order problem, 25x250x250x250 with a 10x10x100x100 core:
+      ST-HOSVD timed in all 24 mode orders beside the orders the Sec. 6.1 cost
+      model picks (the paper's fastest order starts with the second mode).
+
+    Tucker tensors with N(0, 1) cores, orthonormal factors and noise 1e-6 of
+    the norm, so that eps = 1e-4 recovers the core sizes."""
+    import itertools
+
+    import torch
+
+    from synthetic import tucker_tensor_torch
+
+    out = {}
+    dims, core = (200, 200, 200, 200), (20, 20, 20, 20)
+    x = tucker_tensor_torch(dims, core, seed=0, noise=1e-6, device="cuda")
+    torch.cuda.synchronize()
+    nbytes = x.numel() * 8
+
+    def run_st():
+        tucker.sthosvd(x, dims, eps).free()
+
+    def run_hooi():
+        tucker.hooi(x, dims, eps, max_iters=1, tol=0.0)[0].free()
+
+    ms_st = _timed_ms(run_st, stream, reps)
+    ms_hooi = _timed_ms(run_hooi, stream, reps)
+    phases_st, phases_hooi = _phase_ms(tucker, run_st), _phase_ms(tucker, run_hooi)
+    r = tucker.sthosvd(x, dims, eps)
+    ranks, rel = list(r.ranks), tucker.rel_error(x, r)
+    r.free()
+    model = tucker.order_flops(dims, ranks, list(range(4)))
+    out["strong200"] = {
+        "dims": list(dims), "core": list(core), "eps": eps, "ranks": ranks, "rel_error": rel,
+        "input_gb": round(nbytes / 1e9, 3), "sthosvd_ms": round(ms_st, 3),
+        "hooi_iteration_ms": round(ms_hooi - ms_st, 3), "sthosvd_plus_hooi_ms": round(ms_hooi, 3),
+        "sthosvd_input_gb_s": round(nbytes / (ms_st / 1e3) / 1e9, 2),
+        "sthosvd_model_gflop": round(model / 1e9, 2),
+        "sthosvd_model_tflop_s": round(model / (ms_st / 1e3) / 1e12, 4),
+        "fp64_peak_tflop_s": round(FP64_PEAK_TFLOPS, 4),
+        "phase_ms_sthosvd": phases_st, "phase_ms_sthosvd_plus_hooi": phases_hooi,
+        "paper_single_node_s": 3.0,
+        "note": "float64 path; the paper's figure is ST-HOSVD plus one HOOI step on one 24-core node "
+                "(other hardware, context only); model flops are the Sec. 6.1 count, which counts the whole "
+                "Gram (the kernels form one triangle of it)"}
+    del x
+    torch.cuda.empty_cache()
+
+    dims, core = (25, 250, 250, 250), (10, 10, 100, 100)
+    x = tucker_tensor_torch(dims, core, seed=0, noise=1e-6, device="cuda")
+    torch.cuda.synchronize()
+    r = tucker.sthosvd(x, dims, eps)
+    ranks = list(r.ranks)
+    r.free()
+    rows = []
+    for order in itertools.permutations(range(4)):
+        o = list(order)
+        ms = _timed_ms(lambda: tucker.sthosvd(x, dims, eps, mode_order=o).free(), stream, reps)
+        rows.append({"order": o, "ms": round(ms, 3),
+                     "model_gflop": round(tucker.order_flops(dims, ranks, o) / 1e9, 3)})
+    phases_given = _phase_ms(tucker, lambda: tucker.sthosvd(x, dims, eps).free())
+    del x
+    torch.cuda.empty_cache()
+    by_time = sorted(rows, key=lambda e: e["ms"])
+    pos = {tuple(e["order"]): i + 1 for i, e in enumerate(by_time)}
+    picks = {}
+    for rule in ("flops", "ratio", "exhaustive"):
+        o = tucker.mode_order(dims, ranks, rule)
+        e = next(e for e in rows if e["order"] == o)
+        picks[rule] = {"order": o, "ms": e["ms"], "model_gflop": e["model_gflop"], "measured_rank": pos[tuple(o)]}
+    out["mode_order250"] = {
+        "dims": list(dims), "core": list(core), "eps": eps, "ranks": ranks,
+        "input_gb": round(math.prod(dims) * 8 / 1e9, 3),
+        "fastest": by_time[0], "slowest": by_time[-1], "given_order": rows[0], "picks": picks,
+        "phase_ms_given_order": phases_given,
+        "orders": rows,
+        "note": "float64 path, each order timed over 2 calls after one untimed call; measured_rank 1 is the "
+                "fastest of the 24 orders"}
+    return out
+
+
 def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=8):
     """The many-small-tensors workload: `count` 3-way tensors, dims uniform in
     [16, 128], ranks in [4, 16], noise 1e-5, eps 1e-3 (one call of the batched
@@ -459,6 +576,10 @@ def main():
         build.build()
     barrier(world)
     tucker.load()
+    if args.paper_shapes_only:
+        if rank == 0:
+            print(json.dumps(measure_paper_shapes(tucker, torch.cuda.current_stream())), flush=True)
+        return 0
     w = WORKLOADS[WORKLOAD]
     if args.slices:
         import dataclasses
@@ -541,6 +662,12 @@ def main():
                       f"({math.prod(sdims) * 8 / 1e9:.2f} GB), one oracle ST-HOSVD in {secs:.2f} s "
                       f"(numpy/OpenBLAS float64 on all host cores)",
         }
+    # last: these tensors of their own (16 GB between them) run after the end-to-end leg
+    if not args.no_next and world == 1:
+        try:
+            line["next_rows"]["paper_shapes"] = measure_paper_shapes(tucker, stream)
+        except Exception as e:  # recorded in the line; the headline measurement above stands
+            line["next_rows"]["paper_shapes"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

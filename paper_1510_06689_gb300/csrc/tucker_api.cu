@@ -542,8 +542,8 @@ static int expand_modes(const tucker_result *r, int skip, double *final_out, Dev
 
 // Algorithm 2 (HOOI) after Algorithm 1 has filled `out` (ranks fixed).
 // Each iteration: for n = 0..N-1, Y = X x {U_m^T}_{m != n} with the factors
-// as updated so far (the TTM chain takes the largest reductions I_m / R_m
-// first), S = Y_(n) Y_(n)^T, U_n = leading R_n eigenvectors of S; then
+// as updated so far (formed from a shared partial product, below),
+// S = Y_(n) Y_(n)^T, U_n = leading R_n eigenvectors of S; then
 // G = Y x_{N-1} U_{N-1}^T from the last Y.  fit[k] = ||X||^2 - ||G||^2.
 static int hooi_iterate(const void *X, tucker_dtype dt, int max_iters, double tol, tucker_precision prec,
                         cudaStream_t s, tucker_result *out, int *iters, double *fit) {
@@ -579,39 +579,74 @@ static int hooi_iterate(const void *X, tucker_dtype dt, int max_iters, double to
   TK_CHECK(core_fit(&prev));
   if (fit) fit[0] = prev;
   *iters = 0;
+  // Y <- src x {U_m^T : m in modes}, the largest reductions I_m / R_m first.
+  // cur holds src's dims on entry and Y's on return; hold owns Y unless no
+  // mode applies (then Y is src).
+  auto contract = [&](const void *src, tucker_dtype sdt, int64_t *cur, int *modes, int cnt, DevBuf &hold,
+                      const void **res, tucker_dtype *rdt) -> int {
+    std::stable_sort(modes, modes + cnt, [&](int a, int b) {
+      return (double)out->dims[a] / out->ranks[a] > (double)out->dims[b] / out->ranks[b];
+    });
+    const void *Y = src;
+    tucker_dtype ydt = sdt;
+    DevBuf ybuf;
+    for (int k = 0; k < cnt; ++k) {
+      const int m = modes[k];
+      int64_t L = 1, B = 1;
+      for (int q = 0; q < m; ++q) L *= cur[q];
+      for (int q = m + 1; q < N; ++q) B *= cur[q];
+      const int64_t J = cur[m], R = out->ranks[m];
+      DevBuf ynew;
+      TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
+      if (prec == TUCKER_PREC_BF16X4)
+        TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, out->factors[m], R, ynew.as<double>(), d_terr, dev, s, &prof));
+      else
+        TK_CHECK(launch_ttm(Y, ydt, L, J, B, out->factors[m], /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev, s,
+                            &prof));
+      ybuf.reset();
+      ybuf.p = ynew.release();
+      ybuf.s = s;
+      Y = ybuf.p;
+      ydt = TUCKER_F64;
+      cur[m] = R;
+    }
+    hold.reset();
+    hold.p = ybuf.release();
+    hold.s = s;
+    *res = Y;
+    *rdt = ydt;
+    return TUCKER_OK;
+  };
+  // Two-level reuse of the products with X: the modes split into a first
+  // half F = {0..h-1} and the rest.  While F's factors are updated, every Y
+  // shares Z_F = X x {U_m^T : m >= h} (those factors do not change until F is
+  // done); the later modes share Z = X x {U_m^T : m < h} with F's new factors.
+  // Each iteration reads X twice instead of N times; the products are those of
+  // Algorithm 2 with the contractions associated differently.
+  const int h = N / 2;
   for (int it = 0; it < max_iters; ++it) {
+    DevBuf zbuf;
+    const void *Z = X;
+    tucker_dtype zdt = dt;
+    int64_t zcur[TUCKER_MAX_MODES];
     for (int n = 0; n < N; ++n) {
+      if (n == 0 || n == h) {  // Z for this half: contract the other half's modes of X
+        int other[TUCKER_MAX_MODES], cnt = 0;
+        for (int m = 0; m < N; ++m)
+          if ((m < h) != (n < h)) other[cnt++] = m;
+        for (int m = 0; m < N; ++m) zcur[m] = out->dims[m];
+        zbuf.reset();
+        TK_CHECK(contract(X, dt, zcur, other, cnt, zbuf, &Z, &zdt));
+      }
       int seq[TUCKER_MAX_MODES], cnt = 0;
       for (int m = 0; m < N; ++m)
-        if (m != n) seq[cnt++] = m;
-      std::stable_sort(seq, seq + cnt, [&](int a, int b) {
-        return (double)out->dims[a] / out->ranks[a] > (double)out->dims[b] / out->ranks[b];
-      });
+        if (m != n && (m < h) == (n < h)) seq[cnt++] = m;
       int64_t cur[TUCKER_MAX_MODES];
-      for (int m = 0; m < N; ++m) cur[m] = out->dims[m];
-      const void *Y = X;
-      tucker_dtype ydt = dt;
+      for (int m = 0; m < N; ++m) cur[m] = zcur[m];
+      const void *Y = nullptr;
+      tucker_dtype ydt = zdt;
       DevBuf ybuf;
-      for (int k = 0; k < cnt; ++k) {
-        const int m = seq[k];
-        int64_t L = 1, B = 1;
-        for (int q = 0; q < m; ++q) L *= cur[q];
-        for (int q = m + 1; q < N; ++q) B *= cur[q];
-        const int64_t J = cur[m], R = out->ranks[m];
-        DevBuf ynew;
-        TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
-        if (prec == TUCKER_PREC_BF16X4)
-          TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, out->factors[m], R, ynew.as<double>(), d_terr, dev, s, &prof));
-        else
-          TK_CHECK(launch_ttm(Y, ydt, L, J, B, out->factors[m], /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev, s,
-                              &prof));
-        ybuf.reset();
-        ybuf.p = ynew.release();
-        ybuf.s = s;
-        Y = ybuf.p;
-        ydt = TUCKER_F64;
-        cur[m] = R;
-      }
+      TK_CHECK(contract(Z, zdt, cur, seq, cnt, ybuf, &Y, &ydt));
       int64_t L = 1, B = 1;
       for (int q = 0; q < n; ++q) L *= cur[q];
       for (int q = n + 1; q < N; ++q) B *= cur[q];
