@@ -165,6 +165,9 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
 // device check; otherwise the caller runs the float64 Jacobi.  Synchronises s.
 int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
                   cudaStream_t s, Prof *prof, double tail_budget = -1.0);
+// The calling thread's last mixed-precision check: residual and its bound,
+// orthogonality and its bound, and the number of unresolved tail columns.
+const double *mp_last_check();
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

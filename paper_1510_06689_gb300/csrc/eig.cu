@@ -726,7 +726,10 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
     if (verified) return TUCKER_OK;
     const char *strict = getenv("TUCKER_EIG_MP_STRICT");  // tests: report instead of falling back
     if (strict && strict[0] == '1') {
-      set_error("mixed-precision eigensolver failed its check (J = %lld)", (long long)J);
+      const double *c = mp_last_check();
+      set_error("mixed-precision eigensolver failed its check (J = %lld): residual %.3g (bound %.3g), "
+                "orthogonality %.3g (bound %.3g), %d tail columns unresolved",
+                (long long)J, c[0], c[1], c[2], c[3], (int)c[4]);
       return TUCKER_ENOCONV;
     }
   }

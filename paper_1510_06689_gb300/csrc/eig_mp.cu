@@ -1473,6 +1473,10 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
 
 // Returns TUCKER_OK with *verified = 1 when lam / V hold a verified result;
 // *verified = 0 leaves them to the float64 Jacobi.
+static thread_local double g_mp_check[5];
+
+const double *mp_last_check() { return g_mp_check; }
+
 int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
                   cudaStream_t s, Prof *prof, double tail_budget) {
   *verified = 0;
@@ -1514,6 +1518,11 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   // the paper's flop count of the eigenvector step (10/3 J^3, Sec. 5.4); bytes: S read, V written
   if (prof) prof->end(10.0 / 3.0 * (double)J * J * J, (double)J * J * 16, 1);
   const double tol_res = 16.0 * m * kU * chk[2], tol_orth = 16.0 * m * kU;
+  g_mp_check[0] = chk[0];
+  g_mp_check[1] = tol_res;
+  g_mp_check[2] = chk[1];
+  g_mp_check[3] = tol_orth;
+  g_mp_check[4] = skipped;
   if (chk[0] <= tol_res && chk[1] <= tol_orth) {
     const int info[2] = {sw, 0};
     TK_CUDA(cudaMemcpyAsync(d_info, info, sizeof info, cudaMemcpyHostToDevice, s));
