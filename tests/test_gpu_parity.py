@@ -408,6 +408,30 @@ def test_hooi_matches_oracle(gpu_lib, precision):
         assert s.max() < (1e-6 if precision == "fp64" else 1e-3)
 
 
+@pytest.mark.parametrize("dims,ranks,eps", [((40,), (1,), 0.1), ((30, 22), (4, 4), 0.2),
+                                             ((18, 16, 14), (4, 3, 3), 0.15),
+                                             ((10, 9, 8, 7, 6), (3, 3, 2, 2, 2), 0.15)])
+def test_hooi_shared_products_any_order(gpu_lib, dims, ranks, eps):
+    """HOOI forms every mode's Y from a product shared by its half of the
+    modes (first half, then the rest); for N = 1, 2, 3 and 5 the fit history
+    still equals Algorithm 2's printed form, where each Y starts from X.  The
+    oracle's rank cuts sit at least 2.7e-3 relative from the threshold here."""
+    x = tucker_tensor_np(dims, ranks, seed=21, noise=0.2)
+    ref = oracle.hooi(x, dims, eps, max_iters=4, tol=0.0)
+    res, iters, fit = gpu_lib.hooi(dev(x), dims, eps, max_iters=4, tol=0.0)
+    assert res.ranks == ref["ranks"]
+    nx2 = ref["norm2"]
+    assert len(fit) == iters + 1
+    # stagnant fits (N <= 2) may stop one iteration apart: compare the common prefix
+    for a, b in zip(fit, ref["history"]):
+        assert abs(a - b) <= 1e-10 * nx2
+    x_hat = gpu_lib.reconstruct(res).cpu().numpy()
+    assert abs(float(((x - x_hat) ** 2).sum()) - fit[-1]) <= 1e-9 * nx2
+    for n in range(len(dims)):
+        u = res.factor(n).cpu().numpy()
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 64 * dims[n] * U
+
+
 def test_hooi_zero_iterations_is_sthosvd(gpu_lib):
     dims, ranks = (16, 12, 10), (3, 3, 2)
     x = dev(tucker_tensor_np(dims, ranks, seed=2, noise=1e-2))
