@@ -60,7 +60,7 @@ typedef enum {
   TUCKER_ENOCONV = -4,     /* Jacobi eigensolver hit its sweep cap */
   TUCKER_ETIMEOUT = -5,    /* reserved: a bounded device wait expired */
   TUCKER_ENONFINITE = -6,  /* input holds Inf/NaN (||X||^2 is not finite) */
-  TUCKER_EUNSUPPORTED = -7 /* valid request this build does not implement */
+  TUCKER_EUNSUPPORTED = -7 /* valid request the library does not implement */
 } tucker_status;
 
 /* Element type of an input tensor.  Internal tensors are always float64. */

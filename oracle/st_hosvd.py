@@ -12,7 +12,7 @@ product for the Gram matrix and the mode-n product, LAPACK's symmetric
 eigensolver (``numpy.linalg.eigh``) for "leading eigenvectors of S", as the
 paper itself uses LAPACK's ``dsyevx`` there (Sec. 5.4).
 
-Readings of points the paper leaves open (each is repeated in the design doc):
+Readings of points the paper leaves open:
 
 * Unfolding (Sec. 2.1): the printed column-index formula is garbled (it uses
   I/I_k where prefix products are meant).  We use the standard map
