@@ -168,6 +168,9 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
 // The calling thread's last mixed-precision check: residual and its bound,
 // orthogonality and its bound, and the number of unresolved tail columns.
 const double *mp_last_check();
+// Largest J the mixed-precision eigensolver takes: 128, or 256 with
+// TUCKER_EIG_WIDE=1 (the wide float32 stage).
+int mp_max_j();
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

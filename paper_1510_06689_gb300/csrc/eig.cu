@@ -714,13 +714,14 @@ static bool dsm_cluster_ok(size_t dsmem) {
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof, double tail_budget) {
   const int64_t m = J + (J & 1);
-  // "mp" (default: mixed precision, J <= 128, float64 Jacobi if unverified) |
+  // "mp" (default: mixed precision, J <= 128 or with TUCKER_EIG_WIDE=1 J <= 256,
+  // float64 Jacobi if unverified) |
   // "jacobi" (float64 Jacobi only) | "dsm" | "l2m" | "l2" (cluster variants)
   const char *ev = getenv("TUCKER_EIG_KERNEL");
   const bool use_dsm = ev && !strcmp(ev, "dsm");
   const bool use_l2 = ev && !strcmp(ev, "l2");
   const bool jacobi_only = ev && (use_dsm || use_l2 || !strcmp(ev, "jacobi") || !strcmp(ev, "l2m"));
-  if (!jacobi_only && J <= 128) {
+  if (!jacobi_only && J <= mp_max_j()) {
     int verified = 0;
     TK_CHECK(launch_eig_mp(d_S, J, d_lam, d_V, d_info, &verified, s, prof, tail_budget));
     if (verified) return TUCKER_OK;

@@ -54,7 +54,9 @@ namespace tk {
 
 namespace {
 
-constexpr int kMpMaxJ = 128;
+constexpr int kTriMaxJ = 128;   // float32 stages with the whole matrix in shared memory
+constexpr int kMpMaxJ = 256;    // the solver as a whole (wide float32 stage above kTriMaxJ)
+constexpr int kGemmMaxK = 256;  // contraction length of the small float64 products
 constexpr int kJ32Threads = 1024;
 constexpr int kJ32MaxSweeps = 40;
 constexpr int kMaxDepth = 5;
@@ -78,7 +80,7 @@ constexpr int kPolishSteps = 1;
 __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restrict__ A, int lda, int n,
                                                            double *__restrict__ X, int ldx, int *__restrict__ sweeps) {
   extern __shared__ __align__(16) float sm32[];
-  __shared__ float4 rot[kMpMaxJ / 2];  // per pair: c, s, t = s / c, (p | q << 16) as bits
+  __shared__ float4 rot[kTriMaxJ / 2];  // per pair: c, s, t = s / c, (p | q << 16) as bits
   __shared__ float red[kJ32Threads / 32];
   __shared__ float scale_s, tol_s;
   __shared__ int rotated;
@@ -276,7 +278,7 @@ struct Tri32Layout {
     z = up(n * (n + 1));
     w = z + up(n * ld);
     part = w + up(n * ld);
-    tf = part + 4 * kNb * kMpMaxJ;
+    tf = part + 4 * kNb * kTriMaxJ;
     vec = tf + ((n + kNb - 1) / kNb) * kNb * kNb;
     total = vec + 8 * n;
   }
@@ -375,24 +377,24 @@ __device__ void apply_wy(float *__restrict__ M, int ldm, int n, int r0, int c0, 
         a0 = fma4(v.x, m, a0);
         a1 = fma4(v.y, m, a1);
       }
-      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g) * kMpMaxJ + 4 * q) = a0;
-      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g + 1) * kMpMaxJ + 4 * q) = a1;
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g) * kTriMaxJ + 4 * q) = a0;
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g + 1) * kTriMaxJ + 4 * q) = a1;
     }
   }
   __syncthreads();
-  if (tid < kMpMaxJ && tid >= 4 * q0 && tid < 4 * nq) {
+  if (tid < kTriMaxJ && tid >= 4 * q0 && tid < 4 * nq) {
     const int c = tid;
     float P[kNb];
 #pragma unroll
     for (int j = 0; j < kNb; ++j)
-      P[j] = (part[j * kMpMaxJ + c] + part[(kNb + j) * kMpMaxJ + c]) +
-             (part[(2 * kNb + j) * kMpMaxJ + c] + part[(3 * kNb + j) * kMpMaxJ + c]);
+      P[j] = (part[j * kTriMaxJ + c] + part[(kNb + j) * kTriMaxJ + c]) +
+             (part[(2 * kNb + j) * kTriMaxJ + c] + part[(3 * kNb + j) * kTriMaxJ + c]);
 #pragma unroll
     for (int i = 0; i < kNb; ++i) {
       float t = 0.f;
 #pragma unroll
       for (int k = 0; k < kNb; ++k) t = fmaf(trans ? T[k * kNb + i] : T[i * kNb + k], P[k], t);
-      part[i * kMpMaxJ + c] = t;
+      part[i * kTriMaxJ + c] = t;
     }
   }
   __syncthreads();
@@ -401,7 +403,7 @@ __device__ void apply_wy(float *__restrict__ M, int ldm, int n, int r0, int c0, 
     if (q < nq) {
       float4 P[kNb];
 #pragma unroll
-      for (int j = 0; j < kNb; ++j) P[j] = *reinterpret_cast<const float4 *>(part + j * kMpMaxJ + 4 * q);
+      for (int j = 0; j < kNb; ++j) P[j] = *reinterpret_cast<const float4 *>(part + j * kTriMaxJ + 4 * q);
       const bool whole = 4 * q >= c0;
 #pragma unroll 2
       for (int r = r0 + p; r < n; r += 16) {
@@ -533,12 +535,12 @@ __device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int 
                           float *Wp, float *vs, int tid, float *red, float *d, float *e, float *tau) {
   const int lane = tid & 31, w4 = tid >> 5;
   const int m = n - j - 1;  // >= 2
-  const bool has_y = m + 2 * kNb <= kMpMaxJ;
+  const bool has_y = m + 2 * kNb <= kTriMaxJ;
   const int c = tid, cc = min(c, m - 1), r = j + 1 + cc;
   float vr[kNb], wr[kNb];
   load8(Vp + r * kNb, vr);
   load8(Wp + r * kNb, wr);
-  const float pp = (pd[cc] + pd[kMpMaxJ + cc]) + (pd[2 * kMpMaxJ + cc] + pd[3 * kMpMaxJ + cc]);
+  const float pp = (pd[cc] + pd[kTriMaxJ + cc]) + (pd[2 * kTriMaxJ + cc] + pd[3 * kTriMaxJ + cc]);
   const float vv = vs[cc];
   const float pq = c < m ? pp : 0.f, v = c < m ? vv : 0.f;
   float y1[kNb], y2[kNb];
@@ -546,9 +548,9 @@ __device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int 
     const int c0 = has_y ? m : 0;
 #pragma unroll
     for (int u = 0; u < kNb; ++u) {
-      const float s2 = (pd[c0 + u] + pd[kMpMaxJ + c0 + u]) + (pd[2 * kMpMaxJ + c0 + u] + pd[3 * kMpMaxJ + c0 + u]);
+      const float s2 = (pd[c0 + u] + pd[kTriMaxJ + c0 + u]) + (pd[2 * kTriMaxJ + c0 + u] + pd[3 * kTriMaxJ + c0 + u]);
       const int cy = c0 + kNb + u;
-      const float s1 = (pd[cy] + pd[kMpMaxJ + cy]) + (pd[2 * kMpMaxJ + cy] + pd[3 * kMpMaxJ + cy]);
+      const float s1 = (pd[cy] + pd[kTriMaxJ + cy]) + (pd[2 * kTriMaxJ + cy] + pd[3 * kTriMaxJ + cy]);
       y1[u] = has_y && u < i ? s1 : 0.f;
       y2[u] = has_y && u < i ? s2 : 0.f;
     }
@@ -603,7 +605,7 @@ __device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int 
   float vj[kNb], wj[kNb];
   load8(Vp + j1 * kNb, vj);
   load8(Wp + j1 * kNb, wj);
-  float x0 = (pd[0] + pd[kMpMaxJ]) + (pd[2 * kMpMaxJ] + pd[3 * kMpMaxJ]);
+  float x0 = (pd[0] + pd[kTriMaxJ]) + (pd[2 * kTriMaxJ] + pd[3 * kTriMaxJ]);
 #pragma unroll
   for (int u = 0; u < kNb; ++u)
     if (u < i) x0 = fmaf(-vj[u], y1[u], fmaf(-wj[u], y2[u], x0));
@@ -625,7 +627,7 @@ __device__ float tri_step(const float *pd, float *Af, int ld, int n, int j, int 
 // signs, and the panel's T factor.  No block barrier.
 __device__ void qr_panel(const float *__restrict__ Z, int lz, float *__restrict__ W, int n, int j0, int nbk, int lane,
                          float *__restrict__ qtau, float *__restrict__ sgn, float *__restrict__ T) {
-  constexpr int kR = kMpMaxJ / 32;
+  constexpr int kR = kTriMaxJ / 32;
   const int mrows = n - j0;
   float P[kR][kNb];
 #pragma unroll
@@ -802,7 +804,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
   // panel's start), then warp 0 completes w and brings the next column up to
   // date and forms its reflector.
   float *Vp = W, *Wp = Z;  // both free until step 3
-  float *vs = part + 4 * kMpMaxJ;  // the current v, contiguous (16-byte aligned)
+  float *vs = part + 4 * kTriMaxJ;  // the current v, contiguous (16-byte aligned)
   float tcur = 0.f;        // threads 0..127: tau of the current column
   for (int k0 = 0; k0 + 2 < n; k0 += kNb) {
     const int nbk = min(kNb, n - 2 - k0);
@@ -818,14 +820,14 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
       {  // partial A22 v: thread (column c, part) sums a quarter of the rows
          // (a multiple of 4, for 16-byte loads of v); when they fit, the
          // threads of columns m .. m + 15 form V^T v and W^T v the same way
-        const int c = tid & (kMpMaxJ - 1), part = tid >> 7;
+        const int c = tid & (kTriMaxJ - 1), part = tid >> 7;
         const int rb = ((m + 15) >> 4) << 2, r1 = min(m, part * rb + rb);
         const float *X = nullptr;
         int xs = 0;
         if (c < m) {
           X = Af + (j + 1) * ld + (j + 1 + c);
           xs = ld;
-        } else if (m + 2 * kNb <= kMpMaxJ && c < m + 2 * kNb) {
+        } else if (m + 2 * kNb <= kTriMaxJ && c < m + 2 * kNb) {
           const int u = c - m;
           X = (u < kNb ? Vp + u : Wp + (u - kNb)) + (j + 1) * kNb;
           xs = kNb;
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
           }
           for (; r < r1; ++r) acc = fmaf(X[r * xs], vs[r], acc);
         }
-        pd[part * kMpMaxJ + c] = acc + acc2;
+        pd[part * kTriMaxJ + c] = acc + acc2;
       }
       __syncthreads();
       if (tid < 128) tcur = tri_step(pd, Af, ld, n, j, i, tcur, i + 1 < nbk, Vp, Wp, vs, tid, red, d, e, tau);
@@ -851,7 +853,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
     // part) keeps row c of V and W and takes rows part, part + 4, ...
     const int t0 = k0 + nbk, mt = n - t0;
     {
-      const int c = tid & (kMpMaxJ - 1), part = tid >> 7;
+      const int c = tid & (kTriMaxJ - 1), part = tid >> 7;
       if (c < mt) {
         float vc[kNb], wc[kNb];
         load8(Vp + (t0 + c) * kNb, vc);
@@ -1023,6 +1025,298 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
 }
 
 // ---------------------------------------------------------------------------
+// First stage for kTriMaxJ < n <= kMpMaxJ (one CTA of kW32Threads), the steps
+// of k_eig32_tri with a matrix too large for a full float32 copy in shared
+// memory.  The lower triangle is packed by columns in shared memory (column
+// j holds rows j..n-1 from offset j n - j (j - 1) / 2: 129 KB at n = 256);
+// the eigenvector passes use two n x n float arrays in global memory (they
+// stay in L2), Zg[k n + c] (row k of vector c) and Lg (the L factors of the
+// inverse iteration).
+//   1. Householder tridiagonalization one reflector at a time: the reflector
+//      of column k (v(0) = 1, beta = -sign(alpha) ||x||, tau = (beta -
+//      alpha) / beta), p = tau A22 v (four threads per row of the packed
+//      triangle), w = p - (tau / 2)(p^T v) v, A22 -= v w^T + w v^T.  v stays
+//      in column k below the subdiagonal.
+//   2. Eigenvalues by multisection on Sturm counts (four threads each).
+//   3. Inverse iteration, thread c for the c-th largest eigenvalue.
+//   4. Modified Gram-Schmidt, two passes per vector, in descending
+//      eigenvalue order: vectors of a cluster become an orthonormal basis of
+//      the complement of the larger ones (the role of the Householder QR in
+//      k_eig32_tri).
+//   5. X = Q1 Z by the reflectors from the last to the first.
+// Writes X (float64, columns in descending eigenvalue order).
+// ---------------------------------------------------------------------------
+constexpr int kW32Threads = 1024;
+
+__host__ __device__ __forceinline__ int packed_col(int n, int j) { return j * n - j * (j - 1) / 2; }
+
+// floats: the packed triangle (padded to 16 bytes), d, e, e2, tau, lam, pv,
+// zj (n each) and 4 x 256 partial sums
+size_t wide32_smem(int n) { return (size_t)(((n * (n + 1) / 2 + 3) & ~3) + 7 * n + 4 * 256) * sizeof(float); }
+
+// Sum over the block of one value per thread; every thread gets the result.
+// Uses red[0..32]; callers separate consecutive uses by a barrier.
+__device__ __forceinline__ float block_sum32(float v, float *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum32(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    float t = lane < nw ? red[lane] : 0.f;
+    t = warp_sum32(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__restrict__ A, int lda, int n,
+                                                             double *__restrict__ X, int ldx, float *Zg,
+                                                             float *Lg) {
+  extern __shared__ __align__(16) float smw[];
+  float *Ap = smw;
+  float *d = smw + ((n * (n + 1) / 2 + 3) & ~3), *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n,
+        *pv = lam + n, *zj = pv + n, *ps = zj + n;
+  __shared__ float red[33];
+  __shared__ float sc[4];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+
+  // ---- load A * 2^-s into the packed lower triangle (the upper triangle of
+  // A read, as in k_eig32_tri: largest magnitude in [1/2, 1), entries 2^-126
+  // below it flushed to zero, floats built from the float64 bits)
+  unsigned mhi = 0u;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    if (r <= c) mhi = max(mhi, (unsigned)(__double_as_longlong(A[r + (int64_t)lda * c]) >> 32) & 0x7FFFFFFFu);
+  }
+  mhi = __reduce_max_sync(0xffffffffu, mhi);
+  if (lane == 0) red[warp] = __uint_as_float(mhi);
+  __syncthreads();
+  if (tid == 0) {
+    unsigned v = 0u;
+    for (int w = 0; w < nw; ++w) v = max(v, __float_as_uint(red[w]));
+    sc[0] = __uint_as_float(v);
+  }
+  __syncthreads();
+  const unsigned amax = __float_as_uint(sc[0]);
+  const int rebase = (int)(amax >> 20) - 126;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    if (r <= c) {  // A(r, c) = A(c, r): row c of packed column r
+      const unsigned long long b = (unsigned long long)__double_as_longlong(A[r + (int64_t)lda * c]);
+      const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b, mag = hi & 0x7FFFFFFFu;
+      const int x = max((int)mag - (rebase << 20), 0);
+      const unsigned f = (amax == 0u || mag == 0u) ? 0u : ((hi & 0x80000000u) | __funnelshift_l(lo, (unsigned)x, 3));
+      Ap[packed_col(n, r) + (c - r)] = __uint_as_float(f);
+    }
+  }
+  __syncthreads();
+
+  // ---- 1. tridiagonalization
+  for (int k = 0; k + 2 < n; ++k) {
+    float *colk = Ap + packed_col(n, k);  // rows k..n-1 of column k
+    const int m = n - k - 1;              // rows k+1..n-1: x, then v
+    float xv = (tid >= 1 && tid < m) ? colk[1 + tid] : 0.f;
+    const float sig = block_sum32(xv * xv, red);
+    if (tid == 0) {
+      const float alpha = colk[1];
+      float t = 0.f, beta = alpha, scale = 0.f;
+      if (sig > 0.f) {
+        beta = -copysignf(sqrtf(fmaf(alpha, alpha, sig)), alpha);
+        t = (beta - alpha) / beta;
+        scale = 1.f / (alpha - beta);
+      }
+      d[k] = colk[0];
+      e[k] = beta;
+      tau[k] = t;
+      sc[1] = scale;
+    }
+    __syncthreads();
+    if (tid < m) colk[1 + tid] = tid == 0 ? 1.f : colk[1 + tid] * sc[1];
+    __syncthreads();
+    const float t = tau[k];
+    const float *v = colk + 1;  // v[a], row k + 1 + a
+    // p = t A22 v: four threads per row a, columns b = part (mod 4)
+    {
+      const int a = tid >> 2, part = tid & 3;
+      float acc = 0.f;
+      if (a < m) {
+        const int ga = k + 1 + a;
+        for (int b = part; b < m; b += 4) {
+          const int gb = k + 1 + b;
+          const float aab = b <= a ? Ap[packed_col(n, gb) + (ga - gb)] : Ap[packed_col(n, ga) + (gb - ga)];
+          acc = fmaf(aab, v[b], acc);
+        }
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (a < m && part == 0) pv[a] = t * acc;
+    }
+    __syncthreads();
+    const float pvv = block_sum32(tid < m ? pv[tid] * v[tid] : 0.f, red);
+    const float half = 0.5f * t * pvv;
+    if (tid < m) pv[tid] = fmaf(-half, v[tid], pv[tid]);  // w
+    __syncthreads();
+    // A22 -= v w^T + w v^T on the packed lower triangle: warp per column b
+    for (int b = warp; b < m; b += nw) {
+      float *col = Ap + packed_col(n, k + 1 + b);  // rows k+1+b..: local rows a >= b
+      const float vb = v[b], wb = pv[b];
+      for (int a = b + lane; a < m; a += 32) col[a - b] -= fmaf(v[a], wb, pv[a] * vb);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d[n - 2] = Ap[packed_col(n, n - 2)];
+    e[n - 2] = Ap[packed_col(n, n - 2) + 1];
+    d[n - 1] = Ap[packed_col(n, n - 1)];
+    e[n - 1] = 0.f;
+    tau[n - 2] = 0.f;
+    tau[n - 1] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) e2[i] = e[i] * e[i];
+  if (warp == 0) {  // Gershgorin bounds and ||T||
+    float lo = FLT_MAX, hi = -FLT_MAX;
+    for (int i = lane; i < n; i += 32) {
+      const float r = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+      lo = fminf(lo, d[i] - r);
+      hi = fmaxf(hi, d[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const float tn = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), FLT_MIN);
+      sc[0] = lo - 0x1p-20f * tn;
+      sc[1] = hi + 0x1p-20f * tn;
+      sc[2] = tn;
+    }
+  }
+  __syncthreads();
+  const float gl = sc[0], gu = sc[1], tn = sc[2];
+  const float piv = 0x1p-23f * tn;
+
+  // ---- 2. multisection: threads 4 i .. 4 i + 3 find the i-th smallest eigenvalue
+  {
+    const int i = tid >> 2, sub = tid & 3;
+    float lo = gl, hi = gu;
+    for (int it = 0; it < 12; ++it) {
+      const float x = lo + (hi - lo) * (0.2f * (float)(sub + 1));
+      int cnt = 0;
+      if (i < n) {
+        float q = d[0] - x;
+        for (int k = 0;; ++k) {
+          if (fabsf(q) < piv) q = -piv;
+          cnt += q < 0.f;
+          if (k + 1 >= n) break;
+          q = d[k + 1] - x - __fdividef(e2[k], q);
+        }
+      }
+      float nlo = lo, nhi = hi;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int cs = __shfl_sync(0xffffffffu, cnt, (lane & ~3) | s);
+        const float xs = __shfl_sync(0xffffffffu, x, (lane & ~3) | s);
+        if (cs <= i) nlo = fmaxf(nlo, xs);
+        else nhi = fminf(nhi, xs);
+      }
+      lo = nlo;
+      hi = nhi;
+    }
+    if (i < n && sub == 0) lam[n - 1 - i] = 0.5f * (lo + hi);  // descending order
+  }
+  __syncthreads();
+
+  // ---- 3. inverse iteration: thread c solves (T - l_c I) z = b twice
+  for (int c = tid; c < n; c += nt) {
+    const float s = lam[c];
+    float D = d[0] - s;
+    for (int k = 0; k + 1 < n; ++k) {
+      if (fabsf(D) < piv) D = D < 0.f ? -piv : piv;
+      const float L = __fdividef(e[k], D);
+      Lg[k * n + c] = L;
+      D = d[k + 1] - s - L * e[k];
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      float Dk = d[0] - s, y = 0.f;
+      for (int k = 0; k < n; ++k) {  // forward: y = L^-1 b, z = D^-1 y
+        if (k > 0) Dk = d[k] - s - Lg[(k - 1) * n + c] * e[k - 1];
+        if (fabsf(Dk) < piv) Dk = Dk < 0.f ? -piv : piv;
+        const float b = pass == 0 ? start_entry(c, k) : Zg[k * n + c];
+        y = k == 0 ? b : b - Lg[(k - 1) * n + c] * y;
+        Zg[k * n + c] = __fdividef(y, Dk);
+      }
+      float xn = Zg[(n - 1) * n + c], nrm = xn * xn;
+      for (int k = n - 2; k >= 0; --k) {  // backward: x = L^-T z
+        xn = Zg[k * n + c] - Lg[k * n + c] * xn;
+        Zg[k * n + c] = xn;
+        nrm = fmaf(xn, xn, nrm);
+      }
+      const bool good = nrm > 0.f && nrm <= FLT_MAX;
+      const float r = good ? rsqrtf(nrm) : 0.f;
+      for (int k = 0; k < n; ++k) Zg[k * n + c] = good ? Zg[k * n + c] * r : (k == c ? 1.f : 0.f);
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. modified Gram-Schmidt, two passes per vector, descending order
+  for (int j = 0; j < n; ++j) {
+    for (int r = tid; r < n; r += nt) zj[r] = Zg[r * n + j];
+    __syncthreads();
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      // h_i = q_i^T z_j (thread i; rows of consecutive i are contiguous)
+      for (int i = tid; i < j; i += nt) {
+        float h = 0.f;
+        for (int r = 0; r < n; ++r) h = fmaf(Zg[r * n + i], zj[r], h);
+        pv[i] = h;
+      }
+      __syncthreads();
+      // z_j -= sum_i h_i q_i (warp per row, lanes along the row)
+      for (int r = warp; r < n; r += nw) {
+        float acc = 0.f;
+        for (int i = lane; i < j; i += 32) acc = fmaf(Zg[r * n + i], pv[i], acc);
+        acc = warp_sum32(acc);
+        if (lane == 0) zj[r] -= acc;
+      }
+      __syncthreads();
+    }
+    const float nrm = block_sum32(tid < n ? zj[tid] * zj[tid] : 0.f, red);
+    const float rn = nrm > 0.f && nrm <= FLT_MAX ? rsqrtf(nrm) : 0.f;
+    for (int r = tid; r < n; r += nt) Zg[r * n + j] = zj[r] * rn;
+    __syncthreads();
+  }
+
+  // ---- 5. X = Q1 Z: H_k = I - tau_k v_k v_k^T (v_k(0) = 1 at row k + 1, the
+  // rest below the subdiagonal of packed column k), k from n - 3 down to 0;
+  // thread (c, g): column c, rows of class g (mod 4), partial sums in ps
+  {
+    const int c = tid & 255, g = tid >> 8;
+    for (int k = n - 3; k >= 0; --k) {
+      const float t = tau[k];
+      if (t == 0.f) continue;  // the same for every thread
+      const float *v = Ap + packed_col(n, k) + 1;  // v[a] for row k + 1 + a, v[0] = 1
+      const int m = n - k - 1;
+      float s = 0.f;
+      if (c < n)
+        for (int a = g; a < m; a += 4) s = fmaf(v[a], Zg[(k + 1 + a) * n + c], s);
+      ps[g * 256 + c] = s;
+      __syncthreads();
+      if (c < n) {
+        const float f = t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
+        for (int a = g; a < m; a += 4) Zg[(k + 1 + a) * n + c] -= f * v[a];
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    X[r + (int64_t)ldx * c] = (double)Zg[r * n + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // C (M x N) = op(A) B (+ D), float64, column-major.  op(A) = A (M x K, lda) or
 // A^T (A is K x M).  8 x 8 outputs per CTA of 64 threads; the CTA's rows of
 // op(A) and columns of B (K <= 256) are staged in shared memory.  C may alias
@@ -1032,8 +1326,8 @@ constexpr int kGT = 8;
 __global__ void __launch_bounds__(kGT *kGT) k_dgemm_small(int M, int N, int K, const double *__restrict__ A, int lda,
                                                           int transA, const double *__restrict__ B, int ldb,
                                                           const double *D, int ldd, double *C, int ldc) {
-  __shared__ double As[kGT][kMpMaxJ * 2 + 1];
-  __shared__ double Bs[kGT][kMpMaxJ * 2 + 1];
+  __shared__ double As[kGT][kGemmMaxK + 1];
+  __shared__ double Bs[kGT][kGemmMaxK + 1];
   const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
   const int tx = threadIdx.x % kGT, ty = threadIdx.x / kGT;
   for (int e = threadIdx.x; e < kGT * K; e += kGT * kGT) {
@@ -1339,8 +1633,8 @@ struct MpWork {
 
 int gemm(int M, int N, int K, const double *A, int lda, int transA, const double *B, int ldb, const double *D, int ldd,
          double *C, int ldc, cudaStream_t s) {
-  if (K > 2 * kMpMaxJ) {
-    set_error("small GEMM: K = %d exceeds %d", K, 2 * kMpMaxJ);
+  if (K > kGemmMaxK) {
+    set_error("small GEMM: K = %d exceeds %d", K, kGemmMaxK);
     return TUCKER_EINVAL;
   }
   dim3 grid((M + kGT - 1) / kGT, (N + kGT - 1) / kGT);
@@ -1392,7 +1686,12 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
     const char *e = std::getenv("TUCKER_EIG32");
     return e && std::strcmp(e, "jacobi") == 0;
   }();
-  if (use_jacobi) {
+  if (m > kTriMaxJ) {  // the wide stage; E (m x m float64) holds its two float arrays until the first step's E
+    const size_t smemw = wide32_smem(m);
+    TK_CUDA(allow_max_smem(k_eig32_wide));
+    float *zs = reinterpret_cast<float *>(E);
+    k_eig32_wide<<<1, kW32Threads, smemw, s>>>(A, lda, m, tx0 + (size_t)m * m, m, zs, zs + (size_t)m * m);
+  } else if (use_jacobi) {
     const size_t smem32 = jacobi32_smem(m);
     TK_CUDA(allow_max_smem(k_jacobi32));
     k_jacobi32<<<1, kJ32Threads, smem32, s>>>(A, lda, m, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr);
@@ -1477,10 +1776,19 @@ static thread_local double g_mp_check[5];
 
 const double *mp_last_check() { return g_mp_check; }
 
+int mp_max_j() {
+  // J above kTriMaxJ takes the wide float32 stage only with TUCKER_EIG_WIDE=1
+  static const int lim = [] {
+    const char *e = std::getenv("TUCKER_EIG_WIDE");
+    return e && e[0] == '1' ? kMpMaxJ : kTriMaxJ;
+  }();
+  return lim;
+}
+
 int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int *d_info, int *verified,
                   cudaStream_t s, Prof *prof, double tail_budget) {
   *verified = 0;
-  if (J < 1 || J > kMpMaxJ) return TUCKER_OK;
+  if (J < 1 || J > mp_max_j()) return TUCKER_OK;
   const int m = (int)J;
   void *mem = nullptr;
   TK_CUDA(cudaMallocAsync(&mem, MpWork::bytes(m), s));
