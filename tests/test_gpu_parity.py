@@ -15,6 +15,7 @@ Tolerances (derived from the float64 arithmetic; u = 2^-53):
   compared after aligning factor signs, to 1e-10 ||G||.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -147,6 +148,35 @@ def test_eig_random_psd(gpu_lib, eig_path, j):
     rng = np.random.default_rng(j)
     a = rng.standard_normal((j, 2 * j + 3)) * (0.7 ** np.arange(j))[:, None]
     _check_eig(gpu_lib, a @ a.T)
+
+
+WIDE = pytest.mark.skipif(os.environ.get("TUCKER_EIG_WIDE") != "1",
+                          reason="the wide float32 stage (128 < J <= 256) is opt-in: TUCKER_EIG_WIDE=1")
+
+
+@WIDE
+@pytest.mark.parametrize("j,r,floor", [(160, 40, 1e-12), (200, 20, 1e-12), (250, 100, 1e-12), (256, 10, 1e-6)])
+def test_eig_wide_tucker_grams(gpu_lib, monkeypatch, j, r, floor):
+    """The wide float32 stage under the strict check (no fallback) on Grams
+    shaped like Tucker modes: r signal eigenvalues within about 10% of each
+    other over a noise floor holding `floor` of the energy."""
+    monkeypatch.setenv("TUCKER_EIG_KERNEL", "mp")
+    monkeypatch.setenv("TUCKER_EIG_MP_STRICT", "1")
+    rng = np.random.default_rng(j)
+    q, _ = np.linalg.qr(rng.standard_normal((j, j)))
+    sig = 1e4 * (1 + 0.1 * rng.standard_normal(r))
+    lam = np.concatenate([sig, floor * sig.sum() / j * (1 + 0.1 * rng.random(j - r))])
+    s = (q * lam) @ q.T
+    _check_eig(gpu_lib, 0.5 * (s + s.T))
+
+
+@WIDE
+def test_sthosvd_wide_dims(gpu_lib, monkeypatch):
+    """ST-HOSVD with a mode of 200 (the wide stage, strict) against the oracle."""
+    monkeypatch.setenv("TUCKER_EIG_MP_STRICT", "1")
+    dims, ranks = (200, 24, 20), (10, 5, 4)
+    x = tucker_tensor_np(dims, ranks, seed=7, noise=1e-4)
+    compare_sthosvd(gpu_lib, x, dims, 1e-3)
 
 
 @pytest.mark.parametrize("j", [5, 48, 130])
