@@ -1039,11 +1039,13 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
 //      in column k below the subdiagonal.
 //   2. Eigenvalues by multisection on Sturm counts (four threads each).
 //   3. Inverse iteration, thread c for the c-th largest eigenvalue.
-//   4. Modified Gram-Schmidt, two passes per vector, in descending
-//      eigenvalue order: vectors of a cluster become an orthonormal basis of
-//      the complement of the larger ones (the role of the Householder QR in
-//      k_eig32_tri).
-//   5. X = Q1 Z by the reflectors from the last to the first.
+//   4. The Q factor of the vectors' Householder QR in descending eigenvalue
+//      order, signs kept, as in k_eig32_tri: vectors of a cluster become an
+//      orthonormal basis of the complement of the larger ones.  (Modified
+//      Gram-Schmidt, even twice, loses orthogonality on strongly graded
+//      spectra, where many vectors come out nearly parallel.)
+//   5. X = Q1 Q by the reflectors from the last to the first.
+// Every reflector is LAPACK's larfg with the scaled norm of tri_reflect.
 // Writes X (float64, columns in descending eigenvalue order).
 // ---------------------------------------------------------------------------
 constexpr int kW32Threads = 1024;
@@ -1068,6 +1070,58 @@ __device__ __forceinline__ float block_sum32(float v, float *red) {
   }
   __syncthreads();
   return red[32];
+}
+
+__device__ __forceinline__ float block_max32(float v, float *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    float t = lane < nw ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+struct Refl {
+  float t, beta, scal;
+};
+
+// LAPACK's larfg for x[0..m-1] in shared memory (m <= blockDim), every
+// thread taking part and getting the same result: H x = beta e_1 with
+// H = I - t v v^T, v(0) = 1, v(1..) = x(1..) scal.  As in tri_reflect,
+// entries of x(1..) below 2^-100 count as zero (t = 0), and below 2^-40 the
+// norm is formed from x / max|x|, so that no square that matters is
+// subnormal (H stays orthogonal).  x[0] is read before the first barrier:
+// the caller may overwrite x once this returns.
+__device__ Refl wide_larfg(const float *x, int m, float *red) {
+  const int tid = threadIdx.x;
+  const float alpha = x[0];
+  const float xi = (tid >= 1 && tid < m) ? x[tid] : 0.f;
+  const float mx = block_max32(fabsf(xi), red);
+  const float sq = block_sum32(xi * xi, red);
+  Refl h{0.f, alpha, 0.f};
+  if (mx > 0x1p-100f) {  // the same in every thread
+    float nrm;
+    if (mx >= 0x1p-40f) {
+      nrm = sqrtf(fmaf(alpha, alpha, sq));
+    } else {
+      const float sv = fmaxf(mx, fabsf(alpha)), sx = 1.f / sv;
+      const float v = xi * sx;
+      const float sg = block_sum32(v * v, red);
+      const float aa = alpha * sx;
+      nrm = sv * sqrtf(fmaf(aa, aa, sg));
+    }
+    h.beta = alpha >= 0.f ? -nrm : nrm;
+    h.t = fmaf(-alpha, __frcp_rn(h.beta), 1.f);
+    h.scal = __frcp_rn(alpha - h.beta);
+  }
+  return h;
 }
 
 __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__restrict__ A, int lda, int n,
@@ -1116,25 +1170,15 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__r
   for (int k = 0; k + 2 < n; ++k) {
     float *colk = Ap + packed_col(n, k);  // rows k..n-1 of column k
     const int m = n - k - 1;              // rows k+1..n-1: x, then v
-    float xv = (tid >= 1 && tid < m) ? colk[1 + tid] : 0.f;
-    const float sig = block_sum32(xv * xv, red);
+    const Refl h = wide_larfg(colk + 1, m, red);
     if (tid == 0) {
-      const float alpha = colk[1];
-      float t = 0.f, beta = alpha, scale = 0.f;
-      if (sig > 0.f) {
-        beta = -copysignf(sqrtf(fmaf(alpha, alpha, sig)), alpha);
-        t = (beta - alpha) / beta;
-        scale = 1.f / (alpha - beta);
-      }
       d[k] = colk[0];
-      e[k] = beta;
-      tau[k] = t;
-      sc[1] = scale;
+      e[k] = h.beta;
+      tau[k] = h.t;
     }
+    if (tid < m) colk[1 + tid] = tid == 0 ? 1.f : colk[1 + tid] * h.scal;
     __syncthreads();
-    if (tid < m) colk[1 + tid] = tid == 0 ? 1.f : colk[1 + tid] * sc[1];
-    __syncthreads();
-    const float t = tau[k];
+    const float t = h.t;
     const float *v = colk + 1;  // v[a], row k + 1 + a
     // p = t A22 v: four threads per row a, columns b = part (mod 4)
     {
@@ -1261,34 +1305,64 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__r
   }
   __syncthreads();
 
-  // ---- 4. modified Gram-Schmidt, two passes per vector, descending order
-  for (int j = 0; j < n; ++j) {
-    for (int r = tid; r < n; r += nt) zj[r] = Zg[r * n + j];
-    __syncthreads();
-    for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      // h_i = q_i^T z_j (thread i; rows of consecutive i are contiguous)
-      for (int i = tid; i < j; i += nt) {
-        float h = 0.f;
-        for (int r = 0; r < n; ++r) h = fmaf(Zg[r * n + i], zj[r], h);
-        pv[i] = h;
-      }
+  // ---- 4. Z <- Q of Z = Q R (Householder, columns in descending eigenvalue
+  // order), signs kept: reflector j from column j's rows j.. (v below the
+  // diagonal of Z's column j, tau in qt[j], sign of R(j, j) in qs[j]),
+  // applied to the columns after j by threads (c, g): column c, rows of
+  // class g (mod 4); then Q = H_0 ... H_{n-1} I in Lg (the L factors are
+  // spent), each H_j touching only rows and columns from j on.
+  float *qt = lam, *qs = e2;  // spent after steps 2 and 3
+  {
+    const int c = tid & 255, g = tid >> 8;
+    for (int j = 0; j < n; ++j) {
+      const int mj = n - j;
+      for (int r = tid; r < mj; r += nt) zj[r] = Zg[(j + r) * n + j];
       __syncthreads();
-      // z_j -= sum_i h_i q_i (warp per row, lanes along the row)
-      for (int r = warp; r < n; r += nw) {
-        float acc = 0.f;
-        for (int i = lane; i < j; i += 32) acc = fmaf(Zg[r * n + i], pv[i], acc);
-        acc = warp_sum32(acc);
-        if (lane == 0) zj[r] -= acc;
+      const Refl h = wide_larfg(zj, mj, red);
+      if (tid == 0) {
+        qt[j] = h.t;
+        qs[j] = h.beta < 0.f ? -1.f : 1.f;
+      }
+      if (tid < mj) zj[tid] = tid == 0 ? 1.f : zj[tid] * h.scal;
+      __syncthreads();
+      if (tid >= 1 && tid < mj) Zg[(j + tid) * n + j] = zj[tid];
+      if (h.t != 0.f) {  // the same in every thread
+        float sum = 0.f;
+        if (c > j && c < n)
+          for (int a = g; a < mj; a += 4) sum = fmaf(zj[a], Zg[(j + a) * n + c], sum);
+        ps[g * 256 + c] = sum;
+        __syncthreads();
+        if (c > j && c < n) {
+          const float f = h.t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
+          for (int a = g; a < mj; a += 4) Zg[(j + a) * n + c] -= f * zj[a];
+        }
       }
       __syncthreads();
     }
-    const float nrm = block_sum32(tid < n ? zj[tid] * zj[tid] : 0.f, red);
-    const float rn = nrm > 0.f && nrm <= FLT_MAX ? rsqrtf(nrm) : 0.f;
-    for (int r = tid; r < n; r += nt) Zg[r * n + j] = zj[r] * rn;
+    for (int idx = tid; idx < n * n; idx += nt) Lg[idx] = idx / n == idx % n ? 1.f : 0.f;
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+      const float t = qt[j];
+      if (t == 0.f) continue;  // the same in every thread
+      const int mj = n - j;
+      for (int r = tid; r < mj; r += nt) zj[r] = r == 0 ? 1.f : Zg[(j + r) * n + j];
+      __syncthreads();
+      float sum = 0.f;
+      if (c >= j && c < n)
+        for (int a = g; a < mj; a += 4) sum = fmaf(zj[a], Lg[(j + a) * n + c], sum);
+      ps[g * 256 + c] = sum;
+      __syncthreads();
+      if (c >= j && c < n) {
+        const float f = t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
+        for (int a = g; a < mj; a += 4) Lg[(j + a) * n + c] -= f * zj[a];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < n * n; idx += nt) Lg[idx] *= qs[idx % n];
     __syncthreads();
   }
 
-  // ---- 5. X = Q1 Z: H_k = I - tau_k v_k v_k^T (v_k(0) = 1 at row k + 1, the
+  // ---- 5. X = Q1 Q (Q in Lg): H_k = I - tau_k v_k v_k^T (v_k(0) = 1 at row k + 1, the
   // rest below the subdiagonal of packed column k), k from n - 3 down to 0;
   // thread (c, g): column c, rows of class g (mod 4), partial sums in ps
   {
@@ -1300,19 +1374,19 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__r
       const int m = n - k - 1;
       float s = 0.f;
       if (c < n)
-        for (int a = g; a < m; a += 4) s = fmaf(v[a], Zg[(k + 1 + a) * n + c], s);
+        for (int a = g; a < m; a += 4) s = fmaf(v[a], Lg[(k + 1 + a) * n + c], s);
       ps[g * 256 + c] = s;
       __syncthreads();
       if (c < n) {
         const float f = t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
-        for (int a = g; a < m; a += 4) Zg[(k + 1 + a) * n + c] -= f * v[a];
+        for (int a = g; a < m; a += 4) Lg[(k + 1 + a) * n + c] -= f * v[a];
       }
       __syncthreads();
     }
   }
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx % n, c = idx / n;
-    X[r + (int64_t)ldx * c] = (double)Zg[r * n + c];
+    X[r + (int64_t)ldx * c] = (double)Lg[r * n + c];
   }
 }
 
