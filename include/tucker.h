@@ -28,9 +28,10 @@
  * - Inputs are never modified.  Errors are reported only through the returned
  *   tucker_status (never by exceptions, exit() or a device trap); the text of
  *   the last error of the calling thread is available from tucker_last_error().
- * - Device kernels contain no unbounded waits: the only iterative kernel (the
- *   Jacobi eigensolver) stops after a fixed number of sweeps and reports
- *   TUCKER_ENOCONV.
+ * - Device kernels contain no unbounded waits: the Jacobi eigensolver stops
+ *   after a fixed number of sweeps (TUCKER_ENOCONV), and every wait of the
+ *   tensor-core kernels gives up after a bounded time, sets an error flag and
+ *   returns (TUCKER_ETIMEOUT).
  */
 #ifndef TUCKER_GB300_H
 #define TUCKER_GB300_H
@@ -58,7 +59,7 @@ typedef enum {
   TUCKER_ENOMEM = -2,      /* device or pinned host allocation failed */
   TUCKER_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
   TUCKER_ENOCONV = -4,     /* Jacobi eigensolver hit its sweep cap */
-  TUCKER_ETIMEOUT = -5,    /* reserved: a bounded device wait expired */
+  TUCKER_ETIMEOUT = -5,    /* a bounded device wait of a tensor-core kernel expired */
   TUCKER_ENONFINITE = -6,  /* input holds Inf/NaN (||X||^2 is not finite) */
   TUCKER_EUNSUPPORTED = -7 /* valid request the library does not implement */
 } tucker_status;
@@ -66,14 +67,25 @@ typedef enum {
 /* Element type of an input tensor.  Internal tensors are always float64. */
 typedef enum { TUCKER_F64 = 0, TUCKER_F32 = 1 } tucker_dtype;
 
-/* Arithmetic of the Gram step.  TUCKER_PREC_FP64 is the plain method.
- * TUCKER_PREC_BF16X4 forms each Gram on the BF16 tensor cores from four exact
- * 7-bit integer slices of every entry (28 bits below a power-of-two bound of
- * max|Y|), with exact FP32 accumulation in tensor memory and float64
- * reduction (see tucker_gram_split); eigensolve and rank rule stay
- * float64 while the TTM also runs on the tensor cores (see tucker_ttm_split).
- * It needs I_n <= 128 at every mode. */
+/* Arithmetic of the Gram and mode-product steps.  TUCKER_PREC_FP64 is the
+ * plain method.  TUCKER_PREC_BF16X4 ("BF16 digits") runs both on the BF16
+ * tensor cores with exact integer digits: the Gram rounds every entry to 21
+ * bits below the power of two above its row's largest magnitude in a group
+ * of 512 columns and splits it into three balanced 7-bit digits (see
+ * tucker_gram_split); the mode product rounds each column of the unfolding
+ * and of U_n to 28 bits and splits them into four digits (see
+ * tucker_ttm_split).  Digit products accumulate exactly in FP32 tensor
+ * memory and are reduced in float64; ||X||^2, the eigensolver and the rank
+ * rule stay float64.  The name counts the four digit tiles each operand
+ * stage holds.  It needs I_n <= 128 at every mode. */
 typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_BF16X4 = 1 } tucker_precision;
+
+/* Which eigensolver produced a mode's eigenpairs (tucker_result.eig_path). */
+typedef enum {
+  TUCKER_EIG_MIXED = 0,          /* mixed-precision solver, result verified on the device */
+  TUCKER_EIG_JACOBI = 1,         /* float64 Jacobi (J outside the mixed-precision range, or forced) */
+  TUCKER_EIG_JACOBI_FALLBACK = 2 /* float64 Jacobi after the mixed-precision result failed its check */
+} tucker_eig_path;
 
 /* Result of an ST-HOSVD (Algorithm 1's output (G, {U_n}) plus diagnostics).
  * Owned by the library; release with tucker_result_free(). */
@@ -96,6 +108,10 @@ typedef struct tucker_result {
   double tail[TUCKER_MAX_MODES];      /* discarded eigenvalue sum per mode (clamped at 0) */
   double norm2_x;                     /* ||X||^2 */
   double threshold;                   /* eps^2 ||X||^2 / N (0 when eps <= 0) */
+  int eig_path[TUCKER_MAX_MODES];     /* tucker_eig_path of each mode's eigensolve */
+  int eig_resolved[TUCKER_MAX_MODES]; /* leading eigenvalues of mode n resolved one by one (I_n unless a
+                                         tail cluster was left unresolved; eigvals past this count are
+                                         Rayleigh quotients whose sum is exact) */
   void *priv;                         /* library bookkeeping; do not touch */
 } tucker_result;
 
@@ -341,6 +357,16 @@ TUCKER_API const char *tucker_status_string(int status);
 TUCKER_API const char *tucker_last_error(void);
 /* Number of kernels this library has launched in this process. */
 TUCKER_API int64_t tucker_launch_count(void);
+
+/* Float64 throughput of the current GPU: a register-resident loop of
+ * independent fused multiply-adds (no memory traffic) over every SM, timed
+ * with CUDA events on `stream` after one untimed launch.  The float64 phases
+ * of Algorithm 1 (Gram, mode products, eigensolver refinement) are bound by
+ * this rate, so it is the roofline peak they are reported against.
+ *   tflops  host double: 2 x fused multiply-adds / time, in TFLOP/s.
+ *   ms      host double (may be NULL): duration of the timed launch.
+ * Synchronises `stream`.  No counterpart in the paper (a measurement aid). */
+TUCKER_API int tucker_fp64_peak(double *tflops, double *ms, void *stream);
 
 /* Per-phase device timing with CUDA events recorded on the caller's stream. */
 typedef enum {

@@ -34,11 +34,13 @@ Readings of points the paper leaves open:
   normalised RMS error is ||X - X~|| / ||X||, formed from the explicit
   difference.  A subtensor uses the same product with row subsets of the
   factors (Sec. 2.3).
-* HOOI (Algorithm 2): ranks fixed by the ST-HOSVD that starts it; within an
-  iteration every mode uses the factors already updated in that iteration
-  (the loop of Algorithm 2 as printed); the stopping test "||X||^2 - ||G||^2
-  ceases to decrease" is read as: stop after an iteration whose decrease is
-  at most tol ||X||^2 (tol = 0: no decrease at all), or after max_iters.
+* HOOI (Sec. 2.2; Algorithm 2 is the source): alternating best rank-R_n
+  subspaces, each factor the leading left singular subspace of X projected on
+  the other factors' latest values; ranks fixed by the ST-HOSVD that starts
+  it; the core is X projected on all factors.  The stopping test
+  "||X||^2 - ||G||^2 ceases to decrease" is read as: stop after an iteration
+  whose decrease is at most tol ||X||^2 (tol = 0: no decrease at all), or
+  after max_iters.
 * Mode-order flop model (the ST-HOSVD cost of Sec. 6.1 with P = 1): the step on
   mode n, with J the product of the current dimensions, costs
   2 I_n J (Gram) + 2 R_n J (TTM) + 10/3 I_n^3 (eigenvectors); J then shrinks
@@ -233,8 +235,26 @@ def reconstruct_sub(core_flat, ranks, factors, lo, hi):
     return np.asarray(g).ravel(order="F")
 
 
+def _project(x, factors, skip=None):
+    """X x_m U_m^T over every mode m except `skip` (Sec. 2.1 mode products)."""
+    y = x
+    for m, u in enumerate(factors):
+        if m != skip:
+            y = ttm(y, m, u.T)
+    return y
+
+
 def hooi(x_flat, dims, eps, max_iters=10, tol=0.0, order=None):
-    """Algorithm 2 (HOOI), started from Algorithm 1 with the same eps.
+    """HOOI (Sec. 2.2, Algorithm 2), started from Algorithm 1 with the same eps.
+
+    HOOI maximises ||G|| = ||X x_1 U_1^T ... x_N U_N^T|| over factors with
+    orthonormal columns, one factor at a time.  With every other factor
+    fixed, the best U_n is the leading R_n-dimensional left singular subspace
+    of W_(n), W = X x_{m != n} U_m^T, i.e. the leading eigenvectors of the
+    Gram W_(n) W_(n)^T.  One iteration updates U_1, ..., U_N in turn, each
+    against the others' latest values; the core for the final factors is the
+    projection G = X x {U_m^T}.  Since ||X - X~||^2 = ||X||^2 - ||G||^2 for
+    orthonormal factors, the fit ||X||^2 - ||G||^2 never increases.
 
     Returns the ST-HOSVD dict updated with the refined core and factors, the
     fit history ||X||^2 - ||G||^2 (one value for the start and one per
@@ -247,25 +267,22 @@ def hooi(x_flat, dims, eps, max_iters=10, tol=0.0, order=None):
     x = as_tensor(x_flat, dims)
     nx2 = res["norm2"]
     factors = [u.copy() for u in res["factors"]]
-    core = as_tensor(res["core"], ranks)
-    history = [nx2 - norm2(core)]
+    history = [nx2 - norm2(as_tensor(res["core"], ranks))]
     iters = 0
     for _ in range(max_iters):
         for n in range(n_modes):
-            y = x
-            for m in range(n_modes):  # Y = X x {U_m^T}, m != n
-                if m != n:
-                    y = ttm(y, m, factors[m].T)
-            _, v = leading_eigenpairs(gram(y, n))
+            w = _project(x, factors, skip=n)
+            _, v = leading_eigenpairs(gram(w, n))
             factors[n] = v[:, : ranks[n]].copy()
-        core = ttm(y, n_modes - 1, factors[n_modes - 1].T)  # the last Y of the loop
+        core = _project(x, factors)
         iters += 1
         history.append(nx2 - norm2(core))
         if history[-2] - history[-1] <= tol * nx2:
             break
     out = dict(res)
     out["factors"] = factors
-    out["core"] = np.asarray(core).ravel(order="F").copy()
+    if iters:
+        out["core"] = np.asarray(core).ravel(order="F").copy()
     out["history"] = history
     out["iters"] = iters
     return out

@@ -148,9 +148,10 @@ int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const 
 int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
                      double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof,
                      const int *d_colexp = nullptr);
-// Jacobi eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
-// matrix fits in shared memory).  d_info[0] = sweeps, d_info[1] = 0 if
-// converged else 1.
+// Eigensolver.  d_ws holds eig_workspace_doubles(J) doubles (0 when the
+// matrix fits in shared memory).  d_info holds 4 ints: [0] Jacobi sweeps,
+// [1] 0 if converged else 1, [2] the tucker_eig_path that ran, [3] the
+// number of leading eigenvalues resolved one by one.
 int64_t eig_workspace_doubles(int64_t J);
 // tail_budget >= 0 (the rank rule's threshold) lets the mixed-precision
 // solver leave clusters unresolved whose eigenvalues, with all smaller ones,
@@ -171,6 +172,9 @@ const double *mp_last_check();
 // Largest J the mixed-precision eigensolver takes: 128, or 256 with
 // TUCKER_EIG_WIDE=1 (the wide float32 stage).
 int mp_max_j();
+// Float64 fused multiply-add throughput of the device (TFLOP/s) and the timed
+// launch's duration; synchronises s.
+int fp64_peak(double *tflops, double *ms, const DeviceInfo &dev, cudaStream_t s);
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

@@ -711,6 +711,15 @@ static bool dsm_cluster_ok(size_t dsmem) {
   return ok;
 }
 
+namespace {
+__global__ void k_eig_tag(int *info, int path, int resolved) {
+  if (threadIdx.x == 0) {
+    info[2] = path;
+    info[3] = resolved;
+  }
+}
+}  // namespace
+
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof, double tail_budget) {
   const int64_t m = J + (J & 1);
@@ -721,6 +730,11 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
   const bool use_dsm = ev && !strcmp(ev, "dsm");
   const bool use_l2 = ev && !strcmp(ev, "l2");
   const bool jacobi_only = ev && (use_dsm || use_l2 || !strcmp(ev, "jacobi") || !strcmp(ev, "l2m"));
+  // d_info[2] records which solver ran (tucker_eig_path), d_info[3] how many
+  // leading eigenvalues were resolved one by one (the mixed-precision path
+  // writes both itself)
+  const int path_jacobi[1] = {TUCKER_EIG_JACOBI}, path_fallback[1] = {TUCKER_EIG_JACOBI_FALLBACK};
+  const int *path = path_jacobi;
   if (!jacobi_only && J <= mp_max_j()) {
     int verified = 0;
     TK_CHECK(launch_eig_mp(d_S, J, d_lam, d_V, d_info, &verified, s, prof, tail_budget));
@@ -733,7 +747,10 @@ int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double 
                 (long long)J, c[0], c[1], c[2], c[3], (int)c[4]);
       return TUCKER_ENOCONV;
     }
+    path = path_fallback;
   }
+  k_eig_tag<<<1, 32, 0, s>>>(d_info, path[0], (int)J);
+  TK_LAUNCHED();
   if (J > kOneCtaMaxJ && J <= kDsmMaxJ && !use_l2 && (use_dsm || d_ws)) {
     const size_t dsmem = use_dsm ? (size_t)((m * (m + 1) / 2 + m * m + 15) / 16) * sizeof(double) : 0;
     if (use_dsm ? dsm_cluster_ok<false>(dsmem) : dsm_cluster_ok<true>(0)) {

@@ -1575,8 +1575,12 @@ __global__ void __launch_bounds__(kStatThreads) k_oa_E(const double *__restrict_
     if (Xp) Xp[e] = X[a + (int64_t)m * j];
     const double r = (i == j ? 1.0 : 0.0) - P[i + (int64_t)m * j];
     double v;
+    // S = X^T A X is symmetric in exact arithmetic; its computed form is not
+    // (rounding of order m u ||A||).  Only its symmetric part enters E:
+    // otherwise that asymmetry, divided by the gap lam_j - lam_i, leaves
+    // E + E^T != R and the step cannot restore orthogonality.
     if (a == b || lab[a] == lab[b]) v = 0.5 * r;
-    else v = (S[i + (int64_t)m * j] + lam[j] * r) / (lam[j] - lam[i]);
+    else v = (0.5 * (S[i + (int64_t)m * j] + S[j + (int64_t)m * i]) + lam[j] * r) / (lam[j] - lam[i]);
     E[e] = v;
   }
 }
@@ -1906,7 +1910,7 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   g_mp_check[3] = tol_orth;
   g_mp_check[4] = skipped;
   if (chk[0] <= tol_res && chk[1] <= tol_orth) {
-    const int info[2] = {sw, 0};
+    const int info[4] = {sw, 0, TUCKER_EIG_MIXED, m - skipped};
     TK_CUDA(cudaMemcpyAsync(d_info, info, sizeof info, cudaMemcpyHostToDevice, s));
     TK_CUDA(cudaStreamSynchronize(s));
     *verified = 1;

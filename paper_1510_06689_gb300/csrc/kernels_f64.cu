@@ -12,6 +12,8 @@
 // memory.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -476,6 +478,70 @@ int launch_norm2(const void *x, tucker_dtype dt, int64_t n, double *d_partials, 
   return TUCKER_OK;
 }
 
+// ---------------------------------------------------------------------------
+// float64 throughput probe: kPeakChains independent fused multiply-add chains
+// per thread in registers (no memory traffic inside the loop), enough in
+// flight to hide the pipe's latency; x <- x m + c with m < 1 stays bounded.
+// The sum is stored so the loop is not removed.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kPeakChains = 8;
+constexpr int kPeakIters = 4096;
+constexpr int kPeakThreads = 512;
+
+__global__ void __launch_bounds__(kPeakThreads) k_fp64_peak(double m, double c, double *__restrict__ out) {
+  double x[kPeakChains];
+#pragma unroll
+  for (int k = 0; k < kPeakChains; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+#pragma unroll 4
+  for (int it = 0; it < kPeakIters; ++it)
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) x[k] = fma(x[k], m, c);
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < kPeakChains; ++k) t += x[k];
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+}  // namespace
+
+int fp64_peak(double *tflops, double *ms_out, const DeviceInfo &dev, cudaStream_t s) {
+  int occ = 0;
+  TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fp64_peak, kPeakThreads, 0));
+  const int blocks = dev.sms * std::max(occ, 1) * 4;  // four full waves
+  double *out = nullptr;
+  TK_CUDA(cudaMallocAsync(&out, sizeof(double) * blocks, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = TUCKER_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("cudaEventCreate failed");
+    st = TUCKER_ECUDA;
+  }
+  float ms = 0.f;
+  for (int rep = 0; rep < 2 && st == TUCKER_OK; ++rep) {  // the first launch is untimed
+    cudaEventRecord(e0, s);
+    k_fp64_peak<<<blocks, kPeakThreads, 0, s>>>(0.999999, 1e-7, out);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("float64 probe launch failed");
+      st = TUCKER_ECUDA;
+      break;
+    }
+    bump_launches();
+    cudaEventRecord(e1, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      set_error("float64 probe timing failed");
+      st = TUCKER_ECUDA;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  if (st != TUCKER_OK) return st;
+  const double flops = 2.0 * kPeakChains * (double)kPeakIters * kPeakThreads * blocks;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  if (ms_out) *ms_out = ms;
+  return TUCKER_OK;
+}
+
 int64_t gram_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
   GramPlan p = gram_plan(L, J, B, dev);
   return (int64_t)std::max(p.nsplit, 1) * p.n_micro * 16;
@@ -574,12 +640,18 @@ int gram_noalloc_typed(const T *y, int64_t L, int64_t J, int64_t B, double *d_S,
               (long long)J, (long long)(per_split * 8), (long long)TUCKER_NOALLOC_SCRATCH_BYTES);
     return TUCKER_EINVAL;
   }
+  const int planned = p.nsplit;
   if (p.nsplit > max_splits) {  // fewer, longer column ranges so the partials fit
     const int64_t chunks = (p.K + p.kc - 1) / p.kc;
     const int64_t chunks_per = (chunks + max_splits - 1) / max_splits;
     p.cols_per_split = chunks_per * p.kc;
     p.nsplit = (int)((p.K + p.cols_per_split - 1) / p.cols_per_split);
   }
+  // TUCKER_NOALLOC_TRACE=1 prints the split plan (tests use it to reach the capped case)
+  const char *trace = getenv("TUCKER_NOALLOC_TRACE");
+  if (trace && trace[0] == '1')
+    fprintf(stderr, "tucker_gram_noalloc: J=%lld planned_splits=%d scratch_fits=%lld used_splits=%d\n",
+            (long long)J, planned, (long long)max_splits, p.nsplit);
   double *ws = nullptr;
   TK_CHECK(noalloc_scratch(&ws));
   TK_CHECK(set_smem(k_gram_partial<T>, p.smem, dev));

@@ -305,6 +305,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   TK_CHECK(S.alloc(sizeof(double) * maxJ * maxJ, s));
   TK_CHECK(lam.alloc(sizeof(double) * maxJ, s));
   TK_CHECK(V.alloc(sizeof(double) * maxJ * maxJ, s));
+  // scal: ||X||^2 | tail | rank | eigensolver info (4 ints) | spare | TTM error flag
   double *d_nx2 = scal.as<double>();
   double *d_tail = d_nx2 + 1;
   int64_t *d_rank = reinterpret_cast<int64_t *>(d_nx2 + 2);
@@ -405,7 +406,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
                         d_info, s, &prof, keep_all ? -1.0 : threshold));
     // rank step
     TK_CHECK(launch_rank_cut(lam.as<double>(), J, threshold, keep_all, d_rank, d_tail, s, &prof));
-    TK_CUDA(cudaMemcpyAsync(h, d_tail, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaMemcpyAsync(h, d_tail, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(h + 8, lam.as<double>(), sizeof(double) * J, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
     if (prec == TUCKER_PREC_BF16X4 && reinterpret_cast<int *>(h + 5)[0] != 0) {
@@ -414,7 +415,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     }
     const double tail = h[0];
     int64_t R;
-    int info[2];
+    int info[4];  // sweeps, not converged, eigensolver path, resolved count
     memcpy(&R, h + 1, sizeof R);
     memcpy(info, h + 2, sizeof info);
     if (info[1] != 0 || fault_injection("noconv")) {
@@ -435,6 +436,8 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     out->ranks[n] = R;
     out->tail[n] = tail;
     out->sweeps[n] = info[0];
+    out->eig_path[n] = info[2];
+    out->eig_resolved[n] = info[3];
 
     // factor U_n = leading R eigenvectors (first R columns of V)
     TK_CHECK(factor_bufs[n].alloc(sizeof(double) * J * R, s));
@@ -453,6 +456,9 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     else
       TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(),
                           dev, s, &prof));
+    // TUCKER_FAULT=timeout: raise the error flag a tensor-core wait raises on
+    // expiry (host-side injection; no kernel is made to stall)
+    if (fault_injection("timeout")) TK_CUDA(cudaMemsetAsync(d_terr, 1, 1, s));
     ybuf.reset();
     ybuf.p = ynew.release();
     ybuf.s = s;
@@ -465,7 +471,8 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   TK_CUDA(cudaStreamSynchronize(s));
   prof.flush();
   if (terr) {
-    set_error("split-precision TTM: a bounded tensor-core wait expired");
+    set_error("a bounded tensor-core wait expired (split-precision mode product)%s",
+              fault_injection("timeout") ? " [injected by TUCKER_FAULT=timeout]" : "");
     return TUCKER_ETIMEOUT;
   }
   out->core = static_cast<double *>(ybuf.release());
@@ -563,8 +570,8 @@ static int hooi_iterate(const void *X, tucker_dtype dt, int max_iters, double to
   TK_CHECK(partials.alloc(sizeof(double) * norm2_partials(), s));
   TK_CHECK(scal.alloc(64, s));
   double *d_g2 = scal.as<double>();
-  int *d_info = reinterpret_cast<int *>(d_g2 + 1);
-  int *d_terr = reinterpret_cast<int *>(d_g2 + 2);
+  int *d_info = reinterpret_cast<int *>(d_g2 + 1);  // 4 ints
+  int *d_terr = reinterpret_cast<int *>(d_g2 + 4);
   TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
   const double nx2 = out->norm2_x;
   auto core_fit = [&](double *f) -> int {
@@ -751,6 +758,17 @@ const char *tucker_status_string(int status) {
 const char *tucker_last_error(void) { return g_err; }
 
 int64_t tucker_launch_count(void) { return g_launches.load(); }
+
+int tucker_fp64_peak(double *tflops, double *ms, void *stream) {
+  g_err[0] = 0;
+  if (!tflops) {
+    set_error("tflops is NULL");
+    return TUCKER_EINVAL;
+  }
+  DeviceInfo dev;
+  TK_CHECK(device_info(&dev));
+  return fp64_peak(tflops, ms, dev, static_cast<cudaStream_t>(stream));
+}
 
 void tucker_profile_enable(int on) {
   std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -1223,7 +1241,7 @@ int tucker_eig(const double *S, int64_t J, double *lam, double *V, int *sweeps, 
   DevBuf ws, info;
   const int64_t ews = eig_workspace_doubles(J);
   if (ews > 0) TK_CHECK(ws.alloc(sizeof(double) * ews, s));
-  TK_CHECK(info.alloc(2 * sizeof(int), s));
+  TK_CHECK(info.alloc(4 * sizeof(int), s));
   TK_CHECK(launch_eig(S, J, lam, V, ews > 0 ? ws.as<double>() : nullptr, info.as<int>(), s, &prof));
   int h[2];
   TK_CUDA(cudaMemcpyAsync(h, info.p, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -28,8 +28,9 @@ EXPORTS = (
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
-    "tucker_mode_order", "tucker_sthosvd_batched",
+    "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak",
 )
+EIG_PATHS = ("mixed", "jacobi", "jacobi_fallback")
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
 
 
@@ -53,6 +54,8 @@ class _Result(ctypes.Structure):
         ("tail", ctypes.c_double * MAX_MODES),
         ("norm2_x", ctypes.c_double),
         ("threshold", ctypes.c_double),
+        ("eig_path", ctypes.c_int * MAX_MODES),
+        ("eig_resolved", ctypes.c_int * MAX_MODES),
         ("priv", ctypes.c_void_p),
     ]
 
@@ -104,6 +107,7 @@ def load(path=LIB_PATH):
         "tucker_launch_count": (i64, []),
         "tucker_profile_enable": (None, [i32]),
         "tucker_profile_read": (None, [ctypes.POINTER(_Profile)]),
+        "tucker_fp64_peak": (i32, [pdbl, pdbl, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -173,6 +177,8 @@ class Result:
         self.threshold = raw.threshold
         self.on_host = bool(raw.on_host)
         self.eigvals = [[raw.eigvals[i][k] for k in range(self.dims[i])] for i in range(n)]
+        self.eig_paths = tuple(EIG_PATHS[raw.eig_path[i]] for i in range(n))
+        self.eig_resolved = tuple(raw.eig_resolved[i] for i in range(n))
 
     @property
     def raw(self):
@@ -366,6 +372,14 @@ def gram_noalloc(y, L, J, B, out=None, stream=None):
     library (its split-K scratch is a static device array).  ``out`` (J x J
     float64, caller-allocated) receives S when given."""
     lib = load()
+    L, J, B = int(L), int(J), int(B)
+    # the C side cannot see a tensor's type or size: a wrong `out` or a short `y`
+    # would become an out-of-bounds device access, so they are checked here
+    if y.numel() < L * J * B:
+        raise TuckerError(-1, f"y holds {y.numel()} elements, the ({L}, {J}, {B}) view needs {L * J * B}")
+    if out is not None:
+        if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.numel() != J * J:
+            raise TuckerError(-1, "out must be a contiguous float64 CUDA tensor of J*J elements")
     s = out if out is not None else torch.empty((J, J), dtype=torch.float64, device="cuda")
     _check(lib.tucker_gram_noalloc(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
                                    _stream(stream)))
@@ -444,3 +458,10 @@ def profile_read():
 
 def launch_count():
     return int(load().tucker_launch_count())
+
+
+def fp64_peak(stream=None):
+    """(TFLOP/s, ms) of the library's float64 fused multiply-add probe on the current GPU."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().tucker_fp64_peak(ctypes.byref(tf), ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value

@@ -165,3 +165,19 @@ def test_batched_arguments_rejected_on_host(lib):
     assert lib.tucker_sthosvd_batched(null_x, 0, good, 3, 2, 1e-3, 0, 0, None, res) == -1
     assert lib.tucker_sthosvd_batched(fake, 0, good, 3, 2, 1e-3, 0, 65, None, res) == -1  # too many workers
     assert lib.tucker_sthosvd_batched(fake, 0, good, 3, 0, 1e-3, 0, 0, None, res) == 0    # nothing to do
+
+
+def test_gram_noalloc_binding_checks_buffers_before_the_call(lib):
+    """The C side cannot see a tensor's type or size, so the binding rejects a
+    wrong output buffer or a short input before calling it."""
+    import torch
+
+    from paper_1510_06689_gb300 import tucker
+
+    y = torch.zeros(4 * 5 * 6, dtype=torch.float64)
+    with pytest.raises(tucker.TuckerError, match="elements"):
+        tucker.gram_noalloc(y[:-1], 4, 5, 6)
+    for bad in (torch.zeros((5, 5), dtype=torch.float32), torch.zeros((4, 5), dtype=torch.float64),
+                torch.zeros((5, 5), dtype=torch.float64), torch.zeros((5, 10), dtype=torch.float64)[:, ::2]):
+        with pytest.raises(tucker.TuckerError, match="out must be"):
+            tucker.gram_noalloc(y, 4, 5, 6, out=bad)

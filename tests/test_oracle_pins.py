@@ -422,6 +422,21 @@ def test_order_flops_hand_count():
     assert osth.best_order((4, 6), (2, 3)) == [0, 1]
 
 
+def test_greedy_flops_order_hand_count():
+    # dims (5, 4, 3), ranks (1, 4, 2): the cost of a step on mode n is
+    # 2 I_n J + 2 R_n J + 10/3 I_n^3 with J the product of the current dims.
+    # Step 1, J = 60: mode 0: 600 + 120 + 416.67 = 1136.67; mode 1: 480 + 480 +
+    #   213.33 = 1173.33; mode 2: 360 + 240 + 90 = 690 -> mode 2, J becomes 5*4*2 = 40.
+    # Step 2, J = 40: mode 0: 400 + 80 + 416.67 = 896.67; mode 1: 320 + 320 +
+    #   213.33 = 853.33 -> mode 1 (with J left at 60 it would be mode 0).
+    # Step 3: mode 0.
+    assert osth.greedy_order((5, 4, 3), (1, 4, 2), "flops") == [2, 1, 0]
+    # step 3 at J = 5*4*2 = 40: 400 + 80 + 416.67; total 690 + 853.33 + 896.67 = 2440
+    assert osth.order_flops((5, 4, 3), (1, 4, 2), (2, 1, 0)) == pytest.approx(2440.0)
+    # ratio rule: I_n / R_n = 5, 1, 1.5 -> 0, then 2, then 1
+    assert osth.greedy_order((5, 4, 3), (1, 4, 2), "ratio") == [0, 2, 1]
+
+
 def test_order_heuristics_on_the_papers_mode_order_problem():
     # Sec. 8.3: 25 x 250 x 250 x 250 with core 10 x 10 x 100 x 100; the second
     # mode has by far the largest compression ratio I_n / R_n = 25
@@ -456,6 +471,7 @@ def _pins_pass():
         lambda: test_hooi_noisy_monotone_stationary_and_pythagorean(),
         lambda: test_order_flops_hand_count(),
         lambda: test_order_heuristics_on_the_papers_mode_order_problem(),
+        lambda: test_greedy_flops_order_hand_count(),
     ]
     for c in checks:
         try:
@@ -558,11 +574,29 @@ def _mut_greedy_max(dims, ranks, rule, _orig=osth.greedy_order):
     return _orig(dims, ranks, rule)[::-1]
 
 
+def _mut_greedy_no_shrink(dims, ranks, rule):
+    # the current dims are never updated after a pick
+    left = list(range(len(dims)))
+    cur = [int(d) for d in dims]
+    order = []
+    while left:
+        if rule == "flops":
+            j = math.prod(cur)
+            pick = min(left, key=lambda n: (2.0 * dims[n] * j + 2.0 * ranks[n] * j + 10.0 / 3.0 * float(dims[n]) ** 3,
+                                            n))
+        else:
+            pick = min(left, key=lambda n: (-dims[n] / ranks[n], n))
+        order.append(pick)
+        left.remove(pick)
+    return order
+
+
 MUTATIONS = {
     "subtensor_ignores_lo": ("reconstruct_sub", _mut_sub_ignores_lo),
     "hooi_never_updates": ("hooi", _mut_hooi_no_update),
     "ttm_flops_with_I": ("order_flops", _mut_ttm_flops_with_i),
     "greedy_reversed": ("greedy_order", _mut_greedy_max),
+    "greedy_no_shrink": ("greedy_order", _mut_greedy_no_shrink),
     "threshold_without_N": ("sthosvd", _mut_threshold_without_n),
     "unfold_column_order": ("unfold", _mut_unfold_c_order),
     "fold_column_order": ("fold", _mut_fold_c_order),

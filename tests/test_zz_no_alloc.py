@@ -67,3 +67,41 @@ def test_noalloc_gram_rejects_oversize(gpu_lib):
         gpu_lib.gram_noalloc(y, 1, 1025, 2, out=torch.empty((1025, 1025), dtype=torch.float64, device="cuda"))
     assert e.value.status == -1
     assert "1025" in str(e.value)
+
+
+CAP_SHAPES = [(1, 1024, 4000), (1, 256, 20000), (1, 512, 8000)]
+
+
+def _run_capped(gpu_lib, monkeypatch, capfd, L, J, B):
+    """Two noalloc calls against tucker_gram; returns whether the split plan
+    needed more partial sums than the static scratch holds."""
+    import torch
+
+    rng = np.random.default_rng(J + B)
+    y = rng.standard_normal(L * J * B)
+    yd = torch.from_numpy(y).cuda()
+    ref = gpu_lib.gram(yd, L, J, B).cpu().numpy()
+    bound = _bound(y, L, J, B)
+    monkeypatch.setenv("TUCKER_NOALLOC_TRACE", "1")
+    for _ in range(2):
+        got = gpu_lib.gram_noalloc(yd, L, J, B).cpu().numpy()
+        assert np.all(np.abs(got - ref) <= bound + 1e-300)
+    monkeypatch.delenv("TUCKER_NOALLOC_TRACE")
+    err = capfd.readouterr().err
+    line = [ln for ln in err.splitlines() if ln.startswith("tucker_gram_noalloc:")][-1]
+    kv = dict(tok.split("=") for tok in line.split()[1:])
+    assert int(kv["used_splits"]) <= int(kv["scratch_fits"])
+    return int(kv["planned_splits"]) > int(kv["scratch_fits"])
+
+
+@pytest.mark.parametrize("L,J,B", CAP_SHAPES)
+def test_noalloc_gram_caps_splits_to_the_scratch(gpu_lib, monkeypatch, capfd, L, J, B):
+    """Shapes whose split plan can need more partial sums than the static
+    scratch holds: the call then runs fewer, longer column ranges and still
+    matches tucker_gram (checked twice in a row)."""
+    _run_capped(gpu_lib, monkeypatch, capfd, L, J, B)
+
+
+def test_noalloc_cap_is_reached(gpu_lib, monkeypatch, capfd):
+    """At least one of those shapes takes the capped branch on this GPU."""
+    assert any(_run_capped(gpu_lib, monkeypatch, capfd, *shape) for shape in CAP_SHAPES)
