@@ -36,8 +36,17 @@ if ROOT not in sys.path:
 
 METRIC = "ST-HOSVD input GB/s & Gram TFLOP/s, split-prec vs FP64 on GB300, equal rel. error"
 WORKLOAD = "combustion5"
-# Float64 pipe peak of one GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Float64 pipe peak of one GB300 as derived from the unit counts: 152 SMs x
+# 2 DFMA/clk/SM x 2 flop x 2.07 GHz.  The bench measures the rate with the
+# library's float64 probe (tucker_fp64_peak) and reports the float64 phases
+# against that measurement; this figure is the fallback and the cross-check.
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK = {"tflops": FP64_DERIVED_TFLOPS, "source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz"}
+# Arithmetic each precision runs in (the bench line's dtype).
+DTYPES = {"bf16x4": "bf16x4-split (f64 in/out: Gram 3 BF16 digits of 21-bit entries, TTM 4 digits of 28-bit; "
+                    "exact FP32 accumulation, f64 reduction)",
+          "e4m3x4": "e4m3x4-split (f64/f32 in, f64 out: Gram 4 E4M3 digits of 15-bit entries; TTM as bf16x4)",
+          "fp64": "f64"}
 # ncu DRAM traffic, keyed by kernel and the hash of the kernel source it was
 # captured with (profiles/*_combustion5_t2.md): measured
 # dram__bytes_read.sum + dram__bytes_write.sum of the mode-1 launch on the
@@ -57,7 +66,15 @@ TRAFFIC = {("k_gram_partial", "f172da5c229e3897"): {"ratio": 1.6274e9 / 1.6260e9
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB)"},
            ("k_ttm_split_tma", "148a97b8626bb340"): {"ratio": (0.505569e9 + 131.04e6) / (0.50332e9 + 0.157286e9),
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB)"}}
-HBM_PEAK_GBS = 6782.4  # MEASURED_PEAKS.json hbm_gbs
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 
 
 KERNEL_FILES = {"k_gram_partial": "kernels_f64.cu", "k_ttm": "kernels_f64.cu", "k_sumsq": "kernels_f64.cu",
@@ -226,15 +243,17 @@ def reference_main(args):
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     value = x.nbytes / t / 1e9
-    sample = f"first {slices} of {w.dims[-1]} time slices ({x.nbytes / 1e9:.2f} GB), numpy/OpenBLAS float64 oracle"
-    cores = os.cpu_count()
+    cpu = host_cpu_info()
+    cores = cpu["usable_cores"]
+    sample = (f"first {slices} of {w.dims[-1]} time slices ({x.nbytes / 1e9:.2f} GB), numpy/OpenBLAS float64 "
+              f"oracle on {cores} cores of {cpu['model']}")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(w, args.eps, "oracle"),
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu": cpu},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -282,9 +301,12 @@ def time_method(tucker, x, dims, eps, precision, steps, warmup, world, local, st
     res = tucker.sthosvd(x, dims, eps, precision=precision)
     rel = tucker.rel_error(x, res)
     sweeps = list(res.sweeps)
+    paths = list(res.eig_paths)
+    resolved = list(res.eig_resolved)
     res.free()
     return {"ms": ms, "prof": prof, "ranks": tuple(ranks), "rel": rel, "sweeps": sweeps, "launches": launches,
-            "clocks": sampler.summary()}
+            "clocks": sampler.summary(), "eig_paths": paths, "eig_resolved": resolved,
+            "eig_fallbacks": sum(p == "jacobi_fallback" for p in paths)}
 
 
 # Kernel of each profiled phase, its bound and the peak it is measured against.
@@ -319,13 +341,12 @@ def phase_roofline(prof, phase, steps, path):
         achieved = per_bytes / (per_ms / 1e3) / 1e9
         r = {"kernel": f"{kernel} ({what})", "bound": "hbm", "achieved": round(achieved, 2), "peak": HBM_PEAK_GBS,
              "unit": "GB/s", "frac": round(achieved / HBM_PEAK_GBS, 4),
-             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+             "peak_source": HBM_PEAK_SOURCE}
     else:
         achieved = per_flops / (per_ms / 1e3) / 1e12
         r = {"kernel": f"{kernel} ({what})", "bound": "alu", "achieved": round(achieved, 5),
-             "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 5),
-             "peak_source": "derived: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (recipe nominal FP64 "
-                            "1.25 TFLOP/s; measured DFMA loop 1.193 TFLOP/s)"}
+             "peak": round(FP64_PEAK["tflops"], 4), "unit": "TFLOP/s",
+             "frac": round(achieved / FP64_PEAK["tflops"], 5), "peak_source": FP64_PEAK["source"]}
         if phase == "eig":
             r["flops_source"] = "the paper's count of the eigenvector step, 10/3 J^3 per mode (Sec. 5.4)"
     tr = TRAFFIC.get((kernel, kernel_source_hash(kernel))) if kernel in KERNEL_FILES else None
@@ -489,7 +510,7 @@ def measure_paper_shapes(tucker, stream, eps=1e-4, reps=2):
         "sthosvd_input_gb_s": round(nbytes / (ms_st / 1e3) / 1e9, 2),
         "sthosvd_model_gflop": round(model / 1e9, 2),
         "sthosvd_model_tflop_s": round(model / (ms_st / 1e3) / 1e12, 4),
-        "fp64_peak_tflop_s": round(FP64_PEAK_TFLOPS, 4),
+        "fp64_peak_tflop_s": round(FP64_PEAK["tflops"], 4),
         "phase_ms_sthosvd": phases_st, "phase_ms_sthosvd_plus_hooi": phases_hooi,
         "paper_single_node_s": 3.0,
         "note": "float64 path; the paper's figure is ST-HOSVD plus one HOOI step on one 24-core node "
@@ -559,6 +580,135 @@ def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=8):
             "true_ranks_recovered": ok, "precision": precision, "workers": workers}
 
 
+def measure_fp64_peak(tucker, stream):
+    """The float64 pipe's rate from the library's FMA probe (median of 5, CUDA events)."""
+    import torch
+
+    runs = [tucker.fp64_peak(stream) for _ in range(5)]
+    torch.cuda.synchronize()
+    tf = statistics.median(r[0] for r in runs)
+    return {"tflops": tf, "ms_per_launch": round(statistics.median(r[1] for r in runs), 3),
+            "source": "measured: tucker_fp64_peak register-resident DFMA loop over all SMs, median of 5 "
+                      "(CUDA events)",
+            "derived_tflops": round(FP64_DERIVED_TFLOPS, 4)}
+
+
+def host_cpu_info():
+    """Model name, usable cores and the numpy BLAS threads of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        usable = os.cpu_count()
+    quota = None
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            q, per = f.read().split()[:2]
+            if q != "max":
+                quota = round(int(q) / int(per), 2)
+    except (OSError, ValueError):
+        pass
+    return {"model": model or "unknown", "machine": os.uname().machine, "usable_cores": usable,
+            "os_cpu_count": os.cpu_count(), "cgroup_cpu_quota": quota}
+
+
+def _time_calls(fn, stream, reps, warm=1):
+    """(median ms, list of ms) of `reps` calls of fn, each bracketed by CUDA events on `stream`."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out), out
+
+
+def measure_config(tucker, stream, w, eps, precisions, reps, warm=1, orders=(None,)):
+    """One workload of the list, generated on the device: per precision and mode
+    order, the median time of `reps` ST-HOSVDs, the ranks, the relative error
+    from the explicit difference and the eigensolver paths."""
+    import torch
+
+    from synthetic import tucker_tensor_torch
+
+    x = tucker_tensor_torch(w.dims, w.ranks, seed=0, decay=w.decay, smooth=w.smooth, noise=w.noise,
+                            dtype=w.dtype, device="cuda")
+    torch.cuda.synchronize()
+    nbytes = x.numel() * x.element_size()
+    out = {"workload": f"{w.name}: {'x'.join(map(str, w.dims))} {'float32' if w.dtype == 'f32' else 'float64'}, "
+                       f"generating ranks {tuple(w.ranks)}, noise {w.noise}",
+           "eps": eps, "input_bytes": nbytes, "runs": []}
+    for order in orders:
+        for prec in precisions:
+            row = {"precision": prec, "mode_order": None if order is None else [o + 1 for o in order]}
+            try:
+                med, all_ms = _time_calls(lambda: tucker.sthosvd(x, w.dims, eps, mode_order=order,
+                                                                 precision=prec).free(), stream, reps, warm)
+                r = tucker.sthosvd(x, w.dims, eps, mode_order=order, precision=prec)
+                row.update({"ms": round(med, 3), "reps": reps, "input_gb_s": round(nbytes / (med / 1e3) / 1e9, 3),
+                            "ranks": list(r.ranks), "rel_error": tucker.rel_error(x, r),
+                            "eig_paths": list(r.eig_paths), "eig_resolved": list(r.eig_resolved),
+                            "eig_fallbacks": sum(p == "jacobi_fallback" for p in r.eig_paths)})
+                r.free()
+                row["phase_ms"] = _phase_ms(tucker, lambda: tucker.sthosvd(x, w.dims, eps, mode_order=order,
+                                                                            precision=prec).free())
+            except Exception as e:  # recorded; the other rows stand
+                row["error"] = f"{type(e).__name__}: {e}"
+            out["runs"].append(row)
+    ref = {(r["mode_order"] and tuple(r["mode_order"])): r for r in out["runs"] if r["precision"] == "fp64"}
+    for r in out["runs"]:
+        f = ref.get(r["mode_order"] and tuple(r["mode_order"]))
+        if f and r is not f and "error" not in r and "error" not in f:
+            r["vs_fp64"] = {"same_ranks": r["ranks"] == f["ranks"],
+                            "rel_error_diff": abs(r["rel_error"] - f["rel_error"]),
+                            "speedup": round(f["ms"] / r["ms"], 3)}
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_configs(tucker, stream, args):
+    """Every other workload of the list: the 64^3 cube (median of 21), the
+    combustion tensor at eps = 1e-3, the float32 combustion tensor (eps = 1e-4)
+    and the 512^2 x 256 x 64 tensor in mode orders 1..4 and 4..1."""
+    from synthetic import WORKLOADS
+
+    precs = [p for p in ("bf16x4", "e4m3x4", "fp64") if p in tucker.PREC]
+    out = {}
+    out["cube64"] = measure_config(tucker, stream, WORKLOADS["cube64"], 1e-3, precs, reps=21, warm=5)
+    out["combustion5_eps1e-3"] = measure_config(tucker, stream, WORKLOADS["combustion5"], 1e-3,
+                                                 [p for p in precs if p != "e4m3x4"], reps=5)
+    out["combustion5_f32"] = measure_config(tucker, stream, WORKLOADS["combustion5_f32"], 1e-4, precs, reps=5)
+    out["large4"] = measure_config(tucker, stream, WORKLOADS["large4"], 1e-4,
+                                   [p for p in precs if p != "e4m3x4"], reps=2,
+                                   orders=((0, 1, 2, 3), (3, 2, 1, 0)))
+    return out
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -576,6 +726,7 @@ def main():
         build.build()
     barrier(world)
     tucker.load()
+    FP64_PEAK.update(measure_fp64_peak(tucker, torch.cuda.current_stream()))
     if args.paper_shapes_only:
         if rank == 0:
             print(json.dumps(measure_paper_shapes(tucker, torch.cuda.current_stream())), flush=True)
@@ -594,6 +745,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     methods = ["bf16x4", "fp64"] if args.precision == "both" else [args.precision]
+    methods = [m for m in methods if m in tucker.PREC]
     timed = {m: time_method(tucker, x, dims, args.eps, m, args.steps, args.warmup, world, local, stream)
              for m in methods}
     # "equal rel. error": the split-precision result counts only with the float64 ranks and error
@@ -612,17 +764,24 @@ def main():
     def summary(m):
         tm = timed[m]
         g = tm["prof"]["gram"]
+        top, rows = roofline_of(tm, args.steps, m)
         return {"value": round(world * w.nbytes / (tm["ms"] / 1e3) / 1e9, 4), "ms_per_step": round(tm["ms"], 3),
+                "dtype": DTYPES[m],
                 "gram_tflops": round(g["flops"] / (g["ms"] / 1e3) / 1e12, 4) if g["ms"] > 0 else None,
                 "ranks": list(tm["ranks"]), "rel_error": tm["rel"], "jacobi_sweeps": tm["sweeps"],
-                "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in tm["prof"].items()}}
+                "eig_paths": tm["eig_paths"], "eig_resolved": tm["eig_resolved"],
+                "eig_fallbacks": tm["eig_fallbacks"],
+                "phase_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in tm["prof"].items()},
+                "roofline": top, "rooflines": rows}
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args.eps, head),
+        "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic", "config": config_dict(w, args.eps, head),
         "gram_tflops": round(gram_tflops, 4) if gram_tflops else None,
         "ranks": list(t["ranks"]), "rel_error": t["rel"], "jacobi_sweeps": t["sweeps"],
+        "eig_paths": t["eig_paths"], "eig_fallbacks": t["eig_fallbacks"],
+        "fp64_peak": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in FP64_PEAK.items()},
         "methods": {m: summary(m) for m in methods},
         "equal_rel_error": equal,
         "phase_share": {k: round(v["ms"] / args.steps / ms, 4) for k, v in t["prof"].items()},
@@ -639,29 +798,47 @@ def main():
     if not args.no_e2e:
         xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
         xh.copy_(x)
+        # the raw copy rate of the same pinned buffer (one cudaMemcpyAsync), beside the end-to-end figure
+        h2d_ms, _ = _time_calls(lambda: x.copy_(xh, non_blocking=True), stream, reps=3)
         del x
         torch.cuda.empty_cache()
-        r = tucker.sthosvd_host(xh, dims, args.eps, precision=head)
-        d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)) + sum(d + 3 for d in dims) + 1)
-        r.free()
-        barrier(world)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            tucker.sthosvd_host(xh, dims, args.eps, precision=head).free()
-        t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / args.steps)
-        line["e2e"] = {"value": round(world * w.nbytes / t_e2e / 1e9, 4), "unit": "GB/s",
-                       "h2d_bytes_per_step": w.nbytes, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": round(t_e2e * 1e3, 3), "precision": head}
+
+        def e2e(prec, steps):
+            r = tucker.sthosvd_host(xh, dims, args.eps, precision=prec)
+            d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)))
+            r.free()
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                tucker.sthosvd_host(xh, dims, args.eps, precision=prec).free()
+            t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+            return {"value": round(world * w.nbytes / t_e2e / 1e9, 4), "unit": "GB/s",
+                    "h2d_bytes_per_step": w.nbytes, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(t_e2e * 1e3, 3), "precision": prec, "steps": steps}
+
+        line["e2e"] = e2e(head, args.steps)
+        line["e2e"]["raw_h2d"] = {"gb_s": round(w.nbytes / (h2d_ms / 1e3) / 1e9, 2), "ms": round(h2d_ms, 3),
+                                  "what": "one cudaMemcpyAsync of the same pinned buffer to the device, "
+                                          "median of 3 (CUDA events)"}
+        if "fp64" in timed and head != "fp64":
+            line["e2e_fp64"] = e2e("fp64", 2)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         src = xh if xh is not None else x.cpu()
         gbs, secs, sdims = run_oracle_sample(w, args.eps, min(args.cpu_slices, w.dims[-1]), x_host=src.numpy())
+        cpu = host_cpu_info()
         line["cpu_baseline"] = {
-            "value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "value": round(gbs, 4), "unit": "GB/s", "cores": cpu["usable_cores"], "kind": "oracle",
+            "cpu": cpu,
             "sample": f"first {sdims[-1]} of {w.dims[-1]} time slices of the same tensor "
                       f"({math.prod(sdims) * 8 / 1e9:.2f} GB), one oracle ST-HOSVD in {secs:.2f} s "
-                      f"(numpy/OpenBLAS float64 on all host cores)",
+                      f"(numpy/OpenBLAS float64 on {cpu['usable_cores']} cores of {cpu['model']}); "
+                      f"the reference arm times the first {max(1, args.cpu_slices // 2)} slices",
         }
+    if not args.no_next and world == 1:
+        del xh
+        xh = None
+        line["configs"] = measure_configs(tucker, stream, args)
     # last: these tensors of their own (16 GB between them) run after the end-to-end leg
     if not args.no_next and world == 1:
         try:

@@ -723,7 +723,7 @@ __global__ void k_eig_tag(int *info, int path, int resolved) {
 int launch_eig(const double *d_S, int64_t J, double *d_lam, double *d_V, double *d_ws, int *d_info,
                cudaStream_t s, Prof *prof, double tail_budget) {
   const int64_t m = J + (J & 1);
-  // "mp" (default: mixed precision, J <= 128 or with TUCKER_EIG_WIDE=1 J <= 256,
+  // "mp" (default: mixed precision, J <= 256 (J <= 128 with TUCKER_EIG_WIDE=0),
   // float64 Jacobi if unverified) |
   // "jacobi" (float64 Jacobi only) | "dsm" | "l2m" | "l2" (cluster variants)
   const char *ev = getenv("TUCKER_EIG_KERNEL");

@@ -1855,10 +1855,11 @@ static thread_local double g_mp_check[5];
 const double *mp_last_check() { return g_mp_check; }
 
 int mp_max_j() {
-  // J above kTriMaxJ takes the wide float32 stage only with TUCKER_EIG_WIDE=1
+  // J above kTriMaxJ takes the wide float32 stage; TUCKER_EIG_WIDE=0 restricts
+  // the mixed-precision solver to J <= kTriMaxJ (the float64 Jacobi above)
   static const int lim = [] {
     const char *e = std::getenv("TUCKER_EIG_WIDE");
-    return e && e[0] == '1' ? kMpMaxJ : kTriMaxJ;
+    return e && e[0] == '0' ? kTriMaxJ : kMpMaxJ;
   }();
   return lim;
 }

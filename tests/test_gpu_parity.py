@@ -150,8 +150,8 @@ def test_eig_random_psd(gpu_lib, eig_path, j):
     _check_eig(gpu_lib, a @ a.T)
 
 
-WIDE = pytest.mark.skipif(os.environ.get("TUCKER_EIG_WIDE") != "1",
-                          reason="the wide float32 stage (128 < J <= 256) is opt-in: TUCKER_EIG_WIDE=1")
+WIDE = pytest.mark.skipif(os.environ.get("TUCKER_EIG_WIDE") == "0",
+                          reason="the wide float32 stage (128 < J <= 256) is switched off: TUCKER_EIG_WIDE=0")
 
 
 @WIDE
