@@ -78,7 +78,18 @@ typedef enum { TUCKER_F64 = 0, TUCKER_F32 = 1 } tucker_dtype;
  * memory and are reduced in float64; ||X||^2, the eigensolver and the rank
  * rule stay float64.  The name counts the four digit tiles each operand
  * stage holds.  It needs I_n <= 128 at every mode. */
-typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_BF16X4 = 1 } tucker_precision;
+typedef enum {
+  TUCKER_PREC_FP64 = 0,
+  TUCKER_PREC_BF16X4 = 1,
+  /* The Gram on the FP8 tensor cores (tcgen05 kind::f8f6f4): every entry is
+   * rounded to 15 bits below its (row, 512-column group) power of two and
+   * split into four balanced base-16 digits that E4M3 holds exactly (see
+   * tucker_gram_split_e4m3); ||X||^2 comes from a float64 pass over X and the
+   * mode product is that of TUCKER_PREC_BF16X4.  16 bits per entry instead
+   * of 22: its error against float64 is measured, not bounded to the float64
+   * path's. */
+  TUCKER_PREC_E4M3X4 = 2
+} tucker_precision;
 
 /* Which eigensolver produced a mode's eigenpairs (tucker_result.eig_path). */
 typedef enum {
@@ -303,6 +314,18 @@ TUCKER_API int tucker_rank_cut(const double *lam, int64_t J, double threshold, i
  *   step of Algorithm 1. */
 TUCKER_API int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
                                  void *stream);
+
+/* The Gram of tucker_gram_split (same arguments, view, output and error
+ * codes) from E4M3 digits on the FP8 tensor cores: each entry is rounded to
+ * the integer v = round(y 2^(15 - E_ig)) (|v| <= 2^15) and split into four
+ * balanced base-16 digits (|d| <= 8, exact in E4M3); the seven digit-product
+ * levels accumulate exactly in FP32 tensor memory (four accumulators, scaled
+ * digit tiles folding pairs of levels) and are reduced in float64.  The only
+ * difference from the float64 Gram is the rounding of Y to 15 bits below each
+ * local power of two (radius 2^(E_ig - 16)).  J <= 128.  No counterpart in
+ * the paper (its Gram is float64, Sec. 5.3). */
+TUCKER_API int tucker_gram_split_e4m3(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
+                                      void *stream);
 
 /* Split-precision TTM step: Z = Y x_n U^T for Y viewed as (L, J, B) and Z as
  * (L, R, B), i.e. Z[l + L(r + R b)] = sum_j U[j + J r] Y[l + L(j + J b)], on the

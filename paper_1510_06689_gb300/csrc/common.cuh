@@ -135,8 +135,9 @@ int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const Devi
 // it is unavailable or refuses the map.
 bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const uint64_t *dims,
                  const uint64_t *strides_bytes, const uint32_t *box, int swizzle = 0);
+// f8: E4M3 digits (four base-16 digits of 15-bit entries, kind::f8f6f4) instead of BF16 ones.
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
-                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp = nullptr);
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp = nullptr, bool f8 = false);
 // *d_out = trace of the J x J matrix S (column-major), summed in index order.
 int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s);
 int gram_split_error(const double *d_ws, int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, int *h_err,

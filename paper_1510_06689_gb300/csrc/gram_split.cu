@@ -458,11 +458,41 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
   if (lane == 0 && gm != 0u) atomicMax(gmax, mag_pattern(gm, kF64));
 }
 
-template <typename T, int kMode>
+// E4M3 variant (kF8): every entry is rounded to v = round(y 2^(15 - E_ig)),
+// |v| <= 2^15, and split into four balanced base-16 digits
+// v = d1 2^12 + d2 2^8 + d3 2^4 + d4 (|d| <= 8, exact in E4M3, and so are
+// 2 d, 16 d and 32 d).  Level L = p + q of a digit product has weight
+// 2^(4 (8 - L)); with only the symmetric part of C counting, four
+// accumulators hold exact integer sums over a 512-column group:
+//   acc0 = 16 L2 + L3 = D1 (16 D1)^T + D1 (2 D2)^T
+//   acc1 = 16 L4 + L5 = D1 (32 D3)^T + D2 (16 D2)^T + D1 (2 D4)^T + D2 (2 D3)^T
+//   acc2 = 16 L6 + L7 = D2 (32 D4)^T + D3 (16 D3)^T + D3 (2 D4)^T
+//   acc3 = L8         = D4 D4^T
+// (per column at most 1152, 3328, 3200 and 64: far below 2^24 over a group),
+// drained with weights 2^20, 2^12, 2^4, 2^0, so that S = (C + C^T) 2^(E_i +
+// E_j - 31).  The B operands lie as stacked pairs [16 D1; 32 D3], [2 D2; 2 D4],
+// [16 D2; 32 D4] (N = 256), then 2 D3, 16 D3, and the A operands D1..D4
+// (D4 is also the B operand of acc3): seven MMAs of K = 32 per chunk.
+constexpr int kF8Tiles = 12;
+constexpr int kF8TileBytes = kRows * kChunk;      // 128 rows x 32 one-byte digits
+constexpr int kF8Sbo = kChunk / 16 * 128;         // two 16-byte core matrices per 8-row group
+constexpr int kF8StageBytes = kF8Tiles * kF8TileBytes;
+constexpr uint32_t kIdescF8 = idesc_e4m3(kRows, kRows);
+constexpr uint32_t kIdescF8x256 = idesc_e4m3(kRows, 2 * kRows);
+
+// Two floats holding small integers (|x| <= 448) as E4M3 bytes: a in the low byte.
+__device__ __forceinline__ uint32_t e4m3_pair(float a, float b) {
+  unsigned short d;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(b), "f"(a));
+  return d;
+}
+
+template <typename T, int kMode, bool kF8>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict__ y, int64_t L, SplitPlan p,
                                                             const int *__restrict__ Etab,
                                                             int *__restrict__ refs, double *__restrict__ ws,
                                                             int *__restrict__ err) {
+  constexpr int kStage = kF8 ? kF8StageBytes : kStageBytes;
   extern __shared__ __align__(1024) unsigned char dsmem[];
   __shared__ __align__(8) unsigned long long mbar[kStages];
   __shared__ int rowexp[kRows];
@@ -472,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
   unsigned char *stage_base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
   // double-float accumulators of C, element e of thread t at [e][t]
-  float2 *cacc = reinterpret_cast<float2 *>(stage_base + kStages * kStageBytes);
+  float2 *cacc = reinterpret_cast<float2 *>(stage_base + kStages * kStage);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
@@ -525,9 +555,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
     if (ch >= 2 && tid == 0 && !mbar_wait(smem_addr(&mbar[buf]), ((ch - 2) >> 1) & 1)) stop = 1;
     __syncthreads();
     if (stop) return false;
-    if (in_group == 0) my_e1022 = rowexp[row] + 1022;
-    unsigned char *st = stage_base + buf * kStageBytes;
-    {
+    if (in_group == 0) my_e1022 = rowexp[row] + 1022 + (kF8 ? 6 : 0);  // 15 bits: round(y 2^(21 - (E + 6)))
+    unsigned char *st = stage_base + buf * kStage;
+    if constexpr (kF8) {
+      // tiles: 0 16D1, 1 32D3, 2 2D2, 3 2D4, 4 16D2, 5 32D4, 6 2D3, 7 16D3, 8 D1, 9 D2, 10 D3, 11 D4
+      uint32_t w[kF8Tiles][2];
+#pragma unroll
+      for (int k = 0; k < 8; k += 4) {
+        float d[4][4];  // [column][digit]
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float v = small_int_float(scaled_int21(raw[k + h], my_e1022));
+          const float d1 = round_float(v * 0x1p-12f);
+          const float r1 = __fmaf_rn(d1, -4096.0f, v);
+          const float d2 = round_float(r1 * 0x1p-8f);
+          const float r2 = __fmaf_rn(d2, -256.0f, r1);
+          const float d3 = round_float(r2 * 0x1p-4f);
+          d[h][0] = d1;
+          d[h][1] = d2;
+          d[h][2] = d3;
+          d[h][3] = __fmaf_rn(d3, -16.0f, r2);
+        }
+        const float sc[kF8Tiles] = {16.f, 32.f, 2.f, 2.f, 16.f, 32.f, 2.f, 16.f, 1.f, 1.f, 1.f, 1.f};
+        const int dig[kF8Tiles] = {0, 2, 1, 3, 1, 3, 2, 2, 0, 1, 2, 3};
+#pragma unroll
+        for (int t = 0; t < kF8Tiles; ++t)
+          w[t][k >> 2] = e4m3_pair(d[0][dig[t]] * sc[t], d[1][dig[t]] * sc[t]) |
+                         (e4m3_pair(d[2][dig[t]] * sc[t], d[3][dig[t]] * sc[t]) << 16);
+      }
+      const int off = (row >> 3) * kF8Sbo + (kg >> 1) * 128 + (row & 7) * 16 + (kg & 1) * 8;
+#pragma unroll
+      for (int t = 0; t < kF8Tiles; ++t)
+        *reinterpret_cast<uint2 *>(st + t * kF8TileBytes + off) = make_uint2(w[t][0], w[t][1]);
+    } else {
       uint32_t w[kTiles][4];
 #pragma unroll
       for (int k = 0; k < 8; k += 2) {
@@ -555,7 +615,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (kF8 && tid == 0) {
+      fence_after();
+      const uint32_t base = smem_addr(st);
+      const uint32_t acc = in_group == 0 ? 0u : 1u;
+      auto dsc = [&](int t) { return smem_desc(base + t * kF8TileBytes, 128, kF8Sbo); };
+      // each accumulator's first MMA of a group carries `acc` (0: overwrite)
+      mma_f8(tmem + 0, dsc(8), dsc(0), kIdescF8x256, acc);    // acc0 (+)= D1 16D1, acc1 (+)= D1 32D3
+      mma_f8(tmem + 0, dsc(8), dsc(2), kIdescF8x256, 1u);     // acc0 += D1 2D2,    acc1 += D1 2D4
+      mma_f8(tmem + 256, dsc(10), dsc(7), kIdescF8, acc);     // acc2 (+)= D3 16D3
+      mma_f8(tmem + 128, dsc(9), dsc(4), kIdescF8x256, 1u);   // acc1 += D2 16D2,   acc2 += D2 32D4
+      mma_f8(tmem + 128, dsc(9), dsc(6), kIdescF8, 1u);       // acc1 += D2 2D3
+      mma_f8(tmem + 256, dsc(10), dsc(3), kIdescF8, 1u);      // acc2 += D3 2D4
+      mma_f8(tmem + 384, dsc(11), dsc(11), kIdescF8, acc);    // acc3 (+)= D4 D4
+      mma_commit(smem_addr(&mbar[buf]));
+    } else if (tid == 0) {
       fence_after();
       const uint32_t base = smem_addr(st);
 #pragma unroll
@@ -583,7 +657,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
       __syncthreads();
       if (!stop) {  // uniform across the CTA, so the .sync.aligned loads below never diverge
         fence_after();
-        const float wts[4] = {0x1p28f, 0x1p22f, 0x1p14f, 0x1p7f};  // 2^28, 2 2^21, 2^14, 2^7
+        // bf16: 2^28, 2 2^21, 2^14, 2^7; e4m3: 2^20, 2^12, 2^4, 2^0
+        const float wts[4] = {kF8 ? 0x1p20f : 0x1p28f, kF8 ? 0x1p12f : 0x1p22f, kF8 ? 0x1p4f : 0x1p14f,
+                              kF8 ? 1.0f : 0x1p7f};
         const int ei = rowexp[drow] - ref[drow];
 #pragma unroll
         for (int part = 0; part < 4; ++part) {
@@ -1009,7 +1085,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
 __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, const int *__restrict__ refs,
                                                            int nsplit, int J,
                                                            const unsigned long long *__restrict__ gmax, int is_f64,
-                                                           double *__restrict__ S) {
+                                                           int scale_off, double *__restrict__ S) {
   const int idx = blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3), sub = threadIdx.x & 7;
   const bool live = idx < J * J;
   const int i = live ? idx % J : 0, j = live ? idx / J : 0;
@@ -1020,7 +1096,7 @@ __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restr
       const float2 a = c[i * kRows + j], b = c[j * kRows + i];
       const int ri = refs[sp * kRows + i], rj = refs[sp * kRows + j];
       if (ri != kZeroExp && rj != kZeroExp)
-        s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - 43);
+        s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - scale_off);
     }
   s += __shfl_xor_sync(0xffffffffu, s, 4);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
@@ -1032,6 +1108,7 @@ __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restr
 }
 
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kRows * kRows * sizeof(float2) + 1024;
+constexpr size_t kSmemBytesF8 = (size_t)kStages * kF8StageBytes + (size_t)kRows * kRows * sizeof(float2) + 1024;
 
 // oct: the tiled L > 1 path, whose columns are counted as 32 per chunk of
 // 8 l x 4 b (a ragged last quad of b reads zeros past B)
@@ -1103,13 +1180,13 @@ bool use_oct(const void *y, tucker_dtype dt, int64_t L, int64_t B) {
          L < (1ll << 31) && (B + 3) / 4 * 4 < (1ll << 31);
 }
 
-template <typename T, int kMode>
+template <typename T, int kMode, bool kF8 = false>
 int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &w, const DeviceInfo &dev,
                    cudaStream_t s) {
   (void)dev;
-  TK_CUDA(allow_max_smem(k_gram_split<T, kMode>));
-  k_gram_split<T, kMode><<<p.nsplit, kThreads, kSmemBytes, s>>>(static_cast<const T *>(y), L, p, w.table, w.refs,
-                                                                w.partials, w.err);
+  TK_CUDA(allow_max_smem(k_gram_split<T, kMode, kF8>));
+  k_gram_split<T, kMode, kF8><<<p.nsplit, kThreads, kF8 ? kSmemBytesF8 : kSmemBytes, s>>>(
+      static_cast<const T *>(y), L, p, w.table, w.refs, w.partials, w.err);
   TK_LAUNCHED();
   return TUCKER_OK;
 }
@@ -1193,12 +1270,12 @@ int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const Devi
 }
 
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
-                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp) {
+                      const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp, bool f8) {
   if (J > kRows) {
     set_error("split-precision Gram supports J <= %d (got %lld)", kRows, (long long)J);
     return TUCKER_EUNSUPPORTED;
   }
-  const bool oct = use_oct(y, dt, L, B);
+  const bool oct = !f8 && use_oct(y, dt, L, B);  // the E4M3 digits run in the register-staged kernel
   const SplitPlan p = split_plan(L, J, B, dev, oct);
   if (p.ngroups > 0x7FFFFFFFll) {
     set_error("split-precision Gram: too many column groups (%lld)", (long long)p.ngroups);
@@ -1239,7 +1316,18 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (prof) prof->end(0.0, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM);
   bool ran = false;
-  if (L == 1) {
+  if (f8) {
+    if (f64) {
+      if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided, true>(y, L, p, w, dev, s)));
+      else if (mode == kColsContig) TK_CHECK((run_gram_split<double, kColsContig, true>(y, L, p, w, dev, s)));
+      else TK_CHECK((run_gram_split<double, kColsGeneric, true>(y, L, p, w, dev, s)));
+    } else {
+      if (mode == kColsStrided) TK_CHECK((run_gram_split<float, kColsStrided, true>(y, L, p, w, dev, s)));
+      else if (mode == kColsContig) TK_CHECK((run_gram_split<float, kColsContig, true>(y, L, p, w, dev, s)));
+      else TK_CHECK((run_gram_split<float, kColsGeneric, true>(y, L, p, w, dev, s)));
+    }
+    ran = true;
+  } else if (L == 1) {
     if (f64) TK_CHECK(run_gram_split_bulk<double>(y, p, w, s, &ran));
     else TK_CHECK(run_gram_split_bulk<float>(y, p, w, s, &ran));
   } else if (oct) {
@@ -1260,8 +1348,9 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   }
   if (prof) prof->end((double)J * (J + 1) * (double)L * B, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
+  // S = (C + C^T) 2^(ref_i + ref_j - off): off = 2 x 21 + 1 for the BF16 digits, 2 x 15 + 1 for E4M3
   k_gram_split_reduce<<<(unsigned)((J * J + 31) / 32), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
-                                                                      d_S);
+                                                                      f8 ? 31 : 43, d_S);
   TK_LAUNCHED();
   if (prof) prof->end((double)p.nsplit * J * J * 2, (double)p.nsplit * kRows * kRows * 8, 1);
   return TUCKER_OK;

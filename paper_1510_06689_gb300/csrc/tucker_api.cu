@@ -312,10 +312,12 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   int *d_info = reinterpret_cast<int *>(d_nx2 + 3);
   int *d_terr = reinterpret_cast<int *>(d_nx2 + 6);
   TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
-  if (prec == TUCKER_PREC_BF16X4) {
+  const bool split = prec != TUCKER_PREC_FP64;  // tensor-core digits for the Gram and the mode product
+  const bool f8 = prec == TUCKER_PREC_E4M3X4;
+  if (split) {
     for (int n = 0; n < N; ++n)
       if (dims[n] > 128) {
-        set_error("TUCKER_PREC_BF16X4 needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
+        set_error("split precision needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
         return TUCKER_EUNSUPPORTED;
       }
   }
@@ -328,6 +330,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   // takes ||X||^2 as the trace of its first Gram (equal in exact arithmetic;
   // the 21-bit rounding of the Gram moves it by ~1e-10 relative), saving a
   // float64-bound pass over X; it is read back after the first Gram.
+  // (the E4M3 Gram rounds entries to 15 bits: its trace is too coarse for the threshold)
   const bool norm_from_trace = prec == TUCKER_PREC_BF16X4;
   const int keep_all = !(eps > 0.0);
   double nx2 = 0.0, threshold = 0.0;
@@ -381,12 +384,12 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
 
     // Gram step (with L > 1 its exponent pass also leaves the column exponents the TTM needs)
     DevBuf colexp;
-    if (prec == TUCKER_PREC_BF16X4) {
+    if (split) {
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
       if (L > 1) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
       TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof,
-                                 L > 1 ? colexp.as<int>() : nullptr));
+                                 L > 1 ? colexp.as<int>() : nullptr, f8));
       TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
       if (k == 0 && norm_from_trace) {
         TK_CHECK(launch_trace(S.as<double>(), J, d_nx2, s));
@@ -409,7 +412,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     TK_CUDA(cudaMemcpyAsync(h, d_tail, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(h + 8, lam.as<double>(), sizeof(double) * J, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
-    if (prec == TUCKER_PREC_BF16X4 && reinterpret_cast<int *>(h + 5)[0] != 0) {
+    if (split && reinterpret_cast<int *>(h + 5)[0] != 0) {
       set_error("split-precision Gram: a bounded tensor-core wait expired (mode %d)", n);
       return TUCKER_ETIMEOUT;
     }
@@ -450,7 +453,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     }
     DevBuf ynew;
     TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
-    if (prec == TUCKER_PREC_BF16X4)
+    if (split)
       TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, factor_bufs[n].as<double>(), R, ynew.as<double>(), d_terr, dev, s,
                                 &prof, L > 1 ? colexp.as<int>() : nullptr));
     else
@@ -605,7 +608,7 @@ static int hooi_iterate(const void *X, tucker_dtype dt, int max_iters, double to
       const int64_t J = cur[m], R = out->ranks[m];
       DevBuf ynew;
       TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
-      if (prec == TUCKER_PREC_BF16X4)
+      if (prec != TUCKER_PREC_FP64)
         TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, out->factors[m], R, ynew.as<double>(), d_terr, dev, s, &prof));
       else
         TK_CHECK(launch_ttm(Y, ydt, L, J, B, out->factors[m], /*ak=*/J, /*aj=*/1, R, ynew.as<double>(), dev, s,
@@ -798,7 +801,7 @@ int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, d
     set_error("unknown dtype %d", (int)dt);
     return TUCKER_EINVAL;
   }
-  if (prec != TUCKER_PREC_FP64 && prec != TUCKER_PREC_BF16X4) {
+  if (prec != TUCKER_PREC_FP64 && prec != TUCKER_PREC_BF16X4 && prec != TUCKER_PREC_E4M3X4) {
     set_error("unknown precision %d", (int)prec);
     return TUCKER_EINVAL;
   }
@@ -1172,7 +1175,20 @@ int tucker_gram(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B,
   return TUCKER_OK;
 }
 
+static int gram_split_entry(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream,
+                            bool f8);
+
 int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream) {
+  return gram_split_entry(Y, dt, L, J, B, S, stream, false);
+}
+
+int tucker_gram_split_e4m3(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S,
+                           void *stream) {
+  return gram_split_entry(Y, dt, L, J, B, S, stream, true);
+}
+
+static int gram_split_entry(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *S, void *stream,
+                            bool f8) {
   g_err[0] = 0;
   if (!Y || !S || L < 1 || B < 1 || J < 1 || (dt != TUCKER_F64 && dt != TUCKER_F32)) {
     set_error("invalid arguments to tucker_gram_split");
@@ -1188,7 +1204,7 @@ int tucker_gram_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int6
   Prof prof(s);
   DevBuf ws;
   TK_CHECK(ws.alloc(sizeof(double) * gram_split_workspace_doubles(L, J, B, dev), s));
-  TK_CHECK(launch_gram_split(Y, dt, L, J, B, S, ws.as<double>(), dev, s, &prof));
+  TK_CHECK(launch_gram_split(Y, dt, L, J, B, S, ws.as<double>(), dev, s, &prof, nullptr, f8));
   int herr = 0;
   TK_CHECK(gram_split_error(ws.as<double>(), L, J, B, dev, &herr, s));
   TK_CUDA(cudaStreamSynchronize(s));

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtucker_gb300.so")
 
 F64, F32 = 0, 1
-PREC = {"fp64": 0, "bf16x4": 1}
+PREC = {"fp64": 0, "bf16x4": 1, "e4m3x4": 2}
 PHASES = ("norm", "gram", "gram_reduce", "eig", "rank", "ttm", "scale", "ttm_l1")
 
 # Every symbol include/tucker.h declares (checked by the CPU test suite).
@@ -28,7 +28,7 @@ EXPORTS = (
     "tucker_norm2", "tucker_gram", "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_status_string",
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
-    "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak",
+    "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak", "tucker_gram_split_e4m3",
 )
 EIG_PATHS = ("mixed", "jacobi", "jacobi_fallback")
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
@@ -101,6 +101,7 @@ def load(path=LIB_PATH):
         "tucker_ttm": (i32, [vp, i32, i64, i64, i64, vp, i64, i32, vp, vp]),
         "tucker_gram_noalloc": (i32, [vp, i32, i64, i64, i64, vp, vp]),
         "tucker_gram_split": (i32, [vp, i32, i64, i64, i64, vp, vp]),
+        "tucker_gram_split_e4m3": (i32, [vp, i32, i64, i64, i64, vp, vp]),
         "tucker_ttm_split": (i32, [vp, i32, i64, i64, i64, vp, i64, vp, vp]),
         "tucker_status_string": (ctypes.c_char_p, [i32]),
         "tucker_last_error": (ctypes.c_char_p, []),
@@ -392,6 +393,15 @@ def gram_split(y, L, J, B, stream=None):
     s = torch.empty((J, J), dtype=torch.float64, device="cuda")
     _check(lib.tucker_gram_split(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
                                  _stream(stream)))
+    return s.t()
+
+
+def gram_split_e4m3(y, L, J, B, stream=None):
+    """Split-precision Gram from E4M3 digits on the FP8 tensor cores (J <= 128)."""
+    lib = load()
+    s = torch.empty((J, J), dtype=torch.float64, device="cuda")
+    _check(lib.tucker_gram_split_e4m3(_dev_ptr(y, "y"), _dtype_code(y), int(L), int(J), int(B), _dev_ptr(s, "S"),
+                                      _stream(stream)))
     return s.t()
 
 

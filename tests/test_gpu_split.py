@@ -295,3 +295,107 @@ def test_sthosvd_split_nonfinite_and_norm_from_trace(gpu_lib):
         with pytest.raises(gpu_lib.TuckerError) as e:
             gpu_lib.sthosvd(dev(y), dims, 1e-4, precision="bf16x4")
         assert e.value.status == -6
+
+
+# ---------------------------------------------------------------------------
+# E4M3 digits (tucker_gram_split_e4m3): entries rounded to 15 bits below the
+# (row, 512-column group) power of two, four balanced base-16 digits, every
+# digit-product level accumulated exactly.  Rounding radius h = 2^(E - 16).
+# ---------------------------------------------------------------------------
+def split_bound_e4m3(y, L, J, B):
+    t = y.astype(np.float64).reshape((L, J, B), order="F")
+    yn = oracle.unfold(t, 1)
+    k = L * B
+    rmax = np.abs(yn).max(axis=1) if yn.size else np.zeros(J)
+    h = np.array([2.0 ** (math.frexp(m)[1] - 16) if m > 0 else 0.0 for m in rmax])
+    a = np.abs(yn)
+    bound = h[:, None] * a.sum(axis=1)[None, :] + a.sum(axis=1)[:, None] * h[None, :] + k * np.outer(h, h)
+    return bound + 2.0 ** -40 * (a @ a.T), oracle.gram(t, 1)
+
+
+@pytest.mark.parametrize("L,J,B,dtype", [(1, 128, 5000, np.float64), (1, 96, 3000, np.float32), (40, 128, 33, np.float64),
+                                         (7, 13, 5, np.float64), (9, 96, 700, np.float32), (1, 1, 1, np.float64),
+                                         (1, 128, 64 * 152 * 9 + 17, np.float64), (16, 77, 1001, np.float64)])
+def test_gram_e4m3_bound(gpu_lib, L, J, B, dtype):
+    rng = np.random.default_rng(L * 7 + J * 3 + B)
+    y = rng.standard_normal(L * J * B).astype(dtype)
+    s = gpu_lib.gram_split_e4m3(dev(y), L, J, B).cpu().numpy()
+    bound, ref = split_bound_e4m3(y, L, J, B)
+    assert np.array_equal(s, s.T)
+    err = np.abs(s - ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+@pytest.mark.parametrize("L,B", [(1, 3000), (6, 500), (40, 70)])
+def test_gram_e4m3_exact_on_15_bit_inputs(gpu_lib, L, B):
+    """Entries v / 2^15 with |v| < 2^15 are held exactly by the four digits,
+    and every level is an exact integer sum, so S 2^30 must equal the integer
+    Gram bit for bit: this checks the digit split, the scaled tiles, the
+    stacked N = 256 operands, the E4M3 descriptors and the drain weights."""
+    rng = np.random.default_rng(21 + L)
+    J = 128
+    v = rng.integers(-(2 ** 15) + 1, 2 ** 15, size=L * J * B)
+    y = v.astype(np.float64) / 2.0 ** 15
+    s = gpu_lib.gram_split_e4m3(dev(y), L, J, B).cpu().numpy()
+    m = v.reshape((L, J, B), order="F").transpose(1, 0, 2).reshape(J, L * B).astype(np.int64)
+    exact = m @ m.T  # |entries| < 2^30 * 3000 < 2^53
+    assert np.array_equal(s * 2.0 ** 30, exact.astype(np.float64))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_sthosvd_e4m3_ranks_and_error(gpu_lib, eps):
+    """ST-HOSVD with the E4M3 Gram on a combustion-shaped float32 tensor.
+
+    Rounding every entry to 15 bits adds about (2^E / rms)^2 2^-32 / 12 of
+    ||Y||^2 (a few 1e-9 for Gaussian-like data) to the discarded eigenvalue
+    sum.  At eps = 1e-3 (threshold 2e-7 ||X||^2 per mode) that is far below
+    the threshold and the ranks are the oracle's; at eps = 1e-4 (2e-9) it is
+    not, and the rank rule, which sees the larger tails, keeps more: the
+    ranks are then at least the oracle's and the error stays within eps."""
+    dims, ranks = (48, 40, 36, 12, 10), (12, 10, 10, 6, 4)
+    x = tucker_tensor_np(dims, ranks, seed=5, decay=0.15, smooth=True, noise=1e-6, dtype="f32")
+    xo = x.astype(np.float64)
+    ref = oracle.sthosvd(xo, dims, eps)
+    res = gpu_lib.sthosvd(dev(x), dims, eps, precision="e4m3x4")
+    if eps >= 1e-3:
+        assert res.ranks == ref["ranks"]
+    else:
+        assert all(a >= b for a, b in zip(res.ranks, ref["ranks"])), (res.ranks, ref["ranks"])
+    for n in range(len(dims)):
+        u = res.factor(n).cpu().numpy()
+        assert np.abs(u.T @ u - np.eye(res.ranks[n])).max() <= 1e-12
+    rel = gpu_lib.rel_error(dev(x), res)
+    assert rel <= eps
+    if res.ranks == ref["ranks"]:
+        rel_ref = oracle.rel_error(xo, ref["core"], ref["ranks"], ref["factors"])
+        assert abs(rel - rel_ref) <= 0.1 * eps, (rel, rel_ref)
+
+
+def test_float32_combustion_workload_full_size(gpu_lib):
+    """The float32 combustion-shaped workload at its stated size (96^3 x 32 x
+    24, 2.7 GB, generating ranks (40, 40, 40, 20, 10), eps = 1e-4) against the
+    float64 oracle: the BF16 digits give the oracle's ranks and an error within
+    1e-3 eps of it; the E4M3 digits give ranks at least the oracle's and an
+    error within eps (their measured difference is what the bench reports)."""
+    dims, ranks = (96, 96, 96, 32, 24), (40, 40, 40, 20, 10)
+    x = tucker_tensor_np(dims, ranks, seed=0, decay=0.15, smooth=True, noise=1e-6, dtype="f32")
+    xo = x.astype(np.float64)
+    eps = 1e-4
+    ref = oracle.sthosvd(xo, dims, eps)
+    assert ref["ranks"] == ranks
+    rel_ref = oracle.rel_error(xo, ref["core"], ref["ranks"], ref["factors"])
+    xd = dev(x)
+    res = gpu_lib.sthosvd(xd, dims, eps, precision="bf16x4")
+    assert res.ranks == ref["ranks"]
+    rel = gpu_lib.rel_error(xd, res)
+    assert abs(rel - rel_ref) <= 1e-3 * eps, (rel, rel_ref)
+    for n in range(len(dims)):
+        u = res.factor(n).cpu().numpy()
+        v = ref["factors"][n]
+        sines = np.linalg.svd(u - v @ (v.T @ u), compute_uv=False)
+        assert sines.max() <= 1e-6, (n, sines.max())
+    res.free()
+    res = gpu_lib.sthosvd(xd, dims, eps, precision="e4m3x4")
+    assert all(a >= b for a, b in zip(res.ranks, ref["ranks"])), res.ranks
+    assert gpu_lib.rel_error(xd, res) <= eps
+    res.free()
