@@ -255,11 +255,16 @@ GramPlan gram_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
 // mode-n product Z(L, K, B) = sum_j A[k, j] Y(L, J, B).  CTA (xsplit, ktile)
 // stages A[k0 .. k0 + kt, :] (as As[j][kl]) once and then streams its column
 // range in chunks of kc columns (Ys[j][kk]); each thread owns 4 k x 4
-// columns.  The DIFF variant reads X instead of writing Z and accumulates
-// (x - z)^2 per CTA (fixed grid, fixed order).
+// columns.  For long contractions (J > kTtmWholeJ) the j range is streamed
+// too, jc rows of A and Y at a time with the accumulators kept in registers,
+// so that shared memory no longer limits the tile to a few warps.  The DIFF
+// variant reads X instead of writing Z and accumulates (x - z)^2 per CTA
+// (fixed grid, fixed order).
 // ---------------------------------------------------------------------------
+constexpr int kTtmWholeJ = 128;   // up to this J, A's tile stays in shared memory for the whole run
+constexpr int kTtmMaxCols = 128;  // columns per chunk (upper bound)
 struct TtmPlan {
-  int J, K, kt, ktp, kc, nkg, ncg, threads, ktiles, xsplit;
+  int J, K, kt, ktp, kc, nkg, ncg, threads, ktiles, xsplit, jc;
   int64_t cols_per_cta, Kc;
   size_t smem;
 };
@@ -270,15 +275,20 @@ __global__ void __launch_bounds__(512) k_ttm(const T *__restrict__ y, int64_t L,
                                              double *__restrict__ z, const TX *__restrict__ x,
                                              double *__restrict__ partial) {
   extern __shared__ __align__(16) double sm[];
-  double *As = sm;                             // [J][ktp]
-  double *Ys = sm + (size_t)p.J * p.ktp;       // [J][kc]
-  __shared__ int64_t colin[kMaxCols], colout[kMaxCols];
+  double *As = sm;                             // [jc][ktp]
+  double *Ys = sm + (size_t)p.jc * p.ktp;      // [jc][kc]
+  __shared__ int64_t colin[kTtmMaxCols], colout[kTtmMaxCols];
   const int k0 = blockIdx.y * p.kt;
   const int kt = min(p.kt, p.K - k0);
-  for (int e = threadIdx.x; e < p.J * p.ktp; e += blockDim.x) {
-    const int j = e / p.ktp, kl = e - j * p.ktp;
-    As[e] = (kl < kt) ? a[(int64_t)(k0 + kl) * ak + (int64_t)j * aj] : 0.0;
-  }
+  const bool stream_j = p.jc < p.J;
+  // rows j0 .. j0 + nj of A's tile into As
+  auto load_a = [&](int j0, int nj) {
+    for (int e = threadIdx.x; e < nj * p.ktp; e += blockDim.x) {
+      const int j = e / p.ktp, kl = e - j * p.ktp;
+      As[e] = (kl < kt) ? a[(int64_t)(k0 + kl) * ak + (int64_t)(j0 + j) * aj] : 0.0;
+    }
+  };
+  if (!stream_j) load_a(0, p.J);
   int kg, cg;
   if (L == 1) {
     kg = threadIdx.x % p.nkg;
@@ -304,30 +314,36 @@ __global__ void __launch_bounds__(512) k_ttm(const T *__restrict__ y, int64_t L,
       colin[t] = vi;
       colout[t] = vo;
     }
-    __syncthreads();
-    load_chunk(y, L, p.J, p.J, p.kc, colin, Ys, p.kc, 1);
-    __syncthreads();
-    if (active) {
-      double acc[4][4];
+    double acc[4][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-      const double *pa = As + 4 * kg;
-      const double *py = Ys + 4 * cg;
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    for (int j0 = 0; j0 < p.J; j0 += p.jc) {
+      const int nj = min(p.jc, p.J - j0);
+      __syncthreads();  // colin / colout written; the previous stage's reads done
+      if (stream_j) load_a(j0, nj);
+      load_chunk(y + (L == 1 ? (int64_t)j0 : L * (int64_t)j0), L, nj, nj, p.kc, colin, Ys, p.kc, 1);
+      __syncthreads();
+      if (active) {
+        const double *pa = As + 4 * kg;
+        const double *py = Ys + 4 * cg;
 #pragma unroll 4
-      for (int j = 0; j < p.J; ++j) {
-        const double2 a01 = *reinterpret_cast<const double2 *>(pa + j * p.ktp);
-        const double2 a23 = *reinterpret_cast<const double2 *>(pa + j * p.ktp + 2);
-        const double2 y01 = *reinterpret_cast<const double2 *>(py + j * p.kc);
-        const double2 y23 = *reinterpret_cast<const double2 *>(py + j * p.kc + 2);
-        const double av[4] = {a01.x, a01.y, a23.x, a23.y};
-        const double yv[4] = {y01.x, y01.y, y23.x, y23.y};
+        for (int j = 0; j < nj; ++j) {
+          const double2 a01 = *reinterpret_cast<const double2 *>(pa + j * p.ktp);
+          const double2 a23 = *reinterpret_cast<const double2 *>(pa + j * p.ktp + 2);
+          const double2 y01 = *reinterpret_cast<const double2 *>(py + j * p.kc);
+          const double2 y23 = *reinterpret_cast<const double2 *>(py + j * p.kc + 2);
+          const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+          const double yv[4] = {y01.x, y01.y, y23.x, y23.y};
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], yv[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], yv[c], acc[r][c]);
+        }
       }
+    }
+    if (active) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int64_t base = colout[4 * cg + c];
@@ -362,18 +378,30 @@ TtmPlan ttm_plan(int64_t L, int64_t J, int64_t B, int64_t K, const DeviceInfo &d
   p.K = (int)K;
   p.Kc = L * B;
   // k tile: As must fit in ~96 KB; at most 128 outputs per tile.
-  int ktp_max = std::max(4, std::min(128, (int)(12288 / J) / 4 * 4));
-  const int ktiles = (int)((K + ktp_max - 1) / ktp_max);
-  p.kt = (int)((K + ktiles - 1) / ktiles);
-  p.ktp = (p.kt + 3) / 4 * 4;
-  p.ktiles = ktiles;
-  p.nkg = p.ktp / 4;
-  // column chunk: Ys within ~64 KB, threads <= 512.
-  p.kc = std::max(4, std::min(kMaxCols, (int)(8192 / J) / 4 * 4));
-  while ((p.kc / 4) * p.nkg > 512 && p.kc > 4) p.kc -= 4;
+  if (J <= kTtmWholeJ) {
+    p.jc = (int)J;
+    int ktp_max = std::max(4, std::min(128, (int)(12288 / J) / 4 * 4));
+    const int ktiles = (int)((K + ktp_max - 1) / ktp_max);
+    p.kt = (int)((K + ktiles - 1) / ktiles);
+    p.ktp = (p.kt + 3) / 4 * 4;
+    p.ktiles = ktiles;
+    p.nkg = p.ktp / 4;
+    // column chunk: Ys within ~64 KB, threads <= 512.
+    p.kc = std::max(4, std::min(kMaxCols, (int)(8192 / J) / 4 * 4));
+    while ((p.kc / 4) * p.nkg > 512 && p.kc > 4) p.kc -= 4;
+  } else {
+    // streamed j: at most 64 outputs a tile, columns enough for 256..512 threads, 64 rows a stage
+    p.jc = 64;
+    const int ktiles = (int)((K + 63) / 64);
+    p.kt = (int)((K + ktiles - 1) / ktiles);
+    p.ktp = (p.kt + 3) / 4 * 4;
+    p.ktiles = ktiles;
+    p.nkg = p.ktp / 4;
+    p.kc = 4 * std::max(8, std::min(kTtmMaxCols / 4, 512 / p.nkg));
+  }
   p.ncg = p.kc / 4;
   p.threads = (p.nkg * p.ncg + 31) / 32 * 32;
-  p.smem = ((size_t)p.J * p.ktp + (size_t)p.J * p.kc) * sizeof(double);
+  p.smem = ((size_t)p.jc * p.ktp + (size_t)p.jc * p.kc) * sizeof(double);
   int occ = occupancy(k_ttm<T, TX, DIFF>, p.threads, p.smem);
   const int64_t slots = (int64_t)dev.sms * occ;
   const int64_t chunks = (p.Kc + p.kc - 1) / p.kc;
