@@ -170,8 +170,9 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
 // The calling thread's last mixed-precision check: residual and its bound,
 // orthogonality and its bound, and the number of unresolved tail columns.
 const double *mp_last_check();
-// Largest J the mixed-precision eigensolver takes: 256 (the wide float32
-// stage above 128), or 128 with TUCKER_EIG_WIDE=0.
+// Largest J the mixed-precision eigensolver takes: 512 (float32 stages: the
+// tridiagonal one up to 128, the wide one up to 256, a cluster Jacobi up to
+// 512), or 128 with TUCKER_EIG_WIDE=0.
 int mp_max_j();
 // Float64 fused multiply-add throughput of the device (TFLOP/s) and the timed
 // launch's duration; synchronises s.

@@ -48,6 +48,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace tk {
@@ -55,8 +57,9 @@ namespace tk {
 namespace {
 
 constexpr int kTriMaxJ = 128;   // float32 stages with the whole matrix in shared memory
-constexpr int kMpMaxJ = 256;    // the solver as a whole (wide float32 stage above kTriMaxJ)
-constexpr int kGemmMaxK = 256;  // contraction length of the small float64 products
+constexpr int kWideMaxJ = 256;  // the wide float32 stage (packed triangle in shared memory)
+constexpr int kMpMaxJ = 512;    // the solver as a whole (cluster float32 Jacobi above kWideMaxJ)
+constexpr int kGemmMaxK = 256;  // contraction rows the small float64 products stage at a time
 constexpr int kJ32Threads = 1024;
 constexpr int kJ32MaxSweeps = 40;
 constexpr int kMaxDepth = 5;
@@ -1025,7 +1028,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
 }
 
 // ---------------------------------------------------------------------------
-// First stage for kTriMaxJ < n <= kMpMaxJ (one CTA of kW32Threads), the steps
+// First stage for kTriMaxJ < n <= kWideMaxJ (one CTA of kW32Threads), the steps
 // of k_eig32_tri with a matrix too large for a full float32 copy in shared
 // memory.  The lower triangle is packed by columns in shared memory (column
 // j holds rows j..n-1 from offset j n - j (j - 1) / 2: 129 KB at n = 256);
@@ -1391,6 +1394,194 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__r
 }
 
 // ---------------------------------------------------------------------------
+// First stage for kWideMaxJ < n <= kMpMaxJ: float32 parallel-order cyclic
+// Jacobi on A / max|A| over a cluster of kJ32ClCtas CTAs.  The float32 S
+// (full, row-major, kept symmetric) and V (column-major) of m = n rounded up
+// to a multiple of 4 live in global memory (4 MB at n = 512: L2-resident)
+// and are updated in place.  Each step of the round-robin tournament (every
+// pair meets once in m - 1 steps): every CTA forms the step's m/2 rotations
+// from S's current entries (the same values in every CTA), applies its fixed
+// share of the 2 x 2 blocks {p_P, q_P} x {p_Q, q_Q} of S (P <= Q, mirrored)
+// and of V's column pairs.  The cluster meets at two barriers per step (after
+// the rotations are read, so that no CTA overwrites an entry another is still
+// reading, and after the updates), whose release/acquire order makes the
+// step's writes visible to the next step.
+// S and V are read and written at L2 (ld.global.cg): no stale L1 line of
+// another CTA's data is ever read.  A rotation is taken while |s_pq|
+// exceeds 2^-23 times the largest diagonal magnitude at the start of the
+// sweep, as in k_jacobi32; the sweeps stop when a whole sweep takes none
+// (the cluster agrees through per-CTA flags) or after kJ32MaxSweeps.
+// Writes X = V (float64, unsorted columns) and the number of sweeps.
+// ---------------------------------------------------------------------------
+constexpr int kJ32ClCtas = 16;
+constexpr int kJ32ClThreads = 1024;
+constexpr int kJ32ClBlocksPerThread = (kMpMaxJ / 2) * (kMpMaxJ / 2 + 1) / 2 / (kJ32ClCtas * kJ32ClThreads) + 1;
+constexpr int kJ32ClVPerThread = (kMpMaxJ / 2) * (kMpMaxJ / 4) / (kJ32ClCtas * kJ32ClThreads);
+
+__global__ void __launch_bounds__(kJ32ClThreads)
+    k_jacobi32_cl(const double *__restrict__ A, int lda, int n, float *S, float *V, int *flags,
+                  double *__restrict__ X, int ldx, int *__restrict__ sweeps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ float4 rot[kMpMaxJ / 2];  // per pair: c, s, t = s / c, (p | q << 16) as bits
+  __shared__ float red[kJ32ClThreads / 32];
+  __shared__ float scale_s, tol_s;
+  __shared__ int rotated;
+  const int m = (n + 3) & ~3, np = m / 2;
+  const int nblk = np * (np + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = (int)cl.block_rank();
+  const int gt = rank * kJ32ClThreads + tid, gstride = kJ32ClCtas * kJ32ClThreads;
+
+  // scale: every CTA finds max|A| itself
+  float mx = 0.f;
+  for (int e = tid; e < n * n; e += kJ32ClThreads) mx = fmaxf(mx, (float)fabs(A[(e % n) + (int64_t)lda * (e / n)]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float v = 0.f;
+    for (int w = 0; w < kJ32ClThreads / 32; ++w) v = fmaxf(v, red[w]);
+    scale_s = v;
+  }
+  __syncthreads();
+  const double inv = scale_s > 0.f ? 1.0 / (double)scale_s : 0.0;
+  for (int e = gt; e < m * m; e += gstride) {
+    const int i = e / m, j = e - (e / m) * m;
+    const int lo = min(i, j), hi = max(i, j);  // read the upper triangle, mirror it
+    __stcg(S + e, (hi < n) ? (float)(A[lo + (int64_t)lda * hi] * inv) : 0.f);
+    __stcg(V + e, (i == j) ? 1.f : 0.f);
+  }
+  // this thread's blocks (P, Q), P <= Q, fixed for the whole run
+  int myblk[kJ32ClBlocksPerThread];
+#pragma unroll
+  for (int k = 0; k < kJ32ClBlocksPerThread; ++k) {
+    const int e = gt + k * gstride;
+    myblk[k] = -1;
+    if (e < nblk) {
+      int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((q + 1) * (q + 2) / 2 <= e) ++q;
+      while (q * (q + 1) / 2 > e) --q;
+      myblk[k] = (e - q * (q + 1) / 2) | (q << 16);
+    }
+  }
+  cl.sync();
+
+  int sweep = 0;
+  for (; sweep < kJ32MaxSweeps; ++sweep) {
+    if (warp == 0) {
+      float d = 0.f;
+      for (int i = lane; i < m; i += 32) d = fmaxf(d, fabsf(__ldcg(S + (int64_t)i * m + i)));
+      for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+      if (lane == 0) {
+        tol_s = FLT_EPSILON * fmaxf(d, FLT_MIN);
+        rotated = 0;
+      }
+    }
+    __syncthreads();
+    const float tol = tol_s;
+    for (int step = 0; step < m - 1; ++step) {
+      if (tid < np) {
+        const int t = tid;
+        int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
+        int q = ((m - 2 - t + step) % (m - 1)) + 1;
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        float c = 1.f, sv = 0.f, tt = 0.f;
+        const float b = __ldcg(S + (int64_t)p * m + q);
+        if (fabsf(b) > tol) {
+          const float a = __ldcg(S + (int64_t)p * m + p), d = __ldcg(S + (int64_t)q * m + q);
+          const float tau = __fdividef(d - a, 2.f * b);
+          const float at = fabsf(tau);
+          const float h = fmaf(tau, tau, 1.f);
+          tt = at > 1e18f ? __fdividef(0.5f, tau) : copysignf(__fdividef(1.f, at + h * rsqrtf(h)), tau);
+          c = rsqrtf(fmaf(tt, tt, 1.f));
+          sv = tt * c;
+          if (sv != 0.f) rotated = 1;
+        }
+        rot[t] = make_float4(c, sv, tt, __int_as_float(p | (q << 16)));
+      }
+      // every CTA has read the entries its rotations come from before any CTA
+      // overwrites them (the diagonal blocks' owners zero s_pq)
+      cl.sync();
+#pragma unroll
+      for (int k = 0; k < kJ32ClBlocksPerThread; ++k) {
+        const int pq = myblk[k];
+        if (pq < 0) continue;
+        const int P = pq & 0xFFFF, Q = pq >> 16;
+        const float4 rP = rot[P];
+        if (P == Q) {
+          if (rP.y == 0.f) continue;
+          const int kk = __float_as_int(rP.w), p1 = kk & 0xFFFF, q1 = kk >> 16;
+          float *spq = S + (int64_t)p1 * m + q1;
+          const float b = __ldcg(spq);
+          __stcg(S + (int64_t)p1 * m + p1, __ldcg(S + (int64_t)p1 * m + p1) - rP.z * b);
+          __stcg(S + (int64_t)q1 * m + q1, __ldcg(S + (int64_t)q1 * m + q1) + rP.z * b);
+          __stcg(spq, 0.f);
+          __stcg(S + (int64_t)q1 * m + p1, 0.f);
+          continue;
+        }
+        const float4 rQ = rot[Q];
+        const float s1 = rP.y, s2 = rQ.y;
+        if (s1 == 0.f && s2 == 0.f) continue;
+        const float c1 = rP.x, c2 = rQ.x;
+        const int kP = __float_as_int(rP.w), kQ = __float_as_int(rQ.w);
+        const int64_t p1 = kP & 0xFFFF, q1 = kP >> 16, p2 = kQ & 0xFFFF, q2 = kQ >> 16;
+        const float x11 = __ldcg(S + p1 * m + p2), x12 = __ldcg(S + p1 * m + q2);
+        const float x21 = __ldcg(S + q1 * m + p2), x22 = __ldcg(S + q1 * m + q2);
+        const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+        const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+        const float z11 = y11 * c2 - y12 * s2, z12 = y11 * s2 + y12 * c2;
+        const float z21 = y21 * c2 - y22 * s2, z22 = y21 * s2 + y22 * c2;
+        __stcg(S + p1 * m + p2, z11);
+        __stcg(S + p2 * m + p1, z11);
+        __stcg(S + p1 * m + q2, z12);
+        __stcg(S + q2 * m + p1, z12);
+        __stcg(S + q1 * m + p2, z21);
+        __stcg(S + p2 * m + q1, z21);
+        __stcg(S + q1 * m + q2, z22);
+        __stcg(S + q2 * m + q1, z22);
+      }
+      // V's column pairs: unit u = (pair t, row quad r4)
+      const int nq = m / 4;
+#pragma unroll
+      for (int k = 0; k <= kJ32ClVPerThread; ++k) {
+        const int u = gt + k * gstride;
+        if (u >= np * nq) continue;
+        const int t = u / nq, r4 = u - t * nq;
+        const float4 r = rot[t];
+        if (r.y == 0.f) continue;
+        const float c = r.x, sv = r.y;
+        const int kk = __float_as_int(r.w);
+        float4 *vp = reinterpret_cast<float4 *>(V + (int64_t)(kk & 0xFFFF) * m) + r4;
+        float4 *vq = reinterpret_cast<float4 *>(V + (int64_t)(kk >> 16) * m) + r4;
+        const float4 a = __ldcg(vp), b = __ldcg(vq);
+        __stcg(vp, make_float4(c * a.x - sv * b.x, c * a.y - sv * b.y, c * a.z - sv * b.z, c * a.w - sv * b.w));
+        __stcg(vq, make_float4(sv * a.x + c * b.x, sv * a.y + c * b.y, sv * a.z + c * b.z, sv * a.w + c * b.w));
+      }
+      cl.sync();
+    }
+    // the cluster agrees on whether any CTA rotated during the sweep
+    if (tid == 0) __stcg(flags + (sweep & 1) * kJ32ClCtas + rank, rotated);
+    cl.sync();
+    int any = 0;
+    for (int r = 0; r < kJ32ClCtas; ++r) any |= __ldcg(flags + (sweep & 1) * kJ32ClCtas + r);
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  for (int e = gt; e < n * n; e += gstride) {
+    const int i = e % n, j = e / n;
+    X[i + (int64_t)ldx * j] = (double)__ldcg(V + (int64_t)j * m + i);
+  }
+  if (rank == 0 && tid == 0 && sweeps) *sweeps = sweep;
+}
+
+// ---------------------------------------------------------------------------
 // C (M x N) = op(A) B (+ D), float64, column-major.  op(A) = A (M x K, lda) or
 // A^T (A is K x M).  8 x 8 outputs per CTA of 64 threads; the CTA's rows of
 // op(A) and columns of B (K <= 256) are staged in shared memory.  C may alias
@@ -1404,20 +1595,24 @@ __global__ void __launch_bounds__(kGT *kGT) k_dgemm_small(int M, int N, int K, c
   __shared__ double Bs[kGT][kGemmMaxK + 1];
   const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
   const int tx = threadIdx.x % kGT, ty = threadIdx.x / kGT;
-  for (int e = threadIdx.x; e < kGT * K; e += kGT * kGT) {
-    const int r = e % kGT, k = e / kGT;
-    const int i = m0 + r;
-    double a = 0.0;
-    if (i < M) a = transA ? A[k + (int64_t)lda * i] : A[i + (int64_t)lda * k];
-    As[r][k] = a;
-    const int j = n0 + r;
-    Bs[r][k] = j < N ? B[k + (int64_t)ldb * j] : 0.0;
-  }
-  __syncthreads();
   const int i = m0 + tx, j = n0 + ty;
-  if (i >= M || j >= N) return;
   double acc = 0.0;
-  for (int k = 0; k < K; ++k) acc = fma(As[tx][k], Bs[ty][k], acc);
+  for (int k0 = 0; k0 < K; k0 += kGemmMaxK) {  // contraction rows in stages of kGemmMaxK
+    const int kn = min(kGemmMaxK, K - k0);
+    if (k0 > 0) __syncthreads();
+    for (int e = threadIdx.x; e < kGT * kn; e += kGT * kGT) {
+      const int r = e % kGT, k = k0 + e / kGT;
+      const int ii = m0 + r;
+      double a = 0.0;
+      if (ii < M) a = transA ? A[k + (int64_t)lda * ii] : A[ii + (int64_t)lda * k];
+      As[r][k - k0] = a;
+      const int jj = n0 + r;
+      Bs[r][k - k0] = jj < N ? B[k + (int64_t)ldb * jj] : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < kn; ++k) acc = fma(As[tx][k], Bs[ty][k], acc);
+  }
+  if (i >= M || j >= N) return;
   if (D) acc += D[i + (int64_t)ldd * j];
   C[i + (int64_t)ldc * j] = acc;
 }
@@ -1450,7 +1645,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // Per-CTA partial sums: part[3 b + 0] = ||off(S)||^2, [1] = ||I - X^T X||^2,
-// [2] = ||A||^2 (with G == nullptr: [0] = ||A - mu I||^2, mu = tr(A) / m).
+// [2] = ||A||^2 (with G == nullptr: [0] = ||A - mu I||^2, [1] = mu = tr(A) / m).
 __global__ void __launch_bounds__(kStatThreads) k_oa_stats(const double *__restrict__ G, int m,
                                                            const double *__restrict__ A, int lda,
                                                            double *__restrict__ part) {
@@ -1486,9 +1681,14 @@ __global__ void __launch_bounds__(kStatThreads) k_oa_stats(const double *__restr
   a2 = block_sum(a2, red);
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x + 0] = off2;
-    part[3 * blockIdx.x + 1] = r2;
+    part[3 * blockIdx.x + 1] = G ? r2 : mu;  // without G: the mean of the diagonal
     part[3 * blockIdx.x + 2] = a2;
   }
+}
+
+// A <- A - mu I (m x m, ld lda).
+__global__ void k_shift_diag(double *A, int lda, int m, double mu) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) A[i + (int64_t)lda * i] -= mu;
 }
 
 // A total order on doubles as unsigned integers (finite values and +-0).
@@ -1582,6 +1782,14 @@ __global__ void __launch_bounds__(kStatThreads) k_oa_E(const double *__restrict_
     if (a == b || lab[a] == lab[b]) v = 0.5 * r;
     else v = (0.5 * (S[i + (int64_t)m * j] + S[j + (int64_t)m * i]) + lam[j] * r) / (lam[j] - lam[i]);
     E[e] = v;
+  }
+}
+
+// P <- (3 I - P) / 2 (the Newton-Schulz coefficient matrix; P is m x m).
+__global__ void k_ns_coef(double *P, int m) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e % m, j = e / m;
+    P[e] = (i == j ? 1.5 : 0.0) - 0.5 * P[e];
   }
 }
 
@@ -1709,12 +1917,40 @@ struct MpWork {
   }
 };
 
+// The cluster Jacobi stage on a 16-CTA cluster (non-portable size, allowed
+// explicitly).  tx (float64, ld m) receives V.
+int launch_jacobi32_cl(const double *A, int lda, int m, float *S32, float *V32, int *flags, double *X, int ldx,
+                       int *sweeps, cudaStream_t s) {
+  static const bool ok = [] {
+    if (cudaFuncSetAttribute(k_jacobi32_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  }();
+  if (!ok) {
+    set_error("the eigensolver's 16-CTA cluster is not available on this device");
+    return TUCKER_EUNSUPPORTED;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kJ32ClCtas);
+  cfg.blockDim = dim3(kJ32ClThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = kJ32ClCtas;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  TK_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi32_cl, A, lda, m, S32, V32, flags, X, ldx, sweeps));
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
 int gemm(int M, int N, int K, const double *A, int lda, int transA, const double *B, int ldb, const double *D, int ldd,
          double *C, int ldc, cudaStream_t s) {
-  if (K > kGemmMaxK) {
-    set_error("small GEMM: K = %d exceeds %d", K, kGemmMaxK);
-    return TUCKER_EINVAL;
-  }
   dim3 grid((M + kGT - 1) / kGT, (N + kGT - 1) / kGT);
   k_dgemm_small<<<grid, kGT * kGT, 0, s>>>(M, N, K, A, lda, transA, B, ldb, D, ldd, C, ldc);
   TK_LAUNCHED();
@@ -1730,7 +1966,8 @@ int products(const double *A, int lda, int m, double *tx, double *G, cudaStream_
 }
 
 // ||A - mu I||_F (mu = tr(A) / m) and ||A||_F, on the host.
-int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStream_t s, double *dev, double *norm) {
+int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStream_t s, double *dev, double *norm,
+                     double *mean = nullptr) {
   k_oa_stats<<<kStatBlocks, kStatThreads, 0, s>>>(nullptr, m, A, lda, w.part);
   TK_LAUNCHED();
   double h[3 * kStatBlocks];
@@ -1743,6 +1980,7 @@ int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStrea
   }
   *dev = std::sqrt(d2);
   if (norm) *norm = std::sqrt(a2);
+  if (mean) *mean = h[1];
   return TUCKER_OK;
 }
 
@@ -1753,7 +1991,7 @@ int scalar_deviation(const double *A, int lda, int m, const MpWork &w, cudaStrea
 // sum to at most budget are left unresolved; their column count goes to
 // *skipped.
 int mp_level(const double *A, int lda, int m, double noise, int depth, const MpWork &w, double *out, cudaStream_t s,
-             double budget, double tail_after, double tail_err, int *skipped) {
+             double budget, double tail_after, double tail_err, int *skipped, double shift = 0.0) {
   double *tx0 = w.tx(depth, 0), *tx1 = w.tx(depth, 1);
   double *G = w.g(depth), *E = w.e(depth);
   int *label = w.labels + depth * w.J, *perm = w.perms + depth * w.J;
@@ -1764,7 +2002,28 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
     const char *e = std::getenv("TUCKER_EIG32");
     return e && std::strcmp(e, "jacobi") == 0;
   }();
-  if (m > kTriMaxJ) {  // the wide stage; E (m x m float64) holds its two float arrays until the first step's E
+  if (m > kWideMaxJ) {  // the cluster Jacobi stage: S, V and the flags in this depth's (free) tx1 region
+    const int mp = (m + 3) & ~3;
+    float *f = reinterpret_cast<float *>(w.tx(depth, 1));
+    f += (4 - (reinterpret_cast<uintptr_t>(f) / sizeof(float)) % 4) % 4;  // 16-byte aligned
+    float *S32 = f, *V32 = f + (size_t)mp * mp;
+    int *flags = reinterpret_cast<int *>(V32 + (size_t)mp * mp);
+    TK_CHECK(launch_jacobi32_cl(A, lda, m, S32, V32, flags, tx0 + (size_t)m * m, m, depth == 0 ? w.sweeps : nullptr,
+                                s));
+    // Thousands of float32 rotations per column leave ||I - X^T X|| near
+    // 1e-5 at m = 512, and the refinement's cluster width grows with it
+    // (the ||A|| ||R|| term): two Newton-Schulz steps X <- X (3 I - X^T X) / 2
+    // in float64 bring it to rounding level first (R -> ~(3/4) R^2 each).
+    double *X = tx0 + (size_t)m * m, *Xn = tx1 + (size_t)m * m;
+    for (int it = 0; it < 2; ++it) {
+      TK_CHECK(gemm(m, m, m, X, m, 1, X, m, nullptr, 0, E, m, s));
+      k_ns_coef<<<(m * m + 255) / 256, 256, 0, s>>>(E, m);
+      TK_LAUNCHED();
+      TK_CHECK(gemm(m, m, m, X, m, 0, E, m, nullptr, 0, Xn, m, s));
+      k_copy_cols<<<(m * m + 255) / 256, 256, 0, s>>>(Xn, m, X, m, m, m);
+      TK_LAUNCHED();
+    }
+  } else if (m > kTriMaxJ) {  // the wide stage; E (m x m float64) holds its two float arrays until the first step's E
     const size_t smemw = wide32_smem(m);
     TK_CUDA(allow_max_smem(k_eig32_wide));
     float *zs = reinterpret_cast<float *>(E);
@@ -1812,7 +2071,9 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
   // stay unresolved: a rank cut never falls inside them
   double suffix[kMpMaxJ + 1];
   suffix[h.nclusters] = 0.0;
-  for (int k = h.nclusters - 1; k >= 0; --k) suffix[k] = suffix[k + 1] + h.csum[k];
+  // (this level's matrix is the original one shifted by -shift)
+  for (int k = h.nclusters - 1; k >= 0; --k)
+    suffix[k] = suffix[k + 1] + h.csum[k] + shift * (double)(h.start[k + 1] - h.start[k]);
   int first_skip = h.nclusters;
   if (budget >= 0.0)
     for (int k = 0; k < h.nclusters; ++k)
@@ -1828,13 +2089,19 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
     double *T = w.t(depth), *C = w.c(depth);
     TK_CHECK(gemm(m, mc, m, A, lda, 0, X + (size_t)m * c0, m, nullptr, 0, T, m, s));
     TK_CHECK(gemm(mc, mc, m, X + (size_t)m * c0, m, 1, T, m, nullptr, 0, C, mc, s));
-    double dev = 0.0;
-    TK_CHECK(scalar_deviation(C, mc, mc, w, s, &dev, nullptr));
+    double dev = 0.0, mu = 0.0;
+    TK_CHECK(scalar_deviation(C, mc, mc, w, s, &dev, nullptr, &mu));
     if (dev <= kClusterC * mc * kU * noise) continue;
+    // The child solves C - mu I (same eigenvectors): its float32 stage then
+    // resolves the cluster's spread rather than its magnitude, and its cluster
+    // width scales with ||C - mu I||.  Without the shift a tight cluster of
+    // large eigenvalues (say 200 within 10%) stays one cluster at every depth.
+    k_shift_diag<<<(mc + 255) / 256, 256, 0, s>>>(C, mc, mc, mu);
+    TK_LAUNCHED();
     double *Q = w.e(depth + 1);  // the child's E is free once it has returned
     double *Qc = w.t(depth + 1);
     TK_CHECK(mp_level(C, mc, mc, noise, depth + 1, w, Qc, s, budget, tail_after + suffix[k + 1],
-                      tail_err + (double)(m - h.start[k + 1]) * h.delta, skipped));
+                      tail_err + (double)(m - h.start[k + 1]) * h.delta, skipped, shift + mu));
     // X_c <- X_c Q
     TK_CHECK(gemm(m, mc, mc, X + (size_t)m * c0, m, 0, Qc, mc, nullptr, 0, Q, m, s));
     k_copy_cols<<<(m * mc + 255) / 256, 256, 0, s>>>(Q, m, X + (size_t)m * c0, m, m, mc);
@@ -1855,8 +2122,9 @@ static thread_local double g_mp_check[5];
 const double *mp_last_check() { return g_mp_check; }
 
 int mp_max_j() {
-  // J above kTriMaxJ takes the wide float32 stage; TUCKER_EIG_WIDE=0 restricts
-  // the mixed-precision solver to J <= kTriMaxJ (the float64 Jacobi above)
+  // J above kTriMaxJ takes the wide float32 stage (up to kWideMaxJ) or the
+  // cluster float32 Jacobi (up to kMpMaxJ); TUCKER_EIG_WIDE=0 restricts the
+  // mixed-precision solver to J <= kTriMaxJ (the float64 Jacobi above)
   static const int lim = [] {
     const char *e = std::getenv("TUCKER_EIG_WIDE");
     return e && e[0] == '0' ? kTriMaxJ : kMpMaxJ;

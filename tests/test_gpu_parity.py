@@ -210,6 +210,33 @@ def test_eig_mp_on_tucker_grams(gpu_lib, monkeypatch, seed):
         _check_eig(gpu_lib, oracle.gram(t, n))
 
 
+@pytest.mark.parametrize("j", [257, 300, 384, 512])
+def test_eig_cluster_stage(gpu_lib, eig_path, j):
+    """256 < J <= 512: the mixed-precision solver's first stage is the float32
+    Jacobi on a 16-CTA cluster (strict: no fallback), and the float64 Jacobi."""
+    rng = np.random.default_rng(j)
+    a = rng.standard_normal((j, j + 40)) * (0.97 ** np.arange(j))[:, None]
+    _check_eig(gpu_lib, a @ a.T)
+
+
+@pytest.mark.parametrize("j,r,floor", [(300, 60, 1e-12), (512, 64, 1e-12), (512, 200, 1e-8), (512, 300, 1e-8),
+                                       (400, 200, 1e-12), (256, 200, 1e-8), (256, 120, 1e-8)])
+def test_eig_cluster_stage_tucker_grams(gpu_lib, monkeypatch, j, r, floor):
+    """Strict solves of Tucker-like Grams: r signal eigenvalues within 10% of
+    each other over a noise cluster holding `floor` of the energy.  Clusters
+    of more than 128 large, close eigenvalues are solved shifted by their
+    mean at the next level (without the shift they stayed one cluster at
+    every depth); J > 256 takes the cluster float32 stage."""
+    monkeypatch.setenv("TUCKER_EIG_KERNEL", "mp")
+    monkeypatch.setenv("TUCKER_EIG_MP_STRICT", "1")
+    rng = np.random.default_rng(j + r)
+    q, _ = np.linalg.qr(rng.standard_normal((j, j)))
+    sig = 1e4 * (1 + 0.1 * rng.standard_normal(r))
+    lam = np.concatenate([sig, floor * sig.sum() / j * (1 + 0.1 * rng.random(j - r))])
+    s = (q * lam) @ q.T
+    _check_eig(gpu_lib, 0.5 * (s + s.T))
+
+
 def test_eig_large_dim(gpu_lib):
     rng = np.random.default_rng(9)
     j = 512
