@@ -126,7 +126,8 @@ int launch_ttm_diff(const double *y, int64_t L, int64_t J, int64_t B, const doub
 // back by gram_split_error().  With L > 1 and d_colexp given (L B ints), the
 // first pass also writes every column's exponent (the scale the split mode
 // product of the same Y needs).
-int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev);
+int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, tucker_dtype dt,
+                                     const void *y);
 // Tiled tensor map of a float64 (f64) or float32 array: rank dimensions
 // (innermost first), byte strides of dimensions 1..rank-1 (multiples of 16),
 // box extents; swizzle 0 (none), 64 or 128 (bytes); out-of-range elements

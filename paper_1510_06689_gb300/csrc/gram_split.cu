@@ -69,7 +69,8 @@ namespace {
 using namespace tc;
 
 constexpr int kThreads = 512;
-constexpr int kRows = 128;         // M = N = 128 (J <= 128, zero padded)
+constexpr int kRows = 128;         // M = N = 128: one block of rows (J zero padded to blocks of 128)
+constexpr int kMaxRows = 512;      // largest J: up to four row blocks, Grams of their pairs
 constexpr int kChunk = 32;         // columns staged per stage
 constexpr int kTiles = 4;          // digit tiles A1, A2, 2 A3, A3 / 256
 constexpr int kTileBytes = kRows * kChunk * 2;
@@ -99,20 +100,25 @@ __device__ __forceinline__ int table_exp(unsigned long long pattern, bool f64) {
 // ref_j) <= 1, so only a row's own range over the CTA's columns limits the
 // float32 exponent range of the double-float accumulators; the per-CTA
 // partial carries the factor 2^(ref_i + ref_j) to the reduction.  All threads
-// call it; ends with a barrier.
-__device__ void cta_row_ref(const int *__restrict__ Etab, int J, int64_t g_begin, int64_t g_end, int *ref,
-                            int *__restrict__ ref_out) {
+// call it; ends with a barrier.  The rows are r0 .. r0 + rows - 1 of the
+// table (J per group).
+__device__ void cta_row_ref(const int *__restrict__ Etab, int J, int r0, int rows, int64_t g_begin, int64_t g_end,
+                            int *ref, int *__restrict__ ref_out) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid < kRows) ref[tid] = kZeroExp;
   __syncthreads();
   const int i = tid % kRows;
-  if (i < J) {
+  if (i < rows) {
     int m = kZeroExp;
-    for (int64_t g = g_begin + tid / kRows; g < g_end; g += nt / kRows) m = max(m, __ldg(Etab + g * J + i));
+    for (int64_t g = g_begin + tid / kRows; g < g_end; g += nt / kRows) m = max(m, __ldg(Etab + g * J + r0 + i));
     atomicMax(&ref[i], m);
   }
   __syncthreads();
   if (tid < kRows) ref_out[tid] = ref[tid];
+}
+__device__ void cta_row_ref(const int *__restrict__ Etab, int J, int64_t g_begin, int64_t g_end, int *ref,
+                            int *__restrict__ ref_out) {
+  cta_row_ref(Etab, J, 0, J, g_begin, g_end, ref, ref_out);
 }
 
 struct SplitPlan {
@@ -121,6 +127,10 @@ struct SplitPlan {
   int64_t cols_per_split;  // a multiple of kGroup, so groups never straddle CTAs
   int nsplit;
   int64_t ngroups;
+  int nrb;                 // row blocks of 128 (J > 128: the diagonal blocks' CTAs are split x block)
+  int npair;               // off-diagonal block pairs (the pair kernel's CTAs are split x pair)
+  int nsplit_pair;         // column ranges of the pair kernel, each of cols_per_split_pair columns
+  int64_t cols_per_split_pair;
   // tiled path (L > 1): a chunk is nl octets of l (8 l each) x nb = 4 / nl
   // consecutive b; chunk ch covers octets nl (ch % nL) .. and b from nb (ch / nL)
   int64_t nL;              // chunks along l (0: not the tiled path)
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
                                                       int contig_pairs, int *__restrict__ E,
                                                       unsigned long long *__restrict__ gmax,
                                                       int *__restrict__ colexp) {
-  __shared__ unsigned rmax[kRows];
+  __shared__ unsigned rmax[kMaxRows];
   __shared__ unsigned cmax[kGroup];
   constexpr bool kF64 = sizeof(T) == 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
   const int64_t c0 = g * kGroup, c1 = min(K, c0 + kGroup);
   const int ncols = (int)(c1 - c0);
   if (contig_pairs) {
-    for (int i = tid; i < kRows; i += 256) rmax[i] = 0u;
+    for (int i = tid; i < kMaxRows; i += 256) rmax[i] = 0u;
     __syncthreads();
     using V2 = typename std::conditional<kF64, double2, float2>::type;
     const V2 *base = reinterpret_cast<const V2 *>(y + c0 * (int64_t)J);
@@ -373,7 +383,7 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
   constexpr int RT = 512 / NQ;            // threads per chunk column
   constexpr int RS = 4 * RT;              // rows per stage: four chunks per thread
   extern __shared__ uint4 stg[];          // 2 stages x RS x NQ chunks
-  __shared__ unsigned rmax[kRows];
+  __shared__ unsigned rmax[kMaxRows];
   __shared__ unsigned cmax[kGroup];
   const int tid = threadIdx.x, lane = tid & 31;
   const int q = tid % NQ, r0 = tid / NQ;
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(512) k_rowgroup_exp_async(const T *__restrict_
   int64_t lq = 0, bq = 0;
   const bool valid = chunk_col(q, lq, bq);
   const int64_t goff = valid ? lq + L * (int64_t)J * bq : 0;
-  for (int i = tid; i < kRows; i += 512) rmax[i] = 0u;
+  for (int i = tid; i < kMaxRows; i += 512) rmax[i] = 0u;
   for (int i = tid; i < kGroup; i += 512) cmax[i] = 0u;
   __syncthreads();
   const int nst = (J + RS - 1) / RS;
@@ -904,7 +914,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int J = p.J;
-  const int64_t c_begin = (int64_t)blockIdx.x * p.cols_per_split;
+  // CTA = (column range, diagonal block of 128 rows r0 ..): J > 128 has p.nrb blocks
+  const int rb = (int)(blockIdx.x % (unsigned)p.nrb);
+  const int r0 = kRows * rb, Jb = min(kRows, J - r0);
+  const int64_t c_begin = (int64_t)(blockIdx.x / (unsigned)p.nrb) * p.cols_per_split;
   const int64_t c_end = min(p.K, c_begin + p.cols_per_split);
   const int nchunks = (int)((c_end - c_begin + kChunk - 1) / kChunk);
   const int64_t g0 = c_begin / kGroup;
@@ -921,12 +934,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
   }
-  cta_row_ref(Etab, J, g0, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
+  cta_row_ref(Etab, J, r0, Jb, g0, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
   // exponents of the group starting at chunk ch go to buffer (ch / kDrainChunks) & 1
   auto load_exps = [&](int ch) {
     if (tid < kRows) {
       const int gi = ch / kDrainChunks;
-      const int e = tid < J ? Etab[(g0 + gi) * J + tid] : kZeroExp;
+      const int e = tid < Jb ? Etab[(g0 + gi) * J + r0 + tid] : kZeroExp;
       rowexp[gi & 1][tid] = e;
       relexp[gi & 1][tid] = e - ref[tid];
     }
@@ -945,10 +958,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     mbar_expect_tx(bar, (uint32_t)(kChunk * kRows * sizeof(T)));
     if (kOct) {  // chunk indices stay below 2^31 (the plan checks it): 32-bit division
       const uint32_t gch = (uint32_t)(c_begin / kChunk) + (uint32_t)ch, nL = (uint32_t)p.nL, bb = gch / nL;
-      tma_load_4d(smem_addr(ring + slot * kRawBytes), &ymap, 0, 0, (int)((uint32_t)p.nl * (gch - bb * nL)),
+      tma_load_4d(smem_addr(ring + slot * kRawBytes), &ymap, 0, r0, (int)((uint32_t)p.nl * (gch - bb * nL)),
                   (int)((uint32_t)p.nb * bb), bar);
     } else {
-      tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, 0, (int)(c_begin + (int64_t)ch * kChunk), bar);
+      tma_load_2d(smem_addr(ring + slot * kRawBytes), &ymap, r0, (int)(c_begin + (int64_t)ch * kChunk), bar);
     }
   };
   if (tid == 0) {
@@ -1078,26 +1091,330 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   for (int e = 0; e < kAccPerThread; ++e) dst[e] = make_float2(H[e], Lo[e]);
 }
 
-// S_ij = sum over CTAs of (C_ij + C_ji) 2^(ref_i + ref_j - 43); NaN throughout
-// when the largest magnitude is not finite (Y holds Inf or NaN).  Eight
-// threads per entry take every eighth partial and combine by a fixed
-// shuffle tree, so the result is the same on every run.
+// ---------------------------------------------------------------------------
+// Off-diagonal blocks for 128 < J <= 512: S_ab = Y_a Y_b^T for row blocks a <
+// b of 128 rows (the diagonal blocks are k_gram_split_bulk's, with a row
+// offset).  A CTA takes one block pair and a column range and streams it in
+// half-chunks of 16 columns: two tensor-map boxes per half (the rows of
+// block a and of block b), a ring of kPRing slots, two digit stages.  The
+// tiled (kOct) path splits each 32-column chunk of the exponent pass into
+// its two halves (16 of its 32 columns: the same groups, so the same
+// exponents).  The digits are those of the diagonal kernel (21 bits below
+// each (row, group) power of two, three balanced digits), but no symmetry
+// folds the levels, so four accumulators hold
+//   acc0 = A1 B1^T                       (level 2, weight 2^28)
+//   acc1 = A1 B2^T + A2 B1^T             (level 3, 2^21)
+//   acc2 = A1 B3^T + A2 B2^T + A3 B1^T   (level 4, 2^14)
+//   acc3 = A2 B3^T + A3 B2^T + A3 (B3 / 128)^T   (levels 5 and 6, 2^7)
+// from six MMAs per half: A1, A2 and A3 against the stacked [B1; B2] (N =
+// 256: two levels each) and A1, A2, A3 against B3, B3 and B3 / 128.  Per
+// 512-column group acc0, acc1 <= 2^23 and acc2 < 10.5e6 are exact integer
+// sums; acc3's level-6 part is rounded as in the diagonal kernel.  The
+// partial is C itself (S_ab = sum over CTAs of C 2^(ref_a + ref_b - 42)).
+// ---------------------------------------------------------------------------
+constexpr int kPH = 16;                                   // columns per half-chunk
+constexpr int kPTile = kRows * kPH * 2;                   // one BF16 digit tile: 128 rows x 16 columns
+constexpr int kPSbo = kPH / 8 * 128;                      // bytes between 8-row core-matrix groups
+constexpr int kPStage = 7 * kPTile;                       // B1, B2, B3, B3/128, A1, A2, A3
+constexpr int kPRawBox = kRows * kPH * 8;                 // one box (sized for float64)
+constexpr int kPSlot = 2 * kPRawBox;                      // the two blocks' boxes
+constexpr int kPRing = 4;
+constexpr int kPGroupHalves = kGroup / kPH;               // 32
+constexpr size_t kPairSmemBytes = (size_t)kPRing * kPSlot + (size_t)kStages * kPStage + 1024;
+
+// (H, Lo) += (2^28 a0 + 2^21 a1 + 2^14 a2 + 2^7 a3) 2^x with sc28 = 2^(28 + x)
+// for an off-diagonal block: a1 = 128 a1h + a1l and 128 a1l + a2 = 2^14 qh + ql
+// move the high parts into p2 = a0 + a1h + qh (exact, < 2^24); r = 128 ql + a3
+// is the one rounded step.
+__device__ __forceinline__ void drain_entry_off(float a0, float a1, float a2, float a3, float sc28, float &H,
+                                                float &Lo) {
+  const float a1h = __fsub_rn(__fmaf_rn(a1, 0x1p-7f, kMagic), kMagic);
+  const float a1l = __fmaf_rn(a1h, -128.0f, a1);
+  const float q = __fmaf_rn(a1l, 128.0f, a2);
+  const float qh = __fsub_rn(__fmaf_rn(q, 0x1p-14f, kMagic), kMagic);
+  const float ql = __fmaf_rn(qh, -16384.0f, q);
+  const float p2 = __fadd_rn(__fadd_rn(a0, a1h), qh);
+  const float r = __fmaf_rn(ql, 128.0f, a3);
+  const float hg = __fmul_rn(p2, sc28);
+  const float lg = __fmul_rn(r, __fmul_rn(sc28, 0x1p-21f));
+  const float s = __fadd_rn(H, hg);  // TwoSum(H, hg)
+  const float bp = __fsub_rn(s, H);
+  const float e = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bp)), __fsub_rn(hg, bp));
+  const float l = __fadd_rn(Lo, __fadd_rn(e, lg));
+  const float t = __fadd_rn(s, l);  // renormalise
+  Lo = __fsub_rn(l, __fsub_rn(t, s));
+  H = t;
+}
+
+// The three digits (s1, s2, s3) of 8 columns of one row as BF16 pairs: from a
+// 128 x kPH box of a 2-D map (column c of row i at raw[c 128 + i]) ...
+template <typename T>
+__device__ __forceinline__ void digits8_box(const T *raw, int row, int kg, int cvt, uint32_t (&w)[3][4]) {
+  const T *src = raw + row + 8 * kg * kRows;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) {
+    float a1, a2, a3, b1, b2, b3;
+    split3(scaled_float(src[k * kRows], cvt), a1, a2, a3);
+    split3(scaled_float(src[(k + 1) * kRows], cvt), b1, b2, b3);
+    w[0][k >> 1] = bf16_pair(a1, b1);
+    w[1][k >> 1] = bf16_pair(a2, b2);
+    w[2][k >> 1] = bf16_pair(a3, b3);
+  }
+}
+// ... or from line kg of a 64-byte swizzled box of 8 l per line (as convert_oct).
+__device__ __forceinline__ void digits8_oct(const unsigned char *raw, int row, int kg, int cvt, uint32_t (&w)[3][4]) {
+  const unsigned char *line = raw + (kg * kRows + row) * 64;
+  const int sw = (row >> 1) & 3;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 y2 = *reinterpret_cast<const double2 *>(line + ((u ^ sw) << 4));
+    float a1, a2, a3, b1, b2, b3;
+    split3(scaled_float(y2.x, cvt), a1, a2, a3);
+    split3(scaled_float(y2.y, cvt), b1, b2, b3);
+    w[0][u] = bf16_pair(a1, b1);
+    w[1][u] = bf16_pair(a2, b2);
+    w[2][u] = bf16_pair(a3, b3);
+  }
+}
+
+template <typename T, bool kOct>
+__global__ void __launch_bounds__(kThreads, 1) k_gram_split_pair(const __grid_constant__ CUtensorMap ymap, SplitPlan p,
+                                                                 const int *__restrict__ Etab,
+                                                                 int *__restrict__ refs, double *__restrict__ ws,
+                                                                 int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  __shared__ __align__(8) unsigned long long raw_full[kPRing];
+  __shared__ __align__(8) unsigned long long mma_done[kStages];
+  __shared__ __align__(16) int rowexp[2][2][kRows];  // [group buffer][block a, b][row]: E_ig
+  __shared__ __align__(16) int relexp[2][2][kRows];  // E_ig - ref_i
+  __shared__ int ref[2][kRows];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int stop;
+  __shared__ int n_issued;
+  unsigned char *ring = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
+  unsigned char *stages = ring + kPRing * kPSlot;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int J = p.J;
+  int pi = (int)(blockIdx.x % (unsigned)p.npair), ba = 0;
+  while (pi >= p.nrb - 1 - ba) {  // pairs (a, b), a < b, in the order (0,1), (0,2), .., (1,2), ..
+    pi -= p.nrb - 1 - ba;
+    ++ba;
+  }
+  const int bb = ba + 1 + pi;
+  const int rA = kRows * ba, rB = kRows * bb;
+  const int JA = min(kRows, J - rA), JB = min(kRows, J - rB);
+  const int64_t c_begin = (int64_t)(blockIdx.x / (unsigned)p.npair) * p.cols_per_split;
+  const int64_t c_end = min(p.K, c_begin + p.cols_per_split);
+  const int nh = 2 * (int)((c_end - c_begin + kChunk - 1) / kChunk);
+  const int64_t g0 = c_begin / kGroup;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kPRing; ++s) mbar_init(smem_addr(&raw_full[s]), 1);
+    for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&mma_done[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  const int64_t g1 = (c_end + kGroup - 1) / kGroup;
+  cta_row_ref(Etab, J, rA, JA, g0, g1, ref[0], refs + (int64_t)blockIdx.x * 2 * kRows);
+  cta_row_ref(Etab, J, rB, JB, g0, g1, ref[1], refs + (int64_t)blockIdx.x * 2 * kRows + kRows);
+  auto load_exps = [&](int hc) {  // the group starting at half hc -> buffer (hc / 32) & 1
+    if (tid < 2 * kRows) {
+      const int gi = hc / kPGroupHalves, side = tid >> 7, i = tid & (kRows - 1);
+      const int e = i < (side ? JB : JA) ? Etab[(g0 + gi) * J + (side ? rB : rA) + i] : kZeroExp;
+      rowexp[gi & 1][side][i] = e;
+      relexp[gi & 1][side][i] = e - ref[side][i];
+    }
+  };
+  load_exps(0);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // half hc -> slot hc % kPRing: block a's box, then block b's
+  auto issue_copy = [&](int hc) {
+    const int slot = hc % kPRing;
+    const uint32_t bar = smem_addr(&raw_full[slot]);
+    const uint32_t dst = smem_addr(ring + slot * kPSlot);
+    mbar_expect_tx(bar, (uint32_t)(2 * kPH * kRows * sizeof(T)));
+    if (kOct) {
+      const uint32_t gch = (uint32_t)(c_begin / kChunk) + (uint32_t)(hc >> 1), h = (uint32_t)(hc & 1);
+      const uint32_t nL = (uint32_t)p.nL, bq = gch / nL;
+      const int oct = (int)((uint32_t)p.nl * (gch - bq * nL) + (p.nl == 4 ? 2 * h : 0u));
+      const int b = (int)((uint32_t)p.nb * bq + (p.nl == 4 ? 0u : h * (uint32_t)(p.nb / 2)));
+      tma_load_4d(dst, &ymap, 0, rA, oct, b, bar);
+      tma_load_4d(dst + kPRawBox, &ymap, 0, rB, oct, b, bar);
+    } else {
+      const int col = (int)(c_begin + (int64_t)hc * kPH);
+      tma_load_2d(dst, &ymap, rA, col, bar);
+      tma_load_2d(dst + kPRawBox, &ymap, rB, col, bar);
+    }
+  };
+  if (tid == 0) {
+    int c = 0;
+    for (; c < kPRing && c < nh; ++c) issue_copy(c);
+    n_issued = c;
+  }
+
+  const int side = tid >> 8, row = tid & (kRows - 1), kg = (tid >> 7) & 1;  // converter role
+  const int q = warp & 3, cb = warp >> 2;                                    // drain role
+  const int drow = 32 * q + lane;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cb);
+  float H[kAccPerThread], Lo[kAccPerThread];
+#pragma unroll
+  for (int e = 0; e < kAccPerThread; ++e) H[e] = Lo[e] = 0.f;
+
+  auto drain = [&](int gi, bool ok) {
+    if (ok) {  // warp-uniform
+      fence_after();
+      const int xi = relexp[gi & 1][0][drow] + 155;  // exponent field of 2^(28 + E_ia - ref_a)
+#pragma unroll
+      for (int part = 0; part < 8; ++part) {
+        uint32_t r[4][4];
+        tmem_ld4x4(taddr + 4 * part, r);
+        const int4 ej = *reinterpret_cast<const int4 *>(&relexp[gi & 1][1][32 * cb + 4 * part]);
+        const int ejs[4] = {ej.x, ej.y, ej.z, ej.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float sc28 = __int_as_float(max(xi + ejs[e], 0) << 23);
+          drain_entry_off(__uint_as_float(r[0][e]), __uint_as_float(r[1][e]), __uint_as_float(r[2][e]),
+                          __uint_as_float(r[3][e]), sc28, H[4 * part + e], Lo[4 * part + e]);
+        }
+      }
+    } else {
+      stop = 1;
+    }
+    fence_before();
+    __syncthreads();
+  };
+
+  int cvt = 0, last_committed = -1;
+  for (int hc = 0; hc < nh && !stop; ++hc) {
+    const int slot = hc % kPRing, st = hc & 1;
+    const int in_group = hc % kPGroupHalves, gi = hc / kPGroupHalves;
+    if (in_group == 0) {
+      cvt = scaled_float_param<T>(rowexp[gi & 1][side][row]);
+      if (hc + kPGroupHalves < nh) load_exps(hc + kPGroupHalves);  // the other buffer, read after later barriers
+    }
+    bool ok = mbar_wait(smem_addr(&raw_full[slot]), (uint32_t)(hc / kPRing) & 1u);
+    if (ok && hc >= 2) ok = mbar_wait(smem_addr(&mma_done[st]), (uint32_t)((hc - 2) >> 1) & 1u);
+    if (ok) {
+      uint32_t w[3][4];
+      const unsigned char *raw = ring + slot * kPSlot + side * kPRawBox;
+      if constexpr (kOct) digits8_oct(raw, row, kg, cvt, w);
+      else digits8_box<T>(reinterpret_cast<const T *>(raw), row, kg, cvt, w);
+      unsigned char *stg = stages + st * kPStage;
+      const int off = (row >> 3) * kPSbo + kg * 128 + (row & 7) * 16;
+      if (side == 0) {  // A1, A2, A3 at tiles 4, 5, 6
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+          *reinterpret_cast<uint4 *>(stg + (4 + t) * kPTile + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      } else {  // B1, B2, B3, B3 / 128 at tiles 0 .. 3
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+          *reinterpret_cast<uint4 *>(stg + t * kPTile + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+        *reinterpret_cast<uint4 *>(stg + 3 * kPTile + off) =
+            make_uint4(bf16x2_mul(w[2][0], 0x3C003C00u), bf16x2_mul(w[2][1], 0x3C003C00u),
+                       bf16x2_mul(w[2][2], 0x3C003C00u), bf16x2_mul(w[2][3], 0x3C003C00u));
+      }
+    } else {
+      stop = 1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (stop) break;
+    if (tid == 32 && hc + kPRing < nh) {  // slot `slot` has been read by every thread
+      issue_copy(hc + kPRing);
+      n_issued = hc + kPRing + 1;
+    }
+    if (tid == 0) {
+      fence_after();
+      const uint32_t base = smem_addr(stages + st * kPStage);
+      auto dsc = [&](int t) { return smem_desc(base + t * kPTile, 128, kPSbo); };
+      const uint32_t acc = in_group == 0 ? 0u : 1u;  // each accumulator's first MMA of a group overwrites
+      mma_bf16(tmem + 0, dsc(4), dsc(0), kIdesc256, acc);    // acc0 (+)= A1 B1, acc1 (+)= A1 B2
+      mma_bf16(tmem + 256, dsc(4), dsc(2), kIdesc, acc);     // acc2 (+)= A1 B3
+      mma_bf16(tmem + 384, dsc(5), dsc(2), kIdesc, acc);     // acc3 (+)= A2 B3
+      mma_bf16(tmem + 128, dsc(5), dsc(0), kIdesc256, 1u);   // acc1 += A2 B1, acc2 += A2 B2
+      mma_bf16(tmem + 256, dsc(6), dsc(0), kIdesc256, 1u);   // acc2 += A3 B1, acc3 += A3 B2
+      mma_bf16(tmem + 384, dsc(6), dsc(3), kIdesc, 1u);      // acc3 += A3 B3 / 128
+      mma_commit(smem_addr(&mma_done[st]));
+    }
+    last_committed = hc;
+    if (in_group == kPGroupHalves - 1 || hc == nh - 1) {
+      drain(gi, __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[st]), (uint32_t)(hc >> 1) & 1u)));
+      if (stop) break;
+    }
+  }
+  if (stop && tid == 0) {
+    if (last_committed >= 0) mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)(last_committed >> 1) & 1u);
+    const int issued = n_issued;
+    for (int c = max(0, issued - kPRing); c < issued; ++c)
+      mbar_wait(smem_addr(&raw_full[c % kPRing]), (uint32_t)(c / kPRing) & 1u);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (stop) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  float2 *dst = reinterpret_cast<float2 *>(ws) + (size_t)blockIdx.x * kRows * kRows + (size_t)drow * kRows + 32 * cb;
+#pragma unroll
+  for (int e = 0; e < kAccPerThread; ++e) dst[e] = make_float2(H[e], Lo[e]);
+}
+
+// S_ij = sum over CTAs of (C_ij + C_ji) 2^(ref_i + ref_j - off) for i and j in
+// one diagonal block of 128 rows (off = 43 for the BF16 digits: 2 x 21 bits
+// and the doubled symmetric part), or of C_ab 2^(ref_a + ref_b - off + 1)
+// from the block pair's partials (J > 128); NaN throughout when the largest
+// magnitude is not finite (Y holds Inf or NaN).  Partials: the diagonal
+// CTAs' (split s, block r) at s nrb + r, then the pair CTAs' (split s, pair
+// t) at nsd nrb + s npair + t; refs likewise (128 per diagonal CTA, 256 per
+// pair CTA: block a's rows, then block b's).  Eight threads per entry take
+// every eighth partial and combine by a fixed shuffle tree, so the result is
+// the same on every run, and S_ij and S_ji are the same value.
 __global__ void __launch_bounds__(256) k_gram_split_reduce(const double *__restrict__ ws, const int *__restrict__ refs,
-                                                           int nsplit, int J,
+                                                           int nsd, int nso, int nrb, int npair, int J,
                                                            const unsigned long long *__restrict__ gmax, int is_f64,
                                                            int scale_off, double *__restrict__ S) {
   const int idx = blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3), sub = threadIdx.x & 7;
   const bool live = idx < J * J;
   const int i = live ? idx % J : 0, j = live ? idx / J : 0;
+  const int bi = i / kRows, bj = j / kRows, ii = i % kRows, jj = j % kRows;
   double s = 0.0;
-  if (live)
-    for (int sp = sub; sp < nsplit; sp += 8) {
-      const float2 *c = reinterpret_cast<const float2 *>(ws) + (size_t)sp * kRows * kRows;
-      const float2 a = c[i * kRows + j], b = c[j * kRows + i];
-      const int ri = refs[sp * kRows + i], rj = refs[sp * kRows + j];
+  if (live && bi == bj) {
+    for (int sp = sub; sp < nsd; sp += 8) {
+      const int c = sp * nrb + bi;
+      const float2 *cp = reinterpret_cast<const float2 *>(ws) + (size_t)c * kRows * kRows;
+      const float2 a = cp[ii * kRows + jj], b = cp[jj * kRows + ii];
+      const int ri = refs[c * kRows + ii], rj = refs[c * kRows + jj];
       if (ri != kZeroExp && rj != kZeroExp)
         s += ldexp(((double)a.x + (double)a.y) + ((double)b.x + (double)b.y), ri + rj - scale_off);
     }
+  } else if (live) {
+    const int a = min(bi, bj), b = max(bi, bj);
+    const int ia = bi < bj ? ii : jj, jb = bi < bj ? jj : ii;
+    const int t = a * nrb - a * (a + 1) / 2 + (b - a - 1);  // pairs (0,1), (0,2), .., (1,2), ..
+    const int64_t c0 = (int64_t)nsd * nrb;
+    const int *rp = refs + c0 * kRows;
+    for (int sp = sub; sp < nso; sp += 8) {
+      const int64_t c = (int64_t)sp * npair + t;
+      const float2 v = (reinterpret_cast<const float2 *>(ws) + (size_t)(c0 + c) * kRows * kRows)[ia * kRows + jb];
+      const int ra = rp[c * 2 * kRows + ia], rb = rp[c * 2 * kRows + kRows + jb];
+      if (ra != kZeroExp && rb != kZeroExp) s += ldexp((double)v.x + (double)v.y, ra + rb - scale_off + 1);
+    }
+  }
   s += __shfl_xor_sync(0xffffffffu, s, 4);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
   s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -1136,10 +1453,17 @@ SplitPlan split_plan(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, boo
     p.K = L * B;
   }
   p.ngroups = (p.K + kGroup - 1) / kGroup;
-  const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ngroups));
-  const int64_t groups_per = (p.ngroups + ns - 1) / ns;
-  p.cols_per_split = groups_per * kGroup;
-  p.nsplit = (int)((p.K + p.cols_per_split - 1) / p.cols_per_split);
+  // about one wave of CTAs for the diagonal blocks (split x block) and one for the pairs
+  p.nrb = (int)((J + kRows - 1) / kRows);
+  p.npair = p.nrb * (p.nrb - 1) / 2;
+  auto splits = [&](int per, int &nsplit, int64_t &cols) {
+    const int64_t ns = std::max<int64_t>(1, std::min<int64_t>((dev.sms + per - 1) / per, p.ngroups));
+    const int64_t groups_per = (p.ngroups + ns - 1) / ns;
+    cols = groups_per * kGroup;
+    nsplit = (int)((p.K + cols - 1) / cols);
+  };
+  splits(p.nrb, p.nsplit, p.cols_per_split);
+  if (p.npair > 0) splits(p.npair, p.nsplit_pair, p.cols_per_split_pair);
   return p;
 }
 
@@ -1152,10 +1476,58 @@ struct SplitWs {
   int *refs;
   unsigned long long *gmax;
   int *err;
+  void *unfolded;  // J > 128 with a layout the tensor maps cannot read: the explicit unfolding
 };
 
+// The explicit mode-n unfolding of Y viewed as (L, J, B): out[j + ld c] =
+// y[l + L (j + J b)] with c = l + L b (the column order of the exponent
+// table's groups), by 32 x 32 tiles through shared memory (reads coalesced
+// along l, writes along j).  Block (x, y): x = the tile of l and the b, y =
+// the tile of j.
+template <typename T>
+__global__ void __launch_bounds__(256) k_unfold(const T *__restrict__ y, int64_t L, int J, int64_t B, int64_t ld,
+                                                int64_t nlt, T *__restrict__ out) {
+  __shared__ T t[32][33];
+  const int64_t lt = blockIdx.x % nlt, b = blockIdx.x / nlt;
+  const int jt = blockIdx.y, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t l = lt * 32 + tx;
+    const int j = jt * 32 + ty + 8 * k;
+    t[ty + 8 * k][tx] = (l < L && j < J) ? y[l + L * (j + (int64_t)J * b)] : T(0);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t l = lt * 32 + ty + 8 * k;
+    const int j = jt * 32 + tx;
+    if (l < L && j < J) out[j + ld * (l + L * b)] = t[tx][ty + 8 * k];
+  }
+}
+
+// Column stride of the unfolding: J rounded up to 16 bytes.
+int64_t unfold_ld(int64_t J, size_t es) {
+  const int64_t q = 16 / (int64_t)es;
+  return (J + q - 1) / q * q;
+}
+
+// True when J > 128 and neither tensor-map path reads Y in place: L == 1 needs
+// 16-byte columns, L > 1 float64 with L a multiple of 8.
+bool needs_unfold(int64_t L, int64_t J, tucker_dtype dt, const void *y) {
+  const size_t es = dt == TUCKER_F64 ? 8 : 4;
+  if (J <= kRows) return false;
+  const bool aligned = reinterpret_cast<uintptr_t>(y) % 16 == 0;
+  if (L == 1) return !((J * (int64_t)es) % 16 == 0 && aligned);
+  return !(dt == TUCKER_F64 && L % 8 == 0 && aligned);
+}
+
+int64_t split_ws_doubles(const SplitPlan &p);
+
+// partial blocks: the diagonal CTAs' then the pair CTAs'
+int64_t split_partials(const SplitPlan &p) { return (int64_t)p.nsplit * p.nrb + (int64_t)p.nsplit_pair * p.npair; }
+
 SplitWs split_ws(double *d_ws, const SplitPlan &p) {
-  const int64_t np = (int64_t)p.nsplit * kRows * kRows;
+  const int64_t np = split_partials(p) * kRows * kRows;
   const int64_t tab = (p.ngroups * p.J + 1) / 2;
   SplitWs w;
   w.gmax = reinterpret_cast<unsigned long long *>(d_ws);
@@ -1163,11 +1535,14 @@ SplitWs split_ws(double *d_ws, const SplitPlan &p) {
   w.partials = d_ws + 4;
   w.table = reinterpret_cast<int *>(d_ws + 4 + np);
   w.refs = reinterpret_cast<int *>(d_ws + 4 + np + tab);
+  w.unfolded = d_ws + split_ws_doubles(p);
   return w;
 }
 
 int64_t split_ws_doubles(const SplitPlan &p) {
-  return 4 + (int64_t)p.nsplit * kRows * kRows + (p.ngroups * p.J + 1) / 2 + (int64_t)p.nsplit * kRows / 2 + 1;
+  const int64_t refs = (int64_t)p.nsplit * p.nrb * kRows + (int64_t)p.nsplit_pair * p.npair * 2 * kRows;
+  const int64_t n = 4 + split_partials(p) * kRows * kRows + (p.ngroups * p.J + 1) / 2 + refs / 2 + 1;
+  return (n + 31) / 32 * 32;  // the unfolding (when needed) starts 256-byte aligned after this
 }
 
 // the tiled L > 1 path: float64, L a multiple of 8, 16-byte aligned Y
@@ -1191,26 +1566,46 @@ int run_gram_split(const void *y, int64_t L, const SplitPlan &p, const SplitWs &
   return TUCKER_OK;
 }
 
+// The off-diagonal block pairs (J > 128): CTAs (split, pair) after the
+// diagonal CTAs' partials and references.
+template <typename T, bool kOct>
+int run_gram_split_pair(const CUtensorMap &pmap, const SplitPlan &p, const SplitWs &w, cudaStream_t s) {
+  SplitPlan pp = p;
+  pp.cols_per_split = p.cols_per_split_pair;
+  const int64_t nd = (int64_t)p.nsplit * p.nrb;
+  TK_CUDA(allow_max_smem(k_gram_split_pair<T, kOct>));
+  k_gram_split_pair<T, kOct><<<p.nsplit_pair * p.npair, kThreads, kPairSmemBytes, s>>>(
+      pmap, pp, w.table, w.refs + nd * kRows, w.partials + nd * kRows * kRows, w.err);
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
 // The tensor-map kernel takes L == 1 with 16-byte column strides, a 16-byte
 // aligned Y and K < 2^31; TUCKER_GRAM_SPLIT_KERNEL=regs forces the
 // register-staged kernel.  Returns 1 when it ran, 0 when it does not apply.
 template <typename T>
-int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cudaStream_t s, bool *ran) {
+int run_gram_split_bulk(const void *y, const SplitPlan &p, const SplitWs &w, cudaStream_t s, bool *ran,
+                        int64_t ld = 0) {
   static const bool regs = [] {
     const char *e = std::getenv("TUCKER_GRAM_SPLIT_KERNEL");
     return e && std::strcmp(e, "regs") == 0;
   }();
   *ran = false;
-  const uint64_t col_bytes = (uint64_t)p.J * sizeof(T);
+  const uint64_t col_bytes = (uint64_t)(ld > 0 ? ld : p.J) * sizeof(T);
   if (regs || col_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(y) % 16 != 0 || p.K >= (1ll << 31)) return TUCKER_OK;
   CUtensorMap map;
   const uint64_t dims[2] = {(uint64_t)p.J, (uint64_t)p.K};
   const uint64_t strides[1] = {col_bytes};
   const uint32_t box[2] = {kRows, kChunk};
   if (!encode_tmap(&map, sizeof(T) == 8, y, 2, dims, strides, box)) return TUCKER_OK;
+  CUtensorMap pmap;
+  const uint32_t pbox[2] = {kRows, kPH};
+  if (p.npair > 0 && !encode_tmap(&pmap, sizeof(T) == 8, y, 2, dims, strides, pbox)) return TUCKER_OK;
   TK_CUDA(allow_max_smem(k_gram_split_bulk<T, false>));
-  k_gram_split_bulk<T, false><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials, w.err);
+  k_gram_split_bulk<T, false><<<p.nsplit * p.nrb, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials,
+                                                                                w.err);
   TK_LAUNCHED();
+  if (p.npair > 0) TK_CHECK((run_gram_split_pair<T, false>(pmap, p, w, s)));
   *ran = true;
   return TUCKER_OK;
 }
@@ -1224,10 +1619,15 @@ int run_gram_split_oct(const void *y, int64_t L, const SplitPlan &p, const Split
   const uint64_t strides[3] = {(uint64_t)L * 8, 64, (uint64_t)L * p.J * 8};
   const uint32_t box[4] = {8, kRows, (uint32_t)p.nl, (uint32_t)p.nb};
   if (!encode_tmap(&map, true, y, 4, dims, strides, box, 64)) return TUCKER_OK;
+  // the pair kernel's half-chunk: 16 of the chunk's 32 columns (2 octets of one b when nl = 4, else half the b)
+  CUtensorMap pmap;
+  const uint32_t pbox[4] = {8, kRows, p.nl == 4 ? 2u : (uint32_t)p.nl, p.nl == 4 ? 1u : (uint32_t)(p.nb / 2)};
+  if (p.npair > 0 && !encode_tmap(&pmap, true, y, 4, dims, strides, pbox, 64)) return TUCKER_OK;
   TK_CUDA(allow_max_smem(k_gram_split_bulk<double, true>));
-  k_gram_split_bulk<double, true><<<p.nsplit, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs, w.partials,
-                                                                            w.err);
+  k_gram_split_bulk<double, true><<<p.nsplit * p.nrb, kThreads, kBulkSmemBytes, s>>>(map, p, w.table, w.refs,
+                                                                                    w.partials, w.err);
   TK_LAUNCHED();
+  if (p.npair > 0) TK_CHECK((run_gram_split_pair<double, true>(pmap, p, w, s)));
   *ran = true;
   return TUCKER_OK;
 }
@@ -1263,19 +1663,31 @@ bool encode_tmap(CUtensorMap *map, bool f64, const void *base, int rank, const u
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev) {
+int64_t gram_split_workspace_doubles(int64_t L, int64_t J, int64_t B, const DeviceInfo &dev, tucker_dtype dt,
+                                     const void *y) {
   int64_t n = split_ws_doubles(split_plan(L, J, B, dev));
   if (L > 1 && L % 8 == 0) n = std::max(n, split_ws_doubles(split_plan(L, J, B, dev, true)));
+  if (needs_unfold(L, J, dt, y)) {  // room for the explicit unfolding after the non-tiled plan's workspace
+    const size_t es = dt == TUCKER_F64 ? 8 : 4;
+    n = std::max(n, split_ws_doubles(split_plan(L, J, B, dev)) + (unfold_ld(J, es) * L * B * (int64_t)es + 7) / 8);
+  }
   return n;
 }
 
 int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, double *d_S, double *d_ws,
                       const DeviceInfo &dev, cudaStream_t s, Prof *prof, int *d_colexp, bool f8) {
-  if (J > kRows) {
-    set_error("split-precision Gram supports J <= %d (got %lld)", kRows, (long long)J);
+  const bool oct = !f8 && use_oct(y, dt, L, B);  // the E4M3 digits run in the register-staged kernel
+  if (J > kMaxRows || (f8 && J > kRows)) {
+    set_error("split-precision Gram supports J <= %d (got %lld)", f8 ? kRows : kMaxRows, (long long)J);
     return TUCKER_EUNSUPPORTED;
   }
-  const bool oct = !f8 && use_oct(y, dt, L, B);  // the E4M3 digits run in the register-staged kernel
+  // J > 128: row blocks and their pairs in the tensor-map kernels, on Y in
+  // place or on its explicit unfolding (then read as L == 1)
+  const bool unfold = !oct && needs_unfold(L, J, dt, y);
+  if (J > kRows && L * B >= (1ll << 31)) {
+    set_error("split-precision Gram with J = %lld > %d needs fewer than 2^31 columns", (long long)J, kRows);
+    return TUCKER_EUNSUPPORTED;
+  }
   const SplitPlan p = split_plan(L, J, B, dev, oct);
   if (p.ngroups > 0x7FFFFFFFll) {
     set_error("split-precision Gram: too many column groups (%lld)", (long long)p.ngroups);
@@ -1314,9 +1726,27 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
                                                               contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, in_bytes, 1);
+  if (unfold) {  // the explicit unfolding (counted with the exponent pass: data movement before the Gram)
+    const size_t es = f64 ? 8 : 4;
+    const int64_t ld = unfold_ld(J, es), nlt = (L + 31) / 32;
+    if (prof) prof->begin(TUCKER_PHASE_SCALE);
+    const dim3 grid((unsigned)(nlt * B), (unsigned)((J + 31) / 32));
+    if (f64)
+      k_unfold<double><<<grid, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, B, ld, nlt,
+                                            static_cast<double *>(w.unfolded));
+    else
+      k_unfold<float><<<grid, 256, 0, s>>>(static_cast<const float *>(y), L, (int)J, B, ld, nlt,
+                                           static_cast<float *>(w.unfolded));
+    TK_LAUNCHED();
+    if (prof) prof->end(0.0, 2 * in_bytes, 1);
+  }
   if (prof) prof->begin(TUCKER_PHASE_GRAM);
   bool ran = false;
-  if (f8) {
+  if (unfold) {
+    const int64_t ld = unfold_ld(J, f64 ? 8 : 4);
+    if (f64) TK_CHECK(run_gram_split_bulk<double>(w.unfolded, p, w, s, &ran, ld));
+    else TK_CHECK(run_gram_split_bulk<float>(w.unfolded, p, w, s, &ran, ld));
+  } else if (f8) {
     if (f64) {
       if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided, true>(y, L, p, w, dev, s)));
       else if (mode == kColsContig) TK_CHECK((run_gram_split<double, kColsContig, true>(y, L, p, w, dev, s)));
@@ -1337,6 +1767,10 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
       return TUCKER_ECUDA;
     }
   }
+  if (!ran && J > kRows) {
+    set_error("split-precision Gram: the tensor map for J = %lld was refused", (long long)J);
+    return TUCKER_ECUDA;
+  }
   if (!ran && f64) {
     if (mode == kColsStrided) TK_CHECK((run_gram_split<double, kColsStrided>(y, L, p, w, dev, s)));
     else if (mode == kColsContig) TK_CHECK((run_gram_split<double, kColsContig>(y, L, p, w, dev, s)));
@@ -1349,10 +1783,12 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
   if (prof) prof->end((double)J * (J + 1) * (double)L * B, in_bytes, 1);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
   // S = (C + C^T) 2^(ref_i + ref_j - off): off = 2 x 21 + 1 for the BF16 digits, 2 x 15 + 1 for E4M3
-  k_gram_split_reduce<<<(unsigned)((J * J + 31) / 32), 256, 0, s>>>(w.partials, w.refs, p.nsplit, (int)J, w.gmax, f64,
+  k_gram_split_reduce<<<(unsigned)((J * J + 31) / 32), 256, 0, s>>>(w.partials, w.refs, p.nsplit, p.nsplit_pair,
+                                                                      p.nrb, p.npair, (int)J, w.gmax, f64,
                                                                       f8 ? 31 : 43, d_S);
   TK_LAUNCHED();
-  if (prof) prof->end((double)p.nsplit * J * J * 2, (double)p.nsplit * kRows * kRows * 8, 1);
+  if (prof)
+    prof->end((double)split_partials(p) * kRows * kRows * 2, (double)split_partials(p) * kRows * kRows * 8, 1);
   return TUCKER_OK;
 }
 

@@ -49,7 +49,8 @@ using namespace tc;
 
 constexpr int kThreads = 512;
 constexpr int kM = 128;           // output rows r (R zero-padded)
-constexpr int kMaxJp = 128;       // contraction length, padded to a multiple of 16
+constexpr int kMaxJp = 128;       // contraction length of one kernel pass, padded to a multiple of 16
+constexpr int kMaxSplitJ = 512;   // longer contractions run in passes of kMaxJp rows
 constexpr int kATiles = 4;        // U1..U4
 constexpr int kBTiles = 4;        // Y1..Y4
 
@@ -162,6 +163,11 @@ struct TtmSplit2Plan {
   int64_t K, ntiles;
   int grid;
   size_t smem;
+  // a part of a longer contraction (J > 128): Y's rows and U's rows are J of
+  // ldj (Y's view (L, ldj, B) and U ldu x R, both offset by the caller) and
+  // accum adds the part's product to Z instead of storing it
+  int64_t ldj, ldu;
+  int accum;
 };
 
 template <typename T>
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
   if (tid < kM) {
     unsigned long long m = 0ull;
     if (tid < p.R)
-      for (int j = 0; j < p.J; ++j) m = max(m, mag_bits(U[j + (int64_t)p.J * tid]));
+      for (int j = 0; j < p.J; ++j) m = max(m, mag_bits(U[j + p.ldu * tid]));
     rowexp[tid] = exp_above(m, true);
   }
   __syncthreads();
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = 8 * jg + k + h;
-        const double v = (r < p.R && j < p.J) ? U[j + (int64_t)p.J * r] : 0.0;
+        const double v = (r < p.R && j < p.J) ? U[j + p.ldu * r] : 0.0;
         digits4(scaled_int28(v, rowexp[r]), d[h]);
       }
 #pragma unroll
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const int64_t in_b = L * (int64_t)p.J, out_b = L * (int64_t)p.R;
+  const int64_t in_b = L * p.ldj, out_b = L * (int64_t)p.R;
   const int ngr = Jp / 8;                       // 8-row groups of a column
   const int upt = (kM2 * ngr + kThreads - 1) / kThreads;  // load units per thread (<= 4)
   const int my_c = tid % kM2;
@@ -287,7 +293,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
           for (int e = 0; e < 4; ++e) {
             const int r = r0 + e;
             if (r >= p.R) continue;
-            z[ob + L * (int64_t)r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + colexp[set][c] - 42);
+            const double v = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + colexp[set][c] - 42);
+            double *zp = z + ob + L * (int64_t)r;
+            *zp = p.accum ? *zp + v : v;
           }
         }
       }
@@ -425,6 +433,9 @@ TtmSplit2Plan ttm_split2_plan(int64_t L, int64_t J, int64_t B, int64_t R, const 
   p.ntiles = (p.K + kM2 - 1) / kM2;
   p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ntiles));
   p.smem = (size_t)4 * p.Rp * p.Jp * 2 + (size_t)2 * 4 * kM2 * p.KH * 2 + 1024;
+  p.ldj = J;
+  p.ldu = J;
+  p.accum = 0;
   return p;
 }
 
@@ -1075,13 +1086,41 @@ int run_ttm_tma(const CUtensorMap &map, const void *y, int64_t L, int64_t J, int
 int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64_t B, const double *U, int64_t R,
                      double *z, int *d_err, const DeviceInfo &dev, cudaStream_t s, Prof *prof,
                      const int *d_colexp) {
-  if (J > kMaxJp || R > kM || R > J) {
-    set_error("split-precision TTM supports R <= J <= %d (got J = %lld, R = %lld)", kMaxJp, (long long)J,
-              (long long)R);
+  if (J > kMaxSplitJ || R > kM || R > J) {
+    set_error("split-precision TTM supports R <= J <= %d and R <= %d (got J = %lld, R = %lld)", kMaxSplitJ, kM,
+              (long long)J, (long long)R);
     return TUCKER_EUNSUPPORTED;
   }
   const double flops = 2.0 * J * R * (double)(L * B);
   const double bytes = (double)(L * B) * (J * (dt == TUCKER_F64 ? 8.0 : 4.0) + R * 8.0) + J * R * 8.0;
+  if (J > kMaxJp) {
+    // Z = sum over parts of 128 rows of Y_part x_n U_part^T: each part is the
+    // register-staged product (its columns scaled by their own part's
+    // exponents), the later ones added to Z in float64
+    if (prof) prof->begin(L == 1 ? TUCKER_PHASE_TTM_L1 : TUCKER_PHASE_TTM);
+    const size_t es = dt == TUCKER_F64 ? 8 : 4;
+    int launches = 0;
+    for (int64_t j0 = 0; j0 < J; j0 += kMaxJp) {
+      TtmSplit2Plan p = ttm_split2_plan(L, std::min<int64_t>(kMaxJp, J - j0), B, R, dev);
+      p.ldj = J;
+      p.ldu = J;
+      p.accum = j0 > 0;
+      const void *yp = static_cast<const char *>(y) + (size_t)(L * j0) * es;
+      if (dt == TUCKER_F64) {
+        TK_CUDA(allow_max_smem(k_ttm_split2<double>));
+        k_ttm_split2<double><<<p.grid, kThreads, p.smem, s>>>(static_cast<const double *>(yp), L, B, U + j0, p, z,
+                                                              d_err);
+      } else {
+        TK_CUDA(allow_max_smem(k_ttm_split2<float>));
+        k_ttm_split2<float><<<p.grid, kThreads, p.smem, s>>>(static_cast<const float *>(yp), L, B, U + j0, p, z,
+                                                             d_err);
+      }
+      TK_LAUNCHED();
+      ++launches;
+    }
+    if (prof) prof->end(flops, bytes, launches);
+    return TUCKER_OK;
+  }
   if (L == 1) {
     const TtmL1Plan q = ttm_l1_plan(J, B, R, y, dt, dev);
     if (q.parts > 0) {

@@ -314,10 +314,12 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   TK_CUDA(cudaMemsetAsync(d_terr, 0, sizeof(int), s));
   const bool split = prec != TUCKER_PREC_FP64;  // tensor-core digits for the Gram and the mode product
   const bool f8 = prec == TUCKER_PREC_E4M3X4;
-  if (split) {
+  if (split) {  // the tensor-core kernels' limits (row blocks of 128 up to 512; the E4M3 Gram one block)
+    const int64_t lim = f8 ? 128 : 512;
     for (int n = 0; n < N; ++n)
-      if (dims[n] > 128) {
-        set_error("split precision needs every I_n <= 128 (I_%d = %lld)", n, (long long)dims[n]);  // Gram and TTM tiles
+      if (dims[n] > lim) {
+        set_error("%s split precision needs every I_n <= %lld (I_%d = %lld)", f8 ? "E4M3" : "BF16", (long long)lim, n,
+                  (long long)dims[n]);
         return TUCKER_EUNSUPPORTED;
       }
   }
@@ -385,7 +387,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     // Gram step (with L > 1 its exponent pass also leaves the column exponents the TTM needs)
     DevBuf colexp;
     if (split) {
-      const int64_t gws = gram_split_workspace_doubles(L, J, B, dev);
+      const int64_t gws = gram_split_workspace_doubles(L, J, B, dev, ydt, Y);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
       if (L > 1) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
       TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof,
@@ -1194,8 +1196,8 @@ static int gram_split_entry(const void *Y, tucker_dtype dt, int64_t L, int64_t J
     set_error("invalid arguments to tucker_gram_split");
     return TUCKER_EINVAL;
   }
-  if (J > 128) {
-    set_error("tucker_gram_split supports J <= 128 (got %lld)", (long long)J);
+  if (J > (f8 ? 128 : 512)) {
+    set_error("tucker_gram_split%s supports J <= %d (got %lld)", f8 ? "_e4m3" : "", f8 ? 128 : 512, (long long)J);
     return TUCKER_EUNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1203,7 +1205,7 @@ static int gram_split_entry(const void *Y, tucker_dtype dt, int64_t L, int64_t J
   TK_CHECK(device_info(&dev));
   Prof prof(s);
   DevBuf ws;
-  TK_CHECK(ws.alloc(sizeof(double) * gram_split_workspace_doubles(L, J, B, dev), s));
+  TK_CHECK(ws.alloc(sizeof(double) * gram_split_workspace_doubles(L, J, B, dev, dt, Y), s));
   TK_CHECK(launch_gram_split(Y, dt, L, J, B, S, ws.as<double>(), dev, s, &prof, nullptr, f8));
   int herr = 0;
   TK_CHECK(gram_split_error(ws.as<double>(), L, J, B, dev, &herr, s));
@@ -1223,8 +1225,9 @@ int tucker_ttm_split(const void *Y, tucker_dtype dt, int64_t L, int64_t J, int64
     set_error("invalid arguments to tucker_ttm_split");
     return TUCKER_EINVAL;
   }
-  if (J > 128 || R > J) {
-    set_error("tucker_ttm_split supports R <= J <= 128 (got J = %lld, R = %lld)", (long long)J, (long long)R);
+  if (J > 512 || R > J || R > 128) {
+    set_error("tucker_ttm_split supports R <= J <= 512 with R <= 128 (got J = %lld, R = %lld)", (long long)J,
+              (long long)R);
     return TUCKER_EUNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
