@@ -148,7 +148,10 @@ def test_gram_split_deterministic_and_rejects_large_j(gpu_lib):
     b = gpu_lib.gram_split(y, 1, 128, 20000).cpu().numpy()
     assert np.array_equal(a, b)
     with pytest.raises(gpu_lib.TuckerError) as e:
-        gpu_lib.gram_split(dev(np.zeros(129 * 2)), 1, 129, 2)
+        gpu_lib.gram_split(dev(np.zeros(513 * 2)), 1, 513, 2)
+    assert e.value.status == -7
+    with pytest.raises(gpu_lib.TuckerError) as e:  # the E4M3 digits take one block of 128 rows
+        gpu_lib.gram_split_e4m3(dev(np.zeros(129 * 2)), 1, 129, 2)
     assert e.value.status == -7
 
 
@@ -188,6 +191,80 @@ def test_ttm_split_bound(gpu_lib, L, J, B, R):
     got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
     err = np.abs(got - ref)
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+# ---------------------------------------------------------------------------
+# 128 < J <= 512: diagonal blocks of 128 rows with a row offset, the pair
+# kernel for the off-diagonal blocks, Y read in place (L = 1 with 16-byte
+# columns; float64 with L a multiple of 8) or through its explicit unfolding
+# (other layouts); the mode product in parts of 128 rows.
+# ---------------------------------------------------------------------------
+WIDE_GRAM = [(1, 512, 3000, np.float64), (1, 256, 5000, np.float64), (1, 300, 2000, np.float64),
+             (1, 257, 1000, np.float64), (1, 200, 1500, np.float32), (1, 130, 800, np.float32),
+             (8, 512, 40, np.float64), (16, 300, 77, np.float64), (24, 129, 50, np.float64),
+             (3, 256, 300, np.float64), (63, 512, 20, np.float64), (5, 200, 100, np.float32),
+             (8, 200, 50, np.float32), (1, 384, 64 * 152 + 9, np.float64)]
+
+
+@pytest.mark.parametrize("L,J,B,dtype", WIDE_GRAM)
+def test_gram_split_wide_bound(gpu_lib, L, J, B, dtype):
+    rng = np.random.default_rng(L * 3 + J * 5 + B)
+    y = rng.standard_normal(L * J * B).astype(dtype)
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    bound, ref = split_bound(y, L, J, B)
+    assert np.array_equal(s, s.T)
+    err = np.abs(s - ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+@pytest.mark.parametrize("L,J,B", [(1, 384, 1500), (8, 300, 70), (5, 256, 90)])
+def test_gram_split_wide_exact_on_leading_digit_inputs(gpu_lib, L, J, B):
+    """One digit per entry: the diagonal blocks and every block pair must be exact."""
+    rng = np.random.default_rng(17 + J)
+    ints = rng.integers(-127, 128, size=L * J * B)
+    ints[0] = 127
+    y = ints.astype(np.float64) / 128.0
+    s = gpu_lib.gram_split(dev(y), L, J, B).cpu().numpy()
+    m = ints.reshape((L, J, B), order="F").transpose(1, 0, 2).reshape(J, L * B).astype(np.int64)
+    assert np.array_equal(s * 2 ** 14, (m @ m.T).astype(np.float64))
+
+
+@pytest.mark.parametrize("L,J,B,R", [(1, 512, 2000, 63), (1, 300, 1500, 40), (63, 512, 30, 63), (8, 256, 100, 48),
+                                     (1, 129, 700, 128)])
+def test_ttm_split_wide_bound(gpu_lib, L, J, B, R):
+    import torch
+
+    rng = np.random.default_rng(L + 3 * J + 7 * B + R)
+    y = rng.standard_normal(L * J * B) * np.exp(rng.standard_normal(L * J * B))
+    u, _ = np.linalg.qr(rng.standard_normal((J, R)))
+    z = gpu_lib.ttm_split(dev(y), L, J, B, torch.from_numpy(u).cuda()).cpu().numpy()
+    bound, ref = ttm_split_bound(y, L, J, B, u)
+    got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+
+
+@pytest.mark.parametrize("dims,ranks,eps,order", [
+    ((200, 40, 30), (10, 5, 4), 1e-3, None),
+    ((300, 20, 16), (12, 6, 5), 1e-4, None),
+    ((160, 150, 24, 8), (12, 10, 6, 3), 1e-4, (0, 1, 2, 3)),
+    ((160, 150, 24, 8), (12, 10, 6, 3), 1e-4, (3, 2, 1, 0)),
+])
+def test_sthosvd_split_wide_modes(gpu_lib, dims, ranks, eps, order):
+    """Modes longer than 128 on the split-precision path: the oracle's ranks and
+    an error within 1e-3 eps of the oracle's (the smoothed, decaying generator of
+    the large 4-way workload, at a size the oracle runs in seconds)."""
+    x = tucker_tensor_np(dims, ranks, seed=3, decay=0.15, smooth=True, noise=1e-6)
+    ref = oracle.sthosvd(x, dims, eps, order)
+    xd = dev(x)
+    res = gpu_lib.sthosvd(xd, dims, eps, order, precision="bf16x4")
+    assert res.ranks == ref["ranks"]
+    rel = gpu_lib.rel_error(xd, res)
+    rel_ref = oracle.rel_error(x, ref["core"], ref["ranks"], ref["factors"])
+    assert abs(rel - rel_ref) <= 1e-3 * eps, (rel, rel_ref)
+    for n in range(len(dims)):
+        u = res.factor(n).cpu().numpy()
+        assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-13 * dims[n]
 
 
 @pytest.mark.parametrize("L,J,B,R", [(1, 64, 500, 16), (1, 128, 777, 48), (8, 128, 100, 40), (40, 48, 7, 20),
@@ -249,7 +326,7 @@ def test_ttm_split_f32_and_limits(gpu_lib):
     got = np.moveaxis(z.reshape((L, R, B), order="F"), 1, 0).reshape(R, -1, order="F")
     assert np.all(np.abs(got - ref) <= bound)
     with pytest.raises(gpu_lib.TuckerError) as e:
-        gpu_lib.ttm_split(dev(np.zeros(129 * 2)), 1, 129, 2, torch.zeros((129, 3), dtype=torch.float64).cuda())
+        gpu_lib.ttm_split(dev(np.zeros(513 * 2)), 1, 513, 2, torch.zeros((513, 3), dtype=torch.float64).cuda())
     assert e.value.status == -7
 
 
