@@ -565,19 +565,31 @@ def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=8):
           for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
     torch.cuda.synchronize()
     nbytes = sum(x.numel() * 8 for x in xs)
-    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)  # warm-up
+    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)  # warm-up (and tuning)
     ok = sum(r.ranks == tuple(rk) for r, rk in zip(res, ranks_list))
+    paths = sorted({p for r in res for p in r.eig_paths})
     del res
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    del res
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        del res
+    ms = statistics.median(times)
+    kc, ctas, cand = tucker.batched_tuning()
     return {"tensors": count, "input_gb": round(nbytes / 1e9, 3), "ms": round(ms, 2),
             "input_gb_s": round(nbytes / (ms / 1e3) / 1e9, 2), "tensors_per_s": round(count / (ms / 1e3), 1),
-            "true_ranks_recovered": ok, "precision": precision, "workers": workers}
+            "true_ranks_recovered": ok, "eig_paths": paths,
+            "path": "device pipeline (float64): per mode one launch per phase for all tensors, work lists and "
+                    "rank cuts on the device, one CUDA graph, one host synchronisation at the end",
+            "tuning": {"cols_per_item": kc, "persistent_ctas": ctas,
+                       "candidate_ms": {f"{c}x{p}": round(m, 3) for (c, p), m in
+                                        zip([(c, p) for c in (512, 2048, 8192) for p in (2, 4)], cand)},
+                       "note": "first mode's Gram, columns per item x CTAs per SM"},
+            "median_of": 3}
 
 
 def measure_fp64_peak(tucker, stream):
@@ -791,7 +803,7 @@ def main():
     line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
     if not args.no_next and world == 1:
         line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, t["rel"], stream)
-        line["next_rows"]["batched"] = measure_batched(tucker, head, stream)
+        line["next_rows"]["batched"] = measure_batched(tucker, "fp64", stream)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     xh = None

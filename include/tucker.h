@@ -205,10 +205,21 @@ TUCKER_API int tucker_hooi(const void *X, tucker_dtype dt, const int64_t *dims, 
 
 /*
  * tucker_sthosvd_batched -- Algorithm 1 on `count` independent tensors (the
- * many-small-tensors workload): each tensor's ST-HOSVD as tucker_sthosvd
- * (identity mode order), the tensors spread over `workers` host threads, each
- * driving its own stream, so that one tensor's per-mode synchronisation
- * overlaps the others' kernels.
+ * many-small-tensors workload), identity mode order.
+ *   When every I_n <= 128 the batch runs as one device pipeline in float64
+ *   (the plain method, whatever `prec`): per mode, one launch per phase for
+ *   all tensors -- a planner kernel that builds the work list of (tensor,
+ *   column range) items from the ranks already chosen on the device, a
+ *   persistent Gram over the items, a per-tensor reduction (the first mode's
+ *   trace gives ||X_t||^2), one Jacobi CTA per tensor, the rank rule on the
+ *   device, a persistent mode product -- captured in one CUDA graph, with no
+ *   host round trip until the results are collected.  The columns per item
+ *   and the persistent grid come from a small autotuner run on the first call
+ *   for a batch shape (see tucker_batched_tuning).  The results' cores and
+ *   factors share one device block, released with the last of them.
+ *   Otherwise each tensor's ST-HOSVD runs as tucker_sthosvd, the tensors
+ *   spread over `workers` host threads, each driving its own stream
+ *   (TUCKER_BATCH=threads forces this path).
  *   X        host array of `count` device pointers (type dt, natural layout).
  *   dims     host array of count x N sizes: row i holds tensor i's I_1..I_N.
  *   eps, prec  as for tucker_sthosvd, shared by all tensors.
@@ -380,6 +391,12 @@ TUCKER_API const char *tucker_status_string(int status);
 TUCKER_API const char *tucker_last_error(void);
 /* Number of kernels this library has launched in this process. */
 TUCKER_API int64_t tucker_launch_count(void);
+
+/* The tuning of the last batched device pipeline: columns per work item,
+ * persistent CTAs, and the six candidates' times in ms (512 / 2048 / 8192
+ * columns x 2 / 4 CTAs per SM, the first mode's Gram).  Any pointer may be
+ * NULL.  Host only. */
+TUCKER_API void tucker_batched_tuning(int64_t *cols_per_item, int *ctas, float *candidate_ms);
 
 /* Float64 throughput of the current GPU: a register-resident loop of
  * independent fused multiply-adds (no memory traffic) over every SM, timed

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <vector>
 
 #include "../../include/tucker.h"
@@ -43,6 +44,22 @@ int64_t bump_launches(int64_t n = 1);
     int s_ = (st);                                                                     \
     if (s_ != TUCKER_OK) return s_;                                                    \
   } while (0)
+
+// Library bookkeeping behind tucker_result.priv: the device, and for results
+// of the batched pipeline the device block their core and factors live in
+// (released when the last result that shares it is freed).
+struct ResultPriv {
+  int device = 0;
+  std::shared_ptr<void> block;
+};
+
+// The batched device pipeline (every I_n <= 128): fills out[0..count) like
+// tucker_sthosvd with the identity mode order, in float64.  *handled = 0
+// when the batch does not suit it (the caller then takes the per-tensor path).
+int sthosvd_batched_device(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, int count, double eps,
+                           cudaStream_t s, tucker_result *out, int *handled);
+
+void batched_last_tuning(int64_t *kc, int *grid, float *ms6);
 
 // ---------------------------------------------------------------------------
 // device description (cached per device)
@@ -178,6 +195,15 @@ int mp_max_j();
 // Float64 fused multiply-add throughput of the device (TFLOP/s) and the timed
 // launch's duration; synchronises s.
 int fp64_peak(double *tflops, double *ms, const DeviceInfo &dev, cudaStream_t s);
+// Float64 Jacobi on `count` matrices at once (one CTA each, J <= 128); device
+// arrays of per-matrix pointers and sizes; d_info holds 4 ints per matrix.
+int launch_eig_batched(const double *const *d_S, const int *d_J, double *const *d_lam, double *const *d_V,
+                       int *d_info, int count, int maxJ, cudaStream_t s, const int *d_idx = nullptr,
+                       int threads = 0, const double *d_budget = nullptr);
+// Float32 parallel-order Jacobi on `count` matrices (one CTA each, J <= 128):
+// X_b = the unsorted float32 eigenvectors of A_b as float64 (ld J_b).
+int launch_jacobi32_batched(const double *const *d_A, const int *d_J, double *const *d_X, int count, int maxJ,
+                            cudaStream_t s, const int *d_idx = nullptr, int threads = 0);
 // Rank rule: *d_rank = R, *d_tail = discarded sum.
 int launch_rank_cut(const double *d_lam, int64_t J, double threshold, int keep_all, int64_t *d_rank,
                     double *d_tail, cudaStream_t s, Prof *prof);

@@ -54,9 +54,50 @@ __device__ __forceinline__ void decode_pair_block(int e, int &P, int &Q) {
   P = e - q * (q + 1) / 2;
 }
 
+// The body of the one-CTA Jacobi (below), also run by the batched kernel (one
+// CTA per matrix).
+__device__ __forceinline__ void jacobi_body(const double *__restrict__ S_in, int J, double *__restrict__ lam,
+                                            double *__restrict__ V_out, double *__restrict__ gws,
+                                            int *__restrict__ info, double floor_rel = 0.0, double budget = -1.0);
+
 __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict__ S_in, int J,
                                                          double *__restrict__ lam, double *__restrict__ V_out,
                                                          double *__restrict__ gws, int *__restrict__ info) {
+  jacobi_body(S_in, J, lam, V_out, gws, info);
+}
+
+// Many matrices at once: CTA b solves matrix b (J_b <= kSmemMaxJ, S and V in
+// shared memory) from the descriptor arrays; a J_b of 0 skips the CTA.
+__global__ void __launch_bounds__(kEigThreads) k_jacobi_batched(const double *const *__restrict__ S, const int *__restrict__ Js,
+                                                                 double *const *__restrict__ lam,
+                                                                 double *const *__restrict__ V,
+                                                                 int *__restrict__ info, const int *__restrict__ idx,
+                                                                 const double *__restrict__ budget) {
+  const int b = idx ? idx[blockIdx.x] : (int)blockIdx.x, J = Js[b];
+  // absolute floor u max|s_ii|: eigenvalues to within ~J u ||S|| (backward
+  // stable, as LAPACK's), without resolving tiny eigenvalues to relative
+  // accuracy; with a budget, the tail the rank rule discards is left unresolved
+  const double bud = budget ? budget[b] : -1.0;
+  if (J > 0) jacobi_body(S[b], J, lam[b], V[b], nullptr, info + 4 * b, DBL_EPSILON, bud);
+  if (threadIdx.x == 0 && !(bud >= 0.0)) info[4 * b + 2] = 0;  // no tail
+}
+
+__device__ __forceinline__ void jacobi_body(const double *__restrict__ S_in, int J, double *__restrict__ lam,
+                                            double *__restrict__ V_out, double *__restrict__ gws,
+                                            int *__restrict__ info, double floor_rel, double budget) {
+  // budget >= 0 (S positive semidefinite): at each sweep's start the tail set
+  // is the longest run of the smallest diagonal entries whose sum tau (negative
+  // ones as 0) is at most budget / 2 and at most the next diagonal entry above
+  // the run; rotations between two tail indices are skipped.  The tail block
+  // is a principal submatrix, so its eigenvalues lie in [0, tau]: below every
+  // other eigenvalue, with a sum below the threshold, so every rank cut with
+  // that threshold discards the whole tail and nothing it would not discard
+  // with resolved eigenvalues; the tail's trace (the discarded sum) does not
+  // depend on rotations inside it.  The ranks, the retained vectors and the
+  // discarded sum are those of the fully resolved problem; the tail's values
+  // are Rayleigh quotients.  info[2] = the tail's size at the end.
+  __shared__ unsigned char in_tail[TUCKER_MAX_DIM];
+  __shared__ int tail_len;
   extern __shared__ __align__(16) double dyn[];
   __shared__ double cs[kMaxPairs], sn[kMaxPairs];
   __shared__ int pp[kMaxPairs], qq[kMaxPairs];
@@ -77,7 +118,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict
   if (tid == 0) {
     double mx = 0.0;
     for (int i = 0; i < J; ++i) mx = fmax(mx, fabs(S_in[i + (int64_t)J * i]));
-    abs_floor = mx * (DBL_EPSILON * DBL_EPSILON) + DBL_MIN;
+    abs_floor = mx * (floor_rel > 0.0 ? floor_rel : DBL_EPSILON * DBL_EPSILON) + DBL_MIN;
   }
   __syncthreads();
 
@@ -85,8 +126,42 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict
   bool converged = false;
   const int nblk = np * (np + 1) / 2;
   for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) rotated = 0;
+    if (tid == 0) {
+      rotated = 0;
+      tail_len = 0;
+    }
     __syncthreads();
+    if (budget >= 0.0) {
+      // over the J entries (not the zero padding row): ascending order (ties:
+      // the higher index first); entry i closes the run of the k_i smallest
+      // entries, with sum acc and the next entry above nxt
+      for (int i = tid; i < J; i += nt) {
+        const double di = Sp[pidx(i, i)];
+        double acc = 0.0, nxt = INFINITY;
+        int k = 0;
+        for (int j = 0; j < J; ++j) {
+          const double dj = Sp[pidx(j, j)];
+          if (dj < di || (dj == di && j >= i)) {
+            acc += fmax(dj, 0.0);
+            ++k;
+          } else {
+            nxt = fmin(nxt, dj);
+          }
+        }
+        if (k < J && acc <= 0.5 * budget && acc <= nxt) atomicMax(&tail_len, k);  // one index stays resolved
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += nt) {  // the run of the tail_len smallest entries (and the padding row)
+        const double di = Sp[pidx(i, i)];
+        int k = 0;
+        for (int j = 0; j < J; ++j) {
+          const double dj = Sp[pidx(j, j)];
+          k += dj < di || (dj == di && j >= i);
+        }
+        in_tail[i] = i >= J || k <= tail_len;
+      }
+      __syncthreads();
+    }
     for (int step = 0; step < m - 1; ++step) {
       for (int t = tid; t < np; t += nt) {
         int p = (t == 0) ? 0 : ((t - 1 + step) % (m - 1)) + 1;
@@ -97,7 +172,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict
           q = tmp;
         }
         double c = 1.0, s = 0.0;
-        const double b = Sp[pidx(p, q)];
+        const double b = (budget >= 0.0 && in_tail[p] && in_tail[q]) ? 0.0 : Sp[pidx(p, q)];
         if (b != 0.0) {
           const double a = Sp[pidx(p, p)], d = Sp[pidx(q, q)];
           const double ab = fabs(b);
@@ -191,6 +266,7 @@ __global__ void __launch_bounds__(kEigThreads) k_jacobi(const double *__restrict
   if (tid == 0) {
     info[0] = converged ? sweep + 1 : kMaxSweeps;
     info[1] = converged ? 0 : 1;
+    if (budget >= 0.0) info[2] = tail_len;
   }
 }
 
@@ -649,6 +725,30 @@ __global__ void k_rank_cut(const double *__restrict__ lam, int J, double thresho
 }
 
 }  // namespace
+
+// Float64 Jacobi on many matrices (J <= 128 each), one CTA per matrix; the
+// arrays are device arrays indexed by matrix (info: 4 ints per matrix: sweeps,
+// not converged, unresolved tail size (with a budget), spare); with d_idx, CTA
+// b solves matrix d_idx[b] (count of them), each CTA `threads` wide with
+// shared memory for J <= maxJ; with d_budget (per matrix, < 0: none) the
+// rank rule's tail within that budget is left unresolved.
+int launch_eig_batched(const double *const *d_S, const int *d_J, double *const *d_lam, double *const *d_V,
+                       int *d_info, int count, int maxJ, cudaStream_t s, const int *d_idx, int threads,
+                       const double *d_budget) {
+  if (maxJ > kSmemMaxJ) {
+    set_error("batched eigensolver takes J <= %d (got %d)", kSmemMaxJ, maxJ);
+    return TUCKER_EUNSUPPORTED;
+  }
+  const int m = maxJ + (maxJ & 1);
+  const size_t smem = (size_t)(m * (m + 1) / 2 + m * m) * sizeof(double);
+  TK_CUDA(allow_max_smem(k_jacobi_batched));
+  if (count > 0) {
+    k_jacobi_batched<<<count, threads > 0 ? threads : kEigThreads, smem, s>>>(d_S, d_J, d_lam, d_V, d_info, d_idx,
+                                                                              d_budget);
+    TK_LAUNCHED();
+  }
+  return TUCKER_OK;
+}
 
 // J up to this size runs in one CTA with S and V in shared memory; larger J
 // run on a cluster.

@@ -80,8 +80,26 @@ constexpr int kPolishSteps = 1;
 // sweep (an absolute criterion: the float64 refinement that follows needs no
 // more).  Writes X = V (float64, unsorted columns) and the number of sweeps.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void jacobi32_body(const double *__restrict__ A, int lda, int n, double *__restrict__ X,
+                                              int ldx, int *__restrict__ sweeps);
+
 __global__ void __launch_bounds__(kJ32Threads) k_jacobi32(const double *__restrict__ A, int lda, int n,
                                                            double *__restrict__ X, int ldx, int *__restrict__ sweeps) {
+  jacobi32_body(A, lda, n, X, ldx, sweeps);
+}
+
+// Many matrices at once, one CTA each (J_b <= 128; J_b = 0 skips the CTA):
+// A_b (ld J_b) in, X_b = V (float64, ld J_b, unsorted columns) out.
+__global__ void __launch_bounds__(kJ32Threads) k_jacobi32_batched(const double *const *__restrict__ A,
+                                                                   const int *__restrict__ Js,
+                                                                   double *const *__restrict__ X,
+                                                                   const int *__restrict__ idx) {
+  const int b = idx ? idx[blockIdx.x] : (int)blockIdx.x, J = Js[b];
+  if (J > 0) jacobi32_body(A[b], J, J, X[b], J, nullptr);
+}
+
+__device__ __forceinline__ void jacobi32_body(const double *__restrict__ A, int lda, int n, double *__restrict__ X,
+                                              int ldx, int *__restrict__ sweeps) {
   extern __shared__ __align__(16) float sm32[];
   __shared__ float4 rot[kTriMaxJ / 2];  // per pair: c, s, t = s / c, (p | q << 16) as bits
   __shared__ float red[kJ32Threads / 32];
@@ -227,6 +245,25 @@ size_t jacobi32_smem(int n) {
   const int m = (n + 3) & ~3, np = m / 2;
   return (size_t)(((m * (m + 1) + 3) & ~3) + m * m) * sizeof(float) + (size_t)np * (np + 1) / 2 * sizeof(int) + 16;
 }
+
+}  // namespace
+
+// The float32 Jacobi stage on `count` matrices (one CTA each, J <= 128).
+int launch_jacobi32_batched(const double *const *d_A, const int *d_J, double *const *d_X, int count, int maxJ,
+                            cudaStream_t s, const int *d_idx, int threads) {
+  if (maxJ > kTriMaxJ) {
+    set_error("batched float32 Jacobi takes J <= %d (got %d)", kTriMaxJ, maxJ);
+    return TUCKER_EUNSUPPORTED;
+  }
+  TK_CUDA(allow_max_smem(k_jacobi32_batched));
+  if (count > 0) {
+    k_jacobi32_batched<<<count, threads > 0 ? threads : kJ32Threads, jacobi32_smem(maxJ), s>>>(d_A, d_J, d_X, d_idx);
+    TK_LAUNCHED();
+  }
+  return TUCKER_OK;
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // float32 tridiagonal eigensolver on A scaled by a power of two (largest

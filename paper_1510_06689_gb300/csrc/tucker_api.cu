@@ -249,11 +249,15 @@ static int check_order(const int *order, int N, int *out) {
 
 static size_t elem_size(tucker_dtype dt) { return dt == TUCKER_F64 ? 8 : 4; }
 
-struct Priv {
-  int device = 0;
-};
+using Priv = ResultPriv;
 
 static void free_result_device(tucker_result *r) {
+  const Priv *pv = static_cast<const Priv *>(r->priv);
+  if (pv && pv->block) {  // core and factors live in a block shared by a batch (freed with its last result)
+    r->core = nullptr;
+    for (int n = 0; n < TUCKER_MAX_MODES; ++n) r->factors[n] = nullptr;
+    return;
+  }
   if (r->on_host) {
     free(r->core);
     for (int n = 0; n < TUCKER_MAX_MODES; ++n) free(r->factors[n]);
@@ -764,6 +768,10 @@ const char *tucker_last_error(void) { return g_err; }
 
 int64_t tucker_launch_count(void) { return g_launches.load(); }
 
+void tucker_batched_tuning(int64_t *cols_per_item, int *ctas, float *candidate_ms) {
+  batched_last_tuning(cols_per_item, ctas, candidate_ms);
+}
+
 int tucker_fp64_peak(double *tflops, double *ms, void *stream) {
   g_err[0] = 0;
   if (!tflops) {
@@ -954,6 +962,18 @@ int tucker_sthosvd_batched(const void *const *X, tucker_dtype dt, const int64_t 
     if (!X[i]) {
       set_error("tensor %d is NULL", i);
       return TUCKER_EINVAL;
+    }
+  }
+  {  // every I_n <= 128: the batched device pipeline (float64), no host round trip between phases
+    int handled = 0;
+    const int st = sthosvd_batched_device(X, dt, dims, N, count, eps, static_cast<cudaStream_t>(stream), out, &handled);
+    if (handled) {
+      if (st != TUCKER_OK) {
+        const std::string msg = tucker_last_error();
+        for (int i = 0; i < count; ++i) tucker_result_free(&out[i]);
+        set_error("%s", msg.c_str());
+      }
+      return st;
     }
   }
   if (workers == 0) workers = 8;

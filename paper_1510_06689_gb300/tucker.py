@@ -29,6 +29,7 @@ EXPORTS = (
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
     "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak", "tucker_gram_split_e4m3",
+    "tucker_batched_tuning",
 )
 EIG_PATHS = ("mixed", "jacobi", "jacobi_fallback")
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
@@ -109,6 +110,7 @@ def load(path=LIB_PATH):
         "tucker_profile_enable": (None, [i32]),
         "tucker_profile_read": (None, [ctypes.POINTER(_Profile)]),
         "tucker_fp64_peak": (i32, [pdbl, pdbl, vp]),
+        "tucker_batched_tuning": (None, [pi64, pi32, ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -468,6 +470,14 @@ def profile_read():
 
 def launch_count():
     return int(load().tucker_launch_count())
+
+
+def batched_tuning():
+    """(columns per work item, persistent CTAs, candidate ms) of the last batched device pipeline."""
+    kc, grid = ctypes.c_int64(), ctypes.c_int()
+    ms = (ctypes.c_float * 6)()
+    load().tucker_batched_tuning(ctypes.byref(kc), ctypes.byref(grid), ms)
+    return kc.value, grid.value, list(ms)
 
 
 def fp64_peak(stream=None):

@@ -504,26 +504,90 @@ def test_hooi_zero_iterations_is_sthosvd(gpu_lib):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
-def test_batched_matches_single_calls_and_oracle(gpu_lib, precision):
-    """Many small tensors (the batched workload's shape mix, smaller): each result
-    equals the single-tensor call bit for bit and matches the oracle."""
+def test_batched_thread_path_matches_single_calls(gpu_lib, monkeypatch, precision):
+    """The per-tensor batched path (host worker threads, TUCKER_BATCH=threads):
+    each result equals the single-tensor call bit for bit."""
     from synthetic import random_dims_ranks
 
-    dims_list, ranks_list = random_dims_ranks(24, seed=3, dim_range=(16, 48), rank_range=(4, 10))
-    xs_np = [tucker_tensor_np(d, r, seed=4, tensor=i, noise=1e-4) for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
-    xs = [dev(x) for x in xs_np]
-    eps = 1e-3
-    res = gpu_lib.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=4)
-    assert len(res) == len(xs)
-    for x_np, x, d, r in zip(xs_np, xs, dims_list, res):
-        one = gpu_lib.sthosvd(x, d, eps, precision=precision)
+    monkeypatch.setenv("TUCKER_BATCH", "threads")
+    dims_list, ranks_list = random_dims_ranks(16, seed=3, dim_range=(16, 48), rank_range=(4, 10))
+    xs = [dev(tucker_tensor_np(d, r, seed=4, tensor=i, noise=1e-4)) for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
+    res = gpu_lib.sthosvd_batched(xs, dims_list, 1e-3, precision=precision, workers=4)
+    for x, d, r in zip(xs, dims_list, res):
+        one = gpu_lib.sthosvd(x, d, 1e-3, precision=precision)
         assert r.ranks == one.ranks
         assert np.array_equal(r.core().cpu().numpy(), one.core().cpu().numpy())
-        ref = oracle.sthosvd(x_np, d, eps)
-        assert r.ranks == ref["ranks"]
+
+
+def _check_batched_against_oracle(gpu_lib, xs_np, xs, dims_list, res, eps):
+    for x_np, x, d, r in zip(xs_np, xs, dims_list, res):
+        ref = oracle.sthosvd(x_np.astype(np.float64), d, eps)
+        assert r.ranks == ref["ranks"], (d, r.ranks, ref["ranks"])
+        assert r.norm2 == pytest.approx(ref["norm2"], rel=1e-13)
+        for n in range(len(d)):
+            u = r.factor(n).cpu().numpy()
+            v = ref["factors"][n]
+            lam = ref["eigvals"][n]
+            k = ref["ranks"][n]
+            assert np.abs(u.T @ u - np.eye(k)).max() <= 1e-13 * d[n]
+            # the retained eigenvalues individually; the discarded ones the solver may leave
+            # unresolved (Rayleigh quotients of a basis of their subspace): their sum, and each
+            # in [0, their sum] as the eigenvalues of a positive semidefinite block are
+            got = np.asarray(r.eigvals[n])
+            tol = 1e-12 * max(lam[0], 1e-300)
+            n_tail = max(d[n] - k, 1)
+            res_n = r.eig_resolved[n]
+            assert k <= res_n <= d[n]
+            assert np.abs(got[:res_n] - lam[:res_n]).max(initial=0.0) <= tol
+            assert abs(got[k:].sum() - lam[k:].sum()) <= tol * n_tail
+            assert abs(r.tails[n] - lam[k:].sum()) <= tol * n_tail
+            assert np.all(got[res_n:] >= -tol) and np.all(got[res_n:] <= got[res_n:].sum() + tol)
+            if eps == 0.0:
+                assert res_n == d[n]
+            gap = (lam[k - 1] - lam[k]) if k < d[n] else lam[k - 1]
+            if k < d[n] and gap >= 1e-4 * lam[0]:
+                assert principal_sines(v, u).max() <= 1e-8
         rel = gpu_lib.rel_error(x, r)
-        rel_ref = oracle.rel_error(x_np, ref["core"], ref["ranks"], ref["factors"])
-        assert abs(rel - rel_ref) <= 1e-3 * eps
+        rel_ref = oracle.rel_error(x_np.astype(np.float64), ref["core"], ref["ranks"], ref["factors"])
+        assert abs(rel - rel_ref) <= 1e-12, (rel, rel_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
+def test_batched_device_pipeline_matches_oracle(gpu_lib, precision):
+    """Many small tensors of mixed sizes (the batched workload's mix, smaller) in
+    the device pipeline: each tensor's ranks, eigenvalues, factor subspaces and
+    error against the float64 oracle (the pipeline computes in float64)."""
+    from synthetic import random_dims_ranks
+
+    dims_list, ranks_list = random_dims_ranks(40, seed=3, dim_range=(16, 64), rank_range=(4, 12))
+    xs_np = [tucker_tensor_np(d, r, seed=4, tensor=i, noise=1e-4) for i, (d, r) in enumerate(zip(dims_list, ranks_list))]
+    xs = [dev(x) for x in xs_np]
+    res = gpu_lib.sthosvd_batched(xs, dims_list, 1e-3, precision=precision)
+    assert len(res) == len(xs)
+    assert all(p == "jacobi" for r in res for p in r.eig_paths)
+    _check_batched_against_oracle(gpu_lib, xs_np, xs, dims_list, res, 1e-3)
+    kc, ctas, ms = gpu_lib.batched_tuning()
+    assert kc in (512, 2048, 8192) and ctas > 0 and min(ms) > 0
+
+
+def test_batched_device_pipeline_edges(gpu_lib):
+    """Four-way float32 tensors, keep-all (eps = 0), modes of length 1 and 128,
+    a batch of one, and results freed in any order (they share one block)."""
+    rng = np.random.default_rng(8)
+    dims_list = [(12, 9, 7, 5), (1, 20, 3, 2), (128, 4, 3, 2), (17, 16, 15, 14)]
+    xs_np = [rng.standard_normal(int(np.prod(d))).astype(np.float32) for d in dims_list]
+    xs = [dev(x) for x in xs_np]
+    res = gpu_lib.sthosvd_batched(xs, dims_list, 0.0)
+    for d, r in zip(dims_list, res):
+        assert r.ranks == d
+    _check_batched_against_oracle(gpu_lib, xs_np, xs, dims_list, res, 0.0)
+    res[0].free()
+    res[2].free()
+    g = res[3].core().cpu().numpy()  # the shared block is still held by the others
+    assert np.isfinite(g).all()
+    one = gpu_lib.sthosvd_batched([xs[1]], [dims_list[1]], 0.5)
+    ref = oracle.sthosvd(xs_np[1].astype(np.float64), dims_list[1], 0.5)
+    assert one[0].ranks == ref["ranks"]
 
 
 def test_host_entry_point(gpu_lib):
