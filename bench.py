@@ -755,6 +755,13 @@ def main():
                             device="cuda")
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    # the end-to-end leg's pinned host copy of X, made before the other legs hold host or device memory
+    xh, h2d_ms = None, None
+    if not args.no_e2e:
+        xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
+        xh.copy_(x)
+        # the raw copy rate of the same pinned buffer (one cudaMemcpyAsync), beside the end-to-end figure
+        h2d_ms, _ = _time_calls(lambda: x.copy_(xh, non_blocking=True), stream, reps=3)
 
     methods = ["bf16x4", "fp64"] if args.precision == "both" else [args.precision]
     methods = [m for m in methods if m in tucker.PREC]
@@ -801,20 +808,9 @@ def main():
         "gpu_launches": t["launches"], "clocks": t["clocks"],
     }
     line["roofline"], line["rooflines"] = roofline_of(t, args.steps, head)
-    if not args.no_next and world == 1:
-        line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, t["rel"], stream)
-        line["next_rows"]["batched"] = measure_batched(tucker, "fp64", stream)
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
-    xh = None
-    if not args.no_e2e:
-        xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
-        xh.copy_(x)
-        # the raw copy rate of the same pinned buffer (one cudaMemcpyAsync), beside the end-to-end figure
-        h2d_ms, _ = _time_calls(lambda: x.copy_(xh, non_blocking=True), stream, reps=3)
-        del x
-        torch.cuda.empty_cache()
-
+    if xh is not None:
         def e2e(prec, steps):
             r = tucker.sthosvd_host(xh, dims, args.eps, precision=prec)
             d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)))
@@ -834,6 +830,9 @@ def main():
                                           "median of 3 (CUDA events)"}
         if "fp64" in timed and head != "fp64":
             line["e2e_fp64"] = e2e("fp64", 2)
+    if not args.no_next and world == 1:
+        line["next_rows"] = measure_next_rows(tucker, x, w, args.eps, head, ms, t["rel"], stream)
+        line["next_rows"]["batched"] = measure_batched(tucker, "fp64", stream)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         src = xh if xh is not None else x.cpu()
@@ -847,9 +846,9 @@ def main():
                       f"(numpy/OpenBLAS float64 on {cpu['usable_cores']} cores of {cpu['model']}); "
                       f"the reference arm times the first {max(1, args.cpu_slices // 2)} slices",
         }
+    x = xh = src = None  # the remaining legs make tensors of their own
+    torch.cuda.empty_cache()
     if not args.no_next and world == 1:
-        del xh
-        xh = None
         line["configs"] = measure_configs(tucker, stream, args)
     # last: these tensors of their own (16 GB between them) run after the end-to-end leg
     if not args.no_next and world == 1:

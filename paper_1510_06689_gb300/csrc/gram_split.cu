@@ -267,6 +267,53 @@ __device__ __forceinline__ unsigned ldg_mag(const T *p) {
   else return __ldg(reinterpret_cast<const unsigned *>(p)) & 0x7FFFFFFFu;
 }
 
+// Contiguous columns of J = 64 HP entries (L == 1), also taking each
+// column's largest magnitude: warp w reads columns w kC + 8 kC i .. + kC - 1
+// (kC = 8 / HP columns, eight 16-byte pairs per lane in flight), lane l
+// holding rows 2 l + 64 h and 2 l + 64 h + 1 (h < HP) throughout, so the
+// row maxima stay in registers until one atomic per row at the end and a
+// column's maximum is one warp reduction (no atomics).  cmax[cc] gets the
+// magnitude bits of column c0 + cc (cc < ncols); rmax must be zeroed.
+template <typename T, int HP>
+__device__ __forceinline__ void exp_cols_contig(const T *__restrict__ y, int64_t c0, int ncols, unsigned *rmax,
+                                                unsigned *cmax, int lane, int warp) {
+  using V2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+  constexpr int kC = 8 / HP;
+  unsigned rm[2 * HP];
+#pragma unroll
+  for (int h = 0; h < 2 * HP; ++h) rm[h] = 0u;
+  for (int cb = warp * kC; cb < ncols; cb += 8 * kC) {  // warp-uniform
+    V2 v[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int cc = cb + s / HP, h = s % HP;
+      if (cc < ncols) {
+        v[s] = __ldg(reinterpret_cast<const V2 *>(y + (c0 + cc) * (int64_t)(64 * HP) + 2 * lane + 64 * h));
+      } else {
+        v[s].x = v[s].y = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kC; ++u) {
+      unsigned cm = 0u;
+#pragma unroll
+      for (int h = 0; h < HP; ++h) {
+        const unsigned a = hi_mag(v[u * HP + h].x), b = hi_mag(v[u * HP + h].y);
+        rm[2 * h] = max(rm[2 * h], a);
+        rm[2 * h + 1] = max(rm[2 * h + 1], b);
+        cm = max(cm, max(a, b));
+      }
+      cm = __reduce_max_sync(0xffffffffu, cm);
+      if (lane == 0 && cb + u < ncols) cmax[cb + u] = cm;
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < HP; ++h) {
+    atomicMax(&rmax[2 * lane + 64 * h], rm[2 * h]);
+    atomicMax(&rmax[2 * lane + 64 * h + 1], rm[2 * h + 1]);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, int64_t L, int J, int64_t K,
                                                       int contig_pairs, int *__restrict__ E,
@@ -279,12 +326,26 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
   const int64_t g = blockIdx.x;
   const int64_t c0 = g * kGroup, c1 = min(K, c0 + kGroup);
   const int ncols = (int)(c1 - c0);
-  if (contig_pairs) {
+  if (contig_pairs && colexp && J % 64 == 0) {
+    // column exponents too: warps over whole columns
     for (int i = tid; i < kMaxRows; i += 256) rmax[i] = 0u;
+    __syncthreads();
+    switch (J / 64) {
+      case 1: exp_cols_contig<T, 1>(y, c0, ncols, rmax, cmax, lane, warp); break;
+      case 2: exp_cols_contig<T, 2>(y, c0, ncols, rmax, cmax, lane, warp); break;
+      case 4: exp_cols_contig<T, 4>(y, c0, ncols, rmax, cmax, lane, warp); break;
+      default: exp_cols_contig<T, 8>(y, c0, ncols, rmax, cmax, lane, warp); break;
+    }
+    __syncthreads();
+    for (int cc = tid; cc < ncols; cc += 256) colexp[c0 + cc] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
+  } else if (contig_pairs) {
+    for (int i = tid; i < kMaxRows; i += 256) rmax[i] = 0u;
+    if (colexp)
+      for (int cc = tid; cc < kGroup; cc += 256) cmax[cc] = 0u;
     __syncthreads();
     using V2 = typename std::conditional<kF64, double2, float2>::type;
     const V2 *base = reinterpret_cast<const V2 *>(y + c0 * (int64_t)J);
-    const int n2 = ncols * J / 2;  // pairs; pair e covers rows (2e) % J and (2e) % J + 1
+    const int n2 = ncols * J / 2;  // pairs; pair e covers rows (2e) % J and (2e) % J + 1 of column (2e) / J
     const int r0 = (2 * tid) % J;
     unsigned m0 = 0u, m1 = 0u;
     int e = tid;
@@ -294,17 +355,25 @@ __global__ void __launch_bounds__(256) k_rowgroup_exp(const T *__restrict__ y, i
       for (int u = 0; u < 4; ++u) v[u] = __ldg(base + e + u * 256);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        m0 = max(m0, hi_mag(v[u].x));
-        m1 = max(m1, hi_mag(v[u].y));
+        const unsigned a = hi_mag(v[u].x), b = hi_mag(v[u].y);
+        m0 = max(m0, a);
+        m1 = max(m1, b);
+        if (colexp) atomicMax(&cmax[(2 * (e + u * 256)) / J], max(a, b));  // J < 64 only
       }
     }
     for (; e < n2; e += 256) {
       const V2 v = __ldg(base + e);
-      m0 = max(m0, hi_mag(v.x));
-      m1 = max(m1, hi_mag(v.y));
+      const unsigned a = hi_mag(v.x), b = hi_mag(v.y);
+      m0 = max(m0, a);
+      m1 = max(m1, b);
+      if (colexp) atomicMax(&cmax[(2 * e) / J], max(a, b));
     }
     atomicMax(&rmax[r0], m0);
     atomicMax(&rmax[r0 + 1], m1);
+    if (colexp) {
+      __syncthreads();
+      for (int cc = tid; cc < ncols; cc += 256) colexp[c0 + cc] = exp_above(mag_pattern(cmax[cc], kF64), kF64);
+    }
   } else {
     // lane `lane` reads columns c0 + lane + 32 k, k < 16; their offsets are
     // computed once and reused for every row
@@ -1720,10 +1789,10 @@ int launch_gram_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int6
     }
   } else if (f64)
     k_rowgroup_exp<double><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const double *>(y), L, (int)J, p.K,
-                                                               contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
+                                                               contig_pairs, w.table, w.gmax, d_colexp);
   else
     k_rowgroup_exp<float><<<(unsigned)p.ngroups, 256, 0, s>>>(static_cast<const float *>(y), L, (int)J, p.K,
-                                                              contig_pairs, w.table, w.gmax, L > 1 ? d_colexp : nullptr);
+                                                              contig_pairs, w.table, w.gmax, d_colexp);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, in_bytes, 1);
   if (unfold) {  // the explicit unfolding (counted with the exponent pass: data movement before the Gram)

@@ -444,37 +444,81 @@ TtmSplit2Plan ttm_split2_plan(int64_t L, int64_t J, int64_t B, int64_t R, const 
 // is the contiguous vector y[c J .. c J + J - 1].  The CTA's warps have
 // fixed roles and meet only at mbarriers, so conversion, tensor-core work
 // and the drain of the previous tile overlap:
-//   16 converter warps take whole columns (8 per warp per tile): lanes read
-//      consecutive 16-byte pairs (coalesced), a warp reduction gives the
-//      column exponent, and each digit row goes to a 128-byte swizzled
-//      K-major tile (one row per store instruction, no bank conflicts); two
-//      columns per warp are in flight in registers;
-//   1 MMA warp issues the tile's MMAs (columns are the M = 128 rows, U the N
-//      operand: 4 MMAs per k-step, one per digit of Y against U's stacked
+//   16 converter warps take whole columns (8 per warp per tile) in halves of
+//      64 entries (the K-parts of the MMA): lanes read consecutive 16-byte
+//      pairs (coalesced), scale them by the column exponent (from the
+//      exponent pass, or a pass of its own) and write each digit row to a
+//      128-byte swizzled K-major tile (one row per store instruction, no
+//      bank conflicts).  All first halves of a tile are written before the
+//      second halves, so the MMAs of one half run while the other is
+//      converted; eight half-columns per warp are in flight in registers;
+//   1 MMA warp issues each half's MMAs (columns are the M = 128 rows, U the
+//      N operand: 4 MMAs per k-step, one per digit of Y against U's stacked
 //      digit tiles) into one of two TMEM accumulator sets;
 //   8 drain warps (two per TMEM lane quarter) assemble each output exactly
-//      from the four levels, stage the tile's outputs (R contiguous doubles
-//      per column: the tile's output is one contiguous block) in shared
-//      memory and write them out row by row.
-// Barriers: a_full (converters -> MMA: digits written), a_free (MMA commit:
-// digits read), acc_full[2] (MMA commit: a set holds a finished tile),
-// acc_free[2] (drain -> MMA: set read out), cexp[4] (converters -> drain:
-// column exponents of a tile, in a ring of four slots).  Every wait is
-// bounded and also gives up once another role has flagged an error.
+//      from the four levels and store it from registers (a thread's four
+//      consecutive outputs of one column fill one 32-byte sector).
+// Barriers: part_full[2] (converters -> MMA: a half's digits written),
+// part_free[2] (MMA commit: a half's digits read), acc_full[2] (MMA commit:
+// a set holds a finished tile), acc_free[2] (drain -> MMA: set read out).
+// Every wait is bounded and also gives up once another role has flagged an
+// error.
 // ---------------------------------------------------------------------------
 struct TtmL1Plan {
-  int J, Jp, R, Rp, parts, Rs, tmem_cols;
+  int J, Jp, R, Rp, parts, tmem_cols;
   int64_t K, ntiles;
   int grid;
-  size_t u_bytes, a_bytes, stg_bytes, smem;
+  size_t u_bytes, a_bytes, smem;
 };
 
 constexpr int kL1Conv = 16;                             // converter warps
 constexpr int kL1Drain = 8;                             // drain warps (two per TMEM lane quarter)
 constexpr int kL1Threads = (kL1Conv + kL1Drain + 1) * 32;
 constexpr int kL1ColsPerWarp = kM2 / kL1Conv;           // 8
-constexpr int kL1Depth = 4;                             // columns in flight per converter warp (64 KB per SM)
-constexpr int kL1Slots = 4;                             // column-exponent ring
+
+// v = round(|y| 2^(28 - f)) (ties away from zero) for |y| < 2^f, as its
+// balanced digits v = d0 2^21 + d1 2^14 + d2 2^7 + d3 (0 <= d0 <= 128,
+// -64 <= d1, d2, d3 <= 63), each carrying y's sign, as exact floats.  With
+// m29 the leading 29 bits of the significand (its 24 bits, shifted, for
+// float) and sh the distance of y's exponent below f (>= 0), v =
+// ((m29 >> sh) + 1) >> 1: the dropped bits decide no rounding the kept ones
+// do not.  Adding 64 (1 + 2^7 + 2^14) turns the lower three digits into
+// plain 7-bit fields e (digit e - 64); a field placed below the exponent
+// bits of 2^23 reads as the float 2^23 + e, and subtracting 2^23 + 64 (2^23
+// for the top digit) leaves the digit, exactly; y's sign set on both
+// operands carries over to the difference.  Zeros and subnormals give 0.
+__device__ __forceinline__ void digits28_from_v(unsigned t, unsigned sign, float (&d)[4]) {
+  const unsigned v = (t + 0x204081u) >> 1;  // ((t + 1) >> 1) + 64 (1 + 2^7 + 2^14)
+  const unsigned M = sign | 0x4B000000u;    // the bits of +-2^23
+  const float m0 = __uint_as_float(M), m64 = __uint_as_float(M | 64u);
+  d[3] = __fsub_rn(__uint_as_float((v & 127u) | M), m64);
+  d[2] = __fsub_rn(__uint_as_float(((v >> 7) & 127u) | M), m64);
+  d[1] = __fsub_rn(__uint_as_float(((v >> 14) & 127u) | M), m64);
+  d[0] = __fsub_rn(__uint_as_float((v >> 21) | M), m0);
+}
+__device__ __forceinline__ unsigned shr_clamped(unsigned x, unsigned sh) {  // x >> sh, 0 for sh >= 32
+  unsigned r;
+  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(sh));
+  return r;
+}
+// f1022 = f + 1022
+__device__ __forceinline__ void digits28(double y, int f1022, float (&d)[4]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned ex = (hi >> 20) & 0x7FFu;
+  const unsigned m29 = __funnelshift_l(lo, (hi & 0xFFFFFu) | 0x100000u, 8);  // (m53 >> 24)
+  unsigned t = shr_clamped(m29, (unsigned)(f1022 - (int)ex));
+  t = ex ? t : 0u;
+  digits28_from_v(t, hi & 0x80000000u, d);
+}
+__device__ __forceinline__ void digits28(float y, int f1022, float (&d)[4]) {
+  const unsigned b = __float_as_uint(y);
+  const unsigned ex = (b >> 23) & 0xFFu;
+  const unsigned m29 = ((b & 0x7FFFFFu) | 0x800000u) << 5;
+  unsigned t = shr_clamped(m29, (unsigned)(f1022 - 896 - (int)ex));  // f + 126 - ex
+  t = ex ? t : 0u;
+  digits28_from_v(t, b & 0x80000000u, d);
+}
 
 // round(|y| 2^(28 - f)) etc. are above; the two roles' bounded wait:
 // true once the phase of `parity` has completed, false on expiry (which
@@ -495,25 +539,24 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
 }
 
-template <typename T>
+// P: K-parts of 64 entries (1 for J <= 64, else 2); colexp: the exponent
+// above each column's largest magnitude.
+template <typename T, int P>
 __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restrict__ y, const double *__restrict__ U,
-                                                              TtmL1Plan p, double *__restrict__ z,
-                                                              int *__restrict__ err) {
+                                                              const int *__restrict__ colexp, TtmL1Plan p,
+                                                              double *__restrict__ z, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
-  __shared__ __align__(8) unsigned long long a_full, a_free, acc_full[2], acc_free[2], cexp_full[kL1Slots];
-  __shared__ int colexp[kL1Slots][kM2];
+  __shared__ __align__(8) unsigned long long part_full[2], part_free[2], acc_full[2], acc_free[2];
   __shared__ int rowexp[kM];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int stop;
-  __shared__ int drain_go;
   constexpr bool kF64 = sizeof(T) == 8;
   using V2 = typename std::conditional<kF64, double2, float2>::type;
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char *At = base;                                  // 4 digit tiles, SW128 K-major
   unsigned char *Ut = base + p.a_bytes;                      // 4 digit tiles, no swizzle
-  double *stg = reinterpret_cast<double *>(Ut + p.u_bytes);  // 128 x Rs output staging
-  const int a_tile = p.parts * kM2 * 128;
+  const int a_tile = P * kM2 * 128;
   const int u_tile = p.Rp * p.Jp * 2;
   const uint32_t sbo_u = (uint32_t)(p.Jp / 8) * 128u;
   uint32_t idesc_q[kBTiles];  // N = (4 - q) Rp: digit q of Y against U1 .. U(4-q)
@@ -528,13 +571,12 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_addr(&a_full), kL1Conv);
-    mbar_init(smem_addr(&a_free), 1);
     for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_addr(&part_full[k]), kL1Conv);
+      mbar_init(smem_addr(&part_free[k]), 1);
       mbar_init(smem_addr(&acc_full[k]), 1);
       mbar_init(smem_addr(&acc_free[k]), kL1Drain);
     }
-    for (int k = 0; k < kL1Slots; ++k) mbar_init(smem_addr(&cexp_full[k]), kL1Conv);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
   }
@@ -566,7 +608,7 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
     for (int t = 0; t < kATiles; ++t)
       *reinterpret_cast<uint4 *>(Ut + t * u_tile + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
   }
-  // zero the A tiles once: K columns past J (up to the 64-wide part) stay zero
+  // zero the A tiles once: K columns past Jp (up to the 64-wide part) stay zero
   for (int e = tid; e < (int)(p.a_bytes / 16); e += kL1Threads) reinterpret_cast<uint4 *>(At)[e] = make_uint4(0, 0, 0, 0);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   fence_before();
@@ -578,59 +620,68 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
 
   if (warp < kL1Conv) {
     // ---------------- converters ----------------
-    // column m of tile t, entries j = 2 lane + 64 h (h < 2) as two pairs
-    auto load_col = [&](int it, int m, V2(&v)[2]) {
-      const int64_t t = t0 + (int64_t)it * tstride;
-      const int64_t c = t * kM2 + m;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * lane + 64 * h;
-        if (it < ntc && c < p.K && j < p.J)
-          v[h] = __ldg(reinterpret_cast<const V2 *>(y + c * (int64_t)p.J + j));
-        else
-          v[h].x = v[h].y = T(0);
-      }
+    // half h of column m of this CTA's tile it: entries j = 2 lane + 64 h (a pair)
+    auto load_half = [&](int it, int m, int h, V2 &v) {
+      const int64_t c = (t0 + (int64_t)it * tstride) * kM2 + m;
+      const int j = 2 * lane + 64 * h;
+      if (it < ntc && c < p.K && j < p.J)
+        v = __ldg(reinterpret_cast<const V2 *>(y + c * (int64_t)p.J + j));
+      else
+        v.x = v.y = T(0);
     };
-    V2 cb[kL1Depth][2];
+    auto load_exp = [&](int it, int m) {
+      const int64_t c = (t0 + (int64_t)it * tstride) * kM2 + m;
+      return (it < ntc && c < p.K) ? __ldg(colexp + c) : 0;
+    };
+    // slot k holds column warp + 16 k: its current half, and its exponent
+    V2 cb[kL1ColsPerWarp];
+    int fx[kL1ColsPerWarp];
 #pragma unroll
-    for (int k = 0; k < kL1Depth; ++k) load_col(0, warp + kL1Conv * k, cb[k]);
-    for (int it = 0; it < ntc; ++it) {
-      if (it >= 1) {  // the previous tile's MMAs have read the digit tiles
-        int ok = 0;
-        if (lane == 0) ok = role_wait(smem_addr(&a_free), (uint32_t)((it - 1) & 1), &stop);
-        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      }
-      const int slot = it % kL1Slots;
+    for (int k = 0; k < kL1ColsPerWarp; ++k) {
+      load_half(0, warp + kL1Conv * k, 0, cb[k]);
+      fx[k] = load_exp(0, warp + kL1Conv * k);
+    }
+    // this lane's byte offset within a digit row: 16-byte chunk lane / 4 of the
+    // 128-byte row, XOR-swizzled by the row's index mod 8 (= warp mod 8 for
+    // every column of this warp)
+    const int lane_off = (((lane >> 2) ^ (warp & 7)) << 4) + (lane & 3) * 4;
+    bool ok = true;
+    for (int it = 0; it < ntc && ok; ++it) {
 #pragma unroll
-      for (int k = 0; k < kL1ColsPerWarp; ++k) {
-        const int m = warp + kL1Conv * k;
-        V2(&v)[2] = cb[k % kL1Depth];
-        const unsigned mx = __reduce_max_sync(
-            0xffffffffu, max(max(hi_mag(v[0].x), hi_mag(v[0].y)), max(hi_mag(v[1].x), hi_mag(v[1].y))));
-        const int f = exp_above(mag_pattern(mx, kF64), kF64);
-        if (lane == 0) colexp[slot][m] = f;
-        const int f1022 = f + 1022;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (2 * lane + 64 * h < p.Jp) {
-            float d0[4], d1[4];
-            digits4_float(scaled_int28_bits(v[h].x, f1022), d0);
-            digits4_float(scaled_int28_bits(v[h].y, f1022), d1);
-            const int off = h * (kM2 * 128) + m * 128 + (((lane >> 2) ^ (m & 7)) << 4) + (lane & 3) * 4;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint32_t *>(At + q * a_tile + off) = bf16_pair(d0[q], d1[q]);
+      for (int h = 0; h < P; ++h) {
+        if (it >= 1) {  // the previous tile's MMAs have read this half
+          int w = 0;
+          if (lane == 0) w = role_wait(smem_addr(&part_free[h]), (uint32_t)((it - 1) & 1), &stop);
+          if (!__shfl_sync(0xffffffffu, w, 0)) {
+            ok = false;
+            break;
           }
         }
-        // refill: the column kL1Depth ahead (possibly of this CTA's next tile)
-        const int kn = k + kL1Depth;
-        if (kn < kL1ColsPerWarp) load_col(it, warp + kL1Conv * kn, v);
-        else load_col(it + 1, warp + kL1Conv * (kn - kL1ColsPerWarp), v);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(smem_addr(&cexp_full[slot]));
-        mbar_arrive(smem_addr(&a_full));
+        unsigned char *Ah = At + h * (kM2 * 128) + lane_off;
+#pragma unroll
+        for (int k = 0; k < kL1ColsPerWarp; ++k) {
+          const int m = warp + kL1Conv * k;
+          if (2 * lane + 64 * h < p.Jp) {
+            const int f1022 = fx[k] + 1022;
+            float d0[4], d1[4];
+            digits28(cb[k].x, f1022, d0);
+            digits28(cb[k].y, f1022, d1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint32_t *>(Ah + q * a_tile + m * 128) = bf16_pair(d0[q], d1[q]);
+          }
+          // refill: the next half of this column, or the first half of the
+          // column this slot takes in the next tile (with its exponent)
+          if (h + 1 < P) {
+            load_half(it, m, h + 1, cb[k]);
+          } else {
+            load_half(it + 1, m, 0, cb[k]);
+            fx[k] = load_exp(it + 1, m);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&part_full[h]));
       }
     }
   } else if (warp < kL1Conv + kL1Drain) {
@@ -638,18 +689,22 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
     const int dw = warp - kL1Conv;
     const int q = warp & 3;           // the TMEM lane quarter this warp may read
     const int half = dw >> 2;         // which half of the r range
-    const int m = 32 * q + lane;
+    const int m = 32 * q + lane;      // this thread's column of the tile
     const int rh = p.Rp / 2;          // a multiple of 8
+    const bool vec = (p.R % 2) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+    auto col_of = [&](int it) { return (t0 + (int64_t)it * tstride) * kM2 + m; };
+    int fnext = (ntc > 0 && col_of(0) < p.K) ? __ldg(colexp + col_of(0)) : 0;
     for (int it = 0; it < ntc; ++it) {
-      const int set = it & 1, slot = it % kL1Slots;
-      if (dw == 0 && lane == 0) {
-        drain_go = role_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1), &stop) &&
-                   role_wait(smem_addr(&cexp_full[slot]), (uint32_t)((it / kL1Slots) & 1), &stop);
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");
-      if (!drain_go) break;
+      const int set = it & 1;
+      int w = 0;
+      if (lane == 0) w = role_wait(smem_addr(&acc_full[set]), (uint32_t)((it >> 1) & 1), &stop);
+      if (!__shfl_sync(0xffffffffu, w, 0)) break;
       fence_after();
-      const int fcol = colexp[slot][m];
+      const int64_t c = col_of(it);
+      const bool valid = c < p.K;
+      const int fcol = fnext;
+      fnext = (it + 1 < ntc && col_of(it + 1) < p.K) ? __ldg(colexp + col_of(it + 1)) : 0;
+      double *zc = z + c * (int64_t)p.R;
       const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(set * 4 * p.Rp);
       for (int r0 = half * rh; r0 < (half + 1) * rh; r0 += 4) {
         uint32_t a[4][4];
@@ -659,55 +714,67 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
                        : "=r"(a[lev][0]), "=r"(a[lev][1]), "=r"(a[lev][2]), "=r"(a[lev][3])
                        : "r"(tb + (uint32_t)(lev * p.Rp + r0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid && r0 < p.R) {
+          double o[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = r0 + e;
-          if (r < p.R)
-            stg[m * p.Rs + r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + fcol - 42);
+          for (int e = 0; e < 4; ++e)
+            o[e] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r0 + e] + fcol - 42);
+          if (vec) {  // R even: (r0, r0 + 1) and (r0 + 2, r0 + 3) are whole pairs or past R
+            *reinterpret_cast<double2 *>(zc + r0) = make_double2(o[0], o[1]);
+            if (r0 + 2 < p.R) *reinterpret_cast<double2 *>(zc + r0 + 2) = make_double2(o[2], o[3]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (r0 + e < p.R) zc[r0 + e] = o[e];
+          }
         }
       }
       fence_before();
-      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");
+      __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&acc_free[set]));  // this warp's reads of the set are complete
-      // the tile's output is z[t 128 R ..]: rows of R contiguous doubles
-      const int64_t t = t0 + (int64_t)it * tstride;
-      double *zt = z + t * kM2 * (int64_t)p.R;
-      const int nvalid = (int)(p.K - t * kM2 < kM2 ? p.K - t * kM2 : kM2);
-      for (int mm = dw; mm < nvalid; mm += kL1Drain)
-        for (int r = lane; r < p.R; r += 32) zt[(int64_t)mm * p.R + r] = stg[mm * p.Rs + r];
-      asm volatile("bar.sync 1, %0;" ::"n"(kL1Drain * 32) : "memory");  // staging free for the next tile
     }
   } else if (lane == 0) {
     // ---------------- MMA issue ----------------
     const uint32_t ab = smem_addr(At), ub = smem_addr(Ut);
-    int issued = -1;
+    const int nks = p.Jp / 16;
+    int last_h = -1, last_par = 0;  // the last commit of part_free: no MMA of ours runs past it
     for (int it = 0; it < ntc; ++it) {
       const int set = it & 1;
-      if (!role_wait(smem_addr(&a_full), (uint32_t)(it & 1), &stop)) break;
       if (it >= 2 && !role_wait(smem_addr(&acc_free[set]), (uint32_t)(((it - 2) >> 1) & 1), &stop)) break;
-      fence_after();
       // U's four digit tiles are stacked rows of one K-major operand (U1 first),
       // so the MMA of Y's digit q against its first (4 - q) Rp rows, written
       // at column q Rp of the set, adds Y_q U_a into level q + a for every
       // a <= 3 - q at once: 4 MMAs per k-step carry the 10 digit products.
       const uint32_t d0 = tmem + (uint32_t)(set * 4 * p.Rp);
-      for (int ks = 0; ks < p.Jp / 16; ++ks) {
-        const uint32_t koff = (uint32_t)((ks >> 2) * (kM2 * 128) + (ks & 3) * 32);
-        const uint64_t ucat = smem_desc(ub + 256 * ks, 128, sbo_u);
+      bool ok = true;
 #pragma unroll
-        for (int q = 0; q < kBTiles; ++q) {
-          const uint64_t ya = smem_desc_sw128(ab + q * a_tile + koff, 1024);
-          // levels q..3 start accumulating at the first k-step of digit q = 0;
-          // later digits add into levels the q = 0 MMA has already initialised
-          mma_bf16(d0 + q * p.Rp, ya, ucat, idesc_q[q], (ks == 0 && q == 0) ? 0u : 1u);
+      for (int h = 0; h < P; ++h) {
+        if (!role_wait(smem_addr(&part_full[h]), (uint32_t)(it & 1), &stop)) {
+          ok = false;
+          break;
         }
+        fence_after();
+        for (int ks = 4 * h; ks < nks && ks < 4 * h + 4; ++ks) {
+          const uint32_t koff = (uint32_t)(h * (kM2 * 128) + (ks & 3) * 32);
+          const uint64_t ucat = smem_desc(ub + 256 * ks, 128, sbo_u);
+#pragma unroll
+          for (int q = 0; q < kBTiles; ++q) {
+            const uint64_t ya = smem_desc_sw128(ab + q * a_tile + koff, 1024);
+            // levels q..3 start accumulating at the first k-step of digit q = 0;
+            // later digits add into levels the q = 0 MMA has already initialised
+            mma_bf16(d0 + q * p.Rp, ya, ucat, idesc_q[q], (ks == 0 && q == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(smem_addr(&part_free[h]));
+        last_h = h;
+        last_par = it & 1;
       }
-      mma_commit(smem_addr(&a_free));
+      if (!ok) break;
       mma_commit(smem_addr(&acc_full[set]));
-      issued = it;
     }
-    // no MMA of ours may still run when TMEM is released
-    if (issued >= 0) mbar_wait(smem_addr(&a_free), (uint32_t)(issued & 1));
+    // no MMA of ours may still run when TMEM is released (a commit tracks all
+    // earlier MMAs of this thread)
+    if (last_h >= 0) mbar_wait(smem_addr(&part_free[last_h]), (uint32_t)last_par);
   }
   fence_before();
   __syncthreads();
@@ -726,7 +793,6 @@ TtmL1Plan ttm_l1_plan(int64_t J, int64_t B, int64_t R, const void *y, tucker_dty
   p.R = (int)R;
   p.Rp = (int)((R + 15) / 16 * 16);
   p.parts = (p.Jp + 63) / 64;
-  p.Rs = p.R | 1;
   const int cols = 2 * 4 * p.Rp;  // two accumulator sets of four levels
   p.tmem_cols = 32;
   while (p.tmem_cols < cols) p.tmem_cols <<= 1;
@@ -735,10 +801,9 @@ TtmL1Plan ttm_l1_plan(int64_t J, int64_t B, int64_t R, const void *y, tucker_dty
   p.grid = (int)std::max<int64_t>(1, std::min<int64_t>(dev.sms, p.ntiles));
   p.a_bytes = (size_t)4 * p.parts * kM2 * 128;
   p.u_bytes = (size_t)4 * p.Rp * p.Jp * 2;
-  p.stg_bytes = (size_t)kM2 * p.Rs * 8;
-  p.smem = 1024 + p.a_bytes + p.u_bytes + p.stg_bytes;
+  p.smem = 1024 + p.a_bytes + p.u_bytes;
   const size_t elem = dt == TUCKER_F64 ? 8 : 4;
-  const bool ok = J % 2 == 0 && cols <= 512 && reinterpret_cast<uintptr_t>(y) % (2 * elem) == 0 &&
+  const bool ok = J % 2 == 0 && J <= kMaxJp && cols <= 512 && reinterpret_cast<uintptr_t>(y) % (2 * elem) == 0 &&
                   p.smem + 4096 <= (size_t)dev.smem_optin;
   if (!ok) p.parts = 0;
   return p;
@@ -1015,6 +1080,36 @@ __global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ y, int64_t
 }
 
 
+// column exponents of contiguous columns (L == 1) when no exponent pass has
+// run: a warp per column, its lanes over the column's entries (coalesced)
+template <typename T>
+__global__ void __launch_bounds__(256) k_colexp_l1(const T *__restrict__ y, int J, int64_t B,
+                                                   int *__restrict__ colexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = w0; c < B; c += nw) {
+    unsigned mx = 0u;
+    for (int j = lane; j < J; j += 32) mx = max(mx, hi_mag(__ldg(y + c * (int64_t)J + j)));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) colexp[c] = exp_above(mag_pattern(mx, sizeof(T) == 8), sizeof(T) == 8);
+  }
+}
+
+template <typename T>
+int run_ttm_l1(const void *y, const double *U, const int *d_colexp, const TtmL1Plan &q, double *z, int *d_err,
+               cudaStream_t s) {
+  if (q.parts == 1) {
+    TK_CUDA(allow_max_smem(k_ttm_split_l1<T, 1>));
+    k_ttm_split_l1<T, 1><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const T *>(y), U, d_colexp, q, z, d_err);
+  } else {
+    TK_CUDA(allow_max_smem(k_ttm_split_l1<T, 2>));
+    k_ttm_split_l1<T, 2><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const T *>(y), U, d_colexp, q, z, d_err);
+  }
+  TK_LAUNCHED();
+  return TUCKER_OK;
+}
+
 // The plan, or parts == 0 when the shape does not suit the tensor-map kernel.
 TtmTmaPlan ttm_tma_plan(int64_t L, int64_t J, int64_t B, int64_t R, tucker_dtype dt, const void *y,
                         const DeviceInfo &dev) {
@@ -1125,15 +1220,23 @@ int launch_ttm_split(const void *y, tucker_dtype dt, int64_t L, int64_t J, int64
     const TtmL1Plan q = ttm_l1_plan(J, B, R, y, dt, dev);
     if (q.parts > 0) {
       if (prof) prof->begin(TUCKER_PHASE_TTM_L1);
-      if (dt == TUCKER_F64) {
-        TK_CUDA(allow_max_smem(k_ttm_split_l1<double>));
-        k_ttm_split_l1<double><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const double *>(y), U, q, z, d_err);
-      } else {
-        TK_CUDA(allow_max_smem(k_ttm_split_l1<float>));
-        k_ttm_split_l1<float><<<q.grid, kL1Threads, q.smem, s>>>(static_cast<const float *>(y), U, q, z, d_err);
+      int *tmp = nullptr;
+      int launches = 1;
+      if (!d_colexp) {  // no exponent pass ran: the column exponents first
+        TK_CUDA(cudaMallocAsync(&tmp, sizeof(int) * (size_t)B, s));
+        const unsigned blocks = (unsigned)std::min<int64_t>((B + 7) / 8, (int64_t)dev.sms * 16);
+        if (dt == TUCKER_F64)
+          k_colexp_l1<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(y), (int)J, B, tmp);
+        else
+          k_colexp_l1<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(y), (int)J, B, tmp);
+        TK_LAUNCHED();
+        d_colexp = tmp;
+        ++launches;
       }
-      TK_LAUNCHED();
-      if (prof) prof->end(flops, bytes, 1);
+      if (dt == TUCKER_F64) TK_CHECK(run_ttm_l1<double>(y, U, d_colexp, q, z, d_err, s));
+      else TK_CHECK(run_ttm_l1<float>(y, U, d_colexp, q, z, d_err, s));
+      if (tmp) TK_CUDA(cudaFreeAsync(tmp, s));
+      if (prof) prof->end(flops, bytes, launches);
       return TUCKER_OK;
     }
   }

@@ -388,14 +388,15 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     for (int m = n + 1; m < N; ++m) B *= cur[m];
     const int64_t J = cur[n];
 
-    // Gram step (with L > 1 its exponent pass also leaves the column exponents the TTM needs)
+    // Gram step (its exponent pass also leaves the column exponents the TTM needs)
     DevBuf colexp;
+    const bool want_colexp = L > 1 || J <= 128;  // longer contiguous columns: the TTM scales its parts itself
     if (split) {
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev, ydt, Y);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
-      if (L > 1) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
+      if (want_colexp) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
       TK_CHECK(launch_gram_split(Y, ydt, L, J, B, S.as<double>(), gramws.as<double>(), dev, s, &prof,
-                                 L > 1 ? colexp.as<int>() : nullptr, f8));
+                                 want_colexp ? colexp.as<int>() : nullptr, f8));
       TK_CHECK(gram_split_error(gramws.as<double>(), L, J, B, dev, reinterpret_cast<int *>(h + 5), s));
       if (k == 0 && norm_from_trace) {
         TK_CHECK(launch_trace(S.as<double>(), J, d_nx2, s));
@@ -461,7 +462,7 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     TK_CHECK(ynew.alloc(sizeof(double) * L * R * B, s));
     if (split)
       TK_CHECK(launch_ttm_split(Y, ydt, L, J, B, factor_bufs[n].as<double>(), R, ynew.as<double>(), d_terr, dev, s,
-                                &prof, L > 1 ? colexp.as<int>() : nullptr));
+                                &prof, want_colexp ? colexp.as<int>() : nullptr));
     else
       TK_CHECK(launch_ttm(Y, ydt, L, J, B, factor_bufs[n].as<double>(), /*ak=*/J, /*aj=*/1, R, ynew.as<double>(),
                           dev, s, &prof));
