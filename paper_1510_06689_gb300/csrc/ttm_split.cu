@@ -9,16 +9,17 @@
 //   * U's column r is scaled by 2^(28 - e_r) (2^e_r above its largest
 //     magnitude) and every column c of Y (its J entries, all inside one tile)
 //     by 2^(28 - f_c); both are rounded to integers and split into four
-//     balanced digits v = s1 2^21 + s2 2^14 + s3 2^7 + s4 (|s1| <= 128,
-//     |s2..s4| <= 64), exact in BF16.  The TTM output feeds every later mode
+//     digits v = s1 2^21 + s2 2^14 + s3 2^7 + s4, exact in BF16 (U's
+//     balanced, |s1| <= 128, |s2..s4| <= 64; Y's with |s1|, |s3| <= 128).  The TTM output feeds every later mode
 //     and the core, so it keeps 28 bits (21 were measurably too few).
 //   * D = U_a Y_b^T products of levels a + b = 2..5 go to four exact TMEM
 //     accumulators:
 //       acc0 = U1 Y1^T,  acc1 = U1 Y2^T + U2 Y1^T,
 //       acc2 = U1 Y3^T + U2 Y2^T + U3 Y1^T,
 //       acc3 = U1 Y4^T + U2 Y3^T + U3 Y2^T + U4 Y1^T.
-//     With J <= 128 every level stays below 2^22 (acc3 <= 128 (2 2^13 + 2 2^12)),
-//     so all four are exact integers.  Levels 6..8 (products of two low
+//     Y's digits come from a 14-bit split of v (below), so its third digit
+//     reaches 128 too; with J <= 128 every level stays below 2^22 (acc2,
+//     acc3 <= 128 (3 2^13 + 2^12)), so all four are exact integers.  Levels 6..8 (products of two low
 //     digits of different entries, zero-mean) are dropped: at most ~2^-27 of
 //     sum_j |U_jr| |y_jc|.
 //   * Each output is assembled exactly in int64,
@@ -100,34 +101,57 @@ __device__ __forceinline__ double scaled_ll_to_double(long long v, int sc) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | frac));
 }
 
-// round(|y| 2^(28 - f)) with the sign of y, from the bits in 32-bit integer
-// arithmetic (ties away from zero); f1022 = f + 1022 and |y| < 2^f.  With m29
-// the leading 29 bits of the significand, v = (m29 + 2^sh) >> (sh + 1) for
-// sh = f + 1022 - exponent field; the lower bits cannot change the result.
-__device__ __forceinline__ int scaled_int28_bits(double y, int f1022) {
+// v = round(|y| 2^(28 - f)) (ties away from zero) for |y| < 2^f, as four
+// digits v = d0 2^21 + d1 2^14 + d2 2^7 + d3 carrying y's sign, as exact
+// floats (|d0|, |d2| <= 128, |d1|, |d3| <= 64).  With m29 the leading 29 bits
+// of the significand (its 24 bits, shifted, for float) and sh the distance of
+// y's exponent below f (>= 0), t = m29 >> sh and v = (t + 1) >> 1: the
+// dropped bits decide no rounding the kept ones do not.  The integer part is
+// kept short (the integer pipe is the busy one in this kernel): v's top and
+// low 14 bits become exact floats by placing them below the exponent bits of
+// 2^23 (with y's sign) and subtracting 2^23, and each splits into two base-128
+// digits by round-to-nearest on the float pipe.  Zeros and subnormals give 0.
+__device__ __forceinline__ void digits28_from_t(unsigned t, unsigned sign, float (&d)[4]) {
+  const unsigned t1 = t + 1u;
+  const unsigned M = sign | 0x4B000000u;  // the bits of +-2^23
+  const float mf = __uint_as_float(M);
+  const float fh = __fsub_rn(__uint_as_float((t1 >> 15) | M), mf);             // +-(v >> 14) <= 2^14
+  const float fl = __fsub_rn(__uint_as_float(((t1 >> 1) & 0x3FFFu) | M), mf);  // +-(v mod 2^14)
+  constexpr float kRound = 12582912.0f;                                        // 1.5 2^23
+  d[0] = __fsub_rn(__fmaf_rn(fh, 0x1p-7f, kRound), kRound);
+  d[1] = __fmaf_rn(d[0], -128.0f, fh);
+  d[2] = __fsub_rn(__fmaf_rn(fl, 0x1p-7f, kRound), kRound);
+  d[3] = __fmaf_rn(d[2], -128.0f, fl);
+}
+// the pair (a, b) as BF16 (a in the low half), by the conversion instruction;
+// exact for values with at most 8 significant bits
+__device__ __forceinline__ uint32_t bf16_pack(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+__device__ __forceinline__ unsigned shr_clamped(unsigned x, unsigned sh) {  // x >> sh, 0 for sh >= 32
+  unsigned r;
+  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(sh));
+  return r;
+}
+// f1022 = f + 1022
+__device__ __forceinline__ void digits28(double y, int f1022, float (&d)[4]) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(y);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const int ex = (int)((hi >> 20) & 0x7FFu);
-  const unsigned m29 = (((hi & 0xFFFFFu) | 0x100000u) << 8) | (lo >> 24);
-  const int sh = max(min(f1022 - ex, 30), 0);
-  unsigned v = (m29 + (1u << sh)) >> (sh + 1);
-  v = ex ? v : 0u;
-  const int sgn = (int)hi >> 31;
-  return ((int)v ^ sgn) - sgn;
+  const unsigned ex = (hi >> 20) & 0x7FFu;
+  const unsigned m29 = __funnelshift_l(lo, (hi & 0xFFFFFu) | 0x100000u, 8);  // (m53 >> 24)
+  unsigned t = shr_clamped(m29, (unsigned)(f1022 - (int)ex));
+  t = ex ? t : 0u;
+  digits28_from_t(t, hi & 0x80000000u, d);
 }
-__device__ __forceinline__ int scaled_int28_bits(float y, int f1022) {
-  return scaled_int28(y, f1022 - 1022);
-}
-
-// the four balanced digits of v (|v| <= 2^28) as exact floats
-__device__ __forceinline__ void digits4_float(int v, float (&d)[4]) {
-  const int h = (v + 64) >> 7;  // |h| <= 2^21
-  d[3] = small_int_float(v - (h << 7));
-  const float hf = small_int_float(h);
-  d[0] = round_float(hf * 0x1p-14f);
-  const float r = __fmaf_rn(d[0], -16384.0f, hf);
-  d[1] = round_float(r * 0x1p-7f);
-  d[2] = __fmaf_rn(d[1], -128.0f, r);
+__device__ __forceinline__ void digits28(float y, int f1022, float (&d)[4]) {
+  const unsigned b = __float_as_uint(y);
+  const unsigned ex = (b >> 23) & 0xFFu;
+  const unsigned m29 = ((b & 0x7FFFFFu) | 0x800000u) << 5;
+  unsigned t = shr_clamped(m29, (unsigned)(f1022 - 896 - (int)ex));  // f + 126 - ex
+  t = ex ? t : 0u;
+  digits28_from_t(t, b & 0x80000000u, d);
 }
 
 // sum_k a_k 2^(28 - 7k) 2^sc as a float64, from four float accumulators that
@@ -350,8 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
           float d0[4], d1[4];
-          digits4_float(scaled_int28_bits(raw[k][e], e_col + 1022), d0);
-          digits4_float(scaled_int28_bits(raw[k][e + 1], e_col + 1022), d1);
+          digits28(raw[k][e], e_col + 1022, d0);
+          digits28(raw[k][e + 1], e_col + 1022, d1);
 #pragma unroll
           for (int q = 0; q < kBTiles; ++q) w[q][e >> 1] = bf16_pair(d0[q], d1[q]);
         }
@@ -475,50 +499,6 @@ constexpr int kL1Conv = 16;                             // converter warps
 constexpr int kL1Drain = 8;                             // drain warps (two per TMEM lane quarter)
 constexpr int kL1Threads = (kL1Conv + kL1Drain + 1) * 32;
 constexpr int kL1ColsPerWarp = kM2 / kL1Conv;           // 8
-
-// v = round(|y| 2^(28 - f)) (ties away from zero) for |y| < 2^f, as its
-// balanced digits v = d0 2^21 + d1 2^14 + d2 2^7 + d3 (0 <= d0 <= 128,
-// -64 <= d1, d2, d3 <= 63), each carrying y's sign, as exact floats.  With
-// m29 the leading 29 bits of the significand (its 24 bits, shifted, for
-// float) and sh the distance of y's exponent below f (>= 0), v =
-// ((m29 >> sh) + 1) >> 1: the dropped bits decide no rounding the kept ones
-// do not.  Adding 64 (1 + 2^7 + 2^14) turns the lower three digits into
-// plain 7-bit fields e (digit e - 64); a field placed below the exponent
-// bits of 2^23 reads as the float 2^23 + e, and subtracting 2^23 + 64 (2^23
-// for the top digit) leaves the digit, exactly; y's sign set on both
-// operands carries over to the difference.  Zeros and subnormals give 0.
-__device__ __forceinline__ void digits28_from_v(unsigned t, unsigned sign, float (&d)[4]) {
-  const unsigned v = (t + 0x204081u) >> 1;  // ((t + 1) >> 1) + 64 (1 + 2^7 + 2^14)
-  const unsigned M = sign | 0x4B000000u;    // the bits of +-2^23
-  const float m0 = __uint_as_float(M), m64 = __uint_as_float(M | 64u);
-  d[3] = __fsub_rn(__uint_as_float((v & 127u) | M), m64);
-  d[2] = __fsub_rn(__uint_as_float(((v >> 7) & 127u) | M), m64);
-  d[1] = __fsub_rn(__uint_as_float(((v >> 14) & 127u) | M), m64);
-  d[0] = __fsub_rn(__uint_as_float((v >> 21) | M), m0);
-}
-__device__ __forceinline__ unsigned shr_clamped(unsigned x, unsigned sh) {  // x >> sh, 0 for sh >= 32
-  unsigned r;
-  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(sh));
-  return r;
-}
-// f1022 = f + 1022
-__device__ __forceinline__ void digits28(double y, int f1022, float (&d)[4]) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned ex = (hi >> 20) & 0x7FFu;
-  const unsigned m29 = __funnelshift_l(lo, (hi & 0xFFFFFu) | 0x100000u, 8);  // (m53 >> 24)
-  unsigned t = shr_clamped(m29, (unsigned)(f1022 - (int)ex));
-  t = ex ? t : 0u;
-  digits28_from_v(t, hi & 0x80000000u, d);
-}
-__device__ __forceinline__ void digits28(float y, int f1022, float (&d)[4]) {
-  const unsigned b = __float_as_uint(y);
-  const unsigned ex = (b >> 23) & 0xFFu;
-  const unsigned m29 = ((b & 0x7FFFFFu) | 0x800000u) << 5;
-  unsigned t = shr_clamped(m29, (unsigned)(f1022 - 896 - (int)ex));  // f + 126 - ex
-  t = ex ? t : 0u;
-  digits28_from_v(t, b & 0x80000000u, d);
-}
 
 // round(|y| 2^(28 - f)) etc. are above; the two roles' bounded wait:
 // true once the phase of `parity` has completed, false on expiry (which
@@ -668,7 +648,7 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
             digits28(cb[k].y, f1022, d1);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint32_t *>(Ah + q * a_tile + m * 128) = bf16_pair(d0[q], d1[q]);
+              *reinterpret_cast<uint32_t *>(Ah + q * a_tile + m * 128) = bf16_pack(d0[q], d1[q]);
           }
           // refill: the next half of this column, or the first half of the
           // column this slot takes in the next tile (with its exponent)
@@ -965,8 +945,8 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
       for (int k = 0; k < 8; k += 2) {
         float d0[4], d1[4];
         const T y0 = m_in_box ? raw[k * p.BL] : T(0), y1 = m_in_box ? raw[(k + 1) * p.BL] : T(0);
-        digits4_float(scaled_int28_bits(y0, f1022), d0);
-        digits4_float(scaled_int28_bits(y1, f1022), d1);
+        digits28(y0, f1022, d0);
+        digits28(y1, f1022, d1);
 #pragma unroll
         for (int qq = 0; qq < kBTiles; ++qq) w[qq][k >> 1] = bf16_pair(d0[qq], d1[qq]);
       }
