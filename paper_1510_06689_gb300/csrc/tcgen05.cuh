@@ -105,6 +105,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
 }
 
 // Bounded polling wait for the phase with the given parity; false on expiry.
+// one arrival (release semantics at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   for (long long it = 0; it < kTcWaitLimit; ++it) {
     uint32_t ok;

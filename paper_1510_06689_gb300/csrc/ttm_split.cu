@@ -515,10 +515,6 @@ __device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar) : "memory");
-}
-
 // P: K-parts of 64 entries (1 for J <= 64, else 2); colexp: the exponent
 // above each column's largest magnitude.
 template <typename T, int P>
