@@ -45,6 +45,8 @@ namespace {
 constexpr int kBtMaxJ = 128;     // every mode of a batched tensor (the one-CTA Jacobi's limit)
 constexpr int kBtThreads = 256;
 constexpr int kBtStage = 32;     // columns staged in shared memory at a time
+static_assert(kBtThreads == 256 && kBtStage == 32 && kBtMaxJ <= 128,
+              "the stage loader's fixed trip counts assume 8 warps, 32 columns and J <= 128");
 constexpr int kBtMaxModes = TUCKER_MAX_MODES;
 
 struct BtItem {
@@ -152,19 +154,36 @@ __device__ __forceinline__ void bt_load_stage(const T *__restrict__ y, int64_t L
     colbase[tid] = v;
   }
   __syncthreads();
-  const int total = kBtStage * ld;
-  if (L == 1) {  // a column is J contiguous entries: threads along j
-    for (int e = tid; e < total; e += kBtThreads) {
-      const int kk = e / ld, j = e - kk * ld;
-      const int64_t base = colbase[kk];
-      Ys[e] = (j < J && base >= 0) ? (double)y[base + j] : 0.0;
+  // 16 loads in flight per thread before their shared-memory stores (ld <= 128)
+  if (L == 1) {  // a column is J contiguous entries: a warp per column, lanes along j
+    const int w = tid >> 5, lane = tid & 31;
+    double v[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t base = colbase[w + 8 * q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = lane + 32 * i;
+        v[q][i] = (j < J && base >= 0) ? (double)y[base + j] : 0.0;
+      }
     }
-  } else {  // a row segment runs along l: threads along the columns
-    for (int e = tid; e < total; e += kBtThreads) {
-      const int j = e / kBtStage, kk = e - j * kBtStage;
-      const int64_t base = colbase[kk];
-      Ys[kk * ld + j] = (j < J && base >= 0) ? (double)y[base + L * (int64_t)j] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (lane + 32 * i < ld) Ys[(w + 8 * q) * ld + lane + 32 * i] = v[q][i];
+  } else {  // a row segment runs along l: threads along the columns, rows j = tid / 32 + 8 i
+    const int kk = tid & (kBtStage - 1), j0 = tid / kBtStage;
+    const int64_t base = colbase[kk];
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int j = j0 + 8 * i;
+      v[i] = (j < J && base >= 0) ? (double)y[base + L * (int64_t)j] : 0.0;
     }
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (j0 + 8 * i < ld) Ys[kk * ld + j0 + 8 * i] = v[i];
   }
   __syncthreads();
 }
@@ -336,19 +355,27 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_ttm(const BtTensor *__restric
       const int j = e / Rp, r = e - j * Rp;
       Us[e] = r < R ? Ut[j + (int64_t)J * r] : 0.0;
     }
-    const int rt = tid >> 3, ct = tid & 7;  // 4 rows r, 4 stage columns
-    const bool active = 4 * rt < R;
+    // thread (split sp, rows 4 rt.., stage columns 4 ct..): with few rows the
+    // contraction over j is split sp_n ways so that every thread works, the
+    // partial tiles summed through shared memory in split order
+    const int combos = ((R + 3) >> 2) * 8;
+    int sp_n = 1;
+    while (sp_n < 8 && 2 * sp_n * combos <= kBtThreads) sp_n *= 2;
+    const int sp = tid / combos, rest = tid - sp * combos;
+    const int rt = rest >> 3, ct = rest & 7;  // 4 rows r, 4 stage columns
+    const bool active = sp < sp_n;
+    const int jlo = J * sp / sp_n, jhi = J * (sp + 1) / sp_n;
     for (int64_t c0 = item.c0; c0 < item.c1; c0 += kBtStage) {
       bt_load_stage<T>(y, L, J, Jp, c0, min(item.c1, c0 + kBtStage), Ys, colbase);  // (its barriers cover Us too)
+      double acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
       if (active) {
-        double acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
         const double *pu = Us + 4 * rt;
         const double *py = Ys + 4 * ct * Jp;
-        for (int j = 0; j < J; ++j) {
+        for (int j = jlo; j < jhi; ++j) {
           const double2 u01 = *reinterpret_cast<const double2 *>(pu + j * Rp);
           const double2 u23 = *reinterpret_cast<const double2 *>(pu + j * Rp + 2);
           const double uv[4] = {u01.x, u01.y, u23.x, u23.y};
@@ -358,6 +385,24 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_ttm(const BtTensor *__restric
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = fma(uv[a], yv[b], acc[a][b]);
         }
+      }
+      if (sp_n > 1) {  // uniform over the CTA (one item at a time)
+        __syncthreads();  // the stage has been read: its buffer takes the partial tiles
+        double *red = Ys;  // sp_n x combos tiles of 16 <= kBtStage x kBtMaxJ doubles
+        if (active && sp > 0)
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) red[(sp * combos + rest) * 16 + 4 * a + b] = acc[a][b];
+        __syncthreads();
+        if (sp == 0)
+          for (int s2 = 1; s2 < sp_n; ++s2)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] += red[(s2 * combos + rest) * 16 + 4 * a + b];
+      }
+      if (active && sp == 0) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int64_t c = c0 + 4 * ct + b;
