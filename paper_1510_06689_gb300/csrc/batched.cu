@@ -424,15 +424,77 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_ttm(const BtTensor *__restric
 // C = op(A) B for J x J matrices (ld J) by the whole CTA, entries spread over
 // its threads; op(A) = A^T when transA.  Operands may have been written
 // earlier by this CTA (plain loads, after a barrier).
-__device__ void bt_gemm(int J, const double *A, int transA, const double *B, double *C) {
-  for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
-    const int i = e % J, j = e / J;
-    double acc = 0.0;
-    if (transA)
-      for (int k = 0; k < J; ++k) acc = fma(A[k + J * i], B[k + J * j], acc);
-    else
-      for (int k = 0; k < J; ++k) acc = fma(A[i + J * k], B[k + J * j], acc);
-    C[e] = acc;
+// C = op(A) B for J x J column-major matrices (J <= 128; op(A) = A or A^T),
+// by the whole CTA: panels of 32 k of op(A) and B pass through shared memory
+// k-major (row stride J4 + 2 = padded J rounded to 4, plus 2), and each thread
+// accumulates up to four 4 x 4 tiles of C in registers (8 shared loads per 16
+// FMAs), so the float64 pipe, not the loads, bounds it.  `sm` holds 2 x 32 x
+// (J4 + 2) doubles.  Ends with a barrier (C complete).
+constexpr int kGemmK = 32;
+constexpr size_t kGemmSmem = (size_t)2 * kGemmK * (kBtMaxJ + 2) * sizeof(double);
+__device__ void bt_gemm(int J, const double *A, int transA, const double *B, double *C, double *sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int J4 = (J + 3) & ~3, ld = J4 + 2, tn = J4 / 4, ntiles = tn * tn;
+  double *Ap = sm, *Bp = sm + kGemmK * ld;
+  double acc[4][16];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[u][e] = 0.0;
+  for (int k0 = 0; k0 < J4; k0 += kGemmK) {
+    __syncthreads();  // the previous panels are read out
+    for (int e = tid; e < kGemmK * J4; e += nt) {
+      // op(A)[i][k0 + kk] -> Ap[kk][i]: k fastest for A^T (contiguous in memory), i fastest for A
+      int i, kk;
+      if (transA) {
+        i = e / kGemmK;
+        kk = e - i * kGemmK;
+      } else {
+        kk = e / J4;
+        i = e - kk * J4;
+      }
+      const int k = k0 + kk;
+      double a = 0.0;
+      if (i < J && k < J) a = transA ? A[k + (int64_t)J * i] : A[i + (int64_t)J * k];
+      Ap[kk * ld + i] = a;
+    }
+    for (int e = tid; e < kGemmK * J4; e += nt) {  // B[k0 + kk][j] -> Bp[kk][j], k fastest
+      const int j = e / kGemmK, kk = e - j * kGemmK, k = k0 + kk;
+      Bp[kk * ld + j] = (j < J && k < J) ? B[k + (int64_t)J * j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tile = tid + u * nt;
+      if (tile >= ntiles) break;
+      const int ti = tile % tn, tj = tile / tn;
+      const double *pa = Ap + 4 * ti, *pb = Bp + 4 * tj;
+#pragma unroll 4
+      for (int kk = 0; kk < kGemmK; ++kk) {
+        const double2 a01 = *reinterpret_cast<const double2 *>(pa + kk * ld);
+        const double2 a23 = *reinterpret_cast<const double2 *>(pa + kk * ld + 2);
+        const double2 b01 = *reinterpret_cast<const double2 *>(pb + kk * ld);
+        const double2 b23 = *reinterpret_cast<const double2 *>(pb + kk * ld + 2);
+        const double av[4] = {a01.x, a01.y, a23.x, a23.y}, bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[u][4 * c + r] = fma(av[r], bv[c], acc[u][4 * c + r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int tile = tid + u * nt;
+    if (tile >= ntiles) break;
+    const int ti = tile % tn, tj = tile / tn;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = 4 * ti + r, j = 4 * tj + c;
+        if (i < J && j < J) C[i + (int64_t)J * j] = acc[u][4 * c + r];
+      }
   }
   __syncthreads();
 }
@@ -445,20 +507,21 @@ __device__ void bt_gemm(int J, const double *A, int transA, const double *B, dou
 __global__ void __launch_bounds__(kBtThreads) k_bt_presolve(const BtTensor *__restrict__ Tn, const double *__restrict__ S,
                                                             double *__restrict__ X, double *__restrict__ W,
                                                             double *__restrict__ S2) {
+  extern __shared__ __align__(16) double gsm[];
   const int t = blockIdx.x, J = (int)Tn[t].J;
   const int64_t o = (int64_t)t * kBtMaxJ * kBtMaxJ;
   double *Xt = X + o, *Wt = W + o, *S2t = S2 + o;
   const double *St = S + o;
   for (int it = 0; it < 2; ++it) {
-    bt_gemm(J, Xt, 1, Xt, Wt);  // P = X^T X
+    bt_gemm(J, Xt, 1, Xt, Wt, gsm);  // P = X^T X
     for (int e = threadIdx.x; e < J * J; e += blockDim.x) Wt[e] = (e % J == e / J ? 1.5 : 0.0) - 0.5 * Wt[e];
     __syncthreads();
-    bt_gemm(J, Xt, 0, Wt, S2t);  // X P into S2, then back to X
+    bt_gemm(J, Xt, 0, Wt, S2t, gsm);  // X P into S2, then back to X
     for (int e = threadIdx.x; e < J * J; e += blockDim.x) Xt[e] = S2t[e];
     __syncthreads();
   }
-  bt_gemm(J, St, 0, Xt, Wt);   // S X
-  bt_gemm(J, Xt, 1, Wt, S2t);  // X^T S X
+  bt_gemm(J, St, 0, Xt, Wt, gsm);   // S X
+  bt_gemm(J, Xt, 1, Wt, S2t, gsm);  // X^T S X
 }
 
 // After the float64 Jacobi (W = its eigenvectors of S2, sorted with their
@@ -466,10 +529,11 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_presolve(const BtTensor *__re
 // entry of a column positive, the lowest row on ties).
 __global__ void __launch_bounds__(kBtThreads) k_bt_backsolve(const BtTensor *__restrict__ Tn, const double *__restrict__ X,
                                                              const double *__restrict__ W, double *__restrict__ V) {
+  extern __shared__ __align__(16) double gsm[];
   const int t = blockIdx.x, J = (int)Tn[t].J;
   const int64_t o = (int64_t)t * kBtMaxJ * kBtMaxJ;
   double *Vt = V + o;
-  bt_gemm(J, X + o, 0, W + o, Vt);
+  bt_gemm(J, X + o, 0, W + o, Vt, gsm);
   for (int r = threadIdx.x; r < J; r += blockDim.x) {
     double *col = Vt + (int64_t)J * r;
     double best = -1.0;
@@ -566,7 +630,7 @@ int bt_run_mode(const BtArena &a, int count, int N, int k, int64_t kc, int cap, 
     if (n > 0)
       TK_CHECK(launch_jacobi32_batched(a.Sp, Jk, a.Xp, n, 32 * (c + 1), s, a.cidx + a.coff[k][c], kBtEigThreads));
   }
-  k_bt_presolve<<<count, kBtThreads, 0, s>>>(a.T, a.S, a.X, a.W, a.S2);
+  k_bt_presolve<<<count, kBtThreads, kGemmSmem, s>>>(a.T, a.S, a.X, a.W, a.S2);
   TK_LAUNCHED();
   for (int c = 0; c < kBtClasses; ++c) {
     const int n = a.coff[k][c + 1] - a.coff[k][c];
@@ -574,7 +638,7 @@ int bt_run_mode(const BtArena &a, int count, int N, int k, int64_t kc, int cap, 
       TK_CHECK(launch_eig_batched(a.S2p, Jk, a.lamp + (int64_t)k * count, a.Wp, a.info + (int64_t)k * 4 * count, n,
                                   32 * (c + 1), s, a.cidx + a.coff[k][c], kBtEigThreads, a.budget));
   }
-  k_bt_backsolve<<<count, kBtThreads, 0, s>>>(a.T, a.X, a.W, a.V + (int64_t)k * count * kBtMaxJ * kBtMaxJ);
+  k_bt_backsolve<<<count, kBtThreads, kGemmSmem, s>>>(a.T, a.X, a.W, a.V + (int64_t)k * count * kBtMaxJ * kBtMaxJ);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, 0.0, 4);
   if (prof) prof->begin(TUCKER_PHASE_RANK);
@@ -737,6 +801,8 @@ int bt_impl(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, i
   const size_t ttm_smem = (size_t)maxJ * ((maxJ + 3) & ~3) * sizeof(double);
   TK_CUDA(cudaFuncSetAttribute(k_bt_ttm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_smem));
   TK_CUDA(cudaFuncSetAttribute(k_bt_ttm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_smem));
+  TK_CUDA(cudaFuncSetAttribute(k_bt_presolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
+  TK_CUDA(cudaFuncSetAttribute(k_bt_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
   const double eps2_over_n = eps > 0.0 ? eps * eps / N : 0.0;
 
   // autotuner: columns per item and persistent grid, timed on the first mode's Gram
