@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   __shared__ int ref[kRows];
   __shared__ uint32_t tmem_slot;
   __shared__ int stop;
-  __shared__ int n_issued;  // copies issued so far (thread 0, then thread 32)
+  __shared__ int n_issued;  // copies issued so far (the group leaders, atomically)
   // offsets from dsmem keep the shared address space visible (shared loads and stores)
   unsigned char *ring = dsmem + ((1024u - (smem_addr(dsmem) & 1023u)) & 1023u);
   unsigned char *stages = ring + kRing * kRawBytes;
@@ -1002,6 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&mma_done[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     stop = 0;
+    n_issued = 0;
   }
   cta_row_ref(Etab, J, r0, Jb, g0, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
   // exponents of the group starting at chunk ch go to buffer (ch / kDrainChunks) & 1
@@ -1020,7 +1021,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   const uint32_t tmem = tmem_slot;
 
   // chunk ch -> slot ch % kRing as the box at (row 0, column c_begin + 32 ch)
-  // (thread 0 for the first ring, then thread 32: the MMAs are thread 0's)
+  // (thread 0 for the first ring, then the leader of the group that converts
+  // the chunk the slot held)
   auto issue_copy = [&](int ch) {
     const int slot = ch % kRing;
     const uint32_t bar = smem_addr(&raw_full[slot]);
@@ -1036,10 +1038,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
   if (tid == 0) {
     int c = 0;
     for (; c < kRing && c < nchunks; ++c) issue_copy(c);
-    n_issued = c;  // read on the error path after the barriers that follow
+    atomicMax(&n_issued, c);  // the leaders raise it too; read on the error path
   }
 
-  const int row = tid & (kRows - 1), kg = tid >> 7;       // converter role
+  // converter role: two groups of 8 warps take alternate chunks (group grp the
+  // chunks with ch & 1 == grp, into digit stage grp); thread (row, 16-column
+  // half kh of the chunk); gtid == 0 is the group's leader
+  const int grp = warp >> 3, gtid = tid & 255;
+  const int row = gtid & (kRows - 1), kh = gtid >> 7;
   const int q = warp & 3, cb = warp >> 2;                  // drain role: TMEM lanes 32 q.., columns 32 cb..
   const int drow = 32 * q + lane;
   const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cb);
@@ -1047,7 +1053,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
 #pragma unroll
   for (int e = 0; e < kAccPerThread; ++e) H[e] = Lo[e] = 0.f;
 
+  bool bad = false;   // this thread met a failed (expired) wait
+  bool halt = false;  // some thread did: every thread stops at the same drain barrier
   // fold the group's four levels into the double-float registers (warp-uniform `ok`)
+  // every MMA up to chunk `last` complete: chunk c's commit completes phase
+  // c >> 1 of mma_done[c & 1].  A thread waits first on its own group's stage
+  // (whose every phase it has waited on in turn) for its group's last chunk,
+  // which implies all earlier chunks (a leader issues only after the previous
+  // chunk completed), so the other stage's barrier is at most one phase
+  // behind the one awaited next.
+  auto all_done = [&](int last) -> bool {
+    if (bad) return false;
+    const int mine = (last & 1) == grp ? last : last - 1;
+    if (mine >= 0 && !mbar_wait(smem_addr(&mma_done[mine & 1]), (uint32_t)(mine >> 1) & 1u)) return false;
+    if (mine != last && !mbar_wait(smem_addr(&mma_done[last & 1]), (uint32_t)(last >> 1) & 1u)) return false;
+    return true;
+  };
   auto drain = [&](int gi, bool ok) {
     if (ok) {  // warp-uniform, so the .sync.aligned loads below never diverge
       fence_after();
@@ -1066,21 +1087,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
         }
       }
     } else {
-      stop = 1;
+      bad = true;
     }
     fence_before();
-    __syncthreads();
+    // the column group's one block barrier; a failed wait anywhere stops every thread here
+    if (__syncthreads_or(bad ? 1 : 0)) halt = true;
   };
 
   // Chunks go four at a time (the ring depth), so slot, stage and every
   // mbarrier parity below are compile-time constants: chunk ch0 + u uses slot
-  // u, digit stage u & 1, the ring phase (ch0 / 4) & 1 and, for the stage,
-  // commit number (ch0 + u) >> 1 (parity (u >> 1) & 1, as ch0 / 2 is even).
-  // Groups are 16 chunks, so a group starts only at u == 0 and ends at u == 3
-  // (or at the last chunk, drained after the loop).
+  // u, digit stage u & 1 (converter group u & 1), the ring phase (ch0 / 4) & 1
+  // and, for the stage, commit number (ch0 + u) >> 1 (parity (u >> 1) & 1, as
+  // ch0 / 2 is even).  A group converts its chunk, meets at its own named
+  // barrier, and its leader waits for the other group's previous chunk's MMAs
+  // (so the MMAs stay in chunk order in one accumulator stream), refills the
+  // slot and issues the chunk's MMAs; meanwhile the other group converts the
+  // next chunk.  The one block barrier is the drain's, once per 512-column
+  // group (16 chunks: a column group starts only at u == 0 and ends at u == 3,
+  // or at the last chunk, drained after the loop).  After a failed wait a
+  // thread skips its work but keeps its barriers, so every thread reaches
+  // every drain barrier; the failure stops all of them there.
   int cvt = 0, last_committed = -1;
   bool tail_drain = false;
-  for (int ch0 = 0; ch0 < nchunks && !stop; ch0 += kRing) {
+  for (int ch0 = 0; ch0 < nchunks && !halt; ch0 += kRing) {
     const uint32_t ring_par = (uint32_t)(ch0 / kRing) & 1u;
 #pragma unroll
     for (int u = 0; u < kRing; ++u) {
@@ -1089,57 +1118,67 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
       const int in_group = ch % kDrainChunks, gi = ch / kDrainChunks;
       if (u == 0 && in_group == 0) {
         cvt = scaled_float_param<T>(rowexp[gi & 1][row]);
-        // the next group's exponents go to the other buffer, read after a later barrier
+        // the next column group's exponents go to the other buffer, read after the drain barrier
         if (ch + kDrainChunks < nchunks) load_exps(ch + kDrainChunks);
       }
-      bool ok = mbar_wait(smem_addr(&raw_full[u]), ring_par);
-      if (ok && ch >= 2) ok = mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)(((u + 2) >> 1) & 1));
-      if (ok)
-        if constexpr (kOct) convert_oct(ring + u * kRawBytes, row, kg, cvt, stages + (u & 1) * kStageBytes);
-        else convert_bulk<T>(reinterpret_cast<const T *>(ring + u * kRawBytes), row, kg, cvt, stages + (u & 1) * kStageBytes);
-      else
-        stop = 1;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (stop) break;
-      if (tid == 32 && ch + kRing < nchunks) {  // slot u has been read by every thread
-        issue_copy(ch + kRing);
-        n_issued = ch + kRing + 1;
-      }
-      if (tid == 0) {
-        fence_after();
-        const uint32_t base = smem_addr(stages + (u & 1) * kStageBytes);
+      if ((u & 1) == grp) {
+        if (!bad) bad = !mbar_wait(smem_addr(&raw_full[u]), ring_par);
+        if (!bad && ch >= 2) bad = !mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)(((u + 2) >> 1) & 1));
+        if (!bad) {
 #pragma unroll
-        for (int k = 0; k < kChunk / 16; ++k) {
-          const uint32_t acc = (u == 0 && in_group == 0 && k == 0) ? 0u : 1u;
-          const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * k, 128, kSbo);
-          const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * k, 128, kSbo);
-          const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * k, 128, kSbo);
-          const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * k, 128, kSbo);
-          mma_bf16(tmem + 0, a1, a1, kIdesc256, acc);
-          mma_bf16(tmem + 256, a2, a2, kIdesc256, acc);
-          mma_bf16(tmem + 256, a1, a3x2, kIdesc, 1u);
-          mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
+          for (int h = 0; h < 2; ++h) {
+            const int kg = 2 * kh + h;
+            if constexpr (kOct) convert_oct(ring + u * kRawBytes, row, kg, cvt, stages + (u & 1) * kStageBytes);
+            else convert_bulk<T>(reinterpret_cast<const T *>(ring + u * kRawBytes), row, kg, cvt, stages + (u & 1) * kStageBytes);
+          }
         }
-        mma_commit(smem_addr(&mma_done[u & 1]));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("bar.sync %0, 256;" ::"r"(1 + grp) : "memory");
+        if (gtid == 0 && !bad) {
+          // the other group's chunk ch - 1 goes first in the accumulators
+          if (ch >= 1) bad = !mbar_wait(smem_addr(&mma_done[(u + 1) & 1]), (uint32_t)(((u + 3) >> 1) & 1));
+          if (!bad) {
+            if (ch + kRing < nchunks) {  // slot u has been read by this group
+              issue_copy(ch + kRing);
+              atomicMax(&n_issued, ch + kRing + 1);
+            }
+            fence_after();
+            const uint32_t base = smem_addr(stages + (u & 1) * kStageBytes);
+#pragma unroll
+            for (int k = 0; k < kChunk / 16; ++k) {
+              const uint32_t acc = (u == 0 && in_group == 0 && k == 0) ? 0u : 1u;
+              const uint64_t a1 = smem_desc(base + 0 * kTileBytes + 256 * k, 128, kSbo);
+              const uint64_t a2 = smem_desc(base + 1 * kTileBytes + 256 * k, 128, kSbo);
+              const uint64_t a3x2 = smem_desc(base + 2 * kTileBytes + 256 * k, 128, kSbo);
+              const uint64_t a3q = smem_desc(base + 3 * kTileBytes + 256 * k, 128, kSbo);
+              mma_bf16(tmem + 0, a1, a1, kIdesc256, acc);
+              mma_bf16(tmem + 256, a2, a2, kIdesc256, acc);
+              mma_bf16(tmem + 256, a1, a3x2, kIdesc, 1u);
+              mma_bf16(tmem + 384, a3x2, a3q, kIdesc, 1u);
+            }
+            mma_commit(smem_addr(&mma_done[u & 1]));
+            last_committed = ch;
+          }
+        }
       }
-      last_committed = ch;
       if (u == kRing - 1 && in_group == kDrainChunks - 1) {
-        drain(gi, __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[u & 1]), (uint32_t)((u >> 1) & 1))));
-        if (stop) break;
+        drain(gi, __all_sync(0xffffffffu, all_done(ch)));
+        if (halt) break;
       } else if (ch == nchunks - 1) {
         tail_drain = true;
       }
     }
   }
-  if (tail_drain && !stop) {
+  if (tail_drain && !halt) {
     const int ch = nchunks - 1;
-    drain(ch / kDrainChunks,
-          __all_sync(0xffffffffu, mbar_wait(smem_addr(&mma_done[ch & 1]), (uint32_t)(ch >> 1) & 1u)));
+    drain(ch / kDrainChunks, __all_sync(0xffffffffu, all_done(ch)));
   }
+  if (halt && tid == 0) stop = 1;
+  __syncthreads();
+  if (stop && gtid == 0 && last_committed >= 0)  // each leader: its own MMAs finish before TMEM goes
+    mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)(last_committed >> 1) & 1u);
   if (stop && tid == 0) {
-    // let our own MMAs and bulk copies finish (bounded) before TMEM and shared memory go
-    if (last_committed >= 0) mbar_wait(smem_addr(&mma_done[last_committed & 1]), (uint32_t)(last_committed >> 1) & 1u);
+    // let the bulk copies finish (bounded) before shared memory goes
     const int issued = n_issued;
     for (int c = max(0, issued - kRing); c < issued; ++c)
       mbar_wait(smem_addr(&raw_full[c % kRing]), (uint32_t)(c / kRing) & 1u);
