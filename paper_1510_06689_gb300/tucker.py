@@ -164,6 +164,13 @@ def _copy_out(ptr, n):
     return torch.as_tensor(_DevArray(ptr, (n,)), device="cuda").clone()
 
 
+def _doubles(ptr, count):
+    """`count` doubles at a library pointer as a list (one slice, not per-element indexing)."""
+    if not ptr or count <= 0:
+        return []
+    return ptr[:count]
+
+
 class Result:
     """An ST-HOSVD result (core, factors, ranks, eigenvalues) owned by the library."""
 
@@ -179,7 +186,7 @@ class Result:
         self.norm2 = raw.norm2_x
         self.threshold = raw.threshold
         self.on_host = bool(raw.on_host)
-        self.eigvals = [[raw.eigvals[i][k] for k in range(self.dims[i])] for i in range(n)]
+        self.eigvals = [_doubles(raw.eigvals[i], self.dims[i]) for i in range(n)]
         self.eig_paths = tuple(EIG_PATHS[raw.eig_path[i]] for i in range(n))
         self.eig_resolved = tuple(raw.eig_resolved[i] for i in range(n))
 
