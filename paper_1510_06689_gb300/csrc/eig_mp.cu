@@ -1528,9 +1528,10 @@ __global__ void __launch_bounds__(kJ32ClThreads)
           q = tmp;
         }
         float c = 1.f, sv = 0.f, tt = 0.f;
-        const float b = __ldcg(S + (int64_t)p * m + q);
+        // the three entries in one round trip
+        const float b = __ldcg(S + (int64_t)p * m + q), a = __ldcg(S + (int64_t)p * m + p),
+                    d = __ldcg(S + (int64_t)q * m + q);
         if (fabsf(b) > tol) {
-          const float a = __ldcg(S + (int64_t)p * m + p), d = __ldcg(S + (int64_t)q * m + q);
           const float tau = __fdividef(d - a, 2.f * b);
           const float at = fabsf(tau);
           const float h = fmaf(tau, tau, 1.f);
@@ -1544,31 +1545,67 @@ __global__ void __launch_bounds__(kJ32ClThreads)
       // every CTA has read the entries its rotations come from before any CTA
       // overwrites them (the diagonal blocks' owners zero s_pq)
       cl.sync();
+      // Every entry of S belongs to one 2 x 2 block and every V column pair to
+      // one unit, each applied by one thread: all of this thread's loads go
+      // first (one round trip to L2), then the updates and stores.
+      float4 xs[kJ32ClBlocksPerThread];
+      bool live[kJ32ClBlocksPerThread];
 #pragma unroll
       for (int k = 0; k < kJ32ClBlocksPerThread; ++k) {
         const int pq = myblk[k];
+        live[k] = false;
+        xs[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pq < 0) continue;
         const int P = pq & 0xFFFF, Q = pq >> 16;
-        const float4 rP = rot[P];
+        const float4 rP = rot[P], rQ = rot[Q];
+        const int kP = __float_as_int(rP.w), kQ = __float_as_int(rQ.w);
+        const int64_t p1 = kP & 0xFFFF, q1 = kP >> 16, p2 = kQ & 0xFFFF, q2 = kQ >> 16;
         if (P == Q) {
           if (rP.y == 0.f) continue;
-          const int kk = __float_as_int(rP.w), p1 = kk & 0xFFFF, q1 = kk >> 16;
-          float *spq = S + (int64_t)p1 * m + q1;
-          const float b = __ldcg(spq);
-          __stcg(S + (int64_t)p1 * m + p1, __ldcg(S + (int64_t)p1 * m + p1) - rP.z * b);
-          __stcg(S + (int64_t)q1 * m + q1, __ldcg(S + (int64_t)q1 * m + q1) + rP.z * b);
-          __stcg(spq, 0.f);
-          __stcg(S + (int64_t)q1 * m + p1, 0.f);
+          live[k] = true;  // s_pq, s_pp, s_qq
+          xs[k] = make_float4(__ldcg(S + p1 * m + q1), __ldcg(S + p1 * m + p1), __ldcg(S + q1 * m + q1), 0.f);
+        } else {
+          if (rP.y == 0.f && rQ.y == 0.f) continue;
+          live[k] = true;
+          xs[k] = make_float4(__ldcg(S + p1 * m + p2), __ldcg(S + p1 * m + q2), __ldcg(S + q1 * m + p2),
+                              __ldcg(S + q1 * m + q2));
+        }
+      }
+      const int nq = m / 4;  // V's column pairs: unit u = (pair t, row quad r4)
+      float4 va[kJ32ClVPerThread + 1], vb[kJ32ClVPerThread + 1];
+#pragma unroll
+      for (int k = 0; k <= kJ32ClVPerThread; ++k) {
+        const int u = gt + k * gstride;
+        va[k] = vb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u >= np * nq) continue;
+        const int t = u / nq, r4 = u - t * nq;
+        const float4 r = rot[t];
+        if (r.y == 0.f) continue;
+        const int kk = __float_as_int(r.w);
+        va[k] = __ldcg(reinterpret_cast<const float4 *>(V + (int64_t)(kk & 0xFFFF) * m) + r4);
+        vb[k] = __ldcg(reinterpret_cast<const float4 *>(V + (int64_t)(kk >> 16) * m) + r4);
+      }
+#pragma unroll
+      for (int k = 0; k < kJ32ClBlocksPerThread; ++k) {
+        if (!live[k]) continue;
+        const int pq = myblk[k];
+        const int P = pq & 0xFFFF, Q = pq >> 16;
+        const float4 rP = rot[P];
+        const int kP = __float_as_int(rP.w);
+        const int64_t p1 = kP & 0xFFFF, q1 = kP >> 16;
+        if (P == Q) {
+          const float b = xs[k].x;
+          __stcg(S + p1 * m + p1, xs[k].y - rP.z * b);
+          __stcg(S + q1 * m + q1, xs[k].z + rP.z * b);
+          __stcg(S + p1 * m + q1, 0.f);
+          __stcg(S + q1 * m + p1, 0.f);
           continue;
         }
         const float4 rQ = rot[Q];
-        const float s1 = rP.y, s2 = rQ.y;
-        if (s1 == 0.f && s2 == 0.f) continue;
-        const float c1 = rP.x, c2 = rQ.x;
-        const int kP = __float_as_int(rP.w), kQ = __float_as_int(rQ.w);
-        const int64_t p1 = kP & 0xFFFF, q1 = kP >> 16, p2 = kQ & 0xFFFF, q2 = kQ >> 16;
-        const float x11 = __ldcg(S + p1 * m + p2), x12 = __ldcg(S + p1 * m + q2);
-        const float x21 = __ldcg(S + q1 * m + p2), x22 = __ldcg(S + q1 * m + q2);
+        const float s1 = rP.y, s2 = rQ.y, c1 = rP.x, c2 = rQ.x;
+        const int kQ = __float_as_int(rQ.w);
+        const int64_t p2 = kQ & 0xFFFF, q2 = kQ >> 16;
+        const float x11 = xs[k].x, x12 = xs[k].y, x21 = xs[k].z, x22 = xs[k].w;
         const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
         const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
         const float z11 = y11 * c2 - y12 * s2, z12 = y11 * s2 + y12 * c2;
@@ -1582,8 +1619,6 @@ __global__ void __launch_bounds__(kJ32ClThreads)
         __stcg(S + q1 * m + q2, z22);
         __stcg(S + q2 * m + q1, z22);
       }
-      // V's column pairs: unit u = (pair t, row quad r4)
-      const int nq = m / 4;
 #pragma unroll
       for (int k = 0; k <= kJ32ClVPerThread; ++k) {
         const int u = gt + k * gstride;
@@ -1595,7 +1630,7 @@ __global__ void __launch_bounds__(kJ32ClThreads)
         const int kk = __float_as_int(r.w);
         float4 *vp = reinterpret_cast<float4 *>(V + (int64_t)(kk & 0xFFFF) * m) + r4;
         float4 *vq = reinterpret_cast<float4 *>(V + (int64_t)(kk >> 16) * m) + r4;
-        const float4 a = __ldcg(vp), b = __ldcg(vq);
+        const float4 a = va[k], b = vb[k];
         __stcg(vp, make_float4(c * a.x - sv * b.x, c * a.y - sv * b.y, c * a.z - sv * b.z, c * a.w - sv * b.w));
         __stcg(vq, make_float4(sv * a.x + c * b.x, sv * a.y + c * b.y, sv * a.z + c * b.z, sv * a.w + c * b.w));
       }
