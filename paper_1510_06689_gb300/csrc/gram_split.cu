@@ -803,14 +803,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split(const T *__restrict_
 // ---------------------------------------------------------------------------
 // L == 1 with 16-byte column strides (J sizeof(T) a multiple of 16, Y 16-byte
 // aligned): the unfolding is a 2-D tensor of K columns of J contiguous
-// entries.  Thread 0 has the tensor-memory accelerator copy each chunk as one
-// 128 x 32 box (cp.async.bulk.tensor; rows >= J and columns >= K arrive as
-// zeros) into a ring of kRing shared-memory slots, completion counted in bytes
-// on the slot's mbarrier: the loads in flight are not bounded by registers,
-// every shared load of the conversion has a constant offset and the ragged
-// edges need no predicates.
-// Every thread converts row tid % 128, columns 8 (tid / 128) .. + 7 of a
-// chunk from shared memory:
+// entries.  The tensor-memory accelerator copies each chunk as one 128 x 32
+// box (cp.async.bulk.tensor; rows >= J and columns >= K arrive as zeros) into
+// a ring of kRing shared-memory slots, completion counted in bytes on the
+// slot's mbarrier: the loads in flight are not bounded by registers, every
+// shared load of the conversion has a constant offset and the ragged edges
+// need no predicates.  The 16 warps form two groups of eight that convert
+// alternate chunks into their own digit stage; a group's leader refills the
+// slot its group has read and issues the chunk's MMAs once the other group's
+// previous chunk has completed (one in-order accumulator stream).
+// A thread converts row t % 128 and 16 columns (t / 128 of the halves, t the
+// index within its group) of its group's chunks from shared memory:
 //   * f = |y| 2^(21 - E) is built as a float straight from the bits (the
 //     exponent field rebased by one integer subtraction clamped at zero, the
 //     significand cut to 24 bits with the last bit set, i.e. rounded to odd,
