@@ -45,6 +45,7 @@ namespace {
 constexpr int kBtMaxJ = 128;     // every mode of a batched tensor (the one-CTA Jacobi's limit)
 constexpr int kBtThreads = 256;
 constexpr int kBtStage = 32;     // columns staged in shared memory at a time
+constexpr size_t kBtGramSmem = (size_t)2 * kBtStage * kBtMaxJ * sizeof(double);
 static_assert(kBtThreads == 256 && kBtStage == 32 && kBtMaxJ <= 128,
               "the stage loader's fixed trip counts assume 8 warps, 32 columns and J <= 128");
 constexpr int kBtMaxModes = TUCKER_MAX_MODES;
@@ -188,6 +189,59 @@ __device__ __forceinline__ void bt_load_stage(const T *__restrict__ y, int64_t L
   __syncthreads();
 }
 
+// The same stage in two halves, so that the next stage's loads are in flight
+// while the current one is used: bt_fetch loads a thread's 16 entries of the
+// stage at columns [c0, c1) into registers (the layout of bt_load_stage),
+// bt_put stores them into Ys (row stride ld).
+template <typename T>
+__device__ __forceinline__ void bt_fetch(const T *__restrict__ y, int64_t L, int J, int64_t c0, int64_t c1,
+                                         double (&v)[16]) {
+  const int tid = threadIdx.x;
+  if (L == 1) {
+    const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t c = c0 + w + 8 * q;
+      const bool ok = c < c1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = lane + 32 * i;
+        v[4 * q + i] = (ok && j < J) ? (double)y[c * (int64_t)J + j] : 0.0;
+      }
+    }
+  } else {
+    const int kk = tid & (kBtStage - 1), j0 = tid / kBtStage;
+    const int64_t c = c0 + kk;
+    const bool ok = c < c1;
+    int64_t base = 0;
+    if (ok) {
+      const int64_t b = c / L;
+      base = (c - b * L) + L * (int64_t)J * b;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int j = j0 + 8 * i;
+      v[i] = (ok && j < J) ? (double)y[base + L * (int64_t)j] : 0.0;
+    }
+  }
+}
+__device__ __forceinline__ void bt_put(int64_t L, int ld, const double (&v)[16], double *Ys) {
+  const int tid = threadIdx.x;
+  if (L == 1) {
+    const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (lane + 32 * i < ld) Ys[(w + 8 * q) * ld + lane + 32 * i] = v[4 * q + i];
+  } else {
+    const int kk = tid & (kBtStage - 1), j0 = tid / kBtStage;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (j0 + 8 * i < ld) Ys[kk * ld + j0 + 8 * i] = v[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // gram: persistent CTAs over the items.  Thread x owns the 4 x 4 micro-tiles
 // x, x + 256, x + 512 of the upper triangle (at most 528 for J <= 128) and
@@ -200,8 +254,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBtThreads) k_bt_gram(const BtTensor *__restrict__ Tn, const BtItem *__restrict__ items,
                                                         const int *__restrict__ nitems, const double *__restrict__ ybuf,
                                                         int first_mode, double *__restrict__ partials) {
-  __shared__ __align__(16) double Ys[kBtStage * kBtMaxJ];
-  __shared__ int64_t colbase[kBtStage];
+  extern __shared__ __align__(16) double gram_sm[];  // two stages (kBtGramSmem): one used, the next being filled
   const int n = *nitems, tid = threadIdx.x;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const BtItem item = items[it];
@@ -226,8 +279,18 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_gram(const BtTensor *__restri
     for (int u = 0; u < 3; ++u)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.0;
-    for (int64_t c0 = item.c0; c0 < item.c1; c0 += kBtStage) {
-      bt_load_stage<T>(y, d.L, J, Jp, c0, min(item.c1, c0 + kBtStage), Ys, colbase);
+    // stage st is stored into buffer st & 1 after the barrier that ends the
+    // use of stage st - 2 there (every thread has passed stage st - 1's barrier)
+    double v[16];
+    bt_fetch<T>(y, d.L, J, item.c0, min(item.c1, item.c0 + kBtStage), v);
+    __syncthreads();  // the previous item's stages are read out
+    int st = 0;
+    for (int64_t c0 = item.c0; c0 < item.c1; c0 += kBtStage, ++st) {
+      double *Ys = gram_sm + (st & 1) * (kBtStage * kBtMaxJ);
+      bt_put(d.L, Jp, v, Ys);
+      __syncthreads();
+      if (c0 + kBtStage < item.c1)  // the next stage's loads run under this stage's FMAs
+        bt_fetch<T>(y, d.L, J, c0 + kBtStage, min(item.c1, c0 + 2 * kBtStage), v);
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         if (ma[u] < 0) continue;
@@ -244,7 +307,6 @@ __global__ void __launch_bounds__(kBtThreads) k_bt_gram(const BtTensor *__restri
             for (int c = 0; c < 4; ++c) acc[u][4 * r + c] = fma(av[r], bv[c], acc[u][4 * r + c]);
         }
       }
-      __syncthreads();  // the stage is read out before the next one is loaded
     }
     double *P = partials + item.poff;
 #pragma unroll
@@ -612,8 +674,8 @@ int bt_run_mode(const BtArena &a, int count, int N, int k, int64_t kc, int cap, 
   k_bt_plan<<<1, 1024, 0, s>>>(a.T, count, N, k, kc, a.items, cap, a.nitems, a.overflow);
   TK_LAUNCHED();
   const double *yin = k == 0 ? nullptr : a.ybuf[(k - 1) & 1];
-  if (k == 0) k_bt_gram<T><<<grid, kBtThreads, 0, s>>>(a.T, a.items, a.nitems, yin, 1, a.partials);
-  else k_bt_gram<double><<<grid, kBtThreads, 0, s>>>(a.T, a.items, a.nitems, yin, 0, a.partials);
+  if (k == 0) k_bt_gram<T><<<grid, kBtThreads, kBtGramSmem, s>>>(a.T, a.items, a.nitems, yin, 1, a.partials);
+  else k_bt_gram<double><<<grid, kBtThreads, kBtGramSmem, s>>>(a.T, a.items, a.nitems, yin, 0, a.partials);
   TK_LAUNCHED();
   if (prof) prof->end(0.0, 0.0, 2);
   if (prof) prof->begin(TUCKER_PHASE_GRAM_REDUCE);
@@ -801,6 +863,8 @@ int bt_impl(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, i
   const size_t ttm_smem = (size_t)maxJ * ((maxJ + 3) & ~3) * sizeof(double);
   TK_CUDA(cudaFuncSetAttribute(k_bt_ttm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_smem));
   TK_CUDA(cudaFuncSetAttribute(k_bt_ttm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_smem));
+  TK_CUDA(cudaFuncSetAttribute(k_bt_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBtGramSmem));
+  TK_CUDA(cudaFuncSetAttribute(k_bt_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBtGramSmem));
   TK_CUDA(cudaFuncSetAttribute(k_bt_presolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
   TK_CUDA(cudaFuncSetAttribute(k_bt_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
   const double eps2_over_n = eps > 0.0 ? eps * eps / N : 0.0;
@@ -826,7 +890,7 @@ int bt_impl(const void *const *X, tucker_dtype dt, const int64_t *dims, int N, i
         for (int rep = 0; rep < 2; ++rep) {  // the second run is timed
           cudaEventRecord(e0, s);
           k_bt_plan<<<1, 1024, 0, s>>>(a.T, count, N, 0, kc, a.items, (int)cap, a.nitems, a.overflow);
-          k_bt_gram<T><<<grid, kBtThreads, 0, s>>>(a.T, a.items, a.nitems, nullptr, 1, a.partials);
+          k_bt_gram<T><<<grid, kBtThreads, kBtGramSmem, s>>>(a.T, a.items, a.nitems, nullptr, 1, a.partials);
           cudaEventRecord(e1, s);
           bump_launches(2);
           TK_CUDA(cudaGetLastError());
