@@ -335,6 +335,13 @@ def test_ttm_split_f32_and_limits(gpu_lib):
     ((40, 36, 32, 12, 10), (12, 12, 12, 6, 4), 1e-5, "f64"),
     ((40, 36, 32, 12, 10), (12, 12, 12, 6, 4), 1e-3, "f64"),
     ((30, 28, 26, 10, 8), (10, 10, 10, 5, 3), 1e-4, "f32"),
+    # first modes whose columns the exponent pass reads as contiguous pairs and
+    # takes the mode product's column exponents from: J < 64 (lane by lane),
+    # J = 64 and 128 (warps over whole columns), float64 and float32
+    ((32, 40, 30), (8, 6, 5), 1e-3, "f64"),
+    ((16, 48, 40), (5, 8, 6), 1e-3, "f32"),
+    ((64, 24, 20), (8, 6, 5), 1e-3, "f32"),
+    ((128, 30, 20), (10, 6, 5), 1e-3, "f32"),
 ])
 def test_sthosvd_split_matches_oracle_ranks_and_error(gpu_lib, dims, ranks, eps, dtype):
     """Identical ranks; achieved error within 1e-3 eps of the oracle's (stated tolerance)."""
