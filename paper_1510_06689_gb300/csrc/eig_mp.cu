@@ -1069,9 +1069,9 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
 // of k_eig32_tri with a matrix too large for a full float32 copy in shared
 // memory.  The lower triangle is packed by columns in shared memory (column
 // j holds rows j..n-1 from offset j n - j (j - 1) / 2: 129 KB at n = 256);
-// the eigenvector passes use two n x n float arrays in global memory (they
-// stay in L2), Zg[k n + c] (row k of vector c) and Lg (the L factors of the
-// inverse iteration).
+// the eigenvector passes use two n x tri32_ld(n) float arrays in global
+// memory (they stay in L2), Zg[k ld + c] (row k of vector c) and Lg (the L
+// factors of the inverse iteration, then the reflectors of steps 4 and 5).
 //   1. Householder tridiagonalization one reflector at a time: the reflector
 //      of column k (v(0) = 1, beta = -sign(alpha) ||x||, tau = (beta -
 //      alpha) / beta), p = tau A22 v (four threads per row of the packed
@@ -1085,16 +1085,31 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_eig32_tri(const double *__re
 //      Gram-Schmidt, even twice, loses orthogonality on strongly graded
 //      spectra, where many vectors come out nearly parallel.)
 //   5. X = Q1 Q by the reflectors from the last to the first.
-// Every reflector is LAPACK's larfg with the scaled norm of tri_reflect.
+// Steps 4 and 5 go kNb reflectors at a time in compact WY form, as in
+// k_eig32_tri (a warp factors each QR panel in registers; a block of
+// reflectors is three register-tiled passes and three barriers instead of
+// kNb passes and 2 kNb barriers).  The tridiagonalization's reflectors are
+// LAPACK's larfg with the scaled norm of tri_reflect.
 // Writes X (float64, columns in descending eigenvalue order).
 // ---------------------------------------------------------------------------
 constexpr int kW32Threads = 1024;
 
 __host__ __device__ __forceinline__ int packed_col(int n, int j) { return j * n - j * (j - 1) / 2; }
 
-// floats: the packed triangle (padded to 16 bytes), d, e, e2, tau, lam, pv,
-// zj (n each) and 4 x 256 partial sums
-size_t wide32_smem(int n) { return (size_t)(((n * (n + 1) / 2 + 3) & ~3) + 7 * n + 4 * 256) * sizeof(float); }
+// float offsets of the wide stage's shared-memory regions, each 16-byte
+// aligned: the packed triangle, 6 n-vectors, the WY partial products and the
+// T factors of the reflector blocks
+struct WideLayout {
+  int vec, part, tf, total;
+  __host__ __device__ explicit WideLayout(int n) {
+    auto up = [](int v) { return (v + 3) & ~3; };
+    vec = up(n * (n + 1) / 2);
+    part = vec + up(6 * n);
+    tf = part + 4 * kNb * kWideMaxJ;
+    total = tf + ((n + kNb - 1) / kNb) * kNb * kNb;
+  }
+};
+size_t wide32_smem(int n) { return (size_t)WideLayout(n).total * sizeof(float) + 64; }
 
 // Sum over the block of one value per thread; every thread gets the result.
 // Uses red[0..32]; callers separate consecutive uses by a barrier.
@@ -1164,13 +1179,213 @@ __device__ Refl wide_larfg(const float *x, int m, float *red) {
   return h;
 }
 
+// The compact-WY steps of k_eig32_tri for n <= kWideMaxJ, on row-major
+// matrices in global memory (L2-resident) with a row stride that is a
+// multiple of 4 (16-byte rows), by kW32Threads threads.  As apply_wy:
+// M[r0:n, c0:n] <- (I - V op(T) V^T) M[r0:n, c0:n] for the kNb reflectors in
+// columns j0.. of V, in three phases ending with barriers (part: 4 x kNb x
+// kWideMaxJ floats of shared memory).
+__device__ void apply_wy_wide(float *__restrict__ M, int ldm, int n, int r0, int c0, const float *__restrict__ V,
+                              int ldv, int j0, const float *__restrict__ T, bool trans, float *__restrict__ part) {
+  const int tid = threadIdx.x;
+  const int q0 = c0 >> 2, nq = (n + 3) >> 2;
+  {
+    const int q = q0 + (tid & 63), g = (tid >> 6) & 3, p = tid >> 8;
+    if (q < nq) {
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll 4
+      for (int r = r0 + p; r < n; r += 4) {
+        const float4 m = __ldcg(reinterpret_cast<const float4 *>(M + (int64_t)r * ldm + 4 * q));
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(V + (int64_t)r * ldv + j0 + 2 * g));
+        a0 = fma4(v.x, m, a0);
+        a1 = fma4(v.y, m, a1);
+      }
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g) * kWideMaxJ + 4 * q) = a0;
+      *reinterpret_cast<float4 *>(part + (p * kNb + 2 * g + 1) * kWideMaxJ + 4 * q) = a1;
+    }
+  }
+  __syncthreads();
+  if (tid < kWideMaxJ && tid >= 4 * q0 && tid < 4 * nq) {
+    const int c = tid;
+    float P[kNb];
+#pragma unroll
+    for (int j = 0; j < kNb; ++j)
+      P[j] = (part[j * kWideMaxJ + c] + part[(kNb + j) * kWideMaxJ + c]) +
+             (part[(2 * kNb + j) * kWideMaxJ + c] + part[(3 * kNb + j) * kWideMaxJ + c]);
+#pragma unroll
+    for (int i = 0; i < kNb; ++i) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < kNb; ++k) t = fmaf(trans ? T[k * kNb + i] : T[i * kNb + k], P[k], t);
+      part[i * kWideMaxJ + c] = t;
+    }
+  }
+  __syncthreads();
+  {
+    const int q = q0 + (tid & 63), p = tid >> 6;
+    if (q < nq) {
+      float4 P[kNb];
+#pragma unroll
+      for (int j = 0; j < kNb; ++j) P[j] = *reinterpret_cast<const float4 *>(part + j * kWideMaxJ + 4 * q);
+      const bool whole = 4 * q >= c0;
+#pragma unroll 2
+      for (int r = r0 + p; r < n; r += 16) {
+        float *dst = M + (int64_t)r * ldm + 4 * q;
+        float4 m = __ldcg(reinterpret_cast<const float4 *>(dst));
+        const float4 va = __ldcg(reinterpret_cast<const float4 *>(V + (int64_t)r * ldv + j0));
+        const float4 vb = __ldcg(reinterpret_cast<const float4 *>(V + (int64_t)r * ldv + j0 + 4));
+        m = fma4(-va.x, P[0], m);
+        m = fma4(-va.y, P[1], m);
+        m = fma4(-va.z, P[2], m);
+        m = fma4(-va.w, P[3], m);
+        m = fma4(-vb.x, P[4], m);
+        m = fma4(-vb.y, P[5], m);
+        m = fma4(-vb.z, P[6], m);
+        m = fma4(-vb.w, P[7], m);
+        if (whole) {
+          __stcg(reinterpret_cast<float4 *>(dst), m);
+        } else {  // the quad that straddles c0
+          const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (4 * q + u >= c0) __stcg(dst + u, mv[u]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// qr_panel for n <= kWideMaxJ: one warp factors columns j0 .. j0 + nbk - 1
+// (rows j0 .. n-1) of Z in registers (lane l: rows j0 + l + 32 i) and writes
+// the reflectors to W's panel columns, the taus, R's diagonal signs and the
+// panel's T factor.  No block barrier.
+__device__ void qr_panel_wide(const float *__restrict__ Z, int lz, float *__restrict__ W, int n, int j0, int nbk,
+                              int lane, float *__restrict__ qtau, float *__restrict__ sgn, float *__restrict__ T) {
+  constexpr int kR = kWideMaxJ / 32;
+  const int mrows = n - j0;
+  float P[kR][kNb];
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    const int row = lane + 32 * i;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (row < mrows) {
+      a = __ldcg(reinterpret_cast<const float4 *>(Z + (int64_t)(j0 + row) * lz + j0));
+      b = __ldcg(reinterpret_cast<const float4 *>(Z + (int64_t)(j0 + row) * lz + j0 + 4));
+    }
+    P[i][0] = a.x, P[i][1] = a.y, P[i][2] = a.z, P[i][3] = a.w;
+    P[i][4] = b.x, P[i][5] = b.y, P[i][6] = b.z, P[i][7] = b.w;
+  }
+  float tv[kNb];
+#pragma unroll
+  for (int jj = 0; jj < kNb; ++jj) {
+    tv[jj] = 0.f;
+    if (jj >= nbk) continue;  // uniform
+    const float alpha = __shfl_sync(0xffffffffu, P[0][jj], jj);
+    float mx = 0.f, sq = 0.f;
+#pragma unroll
+    for (int i = 0; i < kR; ++i)
+      if (lane + 32 * i > jj) {
+        mx = fmaxf(mx, fabsf(P[i][jj]));
+        sq = fmaf(P[i][jj], P[i][jj], sq);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    float t = 0.f, scal = 0.f, beta = alpha;
+    if (mx > 0x1p-100f) {  // uniform
+      float nrm;
+      if (mx >= 0x1p-40f) {  // uniform
+        nrm = sqrtf(fmaf(alpha, alpha, sq));
+      } else {
+        const float sm = fmaxf(mx, fabsf(alpha)), sx = 1.f / sm;
+        float sg = 0.f;
+#pragma unroll
+        for (int i = 0; i < kR; ++i)
+          if (lane + 32 * i > jj) {
+            const float v = P[i][jj] * sx;
+            sg = fmaf(v, v, sg);
+          }
+        sg = warp_sum32(sg);
+        const float a = alpha * sx;
+        nrm = sm * sqrtf(fmaf(a, a, sg));
+      }
+      beta = alpha >= 0.f ? -nrm : nrm;
+      const float rb = __frcp_rn(beta), rd = __frcp_rn(alpha - beta);
+      t = fmaf(-alpha, rb, 1.f);
+      scal = rd;
+    }
+    tv[jj] = t;
+    if (lane == 0) {
+      qtau[j0 + jj] = t;
+      sgn[j0 + jj] = beta < 0.f ? -1.f : 1.f;
+    }
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const int row = lane + 32 * i;
+      P[i][jj] = row == jj ? 1.f : (row > jj && t != 0.f ? P[i][jj] * scal : 0.f);
+    }
+    if (t != 0.f) {
+      float dd[kNb];
+#pragma unroll
+      for (int c = 0; c < kNb; ++c) {
+        dd[c] = 0.f;
+        if (c > jj)
+#pragma unroll
+          for (int i = 0; i < kR; ++i) dd[c] = fmaf(P[i][jj], P[i][c], dd[c]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < kNb; ++c)
+          if (c > jj) dd[c] += __shfl_xor_sync(0xffffffffu, dd[c], o);
+#pragma unroll
+      for (int c = 0; c < kNb; ++c)
+        if (c > jj)
+#pragma unroll
+          for (int i = 0; i < kR; ++i) P[i][c] = fmaf(-t * dd[c], P[i][jj], P[i][c]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    const int row = lane + 32 * i;
+    if (row < mrows) {
+      __stcg(reinterpret_cast<float4 *>(W + (int64_t)(j0 + row) * lz + j0), make_float4(P[i][0], P[i][1], P[i][2], P[i][3]));
+      __stcg(reinterpret_cast<float4 *>(W + (int64_t)(j0 + row) * lz + j0 + 4), make_float4(P[i][4], P[i][5], P[i][6], P[i][7]));
+    }
+  }
+  float G[kNb * kNb];
+#pragma unroll
+  for (int k = 0; k < kNb; ++k)
+#pragma unroll
+    for (int l = 0; l < kNb; ++l) {
+      G[k * kNb + l] = 0.f;
+      if (k < l)
+#pragma unroll
+        for (int i = 0; i < kR; ++i) G[k * kNb + l] = fmaf(P[i][k], P[i][l], G[k * kNb + l]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < kNb; ++k)
+#pragma unroll
+      for (int l = k + 1; l < kNb; ++l) G[k * kNb + l] += __shfl_xor_sync(0xffffffffu, G[k * kNb + l], o);
+  if (lane < kNb) wy_t_column(G, tv, lane, T);
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__restrict__ A, int lda, int n,
                                                              double *__restrict__ X, int ldx, float *Zg,
                                                              float *Lg) {
   extern __shared__ __align__(16) float smw[];
   float *Ap = smw;
-  float *d = smw + ((n * (n + 1) / 2 + 3) & ~3), *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n,
-        *pv = lam + n, *zj = pv + n, *ps = zj + n;
+  const WideLayout lay(n);
+  float *d = smw + lay.vec, *e = d + n, *e2 = e + n, *tau = e2 + n, *lam = tau + n, *pv = lam + n;
+  float *part = smw + lay.part;  // WY partial products (4 x kNb x kWideMaxJ)
+  float *Tf = smw + lay.tf;      // T factors of the reflector blocks
+  const int lz = tri32_ld(n);    // row stride of Zg and Lg
   __shared__ float red[33];
   __shared__ float sc[4];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -1320,113 +1535,82 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__r
     for (int k = 0; k + 1 < n; ++k) {
       if (fabsf(D) < piv) D = D < 0.f ? -piv : piv;
       const float L = __fdividef(e[k], D);
-      Lg[k * n + c] = L;
+      Lg[k * lz + c] = L;
       D = d[k + 1] - s - L * e[k];
     }
     for (int pass = 0; pass < 2; ++pass) {
       float Dk = d[0] - s, y = 0.f;
       for (int k = 0; k < n; ++k) {  // forward: y = L^-1 b, z = D^-1 y
-        if (k > 0) Dk = d[k] - s - Lg[(k - 1) * n + c] * e[k - 1];
+        if (k > 0) Dk = d[k] - s - Lg[(k - 1) * lz + c] * e[k - 1];
         if (fabsf(Dk) < piv) Dk = Dk < 0.f ? -piv : piv;
-        const float b = pass == 0 ? start_entry(c, k) : Zg[k * n + c];
-        y = k == 0 ? b : b - Lg[(k - 1) * n + c] * y;
-        Zg[k * n + c] = __fdividef(y, Dk);
+        const float b = pass == 0 ? start_entry(c, k) : Zg[k * lz + c];
+        y = k == 0 ? b : b - Lg[(k - 1) * lz + c] * y;
+        Zg[k * lz + c] = __fdividef(y, Dk);
       }
-      float xn = Zg[(n - 1) * n + c], nrm = xn * xn;
+      float xn = Zg[(n - 1) * lz + c], nrm = xn * xn;
       for (int k = n - 2; k >= 0; --k) {  // backward: x = L^-T z
-        xn = Zg[k * n + c] - Lg[k * n + c] * xn;
-        Zg[k * n + c] = xn;
+        xn = Zg[k * lz + c] - Lg[k * lz + c] * xn;
+        Zg[k * lz + c] = xn;
         nrm = fmaf(xn, xn, nrm);
       }
       const bool good = nrm > 0.f && nrm <= FLT_MAX;
       const float r = good ? rsqrtf(nrm) : 0.f;
-      for (int k = 0; k < n; ++k) Zg[k * n + c] = good ? Zg[k * n + c] * r : (k == c ? 1.f : 0.f);
+      for (int k = 0; k < n; ++k) Zg[k * lz + c] = good ? Zg[k * lz + c] * r : (k == c ? 1.f : 0.f);
     }
   }
   __syncthreads();
 
-  // ---- 4. Z <- Q of Z = Q R (Householder, columns in descending eigenvalue
-  // order), signs kept: reflector j from column j's rows j.. (v below the
-  // diagonal of Z's column j, tau in qt[j], sign of R(j, j) in qs[j]),
-  // applied to the columns after j by threads (c, g): column c, rows of
-  // class g (mod 4); then Q = H_0 ... H_{n-1} I in Lg (the L factors are
-  // spent), each H_j touching only rows and columns from j on.
-  float *qt = lam, *qs = e2;  // spent after steps 2 and 3
-  {
-    const int c = tid & 255, g = tid >> 8;
-    for (int j = 0; j < n; ++j) {
-      const int mj = n - j;
-      for (int r = tid; r < mj; r += nt) zj[r] = Zg[(j + r) * n + j];
-      __syncthreads();
-      const Refl h = wide_larfg(zj, mj, red);
-      if (tid == 0) {
-        qt[j] = h.t;
-        qs[j] = h.beta < 0.f ? -1.f : 1.f;
-      }
-      if (tid < mj) zj[tid] = tid == 0 ? 1.f : zj[tid] * h.scal;
-      __syncthreads();
-      if (tid >= 1 && tid < mj) Zg[(j + tid) * n + j] = zj[tid];
-      if (h.t != 0.f) {  // the same in every thread
-        float sum = 0.f;
-        if (c > j && c < n)
-          for (int a = g; a < mj; a += 4) sum = fmaf(zj[a], Zg[(j + a) * n + c], sum);
-        ps[g * 256 + c] = sum;
-        __syncthreads();
-        if (c > j && c < n) {
-          const float f = h.t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
-          for (int a = g; a < mj; a += 4) Zg[(j + a) * n + c] -= f * zj[a];
-        }
-      }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < n * n; idx += nt) Lg[idx] = idx / n == idx % n ? 1.f : 0.f;
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-      const float t = qt[j];
-      if (t == 0.f) continue;  // the same in every thread
-      const int mj = n - j;
-      for (int r = tid; r < mj; r += nt) zj[r] = r == 0 ? 1.f : Zg[(j + r) * n + j];
-      __syncthreads();
-      float sum = 0.f;
-      if (c >= j && c < n)
-        for (int a = g; a < mj; a += 4) sum = fmaf(zj[a], Lg[(j + a) * n + c], sum);
-      ps[g * 256 + c] = sum;
-      __syncthreads();
-      if (c >= j && c < n) {
-        const float f = t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
-        for (int a = g; a < mj; a += 4) Lg[(j + a) * n + c] -= f * zj[a];
-      }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < n * n; idx += nt) Lg[idx] *= qs[idx % n];
-    __syncthreads();
+  // ---- 4. Zg <- Q of Zg = Q R (Householder), columns in descending eigenvalue
+  // order, signs kept, in compact WY blocks of kNb as in k_eig32_tri: a warp
+  // factors each panel in registers (reflectors to Lg, the L factors being
+  // spent), the trailing columns take the panel at once; then the explicit Q
+  // in Zg by the blocks applied to I in reverse order.
+  float *qtau = lam, *sgn = e2;  // spent after steps 2 and 3
+  float *W = Lg;
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, c = idx - r * lz;
+    if (c >= n) Zg[idx] = 0.f;  // padding columns stay zero (and finite)
+    W[idx] = 0.f;
   }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += kNb) {
+    const int nbk = min(kNb, n - j0);
+    float *Tb = Tf + (j0 / kNb) * kNb * kNb;
+    if (warp == 0) qr_panel_wide(Zg, lz, W, n, j0, nbk, lane, qtau, sgn, Tb);
+    __syncthreads();
+    if (j0 + nbk < n) apply_wy_wide(Zg, lz, n, j0, j0 + nbk, W, lz, j0, Tb, true, part);
+  }
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, c = idx - r * lz;
+    Zg[idx] = r == c ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int j0 = ((n - 1) / kNb) * kNb; j0 >= 0; j0 -= kNb)
+    apply_wy_wide(Zg, lz, n, j0, j0, W, lz, j0, Tf + (j0 / kNb) * kNb * kNb, false, part);
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, c = idx - r * n;
+    Zg[r * lz + c] *= sgn[c];
+  }
+  __syncthreads();
 
-  // ---- 5. X = Q1 Q (Q in Lg): H_k = I - tau_k v_k v_k^T (v_k(0) = 1 at row k + 1, the
-  // rest below the subdiagonal of packed column k), k from n - 3 down to 0;
-  // thread (c, g): column c, rows of class g (mod 4), partial sums in ps
-  {
-    const int c = tid & 255, g = tid >> 8;
-    for (int k = n - 3; k >= 0; --k) {
-      const float t = tau[k];
-      if (t == 0.f) continue;  // the same for every thread
-      const float *v = Ap + packed_col(n, k) + 1;  // v[a] for row k + 1 + a, v[0] = 1
-      const int m = n - k - 1;
-      float s = 0.f;
-      if (c < n)
-        for (int a = g; a < m; a += 4) s = fmaf(v[a], Lg[(k + 1 + a) * n + c], s);
-      ps[g * 256 + c] = s;
-      __syncthreads();
-      if (c < n) {
-        const float f = t * ((ps[c] + ps[256 + c]) + (ps[512 + c] + ps[768 + c]));
-        for (int a = g; a < m; a += 4) Lg[(k + 1 + a) * n + c] -= f * v[a];
-      }
-      __syncthreads();
-    }
+  // ---- 5. X = Q1 Zg: the tridiagonalization's reflectors (v_k in packed
+  // column k below the subdiagonal, unit entry at row k + 1) copied to W,
+  // their T factors, and the blocks from the last to the first
+  const int nref = max(n - 2, 0);
+  for (int idx = tid; idx < n * lz; idx += nt) {
+    const int r = idx / lz, k = idx - r * lz;
+    float v = 0.f;
+    if (k < nref) v = r == k + 1 ? 1.f : (r > k + 1 && tau[k] != 0.f ? Ap[packed_col(n, k) + (r - k)] : 0.f);
+    W[idx] = v;
   }
+  __syncthreads();
+  const int nblk = (nref + kNb - 1) / kNb;
+  if (nblk > 0) form_wy_ts(W, lz, nblk, nref, 1, n, tau, Tf, part);  // the QR blocks' T factors are spent
+  for (int j0 = (nblk - 1) * kNb; j0 >= 0; j0 -= kNb)
+    apply_wy_wide(Zg, lz, n, j0 + 1, 0, W, lz, j0, Tf + (j0 / kNb) * kNb * kNb, false, part);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx % n, c = idx / n;
-    X[r + (int64_t)ldx * c] = (double)Lg[r * n + c];
+    X[r + (int64_t)ldx * c] = (double)__ldcg(Zg + (int64_t)r * lz + c);
   }
 }
 
@@ -2095,11 +2279,20 @@ int mp_level(const double *A, int lda, int m, double noise, int depth, const MpW
       k_copy_cols<<<(m * m + 255) / 256, 256, 0, s>>>(Xn, m, X, m, m, m);
       TK_LAUNCHED();
     }
-  } else if (m > kTriMaxJ) {  // the wide stage; E (m x m float64) holds its two float arrays until the first step's E
+  } else if (m > kTriMaxJ) {
+    // the wide stage; G (m x 2m float64, free until the refinement) holds its
+    // two m x tri32_ld(m) float arrays, which it reads and writes as 16-byte
+    // vectors: the workspace's regions start at 8-byte multiples only (odd J),
+    // so the arrays start at G rounded up to 16 bytes (G has 16 J^2 bytes; the
+    // arrays need 8 m (m + 8))
     const size_t smemw = wide32_smem(m);
     TK_CUDA(allow_max_smem(k_eig32_wide));
-    float *zs = reinterpret_cast<float *>(E);
-    k_eig32_wide<<<1, kW32Threads, smemw, s>>>(A, lda, m, tx0 + (size_t)m * m, m, zs, zs + (size_t)m * m);
+    float *zs = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(G) + 15) & ~static_cast<uintptr_t>(15));
+    if ((reinterpret_cast<uintptr_t>(zs) & 15) != 0 || ((size_t)m * tri32_ld(m) * sizeof(float)) % 16 != 0) {
+      set_error("wide eigensolver stage: unaligned scratch");
+      return TUCKER_ECUDA;
+    }
+    k_eig32_wide<<<1, kW32Threads, smemw, s>>>(A, lda, m, tx0 + (size_t)m * m, m, zs, zs + (size_t)m * tri32_ld(m));
   } else if (use_jacobi) {
     const size_t smem32 = jacobi32_smem(m);
     TK_CUDA(allow_max_smem(k_jacobi32));
