@@ -1377,8 +1377,8 @@ __device__ void qr_panel_wide(const float *__restrict__ Z, int lz, float *__rest
 }
 
 __global__ void __launch_bounds__(kW32Threads, 1) k_eig32_wide(const double *__restrict__ A, int lda, int n,
-                                                             double *__restrict__ X, int ldx, float *Zg,
-                                                             float *Lg) {
+                                                             double *__restrict__ X, int ldx,
+                                                             float *__restrict__ Zg, float *__restrict__ Lg) {
   extern __shared__ __align__(16) float smw[];
   float *Ap = smw;
   const WideLayout lay(n);
