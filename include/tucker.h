@@ -392,6 +392,26 @@ TUCKER_API const char *tucker_last_error(void);
 /* Number of kernels this library has launched in this process. */
 TUCKER_API int64_t tucker_launch_count(void);
 
+/* Memory held between calls, for monitoring a long-running process.  Any
+ * pointer may be NULL.
+ *   pool_used      bytes in use in the current device's default stream-ordered
+ *                  pool: every live device-resident result and any temporary a
+ *                  call on another thread holds (other users of that pool count
+ *                  too).  Back at its earlier value once the results made since
+ *                  are freed.
+ *   pool_reserved  bytes that pool holds from the driver; up to 64 GiB stay
+ *                  reserved between calls so repeated ST-HOSVDs do not map
+ *                  memory again.
+ *   host_cached    bytes of pinned host blocks kept after tucker_result_free of
+ *                  host results, for the next host result (at most 4 GiB).
+ * Returns TUCKER_OK or TUCKER_ECUDA. */
+TUCKER_API int tucker_memory_stats(int64_t *pool_used, int64_t *pool_reserved, int64_t *host_cached);
+
+/* Returns the cached pinned host blocks to the driver and trims the current
+ * device's default pool to what is in use.  Synchronises the device.
+ * Returns TUCKER_OK or TUCKER_ECUDA. */
+TUCKER_API int tucker_memory_trim(void);
+
 /* The tuning of the last batched device pipeline: columns per work item,
  * persistent CTAs, and the six candidates' times in ms (512 / 2048 / 8192
  * columns x 2 / 4 CTAs per SM, the first mode's Gram).  Any pointer may be

@@ -45,12 +45,16 @@ int64_t bump_launches(int64_t n = 1);
     if (s_ != TUCKER_OK) return s_;                                                    \
   } while (0)
 
-// Library bookkeeping behind tucker_result.priv: the device, and for results
-// of the batched pipeline the device block their core and factors live in
-// (released when the last result that shares it is freed).
+// Library bookkeeping behind tucker_result.priv: the device; for results of
+// the batched pipeline the device block their core and factors live in
+// (released when the last result that shares it is freed); for host results
+// the pinned block holding core and factors (returned to the host block
+// cache when the result is freed).
 struct ResultPriv {
   int device = 0;
   std::shared_ptr<void> block;
+  void *host_block = nullptr;
+  size_t host_bytes = 0;
 };
 
 // The batched device pipeline (every I_n <= 128): fills out[0..count) like

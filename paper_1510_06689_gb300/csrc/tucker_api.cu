@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -251,7 +252,71 @@ static size_t elem_size(tucker_dtype dt) { return dt == TUCKER_F64 ? 8 : 4; }
 
 using Priv = ResultPriv;
 
-static void free_result_device(tucker_result *r) {
+// Pinned host blocks for results returned in host memory.  A freed result's
+// block is kept (up to kHostCacheCap bytes in all) for the next result of a
+// similar size, so repeated host calls neither pin new pages nor fault fresh
+// pageable ones in, and their device-to-host copies run at DMA speed.  The
+// cache is never destroyed: no CUDA call runs during process teardown.
+struct HostBlockCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> blocks;  // bytes -> block
+  size_t bytes = 0;
+};
+static constexpr size_t kHostCacheCap = size_t(4) << 30;
+
+static HostBlockCache &host_cache() {
+  static HostBlockCache *c = new HostBlockCache;
+  return *c;
+}
+
+// A pinned block of at least `bytes` bytes (*got: its size), or nullptr.  A
+// cached block serves if it is at most twice the request.
+static void *host_block_get(size_t bytes, size_t *got) {
+  bytes = std::max<size_t>(bytes, 16);
+  HostBlockCache &c = host_cache();
+  {
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.blocks.lower_bound(bytes);
+    if (it != c.blocks.end() && it->first / 2 <= bytes) {
+      void *p = it->second;
+      *got = it->first;
+      c.bytes -= it->first;
+      c.blocks.erase(it);
+      return p;
+    }
+  }
+  void *p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *got = bytes;
+  return p;
+}
+
+static void host_block_put(void *p, size_t bytes) {
+  if (!p) return;
+  HostBlockCache &c = host_cache();
+  {
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (c.bytes + bytes <= kHostCacheCap) {
+      c.blocks.emplace(bytes, p);
+      c.bytes += bytes;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
+static size_t host_cache_bytes() {
+  HostBlockCache &c = host_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  return c.bytes;
+}
+
+// `own`: the stream that issued every use of r's device buffers (they are
+// freed on it, in stream order, without a device synchronisation), or nullptr.
+static void free_result_device(tucker_result *r, cudaStream_t *own = nullptr) {
   const Priv *pv = static_cast<const Priv *>(r->priv);
   if (pv && pv->block) {  // core and factors live in a block shared by a batch (freed with its last result)
     r->core = nullptr;
@@ -259,12 +324,21 @@ static void free_result_device(tucker_result *r) {
     return;
   }
   if (r->on_host) {
-    free(r->core);
-    for (int n = 0; n < TUCKER_MAX_MODES; ++n) free(r->factors[n]);
+    // core and factors share one pinned block, which goes back to the cache
+    if (pv) host_block_put(pv->host_block, pv->host_bytes);
   } else {
-    if (r->core) cudaFree(r->core);
+    bool any = r->core != nullptr;
+    for (int n = 0; n < TUCKER_MAX_MODES; ++n) any = any || r->factors[n] != nullptr;
+    if (!any) return;
+    // stream-ordered allocations go back to their pool with cudaFreeAsync
+    // (freed with cudaFree, the pool's in-use count kept growing by every
+    // freed result), after the device synchronisation tucker_result_free
+    // promises unless the caller names the buffers' own stream
+    cudaStream_t fs = own ? *own : cudaStreamLegacy;
+    if (!own) cudaDeviceSynchronize();
+    if (r->core) cudaFreeAsync(r->core, fs);
     for (int n = 0; n < TUCKER_MAX_MODES; ++n)
-      if (r->factors[n]) cudaFree(r->factors[n]);
+      if (r->factors[n]) cudaFreeAsync(r->factors[n], fs);
   }
   r->core = nullptr;
   for (int n = 0; n < TUCKER_MAX_MODES; ++n) r->factors[n] = nullptr;
@@ -769,6 +843,46 @@ const char *tucker_last_error(void) { return g_err; }
 
 int64_t tucker_launch_count(void) { return g_launches.load(); }
 
+int tucker_memory_stats(int64_t *pool_used, int64_t *pool_reserved, int64_t *host_cached) {
+  g_err[0] = 0;
+  if (pool_used || pool_reserved) {
+    int dev = 0;
+    TK_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    TK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t v = 0;
+    if (pool_used) {
+      TK_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+      *pool_used = (int64_t)v;
+    }
+    if (pool_reserved) {
+      TK_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v));
+      *pool_reserved = (int64_t)v;
+    }
+  }
+  if (host_cached) *host_cached = (int64_t)host_cache_bytes();
+  return TUCKER_OK;
+}
+
+int tucker_memory_trim(void) {
+  g_err[0] = 0;
+  TK_CUDA(cudaDeviceSynchronize());
+  std::multimap<size_t, void *> blocks;
+  {
+    HostBlockCache &c = host_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    blocks.swap(c.blocks);
+    c.bytes = 0;
+  }
+  for (auto &b : blocks) TK_CUDA(cudaFreeHost(b.second));
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  TK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  TK_CUDA(cudaMemPoolTrimTo(pool, 0));
+  return TUCKER_OK;
+}
+
 void tucker_batched_tuning(int64_t *cols_per_item, int *ctas, float *candidate_ms) {
   batched_last_tuning(cols_per_item, ctas, candidate_ms);
 }
@@ -857,16 +971,24 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
   out->on_host = 1;
   out->core = nullptr;
   for (int n = 0; n < TUCKER_MAX_MODES; ++n) out->factors[n] = nullptr;
-  int64_t G = 1;
-  for (int n = 0; n < N; ++n) G *= dres.ranks[n];
-  out->core = static_cast<double *>(malloc(sizeof(double) * G));
-  bool ok = out->core != nullptr;
-  for (int n = 0; n < N && ok; ++n) {
-    out->factors[n] = static_cast<double *>(malloc(sizeof(double) * dims[n] * dres.ranks[n]));
-    ok = out->factors[n] != nullptr;
-  }
+  // core and factors in one pinned block: core first, then U_1 .. U_N
+  int64_t total = 1;
+  for (int n = 0; n < N; ++n) total *= dres.ranks[n];
+  const int64_t G = total;
+  for (int n = 0; n < N; ++n) total += dims[n] * dres.ranks[n];
+  size_t got = 0;
+  double *hb = static_cast<double *>(host_block_get(sizeof(double) * total, &got));
+  Priv *pv = static_cast<Priv *>(out->priv);
+  pv->host_block = hb;
+  pv->host_bytes = got;
   cudaError_t e = cudaSuccess;
-  if (ok) {
+  if (hb) {
+    out->core = hb;
+    int64_t off = G;
+    for (int n = 0; n < N; ++n) {
+      out->factors[n] = hb + off;
+      off += dims[n] * dres.ranks[n];
+    }
     e = cudaMemcpyAsync(out->core, dres.core, sizeof(double) * G, cudaMemcpyDeviceToHost, s);
     for (int n = 0; n < N && e == cudaSuccess; ++n)
       e = cudaMemcpyAsync(out->factors[n], dres.factors[n], sizeof(double) * dims[n] * dres.ranks[n],
@@ -876,12 +998,12 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
   // release the device copies (eigenvalues and priv now belong to *out)
   for (int n = 0; n < TUCKER_MAX_MODES; ++n) dres.eigvals[n] = nullptr;
   dres.priv = nullptr;
-  free_result_device(&dres);
-  if (!ok || e != cudaSuccess) {
-    if (!ok) set_error("host allocation failed");
+  free_result_device(&dres, &s);  // produced and copied on s only
+  if (!hb || e != cudaSuccess) {
+    if (!hb) set_error("pinned host allocation of %lld bytes failed", (long long)(sizeof(double) * total));
     else set_error("device-to-host copy failed: %s", cudaGetErrorString(e));
     tucker_result_free(out);
-    return ok ? TUCKER_ECUDA : TUCKER_ENOMEM;
+    return hb ? TUCKER_ECUDA : TUCKER_ENOMEM;
   }
   return TUCKER_OK;
 }

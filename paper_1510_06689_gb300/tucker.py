@@ -29,7 +29,7 @@ EXPORTS = (
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
     "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak", "tucker_gram_split_e4m3",
-    "tucker_batched_tuning",
+    "tucker_batched_tuning", "tucker_memory_stats", "tucker_memory_trim",
 )
 EIG_PATHS = ("mixed", "jacobi", "jacobi_fallback")
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
@@ -111,6 +111,8 @@ def load(path=LIB_PATH):
         "tucker_profile_read": (None, [ctypes.POINTER(_Profile)]),
         "tucker_fp64_peak": (i32, [pdbl, pdbl, vp]),
         "tucker_batched_tuning": (None, [pi64, pi32, ctypes.POINTER(ctypes.c_float)]),
+        "tucker_memory_stats": (i32, [pi64, pi64, pi64]),
+        "tucker_memory_trim": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -199,7 +201,7 @@ class Result:
         n = math.prod(self.ranks)
         if self.on_host:
             buf = (ctypes.c_double * n).from_address(self._raw.core)
-            return torch.tensor(list(buf), dtype=torch.float64)
+            return torch.frombuffer(buf, dtype=torch.float64).clone()
         return _copy_out(self._raw.core, n)
 
     def factor(self, n):
@@ -207,7 +209,7 @@ class Result:
         i, r = self.dims[n], self.ranks[n]
         if self.on_host:
             buf = (ctypes.c_double * (i * r)).from_address(self._raw.factors[n])
-            flat = torch.tensor(list(buf), dtype=torch.float64)
+            flat = torch.frombuffer(buf, dtype=torch.float64).clone()
         else:
             flat = _copy_out(self._raw.factors[n], i * r)
         return flat.view(r, i).t().contiguous()  # column-major storage
@@ -485,6 +487,18 @@ def batched_tuning():
     ms = (ctypes.c_float * 6)()
     load().tucker_batched_tuning(ctypes.byref(kc), ctypes.byref(grid), ms)
     return kc.value, grid.value, list(ms)
+
+
+def memory_stats():
+    """Bytes held between calls: the device pool in use and reserved, and cached pinned host blocks."""
+    used, res, host = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().tucker_memory_stats(ctypes.byref(used), ctypes.byref(res), ctypes.byref(host)))
+    return {"pool_used": used.value, "pool_reserved": res.value, "host_cached": host.value}
+
+
+def memory_trim():
+    """Return cached pinned host blocks and unused pool memory to the driver (synchronises the device)."""
+    _check(load().tucker_memory_trim())
 
 
 def fp64_peak(stream=None):

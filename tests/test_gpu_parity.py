@@ -604,6 +604,45 @@ def test_host_entry_point(gpu_lib):
         assert torch.equal(res_h.factor(n), res_d.factor(n).cpu())
 
 
+def test_results_return_their_memory(gpu_lib):
+    """A freed device result goes back to the stream-ordered pool and a freed
+    host result's pinned block to the host block cache, so repeated calls hold
+    no more memory than one."""
+    import gc
+
+    import torch
+
+    dims, ranks = (40, 36, 30), (6, 5, 4)
+    x = tucker_tensor_np(dims, ranks, seed=16, noise=1e-3)
+    xd = dev(x)
+    gpu_lib.sthosvd(xd, dims, 1e-2).free()
+    gc.collect()
+    torch.cuda.synchronize()
+    before = gpu_lib.memory_stats()["pool_used"]
+    for _ in range(6):
+        r = gpu_lib.sthosvd(xd, dims, 1e-2)
+        res_bytes = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)))
+        held = gpu_lib.memory_stats()["pool_used"]
+        r.free()
+    assert held >= before + res_bytes  # a live result's core and factors are in the pool
+    assert gpu_lib.memory_stats()["pool_used"] <= before
+
+    xh = torch.from_numpy(x).pin_memory()
+    first = gpu_lib.sthosvd_host(xh, dims, 1e-2)
+    core0 = first.core()
+    first.free()
+    cached = gpu_lib.memory_stats()["host_cached"]
+    assert cached >= res_bytes
+    for _ in range(3):
+        r = gpu_lib.sthosvd_host(xh, dims, 1e-2)
+        assert gpu_lib.memory_stats()["host_cached"] < cached  # the block came from the cache
+        assert torch.equal(r.core(), core0)
+        r.free()
+        assert gpu_lib.memory_stats()["host_cached"] == cached
+    gpu_lib.memory_trim()
+    assert gpu_lib.memory_stats()["host_cached"] == 0
+
+
 def test_run_to_run_identical(gpu_lib):
     dims, ranks = (48, 40, 30, 12), (8, 8, 6, 4)
     x = dev(tucker_tensor_np(dims, ranks, seed=7, decay=0.1, noise=1e-5))
