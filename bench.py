@@ -55,8 +55,7 @@ DTYPES = {"bf16x4": "bf16x4-split (f64 in/out: Gram 3 BF16 digits of 21-bit entr
 # algorithmic bytes of the timed run; it is dropped as soon as the kernel
 # source changes.  (Where a file changed after its capture only in comments or
 # in helpers the kernel does not use, the hash is that of the file as it
-# stands: the mode products' file lost the mbarrier arrive helper to the shared
-# tensor-core header, and the Gram file's kernel comment was rewritten.)
+# stands: the Gram file's kernel comment was rewritten.)
 TRAFFIC = {("k_gram_split_bulk", "4f18e3950a8e992b"): {
                "ratio": (1.61277e9 + 3.984128e6) / 1.610612736e9,
                "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB); the tiled mode-2 launch (L = 40) "
@@ -64,10 +63,10 @@ TRAFFIC = {("k_gram_split_bulk", "4f18e3950a8e992b"): {
            ("k_rowgroup_exp", "4f18e3950a8e992b"): {
                "ratio": (1.610713e9 + 10.311424e6) / 1.610612736e9,
                "captured": "mode-1 launch with the column exponents, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_l1", "eada4239a9f6c758"): {"ratio": (1.61719e9 + 473.159424e6) / 2.113929216e9,
+           ("k_ttm_split_l1", "fea6c14821ec6d0b"): {"ratio": (1.617545e9 + 473.28128e6) / 2.113929216e9,
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB in, "
                                                                 "0.50 GB out)"},
-           ("k_ttm_split_tma", "eada4239a9f6c758"): {"ratio": (0.505437e9 + 130.96448e6) / 0.66060288e9,
+           ("k_ttm_split_tma", "fea6c14821ec6d0b"): {"ratio": (0.505482e9 + 131.997952e6) / 0.66060288e9,
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB in, "
                                                                  "0.16 GB out)"}}
 def _measured_hbm():

@@ -157,18 +157,33 @@ __device__ __forceinline__ void digits28(float y, int f1022, float (&d)[4]) {
 // sum_k a_k 2^(28 - 7k) 2^sc as a float64, from four float accumulators that
 // hold integers |a_k| < 2^22 (the levels 2..5 of a digit product): the
 // integers come out of the floats exactly by magic-number addition, pairs
-// combine in 32 bits (|a0 2^7 + a1| < 2^30), and the 50-bit sum is exact in
-// float64.  Its conversion and the power-of-two scale run on the float64
-// pipe (idle in these kernels, where the integer pipe is the busy one);
-// scales outside the normal exponent range take the exact bit assembly.
+// combine in 32 bits (|a0 2^7 + a1| < 2^30, likewise a2, a3), and one wide
+// multiply-add forms w = (a0 2^7 + a1) 2^14 + a2 2^7 + a3, the sum over
+// 2^7 (|w| < 2^45, exact in float64, where it is converted).  The
+// power-of-two scale 2^(sc + 7) is either a float64 multiply (kFp64Scale:
+// where the integer pipe is the busy one and the float64 pipe, narrow on
+// this part, has room for a second instruction) or an integer add to the
+// exponent field; both are exact while the result stays normal (w's
+// exponent is at most 44, so -1022 <= sc + 7 <= 979 suffices).  Other scales
+// take the exact bit assembly.
+template <bool kFp64Scale>
 __device__ __forceinline__ double levels_to_double(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, int sc) {
-  const int i0 = __float_as_int(__fadd_rn(__uint_as_float(a0), 12582912.0f)) - 0x4B400000;
-  const int i1 = __float_as_int(__fadd_rn(__uint_as_float(a1), 12582912.0f)) - 0x4B400000;
-  const int i2 = __float_as_int(__fadd_rn(__uint_as_float(a2), 12582912.0f)) - 0x4B400000;
-  const int i3 = __float_as_int(__fadd_rn(__uint_as_float(a3), 12582912.0f)) - 0x4B400000;
-  const long long v = ((long long)(i0 * 128 + i1) << 21) + ((long long)(i2 * 128 + i3) << 7);
-  if (sc >= -1022 && sc <= 1023) return __dmul_rn((double)v, __longlong_as_double((long long)(sc + 1023) << 52));
-  return scaled_ll_to_double(v, sc);
+  constexpr unsigned kMagic = 0x4B400000u;  // the bits of 1.5 2^23
+  const unsigned u0 = __float_as_uint(__fadd_rn(__uint_as_float(a0), 12582912.0f));
+  const unsigned u1 = __float_as_uint(__fadd_rn(__uint_as_float(a1), 12582912.0f));
+  const unsigned u2 = __float_as_uint(__fadd_rn(__uint_as_float(a2), 12582912.0f));
+  const unsigned u3 = __float_as_uint(__fadd_rn(__uint_as_float(a3), 12582912.0f));
+  // two's-complement wrap-around: the results are the signed pair values
+  const int hi = (int)((u0 - kMagic) * 128u + (u1 - kMagic));
+  const int lo = (int)((u2 - kMagic) * 128u + (u3 - kMagic));
+  const long long w = (long long)hi * 16384 + lo;
+  const int s7 = sc + 7;
+  if (s7 >= -1022 && s7 <= 979) {
+    if (kFp64Scale) return __dmul_rn((double)w, __longlong_as_double((long long)(s7 + 1023) << 52));
+    const long long b = __double_as_longlong((double)w);
+    return w ? __longlong_as_double(b + ((long long)s7 << 52)) : 0.0;
+  }
+  return scaled_ll_to_double(w, s7);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ttm_split2(const T *__restrict_
           for (int e = 0; e < 4; ++e) {
             const int r = r0 + e;
             if (r >= p.R) continue;
-            const double v = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + colexp[set][c] - 42);
+            const double v = levels_to_double<false>(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + colexp[set][c] - 42);
             double *zp = z + ob + L * (int64_t)r;
             *zp = p.accum ? *zp + v : v;
           }
@@ -596,26 +611,46 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
 
   if (warp < kL1Conv) {
     // ---------------- converters ----------------
-    // half h of column m of this CTA's tile it: entries j = 2 lane + 64 h (a pair)
-    auto load_half = [&](int it, int m, int h, V2 &v) {
-      const int64_t c = (t0 + (int64_t)it * tstride) * kM2 + m;
-      const int j = 2 * lane + 64 * h;
-      if (it < ntc && c < p.K && j < p.J)
-        v = __ldg(reinterpret_cast<const V2 *>(y + c * (int64_t)p.J + j));
+    // tile it seen from this warp: its first column (warp) as a pointer to
+    // this lane's pair of entries (j = 2 lane) and to the column's exponent,
+    // and how many of the tile's columns lie from that one on; slot k (column
+    // warp + 16 k) holds data while 16 k < cols.  The next tile's view is
+    // formed once per tile (at its last half, so that the two views are not
+    // held at once), and a load is an offset from a view and one compare.
+    struct View {
+      const T *yp;
+      const int *ep;
+      int cols;
+    };
+    auto view_of = [&](int it) {
+      View v;
+      const int64_t c0 = (t0 + (int64_t)it * tstride) * kM2 + warp;
+      v.yp = y + c0 * (int64_t)p.J + 2 * lane;
+      v.ep = colexp + c0;
+      const int64_t left = it < ntc ? p.K - c0 : 0;
+      v.cols = (int)(left < kM2 ? (left > 0 ? left : 0) : kM2);
+      return v;
+    };
+    const int slot_elems = kL1Conv * p.J;  // entries between a warp's consecutive columns
+    bool jok[P];
+#pragma unroll
+    for (int h = 0; h < P; ++h) jok[h] = 2 * lane + 64 * h < p.J;
+    // half h (entries j = 2 lane + 64 h, a pair) of slot k's column
+    auto load_half = [&](const View &t, int k, int h, V2 &v) {
+      if (kL1Conv * k < t.cols && jok[h])
+        v = __ldg(reinterpret_cast<const V2 *>(t.yp + k * slot_elems + 64 * h));
       else
         v.x = v.y = T(0);
     };
-    auto load_exp = [&](int it, int m) {
-      const int64_t c = (t0 + (int64_t)it * tstride) * kM2 + m;
-      return (it < ntc && c < p.K) ? __ldg(colexp + c) : 0;
-    };
+    auto load_exp = [&](const View &t, int k) { return kL1Conv * k < t.cols ? __ldg(t.ep + kL1Conv * k) : 0; };
     // slot k holds column warp + 16 k: its current half, and its exponent
     V2 cb[kL1ColsPerWarp];
     int fx[kL1ColsPerWarp];
+    View cur = view_of(0);
 #pragma unroll
     for (int k = 0; k < kL1ColsPerWarp; ++k) {
-      load_half(0, warp + kL1Conv * k, 0, cb[k]);
-      fx[k] = load_exp(0, warp + kL1Conv * k);
+      load_half(cur, k, 0, cb[k]);
+      fx[k] = load_exp(cur, k);
     }
     // this lane's byte offset within a digit row: 16-byte chunk lane / 4 of the
     // 128-byte row, XOR-swizzled by the row's index mod 8 (= warp mod 8 for
@@ -623,8 +658,10 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
     const int lane_off = (((lane >> 2) ^ (warp & 7)) << 4) + (lane & 3) * 4;
     bool ok = true;
     for (int it = 0; it < ntc && ok; ++it) {
+      View nxt = cur;
 #pragma unroll
       for (int h = 0; h < P; ++h) {
+        if (h == P - 1) nxt = view_of(it + 1);  // after the last use of cur's pointer
         if (it >= 1) {  // the previous tile's MMAs have read this half
           int w = 0;
           if (lane == 0) w = role_wait(smem_addr(&part_free[h]), (uint32_t)((it - 1) & 1), &stop);
@@ -649,16 +686,17 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
           // refill: the next half of this column, or the first half of the
           // column this slot takes in the next tile (with its exponent)
           if (h + 1 < P) {
-            load_half(it, m, h + 1, cb[k]);
+            load_half(cur, k, h + 1, cb[k]);
           } else {
-            load_half(it + 1, m, 0, cb[k]);
-            fx[k] = load_exp(it + 1, m);
+            load_half(nxt, k, 0, cb[k]);
+            fx[k] = load_exp(nxt, k);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&part_full[h]));
       }
+      cur = nxt;
     }
   } else if (warp < kL1Conv + kL1Drain) {
     // ---------------- drain ----------------
@@ -694,7 +732,7 @@ __global__ void __launch_bounds__(kL1Threads, 1) k_ttm_split_l1(const T *__restr
           double o[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e)
-            o[e] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r0 + e] + fcol - 42);
+            o[e] = levels_to_double<true>(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r0 + e] + fcol - 42);
           if (vec) {  // R even: (r0, r0 + 1) and (r0 + 2, r0 + 3) are whole pairs or past R
             *reinterpret_cast<double2 *>(zc + r0) = make_double2(o[0], o[1]);
             if (r0 + 2 < p.R) *reinterpret_cast<double2 *>(zc + r0 + 2) = make_double2(o[2], o[3]);
@@ -985,7 +1023,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int r = r0 + e;
-            if (r < p.R) zc[p.L * (int64_t)r] = levels_to_double(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + fc - 42);
+            if (r < p.R) zc[p.L * (int64_t)r] = levels_to_double<false>(a[0][e], a[1][e], a[2][e], a[3][e], rowexp[r] + fc - 42);
           }
         }
       }
