@@ -63,10 +63,10 @@ TRAFFIC = {("k_gram_split_bulk", "4f18e3950a8e992b"): {
            ("k_rowgroup_exp", "4f18e3950a8e992b"): {
                "ratio": (1.610713e9 + 10.311424e6) / 1.610612736e9,
                "captured": "mode-1 launch with the column exponents, 128x128x128x48x2 (1.61 GB)"},
-           ("k_ttm_split_l1", "fea6c14821ec6d0b"): {"ratio": (1.617545e9 + 473.28128e6) / 2.113929216e9,
+           ("k_ttm_split_l1", "b803e1d1d0874cd9"): {"ratio": (1.617572e9 + 473.8048e6) / 2.113929216e9,
                                                     "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB in, "
                                                                 "0.50 GB out)"},
-           ("k_ttm_split_tma", "fea6c14821ec6d0b"): {"ratio": (0.505482e9 + 131.997952e6) / 0.66060288e9,
+           ("k_ttm_split_tma", "b803e1d1d0874cd9"): {"ratio": (0.505408e9 + 130.27712e6) / 0.66060288e9,
                                                      "captured": "mode-2 launch, 40x128x128x48x2 (0.50 GB in, "
                                                                  "0.16 GB out)"}}
 def _measured_hbm():

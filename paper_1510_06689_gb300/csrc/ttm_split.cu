@@ -941,10 +941,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
       l0 = 0;
     }
   };
-  // the column exponent of tile row mm (-4000 past the tile's columns: such
-  // a column converts to zeros and is not written)
-  auto col_exp = [&](int it, int mm) -> int {
-    const int s = mm / p.BL, lo = mm - s * p.BL;
+  // the column exponent of the tile row at box position (s, lo), i.e. row
+  // s BL + lo (-4000 past the tile's columns: such a column converts to
+  // zeros and is not written)
+  auto col_exp = [&](int it, int s, int lo) -> int {
     int64_t l0, b0;
     tile_origin(it, l0, b0);
     const int64_t l = l0 + lo, b = b0 + s;
@@ -964,12 +964,16 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
     const int raw_off = (s_m * kTmKH + 8 * jq) * p.BL + loff;  // element (m, 8 jq) of a slot
     const int off = (m >> 3) * (int)kSboA + jq * 128 + (m & 7) * 16;
     int f1022 = 0;
+    // unit u is part pp of tile it in ring slot `slot` (its phase slot_par):
+    // counters, not divisions, on this per-unit path
+    int it = 0, pp = 0, slot = 0;
+    uint32_t slot_par = 0;
     for (int u = 0; u < nunits; ++u) {
-      const int it = u / p.parts, pp = u - it * p.parts, slot = u % p.slots, stg = u & 1;
-      if (pp == 0) f1022 = col_exp(it, m) + 1022;
+      const int stg = u & 1;
+      if (pp == 0) f1022 = col_exp(it, s_m, loff) + 1022;
       int ok = 1;
       if (lane == 0) {
-        ok = role_wait(smem_addr(&raw_full[slot]), (uint32_t)((u / p.slots) & 1), &stop);
+        ok = role_wait(smem_addr(&raw_full[slot]), slot_par, &stop);
         if (ok && u >= 2) ok = role_wait(smem_addr(&mma_done[stg]), (uint32_t)(((u - 2) >> 1) & 1), &stop);
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
@@ -991,6 +995,14 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&a_full[stg]));  // this warp has read slot u and written stage stg
+      if (++pp == p.parts) {
+        pp = 0;
+        ++it;
+      }
+      if (++slot == p.slots) {
+        slot = 0;
+        slot_par ^= 1u;
+      }
     }
   } else if (warp < kTmConv + kTmDrain) {
     // ---------------- drain: TMEM lanes 32 q.. (columns), half of the rows ----------------
@@ -1033,21 +1045,35 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_ttm_split_tma(const __grid_co
     }
   } else if (lane == 0) {
     // ---------------- control: copies and MMAs ----------------
-    auto issue_copy = [&](int u) {  // part u % parts of tile u / parts -> slot u % slots
-      int64_t l0, b0;
-      tile_origin(u / p.parts, l0, b0);
-      const int slot = u % p.slots;
-      const uint32_t bar = smem_addr(&raw_full[slot]);
+    // copy number `issued` is part c_pp of tile c_it into slot c_slot
+    int c_it = 0, c_pp = 0, c_slot = 0;
+    int64_t c_l0 = 0, c_b0 = 0;
+    tile_origin(0, c_l0, c_b0);
+    auto issue_copy = [&]() {
+      const uint32_t bar = smem_addr(&raw_full[c_slot]);
       mbar_expect_tx(bar, (uint32_t)p.raw_slot);
-      tma_load_3d(smem_addr(ring + (size_t)slot * p.raw_slot), &ymap, (int)l0, kTmKH * (u % p.parts), (int)b0, bar);
+      tma_load_3d(smem_addr(ring + (size_t)c_slot * p.raw_slot), &ymap, (int)c_l0, kTmKH * c_pp, (int)c_b0, bar);
+      if (++c_pp == p.parts) {
+        c_pp = 0;
+        tile_origin(++c_it, c_l0, c_b0);
+      }
+      if (++c_slot == p.slots) c_slot = 0;
     };
     int issued = 0, last = -1;
-    for (; issued < p.slots && issued < nunits; ++issued) issue_copy(issued);
+    for (; issued < p.slots && issued < nunits; ++issued) issue_copy();
     const uint32_t ub = smem_addr(Ut);
-    for (int u = 0; u < nunits; ++u) {
-      const int it = u / p.parts, pp = u - it * p.parts, stg = u & 1, set = it & 1;
+    int it = 0, pp = 0;  // unit u is part pp of tile it
+    for (int u = 0; u < nunits; ++u, ++pp) {
+      if (pp == p.parts) {
+        pp = 0;
+        ++it;
+      }
+      const int stg = u & 1, set = it & 1;
       if (!role_wait(smem_addr(&a_full[stg]), (uint32_t)((u >> 1) & 1), &stop)) break;
-      if (issued < nunits) issue_copy(issued++);  // slot u % slots has been read by every converter
+      if (issued < nunits) {  // slot u % slots has been read by every converter
+        issue_copy();
+        ++issued;
+      }
       if (pp == 0 && it >= 2 && !role_wait(smem_addr(&acc_free[set]), (uint32_t)(((it - 2) >> 1) & 1), &stop)) break;
       fence_after();
       const uint32_t ab = smem_addr(Ast + stg * 4 * kATile);
