@@ -814,18 +814,29 @@ def main():
 
     # end to end through the host entry point: H2D of X and D2H of the result inside the timed region
     if xh is not None:
+        def raw_copy_ms():
+            return round(_time_calls(lambda: x.copy_(xh, non_blocking=True), stream, reps=3)[0], 3)
+
         def e2e(prec, steps):
             r = tucker.sthosvd_host(xh, dims, args.eps, precision=prec)
             d2h = 8 * (math.prod(r.ranks) + sum(d * k for d, k in zip(dims, r.ranks)))
             r.free()
+            # the host link is shared: the raw copy rate right before and after
+            # the timed calls shows the state the end-to-end figure saw
+            before = raw_copy_ms()
             barrier(world)
+            step_ms = []
             t0 = time.perf_counter()
             for _ in range(steps):
+                ts = time.perf_counter()
                 tucker.sthosvd_host(xh, dims, args.eps, precision=prec).free()
+                step_ms.append(round((time.perf_counter() - ts) * 1e3, 3))
             t_e2e = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+            after = raw_copy_ms()
             return {"value": round(world * w.nbytes / t_e2e / 1e9, 4), "unit": "GB/s",
                     "h2d_bytes_per_step": w.nbytes, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": round(t_e2e * 1e3, 3), "precision": prec, "steps": steps}
+                    "ms_per_step": round(t_e2e * 1e3, 3), "precision": prec, "steps": steps,
+                    "step_ms": step_ms, "raw_copy_ms_before": before, "raw_copy_ms_after": after}
 
         line["e2e"] = e2e(head, args.steps)
         line["e2e"]["raw_h2d"] = {"gb_s": round(w.nbytes / (h2d_ms / 1e3) / 1e9, 2), "ms": round(h2d_ms, 3),
