@@ -54,13 +54,14 @@ DTYPES = {"bf16x4": "bf16x4-split (f64 in/out: Gram 3 BF16 digits of 21-bit entr
 # algorithmic bytes.  The reported traffic is this ratio times the per-launch
 # algorithmic bytes of the timed run; it is dropped as soon as the kernel
 # source changes.  (Where a file changed after its capture only in comments or
-# in helpers the kernel does not use, the hash is that of the file as it
-# stands: the Gram file's kernel comment was rewritten.)
-TRAFFIC = {("k_gram_split_bulk", "4f18e3950a8e992b"): {
-               "ratio": (1.61277e9 + 3.984128e6) / 1.610612736e9,
+# in code the kernel does not use, the hash is that of the file as it stands:
+# the exponent pass shares its file with the Gram, whose exponent loads
+# changed after the pass's capture.)
+TRAFFIC = {("k_gram_split_bulk", "b2d1f76f5c84a03a"): {
+               "ratio": (1.612927e9 + 4.082432e6) / 1.610612736e9,
                "captured": "mode-1 launch, 128x128x128x48x2 (1.61 GB); the tiled mode-2 launch (L = 40) "
                            "measured 1.031"},
-           ("k_rowgroup_exp", "4f18e3950a8e992b"): {
+           ("k_rowgroup_exp", "b2d1f76f5c84a03a"): {
                "ratio": (1.610713e9 + 10.311424e6) / 1.610612736e9,
                "captured": "mode-1 launch with the column exponents, 128x128x128x48x2 (1.61 GB)"},
            ("k_ttm_split_l1", "b803e1d1d0874cd9"): {"ratio": (1.617572e9 + 473.8048e6) / 2.113929216e9,

@@ -1008,16 +1008,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     n_issued = 0;
   }
   cta_row_ref(Etab, J, r0, Jb, g0, (c_end + kGroup - 1) / kGroup, ref, refs + blockIdx.x * kRows);
-  // exponents of the group starting at chunk ch go to buffer (ch / kDrainChunks) & 1
-  auto load_exps = [&](int ch) {
-    if (tid < kRows) {
-      const int gi = ch / kDrainChunks;
-      const int e = tid < Jb ? Etab[(g0 + gi) * J + r0 + tid] : kZeroExp;
-      rowexp[gi & 1][tid] = e;
-      relexp[gi & 1][tid] = e - ref[tid];
-    }
+  // exponents of column group gi go to buffer gi & 1 (threads < kRows, one
+  // row each); the next group's are loaded at a group's start into a
+  // register and stored at its drain, so no thread waits on the load
+  auto fetch_exp = [&](int gi) -> int { return tid < Jb ? Etab[(g0 + gi) * J + r0 + tid] : kZeroExp; };
+  auto store_exp = [&](int gi, int e) {
+    rowexp[gi & 1][tid] = e;
+    relexp[gi & 1][tid] = e - ref[tid];
   };
-  load_exps(0);
+  if (tid < kRows) store_exp(0, fetch_exp(0));
+  int next_exp = 0;        // threads < kRows: the next group's exponent, in flight
+  bool next_pending = false;
   fence_before();
   __syncthreads();
   fence_after();
@@ -1092,6 +1093,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
     } else {
       bad = true;
     }
+    if (next_pending) {  // the other buffer, read only after the barrier below
+      store_exp(gi + 1, next_exp);
+      next_pending = false;
+    }
     fence_before();
     // the column group's one block barrier; a failed wait anywhere stops every thread here
     if (__syncthreads_or(bad ? 1 : 0)) halt = true;
@@ -1121,8 +1126,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_split_bulk(const __grid_co
       const int in_group = ch % kDrainChunks, gi = ch / kDrainChunks;
       if (u == 0 && in_group == 0) {
         cvt = scaled_float_param<T>(rowexp[gi & 1][row]);
-        // the next column group's exponents go to the other buffer, read after the drain barrier
-        if (ch + kDrainChunks < nchunks) load_exps(ch + kDrainChunks);
+        // the next column group's exponents go to the other buffer at this group's drain
+        if (tid < kRows && ch + kDrainChunks < nchunks) {
+          next_exp = fetch_exp(gi + 1);
+          next_pending = true;
+        }
       }
       if ((u & 1) == grp) {
         if (!bad) bad = !mbar_wait(smem_addr(&raw_full[u]), ring_par);
