@@ -149,9 +149,16 @@ TUCKER_API int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dim
 
 /*
  * tucker_sthosvd_host -- the same computation for a tensor in host memory.
- * Copies X_host (pinned memory recommended) to the device on `stream`, runs
+ * Copies X_host (pinned memory recommended) to the device, runs
  * tucker_sthosvd, and returns the core and factors in library-allocated host
  * memory (out->on_host = 1).  Device buffers are released before returning.
+ * With TUCKER_PREC_BF16X4 and mode 1 processed first, the copy goes in up to
+ * eight chunks of columns of the mode-1 unfolding on a stream of the
+ * library's own, and mode 1's Gram runs chunk by chunk as they land (the
+ * chunks' Grams are summed), so the copy hides that pass; the result then
+ * equals tucker_sthosvd's up to the rounding of that sum (ranks and
+ * discarded sums to ~1e-15 relative).  Otherwise one copy on `stream`.
+ * Synchronises `stream`.
  */
 TUCKER_API int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
                         const int *mode_order, tucker_precision prec, void *stream, tucker_result *out);

@@ -352,7 +352,27 @@ __global__ void k_trace(const double *__restrict__ S, int J, double *__restrict_
   for (int i = 0; i < J; ++i) t += S[i + (int64_t)J * i];
   *out = t;
 }
+
+// S = sum over c < n of the c-th J x J Gram in Sc (the Grams of the column
+// chunks of one unfolding), added in chunk order
+__global__ void k_sum_grams(const double *__restrict__ Sc, int n, int64_t JJ, double *__restrict__ S) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= JJ) return;
+  double t = Sc[i];
+  for (int c = 1; c < n; ++c) t += Sc[(int64_t)c * JJ + i];
+  S[i] = t;
+}
 }  // namespace
+
+// X arriving in column chunks of its first unfolding (the host entry
+// point's copy): chunk c holds columns col[c] .. col[c + 1] - 1 once event
+// ev[c] has completed.
+constexpr int kMaxFeedChunks = 8;
+struct HostFeed {
+  int n = 0;
+  cudaEvent_t ev[kMaxFeedChunks] = {};
+  int64_t col[kMaxFeedChunks + 1] = {};
+};
 
 int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s) {
   k_trace<<<1, 32, 0, s>>>(d_S, (int)J, d_out);
@@ -363,8 +383,11 @@ int launch_trace(const double *d_S, int64_t J, double *d_out, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
+// `feed`: X is still arriving (see HostFeed); only with the BF16 digits and
+// mode 1 processed first, whose Gram then runs chunk by chunk as the columns
+// land (Sec. 2.2: the Gram is a sum over columns).
 static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *order,
-                        tucker_precision prec, cudaStream_t s, tucker_result *out) {
+                        tucker_precision prec, cudaStream_t s, tucker_result *out, const HostFeed *feed = nullptr) {
   DeviceInfo dev;
   TK_CHECK(device_info(&dev));
   Prof prof(s);
@@ -403,8 +426,14 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
   }
 
   void *host = nullptr;
-  TK_CHECK(pinned(sizeof(double) * (8 + maxJ), &host));
+  TK_CHECK(pinned(sizeof(double) * (8 + maxJ) + sizeof(int) * kMaxFeedChunks, &host));
   double *h = static_cast<double *>(host);
+  int *h_chunk_err = reinterpret_cast<int *>(h + 8 + maxJ);  // the fed first Gram's per-chunk error flags
+  int n_chunk_err = 0;
+  if (feed && (prec != TUCKER_PREC_BF16X4 || order[0] != 0 || feed->n < 1 || feed->n > kMaxFeedChunks)) {
+    set_error("internal: a chunked input needs the BF16 digits with mode 1 first");
+    return TUCKER_EINVAL;
+  }
 
   // ||X||^2 and the threshold of the rank rule.  The split-precision path
   // takes ||X||^2 as the trace of its first Gram (equal in exact arithmetic;
@@ -465,7 +494,39 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     // Gram step (its exponent pass also leaves the column exponents the TTM needs)
     DevBuf colexp;
     const bool want_colexp = L > 1 || J <= 128;  // longer contiguous columns: the TTM scales its parts itself
-    if (split) {
+    if (split && k == 0 && feed) {
+      // mode 1 (L = 1) while X arrives: each chunk of columns gets its own
+      // exponent pass and Gram (with its own workspace and error flag) as
+      // soon as it has landed, and the chunks' Grams are added in order; the
+      // 512-column exponent groups are the same as in one pass over X
+      const int nc = feed->n;
+      const size_t es = ydt == TUCKER_F64 ? 8 : 4;
+      auto chunk_y = [&](int c) { return static_cast<const void *>(static_cast<const char *>(Y) + es * J * feed->col[c]); };
+      int64_t gws = 0;
+      for (int c = 0; c < nc; ++c)
+        gws = std::max(gws, gram_split_workspace_doubles(1, J, feed->col[c + 1] - feed->col[c], dev, ydt, chunk_y(c)));
+      TK_CHECK(gramws.alloc(sizeof(double) * gws * nc, s));
+      if (want_colexp) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
+      DevBuf Sc;
+      TK_CHECK(Sc.alloc(sizeof(double) * J * J * nc, s));
+      reinterpret_cast<int *>(h + 5)[0] = 0;  // no single-pass flag this mode
+      for (int c = 0; c < nc; ++c) {
+        const int64_t c0 = feed->col[c], bc = feed->col[c + 1] - c0;
+        double *wsc = gramws.as<double>() + gws * c;
+        TK_CUDA(cudaStreamWaitEvent(s, feed->ev[c], 0));
+        TK_CHECK(launch_gram_split(chunk_y(c), ydt, 1, J, bc, Sc.as<double>() + J * J * c, wsc, dev, s, &prof,
+                                   want_colexp ? colexp.as<int>() + c0 : nullptr, f8));
+        TK_CHECK(gram_split_error(wsc, 1, J, bc, dev, h_chunk_err + c, s));
+      }
+      n_chunk_err = nc;
+      const int64_t JJ = J * J;
+      k_sum_grams<<<(unsigned)((JJ + 255) / 256), 256, 0, s>>>(Sc.as<double>(), nc, JJ, S.as<double>());
+      TK_LAUNCHED();
+      TK_CHECK(launch_trace(S.as<double>(), J, d_nx2, s));
+      TK_CUDA(cudaMemcpyAsync(h, d_nx2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      TK_CHECK(set_norm(h[0]));
+    } else if (split) {
       const int64_t gws = gram_split_workspace_doubles(L, J, B, dev, ydt, Y);
       TK_CHECK(gramws.alloc(sizeof(double) * gws, s));
       if (want_colexp) TK_CHECK(colexp.alloc(sizeof(int) * L * B, s));
@@ -493,7 +554,10 @@ static int sthosvd_impl(const void *X, tucker_dtype dt, const int64_t *dims, int
     TK_CUDA(cudaMemcpyAsync(h, d_tail, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(h + 8, lam.as<double>(), sizeof(double) * J, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
-    if (split && reinterpret_cast<int *>(h + 5)[0] != 0) {
+    bool gram_expired = split && reinterpret_cast<int *>(h + 5)[0] != 0;
+    for (int c = 0; c < n_chunk_err; ++c) gram_expired = gram_expired || h_chunk_err[c] != 0;
+    n_chunk_err = 0;
+    if (gram_expired) {
       set_error("split-precision Gram: a bounded tensor-core wait expired (mode %d)", n);
       return TUCKER_ETIMEOUT;
     }
@@ -910,8 +974,18 @@ void tucker_profile_read(tucker_profile *p) {
   *p = g_prof;
 }
 
+static int sthosvd_entry(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                         const int *mode_order, tucker_precision prec, void *stream, tucker_result *out,
+                         const HostFeed *feed);
+
 int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *mode_order,
                    tucker_precision prec, void *stream, tucker_result *out) {
+  return sthosvd_entry(X, dt, dims, N, eps, mode_order, prec, stream, out, nullptr);
+}
+
+static int sthosvd_entry(const void *X, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                         const int *mode_order, tucker_precision prec, void *stream, tucker_result *out,
+                         const HostFeed *feed) {
   g_err[0] = 0;
   if (!out) {
     set_error("out is NULL");
@@ -937,7 +1011,11 @@ int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dims, int N, d
   TK_CHECK(check_dims(dims, N));
   int order[TUCKER_MAX_MODES];
   TK_CHECK(check_order(mode_order, N, order));
-  int st = sthosvd_impl(X, dt, dims, N, eps, order, prec, static_cast<cudaStream_t>(stream), out);
+  if (feed && (prec != TUCKER_PREC_BF16X4 || order[0] != 0)) {  // no chunked first Gram: wait for the whole copy
+    TK_CUDA(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), feed->ev[feed->n - 1], 0));
+    feed = nullptr;
+  }
+  int st = sthosvd_impl(X, dt, dims, N, eps, order, prec, static_cast<cudaStream_t>(stream), out, feed);
   if (st != TUCKER_OK) {
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     memset(out, 0, sizeof *out);
@@ -963,9 +1041,54 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
   for (int n = 0; n < N; ++n) I *= dims[n];
   DevBuf dX;
   TK_CHECK(dX.alloc(elem_size(dt) * I, s));
-  TK_CUDA(cudaMemcpyAsync(dX.p, X_host, elem_size(dt) * I, cudaMemcpyHostToDevice, s));
+  // With the BF16 digits and mode 1 first, X goes over in up to eight
+  // chunks of whole 512-column groups of its first unfolding on a copy
+  // stream of its own, and mode 1's Gram starts on each chunk as it lands
+  // (the copy hides the first pass over X); otherwise in one copy.
+  int order[TUCKER_MAX_MODES];
+  TK_CHECK(check_order(mode_order, N, order));
+  HostFeed feed;
+  cudaStream_t cs = nullptr;
+  const int64_t B0 = I / dims[0];
+  if (prec == TUCKER_PREC_BF16X4 && order[0] == 0 && B0 >= 2 * 512) {
+    const int64_t per = std::max<int64_t>(512, (B0 / kMaxFeedChunks + 511) / 512 * 512);
+    const int nc = (int)((B0 + per - 1) / per);
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int c = 0; c < nc && ok; ++c) {
+      ok = cudaEventCreateWithFlags(&feed.ev[c], cudaEventDisableTiming) == cudaSuccess;
+      if (ok) feed.n = c + 1;
+    }
+    cudaEvent_t ready = nullptr;  // dX's stream-ordered allocation is usable on the copy stream
+    ok = ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventRecord(ready, s) == cudaSuccess && cudaStreamWaitEvent(cs, ready, 0) == cudaSuccess;
+    if (ready) cudaEventDestroy(ready);
+    const size_t col_bytes = elem_size(dt) * (size_t)dims[0];
+    for (int c = 0; c < nc && ok; ++c) {
+      feed.col[c] = per * c;
+      feed.col[c + 1] = std::min(B0, per * (c + 1));
+      const size_t off = col_bytes * (size_t)feed.col[c], bytes = col_bytes * (size_t)(feed.col[c + 1] - feed.col[c]);
+      ok = cudaMemcpyAsync(static_cast<char *>(dX.p) + off, static_cast<const char *>(X_host) + off, bytes,
+                           cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+           cudaEventRecord(feed.ev[c], cs) == cudaSuccess;
+    }
+    if (!ok) {  // fall back to one copy on the caller's stream, after whatever was issued
+      cudaGetLastError();
+      cudaStreamSynchronize(cs);
+      for (int c = 0; c < feed.n; ++c) cudaEventDestroy(feed.ev[c]);
+      cudaStreamDestroy(cs);
+      cs = nullptr;
+      feed.n = 0;
+    }
+  }
+  if (!cs) TK_CUDA(cudaMemcpyAsync(dX.p, X_host, elem_size(dt) * I, cudaMemcpyHostToDevice, s));
   tucker_result dres;
-  int st = tucker_sthosvd(dX.p, dt, dims, N, eps, mode_order, prec, stream, &dres);
+  int st = sthosvd_entry(dX.p, dt, dims, N, eps, mode_order, prec, stream, &dres, cs ? &feed : nullptr);
+  if (cs) {
+    // X's buffer is freed on the caller's stream: after every copy, whatever path ran
+    cudaStreamWaitEvent(s, feed.ev[feed.n - 1], 0);
+    for (int c = 0; c < feed.n; ++c) cudaEventDestroy(feed.ev[c]);
+    cudaStreamDestroy(cs);
+  }
   if (st != TUCKER_OK) return st;
   *out = dres;
   out->on_host = 1;

@@ -604,6 +604,36 @@ def test_host_entry_point(gpu_lib):
         assert torch.equal(res_h.factor(n), res_d.factor(n).cpu())
 
 
+def test_host_entry_point_chunked_bf16(gpu_lib):
+    """BF16 digits with mode 1 first: the host entry point copies X in column
+    chunks (here 8: seven of 1024 columns and a ragged one of 32) and runs
+    mode 1's Gram chunk by chunk.  Ranks equal the device call's, the result
+    equals it up to the rounding of the chunk sum, and repeated calls agree
+    bit for bit."""
+    import torch
+
+    dims, ranks = (64, 40, 30, 6), (6, 5, 4, 3)
+    x = tucker_tensor_np(dims, ranks, seed=21, noise=1e-4)
+    xh = torch.from_numpy(x).pin_memory()
+    a = gpu_lib.sthosvd_host(xh, dims, 1e-3, precision="bf16x4")
+    b = gpu_lib.sthosvd_host(xh, dims, 1e-3, precision="bf16x4")
+    d = gpu_lib.sthosvd(dev(x), dims, 1e-3, precision="bf16x4")
+    assert a.ranks == b.ranks == d.ranks
+    assert torch.equal(a.core(), b.core())
+    core_d = d.core().cpu()
+    assert (a.core() - core_d).abs().max() <= 1e-9 * core_d.abs().max()
+    for n in range(len(dims)):
+        assert (a.factor(n) - d.factor(n).cpu()).abs().max() <= 1e-8
+        assert a.tails[n] == pytest.approx(d.tails[n], rel=1e-9, abs=1e-15 * d.norm2)
+    assert a.norm2 == pytest.approx(d.norm2, rel=1e-14)
+    # mode 1 not first: one copy, the device call bit for bit
+    order = (1, 0, 2, 3)
+    h2 = gpu_lib.sthosvd_host(xh, dims, 1e-3, mode_order=order, precision="bf16x4")
+    d2 = gpu_lib.sthosvd(dev(x), dims, 1e-3, mode_order=order, precision="bf16x4")
+    assert h2.ranks == d2.ranks
+    assert torch.equal(h2.core(), d2.core().cpu())
+
+
 def test_results_return_their_memory(gpu_lib):
     """A freed device result goes back to the stream-ordered pool and a freed
     host result's pinned block to the host block cache, so repeated calls hold
