@@ -626,6 +626,13 @@ def test_host_entry_point_chunked_bf16(gpu_lib):
         assert (a.factor(n) - d.factor(n).cpu()).abs().max() <= 1e-8
         assert a.tails[n] == pytest.approx(d.tails[n], rel=1e-9, abs=1e-15 * d.norm2)
     assert a.norm2 == pytest.approx(d.norm2, rel=1e-14)
+    # float32 input takes the same chunked path
+    x32 = x.astype(np.float32)
+    h32 = gpu_lib.sthosvd_host(torch.from_numpy(x32).pin_memory(), dims, 1e-3, precision="bf16x4")
+    d32 = gpu_lib.sthosvd(dev(x32), dims, 1e-3, precision="bf16x4")
+    assert h32.ranks == d32.ranks
+    c32 = d32.core().cpu()
+    assert (h32.core() - c32).abs().max() <= 1e-9 * c32.abs().max()
     # mode 1 not first: one copy, the device call bit for bit
     order = (1, 0, 2, 3)
     h2 = gpu_lib.sthosvd_host(xh, dims, 1e-3, mode_order=order, precision="bf16x4")
