@@ -641,6 +641,24 @@ def test_host_entry_point_chunked_bf16(gpu_lib):
     assert torch.equal(h2.core(), d2.core().cpu())
 
 
+@pytest.mark.parametrize("dims", [(200, 40, 30), (65, 40, 30)])
+def test_host_entry_point_chunked_other_grams(gpu_lib, dims):
+    """The chunked first Gram on the other Gram paths: J = 200 (row blocks
+    and their pairs) and J = 65 (520-byte columns, which the tensor map does
+    not take: the register-staged kernel); 1200 columns make three chunks,
+    the last one ragged."""
+    import torch
+
+    ranks = (8, 6, 5)
+    x = tucker_tensor_np(dims, ranks, seed=22, noise=1e-4)
+    a = gpu_lib.sthosvd_host(torch.from_numpy(x).pin_memory(), dims, 1e-3, precision="bf16x4")
+    d = gpu_lib.sthosvd(dev(x), dims, 1e-3, precision="bf16x4")
+    assert a.ranks == d.ranks
+    core_d = d.core().cpu()
+    assert (a.core() - core_d).abs().max() <= 1e-9 * core_d.abs().max()
+    assert a.norm2 == pytest.approx(d.norm2, rel=1e-14)
+
+
 def test_results_return_their_memory(gpu_lib):
     """A freed device result goes back to the stream-ordered pool and a freed
     host result's pinned block to the host block cache, so repeated calls hold
