@@ -1051,9 +1051,11 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
   cudaStream_t cs = nullptr;
   const int64_t B0 = I / dims[0];
   if (prec == TUCKER_PREC_BF16X4 && order[0] == 0 && B0 >= 2 * 512) {
-    const int64_t per = std::max<int64_t>(512, (B0 / kMaxFeedChunks + 511) / 512 * 512);
+    // chunks of ceil(B0 / 8) columns rounded up to whole groups: at most eight
+    const int64_t per = std::max<int64_t>(512, ((B0 + kMaxFeedChunks - 1) / kMaxFeedChunks + 511) / 512 * 512);
     const int nc = (int)((B0 + per - 1) / per);
-    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = nc >= 2 && nc <= kMaxFeedChunks &&
+              cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
     for (int c = 0; c < nc && ok; ++c) {
       ok = cudaEventCreateWithFlags(&feed.ev[c], cudaEventDisableTiming) == cudaSuccess;
       if (ok) feed.n = c + 1;
@@ -1073,9 +1075,9 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
     }
     if (!ok) {  // fall back to one copy on the caller's stream, after whatever was issued
       cudaGetLastError();
-      cudaStreamSynchronize(cs);
+      if (cs) cudaStreamSynchronize(cs);
       for (int c = 0; c < feed.n; ++c) cudaEventDestroy(feed.ev[c]);
-      cudaStreamDestroy(cs);
+      if (cs) cudaStreamDestroy(cs);
       cs = nullptr;
       feed.n = 0;
     }
