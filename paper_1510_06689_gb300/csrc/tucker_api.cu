@@ -333,12 +333,18 @@ static void free_result_device(tucker_result *r, cudaStream_t *own = nullptr) {
     // stream-ordered allocations go back to their pool with cudaFreeAsync
     // (freed with cudaFree, the pool's in-use count kept growing by every
     // freed result), after the device synchronisation tucker_result_free
-    // promises unless the caller names the buffers' own stream
+    // promises unless the caller names the buffers' own stream; on the
+    // result's own device when the caller has another one current
+    int cur = -1;
+    cudaGetDevice(&cur);
+    const bool other = pv && !own && cur >= 0 && pv->device != cur;
+    if (other) cudaSetDevice(pv->device);
     cudaStream_t fs = own ? *own : cudaStreamLegacy;
     if (!own) cudaDeviceSynchronize();
     if (r->core) cudaFreeAsync(r->core, fs);
     for (int n = 0; n < TUCKER_MAX_MODES; ++n)
       if (r->factors[n]) cudaFreeAsync(r->factors[n], fs);
+    if (other) cudaSetDevice(cur);
   }
   r->core = nullptr;
   for (int n = 0; n < TUCKER_MAX_MODES; ++n) r->factors[n] = nullptr;
