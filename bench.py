@@ -112,6 +112,8 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-next", action="store_true",
                    help="skip the HOOI / subtensor / mode-order / batched / paper-shape measurements")
+    p.add_argument("--batched-only", action="store_true",
+                   help="print only the many-small-tensors row (the batched entry point) as one JSON line")
     p.add_argument("--paper-shapes-only", action="store_true",
                    help="print only the paper-problem measurements (200^4 and 25x250^3, float64 path)")
     return p.parse_args()
@@ -583,8 +585,16 @@ def measure_batched(tucker, precision, stream, count=1024, eps=1e-3, workers=8):
         times.append(e0.elapsed_time(e1))
         del res
     ms = statistics.median(times)
+    # one more call with the library's phase events on (untimed above)
+    tucker.profile_enable(True)
+    res = tucker.sthosvd_batched(xs, dims_list, eps, precision=precision, workers=workers)
+    torch.cuda.synchronize()
+    del res
+    prof = tucker.profile_read()
+    tucker.profile_enable(False)
     kc, ctas, cand = tucker.batched_tuning()
     return {"tensors": count, "input_gb": round(nbytes / 1e9, 3), "ms": round(ms, 2),
+            "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
             "input_gb_s": round(nbytes / (ms / 1e3) / 1e9, 2), "tensors_per_s": round(count / (ms / 1e3), 1),
             "true_ranks_recovered": ok, "eig_paths": paths,
             "path": "device pipeline (float64): per mode one launch per phase for all tensors, work lists and "
@@ -743,6 +753,10 @@ def main():
     barrier(world)
     tucker.load()
     FP64_PEAK.update(measure_fp64_peak(tucker, torch.cuda.current_stream()))
+    if args.batched_only:
+        if rank == 0:
+            print(json.dumps(measure_batched(tucker, "fp64", torch.cuda.current_stream())), flush=True)
+        return 0
     if args.paper_shapes_only:
         if rank == 0:
             print(json.dumps(measure_paper_shapes(tucker, torch.cuda.current_stream())), flush=True)
