@@ -2049,6 +2049,15 @@ __global__ void k_ns_coef(double *P, int m) {
   }
 }
 
+// the eigensolver's info record: sweeps, not converged, path, resolved count
+__global__ void k_set_info(int *info, int sweeps, int noconv, int path, int resolved) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  info[0] = sweeps;
+  info[1] = noconv;
+  info[2] = path;
+  info[3] = resolved;
+}
+
 __global__ void k_set_identity(double *X, int ldx, int m) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
     const int i = e % m, j = e / m;
@@ -2086,22 +2095,34 @@ __global__ void __launch_bounds__(1024) k_mp_finalize(const double *__restrict__
     rk[i] = rank;
   }
   __syncthreads();
-  double res = 0.0, orth = 0.0, lmax = 0.0;
-  for (int e = tid; e < m * m; e += nt) {
-    const int i = e % m, j = e / m;
-    // columns sorted at or past u0 span the unresolved tail clusters: not eigenvectors
-    if (rk[j] < u0) res = fmax(res, fabs(T[e] - X[e] * lam[j]));
-    orth = fmax(orth, fabs(P[e] - (i == j ? 1.0 : 0.0)));
-    if (!(T[e] == T[e]) || !(P[e] == P[e])) res = INFINITY;  // NaN fails the check
-  }
-  for (int i = tid; i < m; i += nt) lmax = fmax(lmax, fabs(lam[i]));
-  for (int o = 16; o > 0; o >>= 1) {
-    res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
-    orth = fmax(orth, __shfl_xor_sync(0xffffffffu, orth, o));
-    lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  }
+  // The check's maxima are of magnitudes, so they are taken on the bit
+  // patterns (ordered like the values for non-negative doubles) on the
+  // integer pipe; the float64 pipe (2 lanes per clock per SM here) does only
+  // the residual's multiply-subtract and the diagonal's subtraction.  A NaN
+  // in T or P makes the residual infinite, so the result fails the check.
+  constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
   const int lane = tid & 31, warp = tid >> 5;
-  __shared__ double rr[32], oo[32], ll[32];
+  unsigned long long res = 0ull, orth = 0ull, lmax = 0ull;
+  for (int j = warp; j < m; j += nt / 32) {
+    const bool resolved = rk[j] < u0;  // columns sorted at or past u0 span the unresolved tail clusters
+    const double lj = lam[j];
+    for (int i = lane; i < m; i += 32) {
+      const int64_t e = i + (int64_t)m * j;
+      const double t = T[e], p = P[e];
+      const unsigned long long tb = (unsigned long long)__double_as_longlong(t) & kMag;
+      const unsigned long long pb = (unsigned long long)__double_as_longlong(p) & kMag;
+      if (resolved) res = max(res, (unsigned long long)__double_as_longlong(t - X[e] * lj) & kMag);
+      orth = max(orth, i == j ? (unsigned long long)__double_as_longlong(p - 1.0) & kMag : pb);
+      if (tb > kInf || pb > kInf) res = kInf;  // NaN
+    }
+  }
+  for (int i = tid; i < m; i += nt) lmax = max(lmax, (unsigned long long)__double_as_longlong(lam[i]) & kMag);
+  for (int o = 16; o > 0; o >>= 1) {
+    res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
+    orth = max(orth, __shfl_xor_sync(0xffffffffu, orth, o));
+    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  }
+  __shared__ unsigned long long rr[32], oo[32], ll[32];
   if (lane == 0) {
     rr[warp] = res;
     oo[warp] = orth;
@@ -2109,32 +2130,43 @@ __global__ void __launch_bounds__(1024) k_mp_finalize(const double *__restrict__
   }
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0, b = 0.0, c = 0.0;
+    unsigned long long a = 0ull, b = 0ull, c = 0ull;
     for (int w = 0; w < nt / 32; ++w) {
-      a = fmax(a, rr[w]);
-      b = fmax(b, oo[w]);
-      c = fmax(c, ll[w]);
+      a = max(a, rr[w]);
+      b = max(b, oo[w]);
+      c = max(c, ll[w]);
     }
-    check[0] = a;
-    check[1] = b;
-    check[2] = c;
+    // a residual of NaN (from X or lam) stays NaN: it fails the check too
+    check[0] = __longlong_as_double((long long)a);
+    check[1] = __longlong_as_double((long long)b);
+    check[2] = __longlong_as_double((long long)c);
   }
-  for (int i = tid; i < m; i += nt) {
-    const double di = lam[i];
+  // column i, sorted to position rk[i], signed so that its first entry of
+  // largest magnitude is positive: a warp per column, lanes over rows
+  // (coalesced), the first maximum by a (magnitude, row) reduction
+  for (int i = warp; i < m; i += nt / 32) {
     const int rank = rk[i];
-    lam_out[rank] = di;
+    if (lane == 0) lam_out[rank] = lam[i];
     const double *col = X + (int64_t)m * i;
     double best = -1.0;
-    int br = 0;
-    for (int r = 0; r < m; ++r) {
+    int br = m;
+    for (int r = lane; r < m; r += 32) {
       const double v = fabs(col[r]);
-      if (v > best) {
+      if (v > best) {  // NaN never wins, as in a scan over the rows
         best = v;
         br = r;
       }
     }
-    const double sg = col[br] < 0.0 ? -1.0 : 1.0;
-    for (int r = 0; r < m; ++r) V_out[r + (int64_t)m * rank] = sg * col[r];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+      if (ob > best || (ob == best && orr < br)) {
+        best = ob;
+        br = orr;
+      }
+    }
+    const double sg = (br < m && col[br] < 0.0) ? -1.0 : 1.0;
+    for (int r = lane; r < m; r += 32) V_out[r + (int64_t)m * rank] = sg * col[r];
   }
 }
 
@@ -2444,9 +2476,9 @@ int launch_eig_mp(const double *d_S, int64_t J, double *d_lam, double *d_V, int 
   g_mp_check[3] = tol_orth;
   g_mp_check[4] = skipped;
   if (chk[0] <= tol_res && chk[1] <= tol_orth) {
-    const int info[4] = {sw, 0, TUCKER_EIG_MIXED, m - skipped};
-    TK_CUDA(cudaMemcpyAsync(d_info, info, sizeof info, cudaMemcpyHostToDevice, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    // written on the stream (a copy from the host stack would wait for it)
+    k_set_info<<<1, 32, 0, s>>>(d_info, sw, 0, TUCKER_EIG_MIXED, m - skipped);
+    TK_LAUNCHED();
     *verified = 1;
   }
   return TUCKER_OK;
