@@ -96,19 +96,57 @@ static std::mutex g_prof_mu;
 static std::atomic<bool> g_prof_on{false};
 static tucker_profile g_prof;
 
+// Timing events are reused across calls (per device): creating and
+// destroying two per phase would put host work between the launches of a
+// profiled run.  Never destroyed, like the host block cache.
+struct EventPool {
+  std::mutex mu;
+  std::vector<cudaEvent_t> free[64];
+};
+static EventPool &event_pool() {
+  static EventPool *p = new EventPool;
+  return *p;
+}
+static bool event_get(cudaEvent_t *e) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  EventPool &p = event_pool();
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    if (!p.free[dev].empty()) {
+      *e = p.free[dev].back();
+      p.free[dev].pop_back();
+      return true;
+    }
+  }
+  return cudaEventCreate(e) == cudaSuccess;
+}
+static void event_put(cudaEvent_t e) {
+  int dev = 0;
+  if (!e) return;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaEventDestroy(e);
+    return;
+  }
+  EventPool &p = event_pool();
+  std::lock_guard<std::mutex> lock(p.mu);
+  p.free[dev].push_back(e);
+}
+
 Prof::Prof(cudaStream_t stream) : on(g_prof_on.load()), s(stream) {}
 
 Prof::~Prof() {
   for (auto &r : recs) {
-    if (r.a) cudaEventDestroy(r.a);
-    if (r.b) cudaEventDestroy(r.b);
+    event_put(r.a);
+    event_put(r.b);
   }
 }
 
 void Prof::begin(int phase) {
   if (!on) return;
   Rec r{phase, nullptr, nullptr, 0, 0, 0};
-  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+  if (!event_get(&r.a) || !event_get(&r.b)) {
+    event_put(r.a);
     on = false;
     return;
   }
@@ -136,8 +174,8 @@ void Prof::flush() {
       g_prof.flops[r.phase] += r.flops;
       g_prof.bytes[r.phase] += r.bytes;
     }
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+    event_put(r.a);
+    event_put(r.b);
   }
   recs.clear();
 }
