@@ -626,6 +626,9 @@ def test_host_entry_point_chunked_bf16(gpu_lib):
         assert (a.factor(n) - d.factor(n).cpu()).abs().max() <= 1e-8
         assert a.tails[n] == pytest.approx(d.tails[n], rel=1e-9, abs=1e-15 * d.norm2)
     assert a.norm2 == pytest.approx(d.norm2, rel=1e-14)
+    # pageable host memory: the chunk copies are staged by the driver, same result
+    pg = gpu_lib.sthosvd_host(torch.from_numpy(x.copy()), dims, 1e-3, precision="bf16x4")
+    assert pg.ranks == a.ranks and torch.equal(pg.core(), a.core())
     # float32 input takes the same chunked path
     x32 = x.astype(np.float32)
     h32 = gpu_lib.sthosvd_host(torch.from_numpy(x32).pin_memory(), dims, 1e-3, precision="bf16x4")
