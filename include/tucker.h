@@ -157,11 +157,27 @@ TUCKER_API int tucker_sthosvd(const void *X, tucker_dtype dt, const int64_t *dim
  * library's own, and mode 1's Gram runs chunk by chunk as they land (the
  * chunks' Grams are summed), so the copy hides that pass; the result then
  * equals tucker_sthosvd's up to the rounding of that sum (ranks and
- * discarded sums to ~1e-15 relative).  Otherwise one copy on `stream`.
- * Synchronises `stream`.
+ * discarded sums to ~1e-15 relative).  Otherwise one copy, also on the
+ * library's stream, before the compute.  Synchronises `stream`.
  */
 TUCKER_API int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
                         const int *mode_order, tucker_precision prec, void *stream, tucker_result *out);
+
+/*
+ * tucker_sthosvd_host_many -- tucker_sthosvd_host on `count` host tensors of
+ * one shape and dtype, in order, through two device buffers: the copy of
+ * tensor k + 1 runs while tensor k is compressed, so a stream of tensors
+ * costs about the longer of the two per tensor instead of their sum.  Each
+ * result is what tucker_sthosvd_host returns for that tensor alone.
+ *   X_hosts  count host pointers, prod(dims) elements each (pinned memory
+ *            recommended: a pageable copy cannot overlap).
+ *   out      count results, filled in order (out->on_host = 1).
+ * count = 0 does nothing.  On error every result is released and zeroed.
+ * Device memory: two copies of X at a time.  Synchronises `stream`.
+ */
+TUCKER_API int tucker_sthosvd_host_many(const void *const *X_hosts, int count, tucker_dtype dt, const int64_t *dims,
+                                        int N, double eps, const int *mode_order, tucker_precision prec,
+                                        void *stream, tucker_result *out);
 
 /*
  * tucker_reconstruct -- X~ = G x_1 U_1 ... x_N U_N (Eq. reconstruct, Sec. 2.3).

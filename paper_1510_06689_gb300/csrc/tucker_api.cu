@@ -1067,74 +1067,89 @@ static int sthosvd_entry(const void *X, tucker_dtype dt, const int64_t *dims, in
   return st;
 }
 
-int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
-                        const int *mode_order, tucker_precision prec, void *stream, tucker_result *out) {
-  g_err[0] = 0;
-  if (!out || !X_host) {
-    set_error("X_host and out must be non-null");
-    return TUCKER_EINVAL;
-  }
-  memset(out, 0, sizeof *out);
-  if (dt != TUCKER_F64 && dt != TUCKER_F32) {
-    set_error("unknown dtype %d", (int)dt);
-    return TUCKER_EINVAL;
-  }
-  TK_CHECK(check_dims(dims, N));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int64_t I = 1;
-  for (int n = 0; n < N; ++n) I *= dims[n];
-  DevBuf dX;
-  TK_CHECK(dX.alloc(elem_size(dt) * I, s));
-  // With the BF16 digits and mode 1 first, X goes over in up to eight
-  // chunks of whole 512-column groups of its first unfolding on a copy
-  // stream of its own, and mode 1's Gram starts on each chunk as it lands
-  // (the copy hides the first pass over X); otherwise in one copy.
-  int order[TUCKER_MAX_MODES];
-  TK_CHECK(check_order(mode_order, N, order));
-  HostFeed feed;
+// ---------------------------------------------------------------------------
+// host entry points: X copied in, results copied out
+// ---------------------------------------------------------------------------
+// The copy of a host tensor goes on a stream of the library's own, one event
+// per chunk.  With the BF16 digits and mode 1 first (and at least two
+// 512-column groups) it goes in up to eight chunks of whole groups of the
+// mode-1 unfolding and mode 1's Gram starts on each chunk as it lands
+// (feed->n = chunks); otherwise in one piece, marked by ev[0] (feed->n = 0:
+// the compute waits for all of it).
+struct Copier {
   cudaStream_t cs = nullptr;
+  cudaEvent_t ev[2][kMaxFeedChunks] = {};  // one set per device buffer
+  bool open() {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      cs = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    for (auto &set : ev)
+      for (auto &e : set)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          e = nullptr;
+          cudaGetLastError();
+          close();
+          return false;
+        }
+    return true;
+  }
+  // stream and events are released once their pending work has completed
+  void close() {
+    for (auto &set : ev)
+      for (auto &e : set)
+        if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+    for (auto &set : ev)
+      for (auto &e : set) e = nullptr;
+  }
+};
+
+// Issues X_host -> dX on the copier's stream with event set `set`; fills
+// *feed and *last (the event after the whole copy).
+static int issue_copy(const void *X_host, void *dX, tucker_dtype dt, const int64_t *dims, int64_t I,
+                      tucker_precision prec, const int *order, Copier &cp, int set, HostFeed *feed,
+                      cudaEvent_t *last) {
   const int64_t B0 = I / dims[0];
+  const size_t col_bytes = elem_size(dt) * (size_t)dims[0];
+  feed->n = 0;
   if (prec == TUCKER_PREC_BF16X4 && order[0] == 0 && B0 >= 2 * 512) {
     // chunks of ceil(B0 / 8) columns rounded up to whole groups: at most eight
     const int64_t per = std::max<int64_t>(512, ((B0 + kMaxFeedChunks - 1) / kMaxFeedChunks + 511) / 512 * 512);
     const int nc = (int)((B0 + per - 1) / per);
-    bool ok = nc >= 2 && nc <= kMaxFeedChunks &&
-              cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
-    for (int c = 0; c < nc && ok; ++c) {
-      ok = cudaEventCreateWithFlags(&feed.ev[c], cudaEventDisableTiming) == cudaSuccess;
-      if (ok) feed.n = c + 1;
-    }
-    cudaEvent_t ready = nullptr;  // dX's stream-ordered allocation is usable on the copy stream
-    ok = ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventRecord(ready, s) == cudaSuccess && cudaStreamWaitEvent(cs, ready, 0) == cudaSuccess;
-    if (ready) cudaEventDestroy(ready);
-    const size_t col_bytes = elem_size(dt) * (size_t)dims[0];
-    for (int c = 0; c < nc && ok; ++c) {
-      feed.col[c] = per * c;
-      feed.col[c + 1] = std::min(B0, per * (c + 1));
-      const size_t off = col_bytes * (size_t)feed.col[c], bytes = col_bytes * (size_t)(feed.col[c + 1] - feed.col[c]);
-      ok = cudaMemcpyAsync(static_cast<char *>(dX.p) + off, static_cast<const char *>(X_host) + off, bytes,
-                           cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-           cudaEventRecord(feed.ev[c], cs) == cudaSuccess;
-    }
-    if (!ok) {  // fall back to one copy on the caller's stream, after whatever was issued
-      cudaGetLastError();
-      if (cs) cudaStreamSynchronize(cs);
-      for (int c = 0; c < feed.n; ++c) cudaEventDestroy(feed.ev[c]);
-      if (cs) cudaStreamDestroy(cs);
-      cs = nullptr;
-      feed.n = 0;
+    if (nc >= 2 && nc <= kMaxFeedChunks) {
+      for (int c = 0; c < nc; ++c) {
+        feed->col[c] = per * c;
+        feed->col[c + 1] = std::min(B0, per * (c + 1));
+        feed->ev[c] = cp.ev[set][c];
+        const size_t off = col_bytes * (size_t)feed->col[c];
+        const size_t bytes = col_bytes * (size_t)(feed->col[c + 1] - feed->col[c]);
+        TK_CUDA(cudaMemcpyAsync(static_cast<char *>(dX) + off, static_cast<const char *>(X_host) + off, bytes,
+                                cudaMemcpyHostToDevice, cp.cs));
+        TK_CUDA(cudaEventRecord(cp.ev[set][c], cp.cs));
+      }
+      feed->n = nc;
+      *last = cp.ev[set][nc - 1];
+      return TUCKER_OK;
     }
   }
-  if (!cs) TK_CUDA(cudaMemcpyAsync(dX.p, X_host, elem_size(dt) * I, cudaMemcpyHostToDevice, s));
+  TK_CUDA(cudaMemcpyAsync(dX, X_host, elem_size(dt) * I, cudaMemcpyHostToDevice, cp.cs));
+  TK_CUDA(cudaEventRecord(cp.ev[set][0], cp.cs));
+  *last = cp.ev[set][0];
+  return TUCKER_OK;
+}
+
+// The ST-HOSVD of the tensor in dX once its copy (feed, last) has landed,
+// with core and factors copied to one pinned host block (out->on_host = 1).
+static int sthosvd_to_host(void *dX, tucker_dtype dt, const int64_t *dims, int N, double eps, const int *mode_order,
+                           tucker_precision prec, cudaStream_t s, const HostFeed *feed, cudaEvent_t last,
+                           tucker_result *out) {
+  memset(out, 0, sizeof *out);
+  if (feed->n == 0 && last) TK_CUDA(cudaStreamWaitEvent(s, last, 0));
   tucker_result dres;
-  int st = sthosvd_entry(dX.p, dt, dims, N, eps, mode_order, prec, stream, &dres, cs ? &feed : nullptr);
-  if (cs) {
-    // X's buffer is freed on the caller's stream: after every copy, whatever path ran
-    cudaStreamWaitEvent(s, feed.ev[feed.n - 1], 0);
-    for (int c = 0; c < feed.n; ++c) cudaEventDestroy(feed.ev[c]);
-    cudaStreamDestroy(cs);
-  }
+  const int st = sthosvd_entry(dX, dt, dims, N, eps, mode_order, prec, s, &dres, feed->n > 0 ? feed : nullptr);
   if (st != TUCKER_OK) return st;
   *out = dres;
   out->on_host = 1;
@@ -1175,6 +1190,97 @@ int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims
     return hb ? TUCKER_ECUDA : TUCKER_ENOMEM;
   }
   return TUCKER_OK;
+}
+
+static int check_host_args(const void *const *X, int count, tucker_dtype dt, const int64_t *dims, int N,
+                           const int *mode_order, tucker_result *out, int *order) {
+  if (!out || !X || count < 0) {
+    set_error("X_host and out must be non-null and count >= 0");
+    return TUCKER_EINVAL;
+  }
+  memset(out, 0, sizeof(tucker_result) * (size_t)count);
+  for (int k = 0; k < count; ++k)
+    if (!X[k]) {
+      set_error("host tensor %d is NULL", k);
+      return TUCKER_EINVAL;
+    }
+  if (dt != TUCKER_F64 && dt != TUCKER_F32) {
+    set_error("unknown dtype %d", (int)dt);
+    return TUCKER_EINVAL;
+  }
+  TK_CHECK(check_dims(dims, N));
+  return check_order(mode_order, N, order);
+}
+
+// `count` host tensors of one shape in turn through two device buffers: the
+// copy of tensor k + 1 runs while tensor k is compressed.
+static int sthosvd_host_run(const void *const *X, int count, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                            const int *mode_order, tucker_precision prec, cudaStream_t s, tucker_result *out) {
+  int order[TUCKER_MAX_MODES];
+  TK_CHECK(check_host_args(X, count, dt, dims, N, mode_order, out, order));
+  if (count == 0) return TUCKER_OK;
+  int64_t I = 1;
+  for (int n = 0; n < N; ++n) I *= dims[n];
+  DevBuf dX[2];
+  const int nbuf = count > 1 ? 2 : 1;
+  for (int b = 0; b < nbuf; ++b) TK_CHECK(dX[b].alloc(elem_size(dt) * I, s));
+  Copier cp;
+  if (!cp.open()) {  // no copy stream: copy and compress one tensor at a time on the caller's stream
+    for (int k = 0; k < count; ++k) {
+      TK_CUDA(cudaMemcpyAsync(dX[0].p, X[k], elem_size(dt) * I, cudaMemcpyHostToDevice, s));
+      const HostFeed none;
+      const int st = sthosvd_to_host(dX[0].p, dt, dims, N, eps, mode_order, prec, s, &none, nullptr, out + k);
+      if (st != TUCKER_OK) {
+        for (int j = 0; j < k; ++j) tucker_result_free(out + j);
+        return st;
+      }
+    }
+    return TUCKER_OK;
+  }
+  cudaEvent_t ready = nullptr;  // the buffers' stream-ordered allocations are usable on the copy stream
+  int st = TUCKER_OK;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cp.cs, ready, 0) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("could not order the copy stream after the buffers' allocation");
+    st = TUCKER_ECUDA;
+  }
+  if (ready) cudaEventDestroy(ready);
+  HostFeed feed[2];
+  cudaEvent_t last[2] = {nullptr, nullptr}, issued = nullptr;
+  if (st == TUCKER_OK) st = issue_copy(X[0], dX[0].p, dt, dims, I, prec, order, cp, 0, &feed[0], &last[0]);
+  if (st == TUCKER_OK) issued = last[0];
+  int k = 0;
+  for (; k < count && st == TUCKER_OK; ++k) {
+    const int b = k & 1;
+    // the other buffer's tensor (k - 1) is done: its call returned
+    if (k + 1 < count) {
+      st = issue_copy(X[k + 1], dX[b ^ 1].p, dt, dims, I, prec, order, cp, b ^ 1, &feed[b ^ 1], &last[b ^ 1]);
+      if (st != TUCKER_OK) break;
+      issued = last[b ^ 1];
+    }
+    st = sthosvd_to_host(dX[b].p, dt, dims, N, eps, mode_order, prec, s, &feed[b], last[b], out + k);
+  }
+  // the buffers are freed on the caller's stream: after every copy issued, whatever path ran
+  if (issued) cudaStreamWaitEvent(s, issued, 0);
+  cp.close();
+  if (st != TUCKER_OK)
+    for (int j = 0; j < count; ++j) tucker_result_free(out + j);
+  return st;
+}
+
+int tucker_sthosvd_host(const void *X_host, tucker_dtype dt, const int64_t *dims, int N, double eps,
+                        const int *mode_order, tucker_precision prec, void *stream, tucker_result *out) {
+  g_err[0] = 0;
+  return sthosvd_host_run(&X_host, 1, dt, dims, N, eps, mode_order, prec, static_cast<cudaStream_t>(stream), out);
+}
+
+int tucker_sthosvd_host_many(const void *const *X_hosts, int count, tucker_dtype dt, const int64_t *dims, int N,
+                             double eps, const int *mode_order, tucker_precision prec, void *stream,
+                             tucker_result *out) {
+  g_err[0] = 0;
+  return sthosvd_host_run(X_hosts, count, dt, dims, N, eps, mode_order, prec, static_cast<cudaStream_t>(stream),
+                          out);
 }
 
 int tucker_reconstruct(const tucker_result *r, double *Xhat, void *stream) {

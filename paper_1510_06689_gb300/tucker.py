@@ -29,7 +29,7 @@ EXPORTS = (
     "tucker_last_error", "tucker_launch_count", "tucker_profile_enable", "tucker_profile_read",
     "tucker_gram_noalloc", "tucker_gram_split", "tucker_ttm_split", "tucker_hooi", "tucker_order_flops",
     "tucker_mode_order", "tucker_sthosvd_batched", "tucker_fp64_peak", "tucker_gram_split_e4m3",
-    "tucker_batched_tuning", "tucker_memory_stats", "tucker_memory_trim",
+    "tucker_batched_tuning", "tucker_memory_stats", "tucker_memory_trim", "tucker_sthosvd_host_many",
 )
 EIG_PATHS = ("mixed", "jacobi", "jacobi_fallback")
 ORDER_RULES = {"flops": 0, "ratio": 1, "exhaustive": 2}
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
     sig = {
         "tucker_sthosvd": (i32, [vp, i32, pi64, i32, dbl, pi32, i32, vp, pres]),
         "tucker_sthosvd_host": (i32, [vp, i32, pi64, i32, dbl, pi32, i32, vp, pres]),
+        "tucker_sthosvd_host_many": (i32, [ctypes.POINTER(vp), i32, i32, pi64, i32, dbl, pi32, i32, vp, pres]),
         "tucker_reconstruct": (i32, [pres, vp, vp]),
         "tucker_reconstruct_sub": (i32, [pres, pi64, pi64, vp, vp]),
         "tucker_hooi": (i32, [vp, i32, pi64, i32, dbl, i32, dbl, i32, vp, pres, pi32, pdbl]),
@@ -267,6 +268,30 @@ def sthosvd_host(x, dims, eps, mode_order=None, precision="fp64", stream=None):
                                    _order_arg(mode_order, len(dims)), PREC[precision], _stream(stream),
                                    ctypes.byref(raw)))
     return Result(raw)
+
+
+def sthosvd_host_many(xs, dims, eps, mode_order=None, precision="fp64", stream=None):
+    """Algorithm 1 on several host tensors of one shape in turn, the copy of the
+    next running while the current one is compressed; results on the host."""
+    lib = load()
+    dims, cd = _dims_arg(dims)
+    if not xs:
+        return []
+    code = _dtype_code(xs[0])
+    for x in xs:
+        if x.is_cuda or not x.is_contiguous() or x.numel() != math.prod(dims) or _dtype_code(x) != code:
+            raise ValueError("xs must be contiguous host tensors of one dtype with prod(dims) elements each")
+    count = len(xs)
+    ptrs = (ctypes.c_void_p * count)(*[x.data_ptr() for x in xs])
+    raws = (_Result * count)()
+    _check(lib.tucker_sthosvd_host_many(ptrs, count, code, cd, len(dims), float(eps),
+                                        _order_arg(mode_order, len(dims)), PREC[precision], _stream(stream), raws))
+    out = []
+    for i in range(count):
+        r = _Result()
+        ctypes.memmove(ctypes.byref(r), ctypes.byref(raws[i]), ctypes.sizeof(_Result))
+        out.append(Result(r))
+    return out
 
 
 def reconstruct(result, out=None, stream=None):

@@ -662,6 +662,28 @@ def test_host_entry_point_chunked_other_grams(gpu_lib, dims):
     assert a.norm2 == pytest.approx(d.norm2, rel=1e-14)
 
 
+@pytest.mark.parametrize("precision", ["bf16x4", "fp64"])
+def test_host_many_matches_single_calls(gpu_lib, precision):
+    """tucker_sthosvd_host_many on three different tensors (two device buffers
+    in turn, each copy running while the previous tensor is compressed):
+    every result is the single host call's, bit for bit."""
+    import torch
+
+    dims, ranks = (64, 40, 30, 6), (6, 5, 4, 3)
+    xs = [torch.from_numpy(tucker_tensor_np(dims, ranks, seed=30 + k, noise=1e-4)).pin_memory() for k in range(3)]
+    many = gpu_lib.sthosvd_host_many(xs, dims, 1e-3, precision=precision)
+    assert len(many) == 3
+    for x, m in zip(xs, many):
+        one = gpu_lib.sthosvd_host(x, dims, 1e-3, precision=precision)
+        assert m.on_host and m.ranks == one.ranks
+        assert torch.equal(m.core(), one.core())
+        for n in range(len(dims)):
+            assert torch.equal(m.factor(n), one.factor(n))
+    assert gpu_lib.sthosvd_host_many([], dims, 1e-3) == []
+    single = gpu_lib.sthosvd_host_many(xs[:1], dims, 1e-3, precision=precision)
+    assert torch.equal(single[0].core(), many[0].core())
+
+
 def test_results_return_their_memory(gpu_lib):
     """A freed device result goes back to the stream-ordered pool and a freed
     host result's pinned block to the host block cache, so repeated calls hold
