@@ -181,17 +181,25 @@ class Result:
         self._raw = raw
         n = raw.N
         self.N = n
-        self.dims = tuple(raw.dims[i] for i in range(n))
-        self.ranks = tuple(raw.ranks[i] for i in range(n))
-        self.mode_order = tuple(raw.mode_order[i] for i in range(n))
-        self.sweeps = tuple(raw.sweeps[i] for i in range(n))
-        self.tails = tuple(raw.tail[i] for i in range(n))
+        self.dims = tuple(raw.dims[:n])
+        self.ranks = tuple(raw.ranks[:n])
+        self.mode_order = tuple(raw.mode_order[:n])
+        self.sweeps = tuple(raw.sweeps[:n])
+        self.tails = tuple(raw.tail[:n])
         self.norm2 = raw.norm2_x
         self.threshold = raw.threshold
         self.on_host = bool(raw.on_host)
-        self.eigvals = [_doubles(raw.eigvals[i], self.dims[i]) for i in range(n)]
-        self.eig_paths = tuple(EIG_PATHS[raw.eig_path[i]] for i in range(n))
-        self.eig_resolved = tuple(raw.eig_resolved[i] for i in range(n))
+        self._eigvals = None
+        self.eig_paths = tuple(EIG_PATHS[p] for p in raw.eig_path[:n])
+        self.eig_resolved = tuple(raw.eig_resolved[:n])
+
+    @property
+    def eigvals(self):
+        """The I_n eigenvalues of each mode's Gram, descending (read from the result on first use)."""
+        if self._eigvals is None:
+            raw = self._raw
+            self._eigvals = [_doubles(raw.eigvals[i], self.dims[i]) if raw is not None else [] for i in range(self.N)]
+        return self._eigvals
 
     @property
     def raw(self):
@@ -220,6 +228,7 @@ class Result:
 
     def free(self):
         if self._raw is not None and _lib is not None:
+            self.eigvals  # noqa: B018 - read before the library releases them (they stay readable)
             _lib.tucker_result_free(ctypes.byref(self._raw))
         self._raw = None
 
@@ -286,12 +295,7 @@ def sthosvd_host_many(xs, dims, eps, mode_order=None, precision="fp64", stream=N
     raws = (_Result * count)()
     _check(lib.tucker_sthosvd_host_many(ptrs, count, code, cd, len(dims), float(eps),
                                         _order_arg(mode_order, len(dims)), PREC[precision], _stream(stream), raws))
-    out = []
-    for i in range(count):
-        r = _Result()
-        ctypes.memmove(ctypes.byref(r), ctypes.byref(raws[i]), ctypes.sizeof(_Result))
-        out.append(Result(r))
-    return out
+    return [Result(raws[i]) for i in range(count)]
 
 
 def reconstruct(result, out=None, stream=None):
@@ -328,20 +332,18 @@ def sthosvd_batched(xs, dims_list, eps, precision="fp64", workers=0, stream=None
     if any(len(d) != n for d in dims_list):
         raise ValueError("every tensor needs the same number of modes")
     code = _dtype_code(xs[0])
+    addrs = []
     for x, d in zip(xs, dims_list):
         if _dtype_code(x) != code or x.numel() != math.prod(d):
             raise ValueError("tensors need one dtype and prod(dims) elements each")
-    ptrs = (ctypes.c_void_p * count)(*[_dev_ptr(x, "x").value for x in xs])
+        addrs.append(_dev_ptr(x, "x").value)
+    ptrs = (ctypes.c_void_p * count)(*addrs)
     flat = (ctypes.c_int64 * (count * n))(*[int(v) for d in dims_list for v in d])
     raws = (_Result * count)()
     _check(lib.tucker_sthosvd_batched(ptrs, code, flat, n, count, float(eps), PREC[precision], int(workers),
                                       _stream(stream), raws))
-    out = []
-    for i in range(count):
-        r = _Result()
-        ctypes.memmove(ctypes.byref(r), ctypes.byref(raws[i]), ctypes.sizeof(_Result))
-        out.append(Result(r))
-    return out
+    # each Result views its element of `raws` (the view keeps the array alive)
+    return [Result(raws[i]) for i in range(count)]
 
 
 def order_flops(dims, ranks, order=None):
